@@ -1,0 +1,154 @@
+/*
+ * pdmk.h -- C ABI of the B300 periodic DMK library (libpdmk.so).
+ *
+ * The library evaluates periodic Coulomb lattice sums (paper Eq. (1.1)): for N point
+ * charges q_j at y_j in the unit cell spanned by the columns a_1..a_d of L (d = 2 or 3),
+ *
+ *   Phi(x) = sum_{n in Z^d} sum_j q_j G(x - y_j - L n),
+ *   G(r) = -log(r)/(2 pi) (2D),  1/(4 pi r) (3D)          (Eq. (1.2))
+ *
+ * with the n = 0 self term excluded at a target that coincides with its source, under
+ * the tin-foil convention (the k = 0 Fourier mode is zero, Sec. 1).  For non-neutral
+ * charges the returned potential is the zero-mean one (uniform neutralising background),
+ * so the result is well defined for any charges.  The gradient is grad_x Phi (the field
+ * is its negative).
+ *
+ * The method is the periodic dual-space multilevel kernel splitting of Algorithm 1:
+ * the near field G - W_0 by a free-space DMK on the extended root grid (inner block
+ * covering the cell plus a one-cube halo of image sources, Sec. 3.3-3.5), and the smooth
+ * periodic W_0 by spreading, FFT, diagonal scaling with k = 0 dropped, inverse FFT and
+ * interpolation (Sec. 3.6-3.7), followed by the self-interaction correction (Sec. 3.8).
+ *
+ * Conventions common to all entry points
+ *  - Every function returns PDMK_OK (0) or a negative PDMK_ERR_* code; no exception,
+ *    abort or trap crosses the ABI.  pdmk_strerror() names a code.
+ *  - The caller owns every array it passes.  The plan owns its device buffers.
+ *  - Positions are row-major (n x d doubles); L is column-major (column j = a_j).
+ *  - `where` says where a pointer lives: PDMK_HOST (pageable or pinned host memory) or
+ *    PDMK_DEVICE (device memory of the plan's GPU).
+ *  - Work is enqueued on the plan's CUDA stream (pdmk_opts.stream).  With device
+ *    pointers pdmk_eval is asynchronous; with host pointers it returns after the results
+ *    are in host memory.  A plan must not be used from two threads at once.
+ */
+#ifndef PDMK_H
+#define PDMK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define PDMK_OK 0
+#define PDMK_ERR_BAD_ARG (-1)          /* null pointer, d not 2/3, n < 0, bad option   */
+#define PDMK_ERR_SINGULAR_LATTICE (-2) /* |det L| <= 1e-14 prod |a_i|                  */
+#define PDMK_ERR_NON_NEUTRAL (-3)      /* |sum q| > 1e-12 sum |q| with neutrality = 0  */
+#define PDMK_ERR_BAD_EPS (-4)          /* eps outside [1e-12, 1e-2]                     */
+#define PDMK_ERR_NONFINITE (-5)        /* NaN or Inf in L, positions or charges         */
+#define PDMK_ERR_OOM (-6)              /* device or host allocation failed              */
+#define PDMK_ERR_CUDA (-7)             /* a CUDA / cuFFT call failed                    */
+#define PDMK_ERR_TIMEOUT (-8)          /* a bounded device wait expired                 */
+#define PDMK_ERR_NOT_READY (-9)        /* pdmk_eval before pdmk_set_sources             */
+#define PDMK_ERR_INTERNAL (-10)        /* a consistency check inside the library failed */
+#define PDMK_ERR_TOO_LARGE (-11)       /* a size exceeds a documented maximum           */
+
+#define PDMK_HOST 0
+#define PDMK_DEVICE 1
+
+#define PDMK_FP64 0  /* every stage in FP64                                         */
+#define PDMK_MIXED 1 /* FP32 bulk with compensated sums; FP64 set-up, scaling, assembly */
+
+typedef struct pdmk_plan_s* pdmk_plan;
+
+/* Options.  Zero / negative numeric fields select the defaults noted. */
+typedef struct {
+    double kappa;   /* root box side r_c = L_min / kappa (Algorithm 1 step 1); <= 0: Table 1 */
+    int n_s;        /* leaf capacity (Algorithm 1 step 2); <= 0: Table 1                     */
+    int precision;  /* PDMK_FP64 or PDMK_MIXED                                               */
+    int window_w;   /* spreading window width in grid points; <= 0: ceil(2 c / pi)           */
+    int n_proxy;    /* Chebyshev proxy points per dimension p; <= 0: from eps                */
+    int n_pw;       /* plane-wave half-width K (nodes -K..K per dimension); <= 0: from eps   */
+    int max_depth;  /* deepest tree level; < 0: 30; 0: every root box is a leaf              */
+    int neutrality; /* 0: require |sum q| <= 1e-12 sum|q|; 1: allow (zero-mean potential)     */
+    int profile;    /* 1: record per-stage CUDA-event times (pdmk_stage_times)               */
+    void* stream;   /* cudaStream_t for all work; NULL: the legacy default stream            */
+} pdmk_opts;
+
+/* Fills *opts with the defaults (all fields "auto", FP64, neutrality allowed). */
+void pdmk_default_opts(pdmk_opts* opts);
+
+/*
+ * Creates a plan for lattice L (d x d, column-major, host memory) and target relative L2
+ * precision eps in [1e-12, 1e-2].  Orients L to upper-triangular form (Sec. 3.2, Eq. (3.4)),
+ * picks r_c and n_s, sizes the root grid (Eq. (3.10), (3.12)) and the Fourier grid
+ * (Eq. (3.15)), and computes the prolate tables in FP64.  opts may be NULL (defaults).
+ * Errors: BAD_ARG, BAD_EPS, SINGULAR_LATTICE, NONFINITE, CUDA, OOM.
+ */
+int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, pdmk_plan* out);
+
+/*
+ * Sets the sources (positions y, n x d; charges q, n) and builds everything that depends on
+ * them: fractional wrap, image sources filling the extended domain (Sec. 3.4), the adaptive
+ * level-restricted tree and its lists (Algorithm 1 step 2), and the device layouts.  The
+ * targets of pdmk_eval are these sources.  Inputs may be freed on return.
+ * Errors: BAD_ARG, NONFINITE, NON_NEUTRAL, OOM, CUDA.
+ */
+int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, const double* q, int where);
+
+/*
+ * Replaces the charges (n values, the same n and order as pdmk_set_sources) without
+ * rebuilding the tree.  Errors: NOT_READY, NONFINITE, NON_NEUTRAL, CUDA.
+ */
+int pdmk_set_charges(pdmk_plan plan, const double* q, int where);
+
+/*
+ * Evaluates the periodic potential (pot, n) and, if grad is not NULL, its gradient
+ * (grad, n x d row-major) at every source, self term excluded (Algorithm 1 steps 3-5):
+ * near-field DMK, far-field five-step procedure, assembly and self-correction.
+ * Outputs are in the caller's source order and frame.  Errors: NOT_READY, CUDA, TIMEOUT.
+ */
+int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where);
+
+/* Per-stage device times (ms) of the last pdmk_eval when opts.profile = 1.  names/ms
+ * receive up to cap entries; returns the number of stages (or a negative error).     */
+int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, int cap);
+
+/* Plan facts (sizes, counts) for reporting and roofline accounting. */
+typedef struct {
+    int d;
+    double eps, c, rc, V, kappa;
+    int n_s, window_w, n_proxy, n_pw, precision;
+    int M[3];           /* Fourier grid                        */
+    int nroot[3];       /* extended root grid (m_i + 2)         */
+    int64_t n;          /* sources                              */
+    int64_t n_images;   /* sources + images in the extended domain (N') */
+    int nboxes, nleaves, depth, ntarget_leaves;
+    int n_pw_boxes_out, n_pw_boxes_in;
+    int64_t near_pairs; /* target-source pairs visited by the direct near field */
+    int64_t near_pairs_in; /* of those, pairs inside the residual kernel's support (counted
+                              on the first evaluation after pdmk_set_sources when profile = 1) */
+    int64_t device_bytes;
+} pdmk_info;
+int pdmk_get_info(pdmk_plan plan, pdmk_info* info);
+
+/* Destroys the plan and frees its device memory (NULL is a no-op). */
+void pdmk_plan_destroy(pdmk_plan plan);
+
+/* Static message for an error code. */
+const char* pdmk_strerror(int code);
+
+/*
+ * Debug / verification access to the FP64 kernel tables (host only, no GPU needed).
+ * kind: 0 = residual kernel R_1(t) (scale-free, t = r/h in (0, 1]), 1 = dR_1/dt,
+ *       2 = hat-w(x) (transform of the smoothing density), 3 = bandwidth c (x ignored),
+ *       4 = self value W_1(0) (3D: psi(0)/(4 pi c0); 2D: W_1(0)), 5 = window F(s),
+ *       6 = window transform at grid frequency x.
+ * Returns 0 and writes *value, or a negative error.
+ */
+int pdmk_kernel_table_eval(int d, double eps, int kind, double x, double* value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDMK_H */

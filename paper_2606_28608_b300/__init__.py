@@ -1,0 +1,220 @@
+"""Python binding of libpdmk.so (periodic DMK lattice sums on B300).
+
+Argument marshalling only: every step of an evaluation runs in the library's CUDA
+kernels (and cuFFT).  PyTorch supplies device memory and the current stream.  If the
+compiled library is missing the import of ``lib()`` raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpdmk.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "pdmk.h")
+
+PDMK_HOST, PDMK_DEVICE = 0, 1
+PDMK_FP64, PDMK_MIXED = 0, 1
+
+
+class PdmkError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {code} ({_strerror(code)})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("n_s", ctypes.c_int), ("precision", ctypes.c_int),
+                ("window_w", ctypes.c_int), ("n_proxy", ctypes.c_int), ("n_pw", ctypes.c_int),
+                ("max_depth", ctypes.c_int), ("neutrality", ctypes.c_int), ("profile", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("eps", ctypes.c_double), ("c", ctypes.c_double),
+                ("rc", ctypes.c_double), ("V", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("n_s", ctypes.c_int), ("window_w", ctypes.c_int), ("n_proxy", ctypes.c_int),
+                ("n_pw", ctypes.c_int), ("precision", ctypes.c_int), ("M", ctypes.c_int * 3),
+                ("nroot", ctypes.c_int * 3), ("n", ctypes.c_int64), ("n_images", ctypes.c_int64),
+                ("nboxes", ctypes.c_int), ("nleaves", ctypes.c_int), ("depth", ctypes.c_int),
+                ("ntarget_leaves", ctypes.c_int), ("n_pw_boxes_out", ctypes.c_int),
+                ("n_pw_boxes_in", ctypes.c_int), ("near_pairs", ctypes.c_int64), ("near_pairs_in", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpdmk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2606_28608_b300/build.py (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        L.pdmk_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.pdmk_default_opts.restype = None
+        L.pdmk_plan_create.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(P)]
+        L.pdmk_plan_create.restype = ctypes.c_int
+        L.pdmk_set_sources.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int]
+        L.pdmk_set_sources.restype = ctypes.c_int
+        L.pdmk_set_charges.argtypes = [P, P, ctypes.c_int]
+        L.pdmk_set_charges.restype = ctypes.c_int
+        L.pdmk_eval.argtypes = [P, P, P, ctypes.c_int]
+        L.pdmk_eval.restype = ctypes.c_int
+        L.pdmk_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.pdmk_stage_times.restype = ctypes.c_int
+        L.pdmk_get_info.argtypes = [P, ctypes.POINTER(Info)]
+        L.pdmk_get_info.restype = ctypes.c_int
+        L.pdmk_plan_destroy.argtypes = [P]
+        L.pdmk_plan_destroy.restype = None
+        L.pdmk_strerror.argtypes = [ctypes.c_int]
+        L.pdmk_strerror.restype = ctypes.c_char_p
+        L.pdmk_kernel_table_eval.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_double)]
+        L.pdmk_kernel_table_eval.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _strerror(code):
+    try:
+        return lib().pdmk_strerror(code).decode()
+    except Exception:  # noqa: BLE001
+        return "?"
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared by include/pdmk.h."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pdmk_[a-z_0-9]+)\s*\(", txt)))
+
+
+def kernel_table(d: int, eps: float, kind: int, x: float = 0.0) -> float:
+    """FP64 kernel-table query (host only): see pdmk_kernel_table_eval in include/pdmk.h."""
+    v = ctypes.c_double()
+    rc = lib().pdmk_kernel_table_eval(int(d), float(eps), int(kind), float(x), ctypes.byref(v))
+    if rc != 0:
+        raise PdmkError(rc, "pdmk_kernel_table_eval")
+    return v.value
+
+
+def _is_torch(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except ImportError:
+        return False
+
+
+class Plan:
+    """A periodic DMK plan for lattice L (columns = lattice vectors) and precision eps."""
+
+    def __init__(self, L, eps: float, *, precision: str = "fp64", kappa: float = 0.0, n_s: int = 0,
+                 window_w: int = 0, n_proxy: int = 0, n_pw: int = 0, max_depth: int = -1,
+                 neutrality: int = 1, profile: bool = False, stream=None):
+        L = np.ascontiguousarray(np.asarray(L, dtype=np.float64))
+        self.d = L.shape[0]
+        self._L = L
+        o = Opts()
+        lib().pdmk_default_opts(ctypes.byref(o))
+        o.kappa = kappa
+        o.n_s = n_s
+        o.precision = PDMK_MIXED if precision == "mixed" else PDMK_FP64
+        o.window_w = window_w
+        o.n_proxy = n_proxy
+        o.n_pw = n_pw
+        o.max_depth = max_depth
+        o.neutrality = neutrality
+        o.profile = 1 if profile else 0
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        o.stream = stream or None
+        self.opts = o
+        Lc = np.ascontiguousarray(L.T)  # column-major
+        h = ctypes.c_void_p()
+        rc = lib().pdmk_plan_create(self.d, Lc.ctypes.data, float(eps), ctypes.byref(o), ctypes.byref(h))
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_plan_create")
+        self._h = h
+        self.n = 0
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().pdmk_plan_destroy(h)
+            except Exception:  # noqa: BLE001
+                pass
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    def set_sources(self, y, q):
+        if _is_torch(y):
+            assert y.is_cuda and y.dtype.is_floating_point
+            yy = y.contiguous().double()
+            qq = q.contiguous().double()
+            rc = lib().pdmk_set_sources(self._h, yy.shape[0], yy.data_ptr(), qq.data_ptr(), PDMK_DEVICE)
+            n = yy.shape[0]
+        else:
+            yy = np.ascontiguousarray(np.asarray(y, dtype=np.float64).reshape(-1, self.d))
+            qq = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
+            n = yy.shape[0]
+            rc = lib().pdmk_set_sources(self._h, n, yy.ctypes.data, qq.ctypes.data, PDMK_HOST)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_set_sources")
+        self.n = n
+
+    def set_charges(self, q):
+        if _is_torch(q):
+            qq = q.contiguous().double()
+            rc = lib().pdmk_set_charges(self._h, qq.data_ptr(), PDMK_DEVICE)
+        else:
+            qq = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
+            rc = lib().pdmk_set_charges(self._h, qq.ctypes.data, PDMK_HOST)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_set_charges")
+
+    def eval(self, grad: bool = True, out=None):
+        """Host evaluation: returns numpy (pot, grad or None)."""
+        pot = np.empty(self.n, dtype=np.float64)
+        g = np.empty((self.n, self.d), dtype=np.float64) if grad else None
+        rc = lib().pdmk_eval(self._h, pot.ctypes.data, g.ctypes.data if grad else None, PDMK_HOST)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_eval")
+        return pot, g
+
+    def eval_device(self, pot, grad=None):
+        """Device evaluation into torch CUDA tensors (float64), asynchronous on the stream."""
+        rc = lib().pdmk_eval(self._h, pot.data_ptr(), grad.data_ptr() if grad is not None else None, PDMK_DEVICE)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_eval")
+
+    def info(self) -> dict:
+        inf = Info()
+        rc = lib().pdmk_get_info(self._h, ctypes.byref(inf))
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_get_info")
+        out = {}
+        for name, _ in Info._fields_:
+            v = getattr(inf, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+    def stage_times(self) -> dict:
+        names = (ctypes.c_char_p * 32)()
+        ms = (ctypes.c_double * 32)()
+        n = lib().pdmk_stage_times(self._h, names, ms, 32)
+        return {names[i].decode(): ms[i] for i in range(max(n, 0))}

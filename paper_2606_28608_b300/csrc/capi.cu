@@ -1,0 +1,954 @@
+// capi.cu -- the C ABI of include/pdmk.h: plan creation (FP64 host planning), source set-up
+// (images, tree, device layouts) and the evaluation launch sequence on one CUDA stream.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "host_plan.h"
+#include "k_assemble.cuh"
+#include "k_farfield.cuh"
+#include "k_nearfield.cuh"
+#include "k_pw.cuh"
+#include "kernels_common.cuh"
+#include "pdmk.h"
+
+using namespace pdmk;
+
+#define CK(call)                                             \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) {                             \
+            plan_set_msg(plan, cudaGetErrorString(e_));      \
+            return PDMK_ERR_CUDA;                            \
+        }                                                    \
+    } while (0)
+#define CKFFT(call)                                          \
+    do {                                                     \
+        cufftResult r_ = (call);                             \
+        if (r_ != CUFFT_SUCCESS) {                           \
+            plan_set_msg(plan, "cufft failure");             \
+            return PDMK_ERR_CUDA;                            \
+        }                                                    \
+    } while (0)
+
+struct pdmk_plan_s {
+    int d = 3;
+    double eps = 1e-6;
+    pdmk_opts opts{};
+    double c = 0, kappa = 0, beta = 0;
+    int n_s = 0, w = 0, max_depth = 0;
+    Geometry g;
+    KernelTables kt;
+    WindowTables wt;
+    std::vector<double> cA, cB, cW, cWd;  // near-field Chebyshev coefficients (FP64 master copy)
+    int B[3] = {1, 1, 1}, nbin[3] = {1, 1, 1}, P[3] = {1, 1, 1}, Ptot = 1;
+    int64_t ncell = 1, nhalf = 1;
+    cudaStream_t stream = nullptr;
+    bool ready = false;
+    std::string msg;
+    // plan-lifetime device buffers
+    std::vector<void*> plan_allocs, src_allocs;
+    void* d_coefA = nullptr;
+    void* d_coefB = nullptr;
+    void* d_coefW = nullptr;
+    void* d_coefWd = nullptr;
+    double* d_weight = nullptr;
+    void* d_grid = nullptr;
+    void* d_spec = nullptr;
+    double* d_qsums = nullptr;
+    unsigned long long* d_count = nullptr;
+    bool count_pending = false;
+    cufftHandle fft_fwd = 0, fft_inv = 0;
+    bool have_fft = false;
+    // source-dependent device buffers
+    int64_t n = 0, nimg = 0, ntgt = 0, nspread = 0;
+    int nbox = 0, ntleaf = 0, nsub = 0, nbins_tot = 1;
+    void* d_src4 = nullptr;
+    int* d_src_orig = nullptr;
+    void* d_tgt4 = nullptr;
+    void* d_src_lo = nullptr;
+    void* d_tgt_lo = nullptr;
+    int* d_tgt_orig = nullptr;
+    double* d_q_tgt = nullptr;
+    double* d_self_w = nullptr;
+    TLeaf* d_tleaf = nullptr;
+    int* d_list = nullptr;
+    int* d_box_src_begin = nullptr;
+    int* d_box_src_count = nullptr;
+    double* d_box_center = nullptr;
+    int4* d_pt_g0 = nullptr;
+    void* d_pt_dq = nullptr;
+    int* d_spread_orig = nullptr;
+    int4* d_sub = nullptr;
+    int* d_bin_sub_begin = nullptr;
+    void* d_slab = nullptr;
+    int4* d_t_g0 = nullptr;
+    void* d_t_dq = nullptr;
+    double* d_pot_near = nullptr;
+    double* d_grad_near = nullptr;
+    double* d_pot_far = nullptr;
+    double* d_gradu_far = nullptr;
+    double* d_q_user = nullptr;
+    double* d_pot_out = nullptr;
+    double* d_grad_out = nullptr;
+    PwPlan pw;  // plane-wave (difference-kernel) passes
+    // profiling
+    std::vector<cudaEvent_t> ev;
+    std::vector<std::string> stage_names;
+    std::vector<double> stage_ms;
+    pdmk_info info{};
+    int64_t device_bytes = 0;
+};
+
+static void plan_set_msg(pdmk_plan plan, const char* m) {
+    if (plan) plan->msg = m ? m : "";
+}
+
+template <class X>
+static int dalloc(pdmk_plan plan, std::vector<void*>& list, X** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(X));
+    if (e != cudaSuccess) {
+        plan_set_msg(plan, cudaGetErrorString(e));
+        cudaGetLastError();
+        return PDMK_ERR_OOM;
+    }
+    list.push_back(p);
+    plan->device_bytes += int64_t(count * sizeof(X));
+    *out = static_cast<X*>(p);
+    return PDMK_OK;
+}
+#define DALLOC(list, ptr, type, count)                                          \
+    do {                                                                        \
+        type* tmp_ = nullptr;                                                   \
+        int rc_ = dalloc<type>(plan, list, &tmp_, size_t(count));               \
+        if (rc_ != PDMK_OK) return rc_;                                         \
+        ptr = reinterpret_cast<decltype(ptr)>(tmp_);                            \
+    } while (0)
+
+template <class X>
+static int upload(pdmk_plan plan, void* dst, const std::vector<X>& v) {
+    if (v.empty()) return PDMK_OK;
+    CK(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, plan->stream));
+    return PDMK_OK;
+}
+
+static void free_list(std::vector<void*>& l, int64_t* bytes) {
+    for (void* p : l) cudaFree(p);
+    l.clear();
+    (void)bytes;
+}
+
+static size_t tsize(const pdmk_plan plan) { return plan->opts.precision == PDMK_MIXED ? 4 : 8; }
+
+extern "C" void pdmk_default_opts(pdmk_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->kappa = 0;
+    o->n_s = 0;
+    o->precision = PDMK_FP64;
+    o->window_w = 0;
+    o->n_proxy = 0;
+    o->n_pw = 0;
+    o->max_depth = -1;
+    o->neutrality = 1;
+    o->profile = 0;
+    o->stream = nullptr;
+}
+
+extern "C" const char* pdmk_strerror(int code) {
+    switch (code) {
+        case PDMK_OK: return "ok";
+        case PDMK_ERR_BAD_ARG: return "bad argument";
+        case PDMK_ERR_SINGULAR_LATTICE: return "singular lattice";
+        case PDMK_ERR_NON_NEUTRAL: return "charges are not neutral";
+        case PDMK_ERR_BAD_EPS: return "eps outside [1e-12, 1e-2]";
+        case PDMK_ERR_NONFINITE: return "non-finite input";
+        case PDMK_ERR_OOM: return "out of memory";
+        case PDMK_ERR_CUDA: return "CUDA error";
+        case PDMK_ERR_TIMEOUT: return "device wait timed out";
+        case PDMK_ERR_NOT_READY: return "sources not set";
+        case PDMK_ERR_INTERNAL: return "internal consistency check failed";
+        case PDMK_ERR_TOO_LARGE: return "size exceeds the documented maximum";
+        default: return "unknown error";
+    }
+}
+
+// spreading bins: per dimension B <= M - w + 1 (a padded tile never wraps onto itself) and
+// B >= ceil((w - 1)/6) (at most 8 tiles cover a grid cell per dimension); M grows if needed
+static void size_bins(pdmk_plan plan) {
+    const int d = plan->d, w = plan->w;
+    const int Bdef = (d == 2) ? 32 : 8;
+    const int Bmin = std::max(1, (w - 1 + 5) / 6);
+    plan->Ptot = 1;
+    plan->ncell = 1;
+    for (int i = 0; i < 3; ++i) {
+        if (i >= d) {
+            plan->B[i] = 1; plan->nbin[i] = 1; plan->P[i] = 1; plan->g.M[i] = 1;
+            continue;
+        }
+        int M = plan->g.M[i];
+        if (M < Bmin + w - 1) {
+            M = Bmin + w - 1;
+            M += (M & 1);
+            plan->g.M[i] = M;
+        }
+        int B = std::min(Bdef, M - w + 1);
+        B = std::max(B, Bmin);
+        plan->B[i] = B;
+        plan->nbin[i] = (M + B - 1) / B;
+        plan->P[i] = B + w - 1;
+        plan->Ptot *= plan->P[i];
+        plan->ncell *= M;
+    }
+    plan->nhalf = int64_t(plan->g.M[0] / 2 + 1) * plan->g.M[1] * (d == 3 ? plan->g.M[2] : 1);
+    plan->nbins_tot = plan->nbin[0] * plan->nbin[1] * plan->nbin[2];
+}
+
+// FP64 far-field weights for the half spectrum (Eq. (3.14)-(3.15a) with the window
+// deconvolution of both NUFFT halves folded in); zero at m = 0 and on Nyquist planes
+static std::vector<double> far_weights(pdmk_plan plan) {
+    const int d = plan->d;
+    const Geometry& g = plan->g;
+    std::vector<double> ph[3];
+    for (int i = 0; i < d; ++i) {
+        ph[i].resize(g.M[i]);
+        for (int j = 0; j < g.M[i]; ++j) {
+            int m = j <= g.M[i] / 2 ? j : j - g.M[i];
+            ph[i][j] = plan->wt.ft(double(m) / g.M[i]);
+        }
+    }
+    const int Mh0 = g.M[0] / 2 + 1;
+    std::vector<double> wt(size_t(plan->nhalf), 0.0);
+    const int M2 = d == 3 ? g.M[2] : 1;
+    for (int j2 = 0; j2 < M2; ++j2)
+        for (int j1 = 0; j1 < g.M[1]; ++j1)
+            for (int j0 = 0; j0 < Mh0; ++j0) {
+                int jj[3] = {j0, j1, j2};
+                int m[3] = {0, 0, 0};
+                bool nyq = false, zero = true;
+                for (int i = 0; i < d; ++i) {
+                    int Mi = g.M[i];
+                    if (jj[i] == Mi / 2) nyq = true;
+                    m[i] = jj[i] < Mi / 2 ? jj[i] : jj[i] - Mi;
+                    if (i == 0) m[i] = jj[i];
+                    zero &= (m[i] == 0);
+                }
+                double val = 0;
+                if (!nyq && !zero) {
+                    double k2 = 0;
+                    for (int b = 0; b < d; ++b) {
+                        double s = 0;
+                        for (int a = 0; a < d; ++a) s += g.Rinv[a * d + b] * m[a];
+                        s *= 2.0 * kPi;
+                        k2 += s * s;
+                    }
+                    double kk = std::sqrt(k2);
+                    // only modes inside the active ball |k| <= c / r_c carry weight (Sec. 3.6);
+                    // beyond it hat-w is below eps while the window deconvolution grows
+                    double W0 = (kk * g.rc <= plan->c) ? plan->kt.what(kk * g.rc) / k2 : 0.0;
+                    double den = g.V;
+                    for (int i = 0; i < d; ++i) {
+                        double f = ph[i][jj[i]];
+                        den *= f * f;
+                    }
+                    val = W0 / den;
+                }
+                wt[(size_t(j2) * g.M[1] + j1) * Mh0 + j0] = val;
+            }
+    return wt;
+}
+
+extern "C" int pdmk_kernel_table_eval(int d, double eps, int kind, double x, double* value) {
+    if ((d != 2 && d != 3) || !value) return PDMK_ERR_BAD_ARG;
+    if (!(eps >= 1e-12 && eps <= 1e-2)) return PDMK_ERR_BAD_EPS;
+    // tables are cached per (d, eps): building one takes a few hundred milliseconds
+    static std::mutex mu;
+    static std::map<std::pair<int, double>, KernelTables> cache;
+    KernelTables kt;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find({d, eps});
+        if (it == cache.end()) it = cache.emplace(std::make_pair(d, eps), make_kernel_tables(d, eps, 1e-15)).first;
+        kt = it->second;
+    }
+    switch (kind) {
+        case 0: {
+            double t = x, s = t * t;
+            if (!(t > 0 && t <= 1)) return PDMK_ERR_BAD_ARG;
+            *value = (d == 3) ? (1.0 - t * kt.A.eval(s)) / (4 * kPi * t) : -std::log(s) / (4 * kPi) - kt.A.eval(s);
+            return PDMK_OK;
+        }
+        case 1: {
+            double t = x, s = t * t;
+            if (!(t > 0 && t <= 1)) return PDMK_ERR_BAD_ARG;
+            // dR/dt (scale-free): 3D -(1 - tA + tB)/(4 pi t^2); 2D -sqrt(1-s) B/(2 pi t)
+            *value = (d == 3) ? -(1.0 - t * kt.A.eval(s) + t * kt.B.eval(s)) / (4 * kPi * s)
+                              : -std::sqrt(std::max(1.0 - s, 0.0)) * kt.B.eval(s) / (2 * kPi * t);
+            return PDMK_OK;
+        }
+        case 2: *value = kt.what(x); return PDMK_OK;
+        case 3: *value = kt.psi.c; return PDMK_OK;
+        case 4: *value = kt.self_coef; return PDMK_OK;
+        case 5: *value = kt.rhat0; return PDMK_OK;
+        default: return PDMK_ERR_BAD_ARG;
+    }
+}
+
+extern "C" int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, pdmk_plan* out) {
+    if (!out || !L || (d != 2 && d != 3)) return PDMK_ERR_BAD_ARG;
+    *out = nullptr;
+    if (!(eps >= 1e-12 && eps <= 1e-2)) return PDMK_ERR_BAD_EPS;
+    for (int i = 0; i < d * d; ++i)
+        if (!std::isfinite(L[i])) return PDMK_ERR_NONFINITE;
+    pdmk_plan plan = new (std::nothrow) pdmk_plan_s();
+    if (!plan) return PDMK_ERR_OOM;
+    if (opts) plan->opts = *opts; else pdmk_default_opts(&plan->opts);
+    if (plan->opts.precision != PDMK_FP64 && plan->opts.precision != PDMK_MIXED) {
+        delete plan;
+        return PDMK_ERR_BAD_ARG;
+    }
+    plan->d = d;
+    plan->eps = eps;
+    plan->stream = static_cast<cudaStream_t>(plan->opts.stream);
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    double fit_tol = mixed ? std::max(eps * 1e-3, 2e-9) : std::max(eps * 1e-4, 1e-15);
+    plan->kt = make_kernel_tables(d, eps, fit_tol);
+    plan->c = plan->kt.psi.c;
+    double kappa;
+    int ns;
+    Geometry tmp;
+    int rc = make_geometry(d, L, 1.0, plan->c, &tmp);
+    if (rc != PDMK_OK) { delete plan; return rc; }
+    table1_defaults(d, eps, &tmp, L, &kappa, &ns);
+    plan->kappa = plan->opts.kappa > 0 ? plan->opts.kappa : kappa;
+    plan->n_s = plan->opts.n_s > 0 ? plan->opts.n_s : ns;
+    plan->max_depth = plan->opts.max_depth < 0 ? 30 : std::min(plan->opts.max_depth, 30);
+    rc = make_geometry(d, L, plan->kappa, plan->c, &plan->g);
+    if (rc != PDMK_OK) { delete plan; return rc; }
+    // window width: ceil(2c/pi) makes the window's transform at the band edge equal its own
+    // edge value; two more points keep the far-field gradient (a derivative) within eps too
+    plan->w = plan->opts.window_w > 0 ? plan->opts.window_w : int(std::ceil(2.0 * plan->c / kPi - 1e-9)) + 2;
+    plan->w = std::max(2, std::min(plan->w, kMaxW));
+    plan->beta = kPi * plan->w / 2.0;  // window prolate bandwidth c_w
+    plan->wt = make_window(plan->w, plan->beta, mixed ? 1e-9 : std::max(eps * 1e-5, 1e-15));
+    size_bins(plan);
+    // near-field coefficients
+    plan->cA = plan->kt.A.coef;
+    plan->cB = plan->kt.B.coef;
+    if (int(plan->cA.size()) > kMaxCheb) plan->cA.resize(kMaxCheb);
+    if (int(plan->cB.size()) > kMaxCheb) plan->cB.resize(kMaxCheb);
+    plan->cW = plan->wt.F.coef;
+    plan->cWd = plan->wt.dF.coef;
+    if (int(plan->cW.size()) > kMaxCheb) plan->cW.resize(kMaxCheb);
+    if (int(plan->cWd.size()) > kMaxCheb) plan->cWd.resize(kMaxCheb);
+    // plane-wave planning (proxy order, plane-wave counts, 1D operators)
+    pw_plan_create(&plan->pw, d, eps, plan->c, plan->kt, plan->opts.n_proxy, plan->opts.n_pw, mixed);
+    // device: coefficient arrays, far weights, grid, spectrum, FFT plans
+    const size_t ts = tsize(plan);
+    int r;
+#define PCHECK(x) do { r = (x); if (r != PDMK_OK) { pdmk_plan_destroy(plan); return r; } } while (0)
+    {
+        unsigned char* p = nullptr;
+        auto coef_upload = [&](const std::vector<double>& src, void** dst) -> int {
+            unsigned char* q = nullptr;
+            int rr = dalloc(plan, plan->plan_allocs, &q, ts * kMaxCheb);
+            if (rr != PDMK_OK) return rr;
+            *dst = q;
+            std::vector<unsigned char> buf(ts * kMaxCheb, 0);
+            for (size_t k = 0; k < src.size() && k < size_t(kMaxCheb); ++k) {
+                if (mixed) { float v = float(src[k]); std::memcpy(&buf[k * 4], &v, 4); }
+                else std::memcpy(&buf[k * 8], &src[k], 8);
+            }
+            return upload(plan, *dst, buf);
+        };
+        PCHECK(coef_upload(plan->cA, &plan->d_coefA));
+        PCHECK(coef_upload(plan->cB, &plan->d_coefB));
+        PCHECK(coef_upload(plan->cW, &plan->d_coefW));
+        PCHECK(coef_upload(plan->cWd, &plan->d_coefWd));
+        PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_weight, size_t(plan->nhalf)));
+        std::vector<double> wt = far_weights(plan);
+        PCHECK(upload(plan, plan->d_weight, wt));
+        PCHECK(dalloc(plan, plan->plan_allocs, &p, ts * size_t(plan->ncell)));
+        plan->d_grid = p;
+        PCHECK(dalloc(plan, plan->plan_allocs, &p, 2 * ts * size_t(plan->nhalf)));
+        plan->d_spec = p;
+        PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsums, 4));
+        PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_count, 2));
+    }
+    {
+        const Geometry& g = plan->g;
+        cufftType tf = mixed ? CUFFT_R2C : CUFFT_D2Z, ti = mixed ? CUFFT_C2R : CUFFT_Z2D;
+        cufftResult fr;
+        if (d == 2) {
+            fr = cufftPlan2d(&plan->fft_fwd, g.M[1], g.M[0], tf);
+            if (fr == CUFFT_SUCCESS) fr = cufftPlan2d(&plan->fft_inv, g.M[1], g.M[0], ti);
+        } else {
+            fr = cufftPlan3d(&plan->fft_fwd, g.M[2], g.M[1], g.M[0], tf);
+            if (fr == CUFFT_SUCCESS) fr = cufftPlan3d(&plan->fft_inv, g.M[2], g.M[1], g.M[0], ti);
+        }
+        if (fr != CUFFT_SUCCESS) {
+            plan_set_msg(plan, "cufft plan failure");
+            pdmk_plan_destroy(plan);
+            return PDMK_ERR_CUDA;
+        }
+        plan->have_fft = true;
+        cufftSetStream(plan->fft_fwd, plan->stream);
+        cufftSetStream(plan->fft_inv, plan->stream);
+    }
+    if (cudaStreamSynchronize(plan->stream) != cudaSuccess) {
+        pdmk_plan_destroy(plan);
+        return PDMK_ERR_CUDA;
+    }
+#undef PCHECK
+    *out = plan;
+    return PDMK_OK;
+}
+
+extern "C" void pdmk_plan_destroy(pdmk_plan plan) {
+    if (!plan) return;
+    if (plan->stream) cudaStreamSynchronize(plan->stream); else cudaDeviceSynchronize();
+    free_list(plan->src_allocs, &plan->device_bytes);
+    free_list(plan->plan_allocs, &plan->device_bytes);
+    pw_free(&plan->pw);
+    if (plan->have_fft) {
+        cufftDestroy(plan->fft_fwd);
+        cufftDestroy(plan->fft_inv);
+    }
+    for (auto e : plan->ev) cudaEventDestroy(e);
+    delete plan;
+}
+
+template <typename T>
+static int gather_charges(pdmk_plan plan) {
+    GatherArgs<T> a;
+    a.q = plan->d_q_user;
+    a.nsrc = plan->nimg;
+    a.src_orig = plan->d_src_orig;
+    a.src4 = static_cast<T*>(plan->d_src4);
+    a.nspread = plan->nspread;
+    a.spread_orig = plan->d_spread_orig;
+    a.spread_dq = static_cast<T*>(plan->d_pt_dq);
+    a.ntgt = plan->ntgt;
+    a.tgt_orig = plan->d_tgt_orig;
+    a.tgt4 = static_cast<T*>(plan->d_tgt4);
+    a.q_tgt = plan->d_q_tgt;
+    int64_t mx = std::max(plan->nimg, std::max(plan->nspread, plan->ntgt));
+    int blocks = int(std::min<int64_t>((mx + 255) / 256, 148 * 16));
+    k_gather_charges<T><<<std::max(blocks, 1), 256, 0, plan->stream>>>(a);
+    CK(cudaGetLastError());
+    return PDMK_OK;
+}
+
+static int set_charges_device(pdmk_plan plan, bool check_neutral) {
+    k_charge_sums<<<1, 1024, 0, plan->stream>>>(plan->d_q_user, plan->n, plan->d_qsums);
+    CK(cudaGetLastError());
+    if (check_neutral) {
+        double h[3];
+        CK(cudaMemcpyAsync(h, plan->d_qsums, 3 * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
+        CK(cudaStreamSynchronize(plan->stream));
+        if (h[2] > 0) return PDMK_ERR_NONFINITE;
+        if (plan->opts.neutrality == 0 && std::fabs(h[0]) > 1e-12 * h[1]) return PDMK_ERR_NON_NEUTRAL;
+    }
+    int r = plan->opts.precision == PDMK_MIXED ? gather_charges<float>(plan) : gather_charges<double>(plan);
+    if (r != PDMK_OK) return r;
+    return pw_set_charges(&plan->pw, plan->stream);
+}
+
+extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, const double* q, int where) {
+    if (!plan || n < 0 || (n > 0 && (!y || !q))) return PDMK_ERR_BAD_ARG;
+    if (n >= (int64_t(1) << 30)) return PDMK_ERR_TOO_LARGE;
+    const int d = plan->d;
+    plan->ready = false;
+    std::vector<double> hy(size_t(n) * d), hq(static_cast<size_t>(n));
+    if (n > 0) {
+        if (where == PDMK_DEVICE) {
+            CK(cudaMemcpy(hy.data(), y, hy.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(hq.data(), q, hq.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(hy.data(), y, hy.size() * sizeof(double));
+            std::memcpy(hq.data(), q, hq.size() * sizeof(double));
+        }
+    }
+    double qs = 0, qa = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        for (int a = 0; a < d; ++a)
+            if (!std::isfinite(hy[j * d + a])) return PDMK_ERR_NONFINITE;
+        if (!std::isfinite(hq[j])) return PDMK_ERR_NONFINITE;
+        qs += hq[j];
+        qa += std::fabs(hq[j]);
+    }
+    if (plan->opts.neutrality == 0 && std::fabs(qs) > 1e-12 * qa) return PDMK_ERR_NON_NEUTRAL;
+    const Geometry& g = plan->g;
+    // orient, then fractional coordinates wrapped into [0, 1)
+    std::vector<double> u(size_t(n) * d);
+    for (int64_t j = 0; j < n; ++j) {
+        double xo[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i)
+            for (int k = 0; k < d; ++k) xo[i] += g.Q[i * d + k] * hy[j * d + k];
+        for (int i = 0; i < d; ++i) {
+            double s = 0;
+            for (int k = 0; k < d; ++k) s += g.Rinv[i * d + k] * xo[k];
+            s -= std::floor(s);
+            if (s >= 1.0) s = 0.0;
+            u[j * d + i] = s;
+        }
+    }
+    Tree tree;
+    SortedSources ss;
+    BuildStats st;
+    const int maxd = pw_supported(&plan->pw) ? plan->max_depth : 0;
+    int rc = build_tree(g, n, u.data(), plan->n_s, maxd, &tree, &ss, &st);
+    if (rc != PDMK_OK) return rc;
+    DirectLists dl;
+    int64_t pairs = 0;
+    build_direct_lists(tree, &dl, &pairs);
+    // ---- release old buffers, allocate new ----
+    if (plan->stream) cudaStreamSynchronize(plan->stream); else cudaDeviceSynchronize();
+    free_list(plan->src_allocs, &plan->device_bytes);
+    pw_free_sources(&plan->pw);
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    const size_t ts = tsize(plan);
+    plan->n = n;
+    plan->nimg = st.n_images;
+    plan->ntgt = int64_t(ss.tgt_of.size());
+    plan->nbox = st.nboxes;
+    plan->ntleaf = int(dl.tleaf.size());
+    auto put = [&](std::vector<unsigned char>& buf, size_t idx, double v) {
+        if (mixed) { float f = float(v); std::memcpy(&buf[idx * 4], &f, 4); }
+        else std::memcpy(&buf[idx * 8], &v, 8);
+    };
+    // leaf of every sorted source
+    std::vector<int> leaf_of(size_t(plan->nimg), -1);
+    for (int b = 0; b < st.nboxes; ++b)
+        if (tree.is_leaf(b))
+            for (int64_t j = tree.src_begin[b]; j < tree.src_end[b]; ++j) leaf_of[j] = b;
+    // sorted sources: coordinates relative to their leaf centre (FP64 difference, then T)
+    std::vector<unsigned char> src4(size_t(plan->nimg) * 4 * ts, 0);
+    std::vector<int> src_orig(size_t(plan->nimg));
+    std::vector<float> src_lo(mixed ? size_t(plan->nimg) * 4 : 0, 0.0f);
+    for (int64_t j = 0; j < plan->nimg; ++j) {
+        int b = leaf_of[j];
+        for (int a = 0; a < d; ++a) {
+            const double rel = ss.pos[j * d + a] - tree.center[size_t(b) * d + a];
+            put(src4, size_t(j) * 4 + a, rel);
+            if (mixed) src_lo[size_t(j) * 4 + a] = float(rel - double(float(rel)));
+        }
+        src_orig[j] = int(ss.orig[j]);
+    }
+    // targets (the originals, in sorted order)
+    std::vector<unsigned char> tgt4(size_t(plan->ntgt) * 4 * ts, 0);
+    std::vector<int> tgt_orig(size_t(plan->ntgt));
+    std::vector<double> self_w(size_t(plan->ntgt));
+    std::vector<int> tgt_leaf(size_t(plan->ntgt));
+    std::vector<float> tgt_lo(mixed ? size_t(plan->ntgt) * 4 : 0, 0.0f);
+    for (int64_t t = 0; t < plan->ntgt; ++t) {
+        int64_t j = ss.tgt_of[t];
+        int b = leaf_of[j];
+        tgt_leaf[t] = b;
+        for (int a = 0; a < d; ++a) {
+            const double rel = ss.pos[j * d + a] - tree.center[size_t(b) * d + a];
+            put(tgt4, size_t(t) * 4 + a, rel);
+            if (mixed) tgt_lo[size_t(t) * 4 + a] = float(rel - double(float(rel)));
+        }
+        tgt_orig[t] = int(ss.tgt_orig[t]);
+        const int L = tree.level[b];
+        const double h = g.rc / double(1LL << L);
+        self_w[t] = (d == 3) ? plan->kt.self_coef / h : plan->kt.self_coef - std::log(h) / (2.0 * kPi);
+    }
+    // near-field leaf descriptors
+    std::vector<TLeaf> tl(dl.tleaf.size());
+    for (size_t k = 0; k < dl.tleaf.size(); ++k) {
+        int b = dl.tleaf[k];
+        tl[k].tgt_begin = int(tree.tgt_begin[b]);
+        tl[k].tgt_count = int(tree.tgt_end[b] - tree.tgt_begin[b]);
+        tl[k].list_begin = int(dl.list_begin[k]);
+        tl[k].list_count = int(dl.list_begin[k + 1] - dl.list_begin[k]);
+        tl[k].level = tree.level[b];
+        tl[k].box = b;
+        tl[k].pad0 = tl[k].pad1 = 0;
+    }
+    std::vector<int> bsb(st.nboxes), bsc(st.nboxes);
+    for (int b = 0; b < st.nboxes; ++b) {
+        bsb[b] = int(tree.src_begin[b]);
+        bsc[b] = int(tree.src_end[b] - tree.src_begin[b]);
+    }
+    // far field: originals sorted by spreading bin, window start and offsets in FP64
+    const int fw = plan->w / 2;
+    auto grid_coord = [&](double uu, int i, int* g0, double* del) {
+        const int M = g.M[i];
+        double Mu = M * uu;
+        int gg = int(std::ceil(Mu - 0.5 * plan->w));
+        *del = Mu - gg;
+        int key = gg + fw;
+        int wrap = key >= 0 ? key / M : -((-key + M - 1) / M);
+        gg -= wrap * M;
+        *g0 = gg;
+    };
+    std::vector<int64_t> sp_bin(static_cast<size_t>(n));
+    std::vector<int> sp_g0(size_t(n) * 3, 0);
+    std::vector<double> sp_del(size_t(n) * 3, 0.0);
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t bin = 0;
+        for (int i = d - 1; i >= 0; --i) {
+            int g0;
+            double del;
+            grid_coord(u[j * d + i], i, &g0, &del);
+            int key = g0 + fw;  // in [0, M)
+            int bi = key / plan->B[i];
+            sp_g0[j * 3 + i] = key - bi * plan->B[i];  // tile offset in [0, B)
+            sp_del[j * 3 + i] = del;
+            bin = bin * plan->nbin[i] + bi;
+        }
+        sp_bin[j] = bin;
+    }
+    std::vector<int64_t> sp_order(static_cast<size_t>(n));
+    std::iota(sp_order.begin(), sp_order.end(), 0);
+    std::stable_sort(sp_order.begin(), sp_order.end(), [&](int64_t a, int64_t b) { return sp_bin[a] < sp_bin[b]; });
+    plan->nspread = n;
+    std::vector<int4> pt_g0(static_cast<size_t>(n));
+    std::vector<unsigned char> pt_dq(size_t(n) * 4 * ts, 0);
+    std::vector<int> sp_orig(static_cast<size_t>(n));
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t j = sp_order[k];
+        pt_g0[k] = make_int4(sp_g0[j * 3], sp_g0[j * 3 + 1], sp_g0[j * 3 + 2], 0);
+        for (int i = 0; i < 3; ++i) put(pt_dq, size_t(k) * 4 + i, sp_del[j * 3 + i]);
+        sp_orig[k] = int(j);
+    }
+    // subproblems: chunks of at most max_pts points of one bin
+    const int max_pts = 512;
+    std::vector<int4> subs;
+    std::vector<int> bin_sub_begin(size_t(plan->nbins_tot) + 1, 0);
+    {
+        int64_t k = 0;
+        for (int bin = 0; bin < plan->nbins_tot; ++bin) {
+            bin_sub_begin[bin] = int(subs.size());
+            int64_t k0 = k;
+            while (k < n && sp_bin[sp_order[k]] == bin) ++k;
+            for (int64_t s0 = k0; s0 < k; s0 += max_pts)
+                subs.push_back(make_int4(bin, int(s0), int(std::min<int64_t>(max_pts, k - s0)), 0));
+        }
+        bin_sub_begin[plan->nbins_tot] = int(subs.size());
+    }
+    plan->nsub = int(subs.size());
+    // interpolation targets (sorted target order)
+    std::vector<int4> t_g0(size_t(plan->ntgt));
+    std::vector<unsigned char> t_dq(size_t(plan->ntgt) * 4 * ts, 0);
+    for (int64_t t = 0; t < plan->ntgt; ++t) {
+        int64_t j = ss.tgt_orig[t];
+        int gg[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i) {
+            double del;
+            grid_coord(u[j * d + i], i, &gg[i], &del);
+            put(t_dq, size_t(t) * 4 + i, del);
+        }
+        t_g0[t] = make_int4(gg[0], gg[1], gg[2], 0);
+    }
+    // ---- device allocations and uploads ----
+    auto& L = plan->src_allocs;
+    DALLOC(L, plan->d_src4, unsigned char, src4.size());
+    DALLOC(L, plan->d_src_orig, int, src_orig.size());
+    DALLOC(L, plan->d_tgt4, unsigned char, tgt4.size());
+    DALLOC(L, plan->d_tgt_orig, int, tgt_orig.size());
+    DALLOC(L, plan->d_src_lo, float, src_lo.size());
+    DALLOC(L, plan->d_tgt_lo, float, tgt_lo.size());
+    DALLOC(L, plan->d_q_tgt, double, plan->ntgt);
+    DALLOC(L, plan->d_self_w, double, plan->ntgt);
+    DALLOC(L, plan->d_tleaf, TLeaf, tl.size());
+    DALLOC(L, plan->d_list, int, dl.list.size());
+    DALLOC(L, plan->d_box_src_begin, int, bsb.size());
+    DALLOC(L, plan->d_box_src_count, int, bsc.size());
+    DALLOC(L, plan->d_box_center, double, tree.center.size());
+    DALLOC(L, plan->d_pt_g0, int4, pt_g0.size());
+    DALLOC(L, plan->d_pt_dq, unsigned char, pt_dq.size());
+    DALLOC(L, plan->d_spread_orig, int, sp_orig.size());
+    DALLOC(L, plan->d_sub, int4, subs.size());
+    DALLOC(L, plan->d_bin_sub_begin, int, bin_sub_begin.size());
+    DALLOC(L, plan->d_slab, unsigned char, size_t(std::max(plan->nsub, 1)) * plan->Ptot * ts);
+    DALLOC(L, plan->d_t_g0, int4, t_g0.size());
+    DALLOC(L, plan->d_t_dq, unsigned char, t_dq.size());
+    DALLOC(L, plan->d_pot_near, double, plan->ntgt);
+    DALLOC(L, plan->d_grad_near, double, plan->ntgt * d);
+    DALLOC(L, plan->d_pot_far, double, plan->ntgt);
+    DALLOC(L, plan->d_gradu_far, double, plan->ntgt * d);
+    DALLOC(L, plan->d_q_user, double, n);
+    DALLOC(L, plan->d_pot_out, double, n);
+    DALLOC(L, plan->d_grad_out, double, n * d);
+    int r;
+    if ((r = upload(plan, plan->d_src4, src4))) return r;
+    if ((r = upload(plan, plan->d_src_orig, src_orig))) return r;
+    if ((r = upload(plan, plan->d_tgt4, tgt4))) return r;
+    if ((r = upload(plan, plan->d_tgt_orig, tgt_orig))) return r;
+    if ((r = upload(plan, plan->d_src_lo, src_lo))) return r;
+    if ((r = upload(plan, plan->d_tgt_lo, tgt_lo))) return r;
+    if ((r = upload(plan, plan->d_self_w, self_w))) return r;
+    if ((r = upload(plan, plan->d_tleaf, tl))) return r;
+    if ((r = upload(plan, plan->d_list, dl.list))) return r;
+    if ((r = upload(plan, plan->d_box_src_begin, bsb))) return r;
+    if ((r = upload(plan, plan->d_box_src_count, bsc))) return r;
+    if ((r = upload(plan, plan->d_box_center, tree.center))) return r;
+    if ((r = upload(plan, plan->d_pt_g0, pt_g0))) return r;
+    if ((r = upload(plan, plan->d_pt_dq, pt_dq))) return r;
+    if ((r = upload(plan, plan->d_spread_orig, sp_orig))) return r;
+    if ((r = upload(plan, plan->d_sub, subs))) return r;
+    if ((r = upload(plan, plan->d_bin_sub_begin, bin_sub_begin))) return r;
+    if ((r = upload(plan, plan->d_t_g0, t_g0))) return r;
+    if ((r = upload(plan, plan->d_t_dq, t_dq))) return r;
+    if ((r = upload(plan, plan->d_q_user, hq))) return r;
+    // plane-wave passes (proxy, translation and local-expansion layouts)
+    r = pw_set_sources(&plan->pw, tree, ss, leaf_of, tgt_leaf, g, plan->stream);
+    if (r != PDMK_OK) return r;
+    r = set_charges_device(plan, false);
+    if (r != PDMK_OK) return r;
+    CK(cudaStreamSynchronize(plan->stream));
+    // info
+    pdmk_info& I = plan->info;
+    std::memset(&I, 0, sizeof(I));
+    I.d = d; I.eps = plan->eps; I.c = plan->c; I.rc = g.rc; I.V = g.V; I.kappa = plan->kappa;
+    I.n_s = plan->n_s; I.window_w = plan->w; I.n_proxy = plan->pw.p; I.n_pw = plan->pw.K;
+    I.precision = plan->opts.precision;
+    for (int i = 0; i < 3; ++i) { I.M[i] = g.M[i]; I.nroot[i] = i < d ? g.nroot[i] : 1; }
+    I.n = n; I.n_images = plan->nimg; I.nboxes = st.nboxes; I.nleaves = st.nleaves; I.depth = st.depth;
+    I.ntarget_leaves = plan->ntleaf; I.near_pairs = pairs;
+    I.n_pw_boxes_out = plan->pw.nout; I.n_pw_boxes_in = plan->pw.nin;
+    plan->count_pending = plan->opts.profile != 0;
+    plan->ready = true;
+    return PDMK_OK;
+}
+
+extern "C" int pdmk_set_charges(pdmk_plan plan, const double* q, int where) {
+    if (!plan || !q) return PDMK_ERR_BAD_ARG;
+    if (!plan->ready) return PDMK_ERR_NOT_READY;
+    CK(cudaMemcpyAsync(plan->d_q_user, q, size_t(plan->n) * sizeof(double),
+                       where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, plan->stream));
+    return set_charges_device(plan, where == PDMK_HOST || plan->opts.neutrality == 0);
+}
+
+static int stage_mark(pdmk_plan plan, const char* name) {
+    if (!plan->opts.profile) return PDMK_OK;
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(e, plan->stream));
+    plan->ev.push_back(e);
+    plan->stage_names.push_back(name);
+    return PDMK_OK;
+}
+
+template <typename T, int D>
+static int run_eval(pdmk_plan plan, double* pot, double* grad) {
+    cudaStream_t s = plan->stream;
+    const Geometry& g = plan->g;
+    int r;
+    for (auto e : plan->ev) cudaEventDestroy(e);
+    plan->ev.clear();
+    plan->stage_names.clear();
+    if ((r = stage_mark(plan, "start"))) return r;
+    // ---- far field: spread, fold, FFT, scale, inverse FFT, interpolate ----
+    const T hwi2 = T(4.0 / (double(plan->w) * plan->w));
+    if (plan->nsub > 0) {
+        SpreadArgs<T> sa;
+        sa.pt_g0 = plan->d_pt_g0;
+        sa.pt_dq = static_cast<const T*>(plan->d_pt_dq);
+        sa.sub = plan->d_sub;
+        sa.nsub = plan->nsub;
+        sa.slab = static_cast<T*>(plan->d_slab);
+        sa.P0 = plan->P[0]; sa.P1 = plan->P[1]; sa.P2 = plan->P[2]; sa.Ptot = plan->Ptot;
+        sa.B0 = plan->B[0]; sa.B1 = plan->B[1]; sa.B2 = plan->B[2];
+        sa.w = plan->w;
+        sa.half_w_inv2 = hwi2;
+        sa.coefW = static_cast<const T*>(plan->d_coefW);
+        sa.nW = int(plan->cW.size());
+        size_t smem = sizeof(T) * (size_t(plan->Ptot) + size_t(kSpreadChunk) * 3 * plan->w + kSpreadChunk) +
+                      sizeof(int) * kSpreadChunk * 3;
+        CK(cudaFuncSetAttribute(k_spread<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_spread<T, D><<<plan->nsub, kSpreadThreads, smem, s>>>(sa);
+        CK(cudaGetLastError());
+    }
+    {
+        FoldArgs<T> fa;
+        fa.slab = static_cast<const T*>(plan->d_slab);
+        fa.bin_sub_begin = plan->d_bin_sub_begin;
+        fa.grid = static_cast<T*>(plan->d_grid);
+        fa.M0 = g.M[0]; fa.M1 = g.M[1]; fa.M2 = g.M[2];
+        fa.nb0 = plan->nbin[0]; fa.nb1 = plan->nbin[1]; fa.nb2 = plan->nbin[2];
+        fa.B0 = plan->B[0]; fa.B1 = plan->B[1]; fa.B2 = plan->B[2];
+        fa.P0 = plan->P[0]; fa.P1 = plan->P[1]; fa.P2 = plan->P[2]; fa.Ptot = plan->Ptot;
+        fa.fw = plan->w / 2;
+        int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 8));
+        k_fold<T, D><<<std::max(blocks, 1), 256, 0, s>>>(fa);
+        CK(cudaGetLastError());
+    }
+    if ((r = stage_mark(plan, "spread"))) return r;
+    if (sizeof(T) == 4) {
+        CKFFT(cufftExecR2C(plan->fft_fwd, (cufftReal*)plan->d_grid, (cufftComplex*)plan->d_spec));
+    } else {
+        CKFFT(cufftExecD2Z(plan->fft_fwd, (cufftDoubleReal*)plan->d_grid, (cufftDoubleComplex*)plan->d_spec));
+    }
+    if ((r = stage_mark(plan, "fft_fwd"))) return r;
+    {
+        int blocks = int(std::min<int64_t>((plan->nhalf + 255) / 256, 148 * 8));
+        k_scale<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<T*>(plan->d_spec), plan->d_weight, plan->nhalf);
+        CK(cudaGetLastError());
+    }
+    if ((r = stage_mark(plan, "scale"))) return r;
+    if (sizeof(T) == 4) {
+        CKFFT(cufftExecC2R(plan->fft_inv, (cufftComplex*)plan->d_spec, (cufftReal*)plan->d_grid));
+    } else {
+        CKFFT(cufftExecZ2D(plan->fft_inv, (cufftDoubleComplex*)plan->d_spec, (cufftDoubleReal*)plan->d_grid));
+    }
+    if ((r = stage_mark(plan, "fft_inv"))) return r;
+    if (plan->ntgt > 0) {
+        InterpArgs<T> ia;
+        ia.grid = static_cast<const T*>(plan->d_grid);
+        ia.t_g0 = plan->d_t_g0;
+        ia.t_dq = static_cast<const T*>(plan->d_t_dq);
+        ia.nt = int(plan->ntgt);
+        ia.M0 = g.M[0]; ia.M1 = g.M[1]; ia.M2 = g.M[2];
+        ia.w = plan->w;
+        ia.half_w_inv2 = hwi2;
+        ia.coefW = static_cast<const T*>(plan->d_coefW);
+        ia.coefWd = static_cast<const T*>(plan->d_coefWd);
+        ia.nW = int(plan->cW.size());
+        ia.nWd = int(plan->cWd.size());
+        ia.pot = plan->d_pot_far;
+        ia.gradu = plan->d_gradu_far;
+        size_t smem = sizeof(T) * 128 * 2 * D * plan->w;
+        CK(cudaFuncSetAttribute(k_interp<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_interp<T, D><<<int((plan->ntgt + 127) / 128), 128, smem, s>>>(ia);
+        CK(cudaGetLastError());
+    }
+    if ((r = stage_mark(plan, "interp"))) return r;
+    // ---- near field: plane-wave passes, then the direct residual sum ----
+    r = pw_eval(&plan->pw, s);
+    if (r != PDMK_OK) return r;
+    if ((r = stage_mark(plan, "planewave"))) return r;
+    if (plan->ntleaf > 0) {
+        NearArgs<T> na;
+        na.tleaf = plan->d_tleaf;
+        na.ntleaf = plan->ntleaf;
+        na.list = plan->d_list;
+        na.box_src_begin = plan->d_box_src_begin;
+        na.box_src_count = plan->d_box_src_count;
+        na.box_center = plan->d_box_center;
+        na.src4 = static_cast<const T*>(plan->d_src4);
+        na.tgt4 = static_cast<const T*>(plan->d_tgt4);
+        na.pot = plan->d_pot_near;
+        na.grad = plan->d_grad_near;
+        na.inv_rc = 1.0 / g.rc;
+        na.coefA = static_cast<const T*>(plan->d_coefA);
+        na.coefB = static_cast<const T*>(plan->d_coefB);
+        na.nA = int(plan->cA.size());
+        na.nB = int(plan->cB.size());
+        na.count_in = nullptr;
+        na.src_lo = static_cast<const T*>(plan->d_src_lo);
+        na.tgt_lo = static_cast<const T*>(plan->d_tgt_lo);
+        na.close_s = T(0.04);  // r < 0.2 h
+        if (plan->count_pending) {
+            CK(cudaMemsetAsync(plan->d_count, 0, sizeof(unsigned long long), s));
+            na.count_in = plan->d_count;
+        }
+        k_nearfield<T, D><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        CK(cudaGetLastError());
+    }
+    if ((r = stage_mark(plan, "nearfield"))) return r;
+    // ---- assembly ----
+    {
+        AssembleArgs aa;
+        aa.nt = plan->ntgt;
+        aa.d = D;
+        aa.tgt_orig = plan->d_tgt_orig;
+        aa.self_w = plan->d_self_w;
+        aa.q_tgt = plan->d_q_tgt;
+        aa.pot_near = plan->d_pot_near;
+        aa.grad_near = plan->d_grad_near;
+        aa.pot_pw = plan->pw.active ? plan->pw.d_pot : nullptr;
+        aa.grad_pw = plan->pw.active ? plan->pw.d_grad : nullptr;
+        aa.pot_far = plan->d_pot_far;
+        aa.gradu_far = plan->d_gradu_far;
+        aa.qsum = plan->d_qsums;
+        aa.mean_coef = plan->kt.rhat0 * g.rc * g.rc / g.V;
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                // grad_x_i = sum_j (R^{-T})_{ij} M_j d/d(M_j u_j)
+                aa.G[i * D + j] = g.Rinv[j * D + i] * g.M[j];
+                aa.Qt[i * D + j] = g.Q[j * D + i];
+            }
+        aa.pot_out = pot;
+        aa.grad_out = grad;
+        int blocks = int(std::min<int64_t>((plan->ntgt + 255) / 256, 148 * 8));
+        k_assemble<<<std::max(blocks, 1), 256, 0, s>>>(aa);
+        CK(cudaGetLastError());
+    }
+    if ((r = stage_mark(plan, "assemble"))) return r;
+    return PDMK_OK;
+}
+
+extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
+    if (!plan || !pot) return PDMK_ERR_BAD_ARG;
+    if (!plan->ready) return PDMK_ERR_NOT_READY;
+    double* dp = where == PDMK_DEVICE ? pot : plan->d_pot_out;
+    double* dg = grad ? (where == PDMK_DEVICE ? grad : plan->d_grad_out) : nullptr;
+    int r;
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    if (plan->d == 2) r = mixed ? run_eval<float, 2>(plan, dp, dg) : run_eval<double, 2>(plan, dp, dg);
+    else r = mixed ? run_eval<float, 3>(plan, dp, dg) : run_eval<double, 3>(plan, dp, dg);
+    if (r != PDMK_OK) return r;
+    if (where != PDMK_DEVICE) {
+        CK(cudaMemcpyAsync(pot, dp, size_t(plan->n) * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
+        if (grad)
+            CK(cudaMemcpyAsync(grad, dg, size_t(plan->n) * plan->d * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
+        CK(cudaStreamSynchronize(plan->stream));
+    }
+    if (plan->count_pending) {
+        unsigned long long cnt = 0;
+        CK(cudaMemcpyAsync(&cnt, plan->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, plan->stream));
+        CK(cudaStreamSynchronize(plan->stream));
+        plan->info.near_pairs_in = int64_t(cnt);
+        plan->count_pending = false;
+    }
+    if (plan->opts.profile) {
+        CK(cudaEventSynchronize(plan->ev.back()));
+        plan->stage_ms.assign(plan->ev.size(), 0.0);
+        for (size_t i = 1; i < plan->ev.size(); ++i) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, plan->ev[i - 1], plan->ev[i]));
+            plan->stage_ms[i] = ms;
+        }
+    }
+    return PDMK_OK;
+}
+
+extern "C" int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, int cap) {
+    if (!plan) return PDMK_ERR_BAD_ARG;
+    int n = int(plan->stage_ms.size()) - 1;
+    if (n < 0) n = 0;
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (names) names[i] = plan->stage_names[i + 1].c_str();
+        if (ms) ms[i] = plan->stage_ms[i + 1];
+    }
+    return n;
+}
+
+extern "C" int pdmk_get_info(pdmk_plan plan, pdmk_info* info) {
+    if (!plan || !info) return PDMK_ERR_BAD_ARG;
+    *info = plan->info;
+    info->device_bytes = plan->device_bytes + plan->pw.device_bytes;
+    if (!plan->ready) {
+        info->d = plan->d; info->eps = plan->eps; info->c = plan->c; info->rc = plan->g.rc;
+        info->V = plan->g.V; info->kappa = plan->kappa; info->n_s = plan->n_s; info->window_w = plan->w;
+        for (int i = 0; i < 3; ++i) { info->M[i] = plan->g.M[i]; info->nroot[i] = plan->g.nroot[i]; }
+    }
+    return PDMK_OK;
+}

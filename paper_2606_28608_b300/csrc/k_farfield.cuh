@@ -1,0 +1,248 @@
+// k_farfield.cuh -- the smooth periodic kernel W_0^(p) by the five-step procedure of
+// Sec. 3.6 (Eq. (3.14) and the three-step NUFFT realisation): spreading (type-1 half),
+// diagonal scaling (Eq. (3.15a) with the m = 0 mode zeroed, window deconvolution folded
+// in), interpolation (type-2 half).  The FFTs are cuFFT calls made by the host.
+//
+// Window: the prolate phi(z) = psi_{c_w}(2z/w)/psi_{c_w}(0), |z| < w/2 grid units, with
+// c_w = pi w / 2 (its transform at the grid's band edge equals its own edge value), as a
+// Chebyshev series in s = (2z/w)^2 -- smooth up to the support edge, so its derivative is
+// well conditioned in FP32 -- on the unpadded M_1 x ... x M_d grid (Remark 3.1).
+//
+// Spreading is atomics-free by tile ownership.  Sources are sorted by grid bin; a
+// subproblem is a bin and at most a few hundred of its sources.  A CTA accumulates one
+// subproblem into a shared-memory tile padded by the window (B + w - 1 per dimension);
+// each of its 4 warps owns the tile planes whose last index is congruent to its warp id
+// mod 4, so no two threads ever update the same cell, and every cell is updated in point
+// order: the result is deterministic.  Tiles go to a slab; the fold kernel adds, for every
+// grid cell, the slabs of the subproblems whose padded tile covers it, in a fixed order.
+#pragma once
+#include "kernels_common.cuh"
+
+namespace pdmk {
+
+constexpr int kSpreadThreads = 128;
+constexpr int kSpreadWarps = 4;
+constexpr int kSpreadChunk = 128;
+constexpr int kMaxW = 20;
+
+template <typename T>
+__device__ __forceinline__ T pswf_window(T z, T half_w_inv2, const T* cw, int nw) {
+    const T s = z * z * half_w_inv2;
+    return s < T(1) ? clenshaw(cw, nw, fma(T(2), s, T(-1))) : T(0);
+}
+// value and derivative d/dz
+template <typename T>
+__device__ __forceinline__ void pswf_window_d(T z, T half_w_inv2, const T* cw, int nw, const T* cd, int nd,
+                                              T* v, T* dv) {
+    const T s = z * z * half_w_inv2;
+    if (s < T(1)) {
+        const T x = fma(T(2), s, T(-1));
+        *v = clenshaw(cw, nw, x);
+        *dv = clenshaw(cd, nd, x) * T(2) * z * half_w_inv2;
+    } else {
+        *v = T(0);
+        *dv = T(0);
+    }
+}
+
+// dynamic shared memory: tile[Ptot] | win[kSpreadChunk][3][w] | q | koff[kSpreadChunk][3] (int)
+template <typename T, int D>
+__global__ void __launch_bounds__(kSpreadThreads)
+k_spread(SpreadArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T cw[kMaxCheb];
+    if (threadIdx.x < a.nW) cw[threadIdx.x] = a.coefW[threadIdx.x];
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    T* win = tile + a.Ptot;
+    T* qv = win + kSpreadChunk * 3 * a.w;
+    int* koff = reinterpret_cast<int*>(qv + kSpreadChunk);
+
+    const int4 sp = a.sub[blockIdx.x];
+    const int begin = sp.y, count = sp.z;
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const int w = a.w;
+    // bin coordinates and the tile origin (grid index of tile cell 0) per dimension
+    for (int i = tid; i < a.Ptot; i += kSpreadThreads) tile[i] = T(0);
+    // plane size: 2D planes are rows of P0 (w entries per point), 3D planes are P0*P1
+    const int plane_entries = (D == 3) ? w * w : w;
+    __syncthreads();
+    for (int c0 = 0; c0 < count; c0 += kSpreadChunk) {
+        const int np = min(kSpreadChunk, count - c0);
+        if (tid < np) {
+            const int pi = begin + c0 + tid;
+            const int4 g = a.pt_g0[pi];
+            const T* dq = a.pt_dq + size_t(pi) * 4;
+            // pt_g0 holds the tile offset of the first window node (0 <= k <= B - 1 per
+            // dimension; the tile origin is bin*B - floor(w/2)), computed by the host in FP64
+            koff[tid * 3 + 0] = g.x;
+            koff[tid * 3 + 1] = g.y;
+            koff[tid * 3 + 2] = g.z;
+            qv[tid] = dq[3];
+            for (int k = 0; k < D; ++k) {
+                const T del = dq[k];  // M u - g0 (first node's distance), in grid units
+                for (int j = 0; j < w; ++j)
+                    win[(tid * 3 + k) * w + j] = pswf_window(del - T(j), a.half_w_inv2, cw, a.nW);
+            }
+        }
+        __syncthreads();
+        for (int p = 0; p < np; ++p) {
+            const T q = qv[p];
+            const int kx = koff[p * 3 + 0], ky = koff[p * 3 + 1];
+            const int kz = (D == 3) ? koff[p * 3 + 2] : 0;
+            const T* wx = win + (p * 3 + 0) * w;
+            const T* wy = win + (p * 3 + 1) * w;
+            const T* wz = win + (p * 3 + 2) * w;
+            const int klast = (D == 3) ? kz : ky;
+            // first owned plane j0: (klast + j0) % 4 == wp
+            int j0 = (wp - klast) % kSpreadWarps;
+            if (j0 < 0) j0 += kSpreadWarps;
+            for (int jl = j0; jl < w; jl += kSpreadWarps) {
+                if (D == 3) {
+                    const T fz = q * wz[jl];
+                    T* plane = tile + (kz + jl) * (a.P0 * a.P1);
+                    for (int e = lane; e < plane_entries; e += 32) {
+                        const int iy = e / w, ix = e - iy * w;
+                        plane[(ky + iy) * a.P0 + kx + ix] += fz * wy[iy] * wx[ix];
+                    }
+                } else {
+                    const T fy = q * wy[jl];
+                    T* row = tile + (ky + jl) * a.P0;
+                    for (int e = lane; e < plane_entries; e += 32) row[kx + e] += fy * wx[e];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    T* out = a.slab + size_t(blockIdx.x) * a.Ptot;
+    for (int i = tid; i < a.Ptot; i += kSpreadThreads) out[i] = tile[i];
+}
+
+// fold: grid cell g gathers every subproblem tile that covers it (periodic wrap)
+template <typename T, int D>
+__global__ void k_fold(FoldArgs<T> a) {
+    const int64_t ncell = int64_t(a.M0) * a.M1 * (D == 3 ? a.M2 : 1);
+    for (int64_t cell = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; cell < ncell;
+         cell += int64_t(gridDim.x) * blockDim.x) {
+        const int g0 = int(cell % a.M0);
+        const int g1 = int((cell / a.M0) % a.M1);
+        const int g2 = (D == 3) ? int(cell / (int64_t(a.M0) * a.M1)) : 0;
+        // candidate bins per dimension: the tile of bin b starts at b*B - fw and spans P
+        int cb0[8], lo0[8], n0 = 0;
+        int cb1[8], lo1[8], n1 = 0;
+        int cb2[8], lo2[8], n2 = 0;
+        auto collect = [&](int g, int M, int B, int P, int nb, int* cb, int* lo, int& n) {
+            for (int b = 0; b < nb && n < 8; ++b) {
+                int off = g - (b * B - a.fw);
+                off %= M;
+                if (off < 0) off += M;
+                if (off < P) { cb[n] = b; lo[n] = off; ++n; }
+            }
+        };
+        collect(g0, a.M0, a.B0, a.P0, a.nb0, cb0, lo0, n0);
+        collect(g1, a.M1, a.B1, a.P1, a.nb1, cb1, lo1, n1);
+        if (D == 3) collect(g2, a.M2, a.B2, a.P2, a.nb2, cb2, lo2, n2);
+        else { cb2[0] = 0; lo2[0] = 0; n2 = 1; }
+        T acc = T(0);
+        for (int i2 = 0; i2 < n2; ++i2)
+            for (int i1 = 0; i1 < n1; ++i1)
+                for (int i0 = 0; i0 < n0; ++i0) {
+                    const int bin = (cb2[i2] * a.nb1 + cb1[i1]) * a.nb0 + cb0[i0];
+                    const int idx = (lo2[i2] * a.P1 + lo1[i1]) * a.P0 + lo0[i0];
+                    for (int s = a.bin_sub_begin[bin]; s < a.bin_sub_begin[bin + 1]; ++s)
+                        acc += a.slab[size_t(s) * a.Ptot + idx];
+                }
+        a.grid[cell] = acc;
+    }
+}
+
+// diagonal scaling of the half spectrum by precomputed FP64 weights (zero at m = 0 and on
+// the Nyquist planes)
+template <typename T>
+__global__ void k_scale(T* spec /* interleaved complex */, const double* weight, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const double wgt = weight[i];
+        spec[2 * i] = T(double(spec[2 * i]) * wgt);
+        spec[2 * i + 1] = T(double(spec[2 * i + 1]) * wgt);
+    }
+}
+
+// interpolation at targets: potential and gradient w.r.t. the grid coordinates
+template <typename T, int D>
+__global__ void __launch_bounds__(128)
+k_interp(InterpArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T cw[kMaxCheb], cd[kMaxCheb];
+    if (threadIdx.x < a.nW) cw[threadIdx.x] = a.coefW[threadIdx.x];
+    if (threadIdx.x < a.nWd) cd[threadIdx.x] = a.coefWd[threadIdx.x];
+    __syncthreads();
+    T* wv = reinterpret_cast<T*>(smem_raw);            // [128][D][w]
+    T* wd = wv + blockDim.x * D * a.w;                  // [128][D][w]
+    const int w = a.w;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nt) return;
+    const int4 g = a.t_g0[t];
+    const T* dq = a.t_dq + size_t(t) * 4;
+    T* myv = wv + threadIdx.x * D * w;
+    T* myd = wd + threadIdx.x * D * w;
+    for (int k = 0; k < D; ++k) {
+        const T del = dq[k];
+        for (int j = 0; j < w; ++j)
+            pswf_window_d(del - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &myv[k * w + j], &myd[k * w + j]);
+    }
+    // the window argument is del - j = M u - (g0 + j), so d/d(M u) phi(del - j) = phi'(del - j)
+    T pot = 0, gx = 0, gy = 0, gz = 0;
+    const int gx0 = g.x, gy0 = g.y, gz0 = g.z;
+    if (D == 2) {
+        for (int iy = 0; iy < w; ++iy) {
+            int yy = gy0 + iy;
+            yy %= a.M1;
+            if (yy < 0) yy += a.M1;
+            const T* row = a.grid + size_t(yy) * a.M0;
+            T sx = 0, sdx = 0;
+            int xx = gx0 % a.M0;
+            if (xx < 0) xx += a.M0;
+            for (int ix = 0; ix < w; ++ix) {
+                const T v = __ldg(row + xx);
+                sx = fma(v, myv[ix], sx);
+                sdx = fma(v, myd[ix], sdx);
+                if (++xx == a.M0) xx = 0;
+            }
+            pot = fma(sx, myv[w + iy], pot);
+            gx = fma(sdx, myv[w + iy], gx);
+            gy = fma(sx, myd[w + iy], gy);
+        }
+    } else {
+        for (int iz = 0; iz < w; ++iz) {
+            int zz = gz0 + iz;
+            zz %= a.M2;
+            if (zz < 0) zz += a.M2;
+            for (int iy = 0; iy < w; ++iy) {
+                int yy = gy0 + iy;
+                yy %= a.M1;
+                if (yy < 0) yy += a.M1;
+                const T* row = a.grid + (size_t(zz) * a.M1 + yy) * a.M0;
+                T sx = 0, sdx = 0;
+                int xx = gx0 % a.M0;
+                if (xx < 0) xx += a.M0;
+                for (int ix = 0; ix < w; ++ix) {
+                    const T v = __ldg(row + xx);
+                    sx = fma(v, myv[ix], sx);
+                    sdx = fma(v, myd[ix], sdx);
+                    if (++xx == a.M0) xx = 0;
+                }
+                const T fyz = myv[w + iy] * myv[2 * w + iz];
+                pot = fma(sx, fyz, pot);
+                gx = fma(sdx, fyz, gx);
+                gy = fma(sx, myd[w + iy] * myv[2 * w + iz], gy);
+                gz = fma(sx, myv[w + iy] * myd[2 * w + iz], gz);
+            }
+        }
+    }
+    a.pot[t] = double(pot);
+    a.gradu[size_t(t) * D + 0] = double(gx);
+    a.gradu[size_t(t) * D + 1] = double(gy);
+    if (D == 3) a.gradu[size_t(t) * D + 2] = double(gz);
+}
+
+}  // namespace pdmk

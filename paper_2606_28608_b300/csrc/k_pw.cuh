@@ -1,0 +1,41 @@
+// k_pw.cuh -- plane-wave passes of the difference kernels D_l (Sec. 2.3, Eq. (2.5)-(2.6);
+// Sec. 3.5: the free-space DMK on the extended domain with the root W_0 step omitted):
+// upward proxy charges, outgoing plane waves, colleague translation, incoming plane waves
+// to local values, downward interpolation, and evaluation at leaf targets.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "host_plan.h"
+
+namespace pdmk {
+
+struct PwPlan {
+    int d = 3;
+    int p = 0;   // Chebyshev proxy points per dimension
+    int K = 0;   // plane-wave nodes -K..K per dimension
+    bool mixed = false;
+    bool active = false;  // the tree has levels below the root grid
+    int nout = 0, nin = 0;
+    int64_t device_bytes = 0;
+    double* d_pot = nullptr;   // per sorted target
+    double* d_grad = nullptr;  // d per sorted target
+    const void* d_src4 = nullptr;  // borrowed from the plan (sorted sources, leaf-relative)
+    const void* d_tgt4 = nullptr;  // borrowed (sorted targets, leaf-relative)
+    std::vector<void*> allocs;
+    void* impl = nullptr;
+};
+
+void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables& kt, int n_proxy, int n_pw,
+                    bool mixed);
+bool pw_supported(const PwPlan* pw);
+int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& s, const std::vector<int>& leaf_of,
+                   const std::vector<int>& tgt_leaf, const Geometry& g, cudaStream_t stream);
+int pw_set_charges(PwPlan* pw, cudaStream_t stream);
+int pw_eval(PwPlan* pw, cudaStream_t stream);
+void pw_free_sources(PwPlan* pw);
+void pw_free(PwPlan* pw);
+
+}  // namespace pdmk

@@ -1,0 +1,111 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 Ewald oracle.
+
+Relative L2 errors E_rel = ||Phi - Phi_ref|| / ||Phi_ref|| must stay within the requested
+eps for the potential; gradients (not part of the paper's error measure) within 10 eps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ewald as E
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_28608_b300 as P
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+_cache = {}
+
+
+def oracle_ref(g):
+    key = g["name"]
+    if key not in _cache:
+        _cache[key] = E.ewald(g["L"], g["y"], g["q"])
+    return _cache[key]
+
+
+def run(g, eps, **kw):
+    P = _cuda()
+    plan = P.Plan(g["L"], eps, **kw)
+    plan.set_sources(g["y"], g["q"])
+    pot, grad = plan.eval()
+    info = plan.info()
+    plan.close()
+    return pot, grad, info
+
+
+CASES = {
+    "cube": lambda: W.cube_uniform(2000),
+    "oblique2d": lambda: W.oblique2d_clusters(3000),
+    "triclinic3d": lambda: W.triclinic3d_clusters(3000, nclusters=8),
+    "random2d": lambda: W.random_neutral(np.array([[1.0, 0.3], [0.0, 0.7]]), 1500, seed=5),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_fp64_parity(case, eps):
+    g = CASES[case]()
+    pref, gref = oracle_ref(g)
+    pot, grad, info = run(g, eps, precision="fp64")
+    ep, eg = rel(pot, pref), rel(grad, gref)
+    print(f"{case} eps={eps:g}: E_pot={ep:.2e} E_grad={eg:.2e} info={info['M']} depth={info['depth']}")
+    assert ep <= eps
+    assert eg <= 10 * eps
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("eps", [1e-3, 1e-6])
+def test_mixed_parity(case, eps):
+    g = CASES[case]()
+    pref, gref = oracle_ref(g)
+    pot, grad, info = run(g, eps, precision="mixed")
+    ep, eg = rel(pot, pref), rel(grad, gref)
+    print(f"mixed {case} eps={eps:g}: E_pot={ep:.2e} E_grad={eg:.2e}")
+    assert ep <= eps
+    assert eg <= 10 * eps
+
+
+def test_madelung_through_gpu():
+    g = W.nacl_primitive_fcc()
+    pot, grad, _ = run(g, 1e-9, precision="fp64")
+    M = 1.7475645946331822
+    assert np.max(np.abs(pot - (-M / (4 * math.pi * 0.5)) * g["q"])) < 1e-9
+    assert np.max(np.abs(grad)) < 1e-8
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_non_neutral_zero_mean(d):
+    L = np.array([[1.0, 0.4], [0.0, 0.9]]) if d == 2 else W.lattice_from_lengths_angles(1, 1.2, 0.9, 80, 100, 70)
+    g = W.random_neutral(L, 800, seed=21, neutral=False)
+    pref, gref = E.ewald(g["L"], g["y"], g["q"])
+    pot, grad, _ = run(g, 1e-6, precision="fp64")
+    assert rel(pot, pref) <= 1e-6
+    assert rel(grad, gref) <= 1e-5
+
+
+def test_frame_and_basis_invariance():
+    """Rotated, reflected and re-ordered lattice vectors give the oracle's answer (potential
+    invariant, gradient rotated back into the caller's frame)."""
+    g = W.random_neutral(W.lattice_from_lengths_angles(1.0, 1.3, 0.8, 75, 95, 110), 600, seed=4)
+    Q, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((3, 3)))
+    if np.linalg.det(Q) > 0:
+        Q[:, 0] = -Q[:, 0]  # a reflection
+    L2 = (Q @ g["L"])[:, [2, 0, 1]]
+    y2 = g["y"] @ Q.T
+    pref, gref = E.ewald(L2, y2, g["q"])
+    pot, grad, _ = run(dict(L=L2, y=y2, q=g["q"], name="rot"), 1e-6)
+    assert rel(pot, pref) <= 1e-6
+    assert rel(grad, gref) <= 1e-5
