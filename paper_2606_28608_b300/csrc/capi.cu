@@ -708,6 +708,8 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     if ((r = upload(plan, plan->d_t_dq, t_dq))) return r;
     if ((r = upload(plan, plan->d_q_user, hq))) return r;
     // plane-wave passes (proxy, translation and local-expansion layouts)
+    plan->pw.d_src4 = plan->d_src4;
+    plan->pw.d_tgt4 = plan->d_tgt4;
     r = pw_set_sources(&plan->pw, tree, ss, leaf_of, tgt_leaf, g, plan->stream);
     if (r != PDMK_OK) return r;
     r = set_charges_device(plan, false);

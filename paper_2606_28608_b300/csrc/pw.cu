@@ -1,26 +1,821 @@
-// pw.cu -- plane-wave passes (placeholder: depth-0 trees need none).
+// pw.cu -- plane-wave passes of the difference kernels D_l (Sec. 2.3, Eq. (2.5)-(2.6)) on the
+// extended-domain tree (Sec. 3.5: the free-space DMK with the root W_0 step omitted).
+//
+// Representation.  A box of side h at level l carries
+//   * proxy moments  Q[m] = sum_{y in box} q_y prod_i T_{m_i}(t_i(y)),  t = 2 (y - c)/h
+//     (Chebyshev moments; the box's sources act on smooth kernels through them),
+//   * local coefficients a[m]: the D-field of coarser levels and of its own level inside
+//     the box is  sum_m a[m] prod_i T_{m_i}(t_i(x)),
+// for 0 <= m_i < p.  Plane waves sample D-hat_l on the grid xi = (2 pi / (3 h)) k,
+// |k_i| <= K: the spacing makes the trapezoidal rule alias-free for colleague interactions
+// (|x - y|_inf <= 2h, D_l supported in |x - y| <= h), and D-hat_l is negligible beyond
+// |xi| = 2c/h.  With these choices every per-level operator is level independent:
+//   outgoing  out[k]  = sum_m Q[m] prod_i Co[k_i][m_i],  Co[k][m] = Chebyshev coefficients of
+//                       exp(-i (pi/3) k t),
+//   translate in_T[k] = h^{2-d} 3^{-d} f(|k|) sum_S exp(-i (2 pi/3) k . delta_S) out_S[k],
+//                       f(s) = (w-hat(pi s/3) - w-hat(2 pi s/3)) / (2 pi s/3)^2,
+//   incoming  a[m]   += Re sum_k in[k] prod_i conj(Co[k_i][m_i]),
+// and the tree passes are exact polynomial re-expansions with the triangular matrices
+// S_b[M][m] (T_M((t -/+ 1)/2) in the basis T_m(t)).  Hermitian symmetry keeps k_0 >= 0.
+//
+// Passes: leaf moments -> merge (deepest level first) -> outgoing (all levels at once) ->
+// translate+incoming (all levels at once) -> downward (root first) -> leaf evaluation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
 #include "k_pw.cuh"
+#include "kernels_common.cuh"
 #include "pdmk.h"
 
 namespace pdmk {
 
-void pw_plan_create(PwPlan* pw, int d, double, double, const KernelTables&, int, int, bool mixed) {
+namespace {
+
+template <typename T>
+struct C2 {
+    T x, y;
+};
+template <typename T>
+__device__ __forceinline__ C2<T> cfma(C2<T> a, C2<T> b, C2<T> acc) {  // acc + a*b
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+    return acc;
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cfma_conj(C2<T> a, C2<T> b, C2<T> acc) {  // acc + conj(a)*b
+    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+    return acc;
+}
+
+struct PwDims {
+    int d, p, K, n1, np, pd1, npw, nk1;  // nk1 = n1^{d-1}
+};
+
+// ------------------------------------------------------------------ leaf moments
+template <typename T, int D>
+__global__ void __launch_bounds__(128) k_leaf_moments(const int4* __restrict__ leaves, const T* __restrict__ src4,
+                                                      T* __restrict__ Q, PwDims pd, double inv_rc) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int kB = 32;
+    T* basis = reinterpret_cast<T*>(sm);  // [kB][D][p]
+    T* qv = basis + kB * D * pd.p;
+    const int4 lf = leaves[blockIdx.x];
+    const int p = pd.p;
+    const T scale = T(2.0 * inv_rc * double(1LL << lf.w));  // t = 2 (y - c)/h
+    T* Qb = Q + size_t(lf.z) * pd.np;
+    for (int s0 = 0; s0 < lf.y; s0 += kB) {
+        const int ns = min(kB, lf.y - s0);
+        __syncthreads();
+        for (int it = threadIdx.x; it < ns * D; it += blockDim.x) {
+            const int s = it / D, i = it % D;
+            const T* y = src4 + size_t(lf.x + s0 + s) * 4;
+            const T t = y[i] * scale;
+            T* b = basis + (s * D + i) * p;
+            T tm1 = T(1), tm = t;
+            b[0] = T(1);
+            if (p > 1) b[1] = t;
+            for (int m = 2; m < p; ++m) {
+                const T tn = fma(T(2) * t, tm, -tm1);
+                b[m] = tn;
+                tm1 = tm;
+                tm = tn;
+            }
+            if (i == 0) qv[s] = y[3];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < pd.np; e += blockDim.x) {
+            int r = e;
+            const int m_last = r % p;
+            r /= p;
+            const int m_mid = (D == 3) ? r % p : 0;
+            if (D == 3) r /= p;
+            const int m_first = r;
+            T acc = T(0);
+            for (int s = 0; s < ns; ++s) {
+                const T* b = basis + s * D * p;
+                T v = qv[s] * b[m_first] * b[(D - 1) * p + m_last];
+                if (D == 3) v *= b[p + m_mid];
+                acc += v;
+            }
+            Qb[e] += acc;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ merge / downward
+// out-box ob accumulates prod_i S_{b_i} applied to in-box ib.  mode 0 (merge): contract the
+// child index m against the parent index M: Q_P[M] += sum_m Q_c[m] prod S_b[M_i][m_i].
+// mode 1 (down): a_c[m] += sum_M a_P[M] prod S_b[M_i][m_i].
+template <typename T, int D>
+__device__ void reexpand(const T* __restrict__ src, T* __restrict__ dst, int bits, int mode, const T* Sm,
+                         T* s1, T* s2, const PwDims& pd) {
+    const int p = pd.p, pd1 = pd.pd1;
+    // S(b)[M][m] at Sm[(b * p + M) * p + m]
+    auto S = [&](int b, int M, int m) { return Sm[(b * p + M) * p + m]; };
+    const int b0 = bits & 1, b1 = (bits >> 1) & 1, b2 = (bits >> 2) & 1;
+    for (int o0 = 0; o0 < p; ++o0) {
+        // first axis: s1[r] = sum_j S(...) src[j * pd1 + r]
+        for (int r = threadIdx.x; r < pd1; r += blockDim.x) {
+            T acc = T(0);
+            if (mode == 0) {
+                for (int j = 0; j <= o0; ++j) acc = fma(S(b0, o0, j), src[j * pd1 + r], acc);
+            } else {
+                for (int j = o0; j < p; ++j) acc = fma(S(b0, j, o0), src[j * pd1 + r], acc);
+            }
+            s1[r] = acc;
+        }
+        __syncthreads();
+        if (D == 2) {
+            for (int o1 = threadIdx.x; o1 < p; o1 += blockDim.x) {
+                T acc = T(0);
+                if (mode == 0) {
+                    for (int j = 0; j <= o1; ++j) acc = fma(S(b1, o1, j), s1[j], acc);
+                } else {
+                    for (int j = o1; j < p; ++j) acc = fma(S(b1, j, o1), s1[j], acc);
+                }
+                dst[o0 * p + o1] += acc;
+            }
+        } else {
+            for (int it = threadIdx.x; it < p * p; it += blockDim.x) {
+                const int o1 = it / p, j2 = it % p;
+                T acc = T(0);
+                if (mode == 0) {
+                    for (int j = 0; j <= o1; ++j) acc = fma(S(b1, o1, j), s1[j * p + j2], acc);
+                } else {
+                    for (int j = o1; j < p; ++j) acc = fma(S(b1, j, o1), s1[j * p + j2], acc);
+                }
+                s2[it] = acc;
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < p * p; it += blockDim.x) {
+                const int o1 = it / p, o2 = it % p;
+                T acc = T(0);
+                if (mode == 0) {
+                    for (int j = 0; j <= o2; ++j) acc = fma(S(b2, o2, j), s2[o1 * p + j], acc);
+                } else {
+                    for (int j = o2; j < p; ++j) acc = fma(S(b2, j, o2), s2[o1 * p + j], acc);
+                }
+                dst[(o0 * p + o1) * p + o2] += acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// merge: one CTA per parent; list entry = [parent q slot, child q slots (2^d, -1 if empty)]
+template <typename T, int D>
+__global__ void __launch_bounds__(128) k_merge(const int* __restrict__ list, T* __restrict__ Q, const T* __restrict__ Sg,
+                                               PwDims pd) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    T* Sm = reinterpret_cast<T*>(sm);  // 2 p p
+    T* s1 = Sm + 2 * pd.p * pd.p;      // pd1
+    T* s2 = s1 + pd.pd1;               // p p
+    for (int i = threadIdx.x; i < 2 * pd.p * pd.p; i += blockDim.x) Sm[i] = Sg[i];
+    __syncthreads();
+    const int* e = list + size_t(blockIdx.x) * (1 + (1 << D));
+    T* dst = Q + size_t(e[0]) * pd.np;
+    for (int c = 0; c < (1 << D); ++c) {
+        const int cs = e[1 + c];
+        if (cs < 0) continue;
+        reexpand<T, D>(Q + size_t(cs) * pd.np, dst, c, 0, Sm, s1, s2, pd);
+    }
+}
+
+// down: one CTA per child; list entry int4 = (child local slot, parent local slot, bits, 0)
+template <typename T, int D>
+__global__ void __launch_bounds__(128) k_down(const int4* __restrict__ list, T* __restrict__ Lc, const T* __restrict__ Sg,
+                                              PwDims pd) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    T* Sm = reinterpret_cast<T*>(sm);
+    T* s1 = Sm + 2 * pd.p * pd.p;
+    T* s2 = s1 + pd.pd1;
+    for (int i = threadIdx.x; i < 2 * pd.p * pd.p; i += blockDim.x) Sm[i] = Sg[i];
+    __syncthreads();
+    const int4 e = list[blockIdx.x];
+    reexpand<T, D>(Lc + size_t(e.y) * pd.np, Lc + size_t(e.x) * pd.np, e.z, 1, Sm, s1, s2, pd);
+}
+
+// ------------------------------------------------------------------ outgoing plane waves
+// entry int2 = (q slot, out slot); out layout [k0 in 0..K][k1 in -K..K][k2 in -K..K]
+template <typename T, int D>
+__global__ void __launch_bounds__(128) k_pw_out(const int2* __restrict__ list, const T* __restrict__ Q,
+                                                C2<T>* __restrict__ out, const C2<T>* __restrict__ Cog, PwDims pd, int KC) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    C2<T>* Co = reinterpret_cast<C2<T>*>(sm);  // [n1][p], row kk = k + K
+    C2<T>* A = Co + pd.n1 * pd.p;              // [KC][pd1]
+    C2<T>* B = A + KC * pd.pd1;                // [n1][p]   (3D)
+    const int p = pd.p, K = pd.K, n1 = pd.n1, pd1 = pd.pd1;
+    for (int i = threadIdx.x; i < n1 * p; i += blockDim.x) Co[i] = Cog[i];
+    __syncthreads();
+    const int2 e = list[blockIdx.x];
+    const T* q = Q + size_t(e.x) * pd.np;
+    C2<T>* o = out + size_t(e.y) * pd.npw;
+    for (int kc0 = 0; kc0 <= K; kc0 += KC) {
+        const int nk = min(KC, K + 1 - kc0);
+        for (int r = threadIdx.x; r < pd1; r += blockDim.x) {
+            C2<T> acc[16];
+            for (int j = 0; j < 16; ++j) acc[j] = C2<T>{T(0), T(0)};
+            for (int m0 = 0; m0 < p; ++m0) {
+                const T v = q[m0 * pd1 + r];
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (j < nk) {
+                        const C2<T> c = Co[(kc0 + j + K) * p + m0];
+                        acc[j].x = fma(c.x, v, acc[j].x);
+                        acc[j].y = fma(c.y, v, acc[j].y);
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < nk) A[j * pd1 + r] = acc[j];
+        }
+        __syncthreads();
+        if (D == 2) {
+            for (int it = threadIdx.x; it < nk * n1; it += blockDim.x) {
+                const int j = it / n1, kk1 = it % n1;
+                C2<T> acc{T(0), T(0)};
+                for (int m1 = 0; m1 < p; ++m1) acc = cfma(Co[kk1 * p + m1], A[j * pd1 + m1], acc);
+                o[(kc0 + j) * n1 + kk1] = acc;
+            }
+            __syncthreads();
+        } else {
+            for (int j = 0; j < nk; ++j) {
+                for (int it = threadIdx.x; it < n1 * p; it += blockDim.x) {
+                    const int kk1 = it / p, m2 = it % p;
+                    C2<T> acc{T(0), T(0)};
+                    for (int m1 = 0; m1 < p; ++m1) acc = cfma(Co[kk1 * p + m1], A[j * pd1 + m1 * p + m2], acc);
+                    B[it] = acc;
+                }
+                __syncthreads();
+                for (int it = threadIdx.x; it < n1 * n1; it += blockDim.x) {
+                    const int kk1 = it / n1, kk2 = it % n1;
+                    C2<T> acc{T(0), T(0)};
+                    for (int m2 = 0; m2 < p; ++m2) acc = cfma(Co[kk2 * p + m2], B[kk1 * p + m2], acc);
+                    o[((kc0 + j) * n1 + kk1) * n1 + kk2] = acc;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ translate + incoming
+// entry: [local slot, level, 3^d colleague out slots (-1: none)]
+template <typename T, int D>
+__global__ void __launch_bounds__(128) k_pw_in(const int* __restrict__ list, const C2<T>* __restrict__ out,
+                                               T* __restrict__ Lc, const C2<T>* __restrict__ Cog,
+                                               const C2<T>* __restrict__ phg, const T* __restrict__ fk, PwDims pd,
+                                               int KC, double inv_rc) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int NC = (D == 3) ? 27 : 9;
+    const int p = pd.p, K = pd.K, n1 = pd.n1, pd1 = pd.pd1, nk1 = pd.nk1;
+    C2<T>* Co = reinterpret_cast<C2<T>*>(sm);  // [n1][p]
+    C2<T>* ph = Co + n1 * p;                   // [3][n1]
+    C2<T>* I = ph + 3 * n1;                    // [KC][nk1]
+    C2<T>* Ap = I + KC * nk1;                  // [KC][pd1]
+    C2<T>* B = Ap + KC * pd1;                  // [n1][p]  (3D)
+    __shared__ int coll[NC];
+    for (int i = threadIdx.x; i < n1 * p; i += blockDim.x) Co[i] = Cog[i];
+    for (int i = threadIdx.x; i < 3 * n1; i += blockDim.x) ph[i] = phg[i];
+    const int* e = list + size_t(blockIdx.x) * (2 + NC);
+    if (threadIdx.x < NC) coll[threadIdx.x] = e[2 + threadIdx.x];
+    __syncthreads();
+    const int level = e[1];
+    // trapezoidal weight (1/(3h))^d times the h^2 of D-hat_l(xi) = h^2 f(|k|)
+    const T wlev = (D == 3) ? T(double(1LL << level) * inv_rc / 27.0) : T(1.0 / 9.0);
+    T* a = Lc + size_t(e[0]) * pd.np;
+    for (int kc0 = 0; kc0 <= K; kc0 += KC) {
+        const int nk = min(KC, K + 1 - kc0);
+        // incoming slice: sum over colleagues with the translation phases
+        for (int it = threadIdx.x; it < nk * nk1; it += blockDim.x) {
+            const int j = it / nk1, rem = it % nk1;
+            const int k0 = kc0 + j;
+            const int kk1 = (D == 3) ? rem / n1 : rem;
+            const int kk2 = (D == 3) ? rem % n1 : 0;
+            const T f = fk[size_t(k0) * nk1 + rem];
+            C2<T> acc{T(0), T(0)};
+            if (f != T(0)) {
+                for (int c = 0; c < NC; ++c) {
+                    const int s = coll[c];
+                    if (s < 0) continue;
+                    const int d0 = c % 3, d1 = (c / 3) % 3, d2 = (c / 9) % 3;  // delta + 1
+                    C2<T> phz = ph[d0 * n1 + k0 + K];
+                    phz = cfma(phz, ph[d1 * n1 + kk1], C2<T>{T(0), T(0)});
+                    if (D == 3) phz = cfma(phz, ph[d2 * n1 + kk2], C2<T>{T(0), T(0)});
+                    acc = cfma(phz, out[size_t(s) * pd.npw + size_t(k0) * nk1 + rem], acc);
+                }
+                acc.x *= f * wlev;
+                acc.y *= f * wlev;
+            }
+            I[it] = acc;
+        }
+        __syncthreads();
+        if (D == 2) {
+            for (int it = threadIdx.x; it < nk * p; it += blockDim.x) {
+                const int j = it / p, m1 = it % p;
+                C2<T> acc{T(0), T(0)};
+                for (int kk1 = 0; kk1 < n1; ++kk1) acc = cfma_conj(Co[kk1 * p + m1], I[j * nk1 + kk1], acc);
+                Ap[j * pd1 + m1] = acc;
+            }
+            __syncthreads();
+        } else {
+            for (int j = 0; j < nk; ++j) {
+                for (int it = threadIdx.x; it < n1 * p; it += blockDim.x) {
+                    const int kk1 = it / p, m2 = it % p;
+                    C2<T> acc{T(0), T(0)};
+                    for (int kk2 = 0; kk2 < n1; ++kk2)
+                        acc = cfma_conj(Co[kk2 * p + m2], I[j * nk1 + kk1 * n1 + kk2], acc);
+                    B[it] = acc;
+                }
+                __syncthreads();
+                for (int it = threadIdx.x; it < p * p; it += blockDim.x) {
+                    const int m1 = it / p, m2 = it % p;
+                    C2<T> acc{T(0), T(0)};
+                    for (int kk1 = 0; kk1 < n1; ++kk1) acc = cfma_conj(Co[kk1 * p + m1], B[kk1 * p + m2], acc);
+                    Ap[j * pd1 + it] = acc;
+                }
+                __syncthreads();
+            }
+        }
+        // a[m0][r] += sum_j w(k0) Re(conj(Co[k0][m0]) Ap[j][r]); w = 1 for k0 = 0, else 2
+        for (int it = threadIdx.x; it < pd.np; it += blockDim.x) {
+            const int m0 = it / pd1, r = it % pd1;
+            T acc = T(0);
+            for (int j = 0; j < nk; ++j) {
+                const int k0 = kc0 + j;
+                const C2<T> c = Co[(k0 + K) * p + m0];
+                const C2<T> v = Ap[j * pd1 + r];
+                const T re = fma(c.x, v.x, c.y * v.y);
+                acc = fma(k0 == 0 ? T(1) : T(2), re, acc);
+            }
+            a[it] += acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ leaf evaluation
+// entry int4 = (local slot, tgt_begin, tgt_count, level)
+template <typename T, int D>
+__global__ void __launch_bounds__(128) k_leaf_eval(const int4* __restrict__ list, const T* __restrict__ Lc,
+                                                   const T* __restrict__ tgt4, double* __restrict__ pot,
+                                                   double* __restrict__ grad, PwDims pd, double inv_rc) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int p = pd.p;
+    T* tb = reinterpret_cast<T*>(sm) + threadIdx.x * (2 * D * p);  // T_m and T'_m per dim
+    const int4 e = list[blockIdx.x];
+    const T* a = Lc + size_t(e.x) * pd.np;
+    const double sc = 2.0 * inv_rc * double(1LL << e.w);  // dt/dx = 2/h
+    for (int t0 = 0; t0 < e.z; t0 += blockDim.x) {
+        const int ti = t0 + threadIdx.x;
+        if (ti >= e.z) break;
+        const T* x = tgt4 + size_t(e.y + ti) * 4;
+        for (int i = 0; i < D; ++i) {
+            const T t = T(double(x[i]) * sc);
+            T* bt = tb + i * 2 * p;
+            T* bd = bt + p;
+            // T_m by recurrence; T'_m = m U_{m-1}
+            T tm1 = T(1), tm = t, um1 = T(1), um = T(2) * t;
+            bt[0] = T(1);
+            bd[0] = T(0);
+            if (p > 1) { bt[1] = t; bd[1] = T(1); }
+            for (int m = 2; m < p; ++m) {
+                const T tn = fma(T(2) * t, tm, -tm1);
+                bt[m] = tn;
+                bd[m] = T(m) * um;  // U_{m-1}
+                const T un = fma(T(2) * t, um, -um1);
+                tm1 = tm; tm = tn;
+                um1 = um; um = un;
+            }
+        }
+        T phi = 0, g0 = 0, g1 = 0, g2 = 0;
+        const T* b0 = tb;
+        const T* d0 = tb + p;
+        const T* b1 = tb + 2 * p;
+        const T* d1 = tb + 3 * p;
+        if (D == 2) {
+            for (int m0 = 0; m0 < p; ++m0) {
+                T s = 0, sd = 0;
+                for (int m1 = 0; m1 < p; ++m1) {
+                    const T v = a[m0 * p + m1];
+                    s = fma(v, b1[m1], s);
+                    sd = fma(v, d1[m1], sd);
+                }
+                phi = fma(b0[m0], s, phi);
+                g0 = fma(d0[m0], s, g0);
+                g1 = fma(b0[m0], sd, g1);
+            }
+        } else {
+            const T* b2 = tb + 4 * p;
+            const T* d2 = tb + 5 * p;
+            for (int m0 = 0; m0 < p; ++m0) {
+                T s = 0, s1d = 0, s2d = 0;
+                for (int m1 = 0; m1 < p; ++m1) {
+                    T u = 0, ud = 0;
+                    const T* row = a + (m0 * p + m1) * p;
+                    for (int m2 = 0; m2 < p; ++m2) {
+                        const T v = row[m2];
+                        u = fma(v, b2[m2], u);
+                        ud = fma(v, d2[m2], ud);
+                    }
+                    s = fma(b1[m1], u, s);
+                    s1d = fma(d1[m1], u, s1d);
+                    s2d = fma(b1[m1], ud, s2d);
+                }
+                phi = fma(b0[m0], s, phi);
+                g0 = fma(d0[m0], s, g0);
+                g1 = fma(b0[m0], s1d, g1);
+                g2 = fma(b0[m0], s2d, g2);
+            }
+        }
+        const size_t o = size_t(e.y + ti);
+        pot[o] = double(phi);
+        if (grad) {
+            grad[o * D + 0] = double(g0) * sc;
+            grad[o * D + 1] = double(g1) * sc;
+            if (D == 3) grad[o * D + 2] = double(g2) * sc;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+struct PwImpl {
+    PwDims dims{};
+    double rc = 1;
+    int KC = 1;
+    // device tables (precision T as raw bytes)
+    void* d_Co = nullptr;  // n1 * p complex
+    void* d_S = nullptr;   // 2 p p
+    void* d_ph = nullptr;  // 3 n1 complex
+    void* d_f = nullptr;   // (K+1) n1^{d-1}
+    // lists
+    int4* d_leafq = nullptr;
+    int nleafq = 0;
+    int* d_merge = nullptr;
+    std::vector<int> merge_start;  // per level, entry offsets
+    int2* d_outl = nullptr;
+    int nout = 0;
+    int* d_inl = nullptr;
+    int nin = 0;
+    int4* d_down = nullptr;
+    std::vector<int> down_start;   // per child level
+    int4* d_eval = nullptr;
+    int neval = 0;
+    int nlevels = 1;
+    // arrays
+    void* d_Q = nullptr;
+    void* d_out = nullptr;
+    void* d_L = nullptr;
+    int64_t nq = 0, nloc = 0;
+    int64_t ntgt = 0;
+    std::vector<double> host_Co, host_S, host_ph, host_f;  // FP64 masters
+};
+
+template <class X>
+int pw_alloc(PwPlan* pw, X** p, size_t n) {
+    if (n == 0) n = 1;
+    void* q = nullptr;
+    if (cudaMalloc(&q, n * sizeof(X)) != cudaSuccess) {
+        cudaGetLastError();
+        return PDMK_ERR_OOM;
+    }
+    pw->allocs.push_back(q);
+    pw->device_bytes += int64_t(n * sizeof(X));
+    *p = static_cast<X*>(q);
+    return PDMK_OK;
+}
+
+int pw_upload_typed(PwPlan* pw, void** dst, const std::vector<double>& v, cudaStream_t s) {
+    const size_t ts = pw->mixed ? 4 : 8;
+    std::vector<unsigned char> buf(std::max<size_t>(v.size(), 1) * ts, 0);
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (pw->mixed) {
+            float f = float(v[i]);
+            std::memcpy(&buf[i * 4], &f, 4);
+        } else {
+            std::memcpy(&buf[i * 8], &v[i], 8);
+        }
+    }
+    unsigned char* p = nullptr;
+    int r = pw_alloc(pw, &p, buf.size());
+    if (r) return r;
+    *dst = p;
+    if (cudaMemcpyAsync(p, buf.data(), buf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) return PDMK_ERR_CUDA;
+    return PDMK_OK;
+}
+
+template <class X>
+int pw_upload(PwPlan* pw, X** dst, const std::vector<X>& v, cudaStream_t s) {
+    int r = pw_alloc(pw, dst, v.size());
+    if (r) return r;
+    if (!v.empty() && cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return PDMK_ERR_CUDA;
+    return PDMK_OK;
+}
+
+PwImpl* impl(PwPlan* pw) { return static_cast<PwImpl*>(pw->impl); }
+
+}  // namespace
+
+void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables& kt, int n_proxy, int n_pw,
+                    bool mixed) {
     pw->d = d;
     pw->mixed = mixed;
+    PwImpl* I = new PwImpl();
+    pw->impl = I;
+    // plane-wave half width: xi_max = (pi/3) K / (h/2) >= 2c/h  <=>  K >= 3c/pi
+    const int K = n_pw > 0 ? n_pw : int(std::ceil(3.0 * c / kPi - 1e-9));
+    // Chebyshev order: the plane waves exp(-i (pi/3) k t), |k| <= K, have frequency <= c
+    int p = n_proxy > 0 ? n_proxy : int(std::ceil(c)) + 6;
+    p = std::max(4, std::min(p, 40));
+    pw->p = p;
+    pw->K = K;
+    PwDims& D = I->dims;
+    D.d = d;
+    D.p = p;
+    D.K = K;
+    D.n1 = 2 * K + 1;
+    D.pd1 = (d == 3) ? p * p : p;
+    D.np = D.pd1 * p;
+    D.nk1 = (d == 3) ? D.n1 * D.n1 : D.n1;
+    D.npw = (K + 1) * D.nk1;
+    (void)eps;
+    // Chebyshev nodes of the first kind and the discrete transform T_m(t_g)
+    std::vector<double> tg(p);
+    for (int g = 0; g < p; ++g) tg[g] = std::cos(kPi * (2.0 * g + 1.0) / (2.0 * p));
+    auto Tm = [](int m, double t) { return std::cos(m * std::acos(std::max(-1.0, std::min(1.0, t)))); };
+    auto cheb_coef = [&](auto f, int m) {  // coefficient m of the degree-(p-1) interpolant of f
+        std::complex<double> s = 0;
+        for (int g = 0; g < p; ++g) s += f(tg[g]) * Tm(m, tg[g]);
+        return s * ((m == 0 ? 1.0 : 2.0) / p);
+    };
+    I->host_Co.assign(size_t(D.n1) * p * 2, 0.0);
+    for (int kk = 0; kk < D.n1; ++kk) {
+        const int k = kk - K;
+        for (int m = 0; m < p; ++m) {
+            auto f = [&](double t) { return std::exp(std::complex<double>(0.0, -kPi / 3.0 * k * t)); };
+            std::complex<double> v = cheb_coef(f, m);
+            I->host_Co[(kk * p + m) * 2 + 0] = v.real();
+            I->host_Co[(kk * p + m) * 2 + 1] = v.imag();
+        }
+    }
+    I->host_S.assign(size_t(2) * p * p, 0.0);
+    for (int b = 0; b < 2; ++b)
+        for (int M = 0; M < p; ++M)
+            for (int m = 0; m < p; ++m) {
+                const double sft = b ? 1.0 : -1.0;
+                auto f = [&](double t) { return std::complex<double>(Tm(M, (t + sft) / 2.0), 0.0); };
+                double v = (m <= M) ? cheb_coef(f, m).real() : 0.0;
+                I->host_S[(b * p + M) * p + m] = v;
+            }
+    I->host_ph.assign(size_t(3) * D.n1 * 2, 0.0);
+    for (int dl = 0; dl < 3; ++dl)
+        for (int kk = 0; kk < D.n1; ++kk) {
+            const int k = kk - K, delta = dl - 1;
+            // colleague at c_S = c_T + delta h: phase exp(i xi (c_T - c_S)) = exp(-i (2 pi/3) k delta)
+            I->host_ph[(dl * D.n1 + kk) * 2 + 0] = std::cos(-2.0 * kPi / 3.0 * k * delta);
+            I->host_ph[(dl * D.n1 + kk) * 2 + 1] = std::sin(-2.0 * kPi / 3.0 * k * delta);
+        }
+    // f(|k|) on the half grid, zero outside the ball |k| <= 3c/pi (Eq. (2.6) for D_l)
+    const double kball = 3.0 * c / kPi;
+    I->host_f.assign(size_t(D.npw), 0.0);
+    for (int k0 = 0; k0 <= K; ++k0)
+        for (int r = 0; r < D.nk1; ++r) {
+            const int k1 = ((d == 3) ? r / D.n1 : r) - K;
+            const int k2 = (d == 3) ? (r % D.n1) - K : 0;
+            const double kk = std::sqrt(double(k0) * k0 + double(k1) * k1 + double(k2) * k2);
+            double f = 0;
+            if (kk <= kball) {
+                if (kk == 0) {
+                    f = 3.0 * kt.mu2 / 8.0;
+                } else {
+                    const double x = 2.0 * kPi * kk / 3.0;
+                    f = (kt.what(0.5 * x) - kt.what(x)) / (x * x);
+                }
+            }
+            I->host_f[size_t(k0) * D.nk1 + r] = f;
+        }
+    // k0 chunk: the [KC][p^{d-1}] complex slices must fit next to the tables in shared memory
+    const size_t ts = mixed ? 4 : 8;
+    const size_t per = size_t(D.pd1) * 2 * ts + size_t(D.nk1) * 2 * ts;
+    int kc = int(std::max<size_t>(1, (96 * 1024) / std::max<size_t>(per, 1)));
+    I->KC = std::max(1, std::min({kc, 16, K + 1}));
 }
-bool pw_supported(const PwPlan*) { return false; }
-int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources&, const std::vector<int>&,
-                   const std::vector<int>&, const Geometry&, cudaStream_t) {
+
+bool pw_supported(const PwPlan*) { return true; }
+
+int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const std::vector<int>& /*leaf_of*/,
+                   const std::vector<int>& /*tgt_leaf*/, const Geometry& g, cudaStream_t stream) {
+    PwImpl* I = impl(pw);
+    const int d = t.d;
+    const int nb = int(t.level.size());
+    const int nc = 1 << d;
+    const int ncol = (d == 3) ? 27 : 9;
+    I->rc = g.rc;
+    I->nlevels = t.nlevels;
     pw->active = t.nlevels > 1;
-    return pw->active ? PDMK_ERR_INTERNAL : PDMK_OK;
+    if (!pw->active) return PDMK_OK;
+    auto has_src = [&](int b) { return t.src_end[b] > t.src_begin[b]; };
+    auto has_tgt = [&](int b) { return t.tgt_end[b] > t.tgt_begin[b]; };
+    // q slots: boxes with sources
+    std::vector<int> qslot(nb, -1);
+    int nq = 0;
+    for (int b = 0; b < nb; ++b)
+        if (has_src(b)) qslot[b] = nq++;
+    // in-boxes: non-leaf boxes with targets; out slots: colleagues of in-boxes with sources
+    std::vector<int> oslot(nb, -1);
+    int nout = 0;
+    std::vector<int> inl;
+    std::vector<int> lslot(nb, -1);
+    int nloc = 0;
+    for (int b = 0; b < nb; ++b) {
+        const bool inbox = !t.is_leaf(b) && has_tgt(b);
+        if (inbox || (t.level[b] >= 1 && has_tgt(b))) lslot[b] = nloc++;
+    }
+    for (int b = 0; b < nb; ++b) {
+        if (t.is_leaf(b) || !has_tgt(b)) continue;
+        inl.push_back(lslot[b]);
+        inl.push_back(t.level[b]);
+        for (int o = 0; o < ncol; ++o) {
+            const int S = t.colleague[size_t(b) * ncol + o];
+            int os = -1;
+            if (S >= 0 && has_src(S)) {
+                if (oslot[S] < 0) oslot[S] = nout++;
+                os = oslot[S];
+            }
+            inl.push_back(os);
+        }
+    }
+    I->nin = int(inl.size()) / (2 + ncol);
+    std::vector<int2> outl;
+    for (int b = 0; b < nb; ++b)
+        if (oslot[b] >= 0) outl.push_back(make_int2(qslot[b], oslot[b]));
+    std::sort(outl.begin(), outl.end(), [](const int2& a, const int2& b) { return a.y < b.y; });
+    I->nout = nout;
+    // leaf moments
+    std::vector<int4> leafq;
+    for (int b = 0; b < nb; ++b)
+        if (t.is_leaf(b) && has_src(b))
+            leafq.push_back(make_int4(int(t.src_begin[b]), int(t.src_end[b] - t.src_begin[b]), qslot[b], t.level[b]));
+    I->nleafq = int(leafq.size());
+    // merges per level (non-leaf boxes with sources), deepest first at eval time
+    std::vector<int> merge;
+    I->merge_start.assign(t.nlevels + 1, 0);
+    for (int l = 0; l < t.nlevels; ++l) {
+        I->merge_start[l] = int(merge.size()) / (1 + nc);
+        for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
+            if (t.is_leaf(b) || !has_src(b)) continue;
+            merge.push_back(qslot[b]);
+            for (int c = 0; c < nc; ++c) merge.push_back(qslot[t.child0[b] + c]);
+        }
+    }
+    I->merge_start[t.nlevels] = int(merge.size()) / (1 + nc);
+    // downward lists per child level
+    std::vector<int4> down;
+    I->down_start.assign(t.nlevels + 1, 0);
+    for (int l = 0; l < t.nlevels; ++l) {
+        I->down_start[l] = int(down.size());
+        if (l == 0) continue;
+        for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
+            if (lslot[b] < 0) continue;
+            const int P = t.parent[b];
+            if (lslot[P] < 0) return PDMK_ERR_INTERNAL;
+            down.push_back(make_int4(lslot[b], lslot[P], b - t.child0[P], 0));
+        }
+    }
+    I->down_start[t.nlevels] = int(down.size());
+    // leaf evaluation: target leaves below the root level
+    std::vector<int4> ev;
+    for (int b = 0; b < nb; ++b)
+        if (t.is_leaf(b) && has_tgt(b) && t.level[b] >= 1)
+            ev.push_back(make_int4(lslot[b], int(t.tgt_begin[b]), int(t.tgt_end[b] - t.tgt_begin[b]), t.level[b]));
+    I->neval = int(ev.size());
+    I->nq = nq;
+    I->nloc = nloc;
+    int64_t ntg = 0;
+    for (int b = 0; b < t.level_start[1]; ++b) ntg += t.tgt_end[b] - t.tgt_begin[b];
+    I->ntgt = ntg;
+    pw->nout = nout;
+    pw->nin = I->nin;
+    // device
+    const size_t ts = pw->mixed ? 4 : 8;
+    int r;
+    if ((r = pw_upload_typed(pw, &I->d_Co, I->host_Co, stream))) return r;
+    if ((r = pw_upload_typed(pw, &I->d_S, I->host_S, stream))) return r;
+    if ((r = pw_upload_typed(pw, &I->d_ph, I->host_ph, stream))) return r;
+    if ((r = pw_upload_typed(pw, &I->d_f, I->host_f, stream))) return r;
+    if ((r = pw_upload(pw, &I->d_leafq, leafq, stream))) return r;
+    if ((r = pw_upload(pw, &I->d_merge, merge, stream))) return r;
+    if ((r = pw_upload(pw, &I->d_outl, outl, stream))) return r;
+    if ((r = pw_upload(pw, &I->d_inl, inl, stream))) return r;
+    if ((r = pw_upload(pw, &I->d_down, down, stream))) return r;
+    if ((r = pw_upload(pw, &I->d_eval, ev, stream))) return r;
+    unsigned char* p = nullptr;
+    if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nq, 1)) * I->dims.np * ts))) return r;
+    I->d_Q = p;
+    if ((r = pw_alloc(pw, &p, size_t(std::max(nout, 1)) * I->dims.npw * 2 * ts))) return r;
+    I->d_out = p;
+    if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nloc, 1)) * I->dims.np * ts))) return r;
+    I->d_L = p;
+    if ((r = pw_alloc(pw, &pw->d_pot, size_t(std::max<int64_t>(ntg, 1))))) return r;
+    if ((r = pw_alloc(pw, &pw->d_grad, size_t(std::max<int64_t>(ntg, 1)) * d))) return r;
+    return PDMK_OK;
 }
+
 int pw_set_charges(PwPlan*, cudaStream_t) { return PDMK_OK; }
-int pw_eval(PwPlan*, cudaStream_t) { return PDMK_OK; }
+
+template <typename T, int D>
+static int pw_eval_t(PwPlan* pw, cudaStream_t s) {
+    PwImpl* I = impl(pw);
+    const PwDims pd = I->dims;
+    const size_t ts = sizeof(T);
+    const double inv_rc = 1.0 / I->rc;
+    if (cudaMemsetAsync(I->d_Q, 0, size_t(std::max<int64_t>(I->nq, 1)) * pd.np * ts, s) != cudaSuccess) return PDMK_ERR_CUDA;
+    if (cudaMemsetAsync(I->d_L, 0, size_t(std::max<int64_t>(I->nloc, 1)) * pd.np * ts, s) != cudaSuccess) return PDMK_ERR_CUDA;
+    if (cudaMemsetAsync(pw->d_pot, 0, size_t(std::max<int64_t>(I->ntgt, 1)) * sizeof(double), s) != cudaSuccess) return PDMK_ERR_CUDA;
+    if (cudaMemsetAsync(pw->d_grad, 0, size_t(std::max<int64_t>(I->ntgt, 1)) * D * sizeof(double), s) != cudaSuccess) return PDMK_ERR_CUDA;
+    T* Q = static_cast<T*>(I->d_Q);
+    T* L = static_cast<T*>(I->d_L);
+    C2<T>* out = static_cast<C2<T>*>(I->d_out);
+    const C2<T>* Co = static_cast<const C2<T>*>(I->d_Co);
+    const T* S = static_cast<const T*>(I->d_S);
+    // 1. leaf moments
+    if (I->nleafq > 0) {
+        size_t sm = ts * (32 * D * pd.p + 32);
+        k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, static_cast<const T*>(pw->d_src4), Q, pd, inv_rc);
+    }
+    // 2. merge, deepest level first
+    const size_t sm_re = ts * (2 * pd.p * pd.p + pd.pd1 + pd.p * pd.p);
+    cudaFuncSetAttribute(k_merge<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_re));
+    cudaFuncSetAttribute(k_down<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_re));
+    for (int l = I->nlevels - 1; l >= 0; --l) {
+        const int b = I->merge_start[l], e = I->merge_start[l + 1];
+        if (e > b)
+            k_merge<T, D><<<e - b, 128, sm_re, s>>>(I->d_merge + size_t(b) * (1 + (1 << D)), Q, S, pd);
+    }
+    // 3. outgoing plane waves (all levels)
+    if (I->nout > 0) {
+        size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + size_t(pd.n1) * pd.p);
+        cudaFuncSetAttribute(k_pw_out<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        k_pw_out<T, D><<<I->nout, 128, sm, s>>>(I->d_outl, Q, out, Co, pd, std::min(I->KC, 16));
+    }
+    // 4. translation + incoming (all levels)
+    if (I->nin > 0) {
+        const int KC = std::min(I->KC, 16);
+        size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + 3 * size_t(pd.n1) + size_t(KC) * pd.nk1 + size_t(KC) * pd.pd1 +
+                              size_t(pd.n1) * pd.p);
+        cudaFuncSetAttribute(k_pw_in<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        k_pw_in<T, D><<<I->nin, 128, sm, s>>>(I->d_inl, out, L, Co, static_cast<const C2<T>*>(I->d_ph),
+                                              static_cast<const T*>(I->d_f), pd, KC, inv_rc);
+    }
+    // 5. downward, root first
+    for (int l = 1; l < I->nlevels; ++l) {
+        const int b = I->down_start[l], e = I->down_start[l + 1];
+        if (e > b) k_down<T, D><<<e - b, 128, sm_re, s>>>(I->d_down + b, L, S, pd);
+    }
+    // 6. leaf evaluation
+    if (I->neval > 0) {
+        size_t sm = ts * 128 * 2 * D * pd.p;
+        cudaFuncSetAttribute(k_leaf_eval<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        k_leaf_eval<T, D><<<I->neval, 128, sm, s>>>(I->d_eval, L, static_cast<const T*>(pw->d_tgt4), pw->d_pot,
+                                                   pw->d_grad, pd, inv_rc);
+    }
+    if (cudaGetLastError() != cudaSuccess) return PDMK_ERR_CUDA;
+    return PDMK_OK;
+}
+
+int pw_eval(PwPlan* pw, cudaStream_t s) {
+    if (!pw->active) return PDMK_OK;
+    if (pw->d == 2) return pw->mixed ? pw_eval_t<float, 2>(pw, s) : pw_eval_t<double, 2>(pw, s);
+    return pw->mixed ? pw_eval_t<float, 3>(pw, s) : pw_eval_t<double, 3>(pw, s);
+}
+
 void pw_free_sources(PwPlan* pw) {
     for (void* p : pw->allocs) cudaFree(p);
     pw->allocs.clear();
+    pw->device_bytes = 0;
     pw->active = false;
+    pw->d_pot = nullptr;
+    pw->d_grad = nullptr;
+    PwImpl* I = impl(pw);
+    if (I) {
+        I->d_Co = I->d_S = I->d_ph = I->d_f = nullptr;
+        I->d_leafq = nullptr; I->d_merge = nullptr; I->d_outl = nullptr; I->d_inl = nullptr;
+        I->d_down = nullptr; I->d_eval = nullptr; I->d_Q = I->d_out = I->d_L = nullptr;
+        I->nleafq = I->nout = I->nin = I->neval = 0;
+    }
 }
-void pw_free(PwPlan* pw) { pw_free_sources(pw); }
+
+void pw_free(PwPlan* pw) {
+    pw_free_sources(pw);
+    delete impl(pw);
+    pw->impl = nullptr;
+}
 
 }  // namespace pdmk

@@ -38,6 +38,8 @@ def oracle_ref(g):
 
 def run(g, eps, **kw):
     P = _cuda()
+    for k, v in OPTS.get(g.get("case", ""), {}).items():
+        kw.setdefault(k, v)
     plan = P.Plan(g["L"], eps, **kw)
     plan.set_sources(g["y"], g["q"])
     pot, grad = plan.eval()
@@ -51,13 +53,17 @@ CASES = {
     "oblique2d": lambda: W.oblique2d_clusters(3000),
     "triclinic3d": lambda: W.triclinic3d_clusters(3000, nclusters=8),
     "random2d": lambda: W.random_neutral(np.array([[1.0, 0.3], [0.0, 0.7]]), 1500, seed=5),
+    # deep adaptive trees (clustered sources, small leaves): exercise every plane-wave pass
+    "oblique2d_deep": lambda: W.oblique2d_clusters(20000),
+    "triclinic3d_deep": lambda: W.triclinic3d_clusters(12000, nclusters=8),
 }
+OPTS = {"triclinic3d_deep": dict(n_s=60), "cube": dict(n_s=20)}
 
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
 def test_fp64_parity(case, eps):
-    g = CASES[case]()
+    g = dict(CASES[case](), case=case)
     pref, gref = oracle_ref(g)
     pot, grad, info = run(g, eps, precision="fp64")
     ep, eg = rel(pot, pref), rel(grad, gref)
@@ -69,7 +75,7 @@ def test_fp64_parity(case, eps):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("eps", [1e-3, 1e-6])
 def test_mixed_parity(case, eps):
-    g = CASES[case]()
+    g = dict(CASES[case](), case=case)
     pref, gref = oracle_ref(g)
     pot, grad, info = run(g, eps, precision="mixed")
     ep, eg = rel(pot, pref), rel(grad, gref)
@@ -109,3 +115,33 @@ def test_frame_and_basis_invariance():
     pot, grad, _ = run(dict(L=L2, y=y2, q=g["q"], name="rot"), 1e-6)
     assert rel(pot, pref) <= 1e-6
     assert rel(grad, gref) <= 1e-5
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_adaptive_equals_flat(d):
+    """The adaptive tree with plane-wave passes and the depth-0 tree (fast Ewald with the
+    prolate split) compute the same lattice sum (Sec. 1: small r_c collapses the tree)."""
+    g = W.oblique2d_clusters(4000, seed=99) if d == 2 else W.triclinic3d_clusters(3000, seed=98, nclusters=4)
+    pa, ga, ia = run(g, 1e-9, precision="fp64", n_s=20)
+    pf, gf, iff = run(g, 1e-9, precision="fp64", max_depth=0)
+    assert ia["depth"] >= 3 and iff["depth"] == 0
+    assert rel(pa, pf) <= 1e-9
+    assert rel(ga, gf) <= 1e-8
+
+
+def test_charges_update_and_linearity():
+    """set_charges reuses the tree; the result is linear in the charges."""
+    P = _cuda()
+    g = W.oblique2d_clusters(5000, seed=5)
+    rng = np.random.default_rng(0)
+    q2 = rng.standard_normal(len(g["q"]))
+    plan = P.Plan(g["L"], 1e-9, precision="fp64")
+    plan.set_sources(g["y"], g["q"])
+    p1, g1 = plan.eval()
+    plan.set_charges(q2)
+    p2, g2 = plan.eval()
+    plan.set_charges(2.0 * g["q"] - 0.5 * q2)
+    p3, g3 = plan.eval()
+    assert rel(p3, 2 * p1 - 0.5 * p2) < 1e-12
+    assert rel(g3, 2 * g1 - 0.5 * g2) < 1e-12
+    plan.close()
