@@ -294,8 +294,8 @@ def main():
             "cpu_baseline": cpu_line, "e2e": e2e,
             "gpu_launches": None, "clocks": clocks,
         }
-        launches_per_step = 9 + (info["depth"] > 0) * 0
-        out["gpu_launches"] = launches_per_step * args.steps
+        out["gpu_launches"] = int(info["launches"]) * args.steps
+        out["config"]["launches_per_step"] = int(info["launches"])
         print(json.dumps(out))
     if pg:
         pg.barrier()

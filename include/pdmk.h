@@ -129,6 +129,7 @@ typedef struct {
     int64_t near_pairs_in; /* of those, pairs inside the residual kernel's support (counted
                               on the first evaluation after pdmk_set_sources when profile = 1) */
     int64_t device_bytes;
+    int launches;       /* kernels this library launched in the last pdmk_eval (cuFFT excluded) */
 } pdmk_info;
 int pdmk_get_info(pdmk_plan plan, pdmk_info* info);
 

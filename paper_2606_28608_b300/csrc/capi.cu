@@ -53,7 +53,13 @@ struct pdmk_plan_s {
     std::vector<double> cA, cB, cW, cWd;  // near-field Chebyshev coefficients (FP64 master copy)
     int B[3] = {1, 1, 1}, nbin[3] = {1, 1, 1}, P[3] = {1, 1, 1}, Ptot = 1;
     int64_t ncell = 1, nhalf = 1;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // the caller's stream
+    cudaStream_t ws = nullptr;      // the plan's own work stream (graph capture needs a non-default stream)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    double* g_pot = nullptr;
+    double* g_grad = nullptr;
+    int evals_since_setup = 0;
     bool ready = false;
     std::string msg;
     // plan-lifetime device buffers
@@ -108,6 +114,7 @@ struct pdmk_plan_s {
     std::vector<double> stage_ms;
     pdmk_info info{};
     int64_t device_bytes = 0;
+    int launches = 0;  // kernels launched by the last eval (this library's own)
 };
 
 static void plan_set_msg(pdmk_plan plan, const char* m) {
@@ -141,7 +148,7 @@ static int dalloc(pdmk_plan plan, std::vector<void*>& list, X** out, size_t coun
 template <class X>
 static int upload(pdmk_plan plan, void* dst, const std::vector<X>& v) {
     if (v.empty()) return PDMK_OK;
-    CK(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, plan->stream));
+    CK(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, plan->ws));
     return PDMK_OK;
 }
 
@@ -323,6 +330,13 @@ extern "C" int pdmk_plan_create(int d, const double* L, double eps, const pdmk_o
     plan->d = d;
     plan->eps = eps;
     plan->stream = static_cast<cudaStream_t>(plan->opts.stream);
+    if (cudaStreamCreateWithFlags(&plan->ws, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete plan;
+        return PDMK_ERR_CUDA;
+    }
     const bool mixed = plan->opts.precision == PDMK_MIXED;
     double fit_tol = mixed ? std::max(eps * 1e-3, 2e-9) : std::max(eps * 1e-4, 1e-15);
     plan->kt = make_kernel_tables(d, eps, fit_tol);
@@ -405,10 +419,10 @@ extern "C" int pdmk_plan_create(int d, const double* L, double eps, const pdmk_o
             return PDMK_ERR_CUDA;
         }
         plan->have_fft = true;
-        cufftSetStream(plan->fft_fwd, plan->stream);
-        cufftSetStream(plan->fft_inv, plan->stream);
+        cufftSetStream(plan->fft_fwd, plan->ws);
+        cufftSetStream(plan->fft_inv, plan->ws);
     }
-    if (cudaStreamSynchronize(plan->stream) != cudaSuccess) {
+    if (cudaStreamSynchronize(plan->ws) != cudaSuccess) {
         pdmk_plan_destroy(plan);
         return PDMK_ERR_CUDA;
     }
@@ -417,9 +431,16 @@ extern "C" int pdmk_plan_create(int d, const double* L, double eps, const pdmk_o
     return PDMK_OK;
 }
 
+static void drop_graph(pdmk_plan plan) {
+    if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
+    plan->gexec = nullptr;
+    plan->g_pot = plan->g_grad = nullptr;
+}
+
 extern "C" void pdmk_plan_destroy(pdmk_plan plan) {
     if (!plan) return;
-    if (plan->stream) cudaStreamSynchronize(plan->stream); else cudaDeviceSynchronize();
+    if (plan->ws) cudaStreamSynchronize(plan->ws);
+    drop_graph(plan);
     free_list(plan->src_allocs, &plan->device_bytes);
     free_list(plan->plan_allocs, &plan->device_bytes);
     pw_free(&plan->pw);
@@ -428,6 +449,9 @@ extern "C" void pdmk_plan_destroy(pdmk_plan plan) {
         cufftDestroy(plan->fft_inv);
     }
     for (auto e : plan->ev) cudaEventDestroy(e);
+    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    if (plan->ws) cudaStreamDestroy(plan->ws);
     delete plan;
 }
 
@@ -447,24 +471,24 @@ static int gather_charges(pdmk_plan plan) {
     a.q_tgt = plan->d_q_tgt;
     int64_t mx = std::max(plan->nimg, std::max(plan->nspread, plan->ntgt));
     int blocks = int(std::min<int64_t>((mx + 255) / 256, 148 * 16));
-    k_gather_charges<T><<<std::max(blocks, 1), 256, 0, plan->stream>>>(a);
+    k_gather_charges<T><<<std::max(blocks, 1), 256, 0, plan->ws>>>(a);
     CK(cudaGetLastError());
     return PDMK_OK;
 }
 
 static int set_charges_device(pdmk_plan plan, bool check_neutral) {
-    k_charge_sums<<<1, 1024, 0, plan->stream>>>(plan->d_q_user, plan->n, plan->d_qsums);
+    k_charge_sums<<<1, 1024, 0, plan->ws>>>(plan->d_q_user, plan->n, plan->d_qsums);
     CK(cudaGetLastError());
     if (check_neutral) {
         double h[3];
-        CK(cudaMemcpyAsync(h, plan->d_qsums, 3 * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
-        CK(cudaStreamSynchronize(plan->stream));
+        CK(cudaMemcpyAsync(h, plan->d_qsums, 3 * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
+        CK(cudaStreamSynchronize(plan->ws));
         if (h[2] > 0) return PDMK_ERR_NONFINITE;
         if (plan->opts.neutrality == 0 && std::fabs(h[0]) > 1e-12 * h[1]) return PDMK_ERR_NON_NEUTRAL;
     }
     int r = plan->opts.precision == PDMK_MIXED ? gather_charges<float>(plan) : gather_charges<double>(plan);
     if (r != PDMK_OK) return r;
-    return pw_set_charges(&plan->pw, plan->stream);
+    return pw_set_charges(&plan->pw, plan->ws);
 }
 
 extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, const double* q, int where) {
@@ -475,6 +499,7 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     std::vector<double> hy(size_t(n) * d), hq(static_cast<size_t>(n));
     if (n > 0) {
         if (where == PDMK_DEVICE) {
+            CK(cudaStreamSynchronize(plan->stream));
             CK(cudaMemcpy(hy.data(), y, hy.size() * sizeof(double), cudaMemcpyDeviceToHost));
             CK(cudaMemcpy(hq.data(), q, hq.size() * sizeof(double), cudaMemcpyDeviceToHost));
         } else {
@@ -516,7 +541,9 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     int64_t pairs = 0;
     build_direct_lists(tree, &dl, &pairs);
     // ---- release old buffers, allocate new ----
-    if (plan->stream) cudaStreamSynchronize(plan->stream); else cudaDeviceSynchronize();
+    cudaStreamSynchronize(plan->ws);
+    drop_graph(plan);
+    plan->evals_since_setup = 0;
     free_list(plan->src_allocs, &plan->device_bytes);
     pw_free_sources(&plan->pw);
     const bool mixed = plan->opts.precision == PDMK_MIXED;
@@ -710,11 +737,11 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     // plane-wave passes (proxy, translation and local-expansion layouts)
     plan->pw.d_src4 = plan->d_src4;
     plan->pw.d_tgt4 = plan->d_tgt4;
-    r = pw_set_sources(&plan->pw, tree, ss, leaf_of, tgt_leaf, g, plan->stream);
+    r = pw_set_sources(&plan->pw, tree, ss, leaf_of, tgt_leaf, g, plan->ws);
     if (r != PDMK_OK) return r;
     r = set_charges_device(plan, false);
     if (r != PDMK_OK) return r;
-    CK(cudaStreamSynchronize(plan->stream));
+    CK(cudaStreamSynchronize(plan->ws));
     // info
     pdmk_info& I = plan->info;
     std::memset(&I, 0, sizeof(I));
@@ -733,16 +760,23 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
 extern "C" int pdmk_set_charges(pdmk_plan plan, const double* q, int where) {
     if (!plan || !q) return PDMK_ERR_BAD_ARG;
     if (!plan->ready) return PDMK_ERR_NOT_READY;
+    // order after the caller's stream (device charges may still be in flight there)
+    CK(cudaEventRecord(plan->ev_fork, plan->stream));
+    CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
     CK(cudaMemcpyAsync(plan->d_q_user, q, size_t(plan->n) * sizeof(double),
-                       where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, plan->stream));
-    return set_charges_device(plan, where == PDMK_HOST || plan->opts.neutrality == 0);
+                       where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, plan->ws));
+    int r = set_charges_device(plan, where == PDMK_HOST || plan->opts.neutrality == 0);
+    if (r != PDMK_OK) return r;
+    CK(cudaEventRecord(plan->ev_join, plan->ws));
+    CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
+    return PDMK_OK;
 }
 
 static int stage_mark(pdmk_plan plan, const char* name) {
     if (!plan->opts.profile) return PDMK_OK;
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
-    CK(cudaEventRecord(e, plan->stream));
+    CK(cudaEventRecord(e, plan->ws));
     plan->ev.push_back(e);
     plan->stage_names.push_back(name);
     return PDMK_OK;
@@ -750,9 +784,10 @@ static int stage_mark(pdmk_plan plan, const char* name) {
 
 template <typename T, int D>
 static int run_eval(pdmk_plan plan, double* pot, double* grad) {
-    cudaStream_t s = plan->stream;
+    cudaStream_t s = plan->ws;
     const Geometry& g = plan->g;
     int r;
+    plan->launches = 0;
     for (auto e : plan->ev) cudaEventDestroy(e);
     plan->ev.clear();
     plan->stage_names.clear();
@@ -776,6 +811,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
                       sizeof(int) * kSpreadChunk * 3;
         CK(cudaFuncSetAttribute(k_spread<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         k_spread<T, D><<<plan->nsub, kSpreadThreads, smem, s>>>(sa);
+        ++plan->launches;
         CK(cudaGetLastError());
     }
     {
@@ -790,6 +826,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         fa.fw = plan->w / 2;
         int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 8));
         k_fold<T, D><<<std::max(blocks, 1), 256, 0, s>>>(fa);
+        ++plan->launches;
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "spread"))) return r;
@@ -802,6 +839,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     {
         int blocks = int(std::min<int64_t>((plan->nhalf + 255) / 256, 148 * 8));
         k_scale<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<T*>(plan->d_spec), plan->d_weight, plan->nhalf);
+        ++plan->launches;
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "scale"))) return r;
@@ -829,13 +867,18 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         size_t smem = sizeof(T) * 128 * 2 * D * plan->w;
         CK(cudaFuncSetAttribute(k_interp<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         k_interp<T, D><<<int((plan->ntgt + 127) / 128), 128, smem, s>>>(ia);
+        ++plan->launches;
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "interp"))) return r;
     // ---- near field: plane-wave passes, then the direct residual sum ----
-    r = pw_eval(&plan->pw, s);
-    if (r != PDMK_OK) return r;
-    if ((r = stage_mark(plan, "planewave"))) return r;
+    static const char* pw_names[5] = {"pw_upward", "pw_out", "pw_translate_in", "pw_downward", "pw_leaf_eval"};
+    for (int ph = 0; ph < 5; ++ph) {
+        r = pw_eval(&plan->pw, s, ph);
+        if (r != PDMK_OK) return r;
+        if ((r = stage_mark(plan, pw_names[ph]))) return r;
+    }
+    plan->launches += plan->pw.launches;
     if (plan->ntleaf > 0) {
         NearArgs<T> na;
         na.tleaf = plan->d_tleaf;
@@ -861,7 +904,15 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
             CK(cudaMemsetAsync(plan->d_count, 0, sizeof(unsigned long long), s));
             na.count_in = plan->d_count;
         }
-        k_nearfield<T, D><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        const int nc = std::max(na.nA, na.nB);
+        if (nc <= 8) k_nearfield<T, D, 8><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        else if (nc <= 12) k_nearfield<T, D, 12><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        else if (nc <= 16) k_nearfield<T, D, 16><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        else if (nc <= 20) k_nearfield<T, D, 20><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        else if (nc <= 24) k_nearfield<T, D, 24><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        else if (nc <= 32) k_nearfield<T, D, 32><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        else k_nearfield<T, D, 40><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        ++plan->launches;
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "nearfield"))) return r;
@@ -891,10 +942,17 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         aa.grad_out = grad;
         int blocks = int(std::min<int64_t>((plan->ntgt + 255) / 256, 148 * 8));
         k_assemble<<<std::max(blocks, 1), 256, 0, s>>>(aa);
+        ++plan->launches;
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "assemble"))) return r;
     return PDMK_OK;
+}
+
+static int launch_eval(pdmk_plan plan, double* dp, double* dg) {
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    if (plan->d == 2) return mixed ? run_eval<float, 2>(plan, dp, dg) : run_eval<double, 2>(plan, dp, dg);
+    return mixed ? run_eval<float, 3>(plan, dp, dg) : run_eval<double, 3>(plan, dp, dg);
 }
 
 extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
@@ -903,20 +961,49 @@ extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
     double* dp = where == PDMK_DEVICE ? pot : plan->d_pot_out;
     double* dg = grad ? (where == PDMK_DEVICE ? grad : plan->d_grad_out) : nullptr;
     int r;
-    const bool mixed = plan->opts.precision == PDMK_MIXED;
-    if (plan->d == 2) r = mixed ? run_eval<float, 2>(plan, dp, dg) : run_eval<double, 2>(plan, dp, dg);
-    else r = mixed ? run_eval<float, 3>(plan, dp, dg) : run_eval<double, 3>(plan, dp, dg);
-    if (r != PDMK_OK) return r;
-    if (where != PDMK_DEVICE) {
-        CK(cudaMemcpyAsync(pot, dp, size_t(plan->n) * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
-        if (grad)
-            CK(cudaMemcpyAsync(grad, dg, size_t(plan->n) * plan->d * sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
-        CK(cudaStreamSynchronize(plan->stream));
+    // the work runs on the plan's stream, ordered after the caller's stream
+    CK(cudaEventRecord(plan->ev_fork, plan->stream));
+    CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
+    // The launch sequence depends only on the plan and the output pointers, so from the second
+    // evaluation on it is replayed from a captured CUDA graph (profiling and the first,
+    // pair-counting evaluation run eagerly).
+    const bool eager = plan->opts.profile || plan->count_pending || plan->evals_since_setup == 0;
+    if (eager) {
+        r = launch_eval(plan, dp, dg);
+        if (r != PDMK_OK) return r;
+    } else {
+        if (!plan->gexec || plan->g_pot != dp || plan->g_grad != dg) {
+            drop_graph(plan);
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(plan->ws, cudaStreamCaptureModeThreadLocal));
+            r = launch_eval(plan, dp, dg);
+            cudaError_t ce = cudaStreamEndCapture(plan->ws, &graph);
+            if (r != PDMK_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return r;
+            }
+            CK(ce);
+            cudaError_t ie = cudaGraphInstantiate(&plan->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ie);
+            plan->g_pot = dp;
+            plan->g_grad = dg;
+        }
+        CK(cudaGraphLaunch(plan->gexec, plan->ws));
     }
+    ++plan->evals_since_setup;
+    if (where != PDMK_DEVICE) {
+        CK(cudaMemcpyAsync(pot, dp, size_t(plan->n) * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
+        if (grad)
+            CK(cudaMemcpyAsync(grad, dg, size_t(plan->n) * plan->d * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
+        CK(cudaStreamSynchronize(plan->ws));
+    }
+    CK(cudaEventRecord(plan->ev_join, plan->ws));
+    CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
     if (plan->count_pending) {
         unsigned long long cnt = 0;
-        CK(cudaMemcpyAsync(&cnt, plan->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, plan->stream));
-        CK(cudaStreamSynchronize(plan->stream));
+        CK(cudaMemcpyAsync(&cnt, plan->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, plan->ws));
+        CK(cudaStreamSynchronize(plan->ws));
         plan->info.near_pairs_in = int64_t(cnt);
         plan->count_pending = false;
     }
@@ -947,6 +1034,7 @@ extern "C" int pdmk_get_info(pdmk_plan plan, pdmk_info* info) {
     if (!plan || !info) return PDMK_ERR_BAD_ARG;
     *info = plan->info;
     info->device_bytes = plan->device_bytes + plan->pw.device_bytes;
+    info->launches = plan->launches;
     if (!plan->ready) {
         info->d = plan->d; info->eps = plan->eps; info->c = plan->c; info->rc = plan->g.rc;
         info->V = plan->g.V; info->kappa = plan->kappa; info->n_s = plan->n_s; info->window_w = plan->w;

@@ -176,19 +176,26 @@ k_interp(InterpArgs<T> a) {
     if (threadIdx.x < a.nW) cw[threadIdx.x] = a.coefW[threadIdx.x];
     if (threadIdx.x < a.nWd) cd[threadIdx.x] = a.coefWd[threadIdx.x];
     __syncthreads();
-    T* wv = reinterpret_cast<T*>(smem_raw);            // [128][D][w]
-    T* wd = wv + blockDim.x * D * a.w;                  // [128][D][w]
+    // window values and derivatives, interleaved by thread: element k of thread t at
+    // k * blockDim + t (lanes never share a bank)
+    T* wv = reinterpret_cast<T*>(smem_raw);
+    T* wd = wv + blockDim.x * D * a.w;
     const int w = a.w;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.nt) return;
     const int4 g = a.t_g0[t];
     const T* dq = a.t_dq + size_t(t) * 4;
-    T* myv = wv + threadIdx.x * D * w;
-    T* myd = wd + threadIdx.x * D * w;
+    const int bs = blockDim.x;
+    T* myv = wv + threadIdx.x;
+    T* myd = wd + threadIdx.x;
     for (int k = 0; k < D; ++k) {
         const T del = dq[k];
-        for (int j = 0; j < w; ++j)
-            pswf_window_d(del - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &myv[k * w + j], &myd[k * w + j]);
+        for (int j = 0; j < w; ++j) {
+            T v, dv;
+            pswf_window_d(del - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &v, &dv);
+            myv[(k * w + j) * bs] = v;
+            myd[(k * w + j) * bs] = dv;
+        }
     }
     // the window argument is del - j = M u - (g0 + j), so d/d(M u) phi(del - j) = phi'(del - j)
     T pot = 0, gx = 0, gy = 0, gz = 0;
@@ -204,13 +211,13 @@ k_interp(InterpArgs<T> a) {
             if (xx < 0) xx += a.M0;
             for (int ix = 0; ix < w; ++ix) {
                 const T v = __ldg(row + xx);
-                sx = fma(v, myv[ix], sx);
-                sdx = fma(v, myd[ix], sdx);
+                sx = fma(v, myv[(ix) * bs], sx);
+                sdx = fma(v, myd[(ix) * bs], sdx);
                 if (++xx == a.M0) xx = 0;
             }
-            pot = fma(sx, myv[w + iy], pot);
-            gx = fma(sdx, myv[w + iy], gx);
-            gy = fma(sx, myd[w + iy], gy);
+            pot = fma(sx, myv[(w + iy) * bs], pot);
+            gx = fma(sdx, myv[(w + iy) * bs], gx);
+            gy = fma(sx, myd[(w + iy) * bs], gy);
         }
     } else {
         for (int iz = 0; iz < w; ++iz) {
@@ -227,15 +234,15 @@ k_interp(InterpArgs<T> a) {
                 if (xx < 0) xx += a.M0;
                 for (int ix = 0; ix < w; ++ix) {
                     const T v = __ldg(row + xx);
-                    sx = fma(v, myv[ix], sx);
-                    sdx = fma(v, myd[ix], sdx);
+                    sx = fma(v, myv[(ix) * bs], sx);
+                    sdx = fma(v, myd[(ix) * bs], sdx);
                     if (++xx == a.M0) xx = 0;
                 }
-                const T fyz = myv[w + iy] * myv[2 * w + iz];
+                const T fyz = myv[(w + iy) * bs] * myv[(2 * w + iz) * bs];
                 pot = fma(sx, fyz, pot);
                 gx = fma(sdx, fyz, gx);
-                gy = fma(sx, myd[w + iy] * myv[2 * w + iz], gy);
-                gz = fma(sx, myv[w + iy] * myd[2 * w + iz], gz);
+                gy = fma(sx, myd[(w + iy) * bs] * myv[(2 * w + iz) * bs], gy);
+                gz = fma(sx, myv[(w + iy) * bs] * myd[(2 * w + iz) * bs], gz);
             }
         }
     }

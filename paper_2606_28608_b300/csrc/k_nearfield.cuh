@@ -1,10 +1,10 @@
 // k_nearfield.cuh -- leaf-level residual-kernel direct sum (Sec. 2.3 and Sec. 3.5; Eq. (2.7)
 // for 3D, the radial-transform residual for 2D).
 //
-// One CTA per target leaf B.  Targets sit in registers (one per thread, the 128 threads
-// split into 128/C groups when B holds C <= 64 targets); the sources of every leaf in B's
-// direct list are streamed through shared memory in tiles of 128, shifted into B's frame
-// once per tile.  Per target the sum is a plain sum inside a tile and a compensated (Kahan)
+// One CTA of 64 threads per target leaf B.  Targets sit in registers (one per thread; the
+// threads split into two groups that share the sources when B holds at most 32 targets); the
+// sources of every leaf in B's direct list are streamed through shared memory in tiles of
+// 64, shifted into B's frame once per tile.  Per target the sum is a plain sum inside a tile and a compensated (Kahan)
 // sum across tiles and groups.  R_{L_B} vanishes for r >= h_{L_B}, so pairs beyond the
 // cut-off cost one compare.  The self pair (r = 0) is skipped; its W_L(0) is removed later.
 //
@@ -15,11 +15,35 @@
 
 namespace pdmk {
 
-constexpr int kNearThreads = 128;
-constexpr int kNearTile = 128;
+constexpr int kNearThreads = 64;
+constexpr int kNearTile = 64;
 constexpr int kNearMaxList = 256;
 
-template <typename T, int D>
+// Clenshaw with a compile-time number of terms (coefficients zero-padded) and coefficients
+// in registers: fully unrolled.
+template <typename T, int NC>
+__device__ __forceinline__ T clenshaw_reg(const T (&c)[NC], T x) {
+    T b1 = T(0), b2 = T(0);
+    const T x2 = x + x;
+#pragma unroll
+    for (int k = NC - 1; k >= 1; --k) {
+        const T b0 = fma(x2, b1, c[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    return fma(x, b1, c[0] - b2);
+}
+
+template <typename T>
+__device__ __forceinline__ T fast_rcp(T x) { return T(1) / x; }
+template <>
+__device__ __forceinline__ float fast_rcp<float>(float x) { return __frcp_rn(x); }
+template <typename T>
+__device__ __forceinline__ T fast_rsqrt(T x) { return T(1) / sqrt(x); }
+template <>
+__device__ __forceinline__ float fast_rsqrt<float>(float x) { return rsqrtf(x); }
+
+template <typename T, int D, int NC>
 __global__ void __launch_bounds__(kNearThreads)
 k_nearfield(NearArgs<T> a) {
     __shared__ T sx[kNearTile], sy[kNearTile], sz[kNearTile], sq[kNearTile];
@@ -30,20 +54,25 @@ k_nearfield(NearArgs<T> a) {
     constexpr int kLo = (sizeof(T) == 4) ? 1 : 0;
     __shared__ T e_shlo[kLo ? 3 : 1][kLo ? kNearMaxList : 1];
     __shared__ T slx[kLo ? kNearTile : 1], sly[kLo ? kNearTile : 1], slz[kLo ? kNearTile : 1];
-    __shared__ T cA[kMaxCheb], cB[kMaxCheb];
     __shared__ double red[4][kNearThreads];
 
     const TLeaf L = a.tleaf[blockIdx.x];
     const int tid = threadIdx.x;
-    if (tid < a.nA) cA[tid] = a.coefA[tid];
-    if (tid < a.nB) cB[tid] = a.coefB[tid];
+    T cA[NC], cB[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        cA[k] = k < a.nA ? a.coefA[k] : T(0);
+        cB[k] = k < a.nB ? a.coefB[k] : T(0);
+    }
 
     const double hinv_d = a.inv_rc * double(1LL << L.level);
     const T hinv = T(hinv_d);
     const T h2inv = T(hinv_d * hinv_d);
     const double* cB_centre = a.box_center + size_t(L.box) * D;
     const int nt = L.tgt_count;
-    const int C = nt <= 32 ? 32 : (nt <= 64 ? 64 : 128);
+    // targets per group: the smallest power of two >= nt (at least 8); the groups split the
+    // source tiles, so small leaves still keep every lane busy
+    const int C = nt <= 8 ? 8 : (nt <= 16 ? 16 : (nt <= 32 ? 32 : 64));
     const int G = kNearThreads / C;
     const int lt = tid % C;
     const int grp = tid / C;
@@ -144,11 +173,11 @@ k_nearfield(NearArgs<T> a) {
                             if (a.count_in) ++nin;
                             const T q = sq[j];
                             const T xc = fma(T(2), s, T(-1));
-                            const T fa = clenshaw(cA, a.nA, xc);
-                            const T fb = clenshaw(cB, a.nB, xc);
+                            const T fa = clenshaw_reg<T, NC>(cA, xc);
+                            const T fb = clenshaw_reg<T, NC>(cB, xc);
                             if (D == 3) {
                                 // R = (1 - t A)/(4 pi r); grad R = -(1 - t A + t B) dr / (4 pi r^3)
-                                const T rinv = T(1) / sqrt(r2);
+                                const T rinv = fast_rsqrt(r2);
                                 const T t = r2 * rinv * hinv;
                                 const T num = fma(-t, fa, T(1));
                                 pp = fma(q * num, rinv, pp);
@@ -160,7 +189,7 @@ k_nearfield(NearArgs<T> a) {
                                 // R = -log(s)/(4 pi) - A(s); grad R = -sqrt(1-s) S(s) dr/(2 pi r^2)
                                 const T lg = log(s);
                                 pp = fma(q, fma(-inv4pi, lg, -fa), pp);
-                                const T gf = -q * sqrt(T(1) - s) * fb / r2;
+                                const T gf = -q * sqrt(T(1) - s) * fb * fast_rcp(r2);
                                 gx = fma(gf, dx, gx);
                                 gy = fma(gf, dy, gy);
                             }

@@ -19,6 +19,7 @@ struct PwPlan {
     bool mixed = false;
     bool active = false;  // the tree has levels below the root grid
     int nout = 0, nin = 0;
+    int launches = 0;  // kernels launched by the last pw_eval
     int64_t device_bytes = 0;
     double* d_pot = nullptr;   // per sorted target
     double* d_grad = nullptr;  // d per sorted target
@@ -34,7 +35,9 @@ bool pw_supported(const PwPlan* pw);
 int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& s, const std::vector<int>& leaf_of,
                    const std::vector<int>& tgt_leaf, const Geometry& g, cudaStream_t stream);
 int pw_set_charges(PwPlan* pw, cudaStream_t stream);
-int pw_eval(PwPlan* pw, cudaStream_t stream);
+// phase 0: leaf moments + upward merges; 1: outgoing plane waves; 2: translation +
+// incoming; 3: downward pass; 4: evaluation at leaf targets
+int pw_eval(PwPlan* pw, cudaStream_t stream, int phase);
 void pw_free_sources(PwPlan* pw);
 void pw_free(PwPlan* pw);
 

@@ -109,9 +109,10 @@ __global__ void __launch_bounds__(128) k_leaf_moments(const int4* __restrict__ l
 }
 
 // ------------------------------------------------------------------ merge / downward
-// out-box ob accumulates prod_i S_{b_i} applied to in-box ib.  mode 0 (merge): contract the
-// child index m against the parent index M: Q_P[M] += sum_m Q_c[m] prod S_b[M_i][m_i].
-// mode 1 (down): a_c[m] += sum_M a_P[M] prod S_b[M_i][m_i].
+// Re-expansion of one box's Chebyshev array into another's, one axis at a time (slices of
+// the first axis through shared memory).  mode 0 (merge): contract the child index m against
+// the parent index M: Q_P[M] += sum_m Q_c[m] prod S_b[M_i][m_i].  mode 1 (down):
+// a_c[m] += sum_M a_P[M] prod S_b[M_i][m_i].
 template <typename T, int D>
 __device__ void reexpand(const T* __restrict__ src, T* __restrict__ dst, int bits, int mode, const T* Sm,
                          T* s1, T* s2, const PwDims& pd) {
@@ -187,9 +188,9 @@ __global__ void __launch_bounds__(128) k_merge(const int* __restrict__ list, T* 
     }
 }
 
-// down: one CTA per child; list entry int4 = (child local slot, parent local slot, bits, 0)
+// down: one CTA per parent; list entry = [parent local slot, child local slots (2^d, -1)]
 template <typename T, int D>
-__global__ void __launch_bounds__(128) k_down(const int4* __restrict__ list, T* __restrict__ Lc, const T* __restrict__ Sg,
+__global__ void __launch_bounds__(128) k_down(const int* __restrict__ list, T* __restrict__ Lc, const T* __restrict__ Sg,
                                               PwDims pd) {
     extern __shared__ __align__(16) unsigned char sm[];
     T* Sm = reinterpret_cast<T*>(sm);
@@ -197,8 +198,228 @@ __global__ void __launch_bounds__(128) k_down(const int4* __restrict__ list, T* 
     T* s2 = s1 + pd.pd1;
     for (int i = threadIdx.x; i < 2 * pd.p * pd.p; i += blockDim.x) Sm[i] = Sg[i];
     __syncthreads();
-    const int4 e = list[blockIdx.x];
-    reexpand<T, D>(Lc + size_t(e.y) * pd.np, Lc + size_t(e.x) * pd.np, e.z, 1, Sm, s1, s2, pd);
+    const int* e = list + size_t(blockIdx.x) * (1 + (1 << D));
+    for (int c = 0; c < (1 << D); ++c) {
+        const int cs = e[1 + c];
+        if (cs < 0) continue;
+        reexpand<T, D>(Lc + size_t(e[0]) * pd.np, Lc + size_t(cs) * pd.np, c, 1, Sm, s1, s2, pd);
+    }
+}
+
+// 2D: the whole re-expansion of all children in two shared-memory phases per parent.
+// merge: Q_P[M0][M1] = sum_c sum_{m0<=M0} S_{b0}[M0][m0] sum_{m1<=M1} S_{b1}[M1][m1] Q_c[m0][m1]
+template <typename T>
+__device__ void merge2d_body(const int* __restrict__ e, T* __restrict__ Q, const T* Sm, T* qc, T* tm,
+                             const PwDims& pd) {
+    const int p = pd.p, pp = p * p;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * pp; i += blockDim.x) {
+        const int c = i / pp, r = i % pp, cs = e[1 + c];
+        qc[i] = cs >= 0 ? Q[size_t(cs) * pd.np + r] : T(0);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * pp; i += blockDim.x) {
+        const int c = i / pp, r = i % pp, m0 = r / p, M1 = r % p, b1 = (c >> 1) & 1;
+        const T* S = Sm + (b1 * p + M1) * p;
+        const T* q = qc + c * pp + m0 * p;
+        T acc = T(0);
+        for (int m1 = 0; m1 <= M1; ++m1) acc = fma(S[m1], q[m1], acc);
+        tm[i] = acc;
+    }
+    __syncthreads();
+    T* dst = Q + size_t(e[0]) * pd.np;
+    for (int r = threadIdx.x; r < pp; r += blockDim.x) {
+        const int M0 = r / p, M1 = r % p;
+        T acc = T(0);
+        for (int c = 0; c < 4; ++c) {
+            if (e[1 + c] < 0) continue;
+            const T* S = Sm + ((c & 1) * p + M0) * p;
+            const T* t = tm + c * pp + M1;
+            for (int m0 = 0; m0 <= M0; ++m0) acc = fma(S[m0], t[m0 * p], acc);
+        }
+        dst[r] = acc;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_merge2d(const int* __restrict__ list, T* __restrict__ Q,
+                                                 const T* __restrict__ Sg, PwDims pd) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int pp = pd.p * pd.p;
+    T* Sm = reinterpret_cast<T*>(sm);  // [2][p][p]
+    for (int i = threadIdx.x; i < 2 * pp; i += blockDim.x) Sm[i] = Sg[i];
+    merge2d_body<T>(list + size_t(blockIdx.x) * 5, Q, Sm, Sm + 2 * pp, Sm + 6 * pp, pd);
+}
+
+// down: a_c[m0][m1] += sum_{M0>=m0} S_{b0}[M0][m0] sum_{M1>=m1} S_{b1}[M1][m1] a_P[M0][M1]
+template <typename T>
+__device__ void down2d_body(const int* __restrict__ e, T* __restrict__ Lc, const T* Sm, T* ap, T* tm,
+                            const PwDims& pd) {
+    const int p = pd.p, pp = p * p;
+    const T* src = Lc + size_t(e[0]) * pd.np;
+    __syncthreads();
+    for (int i = threadIdx.x; i < pp; i += blockDim.x) ap[i] = src[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * pp; i += blockDim.x) {
+        const int b1 = i / pp, r = i % pp, M0 = r / p, m1 = r % p;
+        T acc = T(0);
+        for (int M1 = m1; M1 < p; ++M1) acc = fma(Sm[(b1 * p + M1) * p + m1], ap[M0 * p + M1], acc);
+        tm[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * pp; i += blockDim.x) {
+        const int c = i / pp, r = i % pp, cs = e[1 + c];
+        if (cs < 0) continue;
+        const int m0 = r / p, m1 = r % p, b0 = c & 1, b1 = (c >> 1) & 1;
+        T acc = T(0);
+        for (int M0 = m0; M0 < p; ++M0) acc = fma(Sm[(b0 * p + M0) * p + m0], tm[b1 * pp + M0 * p + m1], acc);
+        Lc[size_t(cs) * pd.np + r] += acc;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_down2d(const int* __restrict__ list, T* __restrict__ Lc,
+                                                const T* __restrict__ Sg, PwDims pd) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int pp = pd.p * pd.p;
+    T* Sm = reinterpret_cast<T*>(sm);  // [2][p][p]
+    for (int i = threadIdx.x; i < 2 * pp; i += blockDim.x) Sm[i] = Sg[i];
+    down2d_body<T>(list + size_t(blockIdx.x) * 5, Lc, Sm, Sm + 2 * pp, Sm + 3 * pp, pd);
+}
+
+// 2D re-expansions with a compile-time order P: register tiles of 4 outputs per thread and
+// fully unrolled contractions (the triangular zeros of S are multiplied through: regular
+// loops beat the saved flops at this size).
+//   merge: R_b0[m0][M1] = sum_{b1,m1} S_b1[M1][m1] Q_(b0,b1)[m0][m1];
+//          Q_P[M0][M1]  = sum_{b0,m0} S_b0[M0][m0] R_b0[m0][M1]
+//   down:  U_b1[M0][m1] = sum_{M1} S_b1[M1][m1] a_P[M0][M1];
+//          a_(b0,b1)[m0][m1] += sum_{M0} S_b0[M0][m0] U_b1[M0][m1]
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_merge2d_p(const int* __restrict__ list, T* __restrict__ Q,
+                                                   const T* __restrict__ Sg, int np) {
+    constexpr int PP = P * P, G = (P + 3) / 4;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Sm = reinterpret_cast<T*>(smraw);  // S[b][M][m]  [2 PP]
+    T* St = Sm + 2 * PP;                  // S[b][m][M]  [2 PP] (transposed)
+    T* qc = St + 2 * PP;                  // [4 PP]
+    T* R = qc + 4 * PP;                   // [2 PP]
+    const int* e = list + size_t(blockIdx.x) * 5;
+    for (int i = threadIdx.x; i < 2 * PP; i += blockDim.x) {
+        const T v = Sg[i];
+        Sm[i] = v;
+        const int b = i / PP, M = (i / P) % P, m = i % P;
+        St[(b * P + m) * P + M] = v;
+    }
+    for (int i = threadIdx.x; i < 4 * PP; i += blockDim.x) {
+        const int c = i / PP, cs = e[1 + c];
+        qc[i] = cs >= 0 ? Q[size_t(cs) * np + (i % PP)] : T(0);
+    }
+    __syncthreads();
+    // phase A: lanes along M1 (St column reads are contiguous, q values are broadcasts)
+    for (int it = threadIdx.x; it < 2 * G * P; it += blockDim.x) {
+        const int b0 = it / (G * P), rem = it % (G * P), g = rem / P, M1 = rem % P;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int b1 = 0; b1 < 2; ++b1) {
+            const T* q = qc + ((b1 << 1) | b0) * PP;
+#pragma unroll
+            for (int m1 = 0; m1 < P; ++m1) {
+                const T s = St[(b1 * P + m1) * P + M1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int m0 = g * 4 + j;
+                    if (m0 < P) acc[j] = fma(s, q[m0 * P + m1], acc[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m0 = g * 4 + j;
+            if (m0 < P) R[b0 * PP + m0 * P + M1] = acc[j];
+        }
+    }
+    __syncthreads();
+    // phase B: lanes along M1 (R rows contiguous, S values broadcasts)
+    T* dst = Q + size_t(e[0]) * np;
+    for (int it = threadIdx.x; it < G * P; it += blockDim.x) {
+        const int g = it / P, M1 = it % P;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int b0 = 0; b0 < 2; ++b0) {
+#pragma unroll
+            for (int m0 = 0; m0 < P; ++m0) {
+                const T r = R[b0 * PP + m0 * P + M1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int M0 = g * 4 + j;
+                    if (M0 < P) acc[j] = fma(Sm[(b0 * P + M0) * P + m0], r, acc[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int M0 = g * 4 + j;
+            if (M0 < P) dst[M0 * P + M1] = acc[j];
+        }
+    }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_down2d_p(const int* __restrict__ list, T* __restrict__ Lc,
+                                                  const T* __restrict__ Sg, int np) {
+    constexpr int PP = P * P, G = (P + 3) / 4;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Sm = reinterpret_cast<T*>(smraw);  // [2 PP] | ap [PP] | U [2 PP]
+    T* ap = Sm + 2 * PP;
+    T* U = ap + PP;
+    const int* e = list + size_t(blockIdx.x) * 5;
+    const T* src = Lc + size_t(e[0]) * np;
+    for (int i = threadIdx.x; i < 2 * PP; i += blockDim.x) Sm[i] = Sg[i];
+    for (int i = threadIdx.x; i < PP; i += blockDim.x) ap[i] = src[i];
+    __syncthreads();
+    // phase A: lanes along m1 (S rows contiguous, a_P values broadcasts)
+    for (int it = threadIdx.x; it < 2 * G * P; it += blockDim.x) {
+        const int b1 = it / (G * P), rem = it % (G * P), g = rem / P, m1 = rem % P;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int M1 = 0; M1 < P; ++M1) {
+            const T s = Sm[(b1 * P + M1) * P + m1];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int M0 = g * 4 + j;
+                if (M0 < P) acc[j] = fma(s, ap[M0 * P + M1], acc[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int M0 = g * 4 + j;
+            if (M0 < P) U[b1 * PP + M0 * P + m1] = acc[j];
+        }
+    }
+    __syncthreads();
+    // phase B: lanes along m1 (U rows contiguous, S values broadcasts)
+    for (int it = threadIdx.x; it < 4 * G * P; it += blockDim.x) {
+        const int c = it / (G * P), rem = it % (G * P), g = rem / P, m1 = rem % P;
+        const int cs = e[1 + c];
+        if (cs < 0) continue;
+        const int b0 = c & 1, b1 = c >> 1;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int M0 = 0; M0 < P; ++M0) {
+            const T u = U[b1 * PP + M0 * P + m1];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int m0 = g * 4 + j;
+                if (m0 < P) acc[j] = fma(Sm[(b0 * P + M0) * P + m0], u, acc[j]);
+            }
+        }
+        T* dst = Lc + size_t(cs) * np;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m0 = g * 4 + j;
+            if (m0 < P) dst[m0 * P + m1] += acc[j];
+        }
+    }
 }
 
 // ------------------------------------------------------------------ outgoing plane waves
@@ -218,6 +439,20 @@ __global__ void __launch_bounds__(128) k_pw_out(const int2* __restrict__ list, c
     C2<T>* o = out + size_t(e.y) * pd.npw;
     for (int kc0 = 0; kc0 <= K; kc0 += KC) {
         const int nk = min(KC, K + 1 - kc0);
+        if (D == 2) {
+            // 2D: one item per (k0, r); p-term dot products
+            for (int it = threadIdx.x; it < nk * pd1; it += blockDim.x) {
+                const int j = it / pd1, r = it % pd1;
+                C2<T> acc{T(0), T(0)};
+                const C2<T>* crow = Co + (kc0 + j + K) * p;
+                for (int m0 = 0; m0 < p; ++m0) {
+                    const T v = q[m0 * pd1 + r];
+                    acc.x = fma(crow[m0].x, v, acc.x);
+                    acc.y = fma(crow[m0].y, v, acc.y);
+                }
+                A[j * pd1 + r] = acc;
+            }
+        } else
         for (int r = threadIdx.x; r < pd1; r += blockDim.x) {
             C2<T> acc[16];
             for (int j = 0; j < 16; ++j) acc[j] = C2<T>{T(0), T(0)};
@@ -363,12 +598,15 @@ __global__ void __launch_bounds__(128) k_pw_in(const int* __restrict__ list, con
 // ------------------------------------------------------------------ leaf evaluation
 // entry int4 = (local slot, tgt_begin, tgt_count, level)
 template <typename T, int D>
-__global__ void __launch_bounds__(128) k_leaf_eval(const int4* __restrict__ list, const T* __restrict__ Lc,
+__global__ void __launch_bounds__(32) k_leaf_eval(const int4* __restrict__ list, const T* __restrict__ Lc,
                                                    const T* __restrict__ tgt4, double* __restrict__ pot,
                                                    double* __restrict__ grad, PwDims pd, double inv_rc) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int p = pd.p;
-    T* tb = reinterpret_cast<T*>(sm) + threadIdx.x * (2 * D * p);  // T_m and T'_m per dim
+    // per-thread T_m and T'_m per dim, interleaved by thread (element k of thread t at
+    // k * blockDim + t) so that lanes never share a bank
+    T* tb = reinterpret_cast<T*>(sm) + threadIdx.x;
+    const int bs = blockDim.x;
     const int4 e = list[blockIdx.x];
     const T* a = Lc + size_t(e.x) * pd.np;
     const double sc = 2.0 * inv_rc * double(1LL << e.w);  // dt/dx = 2/h
@@ -378,17 +616,17 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int4* __restrict__ list
         const T* x = tgt4 + size_t(e.y + ti) * 4;
         for (int i = 0; i < D; ++i) {
             const T t = T(double(x[i]) * sc);
-            T* bt = tb + i * 2 * p;
-            T* bd = bt + p;
+            T* bt = tb + i * 2 * p * bs;
+            T* bd = bt + p * bs;
             // T_m by recurrence; T'_m = m U_{m-1}
             T tm1 = T(1), tm = t, um1 = T(1), um = T(2) * t;
             bt[0] = T(1);
             bd[0] = T(0);
-            if (p > 1) { bt[1] = t; bd[1] = T(1); }
+            if (p > 1) { bt[bs] = t; bd[bs] = T(1); }
             for (int m = 2; m < p; ++m) {
                 const T tn = fma(T(2) * t, tm, -tm1);
-                bt[m] = tn;
-                bd[m] = T(m) * um;  // U_{m-1}
+                bt[m * bs] = tn;
+                bd[m * bs] = T(m) * um;  // U_{m-1}
                 const T un = fma(T(2) * t, um, -um1);
                 tm1 = tm; tm = tn;
                 um1 = um; um = un;
@@ -396,24 +634,24 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int4* __restrict__ list
         }
         T phi = 0, g0 = 0, g1 = 0, g2 = 0;
         const T* b0 = tb;
-        const T* d0 = tb + p;
-        const T* b1 = tb + 2 * p;
-        const T* d1 = tb + 3 * p;
+        const T* d0 = tb + p * bs;
+        const T* b1 = tb + 2 * p * bs;
+        const T* d1 = tb + 3 * p * bs;
         if (D == 2) {
             for (int m0 = 0; m0 < p; ++m0) {
                 T s = 0, sd = 0;
                 for (int m1 = 0; m1 < p; ++m1) {
                     const T v = a[m0 * p + m1];
-                    s = fma(v, b1[m1], s);
-                    sd = fma(v, d1[m1], sd);
+                    s = fma(v, b1[m1 * bs], s);
+                    sd = fma(v, d1[m1 * bs], sd);
                 }
-                phi = fma(b0[m0], s, phi);
-                g0 = fma(d0[m0], s, g0);
-                g1 = fma(b0[m0], sd, g1);
+                phi = fma(b0[m0 * bs], s, phi);
+                g0 = fma(d0[m0 * bs], s, g0);
+                g1 = fma(b0[m0 * bs], sd, g1);
             }
         } else {
-            const T* b2 = tb + 4 * p;
-            const T* d2 = tb + 5 * p;
+            const T* b2 = tb + 4 * p * bs;
+            const T* d2 = tb + 5 * p * bs;
             for (int m0 = 0; m0 < p; ++m0) {
                 T s = 0, s1d = 0, s2d = 0;
                 for (int m1 = 0; m1 < p; ++m1) {
@@ -421,17 +659,17 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int4* __restrict__ list
                     const T* row = a + (m0 * p + m1) * p;
                     for (int m2 = 0; m2 < p; ++m2) {
                         const T v = row[m2];
-                        u = fma(v, b2[m2], u);
-                        ud = fma(v, d2[m2], ud);
+                        u = fma(v, b2[m2 * bs], u);
+                        ud = fma(v, d2[m2 * bs], ud);
                     }
-                    s = fma(b1[m1], u, s);
-                    s1d = fma(d1[m1], u, s1d);
-                    s2d = fma(b1[m1], ud, s2d);
+                    s = fma(b1[m1 * bs], u, s);
+                    s1d = fma(d1[m1 * bs], u, s1d);
+                    s2d = fma(b1[m1 * bs], ud, s2d);
                 }
-                phi = fma(b0[m0], s, phi);
-                g0 = fma(d0[m0], s, g0);
-                g1 = fma(b0[m0], s1d, g1);
-                g2 = fma(b0[m0], s2d, g2);
+                phi = fma(b0[m0 * bs], s, phi);
+                g0 = fma(d0[m0 * bs], s, g0);
+                g1 = fma(b0[m0 * bs], s1d, g1);
+                g2 = fma(b0[m0 * bs], s2d, g2);
             }
         }
         const size_t o = size_t(e.y + ti);
@@ -463,8 +701,8 @@ struct PwImpl {
     int nout = 0;
     int* d_inl = nullptr;
     int nin = 0;
-    int4* d_down = nullptr;
-    std::vector<int> down_start;   // per child level
+    int* d_down = nullptr;
+    std::vector<int> down_start;   // per parent level: entry offsets
     int4* d_eval = nullptr;
     int neval = 0;
     int nlevels = 1;
@@ -532,7 +770,7 @@ void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables&
     // plane-wave half width: xi_max = (pi/3) K / (h/2) >= 2c/h  <=>  K >= 3c/pi
     const int K = n_pw > 0 ? n_pw : int(std::ceil(3.0 * c / kPi - 1e-9));
     // Chebyshev order: the plane waves exp(-i (pi/3) k t), |k| <= K, have frequency <= c
-    int p = n_proxy > 0 ? n_proxy : int(std::ceil(c)) + 6;
+    int p = n_proxy > 0 ? n_proxy : ((int(std::ceil(c)) + 6 + 3) / 4) * 4;
     p = std::max(4, std::min(p, 40));
     pw->p = p;
     pw->K = K;
@@ -676,20 +914,21 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         }
     }
     I->merge_start[t.nlevels] = int(merge.size()) / (1 + nc);
-    // downward lists per child level
-    std::vector<int4> down;
+    // downward lists per parent level: [parent local slot, child local slots]
+    std::vector<int> down;
     I->down_start.assign(t.nlevels + 1, 0);
     for (int l = 0; l < t.nlevels; ++l) {
-        I->down_start[l] = int(down.size());
-        if (l == 0) continue;
+        I->down_start[l] = int(down.size()) / (1 + nc);
         for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
-            if (lslot[b] < 0) continue;
-            const int P = t.parent[b];
-            if (lslot[P] < 0) return PDMK_ERR_INTERNAL;
-            down.push_back(make_int4(lslot[b], lslot[P], b - t.child0[P], 0));
+            if (t.is_leaf(b) || lslot[b] < 0) continue;
+            bool any = false;
+            for (int c = 0; c < nc; ++c) any |= lslot[t.child0[b] + c] >= 0;
+            if (!any) continue;
+            down.push_back(lslot[b]);
+            for (int c = 0; c < nc; ++c) down.push_back(lslot[t.child0[b] + c]);
         }
     }
-    I->down_start[t.nlevels] = int(down.size());
+    I->down_start[t.nlevels] = int(down.size()) / (1 + nc);
     // leaf evaluation: target leaves below the root level
     std::vector<int4> ev;
     for (int b = 0; b < nb; ++b)
@@ -731,69 +970,121 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
 int pw_set_charges(PwPlan*, cudaStream_t) { return PDMK_OK; }
 
 template <typename T, int D>
-static int pw_eval_t(PwPlan* pw, cudaStream_t s) {
+static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     PwImpl* I = impl(pw);
     const PwDims pd = I->dims;
     const size_t ts = sizeof(T);
     const double inv_rc = 1.0 / I->rc;
+    if (phase == 0) {
     if (cudaMemsetAsync(I->d_Q, 0, size_t(std::max<int64_t>(I->nq, 1)) * pd.np * ts, s) != cudaSuccess) return PDMK_ERR_CUDA;
     if (cudaMemsetAsync(I->d_L, 0, size_t(std::max<int64_t>(I->nloc, 1)) * pd.np * ts, s) != cudaSuccess) return PDMK_ERR_CUDA;
     if (cudaMemsetAsync(pw->d_pot, 0, size_t(std::max<int64_t>(I->ntgt, 1)) * sizeof(double), s) != cudaSuccess) return PDMK_ERR_CUDA;
     if (cudaMemsetAsync(pw->d_grad, 0, size_t(std::max<int64_t>(I->ntgt, 1)) * D * sizeof(double), s) != cudaSuccess) return PDMK_ERR_CUDA;
+    }
     T* Q = static_cast<T*>(I->d_Q);
     T* L = static_cast<T*>(I->d_L);
     C2<T>* out = static_cast<C2<T>*>(I->d_out);
     const C2<T>* Co = static_cast<const C2<T>*>(I->d_Co);
     const T* S = static_cast<const T*>(I->d_S);
+    const size_t sm_re = ts * (2 * pd.p * pd.p + pd.pd1 + pd.p * pd.p);
+    const size_t sm_m2 = ts * 10 * pd.p * pd.p;
+    const size_t sm_d2 = ts * 5 * pd.p * pd.p;
     // 1. leaf moments
-    if (I->nleafq > 0) {
+    if (phase == 0 && I->nleafq > 0) {
         size_t sm = ts * (32 * D * pd.p + 32);
         k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, static_cast<const T*>(pw->d_src4), Q, pd, inv_rc);
+        ++pw->launches;
     }
+    // compile-time-order 2D re-expansion kernels (dynamic shared memory of nel elements)
+    int cur_blocks = 0;
+    auto launch_p = [&](auto kern, int nel, const int* lst, T* arr) {
+        const size_t smb = size_t(nel) * ts;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+        kern<<<cur_blocks, 256, smb, s>>>(lst, arr, S, pd.np);
+    };
     // 2. merge, deepest level first
-    const size_t sm_re = ts * (2 * pd.p * pd.p + pd.pd1 + pd.p * pd.p);
-    cudaFuncSetAttribute(k_merge<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_re));
-    cudaFuncSetAttribute(k_down<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_re));
-    for (int l = I->nlevels - 1; l >= 0; --l) {
+    if (D == 2) {
+        cudaFuncSetAttribute(k_merge2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_m2));
+        cudaFuncSetAttribute(k_down2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_d2));
+    } else {
+        cudaFuncSetAttribute(k_merge<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_re));
+        cudaFuncSetAttribute(k_down<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_re));
+    }
+    for (int l = I->nlevels - 1; phase == 0 && l >= 0; --l) {
         const int b = I->merge_start[l], e = I->merge_start[l + 1];
-        if (e > b)
-            k_merge<T, D><<<e - b, 128, sm_re, s>>>(I->d_merge + size_t(b) * (1 + (1 << D)), Q, S, pd);
+        if (e > b) {
+            const int* lst = I->d_merge + size_t(b) * (1 + (1 << D));
+            cur_blocks = e - b;
+            if (D == 2) {
+                switch (pd.p) {
+                    case 16: launch_p(k_merge2d_p<T, 16>, 10 * 16 * 16, lst, Q); break;
+                    case 20: launch_p(k_merge2d_p<T, 20>, 10 * 20 * 20, lst, Q); break;
+                    case 24: launch_p(k_merge2d_p<T, 24>, 10 * 24 * 24, lst, Q); break;
+                    case 28: launch_p(k_merge2d_p<T, 28>, 10 * 28 * 28, lst, Q); break;
+                    case 32: launch_p(k_merge2d_p<T, 32>, 10 * 32 * 32, lst, Q); break;
+                    default: k_merge2d<T><<<e - b, 256, sm_m2, s>>>(lst, Q, S, pd);
+                }
+            } else {
+                k_merge<T, D><<<e - b, 128, sm_re, s>>>(lst, Q, S, pd);
+            }
+            ++pw->launches;
+        }
     }
     // 3. outgoing plane waves (all levels)
-    if (I->nout > 0) {
+    if (phase == 1 && I->nout > 0) {
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + size_t(pd.n1) * pd.p);
         cudaFuncSetAttribute(k_pw_out<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_pw_out<T, D><<<I->nout, 128, sm, s>>>(I->d_outl, Q, out, Co, pd, std::min(I->KC, 16));
+        ++pw->launches;
     }
     // 4. translation + incoming (all levels)
-    if (I->nin > 0) {
+    if (phase == 2 && I->nin > 0) {
         const int KC = std::min(I->KC, 16);
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + 3 * size_t(pd.n1) + size_t(KC) * pd.nk1 + size_t(KC) * pd.pd1 +
                               size_t(pd.n1) * pd.p);
         cudaFuncSetAttribute(k_pw_in<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_pw_in<T, D><<<I->nin, 128, sm, s>>>(I->d_inl, out, L, Co, static_cast<const C2<T>*>(I->d_ph),
                                               static_cast<const T*>(I->d_f), pd, KC, inv_rc);
+        ++pw->launches;
     }
-    // 5. downward, root first
-    for (int l = 1; l < I->nlevels; ++l) {
+    // 5. downward, root first (by parent level)
+    for (int l = 0; phase == 3 && l + 1 < I->nlevels; ++l) {
         const int b = I->down_start[l], e = I->down_start[l + 1];
-        if (e > b) k_down<T, D><<<e - b, 128, sm_re, s>>>(I->d_down + b, L, S, pd);
+        if (e > b) {
+            const int* lst = I->d_down + size_t(b) * (1 + (1 << D));
+            cur_blocks = e - b;
+            if (D == 2) {
+                switch (pd.p) {
+                    case 16: launch_p(k_down2d_p<T, 16>, 5 * 16 * 16, lst, L); break;
+                    case 20: launch_p(k_down2d_p<T, 20>, 5 * 20 * 20, lst, L); break;
+                    case 24: launch_p(k_down2d_p<T, 24>, 5 * 24 * 24, lst, L); break;
+                    case 28: launch_p(k_down2d_p<T, 28>, 5 * 28 * 28, lst, L); break;
+                    case 32: launch_p(k_down2d_p<T, 32>, 5 * 32 * 32, lst, L); break;
+                    default: k_down2d<T><<<e - b, 256, sm_d2, s>>>(lst, L, S, pd);
+                }
+            } else {
+                k_down<T, D><<<e - b, 128, sm_re, s>>>(lst, L, S, pd);
+            }
+            ++pw->launches;
+        }
     }
     // 6. leaf evaluation
-    if (I->neval > 0) {
-        size_t sm = ts * 128 * 2 * D * pd.p;
+    if (phase == 4 && I->neval > 0) {
+        size_t sm = ts * 32 * 2 * D * pd.p;
         cudaFuncSetAttribute(k_leaf_eval<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-        k_leaf_eval<T, D><<<I->neval, 128, sm, s>>>(I->d_eval, L, static_cast<const T*>(pw->d_tgt4), pw->d_pot,
+        k_leaf_eval<T, D><<<I->neval, 32, sm, s>>>(I->d_eval, L, static_cast<const T*>(pw->d_tgt4), pw->d_pot,
                                                    pw->d_grad, pd, inv_rc);
+        ++pw->launches;
     }
     if (cudaGetLastError() != cudaSuccess) return PDMK_ERR_CUDA;
     return PDMK_OK;
 }
 
-int pw_eval(PwPlan* pw, cudaStream_t s) {
+int pw_eval(PwPlan* pw, cudaStream_t s, int phase) {
+    if (phase == 0) pw->launches = 0;
     if (!pw->active) return PDMK_OK;
-    if (pw->d == 2) return pw->mixed ? pw_eval_t<float, 2>(pw, s) : pw_eval_t<double, 2>(pw, s);
-    return pw->mixed ? pw_eval_t<float, 3>(pw, s) : pw_eval_t<double, 3>(pw, s);
+    if (pw->d == 2) return pw->mixed ? pw_eval_t<float, 2>(pw, s, phase) : pw_eval_t<double, 2>(pw, s, phase);
+    return pw->mixed ? pw_eval_t<float, 3>(pw, s, phase) : pw_eval_t<double, 3>(pw, s, phase);
 }
 
 void pw_free_sources(PwPlan* pw) {
