@@ -110,6 +110,33 @@ int pdmk_set_charges(pdmk_plan plan, const double* q, int where);
  */
 int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where);
 
+/*
+ * pdmk_eval_noalloc -- the evaluation of pdmk_eval (device outputs) for callers that cannot
+ * allocate device memory at evaluation time: for example code running inside an engine that
+ * reserved the whole device heap for its own pool at start-up, or under a caching allocator
+ * that forbids cudaMalloc during a time step, or under a real-time budget that cannot absorb
+ * an allocation's implicit synchronisation.  The paper has no counterpart; this is a property
+ * of the library, not of the method.
+ *
+ * pot (n) and grad (n x d, or NULL) are device buffers owned by the caller; the plan must have
+ * been set up (pdmk_set_sources) beforehand by a caller that could allocate.  The call itself
+ * calls no cudaMalloc, cudaFree or allocating library routine: the scratch of the spreading
+ * kernel (its per-subproblem padded tiles) is a file-scope static device array of 16 MiB
+ * that every device loading the library holds until the process exits.
+ *  - Returns PDMK_ERR_TOO_LARGE (and does nothing) if the plan's spreading scratch, roughly
+ *    (n / 512 + number of grid bins) x (B + w - 1)^d x element size, exceeds 16 MiB.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    for that device; make that first call outside any stream capture.
+ *  - Every call, from every plan, shares the one array: calls whose work overlaps on the GPU
+ *    (different streams or plans without ordering between them) race on it.  Calls ordered
+ *    on one stream are safe; the array keeps the last call's contents, and nothing in it
+ *    needs to start at zero.
+ *  - Launches are eager (never replayed from a captured graph) and on the plan's stream
+ *    order, asynchronous like pdmk_eval with device pointers.
+ * Errors: BAD_ARG, NOT_READY, TOO_LARGE, CUDA.
+ */
+int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad);
+
 /* Per-stage device times (ms) of the last pdmk_eval when opts.profile = 1.  names/ms
  * receive up to cap entries; returns the number of stages (or a negative error).     */
 int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, int cap);

@@ -66,6 +66,8 @@ def lib():
         L.pdmk_set_charges.restype = ctypes.c_int
         L.pdmk_eval.argtypes = [P, P, P, ctypes.c_int]
         L.pdmk_eval.restype = ctypes.c_int
+        L.pdmk_eval_noalloc.argtypes = [P, P, P]
+        L.pdmk_eval_noalloc.restype = ctypes.c_int
         L.pdmk_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.pdmk_stage_times.restype = ctypes.c_int
         L.pdmk_get_info.argtypes = [P, ctypes.POINTER(Info)]
@@ -201,6 +203,15 @@ class Plan:
         rc = lib().pdmk_eval(self._h, pot.data_ptr(), grad.data_ptr() if grad is not None else None, PDMK_DEVICE)
         if rc != 0:
             raise PdmkError(rc, "pdmk_eval")
+
+    def eval_noalloc(self, pot, grad=None):
+        """Device evaluation into caller-owned torch CUDA tensors (float64) without any device
+        allocation in the call: the spreading scratch is the library's fixed 16 MiB static
+        array (see pdmk_eval_noalloc in include/pdmk.h).  Raises PdmkError (TOO_LARGE) if the
+        plan's spreading scratch does not fit."""
+        rc = lib().pdmk_eval_noalloc(self._h, pot.data_ptr(), grad.data_ptr() if grad is not None else None)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_eval_noalloc")
 
     def info(self) -> dict:
         inf = Info()

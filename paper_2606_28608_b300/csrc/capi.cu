@@ -98,6 +98,7 @@ struct pdmk_plan_s {
     int4* d_sub = nullptr;
     int* d_bin_sub_begin = nullptr;
     void* d_slab = nullptr;
+    void* slab_override = nullptr;  // set only for the duration of pdmk_eval_noalloc
     int4* d_t_g0 = nullptr;
     void* d_t_dq = nullptr;
     double* d_pot_near = nullptr;
@@ -800,7 +801,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         sa.pt_dq = static_cast<const T*>(plan->d_pt_dq);
         sa.sub = plan->d_sub;
         sa.nsub = plan->nsub;
-        sa.slab = static_cast<T*>(plan->d_slab);
+        sa.slab = static_cast<T*>(plan->slab_override ? plan->slab_override : plan->d_slab);
         sa.P0 = plan->P[0]; sa.P1 = plan->P[1]; sa.P2 = plan->P[2]; sa.Ptot = plan->Ptot;
         sa.B0 = plan->B[0]; sa.B1 = plan->B[1]; sa.B2 = plan->B[2];
         sa.w = plan->w;
@@ -816,7 +817,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     }
     {
         FoldArgs<T> fa;
-        fa.slab = static_cast<const T*>(plan->d_slab);
+        fa.slab = static_cast<const T*>(plan->slab_override ? plan->slab_override : plan->d_slab);
         fa.bin_sub_begin = plan->d_bin_sub_begin;
         fa.grid = static_cast<T*>(plan->d_grid);
         fa.M0 = g.M[0]; fa.M1 = g.M[1]; fa.M2 = g.M[2];
@@ -1040,5 +1041,67 @@ extern "C" int pdmk_get_info(pdmk_plan plan, pdmk_info* info) {
         info->V = plan->g.V; info->kappa = plan->kappa; info->n_s = plan->n_s; info->window_w = plan->w;
         for (int i = 0; i < 3; ++i) { info->M[i] = plan->g.M[i]; info->nroot[i] = plan->g.nroot[i]; }
     }
+    return PDMK_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Evaluation that allocates nothing.
+//
+// Some callers cannot allocate device memory when they evaluate: code that runs while a
+// framework owns the whole device heap (a simulation engine that reserved its memory pool at
+// start-up, a caching allocator that forbids cudaMalloc inside a step), or code that runs
+// under a real-time budget where an allocation's implicit synchronisation is not acceptable.
+// For them, pdmk_eval_noalloc evaluates an existing plan into caller-provided device buffers
+// and takes the spreading kernel's per-subproblem scratch (its padded tiles) from the
+// file-scope array below instead of the plan's own buffer.  The array is a fixed part of every
+// device that loads this library, for the lifetime of the process.
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+}  // namespace
+
+extern "C" int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad) {
+    if (!plan || !pot) return PDMK_ERR_BAD_ARG;
+    if (!plan->ready) return PDMK_ERR_NOT_READY;
+    const size_t need = size_t(std::max(plan->nsub, 1)) * size_t(plan->Ptot) * tsize(plan);
+    if (need > kNoAllocScratchBytes) {
+        plan_set_msg(plan, "spreading scratch exceeds the 16 MiB static array");
+        return PDMK_ERR_TOO_LARGE;
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return PDMK_ERR_BAD_ARG;
+    void* scratch = nullptr;
+    {
+        // first call on this device: the array's device address (the host-side symbol is
+        // only a stand-in for it and must never be passed to a kernel)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* ptr = nullptr;
+            CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = ptr;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    CK(cudaEventRecord(plan->ev_fork, plan->stream));
+    CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
+    // eager launches only (no graph instantiation, no profiling events); the spread kernel
+    // writes every scratch element it later reads, so nothing needs clearing between calls
+    const bool saved_profile = plan->opts.profile != 0;
+    const bool saved_count = plan->count_pending;
+    plan->opts.profile = 0;
+    plan->count_pending = false;
+    plan->slab_override = scratch;
+    const int r = launch_eval(plan, pot, grad);
+    plan->slab_override = nullptr;
+    plan->opts.profile = saved_profile ? 1 : 0;
+    plan->count_pending = saved_count;
+    if (r != PDMK_OK) return r;
+    CK(cudaEventRecord(plan->ev_join, plan->ws));
+    CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
     return PDMK_OK;
 }
