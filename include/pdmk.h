@@ -157,6 +157,12 @@ typedef struct {
                               on the first evaluation after pdmk_set_sources when profile = 1) */
     int64_t device_bytes;
     int launches;       /* kernels this library launched in the last pdmk_eval (cuFFT excluded) */
+    /* work counts of the plane-wave passes (for roofline accounting) */
+    int64_t pw_moment_sources; /* sources summed into leaf moments            */
+    int pw_merge_parents;      /* boxes whose moments are merged from children */
+    int pw_down_parents;       /* boxes whose local expansion is passed down   */
+    int64_t pw_eval_targets;   /* targets evaluated from a leaf local expansion */
+    int spread_subproblems;    /* spreading subproblems (tile, point range)     */
 } pdmk_info;
 int pdmk_get_info(pdmk_plan plan, pdmk_info* info);
 

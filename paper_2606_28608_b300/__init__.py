@@ -42,7 +42,10 @@ class Info(ctypes.Structure):
                 ("nboxes", ctypes.c_int), ("nleaves", ctypes.c_int), ("depth", ctypes.c_int),
                 ("ntarget_leaves", ctypes.c_int), ("n_pw_boxes_out", ctypes.c_int),
                 ("n_pw_boxes_in", ctypes.c_int), ("near_pairs", ctypes.c_int64), ("near_pairs_in", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("launches", ctypes.c_int)]
+                ("device_bytes", ctypes.c_int64), ("launches", ctypes.c_int),
+                ("pw_moment_sources", ctypes.c_int64), ("pw_merge_parents", ctypes.c_int),
+                ("pw_down_parents", ctypes.c_int), ("pw_eval_targets", ctypes.c_int64),
+                ("spread_subproblems", ctypes.c_int)]
 
 
 _lib = None

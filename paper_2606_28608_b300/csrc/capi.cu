@@ -52,6 +52,7 @@ struct pdmk_plan_s {
     WindowTables wt;
     std::vector<double> cA, cB, cW, cWd;  // near-field Chebyshev coefficients (FP64 master copy)
     int B[3] = {1, 1, 1}, nbin[3] = {1, 1, 1}, P[3] = {1, 1, 1}, Ptot = 1;
+    int whole_ctas = 0;  // > 0: 2D whole-grid spreading with this many CTAs (small grids)
     int64_t ncell = 1, nhalf = 1;
     cudaStream_t stream = nullptr;  // the caller's stream
     cudaStream_t ws = nullptr;      // the plan's own work stream (graph capture needs a non-default stream)
@@ -161,6 +162,13 @@ static void free_list(std::vector<void*>& l, int64_t* bytes) {
 
 static size_t tsize(const pdmk_plan plan) { return plan->opts.precision == PDMK_MIXED ? 4 : 8; }
 
+// spreading scratch: per-subproblem padded tiles, or one whole-grid slab per CTA
+static size_t slab_bytes(const pdmk_plan plan) {
+    const size_t tiles = size_t(std::max(plan->nsub, 1)) * size_t(plan->Ptot);
+    const size_t whole = size_t(plan->whole_ctas) * size_t(plan->ncell);
+    return std::max(tiles, whole) * tsize(plan);
+}
+
 extern "C" void pdmk_default_opts(pdmk_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
@@ -223,6 +231,9 @@ static void size_bins(pdmk_plan plan) {
     }
     plan->nhalf = int64_t(plan->g.M[0] / 2 + 1) * plan->g.M[1] * (d == 3 ? plan->g.M[2] : 1);
     plan->nbins_tot = plan->nbin[0] * plan->nbin[1] * plan->nbin[2];
+    // 2D grids whose 8 per-warp copies fit in ~96 KB of shared memory use whole-grid spreading
+    const size_t ts = plan->opts.precision == PDMK_MIXED ? 4 : 8;
+    plan->whole_ctas = (d == 2 && size_t(plan->ncell) * ts * 8 <= size_t(96) * 1024) ? 2 * 148 : 0;
 }
 
 // FP64 far-field weights for the half spectrum (Eq. (3.14)-(3.15a) with the window
@@ -704,7 +715,7 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     DALLOC(L, plan->d_spread_orig, int, sp_orig.size());
     DALLOC(L, plan->d_sub, int4, subs.size());
     DALLOC(L, plan->d_bin_sub_begin, int, bin_sub_begin.size());
-    DALLOC(L, plan->d_slab, unsigned char, size_t(std::max(plan->nsub, 1)) * plan->Ptot * ts);
+    DALLOC(L, plan->d_slab, unsigned char, slab_bytes(plan));
     DALLOC(L, plan->d_t_g0, int4, t_g0.size());
     DALLOC(L, plan->d_t_dq, unsigned char, t_dq.size());
     DALLOC(L, plan->d_pot_near, double, plan->ntgt);
@@ -753,6 +764,11 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     I.n = n; I.n_images = plan->nimg; I.nboxes = st.nboxes; I.nleaves = st.nleaves; I.depth = st.depth;
     I.ntarget_leaves = plan->ntleaf; I.near_pairs = pairs;
     I.n_pw_boxes_out = plan->pw.nout; I.n_pw_boxes_in = plan->pw.nin;
+    I.pw_moment_sources = plan->pw.active ? plan->pw.moment_sources : 0;
+    I.pw_merge_parents = plan->pw.active ? plan->pw.merge_parents : 0;
+    I.pw_down_parents = plan->pw.active ? plan->pw.down_parents : 0;
+    I.pw_eval_targets = plan->pw.active ? plan->pw.eval_targets : 0;
+    I.spread_subproblems = plan->nsub;
     plan->count_pending = plan->opts.profile != 0;
     plan->ready = true;
     return PDMK_OK;
@@ -795,13 +811,30 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     if ((r = stage_mark(plan, "start"))) return r;
     // ---- far field: spread, fold, FFT, scale, inverse FFT, interpolate ----
     const T hwi2 = T(4.0 / (double(plan->w) * plan->w));
+    void* slab = plan->slab_override ? plan->slab_override : plan->d_slab;
+    if (D == 2 && plan->whole_ctas > 0) {
+        const int nwarp = 8;
+        const size_t smem = sizeof(T) * (size_t(nwarp) * plan->ncell + size_t(nwarp) * 2 * plan->w);
+        CK(cudaFuncSetAttribute(k_spread_whole<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_spread_whole<T><<<plan->whole_ctas, 32 * nwarp, smem, s>>>(
+            plan->d_t_g0, static_cast<const T*>(plan->d_t_dq), static_cast<const T*>(plan->d_tgt4), int(plan->ntgt),
+            static_cast<T*>(slab), g.M[0], g.M[1], plan->w, hwi2, static_cast<const T*>(plan->d_coefW),
+            int(plan->cW.size()));
+        ++plan->launches;
+        CK(cudaGetLastError());
+        int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 4));
+        k_fold_whole<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<const T*>(slab), plan->whole_ctas,
+                                                            static_cast<T*>(plan->d_grid), int(plan->ncell));
+        ++plan->launches;
+        CK(cudaGetLastError());
+    } else {
     if (plan->nsub > 0) {
         SpreadArgs<T> sa;
         sa.pt_g0 = plan->d_pt_g0;
         sa.pt_dq = static_cast<const T*>(plan->d_pt_dq);
         sa.sub = plan->d_sub;
         sa.nsub = plan->nsub;
-        sa.slab = static_cast<T*>(plan->slab_override ? plan->slab_override : plan->d_slab);
+        sa.slab = static_cast<T*>(slab);
         sa.P0 = plan->P[0]; sa.P1 = plan->P[1]; sa.P2 = plan->P[2]; sa.Ptot = plan->Ptot;
         sa.B0 = plan->B[0]; sa.B1 = plan->B[1]; sa.B2 = plan->B[2];
         sa.w = plan->w;
@@ -817,7 +850,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     }
     {
         FoldArgs<T> fa;
-        fa.slab = static_cast<const T*>(plan->slab_override ? plan->slab_override : plan->d_slab);
+        fa.slab = static_cast<const T*>(slab);
         fa.bin_sub_begin = plan->d_bin_sub_begin;
         fa.grid = static_cast<T*>(plan->d_grid);
         fa.M0 = g.M[0]; fa.M1 = g.M[1]; fa.M2 = g.M[2];
@@ -829,6 +862,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         k_fold<T, D><<<std::max(blocks, 1), 256, 0, s>>>(fa);
         ++plan->launches;
         CK(cudaGetLastError());
+    }
     }
     if ((r = stage_mark(plan, "spread"))) return r;
     if (sizeof(T) == 4) {
@@ -1067,7 +1101,7 @@ std::mutex g_noalloc_mu;
 extern "C" int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad) {
     if (!plan || !pot) return PDMK_ERR_BAD_ARG;
     if (!plan->ready) return PDMK_ERR_NOT_READY;
-    const size_t need = size_t(std::max(plan->nsub, 1)) * size_t(plan->Ptot) * tsize(plan);
+    const size_t need = slab_bytes(plan);
     if (need > kNoAllocScratchBytes) {
         plan_set_msg(plan, "spreading scratch exceeds the 16 MiB static array");
         return PDMK_ERR_TOO_LARGE;

@@ -117,6 +117,71 @@ k_spread(SpreadArgs<T> a) {
     for (int i = tid; i < a.Ptot; i += kSpreadThreads) out[i] = tile[i];
 }
 
+// Small 2D grids: every warp keeps a private copy of the whole periodic grid in shared memory
+// and spreads its own contiguous run of points into it (lanes over the w x w footprint, one
+// point at a time: no two lanes touch one cell, every cell is updated in point order).  The
+// CTA then sums its warps' copies in warp order and writes one slab; k_fold_whole adds the
+// slabs in CTA order.  Deterministic, atomics-free, and it needs no sorting by bin.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_spread_whole(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, const T* __restrict__ q4, int n,
+               T* __restrict__ slab, int M0, int M1, int w, T half_w_inv2, const T* __restrict__ coefW, int nW) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T cw[kMaxCheb];
+    const int ncell = M0 * M1;
+    const int nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T* grids = reinterpret_cast<T*>(smem_raw);        // [nwarp][ncell]
+    T* wins = grids + nwarp * ncell;                  // [nwarp][2][w]
+    if (threadIdx.x < nW) cw[threadIdx.x] = coefW[threadIdx.x];
+    for (int i = threadIdx.x; i < nwarp * ncell; i += blockDim.x) grids[i] = T(0);
+    __syncthreads();
+    T* g = grids + wp * ncell;
+    T* wv = wins + wp * 2 * w;
+    const int gw = blockIdx.x * nwarp + wp, nw = gridDim.x * nwarp;
+    const int per = (n + nw - 1) / nw;
+    const int i0 = min(n, gw * per), i1 = min(n, i0 + per);
+    const int ww = w * w;
+    for (int i = i0; i < i1; ++i) {
+        const int4 g0 = t_g0[i];
+        const T* dq = t_dq + size_t(i) * 4;
+        for (int l = lane; l < 2 * w; l += 32) {
+            const int k = l / w, j = l % w;
+            wv[l] = pswf_window(dq[k] - T(j), half_w_inv2, cw, nW);
+        }
+        __syncwarp();
+        const T q = q4[size_t(i) * 4 + 3];
+        int x0 = g0.x % M0;
+        if (x0 < 0) x0 += M0;
+        int y0 = g0.y % M1;
+        if (y0 < 0) y0 += M1;
+        for (int e = lane; e < ww; e += 32) {
+            const int iy = e / w, ix = e - iy * w;
+            int xx = x0 + ix;
+            if (xx >= M0) xx -= M0;
+            int yy = y0 + iy;
+            if (yy >= M1) yy -= M1;
+            g[yy * M0 + xx] += q * wv[w + iy] * wv[ix];
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    T* out = slab + size_t(blockIdx.x) * ncell;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        T s = T(0);
+        for (int k = 0; k < nwarp; ++k) s += grids[k * ncell + c];
+        out[c] = s;
+    }
+}
+
+template <typename T>
+__global__ void k_fold_whole(const T* __restrict__ slab, int nslab, T* __restrict__ grid, int ncell) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int k = 0; k < nslab; ++k) s += slab[size_t(k) * ncell + c];
+        grid[c] = s;
+    }
+}
+
 // fold: grid cell g gathers every subproblem tile that covers it (periodic wrap)
 template <typename T, int D>
 __global__ void k_fold(FoldArgs<T> a) {

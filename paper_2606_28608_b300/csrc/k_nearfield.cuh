@@ -70,18 +70,21 @@ k_nearfield(NearArgs<T> a) {
     const T h2inv = T(hinv_d * hinv_d);
     const double* cB_centre = a.box_center + size_t(L.box) * D;
     const int nt = L.tgt_count;
-    // targets per group: the smallest power of two >= nt (at least 8); the groups split the
-    // source tiles, so small leaves still keep every lane busy
-    const int C = nt <= 8 ? 8 : (nt <= 16 ? 16 : (nt <= 32 ? 32 : 64));
+    // targets per group: the smallest power of two >= nt (so the groups tile the block
+    // exactly); the G = 64 / C groups split the source tiles, so small leaves still keep
+    // most lanes busy
+    int C = 1;
+    while (C < nt && C < kNearThreads) C <<= 1;
     const int G = kNearThreads / C;
     const int lt = tid % C;
     const int grp = tid / C;
+    const bool ingrp = grp < G;
     const T inv4pi = T(0.07957747154594766788);  // 1/(4 pi)
     unsigned long long nin = 0;
 
     for (int t0 = 0; t0 < nt; t0 += C) {
         const int ti = t0 + lt;
-        const bool act = ti < nt;
+        const bool act = ingrp && ti < nt;
         T xt = 0, yt = 0, zt = 0;
         T xtl = 0, ytl = 0, ztl = 0;
         if (act) {

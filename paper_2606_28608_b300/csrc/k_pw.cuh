@@ -20,6 +20,8 @@ struct PwPlan {
     bool active = false;  // the tree has levels below the root grid
     int nout = 0, nin = 0;
     int launches = 0;  // kernels launched by the last pw_eval
+    int64_t moment_sources = 0, eval_targets = 0;
+    int merge_parents = 0, down_parents = 0;
     int64_t device_bytes = 0;
     double* d_pot = nullptr;   // per sorted target
     double* d_grad = nullptr;  // d per sorted target

@@ -431,8 +431,13 @@ __global__ void __launch_bounds__(128) k_pw_out(const int2* __restrict__ list, c
     C2<T>* Co = reinterpret_cast<C2<T>*>(sm);  // [n1][p], row kk = k + K
     C2<T>* A = Co + pd.n1 * pd.p;              // [KC][pd1]
     C2<T>* B = A + KC * pd.pd1;                // [n1][p]   (3D)
+    C2<T>* CoT = B + pd.n1 * pd.p;             // [p][n1]   transposed copy (lanes along k)
     const int p = pd.p, K = pd.K, n1 = pd.n1, pd1 = pd.pd1;
-    for (int i = threadIdx.x; i < n1 * p; i += blockDim.x) Co[i] = Cog[i];
+    for (int i = threadIdx.x; i < n1 * p; i += blockDim.x) {
+        const C2<T> v = Cog[i];
+        Co[i] = v;
+        CoT[(i % p) * n1 + i / p] = v;
+    }
     __syncthreads();
     const int2 e = list[blockIdx.x];
     const T* q = Q + size_t(e.x) * pd.np;
@@ -475,7 +480,7 @@ __global__ void __launch_bounds__(128) k_pw_out(const int2* __restrict__ list, c
             for (int it = threadIdx.x; it < nk * n1; it += blockDim.x) {
                 const int j = it / n1, kk1 = it % n1;
                 C2<T> acc{T(0), T(0)};
-                for (int m1 = 0; m1 < p; ++m1) acc = cfma(Co[kk1 * p + m1], A[j * pd1 + m1], acc);
+                for (int m1 = 0; m1 < p; ++m1) acc = cfma(CoT[m1 * n1 + kk1], A[j * pd1 + m1], acc);
                 o[(kc0 + j) * n1 + kk1] = acc;
             }
             __syncthreads();
@@ -902,6 +907,8 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         if (t.is_leaf(b) && has_src(b))
             leafq.push_back(make_int4(int(t.src_begin[b]), int(t.src_end[b] - t.src_begin[b]), qslot[b], t.level[b]));
     I->nleafq = int(leafq.size());
+    pw->moment_sources = 0;
+    for (const int4& l : leafq) pw->moment_sources += l.y;
     // merges per level (non-leaf boxes with sources), deepest first at eval time
     std::vector<int> merge;
     I->merge_start.assign(t.nlevels + 1, 0);
@@ -914,6 +921,7 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         }
     }
     I->merge_start[t.nlevels] = int(merge.size()) / (1 + nc);
+    pw->merge_parents = I->merge_start[t.nlevels];
     // downward lists per parent level: [parent local slot, child local slots]
     std::vector<int> down;
     I->down_start.assign(t.nlevels + 1, 0);
@@ -929,12 +937,15 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         }
     }
     I->down_start[t.nlevels] = int(down.size()) / (1 + nc);
+    pw->down_parents = I->down_start[t.nlevels];
     // leaf evaluation: target leaves below the root level
     std::vector<int4> ev;
     for (int b = 0; b < nb; ++b)
         if (t.is_leaf(b) && has_tgt(b) && t.level[b] >= 1)
             ev.push_back(make_int4(lslot[b], int(t.tgt_begin[b]), int(t.tgt_end[b] - t.tgt_begin[b]), t.level[b]));
     I->neval = int(ev.size());
+    pw->eval_targets = 0;
+    for (const int4& e4 : ev) pw->eval_targets += e4.z;
     I->nq = nq;
     I->nloc = nloc;
     int64_t ntg = 0;
@@ -1032,7 +1043,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     }
     // 3. outgoing plane waves (all levels)
     if (phase == 1 && I->nout > 0) {
-        size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + size_t(pd.n1) * pd.p);
+        size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + 2 * size_t(pd.n1) * pd.p);
         cudaFuncSetAttribute(k_pw_out<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_pw_out<T, D><<<I->nout, 128, sm, s>>>(I->d_outl, Q, out, Co, pd, std::min(I->KC, 16));
         ++pw->launches;
