@@ -1,0 +1,63 @@
+"""Differentiation through the periodic potential (paper_2606_28608_b300.autograd).
+
+Checks: dU/dq = Phi for U = q.Phi/2 (symmetry of the lattice-sum operator), dU/dy = q grad Phi
+against the FP64 oracle, and a general loss against central finite differences."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ewald as E
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_28608_b300.autograd import periodic_potential
+    return torch, periodic_potential
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_energy_gradients(d):
+    torch, pp = _torch()
+    g = W.oblique2d_clusters(1500, seed=17) if d == 2 else W.triclinic3d_clusters(1500, seed=18, nclusters=4)
+    y = torch.tensor(g["y"], device="cuda", requires_grad=True)
+    q = torch.tensor(g["q"], device="cuda", requires_grad=True)
+    pot, grad = pp(g["L"], y, q, eps=1e-9, precision="fp64")
+    U = 0.5 * (q * pot).sum()
+    U.backward()
+    pref, gref = E.ewald(g["L"], g["y"], g["q"])
+    dq = q.grad.cpu().numpy()
+    dy = y.grad.cpu().numpy()
+    assert np.linalg.norm(dq - pref) <= 1e-8 * np.linalg.norm(pref)
+    want = g["q"][:, None] * gref
+    assert np.linalg.norm(dy - want) <= 1e-7 * np.linalg.norm(want)
+
+
+def test_general_loss_finite_differences():
+    torch, pp = _torch()
+    g = W.random_neutral(np.array([[1.0, 0.3], [0.0, 0.8]]), 400, seed=4)
+    rng = np.random.default_rng(1)
+    wgt = torch.tensor(rng.standard_normal(400), device="cuda")
+    y = torch.tensor(g["y"], device="cuda", requires_grad=True)
+    q = torch.tensor(g["q"], device="cuda", requires_grad=True)
+    pot, _ = pp(g["L"], y, q, eps=1e-10, precision="fp64")
+    (wgt * pot).sum().backward()
+
+    def loss(yy, qq):
+        p, _ = pp(g["L"], torch.tensor(yy, device="cuda"), torch.tensor(qq, device="cuda"), eps=1e-10,
+                  precision="fp64")
+        return float((wgt * p).sum())
+
+    h = 1e-4
+    for k, a in ((3, 0), (177, 1)):
+        yp = g["y"].copy(); yp[k, a] += h
+        ym = g["y"].copy(); ym[k, a] -= h
+        fd = (loss(yp, g["q"]) - loss(ym, g["q"])) / (2 * h)
+        assert abs(fd - float(y.grad[k, a])) <= 1e-4 * max(1.0, abs(fd))
+    for k in (5, 250):
+        qp = g["q"].copy(); qp[k] += 1.0
+        fd = loss(g["y"], qp) - loss(g["y"], g["q"])  # linear in q: exact difference
+        assert abs(fd - float(q.grad[k])) <= 1e-8 * max(1.0, abs(fd))
