@@ -687,6 +687,250 @@ __global__ void __launch_bounds__(32) k_leaf_eval(const int4* __restrict__ list,
     }
 }
 
+// ------------------------------------------------------------------ 2D compile-time kernels
+// The orders the planner picks by eps, (P, K) = (16, 9), (24, 16), (32, 23), get kernels with
+// compile-time loop bounds: fully unrolled contractions, no run-time integer division, lanes
+// along the contiguous index of every shared-memory operand.
+
+// leaf moments: Q[m0][m1] = sum_s (q_s T_m0(x_s)) T_m1(y_s), a (P x ns)(ns x P) product per leaf
+template <typename T, int P>
+__global__ void __launch_bounds__(128) k_moments2d_p(const int4* __restrict__ leaves, const T* __restrict__ src4,
+                                                     T* __restrict__ Q, double inv_rc) {
+    constexpr int NB = 32, G = (P + 3) / 4, ITEMS = G * P;
+    constexpr int PER = (ITEMS + 127) / 128;
+    __shared__ T Ax[NB][P];  // q_s T_m(x_s)
+    __shared__ T By[NB][P];  // T_m(y_s)
+    const int4 lf = leaves[blockIdx.x];
+    const T scale = T(2.0 * inv_rc * double(1LL << lf.w));
+    T acc[PER][4];
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[u][j] = T(0);
+    for (int s0 = 0; s0 < lf.y; s0 += NB) {
+        const int ns = min(NB, lf.y - s0);
+        __syncthreads();
+        if (threadIdx.x < 2 * NB) {
+            const int s = threadIdx.x >> 1, dim = threadIdx.x & 1;
+            T* row = dim ? By[s] : Ax[s];
+            if (s < ns) {
+                const T* y = src4 + size_t(lf.x + s0 + s) * 4;
+                const T t = y[dim] * scale;
+                const T w0 = dim ? T(1) : y[3];
+                T tm1 = T(1), tm = t;
+                row[0] = w0;
+                if (P > 1) row[1] = w0 * t;
+#pragma unroll
+                for (int m = 2; m < P; ++m) {
+                    const T tn = fma(T(2) * t, tm, -tm1);
+                    row[m] = w0 * tn;
+                    tm1 = tm;
+                    tm = tn;
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < P; ++m) row[m] = T(0);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int it = threadIdx.x + u * 128;
+            if (it < ITEMS) {
+                const int g = it / P, m1 = it % P;
+                for (int s = 0; s < ns; ++s) {
+                    const T b = By[s][m1];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (g * 4 + j < P) acc[u][j] = fma(Ax[s][g * 4 + j], b, acc[u][j]);
+                }
+            }
+        }
+    }
+    T* Qb = Q + size_t(lf.z) * (P * P);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int it = threadIdx.x + u * 128;
+        if (it < ITEMS) {
+            const int g = it / P, m1 = it % P;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (g * 4 + j < P) Qb[(g * 4 + j) * P + m1] = acc[u][j];
+        }
+    }
+}
+
+// outgoing plane waves, persistent over boxes: A[k0][m1] = sum_m0 Co[k0][m0] Q[m0][m1],
+// out[k0][k1] = sum_m1 Co[k1][m1] A[k0][m1]
+template <typename T, int P, int K>
+__global__ void __launch_bounds__(128) k_pw_out2d_p(const int2* __restrict__ list, int nbox, const T* __restrict__ Q,
+                                                    C2<T>* __restrict__ out, const C2<T>* __restrict__ Cog) {
+    constexpr int N1 = 2 * K + 1, NPW = (K + 1) * N1;
+    __shared__ C2<T> Co[N1][P];    // Co[k + K][m]
+    __shared__ C2<T> CoT[P][N1];   // transposed
+    __shared__ T q[P * P];
+    __shared__ C2<T> A[K + 1][P];
+    for (int i = threadIdx.x; i < N1 * P; i += blockDim.x) {
+        const C2<T> v = Cog[i];
+        Co[i / P][i % P] = v;
+        CoT[i % P][i / P] = v;
+    }
+    for (int b = blockIdx.x; b < nbox; b += gridDim.x) {
+        const int2 e = list[b];
+        __syncthreads();
+        for (int i = threadIdx.x; i < P * P; i += blockDim.x) q[i] = Q[size_t(e.x) * (P * P) + i];
+        __syncthreads();
+        for (int it = threadIdx.x; it < (K + 1) * P; it += blockDim.x) {
+            const int k0 = it / P, m1 = it % P;
+            C2<T> acc{T(0), T(0)};
+#pragma unroll
+            for (int m0 = 0; m0 < P; ++m0) {
+                const C2<T> c = Co[k0 + K][m0];
+                const T v = q[m0 * P + m1];
+                acc.x = fma(c.x, v, acc.x);
+                acc.y = fma(c.y, v, acc.y);
+            }
+            A[k0][m1] = acc;
+        }
+        __syncthreads();
+        C2<T>* o = out + size_t(e.y) * NPW;
+        for (int it = threadIdx.x; it < NPW; it += blockDim.x) {
+            const int k0 = it / N1, kk1 = it % N1;
+            C2<T> acc{T(0), T(0)};
+#pragma unroll
+            for (int m1 = 0; m1 < P; ++m1) acc = cfma(CoT[m1][kk1], A[k0][m1], acc);
+            o[it] = acc;
+        }
+    }
+}
+
+// translation + incoming, persistent over boxes (list entry: local slot, level, 9 out slots)
+template <typename T, int P, int K>
+__global__ void __launch_bounds__(128) k_pw_in2d_p(const int* __restrict__ list, int nbox, const C2<T>* __restrict__ out,
+                                                   T* __restrict__ Lc, const C2<T>* __restrict__ Cog,
+                                                   const C2<T>* __restrict__ phg, const T* __restrict__ fk) {
+    constexpr int N1 = 2 * K + 1, NPW = (K + 1) * N1;
+    __shared__ C2<T> Co[N1][P];
+    __shared__ C2<T> ph[3][N1];
+    __shared__ C2<T> I[NPW];
+    __shared__ C2<T> Ap[K + 1][P];
+    __shared__ int coll[9];
+    for (int i = threadIdx.x; i < N1 * P; i += blockDim.x) Co[i / P][i % P] = Cog[i];
+    for (int i = threadIdx.x; i < 3 * N1; i += blockDim.x) ph[i / N1][i % N1] = phg[i];
+    const T wlev = T(1.0 / 9.0);
+    for (int b = blockIdx.x; b < nbox; b += gridDim.x) {
+        const int* e = list + size_t(b) * 11;
+        __syncthreads();
+        if (threadIdx.x < 9) coll[threadIdx.x] = e[2 + threadIdx.x];
+        __syncthreads();
+        for (int it = threadIdx.x; it < NPW; it += blockDim.x) {
+            const int k0 = it / N1, kk1 = it % N1;
+            const T f = fk[it];
+            C2<T> acc{T(0), T(0)};
+            if (f != T(0)) {
+#pragma unroll
+                for (int c = 0; c < 9; ++c) {
+                    const int s = coll[c];
+                    if (s < 0) continue;
+                    const C2<T> phz = cfma(ph[c % 3][k0 + K], ph[c / 3][kk1], C2<T>{T(0), T(0)});
+                    acc = cfma(phz, out[size_t(s) * NPW + it], acc);
+                }
+                acc.x *= f * wlev;
+                acc.y *= f * wlev;
+            }
+            I[it] = acc;
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < (K + 1) * P; it += blockDim.x) {
+            const int k0 = it / P, m1 = it % P;
+            C2<T> acc{T(0), T(0)};
+#pragma unroll
+            for (int kk1 = 0; kk1 < N1; ++kk1) acc = cfma_conj(Co[kk1][m1], I[k0 * N1 + kk1], acc);
+            Ap[k0][m1] = acc;
+        }
+        __syncthreads();
+        T* a = Lc + size_t(e[0]) * (P * P);
+        for (int it = threadIdx.x; it < P * P; it += blockDim.x) {
+            const int m0 = it / P, m1 = it % P;
+            T acc = T(0);
+#pragma unroll
+            for (int k0 = 0; k0 <= K; ++k0) {
+                const C2<T> c = Co[k0 + K][m0];
+                const C2<T> v = Ap[k0][m1];
+                acc = fma(k0 == 0 ? T(1) : T(2), fma(c.x, v.x, c.y * v.y), acc);
+            }
+            a[it] += acc;
+        }
+    }
+}
+
+// leaf evaluation: the leaf's coefficients in shared memory, T_m / T'_m of the second
+// coordinate in registers, the first coordinate's by recurrence inside the contraction
+template <typename T, int P>
+__global__ void __launch_bounds__(32) k_leaf_eval2d_p(const int4* __restrict__ list, const T* __restrict__ Lc,
+                                                      const T* __restrict__ tgt4, double* __restrict__ pot,
+                                                      double* __restrict__ grad, double inv_rc) {
+    __shared__ T a[P * P];
+    const int4 e = list[blockIdx.x];
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) a[i] = Lc[size_t(e.x) * (P * P) + i];
+    __syncthreads();
+    const double sc = 2.0 * inv_rc * double(1LL << e.w);
+    for (int t0i = 0; t0i < e.z; t0i += blockDim.x) {
+        const int ti = t0i + threadIdx.x;
+        if (ti >= e.z) break;
+        const T* x = tgt4 + size_t(e.y + ti) * 4;
+        const T t0 = T(double(x[0]) * sc), t1 = T(double(x[1]) * sc);
+        T b1[P], d1[P];
+        {
+            T tm1 = T(1), tm = t1, um1 = T(1), um = T(2) * t1;
+            b1[0] = T(1);
+            d1[0] = T(0);
+            if (P > 1) { b1[1] = t1; d1[1] = T(1); }
+#pragma unroll
+            for (int m = 2; m < P; ++m) {
+                const T tn = fma(T(2) * t1, tm, -tm1);
+                b1[m] = tn;
+                d1[m] = T(m) * um;
+                const T un = fma(T(2) * t1, um, -um1);
+                tm1 = tm; tm = tn;
+                um1 = um; um = un;
+            }
+        }
+        T phi = 0, g0 = 0, g1 = 0;
+        T c_prev = T(1), c_cur = t0, u_prev = T(1), u_cur = T(2) * t0;  // T_m0, U_{m0-1} recurrences
+#pragma unroll 1
+        for (int m0 = 0; m0 < P; ++m0) {
+            T s = 0, sd = 0;
+#pragma unroll
+            for (int m1 = 0; m1 < P; ++m1) {
+                const T v = a[m0 * P + m1];
+                s = fma(v, b1[m1], s);
+                sd = fma(v, d1[m1], sd);
+            }
+            T tm0, dm0;
+            if (m0 == 0) { tm0 = T(1); dm0 = T(0); }
+            else if (m0 == 1) { tm0 = t0; dm0 = T(1); }
+            else {
+                const T tn = fma(T(2) * t0, c_cur, -c_prev);
+                c_prev = c_cur; c_cur = tn;
+                tm0 = tn;
+                dm0 = T(m0) * u_cur;
+                const T un = fma(T(2) * t0, u_cur, -u_prev);
+                u_prev = u_cur; u_cur = un;
+            }
+            phi = fma(tm0, s, phi);
+            g0 = fma(dm0, s, g0);
+            g1 = fma(tm0, sd, g1);
+        }
+        const size_t o = size_t(e.y + ti);
+        pot[o] = double(phi);
+        if (grad) {
+            grad[o * 2 + 0] = double(g0) * sc;
+            grad[o * 2 + 1] = double(g1) * sc;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
 struct PwImpl {
     PwDims dims{};
@@ -1001,9 +1245,18 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     const size_t sm_m2 = ts * 10 * pd.p * pd.p;
     const size_t sm_d2 = ts * 5 * pd.p * pd.p;
     // 1. leaf moments
+    // (FP64 at P = 32 would need more than 48 KB of static shared memory: generic kernels)
+    const bool fixed2d = D == 2 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16) ||
+                                    (pd.p == 32 && pd.K == 23 && sizeof(T) == 4));
     if (phase == 0 && I->nleafq > 0) {
-        size_t sm = ts * (32 * D * pd.p + 32);
-        k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, static_cast<const T*>(pw->d_src4), Q, pd, inv_rc);
+        const T* s4 = static_cast<const T*>(pw->d_src4);
+        if (fixed2d && pd.p == 16) k_moments2d_p<T, 16><<<I->nleafq, 128, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
+        else if (fixed2d && pd.p == 24) k_moments2d_p<T, 24><<<I->nleafq, 128, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
+        else if (fixed2d && pd.p == 32) k_moments2d_p<T, 32><<<I->nleafq, 128, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
+        else {
+            size_t sm = ts * (32 * D * pd.p + 32);
+            k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, s4, Q, pd, inv_rc);
+        }
         ++pw->launches;
     }
     // compile-time-order 2D re-expansion kernels (dynamic shared memory of nel elements)
@@ -1042,14 +1295,29 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         }
     }
     // 3. outgoing plane waves (all levels)
-    if (phase == 1 && I->nout > 0) {
+    const int pgrid = 148 * 8;
+    if (phase == 1 && I->nout > 0 && fixed2d) {
+        const int g = std::min(I->nout, pgrid);
+        if (pd.p == 16) k_pw_out2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_outl, I->nout, Q, out, Co);
+        else if (pd.p == 24) k_pw_out2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_outl, I->nout, Q, out, Co);
+        else k_pw_out2d_p<T, 32, 23><<<g, 128, 0, s>>>(I->d_outl, I->nout, Q, out, Co);
+        ++pw->launches;
+    } else if (phase == 1 && I->nout > 0) {
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + 2 * size_t(pd.n1) * pd.p);
         cudaFuncSetAttribute(k_pw_out<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_pw_out<T, D><<<I->nout, 128, sm, s>>>(I->d_outl, Q, out, Co, pd, std::min(I->KC, 16));
         ++pw->launches;
     }
     // 4. translation + incoming (all levels)
-    if (phase == 2 && I->nin > 0) {
+    if (phase == 2 && I->nin > 0 && fixed2d) {
+        const int g = std::min(I->nin, pgrid);
+        const C2<T>* ph = static_cast<const C2<T>*>(I->d_ph);
+        const T* fk = static_cast<const T*>(I->d_f);
+        if (pd.p == 16) k_pw_in2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
+        else if (pd.p == 24) k_pw_in2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
+        else k_pw_in2d_p<T, 32, 23><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
+        ++pw->launches;
+    } else if (phase == 2 && I->nin > 0) {
         const int KC = std::min(I->KC, 16);
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + 3 * size_t(pd.n1) + size_t(KC) * pd.nk1 + size_t(KC) * pd.pd1 +
                               size_t(pd.n1) * pd.p);
@@ -1080,7 +1348,13 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         }
     }
     // 6. leaf evaluation
-    if (phase == 4 && I->neval > 0) {
+    if (phase == 4 && I->neval > 0 && fixed2d) {
+        const T* t4 = static_cast<const T*>(pw->d_tgt4);
+        if (pd.p == 16) k_leaf_eval2d_p<T, 16><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
+        else if (pd.p == 24) k_leaf_eval2d_p<T, 24><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
+        else k_leaf_eval2d_p<T, 32><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
+        ++pw->launches;
+    } else if (phase == 4 && I->neval > 0) {
         size_t sm = ts * 32 * 2 * D * pd.p;
         cudaFuncSetAttribute(k_leaf_eval<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_leaf_eval<T, D><<<I->neval, 32, sm, s>>>(I->d_eval, L, static_cast<const T*>(pw->d_tgt4), pw->d_pot,
