@@ -815,11 +815,28 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     if (D == 2 && plan->whole_ctas > 0) {
         const int nwarp = 8;
         const size_t smem = sizeof(T) * (size_t(nwarp) * plan->ncell + size_t(nwarp) * 2 * plan->w);
-        CK(cudaFuncSetAttribute(k_spread_whole<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_spread_whole<T><<<plan->whole_ctas, 32 * nwarp, smem, s>>>(
-            plan->d_t_g0, static_cast<const T*>(plan->d_t_dq), static_cast<const T*>(plan->d_tgt4), int(plan->ntgt),
-            static_cast<T*>(slab), g.M[0], g.M[1], plan->w, hwi2, static_cast<const T*>(plan->d_coefW),
-            int(plan->cW.size()));
+        const int nW = int(plan->cW.size());
+        const int4* tg = plan->d_t_g0;
+        const T* tdq = static_cast<const T*>(plan->d_t_dq);
+        const T* q4 = static_cast<const T*>(plan->d_tgt4);
+        const T* cwp = static_cast<const T*>(plan->d_coefW);
+        T* sl = static_cast<T*>(slab);
+        const int nt = int(plan->ntgt);
+        auto whole_w = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            kern<<<plan->whole_ctas, 32 * nwarp, smem, s>>>(tg, tdq, q4, nt, sl, g.M[0], g.M[1], hwi2, cwp, nW);
+        };
+        // compile-time widths of the default windows (eps = 1e-3, 1e-6, 1e-9)
+        if (plan->w == 8 && nW <= 16) whole_w(k_spread_whole_w<T, 8, 16>);
+        else if (plan->w == 13 && nW <= 16) whole_w(k_spread_whole_w<T, 13, 16>);
+        else if (plan->w == 13 && nW <= 20) whole_w(k_spread_whole_w<T, 13, 20>);
+        else if (plan->w == 17 && nW <= 20) whole_w(k_spread_whole_w<T, 17, 20>);
+        else if (plan->w == 17 && nW <= 28) whole_w(k_spread_whole_w<T, 17, 28>);
+        else {
+            CK(cudaFuncSetAttribute(k_spread_whole<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            k_spread_whole<T><<<plan->whole_ctas, 32 * nwarp, smem, s>>>(tg, tdq, q4, nt, sl, g.M[0], g.M[1], plan->w,
+                                                                        hwi2, cwp, nW);
+        }
         ++plan->launches;
         CK(cudaGetLastError());
         int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 4));

@@ -25,6 +25,20 @@ constexpr int kSpreadWarps = 4;
 constexpr int kSpreadChunk = 128;
 constexpr int kMaxW = 20;
 
+// Clenshaw with a compile-time number of terms and coefficients in registers
+template <typename T, int NC>
+__device__ __forceinline__ T clenshaw_reg_w(const T (&c)[NC], T x) {
+    T b1 = T(0), b2 = T(0);
+    const T x2 = x + x;
+#pragma unroll
+    for (int k = NC - 1; k >= 1; --k) {
+        const T b0 = fma(x2, b1, c[k] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    return fma(x, b1, c[0] - b2);
+}
+
 template <typename T>
 __device__ __forceinline__ T pswf_window(T z, T half_w_inv2, const T* cw, int nw) {
     const T s = z * z * half_w_inv2;
@@ -161,6 +175,75 @@ k_spread_whole(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, const 
             int yy = y0 + iy;
             if (yy >= M1) yy -= M1;
             g[yy * M0 + xx] += q * wv[w + iy] * wv[ix];
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    T* out = slab + size_t(blockIdx.x) * ncell;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        T s = T(0);
+        for (int k = 0; k < nwarp; ++k) s += grids[k * ncell + c];
+        out[c] = s;
+    }
+}
+
+// The same with compile-time window width W and window-series length NWC (coefficients in
+// registers, footprint index arithmetic folded by the compiler).
+template <typename T, int W, int NWC>
+__global__ void __launch_bounds__(256)
+k_spread_whole_w(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, const T* __restrict__ q4, int n,
+                 T* __restrict__ slab, int M0, int M1, T half_w_inv2, const T* __restrict__ coefW, int nW) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int WW = W * W, KK = (WW + 31) / 32;
+    const int ncell = M0 * M1;
+    const int nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T* grids = reinterpret_cast<T*>(smem_raw);  // [nwarp][ncell]
+    T* wins = grids + nwarp * ncell;            // [nwarp][2 W]
+    T cw[NWC];
+#pragma unroll
+    for (int k = 0; k < NWC; ++k) cw[k] = k < nW ? coefW[k] : T(0);
+    for (int i = threadIdx.x; i < nwarp * ncell; i += blockDim.x) grids[i] = T(0);
+    __syncthreads();
+    T* g = grids + wp * ncell;
+    T* wv = wins + wp * 2 * W;
+    int fy[KK], fx[KK];
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+        const int e = lane + 32 * k;
+        fy[k] = e < WW ? e / W : -1;
+        fx[k] = e < WW ? e % W : 0;
+    }
+    const int gw = blockIdx.x * nwarp + wp, nw = gridDim.x * nwarp;
+    const int per = (n + nw - 1) / nw;
+    const int i0 = min(n, gw * per), i1 = min(n, i0 + per);
+    for (int i = i0; i < i1; ++i) {
+        const int4 g0 = t_g0[i];
+        const T* dq = t_dq + size_t(i) * 4;
+#pragma unroll
+        for (int l0 = 0; l0 < 2 * W; l0 += 32) {
+            const int l = l0 + lane;
+            if (l < 2 * W) {
+                const int k = l / W, j = l - (l / W) * W;
+                const T z = dq[k] - T(j);
+                const T s = z * z * half_w_inv2;
+                wv[l] = s < T(1) ? clenshaw_reg_w<T, NWC>(cw, fma(T(2), s, T(-1))) : T(0);
+            }
+        }
+        __syncwarp();
+        const T q = q4[size_t(i) * 4 + 3];
+        int x0 = g0.x % M0;
+        if (x0 < 0) x0 += M0;
+        int y0 = g0.y % M1;
+        if (y0 < 0) y0 += M1;
+#pragma unroll
+        for (int k = 0; k < KK; ++k) {
+            if (fy[k] >= 0) {
+                int xx = x0 + fx[k];
+                if (xx >= M0) xx -= M0;
+                int yy = y0 + fy[k];
+                if (yy >= M1) yy -= M1;
+                g[yy * M0 + xx] += q * wv[W + fy[k]] * wv[fx[k]];
+            }
         }
         __syncwarp();
     }
