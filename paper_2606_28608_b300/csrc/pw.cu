@@ -692,174 +692,275 @@ __global__ void __launch_bounds__(32) k_leaf_eval(const int4* __restrict__ list,
 // compile-time loop bounds: fully unrolled contractions, no run-time integer division, lanes
 // along the contiguous index of every shared-memory operand.
 
-// leaf moments: Q[m0][m1] = sum_s (q_s T_m0(x_s)) T_m1(y_s), a (P x ns)(ns x P) product per leaf
+// Direct moments of the boxes that send outgoing plane waves:
+//   Q_b[m0][m1] = sum_{y in b} q_y T_m0(t0(y)) T_m1(t1(y)),  t = 2 (y - c_b) / h_b,
+// the same polynomial projection the merges of the child moments produce (the re-expansions
+// S_b are exact), taken straight from the sources so that the upward pass is one launch with
+// no level-to-level dependence.  The box coordinate t is the leaf-relative coordinate scaled
+// to the box plus the leaf centre's offset, (2 i_leaf + 1) 2^(l_b - l_leaf) - (2 i_b + 1),
+// which is exact in T.  One block per (box, segment of at most kDirectSeg sources); eight
+// groups of 16 threads split the segment, each thread owns a (P/4) x (P/4) tile; the group
+// partials meet in shared memory and the block writes its partial to its own slot (the
+// outgoing kernel sums a box's slots in a fixed order).
+constexpr int kDirectSeg = 1024;
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+    using type = float2;
+};
+template <>
+struct V2<double> {
+    using type = double2;
+};
+
 template <typename T, int P>
-__global__ void __launch_bounds__(128) k_moments2d_p(const int4* __restrict__ leaves, const T* __restrict__ src4,
-                                                     T* __restrict__ Q, double inv_rc) {
-    constexpr int NB = 32, G = (P + 3) / 4, ITEMS = G * P;
-    constexpr int PER = (ITEMS + 127) / 128;
-    __shared__ T Ax[NB][P];  // q_s T_m(x_s)
-    __shared__ T By[NB][P];  // T_m(y_s)
-    const int4 lf = leaves[blockIdx.x];
-    const T scale = T(2.0 * inv_rc * double(1LL << lf.w));
-    T acc[PER][4];
+__global__ void __launch_bounds__(128) k_moments_direct2d(const int4* __restrict__ items, const T* __restrict__ src4,
+                                                          const int* __restrict__ src_leaf,
+                                                          const int4* __restrict__ bcoord, T* __restrict__ part,
+                                                          double inv_rc) {
+    using T2 = typename V2<T>::type;
+    constexpr int TP = P / 4, S = P + 2, NS = 128, PP = P * P;
+    static_assert(P % 8 == 0 && (S / 2) % 2 == 1, "row stride must be an odd number of pairs");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* A = reinterpret_cast<T*>(smraw);  // [NS][S]  q T_m(t0)
+    T* B = A + NS * S;                   // [NS][S]  T_m(t1)
+    const int4 it = items[blockIdx.x];   // (first source, count, partial slot, box)
+    const int4 bc = bcoord[it.w];        // (i0, i1, level, -)
+    const T scale = T(2.0 * inv_rc * double(1LL << bc.z));
+    const T ob0 = T(2 * bc.x + 1), ob1 = T(2 * bc.y + 1);
+    const int grp = threadIdx.x >> 4, ti = (threadIdx.x >> 2) & 3, tj = threadIdx.x & 3;
+    T acc[TP][TP];
 #pragma unroll
-    for (int u = 0; u < PER; ++u)
+    for (int r = 0; r < TP; ++r)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[u][j] = T(0);
-    for (int s0 = 0; s0 < lf.y; s0 += NB) {
-        const int ns = min(NB, lf.y - s0);
+        for (int c = 0; c < TP; ++c) acc[r][c] = T(0);
+    for (int c0 = 0; c0 < it.y; c0 += NS) {
+        const int ns = min(NS, it.y - c0);
         __syncthreads();
-        if (threadIdx.x < 2 * NB) {
-            const int s = threadIdx.x >> 1, dim = threadIdx.x & 1;
-            T* row = dim ? By[s] : Ax[s];
-            if (s < ns) {
-                const T* y = src4 + size_t(lf.x + s0 + s) * 4;
-                const T t = y[dim] * scale;
-                const T w0 = dim ? T(1) : y[3];
-                T tm1 = T(1), tm = t;
-                row[0] = w0;
-                if (P > 1) row[1] = w0 * t;
+        if (threadIdx.x < ns) {
+            const int j = it.x + c0 + threadIdx.x;
+            const T* y = src4 + size_t(j) * 4;
+            const int4 lc = bcoord[src_leaf[j]];
+            const T sh = T(1) / T(1 << (lc.z - bc.z));  // exact power of two
+            const T t0 = fma(y[0], scale, fma(T(2 * lc.x + 1), sh, -ob0));
+            const T t1 = fma(y[1], scale, fma(T(2 * lc.y + 1), sh, -ob1));
+            const T q = y[3];
+            T2* ra = reinterpret_cast<T2*>(A + threadIdx.x * S);
+            T2* rb = reinterpret_cast<T2*>(B + threadIdx.x * S);
+            T a0 = q, a1 = q * t0, b0 = T(1), b1 = t1;
+            const T x0 = t0 + t0, x1 = t1 + t1;
 #pragma unroll
-                for (int m = 2; m < P; ++m) {
-                    const T tn = fma(T(2) * t, tm, -tm1);
-                    row[m] = w0 * tn;
-                    tm1 = tm;
-                    tm = tn;
-                }
-            } else {
-#pragma unroll
-                for (int m = 0; m < P; ++m) row[m] = T(0);
+            for (int m = 0; m < P; m += 2) {
+                ra[m / 2] = T2{a0, a1};
+                rb[m / 2] = T2{b0, b1};
+                a0 = fma(x0, a1, -a0);
+                a1 = fma(x0, a0, -a1);
+                b0 = fma(x1, b1, -b0);
+                b1 = fma(x1, b0, -b1);
             }
         }
         __syncthreads();
+        for (int s = grp; s < ns; s += 8) {
+            T a[TP], b[TP];
+            const T2* ra = reinterpret_cast<const T2*>(A + s * S + ti * TP);
+            const T2* rb = reinterpret_cast<const T2*>(B + s * S + tj * TP);
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int it = threadIdx.x + u * 128;
-            if (it < ITEMS) {
-                const int g = it / P, m1 = it % P;
-                for (int s = 0; s < ns; ++s) {
-                    const T b = By[s][m1];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (g * 4 + j < P) acc[u][j] = fma(Ax[s][g * 4 + j], b, acc[u][j]);
-                }
+            for (int u = 0; u < TP / 2; ++u) {
+                const T2 va = ra[u], vb = rb[u];
+                a[2 * u] = va.x;
+                a[2 * u + 1] = va.y;
+                b[2 * u] = vb.x;
+                b[2 * u + 1] = vb.y;
             }
+#pragma unroll
+            for (int r = 0; r < TP; ++r)
+#pragma unroll
+                for (int c = 0; c < TP; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
         }
     }
-    T* Qb = Q + size_t(lf.z) * (P * P);
+    __syncthreads();
+    T* red = A;  // [8][PP] (fits in the staging rows)
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int it = threadIdx.x + u * 128;
-        if (it < ITEMS) {
-            const int g = it / P, m1 = it % P;
+    for (int r = 0; r < TP; ++r)
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (g * 4 + j < P) Qb[(g * 4 + j) * P + m1] = acc[u][j];
-        }
+        for (int c = 0; c < TP; ++c) red[grp * PP + (ti * TP + r) * P + tj * TP + c] = acc[r][c];
+    __syncthreads();
+    T* dst = part + size_t(it.z) * PP;
+    for (int i = threadIdx.x; i < PP; i += blockDim.x) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) s += red[g * PP + i];
+        dst[i] = s;
     }
 }
 
-// outgoing plane waves, persistent over boxes: A[k0][m1] = sum_m0 Co[k0][m0] Q[m0][m1],
-// out[k0][k1] = sum_m1 Co[k1][m1] A[k0][m1]
+// Outgoing plane waves from the summed partial moments, persistent over boxes.  The
+// Chebyshev coefficients of exp(-i a t) are real for even m (the cosine) and imaginary for
+// odd m (the sine), even and odd in k respectively:
+//   Co[k][2j] = ce[|k|][j],  Co[k][2j+1] = i sgn(k) so[|k|][j].
+// Stage 1: A[k0][m1] = sum_m0 Co[k0][m0] Q[m0][m1]      (A.x from even m0, A.y from odd m0)
+// Stage 2: E = sum_j ce[k1][j] A[k0][2j],  O = sum_j so[k1][j] A[k0][2j+1]  (k1 >= 0),
+//          out[k0][+-k1] = E +- i O.
+// List entry: (first partial slot, number of slots); the box's out slot is its index.
 template <typename T, int P, int K>
-__global__ void __launch_bounds__(128) k_pw_out2d_p(const int2* __restrict__ list, int nbox, const T* __restrict__ Q,
-                                                    C2<T>* __restrict__ out, const C2<T>* __restrict__ Cog) {
-    constexpr int N1 = 2 * K + 1, NPW = (K + 1) * N1;
-    __shared__ C2<T> Co[N1][P];    // Co[k + K][m]
-    __shared__ C2<T> CoT[P][N1];   // transposed
-    __shared__ T q[P * P];
+__global__ void __launch_bounds__(128) k_pw_out2d_p(const int2* __restrict__ list, int nbox,
+                                                    const T* __restrict__ part, C2<T>* __restrict__ out,
+                                                    const C2<T>* __restrict__ Cog) {
+    constexpr int N1 = 2 * K + 1, NPW = (K + 1) * N1, H = P / 2, PP = P * P;
+    __shared__ T ce[K + 1][H], so[K + 1][H];    // rows by k (stage 1: k broadcast)
+    __shared__ T ceT[H][K + 1], soT[H][K + 1];  // rows by j (stage 2: lanes along k1)
+    __shared__ T q[PP];
     __shared__ C2<T> A[K + 1][P];
-    for (int i = threadIdx.x; i < N1 * P; i += blockDim.x) {
-        const C2<T> v = Cog[i];
-        Co[i / P][i % P] = v;
-        CoT[i % P][i / P] = v;
+    for (int i = threadIdx.x; i < (K + 1) * H; i += blockDim.x) {
+        const int k = i / H, j = i % H;
+        const T e = Cog[(k + K) * P + 2 * j].x, o = Cog[(k + K) * P + 2 * j + 1].y;
+        ce[k][j] = e;
+        so[k][j] = o;
+        ceT[j][k] = e;
+        soT[j][k] = o;
     }
     for (int b = blockIdx.x; b < nbox; b += gridDim.x) {
         const int2 e = list[b];
         __syncthreads();
-        for (int i = threadIdx.x; i < P * P; i += blockDim.x) q[i] = Q[size_t(e.x) * (P * P) + i];
+        for (int i = threadIdx.x; i < PP; i += blockDim.x) {
+            const T* src = part + size_t(e.x) * PP + i;
+            T s = src[0];
+            for (int u = 1; u < e.y; ++u) s += src[size_t(u) * PP];
+            q[i] = s;
+        }
         __syncthreads();
         for (int it = threadIdx.x; it < (K + 1) * P; it += blockDim.x) {
             const int k0 = it / P, m1 = it % P;
-            C2<T> acc{T(0), T(0)};
+            T ax = T(0), ay = T(0);
 #pragma unroll
-            for (int m0 = 0; m0 < P; ++m0) {
-                const C2<T> c = Co[k0 + K][m0];
-                const T v = q[m0 * P + m1];
-                acc.x = fma(c.x, v, acc.x);
-                acc.y = fma(c.y, v, acc.y);
+            for (int j = 0; j < H; ++j) {
+                ax = fma(ce[k0][j], q[(2 * j) * P + m1], ax);
+                ay = fma(so[k0][j], q[(2 * j + 1) * P + m1], ay);
             }
-            A[k0][m1] = acc;
+            A[k0][m1] = C2<T>{ax, ay};
         }
         __syncthreads();
-        C2<T>* o = out + size_t(e.y) * NPW;
-        for (int it = threadIdx.x; it < NPW; it += blockDim.x) {
-            const int k0 = it / N1, kk1 = it % N1;
-            C2<T> acc{T(0), T(0)};
+        C2<T>* o = out + size_t(b) * NPW;
+        for (int it = threadIdx.x; it < (K + 1) * (K + 1); it += blockDim.x) {
+            const int k0 = it / (K + 1), k1 = it % (K + 1);
+            T ex = T(0), ey = T(0), ox = T(0), oy = T(0);
 #pragma unroll
-            for (int m1 = 0; m1 < P; ++m1) acc = cfma(CoT[m1][kk1], A[k0][m1], acc);
-            o[it] = acc;
+            for (int j = 0; j < H; ++j) {
+                const C2<T> ae = A[k0][2 * j], ao = A[k0][2 * j + 1];
+                const T c = ceT[j][k1], s = soT[j][k1];
+                ex = fma(c, ae.x, ex);
+                ey = fma(c, ae.y, ey);
+                ox = fma(s, ao.x, ox);
+                oy = fma(s, ao.y, oy);
+            }
+            // i O = (-oy, ox)
+            o[k0 * N1 + K + k1] = C2<T>{ex - oy, ey + ox};
+            if (k1 > 0) o[k0 * N1 + K - k1] = C2<T>{ex + oy, ey - ox};
         }
     }
 }
 
-// translation + incoming, persistent over boxes (list entry: local slot, level, 9 out slots)
+// translation + incoming, persistent over boxes (list entry: local slot, level, 9 out slots).
+// Stage 1 sums the colleagues' outgoing waves with the translation phases for the pair of
+// modes (k0, +-k1) at once.  The phases factor by dimension, exp(-i (2 pi/3) k.delta) =
+// v^delta0 u^delta1 with u = exp(-i (2 pi/3) k1), v = exp(-i (2 pi/3) k0), and for
+// delta in {-1, 0, 1}:  u X_+ + conj(u) X_- = Re(u) (X_+ + X_-) + i Im(u) (X_+ - X_-).
+// The mode pair is kept as Sp = I(+k1) + I(-k1), Sm = I(+k1) - I(-k1), which is what the
+// parity of Co needs (conj(Co[k][2j]) = ce[|k|][j], conj(Co[k][2j+1]) = -i sgn(k) so[|k|][j]):
+// Stage 2: Ap[k0][2j] = sum_k1 ce[k1][j] Sp[k0][k1],  Ap[k0][2j+1] = -i sum_k1 so[k1][j] Sm[k0][k1]
+// Stage 3: a[2j][m1] += sum_k0 w ce[k0][j] Re Ap[k0][m1],  a[2j+1][m1] += sum_k0 w so[k0][j] Im Ap[k0][m1]
+// (w = 1 for k0 = 0, else 2: the Hermitian half of the k0 axis).
 template <typename T, int P, int K>
 __global__ void __launch_bounds__(128) k_pw_in2d_p(const int* __restrict__ list, int nbox, const C2<T>* __restrict__ out,
                                                    T* __restrict__ Lc, const C2<T>* __restrict__ Cog,
                                                    const C2<T>* __restrict__ phg, const T* __restrict__ fk) {
-    constexpr int N1 = 2 * K + 1, NPW = (K + 1) * N1;
-    __shared__ C2<T> Co[N1][P];
-    __shared__ C2<T> ph[3][N1];
-    __shared__ C2<T> I[NPW];
-    __shared__ C2<T> Ap[K + 1][P];
+    constexpr int N1 = 2 * K + 1, NPW = (K + 1) * N1, H = P / 2, KH = K + 1;
+    __shared__ T ce[KH][H], so[KH][H];
+    __shared__ C2<T> Sp[KH][KH], Sm[KH][KH];
+    __shared__ C2<T> Ap[KH][P];
+    __shared__ C2<T> u[KH];
     __shared__ int coll[9];
-    for (int i = threadIdx.x; i < N1 * P; i += blockDim.x) Co[i / P][i % P] = Cog[i];
-    for (int i = threadIdx.x; i < 3 * N1; i += blockDim.x) ph[i / N1][i % N1] = phg[i];
+    for (int i = threadIdx.x; i < KH * H; i += blockDim.x) {
+        const int k = i / H, j = i % H;
+        ce[k][j] = Cog[(k + K) * P + 2 * j].x;
+        so[k][j] = Cog[(k + K) * P + 2 * j + 1].y;
+    }
+    for (int i = threadIdx.x; i < KH; i += blockDim.x) u[i] = phg[2 * N1 + K + i];  // delta = +1
     const T wlev = T(1.0 / 9.0);
     for (int b = blockIdx.x; b < nbox; b += gridDim.x) {
         const int* e = list + size_t(b) * 11;
         __syncthreads();
         if (threadIdx.x < 9) coll[threadIdx.x] = e[2 + threadIdx.x];
         __syncthreads();
-        for (int it = threadIdx.x; it < NPW; it += blockDim.x) {
-            const int k0 = it / N1, kk1 = it % N1;
-            const T f = fk[it];
-            C2<T> acc{T(0), T(0)};
-            if (f != T(0)) {
+        for (int it = threadIdx.x; it < KH * KH; it += blockDim.x) {
+            const int k0 = it / KH, k1 = it % KH;
+            const T fw = fk[k0 * N1 + K + k1] * wlev;
+            C2<T> ip{T(0), T(0)}, im{T(0), T(0)};
+            if (fw != T(0)) {
+                const C2<T> uu = u[k1], vv = u[k0];
+                C2<T> rp[3], rm[3];  // per delta0 row: sums over delta1
 #pragma unroll
-                for (int c = 0; c < 9; ++c) {
-                    const int s = coll[c];
-                    if (s < 0) continue;
-                    const C2<T> phz = cfma(ph[c % 3][k0 + K], ph[c / 3][kk1], C2<T>{T(0), T(0)});
-                    acc = cfma(phz, out[size_t(s) * NPW + it], acc);
+                for (int r = 0; r < 3; ++r) {
+                    const int sm_ = coll[r], s0 = coll[r + 3], sp = coll[r + 6];
+                    const size_t op = size_t(k0) * N1 + K + k1, om = size_t(k0) * N1 + K - k1;
+                    const C2<T> z{T(0), T(0)};
+                    const C2<T> pP = sp >= 0 ? out[size_t(sp) * NPW + op] : z;
+                    const C2<T> pM = sm_ >= 0 ? out[size_t(sm_) * NPW + op] : z;
+                    const C2<T> p0 = s0 >= 0 ? out[size_t(s0) * NPW + op] : z;
+                    const C2<T> mP = sp >= 0 ? out[size_t(sp) * NPW + om] : z;
+                    const C2<T> mM = sm_ >= 0 ? out[size_t(sm_) * NPW + om] : z;
+                    const C2<T> m0 = s0 >= 0 ? out[size_t(s0) * NPW + om] : z;
+                    // +k1: p0 + Re(u) (pP + pM) + i Im(u) (pP - pM)
+                    rp[r].x = p0.x + uu.x * (pP.x + pM.x) - uu.y * (pP.y - pM.y);
+                    rp[r].y = p0.y + uu.x * (pP.y + pM.y) + uu.y * (pP.x - pM.x);
+                    // -k1: u -> conj(u)
+                    rm[r].x = m0.x + uu.x * (mP.x + mM.x) + uu.y * (mP.y - mM.y);
+                    rm[r].y = m0.y + uu.x * (mP.y + mM.y) - uu.y * (mP.x - mM.x);
                 }
-                acc.x *= f * wlev;
-                acc.y *= f * wlev;
+                ip.x = fw * (rp[1].x + vv.x * (rp[2].x + rp[0].x) - vv.y * (rp[2].y - rp[0].y));
+                ip.y = fw * (rp[1].y + vv.x * (rp[2].y + rp[0].y) + vv.y * (rp[2].x - rp[0].x));
+                im.x = fw * (rm[1].x + vv.x * (rm[2].x + rm[0].x) - vv.y * (rm[2].y - rm[0].y));
+                im.y = fw * (rm[1].y + vv.x * (rm[2].y + rm[0].y) + vv.y * (rm[2].x - rm[0].x));
             }
-            I[it] = acc;
+            if (k1 == 0) {
+                Sp[k0][0] = ip;  // the +-k1 modes coincide
+                Sm[k0][0] = C2<T>{T(0), T(0)};
+            } else {
+                Sp[k0][k1] = C2<T>{ip.x + im.x, ip.y + im.y};
+                Sm[k0][k1] = C2<T>{ip.x - im.x, ip.y - im.y};
+            }
         }
         __syncthreads();
-        for (int it = threadIdx.x; it < (K + 1) * P; it += blockDim.x) {
-            const int k0 = it / P, m1 = it % P;
-            C2<T> acc{T(0), T(0)};
+        for (int it = threadIdx.x; it < KH * H; it += blockDim.x) {
+            const int k0 = it / H, j = it % H;
+            T ex = T(0), ey = T(0), ox = T(0), oy = T(0);
 #pragma unroll
-            for (int kk1 = 0; kk1 < N1; ++kk1) acc = cfma_conj(Co[kk1][m1], I[k0 * N1 + kk1], acc);
-            Ap[k0][m1] = acc;
+            for (int k1 = 0; k1 < KH; ++k1) {
+                const C2<T> sp = Sp[k0][k1], sm_ = Sm[k0][k1];
+                const T c = ce[k1][j], s = so[k1][j];
+                ex = fma(c, sp.x, ex);
+                ey = fma(c, sp.y, ey);
+                ox = fma(s, sm_.x, ox);
+                oy = fma(s, sm_.y, oy);
+            }
+            Ap[k0][2 * j] = C2<T>{ex, ey};
+            Ap[k0][2 * j + 1] = C2<T>{oy, -ox};  // -i (ox + i oy)
         }
         __syncthreads();
         T* a = Lc + size_t(e[0]) * (P * P);
-        for (int it = threadIdx.x; it < P * P; it += blockDim.x) {
-            const int m0 = it / P, m1 = it % P;
-            T acc = T(0);
+        for (int it = threadIdx.x; it < H * P; it += blockDim.x) {
+            const int j = it / P, m1 = it % P;
+            T ae = T(0), ao = T(0);
 #pragma unroll
-            for (int k0 = 0; k0 <= K; ++k0) {
-                const C2<T> c = Co[k0 + K][m0];
+            for (int k0 = 0; k0 < KH; ++k0) {
                 const C2<T> v = Ap[k0][m1];
-                acc = fma(k0 == 0 ? T(1) : T(2), fma(c.x, v.x, c.y * v.y), acc);
+                const T w = k0 == 0 ? T(1) : T(2);
+                ae = fma(w * ce[k0][j], v.x, ae);
+                ao = fma(w * so[k0][j], v.y, ao);
             }
-            a[it] += acc;
+            a[(2 * j) * P + m1] += ae;
+            a[(2 * j + 1) * P + m1] += ao;
         }
     }
 }
@@ -955,6 +1056,13 @@ struct PwImpl {
     int4* d_eval = nullptr;
     int neval = 0;
     int nlevels = 1;
+    // 2D compile-time orders: direct moments of the out boxes (no merges)
+    bool direct2d = false;
+    int4* d_ditems = nullptr;  // (first source, count, partial slot, box), largest first
+    int nditems = 0;
+    int* d_src_leaf = nullptr;  // leaf box of every sorted source
+    int4* d_bcoord = nullptr;   // (i0, i1, level, 0) per box
+    void* d_part = nullptr;     // partial moments [nditems][p p]
     // arrays
     void* d_Q = nullptr;
     void* d_out = nullptr;
@@ -1097,7 +1205,13 @@ void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables&
 
 bool pw_supported(const PwPlan*) { return true; }
 
-int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const std::vector<int>& /*leaf_of*/,
+// the 2D orders with compile-time kernels (FP64 at P = 32 would exceed the shared memory
+// the static layouts assume)
+static bool direct2d_orders(const PwDims& pd, bool mixed) {
+    return pd.d == 2 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16) || (pd.p == 32 && pd.K == 23 && mixed));
+}
+
+int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const std::vector<int>& leaf_of,
                    const std::vector<int>& /*tgt_leaf*/, const Geometry& g, cudaStream_t stream) {
     PwImpl* I = impl(pw);
     const int d = t.d;
@@ -1145,21 +1259,50 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         if (oslot[b] >= 0) outl.push_back(make_int2(qslot[b], oslot[b]));
     std::sort(outl.begin(), outl.end(), [](const int2& a, const int2& b) { return a.y < b.y; });
     I->nout = nout;
+    pw->moment_sources = 0;
+    // 2D compile-time orders: the out boxes' moments straight from their sources, in
+    // segments of at most kDirectSeg; the out list becomes (first partial slot, count)
+    I->direct2d = direct2d_orders(I->dims, pw->mixed);
+    std::vector<int4> ditems;
+    std::vector<int> src_leaf;
+    std::vector<int4> bcoord;
+    if (I->direct2d) {
+        std::vector<int> box_of_out(nout, -1);
+        for (int b = 0; b < nb; ++b)
+            if (oslot[b] >= 0) box_of_out[oslot[b]] = b;
+        int npart = 0;
+        for (int o = 0; o < nout; ++o) {
+            const int b = box_of_out[o];
+            const int64_t s0 = t.src_begin[b], ns = t.src_end[b] - t.src_begin[b];
+            const int first = npart;
+            for (int64_t c = 0; c < ns; c += kDirectSeg)
+                ditems.push_back(make_int4(int(s0 + c), int(std::min<int64_t>(kDirectSeg, ns - c)), npart++, b));
+            outl[o] = make_int2(first, npart - first);
+        }
+        // largest segments first: the long blocks start in the first wave
+        std::stable_sort(ditems.begin(), ditems.end(), [](const int4& a, const int4& b) { return a.y > b.y; });
+        I->nditems = int(ditems.size());
+        src_leaf = leaf_of;
+        bcoord.resize(nb);
+        for (int b = 0; b < nb; ++b)
+            bcoord[b] = make_int4(int(t.coord[size_t(b) * d]), int(t.coord[size_t(b) * d + 1]), t.level[b], 0);
+        for (const int4& it : ditems) pw->moment_sources += it.y;
+    }
     // leaf moments
     std::vector<int4> leafq;
     for (int b = 0; b < nb; ++b)
-        if (t.is_leaf(b) && has_src(b))
+        if (!I->direct2d && t.is_leaf(b) && has_src(b))
             leafq.push_back(make_int4(int(t.src_begin[b]), int(t.src_end[b] - t.src_begin[b]), qslot[b], t.level[b]));
     I->nleafq = int(leafq.size());
-    pw->moment_sources = 0;
-    for (const int4& l : leafq) pw->moment_sources += l.y;
+    if (!I->direct2d)
+        for (const int4& l : leafq) pw->moment_sources += l.y;
     // merges per level (non-leaf boxes with sources), deepest first at eval time
     std::vector<int> merge;
     I->merge_start.assign(t.nlevels + 1, 0);
     for (int l = 0; l < t.nlevels; ++l) {
         I->merge_start[l] = int(merge.size()) / (1 + nc);
         for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
-            if (t.is_leaf(b) || !has_src(b)) continue;
+            if (I->direct2d || t.is_leaf(b) || !has_src(b)) continue;
             merge.push_back(qslot[b]);
             for (int c = 0; c < nc; ++c) merge.push_back(qslot[t.child0[b] + c]);
         }
@@ -1211,6 +1354,15 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     if ((r = pw_upload(pw, &I->d_down, down, stream))) return r;
     if ((r = pw_upload(pw, &I->d_eval, ev, stream))) return r;
     unsigned char* p = nullptr;
+    if (I->direct2d) {
+        if ((r = pw_upload(pw, &I->d_ditems, ditems, stream))) return r;
+        if ((r = pw_upload(pw, &I->d_src_leaf, src_leaf, stream))) return r;
+        if ((r = pw_upload(pw, &I->d_bcoord, bcoord, stream))) return r;
+        if ((r = pw_alloc(pw, &p, size_t(std::max(I->nditems, 1)) * I->dims.np * ts))) return r;
+        I->d_part = p;
+        nq = 0;  // no per-box moments
+        I->nq = 0;
+    }
     if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nq, 1)) * I->dims.np * ts))) return r;
     I->d_Q = p;
     if ((r = pw_alloc(pw, &p, size_t(std::max(nout, 1)) * I->dims.npw * 2 * ts))) return r;
@@ -1246,17 +1398,24 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     const size_t sm_d2 = ts * 5 * pd.p * pd.p;
     // 1. leaf moments
     // (FP64 at P = 32 would need more than 48 KB of static shared memory: generic kernels)
-    const bool fixed2d = D == 2 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16) ||
-                                    (pd.p == 32 && pd.K == 23 && sizeof(T) == 4));
+    const bool fixed2d = D == 2 && I->direct2d;
+    if (phase == 0 && fixed2d && I->nditems > 0) {
+        const T* s4 = static_cast<const T*>(pw->d_src4);
+        T* part = static_cast<T*>(I->d_part);
+        auto direct = [&](auto kern, int P) {
+            const size_t smb = ts * std::max(2 * 128 * (P + 2), 8 * P * P);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+            kern<<<I->nditems, 128, smb, s>>>(I->d_ditems, s4, I->d_src_leaf, I->d_bcoord, part, inv_rc);
+        };
+        if (pd.p == 16) direct(k_moments_direct2d<T, 16>, 16);
+        else if (pd.p == 24) direct(k_moments_direct2d<T, 24>, 24);
+        else direct(k_moments_direct2d<T, 32>, 32);
+        ++pw->launches;
+    }
     if (phase == 0 && I->nleafq > 0) {
         const T* s4 = static_cast<const T*>(pw->d_src4);
-        if (fixed2d && pd.p == 16) k_moments2d_p<T, 16><<<I->nleafq, 128, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
-        else if (fixed2d && pd.p == 24) k_moments2d_p<T, 24><<<I->nleafq, 128, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
-        else if (fixed2d && pd.p == 32) k_moments2d_p<T, 32><<<I->nleafq, 128, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
-        else {
-            size_t sm = ts * (32 * D * pd.p + 32);
-            k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, s4, Q, pd, inv_rc);
-        }
+        const size_t sm = ts * (32 * D * pd.p + 32);
+        k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, s4, Q, pd, inv_rc);
         ++pw->launches;
     }
     // compile-time-order 2D re-expansion kernels (dynamic shared memory of nel elements)
@@ -1298,9 +1457,10 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     const int pgrid = 148 * 8;
     if (phase == 1 && I->nout > 0 && fixed2d) {
         const int g = std::min(I->nout, pgrid);
-        if (pd.p == 16) k_pw_out2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_outl, I->nout, Q, out, Co);
-        else if (pd.p == 24) k_pw_out2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_outl, I->nout, Q, out, Co);
-        else k_pw_out2d_p<T, 32, 23><<<g, 128, 0, s>>>(I->d_outl, I->nout, Q, out, Co);
+        const T* part = static_cast<const T*>(I->d_part);
+        if (pd.p == 16) k_pw_out2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_outl, I->nout, part, out, Co);
+        else if (pd.p == 24) k_pw_out2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_outl, I->nout, part, out, Co);
+        else k_pw_out2d_p<T, 32, 23><<<g, 128, 0, s>>>(I->d_outl, I->nout, part, out, Co);
         ++pw->launches;
     } else if (phase == 1 && I->nout > 0) {
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + 2 * size_t(pd.n1) * pd.p);
