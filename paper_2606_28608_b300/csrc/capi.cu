@@ -51,6 +51,8 @@ struct pdmk_plan_s {
     KernelTables kt;
     WindowTables wt;
     std::vector<double> cA, cB, cW, cWd;  // near-field Chebyshev coefficients (FP64 master copy)
+    std::vector<double> mA, mB;  // A and B as monomials in x = 2 s - 1 (warp near-field kernel)
+    int near_nh = 0;             // > 0: warp near-field kernel with this many monomial terms
     int B[3] = {1, 1, 1}, nbin[3] = {1, 1, 1}, P[3] = {1, 1, 1}, Ptot = 1;
     int whole_ctas = 0;  // > 0: 2D whole-grid spreading with this many CTAs (small grids)
     int64_t ncell = 1, nhalf = 1;
@@ -69,6 +71,8 @@ struct pdmk_plan_s {
     void* d_coefB = nullptr;
     void* d_coefW = nullptr;
     void* d_coefWd = nullptr;
+    void* d_monoA = nullptr;
+    void* d_monoB = nullptr;
     double* d_weight = nullptr;
     void* d_grid = nullptr;
     void* d_spec = nullptr;
@@ -90,6 +94,9 @@ struct pdmk_plan_s {
     double* d_self_w = nullptr;
     TLeaf* d_tleaf = nullptr;
     int* d_list = nullptr;
+    int2* d_ent = nullptr;      // per direct-list entry: source range
+    void* d_ent_sh = nullptr;   // per entry: shift into the target leaf's frame (4 T)
+    void* d_ent_shlo = nullptr; // per entry: lo part of the shift (mixed)
     int* d_box_src_begin = nullptr;
     int* d_box_src_count = nullptr;
     double* d_box_center = nullptr;
@@ -326,7 +333,43 @@ extern "C" int pdmk_kernel_table_eval(int d, double eps, int kind, double x, dou
     }
 }
 
-extern "C" int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, pdmk_plan* out) {
+extern "C" // Chebyshev series sum_k c_k T_k(x) on [-1, 1] as monomials sum_k a_k x^k (long double
+// recurrence T_{k+1} = 2 x T_k - T_{k-1}).  Returns sum |a_k| / max |f| on a grid: the factor
+// by which Horner's rounding error can exceed Clenshaw's.
+static double cheb_to_mono(const std::vector<double>& c, std::vector<double>* a) {
+    const size_t n = c.size();
+    std::vector<long double> tm1(n + 1, 0.0L), t0(n + 1, 0.0L), acc(n + 1, 0.0L);
+    tm1[0] = 1.0L;  // T_0
+    if (n > 0) for (size_t i = 0; i <= n; ++i) acc[i] += c[0] * tm1[i];
+    if (n > 1) {
+        t0[1] = 1.0L;  // T_1
+        for (size_t i = 0; i <= n; ++i) acc[i] += c[1] * t0[i];
+    }
+    for (size_t k = 2; k < n; ++k) {
+        std::vector<long double> t1(n + 1, 0.0L);
+        for (size_t i = 0; i + 1 <= n; ++i) t1[i + 1] += 2.0L * t0[i];
+        for (size_t i = 0; i <= n; ++i) t1[i] -= tm1[i];
+        for (size_t i = 0; i <= n; ++i) acc[i] += c[k] * t1[i];
+        tm1.swap(t0);
+        t0.swap(t1);
+    }
+    a->assign(n, 0.0);
+    double sa = 0;
+    for (size_t i = 0; i < n; ++i) {
+        (*a)[i] = double(acc[i]);
+        sa += std::fabs((*a)[i]);
+    }
+    double fmax = 0;
+    for (int g = 0; g <= 2000; ++g) {
+        const double x = -1.0 + g / 1000.0;
+        long double v = 0;
+        for (size_t i = n; i-- > 0;) v = v * x + acc[i];
+        fmax = std::max(fmax, std::fabs(double(v)));
+    }
+    return fmax > 0 ? sa / fmax : 1.0;
+}
+
+int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, pdmk_plan* out) {
     if (!out || !L || (d != 2 && d != 3)) return PDMK_ERR_BAD_ARG;
     *out = nullptr;
     if (!(eps >= 1e-12 && eps <= 1e-2)) return PDMK_ERR_BAD_EPS;
@@ -376,6 +419,20 @@ extern "C" int pdmk_plan_create(int d, const double* L, double eps, const pdmk_o
     plan->cB = plan->kt.B.coef;
     if (int(plan->cA.size()) > kMaxCheb) plan->cA.resize(kMaxCheb);
     if (int(plan->cB.size()) > kMaxCheb) plan->cB.resize(kMaxCheb);
+    {
+        // the warp near-field kernel takes the series as monomials when Horner is as
+        // accurate as Clenshaw and the length has a compiled instance
+        const double ampA = cheb_to_mono(plan->cA, &plan->mA), ampB = cheb_to_mono(plan->cB, &plan->mB);
+        const int nmax = int(std::max(plan->cA.size(), plan->cB.size()));
+        static const int kNH[] = {8, 10, 12, 14, 16, 20, 24};
+        plan->near_nh = 0;
+        if (ampA <= 4.0 && ampB <= 4.0)
+            for (int nh : kNH)
+                if (nmax <= nh) {
+                    plan->near_nh = nh;
+                    break;
+                }
+    }
     plan->cW = plan->wt.F.coef;
     plan->cWd = plan->wt.dF.coef;
     if (int(plan->cW.size()) > kMaxCheb) plan->cW.resize(kMaxCheb);
@@ -404,6 +461,8 @@ extern "C" int pdmk_plan_create(int d, const double* L, double eps, const pdmk_o
         PCHECK(coef_upload(plan->cB, &plan->d_coefB));
         PCHECK(coef_upload(plan->cW, &plan->d_coefW));
         PCHECK(coef_upload(plan->cWd, &plan->d_coefWd));
+        PCHECK(coef_upload(plan->mA, &plan->d_monoA));
+        PCHECK(coef_upload(plan->mB, &plan->d_monoB));
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_weight, size_t(plan->nhalf)));
         std::vector<double> wt = far_weights(plan);
         PCHECK(upload(plan, plan->d_weight, wt));
@@ -624,6 +683,39 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
         bsb[b] = int(tree.src_begin[b]);
         bsc[b] = int(tree.src_end[b] - tree.src_begin[b]);
     }
+    // per direct-list entry: source range and the source leaf centre's shift into the target
+    // leaf's frame (FP64 difference, then hi / lo in T)
+    std::vector<int2> ent(dl.list.size());
+    std::vector<unsigned char> ent_sh(dl.list.size() * 4 * ts, 0);
+    std::vector<float> ent_shlo(mixed ? dl.list.size() * 4 : 0, 0.0f);
+    for (size_t k = 0; k < dl.tleaf.size(); ++k) {
+        const int tb = dl.tleaf[k];
+        for (int64_t e = dl.list_begin[k]; e < dl.list_begin[k + 1]; ++e) {
+            const int sb = dl.list[e];
+            ent[e] = make_int2(bsb[sb], bsc[sb]);
+            for (int a = 0; a < d; ++a) {
+                const double sh = tree.center[size_t(sb) * d + a] - tree.center[size_t(tb) * d + a];
+                put(ent_sh, size_t(e) * 4 + a, sh);
+                if (mixed) ent_shlo[size_t(e) * 4 + a] = float(sh - double(float(sh)));
+            }
+        }
+    }
+    // the warp near-field kernel takes leaves in order of decreasing pair count (the long
+    // ones start first)
+    {
+        std::vector<int64_t> cost(tl.size(), 0);
+        for (size_t k = 0; k < tl.size(); ++k) {
+            int64_t ns = 0;
+            for (int e = tl[k].list_begin; e < tl[k].list_begin + tl[k].list_count; ++e) ns += ent[e].y;
+            cost[k] = ns * int64_t(tl[k].tgt_count);
+        }
+        std::vector<size_t> ord(tl.size());
+        std::iota(ord.begin(), ord.end(), size_t(0));
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+        std::vector<TLeaf> tl2(tl.size());
+        for (size_t k = 0; k < ord.size(); ++k) tl2[k] = tl[ord[k]];
+        tl.swap(tl2);
+    }
     // far field: originals sorted by spreading bin, window start and offsets in FP64
     const int fw = plan->w / 2;
     auto grid_coord = [&](double uu, int i, int* g0, double* del) {
@@ -707,6 +799,9 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     DALLOC(L, plan->d_self_w, double, plan->ntgt);
     DALLOC(L, plan->d_tleaf, TLeaf, tl.size());
     DALLOC(L, plan->d_list, int, dl.list.size());
+    DALLOC(L, plan->d_ent, int2, ent.size());
+    DALLOC(L, plan->d_ent_sh, unsigned char, ent_sh.size());
+    DALLOC(L, plan->d_ent_shlo, float, ent_shlo.size());
     DALLOC(L, plan->d_box_src_begin, int, bsb.size());
     DALLOC(L, plan->d_box_src_count, int, bsc.size());
     DALLOC(L, plan->d_box_center, double, tree.center.size());
@@ -738,6 +833,9 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     if ((r = upload(plan, plan->d_box_src_begin, bsb))) return r;
     if ((r = upload(plan, plan->d_box_src_count, bsc))) return r;
     if ((r = upload(plan, plan->d_box_center, tree.center))) return r;
+    if ((r = upload(plan, plan->d_ent, ent))) return r;
+    if ((r = upload(plan, plan->d_ent_sh, ent_sh))) return r;
+    if ((r = upload(plan, plan->d_ent_shlo, ent_shlo))) return r;
     if ((r = upload(plan, plan->d_pt_g0, pt_g0))) return r;
     if ((r = upload(plan, plan->d_pt_dq, pt_dq))) return r;
     if ((r = upload(plan, plan->d_spread_orig, sp_orig))) return r;
@@ -956,8 +1054,21 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
             CK(cudaMemsetAsync(plan->d_count, 0, sizeof(unsigned long long), s));
             na.count_in = plan->d_count;
         }
+        na.ent = plan->d_ent;
+        na.ent_sh = static_cast<const T*>(plan->d_ent_sh);
+        na.ent_shlo = static_cast<const T*>(plan->d_ent_shlo);
+        na.monoA = static_cast<const T*>(plan->d_monoA);
+        na.monoB = static_cast<const T*>(plan->d_monoB);
         const int nc = std::max(na.nA, na.nB);
-        if (nc <= 8) k_nearfield<T, D, 8><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        const int wb = (plan->ntleaf + kNearWarps - 1) / kNearWarps, wt = 32 * kNearWarps;
+        if (plan->near_nh == 8) k_near_warp<T, D, 8><<<wb, wt, 0, s>>>(na);
+        else if (plan->near_nh == 10) k_near_warp<T, D, 10><<<wb, wt, 0, s>>>(na);
+        else if (plan->near_nh == 12) k_near_warp<T, D, 12><<<wb, wt, 0, s>>>(na);
+        else if (plan->near_nh == 14) k_near_warp<T, D, 14><<<wb, wt, 0, s>>>(na);
+        else if (plan->near_nh == 16) k_near_warp<T, D, 16><<<wb, wt, 0, s>>>(na);
+        else if (plan->near_nh == 20) k_near_warp<T, D, 20><<<wb, wt, 0, s>>>(na);
+        else if (plan->near_nh == 24) k_near_warp<T, D, 24><<<wb, wt, 0, s>>>(na);
+        else if (nc <= 8) k_nearfield<T, D, 8><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
         else if (nc <= 12) k_nearfield<T, D, 12><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
         else if (nc <= 16) k_nearfield<T, D, 16><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
         else if (nc <= 20) k_nearfield<T, D, 20><<<plan->ntleaf, kNearThreads, 0, s>>>(na);

@@ -66,6 +66,14 @@ struct NearArgs {
     const T* src_lo;            // 4 per sorted source: lo parts of the leaf-relative coordinates
     const T* tgt_lo;            // 4 per sorted target
     T close_s;
+    // warp kernel: per direct-list entry the source range and the shift of the source leaf's
+    // centre into the target leaf's frame (hi, and lo on the mixed path), 4 T per entry
+    const int2* ent;
+    const T* ent_sh;
+    const T* ent_shlo;
+    // warp kernel: A and B as monomials in x = 2 s - 1 (zero-padded)
+    const T* monoA;
+    const T* monoB;
 };
 
 // -------- far field -----------------------------------------------------------------
