@@ -59,6 +59,10 @@ struct pdmk_plan_s {
     cudaStream_t stream = nullptr;  // the caller's stream
     cudaStream_t ws = nullptr;      // the plan's own work stream (graph capture needs a non-default stream)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // branches of one evaluation: the plane-wave chain (highest priority: many small
+    // latency-bound launches) and the near-field sum run beside the far field on ws
+    cudaStream_t ws_pw = nullptr, ws_near = nullptr;
+    cudaEvent_t ev_s = nullptr, ev_pw = nullptr, ev_near = nullptr;
     cudaGraphExec_t gexec = nullptr;
     double* g_pot = nullptr;
     double* g_grad = nullptr;
@@ -385,11 +389,18 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     plan->d = d;
     plan->eps = eps;
     plan->stream = static_cast<cudaStream_t>(plan->opts.stream);
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (cudaStreamCreateWithFlags(&plan->ws, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&plan->ws_pw, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&plan->ws_near, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
         cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_s, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_pw, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->ev_near, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        delete plan;
+        pdmk_plan_destroy(plan);
         return PDMK_ERR_CUDA;
     }
     const bool mixed = plan->opts.precision == PDMK_MIXED;
@@ -522,6 +533,11 @@ extern "C" void pdmk_plan_destroy(pdmk_plan plan) {
     for (auto e : plan->ev) cudaEventDestroy(e);
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    if (plan->ev_s) cudaEventDestroy(plan->ev_s);
+    if (plan->ev_pw) cudaEventDestroy(plan->ev_pw);
+    if (plan->ev_near) cudaEventDestroy(plan->ev_near);
+    if (plan->ws_pw) cudaStreamDestroy(plan->ws_pw);
+    if (plan->ws_near) cudaStreamDestroy(plan->ws_near);
     if (plan->ws) cudaStreamDestroy(plan->ws);
     delete plan;
 }
@@ -907,6 +923,15 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     plan->ev.clear();
     plan->stage_names.clear();
     if ((r = stage_mark(plan, "start"))) return r;
+    // Three independent branches until assembly: far field on ws, plane-wave passes on
+    // ws_pw, near-field sum on ws_near (one stream when profiling per stage).
+    const bool branches = !plan->opts.profile;
+    cudaStream_t s_pw = branches ? plan->ws_pw : s, s_near = branches ? plan->ws_near : s;
+    if (branches) {
+        CK(cudaEventRecord(plan->ev_s, s));
+        CK(cudaStreamWaitEvent(s_pw, plan->ev_s, 0));
+        CK(cudaStreamWaitEvent(s_near, plan->ev_s, 0));
+    }
     // ---- far field: spread, fold, FFT, scale, inverse FFT, interpolate ----
     const T hwi2 = T(4.0 / (double(plan->w) * plan->w));
     void* slab = plan->slab_override ? plan->slab_override : plan->d_slab;
@@ -1024,7 +1049,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     // ---- near field: plane-wave passes, then the direct residual sum ----
     static const char* pw_names[5] = {"pw_upward", "pw_out", "pw_translate_in", "pw_downward", "pw_leaf_eval"};
     for (int ph = 0; ph < 5; ++ph) {
-        r = pw_eval(&plan->pw, s, ph);
+        r = pw_eval(&plan->pw, s_pw, ph);
         if (r != PDMK_OK) return r;
         if ((r = stage_mark(plan, pw_names[ph]))) return r;
     }
@@ -1051,7 +1076,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         na.tgt_lo = static_cast<const T*>(plan->d_tgt_lo);
         na.close_s = T(0.04);  // r < 0.2 h
         if (plan->count_pending) {
-            CK(cudaMemsetAsync(plan->d_count, 0, sizeof(unsigned long long), s));
+            CK(cudaMemsetAsync(plan->d_count, 0, sizeof(unsigned long long), s_near));
             na.count_in = plan->d_count;
         }
         na.ent = plan->d_ent;
@@ -1061,24 +1086,30 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         na.monoB = static_cast<const T*>(plan->d_monoB);
         const int nc = std::max(na.nA, na.nB);
         const int wb = (plan->ntleaf + kNearWarps - 1) / kNearWarps, wt = 32 * kNearWarps;
-        if (plan->near_nh == 8) k_near_warp<T, D, 8><<<wb, wt, 0, s>>>(na);
-        else if (plan->near_nh == 10) k_near_warp<T, D, 10><<<wb, wt, 0, s>>>(na);
-        else if (plan->near_nh == 12) k_near_warp<T, D, 12><<<wb, wt, 0, s>>>(na);
-        else if (plan->near_nh == 14) k_near_warp<T, D, 14><<<wb, wt, 0, s>>>(na);
-        else if (plan->near_nh == 16) k_near_warp<T, D, 16><<<wb, wt, 0, s>>>(na);
-        else if (plan->near_nh == 20) k_near_warp<T, D, 20><<<wb, wt, 0, s>>>(na);
-        else if (plan->near_nh == 24) k_near_warp<T, D, 24><<<wb, wt, 0, s>>>(na);
-        else if (nc <= 8) k_nearfield<T, D, 8><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
-        else if (nc <= 12) k_nearfield<T, D, 12><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
-        else if (nc <= 16) k_nearfield<T, D, 16><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
-        else if (nc <= 20) k_nearfield<T, D, 20><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
-        else if (nc <= 24) k_nearfield<T, D, 24><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
-        else if (nc <= 32) k_nearfield<T, D, 32><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
-        else k_nearfield<T, D, 40><<<plan->ntleaf, kNearThreads, 0, s>>>(na);
+        if (plan->near_nh == 8) k_near_warp<T, D, 8><<<wb, wt, 0, s_near>>>(na);
+        else if (plan->near_nh == 10) k_near_warp<T, D, 10><<<wb, wt, 0, s_near>>>(na);
+        else if (plan->near_nh == 12) k_near_warp<T, D, 12><<<wb, wt, 0, s_near>>>(na);
+        else if (plan->near_nh == 14) k_near_warp<T, D, 14><<<wb, wt, 0, s_near>>>(na);
+        else if (plan->near_nh == 16) k_near_warp<T, D, 16><<<wb, wt, 0, s_near>>>(na);
+        else if (plan->near_nh == 20) k_near_warp<T, D, 20><<<wb, wt, 0, s_near>>>(na);
+        else if (plan->near_nh == 24) k_near_warp<T, D, 24><<<wb, wt, 0, s_near>>>(na);
+        else if (nc <= 8) k_nearfield<T, D, 8><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 12) k_nearfield<T, D, 12><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 16) k_nearfield<T, D, 16><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 20) k_nearfield<T, D, 20><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 24) k_nearfield<T, D, 24><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 32) k_nearfield<T, D, 32><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
+        else k_nearfield<T, D, 40><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
         ++plan->launches;
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "nearfield"))) return r;
+    if (branches) {
+        CK(cudaEventRecord(plan->ev_pw, s_pw));
+        CK(cudaEventRecord(plan->ev_near, s_near));
+        CK(cudaStreamWaitEvent(s, plan->ev_pw, 0));
+        CK(cudaStreamWaitEvent(s, plan->ev_near, 0));
+    }
     // ---- assembly ----
     {
         AssembleArgs aa;

@@ -1545,6 +1545,8 @@ void pw_free_sources(PwPlan* pw) {
         I->d_leafq = nullptr; I->d_merge = nullptr; I->d_outl = nullptr; I->d_inl = nullptr;
         I->d_down = nullptr; I->d_eval = nullptr; I->d_Q = I->d_out = I->d_L = nullptr;
         I->nleafq = I->nout = I->nin = I->neval = 0;
+        I->d_ditems = nullptr; I->d_src_leaf = nullptr; I->d_bcoord = nullptr; I->d_part = nullptr;
+        I->nditems = 0;
     }
 }
 
