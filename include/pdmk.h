@@ -73,6 +73,10 @@ typedef struct {
     int neutrality; /* 0: require |sum q| <= 1e-12 sum|q|; 1: allow (zero-mean potential)     */
     int profile;    /* 1: record per-stage CUDA-event times (pdmk_stage_times)               */
     void* stream;   /* cudaStream_t for all work; NULL: the legacy default stream            */
+    int wait_test;  /* test hook, 0 in normal use.  1: the first dependent item of the
+                       single-launch downward pass waits on a flag that nothing sets, so its
+                       bounded wait (about 1 s) expires and the evaluation reports
+                       PDMK_ERR_TIMEOUT (2D compile-time orders only; no effect elsewhere) */
 } pdmk_opts;
 
 /* Fills *opts with the defaults (all fields "auto", FP64, neutrality allowed). */
@@ -107,6 +111,10 @@ int pdmk_set_charges(pdmk_plan plan, const double* q, int where);
  * (grad, n x d row-major) at every source, self term excluded (Algorithm 1 steps 3-5):
  * near-field DMK, far-field five-step procedure, assembly and self-correction.
  * Outputs are in the caller's source order and frame.  Errors: NOT_READY, CUDA, TIMEOUT.
+ * TIMEOUT: a bounded wait of the single-launch downward pass (2D, compile-time orders)
+ * expired; the kernel skipped the remaining work and the outputs are invalid, the CUDA
+ * context stays usable.  A host evaluation reports it on return; a device evaluation does
+ * not synchronise, so its timeout is reported by the next pdmk_eval of the plan.
  */
 int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where);
 

@@ -193,6 +193,7 @@ extern "C" void pdmk_default_opts(pdmk_opts* o) {
     o->neutrality = 1;
     o->profile = 0;
     o->stream = nullptr;
+    o->wait_test = 0;
 }
 
 extern "C" const char* pdmk_strerror(int code) {
@@ -450,6 +451,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     if (int(plan->cWd.size()) > kMaxCheb) plan->cWd.resize(kMaxCheb);
     // plane-wave planning (proxy order, plane-wave counts, 1D operators)
     pw_plan_create(&plan->pw, d, eps, plan->c, plan->kt, plan->opts.n_proxy, plan->opts.n_pw, mixed);
+    plan->pw.wait_test = plan->opts.wait_test;
     // device: coefficient arrays, far weights, grid, spectrum, FFT plans
     const size_t ts = tsize(plan);
     int r;
@@ -1155,6 +1157,11 @@ extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
     double* dp = where == PDMK_DEVICE ? pot : plan->d_pot_out;
     double* dg = grad ? (where == PDMK_DEVICE ? grad : plan->d_grad_out) : nullptr;
     int r;
+    // a bounded device wait of an earlier (device) evaluation expired
+    if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+        *plan->pw.h_err = 0;
+        return PDMK_ERR_TIMEOUT;
+    }
     // the work runs on the plan's stream, ordered after the caller's stream
     CK(cudaEventRecord(plan->ev_fork, plan->stream));
     CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
@@ -1191,6 +1198,10 @@ extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
         if (grad)
             CK(cudaMemcpyAsync(grad, dg, size_t(plan->n) * plan->d * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
         CK(cudaStreamSynchronize(plan->ws));
+        if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+            *plan->pw.h_err = 0;
+            return PDMK_ERR_TIMEOUT;
+        }
     }
     CK(cudaEventRecord(plan->ev_join, plan->ws));
     CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
@@ -1260,6 +1271,10 @@ std::mutex g_noalloc_mu;
 extern "C" int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad) {
     if (!plan || !pot) return PDMK_ERR_BAD_ARG;
     if (!plan->ready) return PDMK_ERR_NOT_READY;
+    if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+        *plan->pw.h_err = 0;
+        return PDMK_ERR_TIMEOUT;
+    }
     const size_t need = slab_bytes(plan);
     if (need > kNoAllocScratchBytes) {
         plan_set_msg(plan, "spreading scratch exceeds the 16 MiB static array");

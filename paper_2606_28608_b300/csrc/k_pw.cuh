@@ -27,6 +27,9 @@ struct PwPlan {
     double* d_grad = nullptr;  // d per sorted target
     const void* d_src4 = nullptr;  // borrowed from the plan (sorted sources, leaf-relative)
     const void* d_tgt4 = nullptr;  // borrowed (sorted targets, leaf-relative)
+    int* h_err = nullptr;   // host-mapped flag: a bounded device wait expired (sticky)
+    int* d_err = nullptr;   // its device address
+    int wait_test = 0;      // test hook: make the first dependent downward item wait forever
     std::vector<void*> allocs;
     void* impl = nullptr;
 };

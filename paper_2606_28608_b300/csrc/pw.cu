@@ -959,75 +959,231 @@ __global__ void __launch_bounds__(128) k_pw_in2d_p(const int* __restrict__ list,
                 ae = fma(w * ce[k0][j], v.x, ae);
                 ao = fma(w * so[k0][j], v.y, ao);
             }
-            a[(2 * j) * P + m1] += ae;
-            a[(2 * j + 1) * P + m1] += ao;
+            a[(2 * j) * P + m1] = ae;  // each in-box has one entry: written, not added
+            a[(2 * j + 1) * P + m1] = ao;
         }
     }
 }
 
-// leaf evaluation: the leaf's coefficients in shared memory, T_m / T'_m of the second
-// coordinate in registers, the first coordinate's by recurrence inside the contraction
+// ------------------------------------------------------------------ single-launch downward pass
+// The per-level downward launches are replaced (2D compile-time orders) by one kernel whose
+// blocks take the down items in top-down order from an atomic counter.  An item (parent P,
+// its four children) needs P's coefficients complete, i.e. the item that wrote P finished;
+// that item has a smaller index, so it was taken earlier by a running block, which never
+// waits on a later item: the wait always ends.  It is still bounded (about 1 s of
+// %globaltimer); on expiry the block raises the host-visible error flag and skips, and every
+// later waiter sees the flag and skips at once.  Children that are target leaves are
+// evaluated by the same block right after their coefficients are formed (shared memory),
+// so the leaf coefficients never go back to global memory.
+struct DownItem {
+    int parent;  // local slot of the parent
+    int wait;    // item whose completion makes the parent's coefficients final, or -1
+    int level;   // level of the children
+    int pad;
+    int child[4];  // local slots (-1: no child with targets)
+    int tb[4];     // child that is a target leaf: first sorted target
+    int tc[4];     //   and its target count (0: not a target leaf)
+};
+
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(int* p, int v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <typename T, int P>
-__global__ void __launch_bounds__(32) k_leaf_eval2d_p(const int4* __restrict__ list, const T* __restrict__ Lc,
-                                                      const T* __restrict__ tgt4, double* __restrict__ pot,
-                                                      double* __restrict__ grad, double inv_rc) {
-    __shared__ T a[P * P];
-    const int4 e = list[blockIdx.x];
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) a[i] = Lc[size_t(e.x) * (P * P) + i];
-    __syncthreads();
-    const double sc = 2.0 * inv_rc * double(1LL << e.w);
-    for (int t0i = 0; t0i < e.z; t0i += blockDim.x) {
-        const int ti = t0i + threadIdx.x;
-        if (ti >= e.z) break;
-        const T* x = tgt4 + size_t(e.y + ti) * 4;
-        const T t0 = T(double(x[0]) * sc), t1 = T(double(x[1]) * sc);
-        T b1[P], d1[P];
-        {
-            T tm1 = T(1), tm = t1, um1 = T(1), um = T(2) * t1;
-            b1[0] = T(1);
-            d1[0] = T(0);
-            if (P > 1) { b1[1] = t1; d1[1] = T(1); }
+__global__ void __launch_bounds__(256) k_down_persist2d(const DownItem* __restrict__ items, int nitems,
+                                                        int* __restrict__ counter, int* __restrict__ flags, int* err,
+                                                        int* __restrict__ err_dev,
+                                                        T* __restrict__ Lc, const T* __restrict__ Sg,
+                                                        const T* __restrict__ tgt4, double* __restrict__ pot,
+                                                        double* __restrict__ grad, double inv_rc,
+                                                        unsigned long long limit_ns) {
+    constexpr int PP = P * P, G = (P + 3) / 4, R = P / 4;
+    static_assert(P % 4 == 0, "rows are split four ways");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Sm = reinterpret_cast<T*>(smraw);  // S[b][M][m]   [2 PP]
+    T* ap = Sm + 2 * PP;                  // parent       [PP]
+    T* U = ap + PP;                       // U_b1[M0][m1] [2 PP]
+    T* Lch = U + 2 * PP;                  // children     [4 PP]
+    __shared__ DownItem s_it;
+    __shared__ int s_item, s_ok;
+    for (int i = threadIdx.x; i < 2 * PP; i += blockDim.x) Sm[i] = Sg[i];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(counter, 1);
+            int ok = 1;
+            if (i < nitems) {
+                s_it = items[i];
+                const int w = s_it.wait;
+                if (w >= 0 && ld_relaxed_gpu(flags + w) == 0) {
+                    // poll with relaxed loads (an L2 round trip each); one fence once seen
+                    const unsigned long long t0 = global_ns();
+                    for (;;) {
+                        // (the device copy of the error flag: host-mapped memory is far too
+                        // slow to poll)
+                        if (ld_relaxed_gpu(err_dev) != 0 || global_ns() - t0 > limit_ns) {
+                            ok = 0;
+                            break;
+                        }
+                        if (ld_relaxed_gpu(flags + w) != 0) break;
+                    }
+                    if (!ok) {
+                        st_relaxed_gpu(err_dev, 1);
+                        *reinterpret_cast<volatile int*>(err) = 1;
+                        __threadfence_system();
+                    }
+                }
+                __threadfence();  // order the flag read before the block's reads of the parent
+            }
+            s_item = i;
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (s_item >= nitems) break;
+        if (!s_ok) continue;
+        // parent coefficients (written by another block: read through L2)
+        const T* src = Lc + size_t(s_it.parent) * PP;
+        for (int i = threadIdx.x; i < PP; i += blockDim.x) ap[i] = __ldcg(src + i);
+        __syncthreads();
+        // U_b1[M0][m1] = sum_M1 S_b1[M1][m1] a_P[M0][M1]   (lanes along m1)
+        for (int it = threadIdx.x; it < 2 * G * P; it += blockDim.x) {
+            const int b1 = it / (G * P), rem = it % (G * P), g = rem / P, m1 = rem % P;
+            T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-            for (int m = 2; m < P; ++m) {
-                const T tn = fma(T(2) * t1, tm, -tm1);
-                b1[m] = tn;
-                d1[m] = T(m) * um;
-                const T un = fma(T(2) * t1, um, -um1);
-                tm1 = tm; tm = tn;
-                um1 = um; um = un;
+            for (int M1 = 0; M1 < P; ++M1) {
+                const T s = Sm[(b1 * P + M1) * P + m1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fma(s, ap[(g * 4 + j) * P + M1], acc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) U[b1 * PP + (g * 4 + j) * P + m1] = acc[j];
+        }
+        __syncthreads();
+        // child (b0, b1): own + sum_M0 S_b0[M0][m0] U_b1[M0][m1]
+        for (int it = threadIdx.x; it < 4 * G * P; it += blockDim.x) {
+            const int c = it / (G * P), rem = it % (G * P), g = rem / P, m1 = rem % P;
+            const int cs = s_it.child[c];
+            if (cs < 0) continue;
+            const int b0 = c & 1, b1 = c >> 1;
+            T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int M0 = 0; M0 < P; ++M0) {
+                const T u = U[b1 * PP + M0 * P + m1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fma(Sm[(b0 * P + M0) * P + g * 4 + j], u, acc[j]);
+            }
+            const bool leaf = s_it.tc[c] > 0;  // a leaf holds no incoming of its own
+            T* dst = Lc + size_t(cs) * PP;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int o = (g * 4 + j) * P + m1;
+                const T v = leaf ? acc[j] : __ldcg(dst + o) + acc[j];
+                Lch[c * PP + o] = v;
+                if (!leaf) dst[o] = v;
             }
         }
-        T phi = 0, g0 = 0, g1 = 0;
-        T c_prev = T(1), c_cur = t0, u_prev = T(1), u_cur = T(2) * t0;  // T_m0, U_{m0-1} recurrences
-#pragma unroll 1
-        for (int m0 = 0; m0 < P; ++m0) {
-            T s = 0, sd = 0;
-#pragma unroll
-            for (int m1 = 0; m1 < P; ++m1) {
-                const T v = a[m0 * P + m1];
-                s = fma(v, b1[m1], s);
-                sd = fma(v, d1[m1], sd);
-            }
-            T tm0, dm0;
-            if (m0 == 0) { tm0 = T(1); dm0 = T(0); }
-            else if (m0 == 1) { tm0 = t0; dm0 = T(1); }
-            else {
-                const T tn = fma(T(2) * t0, c_cur, -c_prev);
-                c_prev = c_cur; c_cur = tn;
-                tm0 = tn;
-                dm0 = T(m0) * u_cur;
-                const T un = fma(T(2) * t0, u_cur, -u_prev);
-                u_prev = u_cur; u_cur = un;
-            }
-            phi = fma(tm0, s, phi);
-            g0 = fma(dm0, s, g0);
-            g1 = fma(tm0, sd, g1);
+        // the block's stores, then one GPU-scope fence and the flag (the pattern of a grid
+        // barrier: the fence after the block barrier covers every thread's stores)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_relaxed_gpu(flags + s_item, 1);
         }
-        const size_t o = size_t(e.y + ti);
-        pot[o] = double(phi);
-        if (grad) {
-            grad[o * 2 + 0] = double(g0) * sc;
-            grad[o * 2 + 1] = double(g1) * sc;
+        // leaf evaluation: four lanes per target, lane q takes the rows m0 = 4k + q
+        const int tot = s_it.tc[0] + s_it.tc[1] + s_it.tc[2] + s_it.tc[3];
+        const double sc = 2.0 * inv_rc * double(1LL << s_it.level);
+        const int q = threadIdx.x & 3;
+        for (int base = 0; base < tot; base += 64) {
+            const int pi = base + (threadIdx.x >> 2);
+            const bool act = pi < tot;
+            T phi = 0, g0 = 0, g1 = 0;
+            int c = 0, t = pi;
+            if (act) {
+                while (c < 3 && t >= s_it.tc[c]) {
+                    t -= s_it.tc[c];
+                    ++c;
+                }
+                const T* x = tgt4 + size_t(s_it.tb[c] + t) * 4;
+                const T t0 = T(double(x[0]) * sc), t1 = T(double(x[1]) * sc);
+                T b1[P], d1[P];  // T_m(t1), T'_m(t1)
+                {
+                    T tm1 = T(1), tm = t1, um1 = T(1), um = T(2) * t1;
+                    b1[0] = T(1);
+                    d1[0] = T(0);
+                    b1[1] = t1;
+                    d1[1] = T(1);
+#pragma unroll
+                    for (int m = 2; m < P; ++m) {
+                        const T tn = fma(T(2) * t1, tm, -tm1);
+                        b1[m] = tn;
+                        d1[m] = T(m) * um;
+                        const T un = fma(T(2) * t1, um, -um1);
+                        tm1 = tm;
+                        tm = tn;
+                        um1 = um;
+                        um = un;
+                    }
+                }
+                // T_m(t0), T'_m(t0) for m < 8, then the stride-4 recurrence
+                // T_{m+4} = 2 T_4 T_m - T_{m-4},  T'_{m+4} = 2 T'_4 T_m + 2 T_4 T'_m - T'_{m-4}
+                T tv[8], dv[8];
+                tv[0] = T(1); dv[0] = T(0);
+                tv[1] = t0; dv[1] = T(1);
+#pragma unroll
+                for (int m = 2; m < 8; ++m) {
+                    tv[m] = fma(T(2) * t0, tv[m - 1], -tv[m - 2]);
+                    dv[m] = fma(T(2) * t0, dv[m - 1], fma(T(2), tv[m - 1], -dv[m - 2]));
+                }
+                T A = q == 0 ? tv[0] : q == 1 ? tv[1] : q == 2 ? tv[2] : tv[3];
+                T Am = q == 0 ? tv[4] : q == 1 ? tv[3] : q == 2 ? tv[2] : tv[1];
+                T Dd = q == 0 ? dv[0] : q == 1 ? dv[1] : q == 2 ? dv[2] : dv[3];
+                T Dm = q == 0 ? dv[4] : q == 1 ? dv[3] : q == 2 ? dv[2] : dv[1];  // T_{q-4} = T_{4-q}
+                const T T4 = tv[4], D4 = dv[4];
+                const T* a = Lch + c * PP + q * P;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    T s = 0, sd = 0;
+#pragma unroll
+                    for (int m1 = 0; m1 < P; ++m1) {
+                        const T v = a[k * 4 * P + m1];
+                        s = fma(v, b1[m1], s);
+                        sd = fma(v, d1[m1], sd);
+                    }
+                    phi = fma(A, s, phi);
+                    g0 = fma(Dd, s, g0);
+                    g1 = fma(A, sd, g1);
+                    const T An = fma(T(2) * T4, A, -Am);
+                    const T Dn = fma(T(2) * D4, A, fma(T(2) * T4, Dd, -Dm));
+                    Am = A;
+                    A = An;
+                    Dm = Dd;
+                    Dd = Dn;
+                }
+            }
+            phi += __shfl_xor_sync(0xffffffffu, phi, 1);
+            g0 += __shfl_xor_sync(0xffffffffu, g0, 1);
+            g1 += __shfl_xor_sync(0xffffffffu, g1, 1);
+            phi += __shfl_xor_sync(0xffffffffu, phi, 2);
+            g0 += __shfl_xor_sync(0xffffffffu, g0, 2);
+            g1 += __shfl_xor_sync(0xffffffffu, g1, 2);
+            if (act && q == 0) {
+                const size_t o = size_t(s_it.tb[c] + t);
+                pot[o] = double(phi);
+                if (grad) {
+                    grad[o * 2 + 0] = double(g0) * sc;
+                    grad[o * 2 + 1] = double(g1) * sc;
+                }
+            }
         }
     }
 }
@@ -1063,6 +1219,11 @@ struct PwImpl {
     int* d_src_leaf = nullptr;  // leaf box of every sorted source
     int4* d_bcoord = nullptr;   // (i0, i1, level, 0) per box
     void* d_part = nullptr;     // partial moments [nditems][p p]
+    // single-launch downward pass with folded leaf evaluation (2D compile-time orders)
+    DownItem* d_down_items = nullptr;
+    int ndown_items = 0;
+    int* d_down_flags = nullptr;  // [ndown_items] done flags, [+0] never set, [+1] item counter,
+                                  // [+2] device copy of the error flag
     // arrays
     void* d_Q = nullptr;
     void* d_out = nullptr;
@@ -1325,6 +1486,42 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     }
     I->down_start[t.nlevels] = int(down.size()) / (1 + nc);
     pw->down_parents = I->down_start[t.nlevels];
+    // single-launch downward items (top-down order: the down list is by parent level)
+    std::vector<DownItem> ditems_down;
+    if (I->direct2d) {
+        std::vector<int> box_of_lslot(nloc, -1), writer(nloc, -1);
+        for (int b = 0; b < nb; ++b)
+            if (lslot[b] >= 0) box_of_lslot[lslot[b]] = b;
+        const int ne = I->down_start[t.nlevels];
+        ditems_down.resize(ne);
+        for (int i = 0; i < ne; ++i) {
+            const int* e = &down[size_t(i) * (1 + nc)];
+            DownItem& it = ditems_down[i];
+            it.parent = e[0];
+            it.wait = writer[e[0]];
+            it.level = t.level[box_of_lslot[e[0]]] + 1;
+            it.pad = 0;
+            for (int c = 0; c < 4; ++c) {
+                it.child[c] = e[1 + c];
+                it.tb[c] = 0;
+                it.tc[c] = 0;
+                if (e[1 + c] < 0) continue;
+                writer[e[1 + c]] = i;
+                const int cb = box_of_lslot[e[1 + c]];
+                if (t.is_leaf(cb) && has_tgt(cb) && t.level[cb] >= 1) {
+                    it.tb[c] = int(t.tgt_begin[cb]);
+                    it.tc[c] = int(t.tgt_end[cb] - t.tgt_begin[cb]);
+                }
+            }
+        }
+        if (pw->wait_test)  // test hook: the first dependent item waits on the never-set flag
+            for (DownItem& it : ditems_down)
+                if (it.wait >= 0) {
+                    it.wait = ne;
+                    break;
+                }
+        I->ndown_items = ne;
+    }
     // leaf evaluation: target leaves below the root level
     std::vector<int4> ev;
     for (int b = 0; b < nb; ++b)
@@ -1355,6 +1552,16 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     if ((r = pw_upload(pw, &I->d_eval, ev, stream))) return r;
     unsigned char* p = nullptr;
     if (I->direct2d) {
+        if (!pw->h_err) {
+            if (cudaHostAlloc(reinterpret_cast<void**>(&pw->h_err), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+                cudaHostGetDevicePointer(reinterpret_cast<void**>(&pw->d_err), pw->h_err, 0) != cudaSuccess) {
+                cudaGetLastError();
+                return PDMK_ERR_CUDA;
+            }
+            *pw->h_err = 0;
+        }
+        if ((r = pw_upload(pw, &I->d_down_items, ditems_down, stream))) return r;
+        if ((r = pw_alloc(pw, &I->d_down_flags, size_t(I->ndown_items) + 3))) return r;
         if ((r = pw_upload(pw, &I->d_ditems, ditems, stream))) return r;
         if ((r = pw_upload(pw, &I->d_src_leaf, src_leaf, stream))) return r;
         if ((r = pw_upload(pw, &I->d_bcoord, bcoord, stream))) return r;
@@ -1382,9 +1589,14 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     const PwDims pd = I->dims;
     const size_t ts = sizeof(T);
     const double inv_rc = 1.0 / I->rc;
+    // compile-time 2D orders: direct moments, incoming written (not added) per in-box, and the
+    // single-launch downward pass; no per-box moment or local arrays to clear
+    const bool fixed2d = D == 2 && I->direct2d;
     if (phase == 0) {
+    if (!fixed2d) {
     if (cudaMemsetAsync(I->d_Q, 0, size_t(std::max<int64_t>(I->nq, 1)) * pd.np * ts, s) != cudaSuccess) return PDMK_ERR_CUDA;
     if (cudaMemsetAsync(I->d_L, 0, size_t(std::max<int64_t>(I->nloc, 1)) * pd.np * ts, s) != cudaSuccess) return PDMK_ERR_CUDA;
+    }
     if (cudaMemsetAsync(pw->d_pot, 0, size_t(std::max<int64_t>(I->ntgt, 1)) * sizeof(double), s) != cudaSuccess) return PDMK_ERR_CUDA;
     if (cudaMemsetAsync(pw->d_grad, 0, size_t(std::max<int64_t>(I->ntgt, 1)) * D * sizeof(double), s) != cudaSuccess) return PDMK_ERR_CUDA;
     }
@@ -1396,9 +1608,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     const size_t sm_re = ts * (2 * pd.p * pd.p + pd.pd1 + pd.p * pd.p);
     const size_t sm_m2 = ts * 10 * pd.p * pd.p;
     const size_t sm_d2 = ts * 5 * pd.p * pd.p;
-    // 1. leaf moments
-    // (FP64 at P = 32 would need more than 48 KB of static shared memory: generic kernels)
-    const bool fixed2d = D == 2 && I->direct2d;
+    // 1. moments
     if (phase == 0 && fixed2d && I->nditems > 0) {
         const T* s4 = static_cast<const T*>(pw->d_src4);
         T* part = static_cast<T*>(I->d_part);
@@ -1486,8 +1696,31 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                                               static_cast<const T*>(I->d_f), pd, KC, inv_rc);
         ++pw->launches;
     }
-    // 5. downward, root first (by parent level)
-    for (int l = 0; phase == 3 && l + 1 < I->nlevels; ++l) {
+    // 5. downward, root first (by parent level); the compile-time 2D orders in one launch
+    //    that also evaluates the target leaves
+    if (phase == 3 && fixed2d && I->ndown_items > 0) {
+        if (cudaMemsetAsync(I->d_down_flags, 0, (size_t(I->ndown_items) + 3) * sizeof(int), s) != cudaSuccess)
+            return PDMK_ERR_CUDA;
+        const T* t4 = static_cast<const T*>(pw->d_tgt4);
+        int* counter = I->d_down_flags + I->ndown_items + 1;
+        int* err_dev = I->d_down_flags + I->ndown_items + 2;
+        auto persist = [&](auto kern, int P) {
+            const size_t smb = ts * 9 * P * P;
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+            int per_sm = 0, nsm = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smb);
+            const int grid = std::max(1, std::min(I->ndown_items, std::max(1, per_sm) * nsm));
+            kern<<<grid, 256, smb, s>>>(I->d_down_items, I->ndown_items, counter, I->d_down_flags, pw->d_err, err_dev, L, S,
+                                        t4, pw->d_pot, pw->d_grad, inv_rc, 1000000000ull);
+        };
+        if (pd.p == 16) persist(k_down_persist2d<T, 16>, 16);
+        else if (pd.p == 24) persist(k_down_persist2d<T, 24>, 24);
+        else persist(k_down_persist2d<T, 32>, 32);
+        ++pw->launches;
+    }
+    for (int l = 0; phase == 3 && !fixed2d && l + 1 < I->nlevels; ++l) {
         const int b = I->down_start[l], e = I->down_start[l + 1];
         if (e > b) {
             const int* lst = I->d_down + size_t(b) * (1 + (1 << D));
@@ -1507,14 +1740,8 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
             ++pw->launches;
         }
     }
-    // 6. leaf evaluation
-    if (phase == 4 && I->neval > 0 && fixed2d) {
-        const T* t4 = static_cast<const T*>(pw->d_tgt4);
-        if (pd.p == 16) k_leaf_eval2d_p<T, 16><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
-        else if (pd.p == 24) k_leaf_eval2d_p<T, 24><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
-        else k_leaf_eval2d_p<T, 32><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
-        ++pw->launches;
-    } else if (phase == 4 && I->neval > 0) {
+    // 6. leaf evaluation (folded into the downward launch for the compile-time 2D orders)
+    if (phase == 4 && I->neval > 0 && !fixed2d) {
         size_t sm = ts * 32 * 2 * D * pd.p;
         cudaFuncSetAttribute(k_leaf_eval<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_leaf_eval<T, D><<<I->neval, 32, sm, s>>>(I->d_eval, L, static_cast<const T*>(pw->d_tgt4), pw->d_pot,
@@ -1547,11 +1774,15 @@ void pw_free_sources(PwPlan* pw) {
         I->nleafq = I->nout = I->nin = I->neval = 0;
         I->d_ditems = nullptr; I->d_src_leaf = nullptr; I->d_bcoord = nullptr; I->d_part = nullptr;
         I->nditems = 0;
+        I->d_down_items = nullptr; I->d_down_flags = nullptr;
+        I->ndown_items = 0;
     }
 }
 
 void pw_free(PwPlan* pw) {
     pw_free_sources(pw);
+    if (pw->h_err) cudaFreeHost(pw->h_err);
+    pw->h_err = pw->d_err = nullptr;
     delete impl(pw);
     pw->impl = nullptr;
 }
