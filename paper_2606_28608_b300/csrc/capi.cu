@@ -53,6 +53,8 @@ struct pdmk_plan_s {
     std::vector<double> cA, cB, cW, cWd;  // near-field Chebyshev coefficients (FP64 master copy)
     std::vector<double> mA, mB;  // A and B as monomials in x = 2 s - 1 (warp near-field kernel)
     int near_nh = 0;             // > 0: warp near-field kernel with this many monomial terms
+    std::vector<double> mW, mWd; // window F, dF as monomials in x = 2 s - 1
+    bool far_halo = false;       // 2D FP32 halo-grid spreading / interpolation kernels
     int B[3] = {1, 1, 1}, nbin[3] = {1, 1, 1}, P[3] = {1, 1, 1}, Ptot = 1;
     int whole_ctas = 0;  // > 0: 2D whole-grid spreading with this many CTAs (small grids)
     int64_t ncell = 1, nhalf = 1;
@@ -77,6 +79,8 @@ struct pdmk_plan_s {
     void* d_coefWd = nullptr;
     void* d_monoA = nullptr;
     void* d_monoB = nullptr;
+    void* d_monoW = nullptr;
+    void* d_monoWd = nullptr;
     double* d_weight = nullptr;
     void* d_grid = nullptr;
     void* d_spec = nullptr;
@@ -449,6 +453,17 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     plan->cWd = plan->wt.dF.coef;
     if (int(plan->cW.size()) > kMaxCheb) plan->cW.resize(kMaxCheb);
     if (int(plan->cWd.size()) > kMaxCheb) plan->cWd.resize(kMaxCheb);
+    {
+        // 2D FP32 far field with halo grids: compiled window widths, Horner as accurate as
+        // Clenshaw, the halo no longer than the grid, per-warp halo copies fitting two CTAs
+        // per SM
+        const double ampW = cheb_to_mono(plan->cW, &plan->mW), ampWd = cheb_to_mono(plan->cWd, &plan->mWd);
+        const int nh = plan->w == 8 ? 12 : plan->w == 13 ? 16 : plan->w == 17 ? 20 : 0;
+        const int64_t Mp0 = plan->g.M[0] + plan->w - 1, Mp1 = plan->g.M[1] + plan->w - 1;
+        plan->far_halo = d == 2 && mixed && nh > 0 && int(plan->cW.size()) <= nh && int(plan->cWd.size()) <= nh &&
+                         ampW <= 4.0 && ampWd <= 4.0 && plan->w - 1 <= std::min(plan->g.M[0], plan->g.M[1]) &&
+                         (8 * Mp0 * Mp1 + 16 * plan->w) * 4 <= 112 * 1024;
+    }
     // plane-wave planning (proxy order, plane-wave counts, 1D operators)
     pw_plan_create(&plan->pw, d, eps, plan->c, plan->kt, plan->opts.n_proxy, plan->opts.n_pw, mixed);
     plan->pw.wait_test = plan->opts.wait_test;
@@ -476,6 +491,8 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
         PCHECK(coef_upload(plan->cWd, &plan->d_coefWd));
         PCHECK(coef_upload(plan->mA, &plan->d_monoA));
         PCHECK(coef_upload(plan->mB, &plan->d_monoB));
+        PCHECK(coef_upload(plan->mW, &plan->d_monoW));
+        PCHECK(coef_upload(plan->mWd, &plan->d_monoWd));
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_weight, size_t(plan->nhalf)));
         std::vector<double> wt = far_weights(plan);
         PCHECK(upload(plan, plan->d_weight, wt));
@@ -803,6 +820,8 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
             grid_coord(u[j * d + i], i, &gg[i], &del);
             put(t_dq, size_t(t) * 4 + i, del);
         }
+        // window starts wrapped into [0, M_i) (the kernels index periodically from there)
+        for (int i = 0; i < d; ++i) gg[i] = ((gg[i] % g.M[i]) + g.M[i]) % g.M[i];
         t_g0[t] = make_int4(gg[0], gg[1], gg[2], 0);
     }
     // ---- device allocations and uploads ----
@@ -937,7 +956,27 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     // ---- far field: spread, fold, FFT, scale, inverse FFT, interpolate ----
     const T hwi2 = T(4.0 / (double(plan->w) * plan->w));
     void* slab = plan->slab_override ? plan->slab_override : plan->d_slab;
-    if (D == 2 && plan->whole_ctas > 0) {
+    if (D == 2 && plan->whole_ctas > 0 && plan->far_halo && sizeof(T) == 4) {
+        const int nwarp = 8;
+        const int Mp0 = g.M[0] + plan->w - 1, Mp1 = g.M[1] + plan->w - 1;
+        const size_t smem = sizeof(T) * (size_t(nwarp) * Mp0 * Mp1 + size_t(nwarp) * 2 * plan->w);
+        auto halo = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            kern<<<plan->whole_ctas, 32 * nwarp, smem, s>>>(
+                plan->d_t_g0, static_cast<const T*>(plan->d_t_dq), static_cast<const T*>(plan->d_tgt4),
+                int(plan->ntgt), static_cast<T*>(slab), g.M[0], g.M[1], hwi2, static_cast<const T*>(plan->d_monoW));
+        };
+        if (plan->w == 8) halo(k_spread_halo<T, 8, 12>);
+        else if (plan->w == 13) halo(k_spread_halo<T, 13, 16>);
+        else halo(k_spread_halo<T, 17, 20>);
+        ++plan->launches;
+        CK(cudaGetLastError());
+        int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 4));
+        k_fold_whole<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<const T*>(slab), plan->whole_ctas,
+                                                            static_cast<T*>(plan->d_grid), int(plan->ncell));
+        ++plan->launches;
+        CK(cudaGetLastError());
+    } else if (D == 2 && plan->whole_ctas > 0) {
         const int nwarp = 8;
         const size_t smem = sizeof(T) * (size_t(nwarp) * plan->ncell + size_t(nwarp) * 2 * plan->w);
         const int nW = int(plan->cW.size());
@@ -1026,7 +1065,28 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         CKFFT(cufftExecZ2D(plan->fft_inv, (cufftDoubleComplex*)plan->d_spec, (cufftDoubleReal*)plan->d_grid));
     }
     if ((r = stage_mark(plan, "fft_inv"))) return r;
-    if (plan->ntgt > 0) {
+    if (plan->ntgt > 0 && D == 2 && plan->far_halo && sizeof(T) == 4) {
+        const int Mp0 = g.M[0] + plan->w - 1, Mp1 = g.M[1] + plan->w - 1;
+        const size_t smem = sizeof(T) * size_t(Mp0) * Mp1;
+        auto interp = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            int per_sm = 0, nsm = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+            const int grid = int(std::max<int64_t>(1, std::min<int64_t>((plan->ntgt + 255) / 256,
+                                                                        int64_t(std::max(1, per_sm)) * nsm)));
+            kern<<<grid, 256, smem, s>>>(static_cast<const T*>(plan->d_grid), plan->d_t_g0,
+                                         static_cast<const T*>(plan->d_t_dq), int(plan->ntgt), g.M[0], g.M[1], hwi2,
+                                         static_cast<const T*>(plan->d_monoW), static_cast<const T*>(plan->d_monoWd),
+                                         plan->d_pot_far, plan->d_gradu_far);
+        };
+        if (plan->w == 8) interp(k_interp_halo<T, 8, 12, 12>);
+        else if (plan->w == 13) interp(k_interp_halo<T, 13, 16, 16>);
+        else interp(k_interp_halo<T, 17, 20, 20>);
+        ++plan->launches;
+        CK(cudaGetLastError());
+    } else if (plan->ntgt > 0) {
         InterpArgs<T> ia;
         ia.grid = static_cast<const T*>(plan->d_grid);
         ia.t_g0 = plan->d_t_g0;

@@ -400,4 +400,160 @@ k_interp(InterpArgs<T> a) {
     if (D == 3) a.gradu[size_t(t) * D + 2] = double(gz);
 }
 
+// ---------------------------------------------------------------------------------------
+// 2D FP32 spreading and interpolation with compile-time window width W and series length NH.
+// The window series F (and dF for the gradient) are Horner sums of monomials in
+// x = 2 s - 1 (the host converts the Chebyshev fits; for these series Horner is as accurate
+// as Clenshaw).  Window starts arrive wrapped into [0, M_i), and the grids carry a halo of
+// W - 1 cells on the high side of each axis, so a window never wraps inside the kernel; the
+// halo folds back onto the periodic grid (spreading) or is filled from it (interpolation).
+// Needs W - 1 <= min(M0, M1).
+template <typename T, int NH>
+__device__ __forceinline__ T horner(const T (&c)[NH], T x) {
+    T r = c[NH - 1];
+#pragma unroll
+    for (int k = NH - 2; k >= 0; --k) r = fma(r, x, c[k]);
+    return r;
+}
+
+// Per-warp private halo grids [nwarp][(M0 + W - 1)(M1 + W - 1)]; a warp takes a contiguous
+// range of points (sorted order) and adds each point's W x W block (lanes over the cells,
+// so one instruction never touches a cell twice).  The block folds the halo and its warps'
+// copies in a fixed order into its slab; k_fold_whole sums the slabs.
+template <typename T, int W, int NH>
+__global__ void __launch_bounds__(256, 2)
+k_spread_halo(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, const T* __restrict__ q4, int n,
+              T* __restrict__ slab, int M0, int M1, T half_w_inv2, const T* __restrict__ monoW) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int WW = W * W, KK = (WW + 31) / 32;
+    const int Mp0 = M0 + W - 1, Mp1 = M1 + W - 1, np = Mp0 * Mp1;
+    const int nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T* grids = reinterpret_cast<T*>(smem_raw);  // [nwarp][np]
+    T* wins = grids + nwarp * np;               // [nwarp][2 W]: x window, q * y window
+    T cw[NH];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) cw[k] = monoW[k];
+    for (int i = threadIdx.x; i < nwarp * np; i += blockDim.x) grids[i] = T(0);
+    __syncthreads();
+    T* g = grids + wp * np;
+    T* wv = wins + wp * 2 * W;
+    int off[KK], fxy[KK];  // cell offset in the halo grid; x | (W + y) << 16 window indices
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+        const int e = lane + 32 * k;
+        const int fy = e < WW ? e / W : 0, fx = e < WW ? e % W : 0;
+        fxy[k] = fx | ((W + fy) << 16);
+        off[k] = e < WW ? fy * Mp0 + fx : -1;
+    }
+    const int gw = blockIdx.x * nwarp + wp, nw = gridDim.x * nwarp;
+    const int per = (n + nw - 1) / nw;
+    const int i0 = min(n, gw * per), i1 = min(n, i0 + per);
+    // points in chunks of 32: one coalesced load per lane, then broadcast point by point
+    for (int c0 = i0; c0 < i1; c0 += 32) {
+        const int ii = c0 + lane;
+        int pb = 0;
+        T pdx = T(0), pdy = T(0), pq = T(0);
+        if (ii < i1) {
+            const int4 g0 = t_g0[ii];
+            pb = g0.y * Mp0 + g0.x;
+            pdx = t_dq[size_t(ii) * 4 + 0];
+            pdy = t_dq[size_t(ii) * 4 + 1];
+            pq = q4[size_t(ii) * 4 + 3];
+        }
+        const int cnt = min(32, i1 - c0);
+        for (int j = 0; j < cnt; ++j) {
+            const int base = __shfl_sync(0xffffffffu, pb, j);
+            const T dx = __shfl_sync(0xffffffffu, pdx, j), dy = __shfl_sync(0xffffffffu, pdy, j);
+            const T q = __shfl_sync(0xffffffffu, pq, j);
+            if (lane < 2 * W) {
+                const bool ky = lane >= W;
+                const T z = (ky ? dy : dx) - T(ky ? lane - W : lane);
+                const T s = z * z * half_w_inv2;
+                const T v = s < T(1) ? horner(cw, fma(T(2), s, T(-1))) : T(0);
+                wv[lane] = ky ? v * q : v;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < KK; ++k)
+                if (off[k] >= 0) g[base + off[k]] += wv[fxy[k] >> 16] * wv[fxy[k] & 0xffff];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    T* out = slab + size_t(blockIdx.x) * (size_t(M0) * M1);
+    for (int y = wp; y < M1; y += nwarp)
+        for (int x = lane; x < M0; x += 32) {
+            const bool hx = x + M0 < Mp0, hy = y + M1 < Mp1;
+            T s = T(0);
+            for (int k = 0; k < nwarp; ++k) {
+                const T* gk = grids + k * np;
+                s += gk[y * Mp0 + x];
+                if (hx) s += gk[y * Mp0 + x + M0];
+                if (hy) {
+                    s += gk[(y + M1) * Mp0 + x];
+                    if (hx) s += gk[(y + M1) * Mp0 + x + M0];
+                }
+            }
+            out[y * M0 + x] = s;
+        }
+}
+
+// Interpolation of the potential and its grid-coordinate gradient: each block copies the
+// periodic grid into a halo grid in shared memory once, then its threads take targets in a
+// grid-stride loop (one target per thread).
+template <typename T, int W, int NH, int NHD>
+__global__ void __launch_bounds__(256, 2)
+k_interp_halo(const T* __restrict__ grid, const int4* __restrict__ t_g0, const T* __restrict__ t_dq, int nt, int M0,
+              int M1, T half_w_inv2, const T* __restrict__ monoW, const T* __restrict__ monoWd,
+              double* __restrict__ pot, double* __restrict__ gradu) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Mp0 = M0 + W - 1, Mp1 = M1 + W - 1;
+    T* gs = reinterpret_cast<T*>(smem_raw);  // [Mp1][Mp0]
+    for (int y = threadIdx.x / 32; y < Mp1; y += blockDim.x / 32) {
+        const int yy = y < M1 ? y : y - M1;
+        for (int x = threadIdx.x & 31; x < Mp0; x += 32) gs[y * Mp0 + x] = grid[yy * M0 + (x < M0 ? x : x - M0)];
+    }
+    T cw[NH], cd[NHD];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) cw[k] = monoW[k];
+#pragma unroll
+    for (int k = 0; k < NHD; ++k) cd[k] = monoWd[k];
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int4 g0 = t_g0[t];
+        const T dx = t_dq[size_t(t) * 4 + 0], dy = t_dq[size_t(t) * 4 + 1];
+        T wx[W], dwx[W], wy[W], dwy[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            // phi(z) = F(2 s - 1), s = z^2 / (w/2)^2;  phi'(z) = dF(2 s - 1) 2 z / (w/2)^2
+            const T zx = dx - T(j), zy = dy - T(j);
+            const T sx = zx * zx * half_w_inv2, sy = zy * zy * half_w_inv2;
+            const bool ix = sx < T(1), iy = sy < T(1);
+            const T xx = fma(T(2), sx, T(-1)), xy = fma(T(2), sy, T(-1));
+            wx[j] = ix ? horner(cw, xx) : T(0);
+            wy[j] = iy ? horner(cw, xy) : T(0);
+            dwx[j] = ix ? horner(cd, xx) * T(2) * zx * half_w_inv2 : T(0);
+            dwy[j] = iy ? horner(cd, xy) * T(2) * zy * half_w_inv2 : T(0);
+        }
+        T p = 0, gx = 0, gy = 0;
+        const T* row = gs + g0.y * Mp0 + g0.x;
+#pragma unroll
+        for (int iy = 0; iy < W; ++iy) {
+            T sx = 0, sdx = 0;
+#pragma unroll
+            for (int ix = 0; ix < W; ++ix) {
+                const T v = row[iy * Mp0 + ix];
+                sx = fma(v, wx[ix], sx);
+                sdx = fma(v, dwx[ix], sdx);
+            }
+            p = fma(sx, wy[iy], p);
+            gx = fma(sdx, wy[iy], gx);
+            gy = fma(sx, dwy[iy], gy);
+        }
+        pot[t] = double(p);
+        gradu[size_t(t) * 2 + 0] = double(gx);
+        gradu[size_t(t) * 2 + 1] = double(gy);
+    }
+}
+
 }  // namespace pdmk

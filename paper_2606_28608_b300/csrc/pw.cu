@@ -720,8 +720,10 @@ __global__ void __launch_bounds__(128) k_moments_direct2d(const int4* __restrict
                                                           const int4* __restrict__ bcoord, T* __restrict__ part,
                                                           double inv_rc) {
     using T2 = typename V2<T>::type;
-    constexpr int TP = P / 4, S = P + 2, NS = 128, PP = P * P;
-    static_assert(P % 8 == 0 && (S / 2) % 2 == 1, "row stride must be an odd number of pairs");
+    // row stride: an odd number of pairs (conflict-free row stores), and rows s, s + 1 (the two
+    // 16-lane groups of a warp) offset by 2 mod 32 words so their tile loads use disjoint banks
+    constexpr int TP = P / 4, S = (P == 24) ? 34 : P + 2, NS = 128, PP = P * P;
+    static_assert(P % 8 == 0 && (S / 2) % 2 == 1, "row stride");
     extern __shared__ __align__(16) unsigned char smraw[];
     T* A = reinterpret_cast<T*>(smraw);  // [NS][S]  q T_m(t0)
     T* B = A + NS * S;                   // [NS][S]  T_m(t1)
@@ -795,7 +797,7 @@ __global__ void __launch_bounds__(128) k_moments_direct2d(const int4* __restrict
     }
 }
 
-// Outgoing plane waves from the summed partial moments, persistent over boxes.  The
+// Outgoing plane waves from the summed partial moments, one block per box.  The
 // Chebyshev coefficients of exp(-i a t) are real for even m (the cosine) and imaginary for
 // odd m (the sine), even and odd in k respectively:
 //   Co[k][2j] = ce[|k|][j],  Co[k][2j+1] = i sgn(k) so[|k|][j].
@@ -820,7 +822,9 @@ __global__ void __launch_bounds__(128) k_pw_out2d_p(const int2* __restrict__ lis
         ceT[j][k] = e;
         soT[j][k] = o;
     }
-    for (int b = blockIdx.x; b < nbox; b += gridDim.x) {
+    {
+        const int b = blockIdx.x;  // one block per box: resident blocks overlap their loads
+        if (b >= nbox) return;
         const int2 e = list[b];
         __syncthreads();
         for (int i = threadIdx.x; i < PP; i += blockDim.x) {
@@ -861,7 +865,7 @@ __global__ void __launch_bounds__(128) k_pw_out2d_p(const int2* __restrict__ lis
     }
 }
 
-// translation + incoming, persistent over boxes (list entry: local slot, level, 9 out slots).
+// translation + incoming, one block per box (list entry: local slot, level, 9 out slots).
 // Stage 1 sums the colleagues' outgoing waves with the translation phases for the pair of
 // modes (k0, +-k1) at once.  The phases factor by dimension, exp(-i (2 pi/3) k.delta) =
 // v^delta0 u^delta1 with u = exp(-i (2 pi/3) k1), v = exp(-i (2 pi/3) k0), and for
@@ -888,7 +892,9 @@ __global__ void __launch_bounds__(128) k_pw_in2d_p(const int* __restrict__ list,
     }
     for (int i = threadIdx.x; i < KH; i += blockDim.x) u[i] = phg[2 * N1 + K + i];  // delta = +1
     const T wlev = T(1.0 / 9.0);
-    for (int b = blockIdx.x; b < nbox; b += gridDim.x) {
+    {
+        const int b = blockIdx.x;  // one block per box
+        if (b >= nbox) return;
         const int* e = list + size_t(b) * 11;
         __syncthreads();
         if (threadIdx.x < 9) coll[threadIdx.x] = e[2 + threadIdx.x];
@@ -1613,7 +1619,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         const T* s4 = static_cast<const T*>(pw->d_src4);
         T* part = static_cast<T*>(I->d_part);
         auto direct = [&](auto kern, int P) {
-            const size_t smb = ts * std::max(2 * 128 * (P + 2), 8 * P * P);
+            const size_t smb = ts * std::max(2 * 128 * (P == 24 ? 34 : P + 2), 8 * P * P);
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
             kern<<<I->nditems, 128, smb, s>>>(I->d_ditems, s4, I->d_src_leaf, I->d_bcoord, part, inv_rc);
         };
@@ -1664,9 +1670,8 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         }
     }
     // 3. outgoing plane waves (all levels)
-    const int pgrid = 148 * 8;
     if (phase == 1 && I->nout > 0 && fixed2d) {
-        const int g = std::min(I->nout, pgrid);
+        const int g = I->nout;  // one block per box
         const T* part = static_cast<const T*>(I->d_part);
         if (pd.p == 16) k_pw_out2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_outl, I->nout, part, out, Co);
         else if (pd.p == 24) k_pw_out2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_outl, I->nout, part, out, Co);
@@ -1680,7 +1685,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     }
     // 4. translation + incoming (all levels)
     if (phase == 2 && I->nin > 0 && fixed2d) {
-        const int g = std::min(I->nin, pgrid);
+        const int g = I->nin;  // one block per box
         const C2<T>* ph = static_cast<const C2<T>*>(I->d_ph);
         const T* fk = static_cast<const T*>(I->d_f);
         if (pd.p == 16) k_pw_in2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
