@@ -1006,7 +1006,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 template <typename T, int P>
-__global__ void __launch_bounds__(256) k_down_persist2d(const DownItem* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_down_persist2d(const DownItem* __restrict__ items, int nitems,
                                                         int* __restrict__ counter, int* __restrict__ flags, int* err,
                                                         int* __restrict__ err_dev,
                                                         T* __restrict__ Lc, const T* __restrict__ Sg,
@@ -1027,9 +1027,20 @@ __global__ void __launch_bounds__(256) k_down_persist2d(const DownItem* __restri
         __syncthreads();
         if (threadIdx.x == 0) {
             const int i = atomicAdd(counter, 1);
+            if (i < nitems) s_it = items[i];
+            s_item = i;
+        }
+        __syncthreads();
+        if (s_item >= nitems) break;
+        // the children's own coefficients (written by the incoming kernel) load while the
+        // parent may still be pending; a leaf holds no incoming of its own
+        for (int idx = threadIdx.x; idx < 4 * PP; idx += blockDim.x) {
+            const int c = idx / PP, cs = s_it.child[c];
+            Lch[idx] = (cs >= 0 && s_it.tc[c] == 0) ? __ldcg(Lc + size_t(cs) * PP + (idx - c * PP)) : T(0);
+        }
+        if (threadIdx.x == 0) {
             int ok = 1;
-            if (i < nitems) {
-                s_it = items[i];
+            {
                 const int w = s_it.wait;
                 if (w >= 0 && ld_relaxed_gpu(flags + w) == 0) {
                     // poll with relaxed loads (an L2 round trip each); one fence once seen
@@ -1051,11 +1062,9 @@ __global__ void __launch_bounds__(256) k_down_persist2d(const DownItem* __restri
                 }
                 __threadfence();  // order the flag read before the block's reads of the parent
             }
-            s_item = i;
             s_ok = ok;
         }
         __syncthreads();
-        if (s_item >= nitems) break;
         if (!s_ok) continue;
         // parent coefficients (written by another block: read through L2)
         const T* src = Lc + size_t(s_it.parent) * PP;
@@ -1088,12 +1097,12 @@ __global__ void __launch_bounds__(256) k_down_persist2d(const DownItem* __restri
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[j] = fma(Sm[(b0 * P + M0) * P + g * 4 + j], u, acc[j]);
             }
-            const bool leaf = s_it.tc[c] > 0;  // a leaf holds no incoming of its own
+            const bool leaf = s_it.tc[c] > 0;
             T* dst = Lc + size_t(cs) * PP;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int o = (g * 4 + j) * P + m1;
-                const T v = leaf ? acc[j] : __ldcg(dst + o) + acc[j];
+                const T v = Lch[c * PP + o] + acc[j];
                 Lch[c * PP + o] = v;
                 if (!leaf) dst[o] = v;
             }
@@ -1155,15 +1164,19 @@ __global__ void __launch_bounds__(256) k_down_persist2d(const DownItem* __restri
                 T Dd = q == 0 ? dv[0] : q == 1 ? dv[1] : q == 2 ? dv[2] : dv[3];
                 T Dm = q == 0 ? dv[4] : q == 1 ? dv[3] : q == 2 ? dv[2] : dv[1];  // T_{q-4} = T_{4-q}
                 const T T4 = tv[4], D4 = dv[4];
+                using T2 = typename V2<T>::type;
                 const T* a = Lch + c * PP + q * P;
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
                     T s = 0, sd = 0;
+                    const T2* row = reinterpret_cast<const T2*>(a + k * 4 * P);
 #pragma unroll
-                    for (int m1 = 0; m1 < P; ++m1) {
-                        const T v = a[k * 4 * P + m1];
-                        s = fma(v, b1[m1], s);
-                        sd = fma(v, d1[m1], sd);
+                    for (int m1 = 0; m1 < P; m1 += 2) {
+                        const T2 v = row[m1 / 2];
+                        s = fma(v.x, b1[m1], s);
+                        sd = fma(v.x, d1[m1], sd);
+                        s = fma(v.y, b1[m1 + 1], s);
+                        sd = fma(v.y, d1[m1 + 1], sd);
                     }
                     phi = fma(A, s, phi);
                     g0 = fma(Dd, s, g0);
