@@ -239,16 +239,20 @@ k_nearfield(NearArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Warp-per-leaf variant.  One warp owns a target leaf; its targets sit one per lane in
-// groups of C = 8, 16 or 32 lanes (the G = 32 / C groups split the sources).  The sources of
-// the direct list are streamed as one flat sequence in chunks of 32, shifted into the target
-// leaf's frame once per chunk.  Each lane first culls the chunk with the cut-off test r < h
-// (a bit per source), then evaluates only its accepted pairs, so the expensive branch runs
-// at the density of accepted pairs rather than at the density of any-lane-accepts.  The
-// residual series are Horner sums of monomials in x = 2 s - 1 (the host converts the
-// Chebyshev fits; both are equally accurate for these well-conditioned series), the
-// logarithm, square root and reciprocal use the hardware approximations on the FP32 path.
-// Plain sums inside a chunk, compensated (Kahan) sums across chunks, FP64 across groups.
+// Warp-per-leaf kernel with a compacted pair queue.  One warp owns a target leaf and takes
+// its targets in passes of up to 32 (target t of the pass <-> lane t for the sums).  The
+// sources of the direct list stream as one flat sequence in chunks of 32, one per lane,
+// shifted into the target leaf's frame.  Per chunk:
+//   cull:  for each target t, every lane tests its source against the cut-off r < h; a
+//          ballot appends the accepted (t, source) pairs to a per-warp queue, t-major;
+//   eval:  the queue is evaluated 32 pairs at a time (every lane busy, whatever the
+//          acceptance pattern), and a segmented warp scan keyed by t sums each target's
+//          run of pairs; the run's last lane adds it to the target's chunk sum;
+// then lane t adds the chunk sums to its compensated (Kahan) accumulators.  The order of
+// every sum is fixed by the queue, so results do not depend on scheduling.  The residual
+// series are Horner sums of monomials in x = 2 s - 1 (the host converts the Chebyshev fits;
+// for these series both are equally accurate); on the FP32 path the logarithm, square root
+// and reciprocal use the hardware approximations.
 template <typename T>
 __device__ __forceinline__ T near_log2(T x) { return log2(x); }
 template <>
@@ -268,16 +272,28 @@ __device__ __forceinline__ float near_rcp<float>(float x) {
 
 constexpr int kNearWarps = 4;
 
+// per-warp shared state of the queue kernel
+template <typename T, int D>
+struct NearWarpSmem {
+    static constexpr int kLo = (sizeof(T) == 4) ? 1 : 0;
+    T tx[32], ty[32], tz[D == 3 ? 32 : 1];                       // targets of the pass (hi)
+    T tlx[kLo ? 32 : 1], tly[kLo ? 32 : 1], tlz[(D == 3 && kLo) ? 32 : 1];  // (lo)
+    T sx[32], sy[32], sz[D == 3 ? 32 : 1], sq[32];              // chunk sources (hi), charge
+    T lx[kLo ? 32 : 1], ly[kLo ? 32 : 1], lz[(D == 3 && kLo) ? 32 : 1];     // (lo)
+    T ap[32], agx[32], agy[32], agz[D == 3 ? 32 : 1];           // per-target chunk sums
+    unsigned short q[32 * 32];                                  // pair queue: t << 5 | source
+};
+
 template <typename T, int D, int NH>
 __global__ void __launch_bounds__(32 * kNearWarps)
 k_near_warp(NearArgs<T> a) {
-    constexpr int kLo = (sizeof(T) == 4) ? 1 : 0;
-    constexpr int ZD = (D == 3) ? 32 : 1, ZL = kLo ? 32 : 1, ZZ = (D == 3 && kLo) ? 32 : 1;
-    __shared__ T sx[kNearWarps][32], sy[kNearWarps][32], sz[kNearWarps][ZD], sq[kNearWarps][32];
-    __shared__ T lx[kNearWarps][ZL], ly[kNearWarps][ZL], lz[kNearWarps][ZZ];
+    constexpr int kLo = NearWarpSmem<T, D>::kLo;
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ NearWarpSmem<T, D> smem[kNearWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li = blockIdx.x * kNearWarps + w;
     if (li >= a.ntleaf) return;  // whole warp; the kernel has no block-wide barrier
+    NearWarpSmem<T, D>& S = smem[w];
     const TLeaf L = a.tleaf[li];
     T cA[NH], cB[NH];
 #pragma unroll
@@ -289,37 +305,35 @@ k_near_warp(NearArgs<T> a) {
     const T hinv = T(hinv_d);
     const T h2inv = T(hinv_d * hinv_d);
     const T clog = T(0.0551589000381629);  // ln(2) / (4 pi): -log(s)/(4 pi) = -clog log2(s)
-    const int nt = L.tgt_count;
-    const int C = nt > 16 ? 32 : (nt > 8 ? 16 : 8);
-    const int G = 32 / C;
-    const int lt = lane & (C - 1), g = lane / C;
+    const unsigned lt_mask = (1u << lane) - 1u;
     unsigned long long nin = 0;
     const int2* ent = a.ent + L.list_begin;
     const T* esh = a.ent_sh + size_t(L.list_begin) * 4;
     const T* eshl = kLo ? a.ent_shlo + size_t(L.list_begin) * 4 : nullptr;
     const int ne = L.list_count;
 
-    for (int t0 = 0; t0 < nt; t0 += C) {
-        const int ti = t0 + lt;
-        const bool act = ti < nt;
-        T xt = 0, yt = 0, zt = 0, xtl = 0, ytl = 0, ztl = 0;
-        if (act) {
-            const T* p = a.tgt4 + size_t(L.tgt_begin + ti) * 4;
-            xt = p[0];
-            yt = p[1];
-            if (D == 3) zt = p[2];
+    for (int t0 = 0; t0 < L.tgt_count; t0 += 32) {
+        const int nt = min(32, L.tgt_count - t0);
+        const bool own = lane < nt;  // this lane owns target t0 + lane
+        if (own) {
+            const T* p = a.tgt4 + size_t(L.tgt_begin + t0 + lane) * 4;
+            S.tx[lane] = p[0];
+            S.ty[lane] = p[1];
+            if constexpr (D == 3) S.tz[lane] = p[2];
             if constexpr (kLo) {
-                const T* pl = a.tgt_lo + size_t(L.tgt_begin + ti) * 4;
-                xtl = pl[0];
-                ytl = pl[1];
-                if (D == 3) ztl = pl[2];
+                const T* pl = a.tgt_lo + size_t(L.tgt_begin + t0 + lane) * 4;
+                S.tlx[lane] = pl[0];
+                S.tly[lane] = pl[1];
+                if constexpr (D == 3) S.tlz[lane] = pl[2];
             }
         }
         Kahan<T> kp, kx, ky, kz;
         kp.init(); kx.init(); ky.init(); kz.init();
         int e = 0, off = 0;  // warp-uniform stream position
         while (e < ne) {
+            // ---- chunk of up to 32 sources, lane j <-> source j, in the target leaf's frame
             int filled = 0;
+            T mx = T(0), my = T(0), mz = T(0);
             while (filled < 32 && e < ne) {
                 const int2 bc = ent[e];
                 const int take = min(32 - filled, bc.y - off);
@@ -339,20 +353,23 @@ k_near_warp(NearArgs<T> a) {
                             hi[k] = sum;
                             lo[k] = err + sl[k] + eshl[e * 4 + k];
                         }
-                        sx[w][lane] = hi[0];
-                        sy[w][lane] = hi[1];
-                        lx[w][lane] = lo[0];
-                        ly[w][lane] = lo[1];
+                        mx = hi[0];
+                        my = hi[1];
+                        S.lx[lane] = lo[0];
+                        S.ly[lane] = lo[1];
                         if constexpr (D == 3) {
-                            sz[w][lane] = hi[2];
-                            lz[w][lane] = lo[2];
+                            mz = hi[2];
+                            S.lz[lane] = lo[2];
                         }
                     } else {
-                        sx[w][lane] = s[0] + esh[e * 4 + 0];
-                        sy[w][lane] = s[1] + esh[e * 4 + 1];
-                        if constexpr (D == 3) sz[w][lane] = s[2] + esh[e * 4 + 2];
+                        mx = s[0] + esh[e * 4 + 0];
+                        my = s[1] + esh[e * 4 + 1];
+                        if constexpr (D == 3) mz = s[2] + esh[e * 4 + 2];
                     }
-                    sq[w][lane] = s[3];
+                    S.sx[lane] = mx;
+                    S.sy[lane] = my;
+                    if constexpr (D == 3) S.sz[lane] = mz;
+                    S.sq[lane] = s[3];
                 }
                 filled += take;
                 off += take;
@@ -361,96 +378,126 @@ k_near_warp(NearArgs<T> a) {
                     off = 0;
                 }
             }
-            __syncwarp();
-            // cull: bit k <-> source j = g + k G of the chunk
-            unsigned mask = 0;
-            if (act) {
-                int k = 0;
-                for (int j = g; j < filled; j += G, ++k) {
-                    const T dx = xt - sx[w][j], dy = yt - sy[w][j];
-                    const T dz = (D == 3) ? zt - sz[w][j] : T(0);
-                    const T r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
-                    if (r2 * h2inv < T(1)) mask |= 1u << k;
-                }
+            if (own) {
+                S.ap[lane] = T(0);
+                S.agx[lane] = T(0);
+                S.agy[lane] = T(0);
+                if constexpr (D == 3) S.agz[lane] = T(0);
             }
-            T pp = 0, gx = 0, gy = 0, gz = 0;
-            while (mask) {
-                const int k = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int j = g + k * G;
-                T dx = xt - sx[w][j], dy = yt - sy[w][j];
-                T dz = (D == 3) ? zt - sz[w][j] : T(0);
-                T r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
-                T s = r2 * h2inv;
-                if constexpr (kLo) {
-                    if (s < a.close_s) {
-                        // close pair: (x_hi - y_hi) + (x_lo - y_lo); the hi difference is exact
-                        dx = (xt - sx[w][j]) + (xtl - lx[w][j]);
-                        dy = (yt - sy[w][j]) + (ytl - ly[w][j]);
-                        if constexpr (D == 3) dz = (zt - sz[w][j]) + (ztl - lz[w][j]);
-                        r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
-                        s = r2 * h2inv;
+            __syncwarp();
+            // ---- cull: every lane tests its source against target t; accepted pairs queue
+            //      in (t, source) order
+            const bool hs = lane < filled;
+            int N = 0;
+            for (int t = 0; t < nt; ++t) {
+                const T dx = S.tx[t] - mx, dy = S.ty[t] - my;
+                const T dz = (D == 3) ? S.tz[t] - mz : T(0);
+                const T r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
+                const bool acc = hs && r2 * h2inv < T(1);
+                const unsigned b = __ballot_sync(kFull, acc);
+                if (acc) S.q[N + __popc(b & lt_mask)] = static_cast<unsigned short>((t << 5) | lane);
+                N += __popc(b);
+            }
+            __syncwarp();
+            // ---- evaluate 32 queued pairs at a time
+            for (int r0 = 0; r0 < N; r0 += 32) {
+                const int pidx = r0 + lane;
+                const bool valid = pidx < N;
+                const int qe = valid ? int(S.q[pidx]) : (64 << 5);  // key 64: no target
+                const int t = qe >> 5, j = qe & 31;
+                T pp = 0, gx = 0, gy = 0, gz = 0;
+                if (valid) {
+                    const T xt = S.tx[t], yt = S.ty[t];
+                    const T zt = (D == 3) ? S.tz[t] : T(0);
+                    T dx = xt - S.sx[j], dy = yt - S.sy[j];
+                    T dz = (D == 3) ? zt - S.sz[j] : T(0);
+                    T r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
+                    T s = r2 * h2inv;
+                    if constexpr (kLo) {
+                        if (s < a.close_s) {
+                            // close pair: (x_hi - y_hi) + (x_lo - y_lo); the hi difference is exact
+                            dx = (xt - S.sx[j]) + (S.tlx[t] - S.lx[j]);
+                            dy = (yt - S.sy[j]) + (S.tly[t] - S.ly[j]);
+                            if constexpr (D == 3) dz = (zt - S.sz[j]) + (S.tlz[t] - S.lz[j]);
+                            r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
+                            s = r2 * h2inv;
+                        }
                     }
-                }
-                if (r2 > T(0)) {  // the self pair is skipped
-                    if (a.count_in) ++nin;
-                    const T q = sq[w][j];
-                    const T xc = fma(T(2), s, T(-1));
-                    T fa = cA[NH - 1], fb = cB[NH - 1];
+                    if (r2 > T(0)) {  // the self pair is skipped
+                        if (a.count_in) ++nin;
+                        const T q = S.sq[j];
+                        const T xc = fma(T(2), s, T(-1));
+                        T fa = cA[NH - 1], fb = cB[NH - 1];
 #pragma unroll
-                    for (int m = NH - 2; m >= 0; --m) {
-                        fa = fma(fa, xc, cA[m]);
-                        fb = fma(fb, xc, cB[m]);
-                    }
-                    if constexpr (D == 3) {
-                        // R = (1 - t A)/(4 pi r); grad R = -(1 - t A + t B) dr / (4 pi r^3)
-                        const T rinv = fast_rsqrt(r2);
-                        const T t = r2 * rinv * hinv;
-                        const T num = fma(-t, fa, T(1));
-                        pp = fma(q * num, rinv, pp);
-                        const T gf = -q * fma(t, fb, num) * rinv * rinv * rinv;
-                        gx = fma(gf, dx, gx);
-                        gy = fma(gf, dy, gy);
-                        gz = fma(gf, dz, gz);
-                    } else {
-                        // R = -log(s)/(4 pi) - A(s); grad R = -sqrt(1-s) S(s) dr/(2 pi r^2)
-                        pp = fma(q, fma(-clog, near_log2(s), -fa), pp);
-                        const T gf = -q * near_sqrt_pos(T(1) - s) * fb * near_rcp(r2);
-                        gx = fma(gf, dx, gx);
-                        gy = fma(gf, dy, gy);
+                        for (int m = NH - 2; m >= 0; --m) {
+                            fa = fma(fa, xc, cA[m]);
+                            fb = fma(fb, xc, cB[m]);
+                        }
+                        if constexpr (D == 3) {
+                            // R = (1 - t A)/(4 pi r); grad R = -(1 - t A + t B) dr / (4 pi r^3)
+                            const T rinv = fast_rsqrt(r2);
+                            const T tt = r2 * rinv * hinv;
+                            const T num = fma(-tt, fa, T(1));
+                            pp = q * num * rinv;
+                            const T gf = -q * fma(tt, fb, num) * rinv * rinv * rinv;
+                            gx = gf * dx;
+                            gy = gf * dy;
+                            gz = gf * dz;
+                        } else {
+                            // R = -log(s)/(4 pi) - A(s); grad R = -sqrt(1-s) S(s) dr/(2 pi r^2)
+                            pp = q * fma(-clog, near_log2(s), -fa);
+                            const T gf = -q * near_sqrt_pos(T(1) - s) * fb * near_rcp(r2);
+                            gx = gf * dx;
+                            gy = gf * dy;
+                        }
                     }
                 }
+                // segmented inclusive scan keyed by t (keys are non-decreasing across lanes)
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const T pv = __shfl_up_sync(kFull, pp, o), xv = __shfl_up_sync(kFull, gx, o);
+                    const T yv = __shfl_up_sync(kFull, gy, o);
+                    const T zv = (D == 3) ? __shfl_up_sync(kFull, gz, o) : T(0);
+                    const int tv = __shfl_up_sync(kFull, t, o);
+                    if (lane >= o && tv == t) {
+                        pp += pv;
+                        gx += xv;
+                        gy += yv;
+                        if (D == 3) gz += zv;
+                    }
+                }
+                const int tn = __shfl_down_sync(kFull, t, 1);
+                if (valid && (lane == 31 || tn != t)) {  // last lane of target t's run
+                    S.ap[t] += pp;
+                    S.agx[t] += gx;
+                    S.agy[t] += gy;
+                    if constexpr (D == 3) S.agz[t] += gz;
+                }
+                __syncwarp();
             }
-            if (act) {
-                kp.add(pp);
-                kx.add(gx);
-                ky.add(gy);
-                if (D == 3) kz.add(gz);
+            if (own) {
+                kp.add(S.ap[lane]);
+                kx.add(S.agx[lane]);
+                ky.add(S.agy[lane]);
+                if constexpr (D == 3) kz.add(S.agz[lane]);
             }
             __syncwarp();
         }
-        // combine the groups in a fixed order (FP64): lanes lt + g C
-        double P = kp.value(), X = kx.value(), Y = ky.value(), Z = (D == 3) ? kz.value() : 0.0;
-        for (int o = 16; o >= C; o >>= 1) {
-            P += __shfl_down_sync(0xffffffffu, P, o);
-            X += __shfl_down_sync(0xffffffffu, X, o);
-            Y += __shfl_down_sync(0xffffffffu, Y, o);
-            if (D == 3) Z += __shfl_down_sync(0xffffffffu, Z, o);
-        }
-        if (g == 0 && act) {
+        if (own) {
             const double kpot = (D == 3) ? 0.07957747154594766788 : 1.0;
             const double kgrad = (D == 3) ? 0.07957747154594766788 : 0.15915494309189533577;
-            const size_t o = size_t(L.tgt_begin + ti);
-            a.pot[o] = P * kpot;
+            const size_t o = size_t(L.tgt_begin + t0 + lane);
+            a.pot[o] = kp.value() * kpot;
             if (a.grad) {
-                a.grad[o * D + 0] = X * kgrad;
-                a.grad[o * D + 1] = Y * kgrad;
-                if (D == 3) a.grad[o * D + 2] = Z * kgrad;
+                a.grad[o * D + 0] = kx.value() * kgrad;
+                a.grad[o * D + 1] = ky.value() * kgrad;
+                if (D == 3) a.grad[o * D + 2] = kz.value() * kgrad;
             }
         }
+        __syncwarp();
     }
     if (a.count_in) {
-        for (int o = 16; o > 0; o >>= 1) nin += __shfl_down_sync(0xffffffffu, nin, o);
+        for (int o = 16; o > 0; o >>= 1) nin += __shfl_down_sync(kFull, nin, o);
         if (lane == 0 && nin) atomicAdd(a.count_in, nin);
     }
 }
