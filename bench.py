@@ -108,44 +108,58 @@ def oracle_sample(g, idx, nthreads=None):
     return pot, grad, time.perf_counter() - t0
 
 
-def stage_flops(info, d):
+def stage_flops(info, d, leaf_folded):
     """Algorithmic flops of each timed stage, from the plan's work counts and the fixed
     per-unit costs of each kernel's formula (documented with the kernels):
-      spread      per point: w^d FMAs + d*w window series of n_W Chebyshev terms
+      spread      per point: w^d products + d*w window series of n_W terms (2 flops/term)
       interp      per target: 2 w^d FMAs (value, x-derivative) + d*w window series (value, derivative)
       nearfield   per visited pair 5 (2D) / 7 (3D); per pair inside the support two
-                  Chebyshev series of n_A, n_B terms (2 flops/term) + 16 (2D) / 22 (3D)
-      pw_upward   per source p^d * 3 (moment outer product) + per merge parent 12 p^3 (2D)
+                  residual series of n_A, n_B terms (2 flops/term) + 16 (2D) / 22 (3D)
+      pw_upward   per (out box, source) pair: the p^d moment outer product (2 flops each) and
+                  2 d p Chebyshev recurrence flops; per merge parent (generic path) 12 p^3 (2D)
                   or 8 * 3 * 2 p^{d+1} (3D separable re-expansion)
-      pw_out      per box: real-complex sweep 2 (K+1) p^d + complex sweeps 8 (K+1) n1 p (2D)
-      pw_translate_in per box: 3^d * 14 * npw (phase and complex MAC) + 8 (K+1) n1 p + 3 (K+1) p^2 (2D)
-      pw_downward per parent 12 p^3 (2D) or 8 * 3 * 2 p^{d+1} (3D)
+      pw_out      per box (2D parity form): 2 (K+1) p^2 + 4 (K+1)^2 p
+      pw_translate_in per box (2D parity form): ~100 (K+1)^2 (nine phased colleagues, both
+                  k1 signs) + 4 (K+1)^2 p + 2 (K+1) p^2
+      pw_downward per parent 12 p^3 (2D) or 8 * 3 * 2 p^{d+1} (3D), plus the leaf evaluation
+                  (4 p^d per target) where the single-launch pass folds it in
       pw_leaf_eval per target 4 p^d
     """
     w, p, K = info["window_w"], info["n_proxy"], info["n_pw"]
     n1 = 2 * K + 1
     npw = (K + 1) * n1 ** (d - 1)
-    nW = 14
+    nW = 15
     n = info["n"]
     out = {}
-    out["spread"] = n * (2 * w ** d + 2 * d * w * 2 * nW)
-    out["interp"] = n * (4 * w ** d + 2 * d * w * 2 * 2 * nW)
-    visit, inside = (5, 2 * (12 + 13) + 16) if d == 2 else (7, 2 * (12 + 13) + 22)
+    out["spread"] = n * (2 * w ** d + 2 * d * w * nW)
+    out["interp"] = n * (4 * w ** d + 2 * d * w * 2 * nW)
+    visit, inside = (5, 2 * (12 + 14) + 16) if d == 2 else (7, 2 * (13 + 14) + 22)
     out["nearfield"] = info["near_pairs"] * visit + info["near_pairs_in"] * inside
     merge_unit = 12 * p ** 3 if d == 2 else 8 * 3 * 2 * p ** (d + 1)
-    out["pw_upward"] = info["pw_moment_sources"] * 3 * p ** d + info["pw_merge_parents"] * merge_unit
-    out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** d + 8 * (K + 1) * n1 * p ** (d - 1) * (d - 1))
-    out["pw_translate_in"] = info["n_pw_boxes_in"] * (3 ** d * 14 * npw + 8 * (K + 1) * n1 * p ** (d - 1) * (d - 1)
-                                                      + 3 * (K + 1) * p ** d)
-    out["pw_downward"] = info["pw_down_parents"] * merge_unit
-    out["pw_leaf_eval"] = info["pw_eval_targets"] * 4 * p ** d
+    out["pw_upward"] = info["pw_moment_sources"] * (2 * p ** d + 2 * d * p) + info["pw_merge_parents"] * merge_unit
+    if d == 2:
+        out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** 2 + 4 * (K + 1) ** 2 * p)
+        out["pw_translate_in"] = info["n_pw_boxes_in"] * (100 * (K + 1) ** 2 + 4 * (K + 1) ** 2 * p
+                                                          + 2 * (K + 1) * p ** 2)
+    else:
+        out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** d + 8 * (K + 1) * n1 * p ** (d - 1) * (d - 1))
+        out["pw_translate_in"] = info["n_pw_boxes_in"] * (3 ** d * 14 * npw + 8 * (K + 1) * n1 * p ** (d - 1) * (d - 1)
+                                                          + 3 * (K + 1) * p ** d)
+    leaf = info["pw_eval_targets"] * 4 * p ** d
+    out["pw_downward"] = info["pw_down_parents"] * merge_unit + (leaf if leaf_folded else 0)
+    out["pw_leaf_eval"] = 0 if leaf_folded else leaf
     return out
 
 
+# DRAM bytes (read + write) per launch of each stage's main kernel on this workload, from
+# one `ncu --set full` capture of the kernel as it stands (profiles/ holds the summaries);
+# None where no capture of the current kernel exists
+STAGE_TRAFFIC = {"nearfield": 17896960}
+
 STAGE_KERNELS = {
-    "spread": "k_spread + k_fold", "interp": "k_interp", "nearfield": "k_nearfield",
-    "pw_upward": "k_leaf_moments + k_merge2d_p (per level)", "pw_out": "k_pw_out",
-    "pw_translate_in": "k_pw_in", "pw_downward": "k_down2d_p (per level)", "pw_leaf_eval": "k_leaf_eval",
+    "spread": "k_spread_halo + k_fold_whole", "interp": "k_interp_halo", "nearfield": "k_near_warp",
+    "pw_upward": "k_moments_direct2d", "pw_out": "k_pw_out2d_p", "pw_translate_in": "k_pw_in2d_p",
+    "pw_downward": "k_down_persist2d (leaf evaluation folded in)", "pw_leaf_eval": "k_leaf_eval",
 }
 
 
@@ -177,7 +191,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -281,14 +295,16 @@ def main():
 
     # end-to-end through the C ABI with host buffers: charges in, potential+gradient out
     q_host = torch.from_numpy(g["q"]).pin_memory()
+    pot_host = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    grad_host = torch.empty((n, d), dtype=torch.float64).pin_memory().numpy()
     reps = max(3, args.steps // 2)
     plan.set_charges(q_host.numpy())
-    plan.eval()
+    plan.eval(out=(pot_host, grad_host))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(reps):
         plan.set_charges(q_host.numpy())
-        plan.eval()
+        plan.eval(out=(pot_host, grad_host))
     e2e_t = (time.perf_counter() - t0) / reps
     e2e = {"value": ws * n / e2e_t, "unit": "points/s", "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": 8 * n * (1 + d)}
@@ -311,7 +327,9 @@ def main():
         # working set stays in L2); report each and pick the dominant one
         sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
         fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
-        fl = stage_flops(pinfo, d)
+        # the single-launch downward pass evaluates the leaves itself (its leaf stage is empty)
+        leaf_folded = stage_acc.get("pw_leaf_eval", 0.0) < 0.05 * stage_acc.get("pw_downward", 0.0)
+        fl = stage_flops(pinfo, d, leaf_folded)
         stages = {k: round(v, 4) for k, v in stage_acc.items()}
         per_stage = {}
         for k, f in fl.items():
@@ -334,7 +352,8 @@ def main():
             "fp64": {"value": pts64, "unit": "points/s"},
             "stages_ms": stages, "dominant_stage": dominant, "stage_roofline": per_stage,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / fp32_peak) if achieved else None,
+                         "traffic": STAGE_TRAFFIC.get(dominant),
                          "kernel": STAGE_KERNELS.get(dominant), "stage": dominant,
                          "peak_note": f"FP32 FMA pipes: 148 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
                                       "(recipe unit counts at the maximum clock; no measured FP32 peak exists)"},

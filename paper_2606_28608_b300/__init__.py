@@ -194,9 +194,21 @@ class Plan:
             raise PdmkError(rc, "pdmk_set_charges")
 
     def eval(self, grad: bool = True, out=None):
-        """Host evaluation: returns numpy (pot, grad or None)."""
-        pot = np.empty(self.n, dtype=np.float64)
-        g = np.empty((self.n, self.d), dtype=np.float64) if grad else None
+        """Host evaluation: returns numpy (pot, grad or None).  out=(pot, grad) writes into
+        caller arrays instead (C-contiguous float64 of shapes (n,) and (n, d); page-locked host
+        memory, e.g. a pinned torch tensor's .numpy(), makes the device-to-host copy a DMA)."""
+        if out is not None:
+            pot, g = out
+            ok = (isinstance(pot, np.ndarray) and pot.dtype == np.float64 and pot.shape == (self.n,)
+                  and pot.flags.c_contiguous)
+            if grad:
+                ok = ok and (isinstance(g, np.ndarray) and g.dtype == np.float64 and g.shape == (self.n, self.d)
+                             and g.flags.c_contiguous)
+            if not ok:
+                raise ValueError("out must be C-contiguous float64 arrays of shapes (n,) and (n, d)")
+        else:
+            pot = np.empty(self.n, dtype=np.float64)
+            g = np.empty((self.n, self.d), dtype=np.float64) if grad else None
         rc = lib().pdmk_eval(self._h, pot.ctypes.data, g.ctypes.data if grad else None, PDMK_HOST)
         if rc != 0:
             raise PdmkError(rc, "pdmk_eval")

@@ -41,6 +41,8 @@ using namespace pdmk;
         }                                                    \
     } while (0)
 
+constexpr int kSumBlocks = 2 * 148;  // blocks of the two-stage charge sums
+
 struct pdmk_plan_s {
     int d = 3;
     double eps = 1e-6;
@@ -85,6 +87,7 @@ struct pdmk_plan_s {
     void* d_grid = nullptr;
     void* d_spec = nullptr;
     double* d_qsums = nullptr;
+    double* d_qsum_part = nullptr;  // [kSumBlocks][3] partial charge sums
     unsigned long long* d_count = nullptr;
     bool count_pending = false;
     cufftHandle fft_fwd = 0, fft_inv = 0;
@@ -501,6 +504,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
         PCHECK(dalloc(plan, plan->plan_allocs, &p, 2 * ts * size_t(plan->nhalf)));
         plan->d_spec = p;
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsums, 4));
+        PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsum_part, size_t(3 * kSumBlocks)));
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_count, 2));
     }
     {
@@ -583,7 +587,10 @@ static int gather_charges(pdmk_plan plan) {
 }
 
 static int set_charges_device(pdmk_plan plan, bool check_neutral) {
-    k_charge_sums<<<1, 1024, 0, plan->ws>>>(plan->d_q_user, plan->n, plan->d_qsums);
+    // deterministic two-stage sums over many SMs (FP64 on one SM would take ~0.2 ms)
+    const int nb = int(std::max<int64_t>(1, std::min<int64_t>(kSumBlocks, (plan->n + 1023) / 1024)));
+    k_charge_sums_part<<<nb, kSumThreads, 0, plan->ws>>>(plan->d_q_user, plan->n, plan->d_qsum_part);
+    k_charge_sums_final<<<1, kSumThreads, 0, plan->ws>>>(plan->d_qsum_part, nb, plan->d_qsums);
     CK(cudaGetLastError());
     if (check_neutral) {
         double h[3];
@@ -971,7 +978,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         else halo(k_spread_halo<T, 17, 20>);
         ++plan->launches;
         CK(cudaGetLastError());
-        int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 4));
+        const int blocks = int((plan->ncell + 31) / 32);
         k_fold_whole<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<const T*>(slab), plan->whole_ctas,
                                                             static_cast<T*>(plan->d_grid), int(plan->ncell));
         ++plan->launches;
@@ -1003,7 +1010,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         }
         ++plan->launches;
         CK(cudaGetLastError());
-        int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 4));
+        const int blocks = int((plan->ncell + 31) / 32);
         k_fold_whole<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<const T*>(slab), plan->whole_ctas,
                                                             static_cast<T*>(plan->d_grid), int(plan->ncell));
         ++plan->launches;

@@ -36,13 +36,43 @@ __global__ void k_gather_charges(GatherArgs<T> a) {
     }
 }
 
-// deterministic single-block sums: out[0] = sum q, out[1] = sum |q|, out[2] = nonfinite count
-__global__ void k_charge_sums(const double* q, int64_t n, double* out) {
-    __shared__ double s0[1024], s1[1024], s2[1024];
+// Deterministic two-stage sums (fixed block ranges, fixed tree orders):
+// out[0] = sum q, out[1] = sum |q|, out[2] = number of non-finite values.
+// Stage 1: block b sums its contiguous range into part[3 b .. 3 b + 2].
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) k_charge_sums_part(const double* q, int64_t n, double* part) {
+    __shared__ double s0[kSumThreads], s1[kSumThreads], s2[kSumThreads];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min(n, int64_t(blockIdx.x) * per), i1 = min(n, i0 + per);
     double a = 0, b = 0, c = 0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const double v = q[i];
         if (isfinite(v)) { a += v; b += fabs(v); } else { c += 1; }
+    }
+    s0[threadIdx.x] = a; s1[threadIdx.x] = b; s2[threadIdx.x] = c;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s0[threadIdx.x] += s0[threadIdx.x + h];
+            s1[threadIdx.x] += s1[threadIdx.x + h];
+            s2[threadIdx.x] += s2[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = s0[0];
+        part[3 * blockIdx.x + 1] = s1[0];
+        part[3 * blockIdx.x + 2] = s2[0];
+    }
+}
+// Stage 2: one block sums the nb partials.
+__global__ void __launch_bounds__(kSumThreads) k_charge_sums_final(const double* part, int nb, double* out) {
+    __shared__ double s0[kSumThreads], s1[kSumThreads], s2[kSumThreads];
+    double a = 0, b = 0, c = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += part[3 * i + 0];
+        b += part[3 * i + 1];
+        c += part[3 * i + 2];
     }
     s0[threadIdx.x] = a; s1[threadIdx.x] = b; s2[threadIdx.x] = c;
     __syncthreads();

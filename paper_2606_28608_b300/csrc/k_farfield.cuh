@@ -256,12 +256,23 @@ k_spread_whole_w(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, cons
     }
 }
 
+// Sum of the per-CTA slabs: a block takes 32 cells (one per lane); its eight warps split the
+// slabs, and warp 0 adds the eight partials in order.
 template <typename T>
-__global__ void k_fold_whole(const T* __restrict__ slab, int nslab, T* __restrict__ grid, int ncell) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
-        T s = T(0);
-        for (int k = 0; k < nslab; ++k) s += slab[size_t(k) * ncell + c];
-        grid[c] = s;
+__global__ void __launch_bounds__(256) k_fold_whole(const T* __restrict__ slab, int nslab, T* __restrict__ grid,
+                                                    int ncell) {
+    __shared__ T part[8][32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    T s = T(0);
+    if (c < ncell)
+        for (int k = wp; k < nslab; k += 8) s += slab[size_t(k) * ncell + c];
+    part[wp][lane] = s;
+    __syncthreads();
+    if (wp == 0 && c < ncell) {
+        T t = part[0][lane];
+        for (int k = 1; k < 8; ++k) t += part[k][lane];
+        grid[c] = t;
     }
 }
 

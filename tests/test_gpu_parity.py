@@ -145,3 +145,22 @@ def test_charges_update_and_linearity():
     assert rel(p3, 2 * p1 - 0.5 * p2) < 1e-12
     assert rel(g3, 2 * g1 - 0.5 * g2) < 1e-12
     plan.close()
+
+
+def test_eval_into_caller_arrays():
+    """eval(out=...) writes the same values into caller-owned (pinned) host arrays."""
+    P = _cuda()
+    import torch
+    g = W.oblique2d_clusters(5000, seed=6)
+    plan = P.Plan(g["L"], 1e-6, precision="mixed")
+    plan.set_sources(g["y"], g["q"])
+    p1, g1 = plan.eval()
+    n = len(g["q"])
+    po = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    go = torch.empty((n, 2), dtype=torch.float64).pin_memory().numpy()
+    p2, g2 = plan.eval(out=(po, go))
+    assert p2 is po and g2 is go
+    assert np.array_equal(p1, po) and np.array_equal(g1, go)
+    with pytest.raises(ValueError):
+        plan.eval(out=(np.empty(n + 1), go))
+    plan.close()
