@@ -1155,13 +1155,19 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         na.monoB = static_cast<const T*>(plan->d_monoB);
         const int nc = std::max(na.nA, na.nB);
         const int wb = (plan->ntleaf + kNearWarps - 1) / kNearWarps, wt = 32 * kNearWarps;
-        if (plan->near_nh == 8) k_near_warp<T, D, 8><<<wb, wt, 0, s_near>>>(na);
-        else if (plan->near_nh == 10) k_near_warp<T, D, 10><<<wb, wt, 0, s_near>>>(na);
-        else if (plan->near_nh == 12) k_near_warp<T, D, 12><<<wb, wt, 0, s_near>>>(na);
-        else if (plan->near_nh == 14) k_near_warp<T, D, 14><<<wb, wt, 0, s_near>>>(na);
-        else if (plan->near_nh == 16) k_near_warp<T, D, 16><<<wb, wt, 0, s_near>>>(na);
-        else if (plan->near_nh == 20) k_near_warp<T, D, 20><<<wb, wt, 0, s_near>>>(na);
-        else if (plan->near_nh == 24) k_near_warp<T, D, 24><<<wb, wt, 0, s_near>>>(na);
+        // A is usually two terms shorter than B: its own compile-time length then
+        const bool ash = na.nA <= plan->near_nh - 2;
+#define PDMK_NEAR(NH)                                                                         \
+    (ash ? k_near_warp<T, D, NH, NH - 2><<<wb, wt, 0, s_near>>>(na)                            \
+         : k_near_warp<T, D, NH, NH><<<wb, wt, 0, s_near>>>(na))
+        if (plan->near_nh == 8) PDMK_NEAR(8);
+        else if (plan->near_nh == 10) PDMK_NEAR(10);
+        else if (plan->near_nh == 12) PDMK_NEAR(12);
+        else if (plan->near_nh == 14) PDMK_NEAR(14);
+        else if (plan->near_nh == 16) PDMK_NEAR(16);
+        else if (plan->near_nh == 20) PDMK_NEAR(20);
+        else if (plan->near_nh == 24) PDMK_NEAR(24);
+#undef PDMK_NEAR
         else if (nc <= 8) k_nearfield<T, D, 8><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
         else if (nc <= 12) k_nearfield<T, D, 12><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
         else if (nc <= 16) k_nearfield<T, D, 16><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
@@ -1204,7 +1210,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
         aa.pot_out = pot;
         aa.grad_out = grad;
         int blocks = int(std::min<int64_t>((plan->ntgt + 255) / 256, 148 * 8));
-        k_assemble<<<std::max(blocks, 1), 256, 0, s>>>(aa);
+        k_assemble<D, T><<<std::max(blocks, 1), 256, 0, s>>>(aa);
         ++plan->launches;
         CK(cudaGetLastError());
     }

@@ -1,5 +1,5 @@
 // k_assemble.cuh -- charge gathers into the device layouts, the total charge, and the
-// final assembly (Eq. (3.16)-(3.17), Algorithm 1 step 5) in FP64:
+// final assembly (Eq. (3.16)-(3.17), Algorithm 1 step 5), the potential in FP64:
 //   Phi = Phi_near + Phi_pw + Phi_far - W_{L(i)}(0) q_i - Q hat-R_0(0) / V,
 // gradient = grad_near + grad_pw + R^{-T} (M * grad_gridcoords Phi_far), rotated back to
 // the caller's frame and written in the caller's order.
@@ -104,8 +104,19 @@ struct AssembleArgs {
     double* grad_out;        // user order, d per point, or null
 };
 
-__global__ void k_assemble(AssembleArgs a) {
+// The potential (self term, mean correction, the 2D logarithmic cancellation between the
+// parts) is summed in FP64.  The gradient parts are summed and rotated back to the caller's
+// frame in GT: FP32 on the mixed path (FP64 issue on B300 is a small fraction of FP32, and
+// this kernel runs after the branches join, on the critical path), FP64 on the FP64 path.
+template <int D, typename GT>
+__global__ void __launch_bounds__(256) k_assemble(AssembleArgs a) {
     const double corr = a.qsum[0] * a.mean_coef;
+    GT G[D * D], Qt[D * D];
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) {
+        G[k] = GT(a.G[k]);
+        Qt[k] = GT(a.Qt[k]);
+    }
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < a.nt;
          t += int64_t(gridDim.x) * blockDim.x) {
         double p = a.pot_near[t] + a.pot_far[t] - a.self_w[t] * a.q_tgt[t] - corr;
@@ -113,18 +124,23 @@ __global__ void k_assemble(AssembleArgs a) {
         const int o = a.tgt_orig[t];
         a.pot_out[o] = p;
         if (a.grad_out) {
-            const int d = a.d;
-            double g[3] = {0, 0, 0};
-            for (int i = 0; i < d; ++i) {
-                double s = a.grad_near[t * d + i];
-                if (a.grad_pw) s += a.grad_pw[t * d + i];
-                for (int j = 0; j < d; ++j) s += a.G[i * d + j] * a.gradu_far[t * d + j];
+            GT gu[D], g[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) gu[j] = GT(a.gradu_far[t * D + j]);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                GT s = GT(a.grad_near[t * D + i]);
+                if (a.grad_pw) s += GT(a.grad_pw[t * D + i]);
+#pragma unroll
+                for (int j = 0; j < D; ++j) s = fma(G[i * D + j], gu[j], s);
                 g[i] = s;
             }
-            for (int i = 0; i < d; ++i) {
-                double s = 0;
-                for (int j = 0; j < d; ++j) s += a.Qt[i * d + j] * g[j];
-                a.grad_out[int64_t(o) * d + i] = s;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                GT s = GT(0);
+#pragma unroll
+                for (int j = 0; j < D; ++j) s = fma(Qt[i * D + j], g[j], s);
+                a.grad_out[int64_t(o) * D + i] = double(s);
             }
         }
     }

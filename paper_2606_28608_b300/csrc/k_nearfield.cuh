@@ -284,7 +284,8 @@ struct NearWarpSmem {
     unsigned short q[32 * 32];                                  // pair queue: t << 5 | source
 };
 
-template <typename T, int D, int NH>
+// NH: padded length of the B series; NA <= NH: of the A series (usually two terms shorter)
+template <typename T, int D, int NH, int NA>
 __global__ void __launch_bounds__(32 * kNearWarps)
 k_near_warp(NearArgs<T> a) {
     constexpr int kLo = NearWarpSmem<T, D>::kLo;
@@ -295,12 +296,11 @@ k_near_warp(NearArgs<T> a) {
     if (li >= a.ntleaf) return;  // whole warp; the kernel has no block-wide barrier
     NearWarpSmem<T, D>& S = smem[w];
     const TLeaf L = a.tleaf[li];
-    T cA[NH], cB[NH];
+    T cA[NA], cB[NH];
 #pragma unroll
-    for (int k = 0; k < NH; ++k) {
-        cA[k] = a.monoA[k];
-        cB[k] = a.monoB[k];
-    }
+    for (int k = 0; k < NA; ++k) cA[k] = a.monoA[k];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) cB[k] = a.monoB[k];
     const double hinv_d = a.inv_rc * double(1LL << L.level);
     const T hinv = T(hinv_d);
     const T h2inv = T(hinv_d * hinv_d);
@@ -389,6 +389,7 @@ k_near_warp(NearArgs<T> a) {
             //      in (t, source) order
             const bool hs = lane < filled;
             int N = 0;
+#pragma unroll 4
             for (int t = 0; t < nt; ++t) {
                 const T dx = S.tx[t] - mx, dy = S.ty[t] - my;
                 const T dz = (D == 3) ? S.tz[t] - mz : T(0);
@@ -427,10 +428,10 @@ k_near_warp(NearArgs<T> a) {
                         if (a.count_in) ++nin;
                         const T q = S.sq[j];
                         const T xc = fma(T(2), s, T(-1));
-                        T fa = cA[NH - 1], fb = cB[NH - 1];
+                        T fa = cA[NA - 1], fb = cB[NH - 1];
 #pragma unroll
                         for (int m = NH - 2; m >= 0; --m) {
-                            fa = fma(fa, xc, cA[m]);
+                            if (m < NA - 1) fa = fma(fa, xc, cA[m]);
                             fb = fma(fb, xc, cB[m]);
                         }
                         if constexpr (D == 3) {
