@@ -245,11 +245,12 @@ k_nearfield(NearArgs<T> a) {
 // shifted into the target leaf's frame.  Per chunk:
 //   cull:  for each target t, every lane tests its source against the cut-off r < h; a
 //          ballot appends the accepted (t, source) pairs to a per-warp queue, t-major;
-//   eval:  the queue is evaluated 32 pairs at a time (every lane busy, whatever the
-//          acceptance pattern), and a segmented warp scan keyed by t sums each target's
-//          run of pairs; the run's last lane adds it to the target's chunk sum;
-// then lane t adds the chunk sums to its compensated (Kahan) accumulators.  The order of
-// every sum is fixed by the queue, so results do not depend on scheduling.  The residual
+//   eval:  lane l takes the l-th of 32 equal contiguous blocks of the queue (every lane
+//          busy, whatever the acceptance pattern) and sums in registers while the target
+//          stays the same; each run's sum goes to a slot named by where the run starts;
+// then lane t adds its target's run sums, in queue order, to its compensated (Kahan)
+// accumulators.  The order of every sum is fixed by the queue, so results do not depend
+// on scheduling.  The residual
 // series are Horner sums of monomials in x = 2 s - 1 (the host converts the Chebyshev fits;
 // for these series both are equally accurate); on the FP32 path the logarithm, square root
 // and reciprocal use the hardware approximations.
@@ -280,7 +281,9 @@ struct NearWarpSmem {
     T tlx[kLo ? 32 : 1], tly[kLo ? 32 : 1], tlz[(D == 3 && kLo) ? 32 : 1];  // (lo)
     T sx[32], sy[32], sz[D == 3 ? 32 : 1], sq[32];              // chunk sources (hi), charge
     T lx[kLo ? 32 : 1], ly[kLo ? 32 : 1], lz[(D == 3 && kLo) ? 32 : 1];     // (lo)
-    T ap[32], agx[32], agy[32], agz[D == 3 ? 32 : 1];           // per-target chunk sums
+    // partial sums of the pair runs: [0, 32) a lane's first run, [32, 64) a run that starts
+    // at target t's first pair
+    T rp[64], rx[64], ry[64], rz[D == 3 ? 64 : 1];
     unsigned short q[32 * 32];                                  // pair queue: t << 5 | source
 };
 
@@ -378,17 +381,11 @@ k_near_warp(NearArgs<T> a) {
                     off = 0;
                 }
             }
-            if (own) {
-                S.ap[lane] = T(0);
-                S.agx[lane] = T(0);
-                S.agy[lane] = T(0);
-                if constexpr (D == 3) S.agz[lane] = T(0);
-            }
             __syncwarp();
             // ---- cull: every lane tests its source against target t; accepted pairs queue
-            //      in (t, source) order
+            //      in (t, source) order; lane t records where its target's run starts
             const bool hs = lane < filled;
-            int N = 0;
+            int N = 0, my_start = 0;
 #pragma unroll 4
             for (int t = 0; t < nt; ++t) {
                 const T dx = S.tx[t] - mx, dy = S.ty[t] - my;
@@ -397,90 +394,102 @@ k_near_warp(NearArgs<T> a) {
                 const bool acc = hs && r2 * h2inv < T(1);
                 const unsigned b = __ballot_sync(kFull, acc);
                 if (acc) S.q[N + __popc(b & lt_mask)] = static_cast<unsigned short>((t << 5) | lane);
+                if (lane == t) my_start = N;
                 N += __popc(b);
             }
+            int my_end = __shfl_down_sync(kFull, my_start, 1);
+            if (lane == nt - 1) my_end = N;
             __syncwarp();
-            // ---- evaluate 32 queued pairs at a time
-            for (int r0 = 0; r0 < N; r0 += 32) {
-                const int pidx = r0 + lane;
-                const bool valid = pidx < N;
-                const int qe = valid ? int(S.q[pidx]) : (64 << 5);  // key 64: no target
+            // ---- evaluate: lane l takes the queue block [l R, (l + 1) R) and keeps register
+            //      sums for the current target; a run is written to its slot when the target
+            //      changes (runs start at a block start or at a target's first pair)
+            const int R = (N + 31) >> 5;
+            const int b0 = min(N, lane * R), b1 = min(N, b0 + R);
+            int cur = -1, first = b0;
+            T pp = 0, gx = 0, gy = 0, gz = 0;
+            for (int i = b0; i < b1; ++i) {
+                const int qe = S.q[i];
                 const int t = qe >> 5, j = qe & 31;
-                T pp = 0, gx = 0, gy = 0, gz = 0;
-                if (valid) {
-                    const T xt = S.tx[t], yt = S.ty[t];
-                    const T zt = (D == 3) ? S.tz[t] : T(0);
-                    T dx = xt - S.sx[j], dy = yt - S.sy[j];
-                    T dz = (D == 3) ? zt - S.sz[j] : T(0);
-                    T r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
-                    T s = r2 * h2inv;
-                    if constexpr (kLo) {
-                        if (s < a.close_s) {
-                            // close pair: (x_hi - y_hi) + (x_lo - y_lo); the hi difference is exact
-                            dx = (xt - S.sx[j]) + (S.tlx[t] - S.lx[j]);
-                            dy = (yt - S.sy[j]) + (S.tly[t] - S.ly[j]);
-                            if constexpr (D == 3) dz = (zt - S.sz[j]) + (S.tlz[t] - S.lz[j]);
-                            r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
-                            s = r2 * h2inv;
-                        }
+                if (t != cur) {
+                    if (cur >= 0) {
+                        const int sl = (first == b0) ? lane : 32 + cur;
+                        S.rp[sl] = pp;
+                        S.rx[sl] = gx;
+                        S.ry[sl] = gy;
+                        if constexpr (D == 3) S.rz[sl] = gz;
                     }
-                    if (r2 > T(0)) {  // the self pair is skipped
-                        if (a.count_in) ++nin;
-                        const T q = S.sq[j];
-                        const T xc = fma(T(2), s, T(-1));
-                        T fa = cA[NA - 1], fb = cB[NH - 1];
+                    cur = t;
+                    first = i;
+                    pp = gx = gy = gz = T(0);
+                }
+                const T xt = S.tx[t], yt = S.ty[t];
+                const T zt = (D == 3) ? S.tz[t] : T(0);
+                T dx = xt - S.sx[j], dy = yt - S.sy[j];
+                T dz = (D == 3) ? zt - S.sz[j] : T(0);
+                T r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
+                T s = r2 * h2inv;
+                if constexpr (kLo) {
+                    if (s < a.close_s) {
+                        // close pair: (x_hi - y_hi) + (x_lo - y_lo); the hi difference is exact
+                        dx = (xt - S.sx[j]) + (S.tlx[t] - S.lx[j]);
+                        dy = (yt - S.sy[j]) + (S.tly[t] - S.ly[j]);
+                        if constexpr (D == 3) dz = (zt - S.sz[j]) + (S.tlz[t] - S.lz[j]);
+                        r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
+                        s = r2 * h2inv;
+                    }
+                }
+                if (r2 > T(0)) {  // the self pair is skipped
+                    if (a.count_in) ++nin;
+                    const T q = S.sq[j];
+                    const T xc = fma(T(2), s, T(-1));
+                    T fa = cA[NA - 1], fb = cB[NH - 1];
 #pragma unroll
-                        for (int m = NH - 2; m >= 0; --m) {
-                            if (m < NA - 1) fa = fma(fa, xc, cA[m]);
-                            fb = fma(fb, xc, cB[m]);
-                        }
-                        if constexpr (D == 3) {
-                            // R = (1 - t A)/(4 pi r); grad R = -(1 - t A + t B) dr / (4 pi r^3)
-                            const T rinv = fast_rsqrt(r2);
-                            const T tt = r2 * rinv * hinv;
-                            const T num = fma(-tt, fa, T(1));
-                            pp = q * num * rinv;
-                            const T gf = -q * fma(tt, fb, num) * rinv * rinv * rinv;
-                            gx = gf * dx;
-                            gy = gf * dy;
-                            gz = gf * dz;
-                        } else {
-                            // R = -log(s)/(4 pi) - A(s); grad R = -sqrt(1-s) S(s) dr/(2 pi r^2)
-                            pp = q * fma(-clog, near_log2(s), -fa);
-                            const T gf = -q * near_sqrt_pos(T(1) - s) * fb * near_rcp(r2);
-                            gx = gf * dx;
-                            gy = gf * dy;
-                        }
+                    for (int m = NH - 2; m >= 0; --m) {
+                        if (m < NA - 1) fa = fma(fa, xc, cA[m]);
+                        fb = fma(fb, xc, cB[m]);
+                    }
+                    if constexpr (D == 3) {
+                        // R = (1 - t A)/(4 pi r); grad R = -(1 - t A + t B) dr / (4 pi r^3)
+                        const T rinv = fast_rsqrt(r2);
+                        const T tt = r2 * rinv * hinv;
+                        const T num = fma(-tt, fa, T(1));
+                        pp = fma(q * num, rinv, pp);
+                        const T gf = -q * fma(tt, fb, num) * rinv * rinv * rinv;
+                        gx = fma(gf, dx, gx);
+                        gy = fma(gf, dy, gy);
+                        gz = fma(gf, dz, gz);
+                    } else {
+                        // R = -log(s)/(4 pi) - A(s); grad R = -sqrt(1-s) S(s) dr/(2 pi r^2)
+                        pp = fma(q, fma(-clog, near_log2(s), -fa), pp);
+                        const T gf = -q * near_sqrt_pos(T(1) - s) * fb * near_rcp(r2);
+                        gx = fma(gf, dx, gx);
+                        gy = fma(gf, dy, gy);
                     }
                 }
-                // segmented inclusive scan keyed by t (keys are non-decreasing across lanes)
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const T pv = __shfl_up_sync(kFull, pp, o), xv = __shfl_up_sync(kFull, gx, o);
-                    const T yv = __shfl_up_sync(kFull, gy, o);
-                    const T zv = (D == 3) ? __shfl_up_sync(kFull, gz, o) : T(0);
-                    const int tv = __shfl_up_sync(kFull, t, o);
-                    if (lane >= o && tv == t) {
-                        pp += pv;
-                        gx += xv;
-                        gy += yv;
-                        if (D == 3) gz += zv;
-                    }
-                }
-                const int tn = __shfl_down_sync(kFull, t, 1);
-                if (valid && (lane == 31 || tn != t)) {  // last lane of target t's run
-                    S.ap[t] += pp;
-                    S.agx[t] += gx;
-                    S.agy[t] += gy;
-                    if constexpr (D == 3) S.agz[t] += gz;
-                }
-                __syncwarp();
             }
-            if (own) {
-                kp.add(S.ap[lane]);
-                kx.add(S.agx[lane]);
-                ky.add(S.agy[lane]);
-                if constexpr (D == 3) kz.add(S.agz[lane]);
+            if (cur >= 0) {
+                const int sl = (first == b0) ? lane : 32 + cur;
+                S.rp[sl] = pp;
+                S.rx[sl] = gx;
+                S.ry[sl] = gy;
+                if constexpr (D == 3) S.rz[sl] = gz;
+            }
+            __syncwarp();
+            // ---- lane t adds its target's runs in queue order to the compensated sums
+            if (own && my_end > my_start) {
+                const int k0 = my_start / R;
+                const int s0 = (my_start == k0 * R) ? k0 : 32 + lane;
+                T cp = S.rp[s0], cx = S.rx[s0], cy = S.ry[s0], cz = (D == 3) ? S.rz[s0] : T(0);
+                for (int k = k0 + 1; k * R < my_end; ++k) {
+                    cp += S.rp[k];
+                    cx += S.rx[k];
+                    cy += S.ry[k];
+                    if constexpr (D == 3) cz += S.rz[k];
+                }
+                kp.add(cp);
+                kx.add(cx);
+                ky.add(cy);
+                if constexpr (D == 3) kz.add(cz);
             }
             __syncwarp();
         }
