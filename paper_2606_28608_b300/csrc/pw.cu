@@ -692,6 +692,61 @@ __global__ void __launch_bounds__(32) k_leaf_eval(const int4* __restrict__ list,
 // compile-time loop bounds: fully unrolled contractions, no run-time integer division, lanes
 // along the contiguous index of every shared-memory operand.
 
+// Outgoing plane waves of one box from its moments q (shared memory), by the calling block.
+// The Chebyshev coefficients of exp(-i a t) are real for even m (the cosine) and imaginary
+// for odd m (the sine), even and odd in k respectively:
+//   Co[k][2j] = ce[|k|][j],  Co[k][2j+1] = i sgn(k) so[|k|][j].
+// Stage 1: A[k0][m1] = sum_m0 Co[k0][m0] Q[m0][m1]      (A.x from even m0, A.y from odd m0)
+// Stage 2: E = sum_j ce[k1][j] A[k0][2j],  O = sum_j so[k1][j] A[k0][2j+1]  (k1 >= 0),
+//          out[k0][+-k1] = E +- i O.
+// Shared scratch (T): ce, so [K+1][P/2] (rows by k), ceT, soT [P/2][K+1] (rows by j), and
+// A [K+1][P] complex.  Ends with the block's stores issued.
+template <typename T, int P, int K>
+__device__ void pw_out_box(const T* q, T* scratch, const C2<T>* __restrict__ Cog, C2<T>* __restrict__ o) {
+    constexpr int N1 = 2 * K + 1, H = P / 2, KH = K + 1;
+    T* ce = scratch;           // [KH][H]
+    T* so = ce + KH * H;       // [KH][H]
+    T* ceT = so + KH * H;      // [H][KH]
+    T* soT = ceT + H * KH;     // [H][KH]
+    C2<T>* A = reinterpret_cast<C2<T>*>(soT + H * KH);  // [KH][P]
+    for (int i = threadIdx.x; i < KH * H; i += blockDim.x) {
+        const int k = i / H, j = i % H;
+        const T e = Cog[(k + K) * P + 2 * j].x, od = Cog[(k + K) * P + 2 * j + 1].y;
+        ce[k * H + j] = e;
+        so[k * H + j] = od;
+        ceT[j * KH + k] = e;
+        soT[j * KH + k] = od;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < KH * P; it += blockDim.x) {
+        const int k0 = it / P, m1 = it % P;
+        T ax = T(0), ay = T(0);
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            ax = fma(ce[k0 * H + j], q[(2 * j) * P + m1], ax);
+            ay = fma(so[k0 * H + j], q[(2 * j + 1) * P + m1], ay);
+        }
+        A[k0 * P + m1] = C2<T>{ax, ay};
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < KH * KH; it += blockDim.x) {
+        const int k0 = it / KH, k1 = it % KH;
+        T ex = T(0), ey = T(0), ox = T(0), oy = T(0);
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            const C2<T> ae = A[k0 * P + 2 * j], ao = A[k0 * P + 2 * j + 1];
+            const T c = ceT[j * KH + k1], s = soT[j * KH + k1];
+            ex = fma(c, ae.x, ex);
+            ey = fma(c, ae.y, ey);
+            ox = fma(s, ao.x, ox);
+            oy = fma(s, ao.y, oy);
+        }
+        // i O = (-oy, ox)
+        o[k0 * N1 + K + k1] = C2<T>{ex - oy, ey + ox};
+        if (k1 > 0) o[k0 * N1 + K - k1] = C2<T>{ex + oy, ey - ox};
+    }
+}
+
 // Direct moments of the boxes that send outgoing plane waves:
 //   Q_b[m0][m1] = sum_{y in b} q_y T_m0(t0(y)) T_m1(t1(y)),  t = 2 (y - c_b) / h_b,
 // the same polynomial projection the merges of the child moments produce (the re-expansions
@@ -700,8 +755,9 @@ __global__ void __launch_bounds__(32) k_leaf_eval(const int4* __restrict__ list,
 // to the box plus the leaf centre's offset, (2 i_leaf + 1) 2^(l_b - l_leaf) - (2 i_b + 1),
 // which is exact in T.  One block per (box, segment of at most kDirectSeg sources); eight
 // groups of 16 threads split the segment, each thread owns a (P/4) x (P/4) tile; the group
-// partials meet in shared memory and the block writes its partial to its own slot (the
-// outgoing kernel sums a box's slots in a fixed order).
+// partials meet in shared memory.  A box of one segment goes straight on to its outgoing
+// plane waves; a box of several writes partials to its slots, and the block that completes
+// the box sums them in slot order and computes the outgoing waves.
 constexpr int kDirectSeg = 1024;
 template <typename T>
 struct V2;
@@ -714,11 +770,13 @@ struct V2<double> {
     using type = double2;
 };
 
-template <typename T, int P>
-__global__ void __launch_bounds__(128) k_moments_direct2d(const int4* __restrict__ items, const T* __restrict__ src4,
+template <typename T, int P, int K>
+__global__ void __launch_bounds__(128) k_moments_direct2d(const int4* __restrict__ items, const int4* __restrict__ obox,
+                                                          const T* __restrict__ src4,
                                                           const int* __restrict__ src_leaf,
                                                           const int4* __restrict__ bcoord, T* __restrict__ part,
-                                                          double inv_rc) {
+                                                          int* __restrict__ seg_done, C2<T>* __restrict__ out,
+                                                          const C2<T>* __restrict__ Cog, double inv_rc) {
     using T2 = typename V2<T>::type;
     // row stride: an odd number of pairs (conflict-free row stores), and rows s, s + 1 (the two
     // 16-lane groups of a warp) offset by 2 mod 32 words so their tile loads use disjoint banks
@@ -727,8 +785,9 @@ __global__ void __launch_bounds__(128) k_moments_direct2d(const int4* __restrict
     extern __shared__ __align__(16) unsigned char smraw[];
     T* A = reinterpret_cast<T*>(smraw);  // [NS][S]  q T_m(t0)
     T* B = A + NS * S;                   // [NS][S]  T_m(t1)
-    const int4 it = items[blockIdx.x];   // (first source, count, partial slot, box)
-    const int4 bc = bcoord[it.w];        // (i0, i1, level, -)
+    const int4 it = items[blockIdx.x];   // (first source, count, partial slot, out slot)
+    const int4 ob = obox[it.w];          // (first partial slot, segments, box, -)
+    const int4 bc = bcoord[ob.z];        // (i0, i1, level, -)
     const T scale = T(2.0 * inv_rc * double(1LL << bc.z));
     const T ob0 = T(2 * bc.x + 1), ob1 = T(2 * bc.y + 1);
     const int grp = threadIdx.x >> 4, ti = (threadIdx.x >> 2) & 3, tj = threadIdx.x & 3;
@@ -788,81 +847,34 @@ __global__ void __launch_bounds__(128) k_moments_direct2d(const int4* __restrict
 #pragma unroll
         for (int c = 0; c < TP; ++c) red[grp * PP + (ti * TP + r) * P + tj * TP + c] = acc[r][c];
     __syncthreads();
-    T* dst = part + size_t(it.z) * PP;
+    T* q = red + 8 * PP;  // the box's moments [PP]
+    T* scr = q + PP;      // outgoing-transform scratch
     for (int i = threadIdx.x; i < PP; i += blockDim.x) {
         T s = T(0);
 #pragma unroll
         for (int g = 0; g < 8; ++g) s += red[g * PP + i];
-        dst[i] = s;
+        q[i] = s;
+        if (ob.y > 1) part[size_t(it.z) * PP + i] = s;
     }
-}
-
-// Outgoing plane waves from the summed partial moments, one block per box.  The
-// Chebyshev coefficients of exp(-i a t) are real for even m (the cosine) and imaginary for
-// odd m (the sine), even and odd in k respectively:
-//   Co[k][2j] = ce[|k|][j],  Co[k][2j+1] = i sgn(k) so[|k|][j].
-// Stage 1: A[k0][m1] = sum_m0 Co[k0][m0] Q[m0][m1]      (A.x from even m0, A.y from odd m0)
-// Stage 2: E = sum_j ce[k1][j] A[k0][2j],  O = sum_j so[k1][j] A[k0][2j+1]  (k1 >= 0),
-//          out[k0][+-k1] = E +- i O.
-// List entry: (first partial slot, number of slots); the box's out slot is its index.
-template <typename T, int P, int K>
-__global__ void __launch_bounds__(128) k_pw_out2d_p(const int2* __restrict__ list, int nbox,
-                                                    const T* __restrict__ part, C2<T>* __restrict__ out,
-                                                    const C2<T>* __restrict__ Cog) {
-    constexpr int N1 = 2 * K + 1, NPW = (K + 1) * N1, H = P / 2, PP = P * P;
-    __shared__ T ce[K + 1][H], so[K + 1][H];    // rows by k (stage 1: k broadcast)
-    __shared__ T ceT[H][K + 1], soT[H][K + 1];  // rows by j (stage 2: lanes along k1)
-    __shared__ T q[PP];
-    __shared__ C2<T> A[K + 1][P];
-    for (int i = threadIdx.x; i < (K + 1) * H; i += blockDim.x) {
-        const int k = i / H, j = i % H;
-        const T e = Cog[(k + K) * P + 2 * j].x, o = Cog[(k + K) * P + 2 * j + 1].y;
-        ce[k][j] = e;
-        so[k][j] = o;
-        ceT[j][k] = e;
-        soT[j][k] = o;
-    }
-    {
-        const int b = blockIdx.x;  // one block per box: resident blocks overlap their loads
-        if (b >= nbox) return;
-        const int2 e = list[b];
+    if (ob.y > 1) {
+        // several segments: the block that completes the box sums the partials in slot order
+        // (the counter only decides which block does it) and goes on to the outgoing waves
+        __shared__ int s_last;
+        __threadfence();
         __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(seg_done + it.w, 1) == ob.y - 1;
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
         for (int i = threadIdx.x; i < PP; i += blockDim.x) {
-            const T* src = part + size_t(e.x) * PP + i;
-            T s = src[0];
-            for (int u = 1; u < e.y; ++u) s += src[size_t(u) * PP];
+            const T* src = part + size_t(ob.x) * PP + i;
+            T s = __ldcg(src);
+            for (int u = 1; u < ob.y; ++u) s += __ldcg(src + size_t(u) * PP);
             q[i] = s;
         }
-        __syncthreads();
-        for (int it = threadIdx.x; it < (K + 1) * P; it += blockDim.x) {
-            const int k0 = it / P, m1 = it % P;
-            T ax = T(0), ay = T(0);
-#pragma unroll
-            for (int j = 0; j < H; ++j) {
-                ax = fma(ce[k0][j], q[(2 * j) * P + m1], ax);
-                ay = fma(so[k0][j], q[(2 * j + 1) * P + m1], ay);
-            }
-            A[k0][m1] = C2<T>{ax, ay};
-        }
-        __syncthreads();
-        C2<T>* o = out + size_t(b) * NPW;
-        for (int it = threadIdx.x; it < (K + 1) * (K + 1); it += blockDim.x) {
-            const int k0 = it / (K + 1), k1 = it % (K + 1);
-            T ex = T(0), ey = T(0), ox = T(0), oy = T(0);
-#pragma unroll
-            for (int j = 0; j < H; ++j) {
-                const C2<T> ae = A[k0][2 * j], ao = A[k0][2 * j + 1];
-                const T c = ceT[j][k1], s = soT[j][k1];
-                ex = fma(c, ae.x, ex);
-                ey = fma(c, ae.y, ey);
-                ox = fma(s, ao.x, ox);
-                oy = fma(s, ao.y, oy);
-            }
-            // i O = (-oy, ox)
-            o[k0 * N1 + K + k1] = C2<T>{ex - oy, ey + ox};
-            if (k1 > 0) o[k0 * N1 + K - k1] = C2<T>{ex + oy, ey - ox};
-        }
     }
+    __syncthreads();
+    pw_out_box<T, P, K>(q, scr, Cog, out + size_t(it.w) * ((K + 1) * (2 * K + 1)));
 }
 
 // translation + incoming, one block per box (list entry: local slot, level, 9 out slots).
@@ -1238,6 +1250,8 @@ struct PwImpl {
     int* d_src_leaf = nullptr;  // leaf box of every sorted source
     int4* d_bcoord = nullptr;   // (i0, i1, level, 0) per box
     void* d_part = nullptr;     // partial moments [nditems][p p]
+    int4* d_obox = nullptr;     // per out slot: (first partial slot, segments, box, 0)
+    int* d_seg_done = nullptr;  // per out slot: segments finished in this evaluation
     // single-launch downward pass with folded leaf evaluation (2D compile-time orders)
     DownItem* d_down_items = nullptr;
     int ndown_items = 0;
@@ -1443,7 +1457,7 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     // 2D compile-time orders: the out boxes' moments straight from their sources, in
     // segments of at most kDirectSeg; the out list becomes (first partial slot, count)
     I->direct2d = direct2d_orders(I->dims, pw->mixed);
-    std::vector<int4> ditems;
+    std::vector<int4> ditems, obox;
     std::vector<int> src_leaf;
     std::vector<int4> bcoord;
     if (I->direct2d) {
@@ -1451,13 +1465,15 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         for (int b = 0; b < nb; ++b)
             if (oslot[b] >= 0) box_of_out[oslot[b]] = b;
         int npart = 0;
+        obox.resize(nout);
         for (int o = 0; o < nout; ++o) {
             const int b = box_of_out[o];
             const int64_t s0 = t.src_begin[b], ns = t.src_end[b] - t.src_begin[b];
             const int first = npart;
             for (int64_t c = 0; c < ns; c += kDirectSeg)
-                ditems.push_back(make_int4(int(s0 + c), int(std::min<int64_t>(kDirectSeg, ns - c)), npart++, b));
+                ditems.push_back(make_int4(int(s0 + c), int(std::min<int64_t>(kDirectSeg, ns - c)), npart++, o));
             outl[o] = make_int2(first, npart - first);
+            obox[o] = make_int4(first, npart - first, b, 0);
         }
         // largest segments first: the long blocks start in the first wave
         std::stable_sort(ditems.begin(), ditems.end(), [](const int4& a, const int4& b) { return a.y > b.y; });
@@ -1582,6 +1598,8 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         if ((r = pw_upload(pw, &I->d_down_items, ditems_down, stream))) return r;
         if ((r = pw_alloc(pw, &I->d_down_flags, size_t(I->ndown_items) + 3))) return r;
         if ((r = pw_upload(pw, &I->d_ditems, ditems, stream))) return r;
+        if ((r = pw_upload(pw, &I->d_obox, obox, stream))) return r;
+        if ((r = pw_alloc(pw, &I->d_seg_done, size_t(std::max(nout, 1))))) return r;
         if ((r = pw_upload(pw, &I->d_src_leaf, src_leaf, stream))) return r;
         if ((r = pw_upload(pw, &I->d_bcoord, bcoord, stream))) return r;
         if ((r = pw_alloc(pw, &p, size_t(std::max(I->nditems, 1)) * I->dims.np * ts))) return r;
@@ -1631,14 +1649,20 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     if (phase == 0 && fixed2d && I->nditems > 0) {
         const T* s4 = static_cast<const T*>(pw->d_src4);
         T* part = static_cast<T*>(I->d_part);
-        auto direct = [&](auto kern, int P) {
-            const size_t smb = ts * std::max(2 * 128 * (P == 24 ? 34 : P + 2), 8 * P * P);
+        if (cudaMemsetAsync(I->d_seg_done, 0, size_t(std::max(I->nout, 1)) * sizeof(int), s) != cudaSuccess)
+            return PDMK_ERR_CUDA;
+        C2<T>* outw = static_cast<C2<T>*>(I->d_out);
+        const C2<T>* Cot = static_cast<const C2<T>*>(I->d_Co);
+        auto direct = [&](auto kern, int P, int K) {
+            // staging rows | (group partials, moments, outgoing scratch)
+            const size_t smb = ts * std::max(2 * 128 * (P == 24 ? 34 : P + 2), 9 * P * P + 4 * (K + 1) * P);
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
-            kern<<<I->nditems, 128, smb, s>>>(I->d_ditems, s4, I->d_src_leaf, I->d_bcoord, part, inv_rc);
+            kern<<<I->nditems, 128, smb, s>>>(I->d_ditems, I->d_obox, s4, I->d_src_leaf, I->d_bcoord, part,
+                                              I->d_seg_done, outw, Cot, inv_rc);
         };
-        if (pd.p == 16) direct(k_moments_direct2d<T, 16>, 16);
-        else if (pd.p == 24) direct(k_moments_direct2d<T, 24>, 24);
-        else direct(k_moments_direct2d<T, 32>, 32);
+        if (pd.p == 16) direct(k_moments_direct2d<T, 16, 9>, 16, 9);
+        else if (pd.p == 24) direct(k_moments_direct2d<T, 24, 16>, 24, 16);
+        else direct(k_moments_direct2d<T, 32, 23>, 32, 23);
         ++pw->launches;
     }
     if (phase == 0 && I->nleafq > 0) {
@@ -1682,15 +1706,9 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
             ++pw->launches;
         }
     }
-    // 3. outgoing plane waves (all levels)
-    if (phase == 1 && I->nout > 0 && fixed2d) {
-        const int g = I->nout;  // one block per box
-        const T* part = static_cast<const T*>(I->d_part);
-        if (pd.p == 16) k_pw_out2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_outl, I->nout, part, out, Co);
-        else if (pd.p == 24) k_pw_out2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_outl, I->nout, part, out, Co);
-        else k_pw_out2d_p<T, 32, 23><<<g, 128, 0, s>>>(I->d_outl, I->nout, part, out, Co);
-        ++pw->launches;
-    } else if (phase == 1 && I->nout > 0) {
+    // 3. outgoing plane waves (all levels); fused into the moments launch for the compile-time
+    //    2D orders
+    if (phase == 1 && I->nout > 0 && !fixed2d) {
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + 2 * size_t(pd.n1) * pd.p);
         cudaFuncSetAttribute(k_pw_out<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_pw_out<T, D><<<I->nout, 128, sm, s>>>(I->d_outl, Q, out, Co, pd, std::min(I->KC, 16));
@@ -1791,6 +1809,7 @@ void pw_free_sources(PwPlan* pw) {
         I->d_down = nullptr; I->d_eval = nullptr; I->d_Q = I->d_out = I->d_L = nullptr;
         I->nleafq = I->nout = I->nin = I->neval = 0;
         I->d_ditems = nullptr; I->d_src_leaf = nullptr; I->d_bcoord = nullptr; I->d_part = nullptr;
+        I->d_obox = nullptr; I->d_seg_done = nullptr;
         I->nditems = 0;
         I->d_down_items = nullptr; I->d_down_flags = nullptr;
         I->ndown_items = 0;
