@@ -1178,21 +1178,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_down_persist2d(
                 const T T4 = tv[4], D4 = dv[4];
                 using T2 = typename V2<T>::type;
                 const T* a = Lch + c * PP + q * P;
+                // all R rows in one pass over m1: 2 R independent accumulation chains
+                T s[R], sd[R];
+#pragma unroll
+                for (int k = 0; k < R; ++k) s[k] = sd[k] = T(0);
+#pragma unroll
+                for (int m1 = 0; m1 < P; m1 += 2) {
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        const T2 v = reinterpret_cast<const T2*>(a + k * 4 * P)[m1 / 2];
+                        s[k] = fma(v.x, b1[m1], s[k]);
+                        sd[k] = fma(v.x, d1[m1], sd[k]);
+                        s[k] = fma(v.y, b1[m1 + 1], s[k]);
+                        sd[k] = fma(v.y, d1[m1 + 1], sd[k]);
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    T s = 0, sd = 0;
-                    const T2* row = reinterpret_cast<const T2*>(a + k * 4 * P);
-#pragma unroll
-                    for (int m1 = 0; m1 < P; m1 += 2) {
-                        const T2 v = row[m1 / 2];
-                        s = fma(v.x, b1[m1], s);
-                        sd = fma(v.x, d1[m1], sd);
-                        s = fma(v.y, b1[m1 + 1], s);
-                        sd = fma(v.y, d1[m1 + 1], sd);
-                    }
-                    phi = fma(A, s, phi);
-                    g0 = fma(Dd, s, g0);
-                    g1 = fma(A, sd, g1);
+                    phi = fma(A, s[k], phi);
+                    g0 = fma(Dd, s[k], g0);
+                    g1 = fma(A, sd[k], g1);
                     const T An = fma(T(2) * T4, A, -Am);
                     const T Dn = fma(T(2) * D4, A, fma(T(2) * T4, Dd, -Dm));
                     Am = A;
