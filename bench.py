@@ -108,7 +108,7 @@ def oracle_sample(g, idx, nthreads=None):
     return pot, grad, time.perf_counter() - t0
 
 
-def stage_flops(info, d, leaf_folded):
+def stage_flops(info, d, leaf_folded, out_folded):
     """Algorithmic flops of each timed stage, from the plan's work counts and the fixed
     per-unit costs of each kernel's formula (documented with the kernels):
       spread      per point: w^d products + d*w window series of n_W terms (2 flops/term)
@@ -118,7 +118,8 @@ def stage_flops(info, d, leaf_folded):
       pw_upward   per (out box, source) pair: the p^d moment outer product (2 flops each) and
                   2 d p Chebyshev recurrence flops; per merge parent (generic path) 12 p^3 (2D)
                   or 8 * 3 * 2 p^{d+1} (3D separable re-expansion)
-      pw_out      per box (2D parity form): 2 (K+1) p^2 + 4 (K+1)^2 p
+      pw_out      per box (2D parity form): 2 (K+1) p^2 + 4 (K+1)^2 p; credited to pw_upward
+                  where the moments launch computes the outgoing waves itself
       pw_translate_in per box (2D parity form): ~100 (K+1)^2 (nine phased colleagues, both
                   k1 signs) + 4 (K+1)^2 p + 2 (K+1) p^2
       pw_downward per parent 12 p^3 (2D) or 8 * 3 * 2 p^{d+1} (3D), plus the leaf evaluation
@@ -145,6 +146,9 @@ def stage_flops(info, d, leaf_folded):
         out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** d + 8 * (K + 1) * n1 * p ** (d - 1) * (d - 1))
         out["pw_translate_in"] = info["n_pw_boxes_in"] * (3 ** d * 14 * npw + 8 * (K + 1) * n1 * p ** (d - 1) * (d - 1)
                                                           + 3 * (K + 1) * p ** d)
+    if out_folded:
+        out["pw_upward"] += out["pw_out"]
+        out["pw_out"] = 0
     leaf = info["pw_eval_targets"] * 4 * p ** d
     out["pw_downward"] = info["pw_down_parents"] * merge_unit + (leaf if leaf_folded else 0)
     out["pw_leaf_eval"] = 0 if leaf_folded else leaf
@@ -154,11 +158,12 @@ def stage_flops(info, d, leaf_folded):
 # DRAM bytes (read + write) per launch of each stage's main kernel on this workload, from
 # one `ncu --set full` capture of the kernel as it stands (profiles/ holds the summaries);
 # None where no capture of the current kernel exists
-STAGE_TRAFFIC = {"nearfield": 17896960}
+STAGE_TRAFFIC = {"nearfield": 17895424, "pw_upward": 6190336, "pw_downward": 13728768}
 
 STAGE_KERNELS = {
     "spread": "k_spread_halo + k_fold_whole", "interp": "k_interp_halo", "nearfield": "k_near_warp",
-    "pw_upward": "k_moments_direct2d", "pw_out": "k_pw_out2d_p", "pw_translate_in": "k_pw_in2d_p",
+    "pw_upward": "k_moments_direct2d (outgoing waves folded in)", "pw_out": "k_pw_out",
+    "pw_translate_in": "k_pw_in2d_p",
     "pw_downward": "k_down_persist2d (leaf evaluation folded in)", "pw_leaf_eval": "k_leaf_eval",
 }
 
@@ -329,7 +334,9 @@ def main():
         fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
         # the single-launch downward pass evaluates the leaves itself (its leaf stage is empty)
         leaf_folded = stage_acc.get("pw_leaf_eval", 0.0) < 0.05 * stage_acc.get("pw_downward", 0.0)
-        fl = stage_flops(pinfo, d, leaf_folded)
+        # likewise the moments launch computes the outgoing waves (its outgoing stage is empty)
+        out_folded = stage_acc.get("pw_out", 0.0) < 0.05 * stage_acc.get("pw_upward", 0.0)
+        fl = stage_flops(pinfo, d, leaf_folded, out_folded)
         stages = {k: round(v, 4) for k, v in stage_acc.items()}
         per_stage = {}
         for k, f in fl.items():
