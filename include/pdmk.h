@@ -145,6 +145,28 @@ int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where);
  */
 int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad);
 
+/*
+ * pdmk_eval_adjoint -- vector-Jacobian product of pdmk_eval (the backward pass of a loss on
+ * the potential at the sources).  The evaluation is linear in the charges, Phi = A q, and A is
+ * symmetric: its entries are the periodic pair kernel G_p(y_i - y_j) (Eq. (1.1)-(1.2), zero
+ * mean under the tin-foil convention, Sec. 1), the mean correction (a constant, Eq. (3.17))
+ * and the diagonal self part, all even in the separation.  For the upstream gradient
+ * g = dLoss/dPhi (g_pot, n values):
+ *     g_q = dLoss/dq = A g                              (n values)
+ *     g_y = dLoss/dy = g grad Phi[q] + q grad Phi[g]    (n x d, row-major, caller's frame)
+ * computed with two evaluations on the device (charges q, then charges g; neutrality of g is
+ * not required) and a combine kernel; the plan's charges are the caller's again on return.
+ * g_q or g_y may be NULL (not wanted).  g_grad (an upstream gradient on the returned field)
+ * must be NULL: it would need second derivatives of the kernel.  g_x must be NULL: the targets
+ * are the sources, so their derivative is part of g_y.  where = PDMK_HOST / PDMK_DEVICE for
+ * all pointers.  The first call after pdmk_set_sources allocates n (4 + 2 d) doubles of
+ * scratch (kept until the next pdmk_set_sources or pdmk_plan_destroy).  Ordered after the
+ * plan's stream like pdmk_eval; a host call returns after the copies.
+ * Errors: BAD_ARG, NOT_READY, OOM, CUDA, TIMEOUT.
+ */
+int pdmk_eval_adjoint(pdmk_plan plan, const double* g_pot, const double* g_grad, double* g_q, double* g_y,
+                      double* g_x, int where);
+
 /* Per-stage device times (ms) of the last pdmk_eval when opts.profile = 1.  names/ms
  * receive up to cap entries; returns the number of stages (or a negative error).     */
 int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, int cap);

@@ -71,6 +71,8 @@ def lib():
         L.pdmk_eval.restype = ctypes.c_int
         L.pdmk_eval_noalloc.argtypes = [P, P, P]
         L.pdmk_eval_noalloc.restype = ctypes.c_int
+        L.pdmk_eval_adjoint.argtypes = [P, P, P, P, P, P, ctypes.c_int]
+        L.pdmk_eval_adjoint.restype = ctypes.c_int
         L.pdmk_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.pdmk_stage_times.restype = ctypes.c_int
         L.pdmk_get_info.argtypes = [P, ctypes.POINTER(Info)]
@@ -228,6 +230,29 @@ class Plan:
         rc = lib().pdmk_eval_noalloc(self._h, pot.data_ptr(), grad.data_ptr() if grad is not None else None)
         if rc != 0:
             raise PdmkError(rc, "pdmk_eval_noalloc")
+
+    def eval_adjoint(self, g_pot, want_q: bool = True, want_y: bool = True):
+        """Vector-Jacobian product of the evaluation (pdmk_eval_adjoint): for the upstream
+        gradient g_pot = dLoss/dPhi (n values) returns (dLoss/dq, dLoss/dy) as numpy arrays for
+        numpy input, or CUDA float64 tensors for a CUDA tensor input (None where not wanted)."""
+        if _is_torch(g_pot):
+            import torch
+            g = g_pot.contiguous().to(torch.float64)
+            gq = torch.empty(self.n, dtype=torch.float64, device=g.device) if want_q else None
+            gy = torch.empty((self.n, self.d), dtype=torch.float64, device=g.device) if want_y else None
+            rc = lib().pdmk_eval_adjoint(self._h, g.data_ptr(), None, gq.data_ptr() if want_q else None,
+                                         gy.data_ptr() if want_y else None, None, PDMK_DEVICE)
+        else:
+            g = np.ascontiguousarray(np.asarray(g_pot, dtype=np.float64).reshape(-1))
+            if g.shape[0] != self.n:
+                raise ValueError("g_pot must have one value per source")
+            gq = np.empty(self.n, dtype=np.float64) if want_q else None
+            gy = np.empty((self.n, self.d), dtype=np.float64) if want_y else None
+            rc = lib().pdmk_eval_adjoint(self._h, g.ctypes.data, None, gq.ctypes.data if want_q else None,
+                                         gy.ctypes.data if want_y else None, None, PDMK_HOST)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_eval_adjoint")
+        return gq, gy
 
     def info(self) -> dict:
         inf = Info()

@@ -7,9 +7,10 @@ diagonal, all even in the separation.  For a loss L(Phi) with upstream gradient 
     dL/dq = A g                              (one evaluation with charges g)
     dL/dy = g * grad Phi[q] + q * grad Phi[g]   (the evaluation's own gradient output)
 
-so the backward pass runs the same CUDA evaluation once more, with charges g.  Gradients that
-flow into the returned field (a loss on forces) would need second derivatives of the kernel;
-they are rejected.
+so the backward pass is the library's adjoint entry point (pdmk_eval_adjoint), which runs
+the same CUDA evaluation with charges q and with charges g and combines them on the device.
+Gradients that flow into the returned field (a loss on forces) would need second derivatives
+of the kernel; they are rejected.
 """
 from __future__ import annotations
 
@@ -29,7 +30,6 @@ class _PeriodicPotential(torch.autograd.Function):
         grad = torch.empty((n, d), dtype=torch.float64, device=y.device)
         plan.eval_device(pot, grad)
         ctx.plan = plan
-        ctx.save_for_backward(q.detach(), grad.detach())
         ctx.mark_non_differentiable(grad)
         return pot, grad
 
@@ -38,16 +38,10 @@ class _PeriodicPotential(torch.autograd.Function):
         if g_grad is not None and bool(torch.any(g_grad != 0)):
             raise RuntimeError("gradients through the returned field need second derivatives "
                                "of the periodic kernel, which this library does not provide")
-        q, grad_q = ctx.saved_tensors
         plan = ctx.plan
-        n, d = grad_q.shape
-        g = g_pot.contiguous().to(torch.float64)
-        plan.set_charges(g)
-        pot_g = torch.empty(n, dtype=torch.float64, device=g.device)
-        grad_g = torch.empty((n, d), dtype=torch.float64, device=g.device)
-        plan.eval_device(pot_g, grad_g)
-        dq = pot_g
-        dy = g[:, None] * grad_q + q[:, None] * grad_g
+        # pdmk_eval_adjoint: dq = A g and dy = g grad Phi[q] + q grad Phi[g], on the device
+        dq, dy = plan.eval_adjoint(g_pot.contiguous().to(torch.float64),
+                                   want_q=ctx.needs_input_grad[1], want_y=ctx.needs_input_grad[0])
         plan.close()
         ctx.plan = None
         return dy, dq, None

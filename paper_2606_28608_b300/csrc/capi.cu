@@ -118,6 +118,7 @@ struct pdmk_plan_s {
     int* d_bin_sub_begin = nullptr;
     void* d_slab = nullptr;
     void* slab_override = nullptr;  // set only for the duration of pdmk_eval_noalloc
+    double* d_adj = nullptr;        // adjoint scratch (n (4 + 2 d) doubles), allocated on first use
     int4* d_t_g0 = nullptr;
     void* d_t_dq = nullptr;
     double* d_pot_near = nullptr;
@@ -658,6 +659,7 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     drop_graph(plan);
     plan->evals_since_setup = 0;
     free_list(plan->src_allocs, &plan->device_bytes);
+    plan->d_adj = nullptr;
     pw_free_sources(&plan->pw);
     const bool mixed = plan->opts.precision == PDMK_MIXED;
     const size_t ts = tsize(plan);
@@ -1382,6 +1384,92 @@ extern "C" int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad) {
     plan->opts.profile = saved_profile ? 1 : 0;
     plan->count_pending = saved_count;
     if (r != PDMK_OK) return r;
+    CK(cudaEventRecord(plan->ev_join, plan->ws));
+    CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
+    return PDMK_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Adjoint (vector-Jacobian product) of the evaluation at the sources.  Phi = A q with A
+// symmetric (pair kernel, zero-mean constant and self part all even in the separation), so
+// for upstream g = dLoss/dPhi:  dLoss/dq = A g  and  dLoss/dy = g grad Phi[q] + q grad Phi[g].
+__global__ void k_adjoint_combine(int64_t n, int d, const double* __restrict__ g, const double* __restrict__ q,
+                                  const double* __restrict__ grad_q, const double* __restrict__ grad_g,
+                                  double* __restrict__ g_y) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n * d; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t t = i / d;
+        g_y[i] = g[t] * grad_q[i] + q[t] * grad_g[i];
+    }
+}
+
+extern "C" int pdmk_eval_adjoint(pdmk_plan plan, const double* g_pot, const double* g_grad, double* g_q, double* g_y,
+                                 double* g_x, int where) {
+    if (!plan || !g_pot || (!g_q && !g_y)) return PDMK_ERR_BAD_ARG;
+    if (g_grad || g_x) {
+        plan_set_msg(plan, g_grad ? "upstream gradients on the returned field need second derivatives of the kernel"
+                                  : "the targets are the sources: their derivative is part of g_y");
+        return PDMK_ERR_BAD_ARG;
+    }
+    if (!plan->ready) return PDMK_ERR_NOT_READY;
+    if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+        *plan->pw.h_err = 0;
+        return PDMK_ERR_TIMEOUT;
+    }
+    const int64_t n = plan->n;
+    const int d = plan->d;
+    if (n == 0) return PDMK_OK;
+    if (!plan->d_adj) {
+        double* p = nullptr;
+        int rr = dalloc(plan, plan->src_allocs, &p, size_t(n) * (4 + 2 * d));
+        if (rr != PDMK_OK) return rr;
+        plan->d_adj = p;
+    }
+    double* q_save = plan->d_adj;
+    double* gdev = q_save + n;
+    double* pot_q = gdev + n;
+    double* pot_g = pot_q + n;
+    double* grad_q = pot_g + n;
+    double* grad_g = grad_q + n * d;
+    const size_t nb = size_t(n) * sizeof(double);
+    CK(cudaEventRecord(plan->ev_fork, plan->stream));
+    CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
+    CK(cudaMemcpyAsync(q_save, plan->d_q_user, nb, cudaMemcpyDeviceToDevice, plan->ws));
+    CK(cudaMemcpyAsync(gdev, g_pot, nb, where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       plan->ws));
+    // both evaluations run eagerly: the plan's captured graph stays keyed to the caller's
+    // outputs of pdmk_eval
+    const bool saved_profile = plan->opts.profile != 0, saved_count = plan->count_pending;
+    plan->opts.profile = 0;
+    plan->count_pending = false;
+    int r = launch_eval(plan, pot_q, grad_q);  // grad Phi[q]
+    if (r == PDMK_OK) {
+        CK(cudaMemcpyAsync(plan->d_q_user, gdev, nb, cudaMemcpyDeviceToDevice, plan->ws));
+        r = set_charges_device(plan, false);
+    }
+    if (r == PDMK_OK) r = launch_eval(plan, pot_g, grad_g);  // Phi[g] = A g, grad Phi[g]
+    // the caller's charges again, whatever happened above
+    cudaMemcpyAsync(plan->d_q_user, q_save, nb, cudaMemcpyDeviceToDevice, plan->ws);
+    const int r2 = set_charges_device(plan, false);
+    plan->opts.profile = saved_profile ? 1 : 0;
+    plan->count_pending = saved_count;
+    if (r != PDMK_OK) return r;
+    if (r2 != PDMK_OK) return r2;
+    double* gy_dev = (where == PDMK_DEVICE) ? g_y : grad_q;  // in place is safe: element-wise
+    if (g_y) {
+        const int blocks = int(std::min<int64_t>((n * d + 255) / 256, 148 * 8));
+        k_adjoint_combine<<<std::max(blocks, 1), 256, 0, plan->ws>>>(n, d, gdev, q_save, grad_q, grad_g, gy_dev);
+        CK(cudaGetLastError());
+    }
+    const cudaMemcpyKind out_kind = where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (g_q) CK(cudaMemcpyAsync(g_q, pot_g, nb, out_kind, plan->ws));
+    if (g_y && where != PDMK_DEVICE) CK(cudaMemcpyAsync(g_y, gy_dev, nb * d, out_kind, plan->ws));
+    if (where != PDMK_DEVICE) {
+        CK(cudaStreamSynchronize(plan->ws));
+        if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+            *plan->pw.h_err = 0;
+            return PDMK_ERR_TIMEOUT;
+        }
+    }
     CK(cudaEventRecord(plan->ev_join, plan->ws));
     CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
     return PDMK_OK;

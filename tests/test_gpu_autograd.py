@@ -61,3 +61,49 @@ def test_general_loss_finite_differences():
         qp = g["q"].copy(); qp[k] += 1.0
         fd = loss(g["y"], qp) - loss(g["y"], g["q"])  # linear in q: exact difference
         assert abs(fd - float(q.grad[k])) <= 1e-8 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("d,precision,tol", [(2, "fp64", 1e-8), (3, "fp64", 1e-8), (2, "mixed", 1e-5)])
+def test_eval_adjoint_against_oracle(d, precision, tol):
+    """pdmk_eval_adjoint with a random upstream g: dq = A g is the oracle's potential for
+    charges g (not neutral), dy = g grad Phi[q] + q grad Phi[g] from the oracle's fields."""
+    _torch()
+    import paper_2606_28608_b300 as P
+    g = W.oblique2d_clusters(1200, seed=31) if d == 2 else W.triclinic3d_clusters(1000, seed=32, nclusters=4)
+    n = len(g["q"])
+    up = np.random.default_rng(2).standard_normal(n)
+    plan = P.Plan(g["L"], 1e-9 if precision == "fp64" else 1e-6, precision=precision)
+    plan.set_sources(g["y"], g["q"])
+    p0, g0 = plan.eval()
+    gq, gy = plan.eval_adjoint(up)
+    p_q, f_q = E.ewald(g["L"], g["y"], g["q"])
+    p_g, f_g = E.ewald(g["L"], g["y"], up)
+    assert np.linalg.norm(gq - p_g) <= tol * np.linalg.norm(p_g)
+    want = up[:, None] * f_q + g["q"][:, None] * f_g
+    assert np.linalg.norm(gy - want) <= 10 * tol * np.linalg.norm(want)
+    # the plan's charges are the caller's again
+    p1, g1 = plan.eval()
+    assert np.array_equal(p0, p1) and np.array_equal(g0, g1)
+    plan.close()
+
+
+def test_eval_adjoint_device_matches_host_and_rejects_field_gradients():
+    torch, _ = _torch()
+    import paper_2606_28608_b300 as P
+    g = W.oblique2d_clusters(3000, seed=33)
+    n = len(g["q"])
+    up = np.random.default_rng(3).standard_normal(n)
+    plan = P.Plan(g["L"], 1e-6, precision="mixed")
+    plan.set_sources(g["y"], g["q"])
+    hq, hy = plan.eval_adjoint(up)
+    dq, dy = plan.eval_adjoint(torch.tensor(up, device="cuda"))
+    assert np.array_equal(hq, dq.cpu().numpy()) and np.array_equal(hy, dy.cpu().numpy())
+    only_q, none_y = plan.eval_adjoint(up, want_y=False)
+    assert none_y is None and np.array_equal(only_q, hq)
+    # an upstream gradient on the returned field is refused (BAD_ARG), nothing is written
+    gg = np.zeros((n, 2))
+    out = np.zeros(n)
+    rc = P.lib().pdmk_eval_adjoint(plan._h, up.ctypes.data, gg.ctypes.data, out.ctypes.data, None, None,
+                                   P.PDMK_HOST)
+    assert rc == -1 and not out.any()
+    plan.close()
