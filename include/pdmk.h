@@ -167,6 +167,34 @@ int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad);
 int pdmk_eval_adjoint(pdmk_plan plan, const double* g_pot, const double* g_grad, double* g_q, double* g_y,
                       double* g_x, int where);
 
+/*
+ * Batches of independent cells (many lattices of uneven N and different shapes evaluated
+ * together).  Each cell is a full plan (Algorithm 1 per cell); one evaluation of every cell is
+ * captured into a single CUDA graph on the batch's own stream, where the cells run as
+ * independent branches.  There is no coupling between cells.
+ *
+ * pdmk_batch_create: ncells cells; d[c] in {2, 3}; L packs each cell's d[c] x d[c] lattice
+ *   (column-major, as pdmk_plan_create) one after another; eps[c] per cell; opts (NULL:
+ *   defaults) applies to every cell.  Errors: those of pdmk_plan_create, BAD_ARG, CUDA.
+ * pdmk_batch_set_sources: offsets (ncells + 1 values, offsets[0] = 0, strictly increasing:
+ *   every cell holds at least one source) place cell c's sources at [offsets[c],
+ *   offsets[c+1]) of q, and its positions at rows offsets[c].. of y with d[c] values per row,
+ *   rows packed cell after cell (row-major within a cell).  where as pdmk_set_sources.
+ *   Allocates the per-cell buffers and, for host evaluations, one staging pair.
+ * pdmk_batch_eval: potential (pot, offsets layout) and gradient (grad, the y layout, or
+ *   NULL) at every source of every cell.  The first call runs eagerly, later calls replay the
+ *   captured graph (re-captured when the output pointers change).  Ordered after the stream
+ *   of opts; a host call returns after the copies.  Errors: NOT_READY, CUDA, TIMEOUT.
+ * pdmk_batch_plan: cell c's plan (for pdmk_get_info; owned by the batch), or NULL.
+ */
+typedef struct pdmk_batch_s* pdmk_batch;
+int pdmk_batch_create(int ncells, const int* d, const double* L, const double* eps, const pdmk_opts* opts,
+                      pdmk_batch* out);
+int pdmk_batch_set_sources(pdmk_batch batch, const int64_t* offsets, const double* y, const double* q, int where);
+int pdmk_batch_eval(pdmk_batch batch, double* pot, double* grad, int where);
+pdmk_plan pdmk_batch_plan(pdmk_batch batch, int cell);
+void pdmk_batch_destroy(pdmk_batch batch);
+
 /* Per-stage device times (ms) of the last pdmk_eval when opts.profile = 1.  names/ms
  * receive up to cap entries; returns the number of stages (or a negative error).     */
 int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, int cap);

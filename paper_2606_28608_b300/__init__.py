@@ -73,6 +73,16 @@ def lib():
         L.pdmk_eval_noalloc.restype = ctypes.c_int
         L.pdmk_eval_adjoint.argtypes = [P, P, P, P, P, P, ctypes.c_int]
         L.pdmk_eval_adjoint.restype = ctypes.c_int
+        L.pdmk_batch_create.argtypes = [ctypes.c_int, P, P, P, ctypes.POINTER(Opts), ctypes.POINTER(P)]
+        L.pdmk_batch_create.restype = ctypes.c_int
+        L.pdmk_batch_set_sources.argtypes = [P, P, P, P, ctypes.c_int]
+        L.pdmk_batch_set_sources.restype = ctypes.c_int
+        L.pdmk_batch_eval.argtypes = [P, P, P, ctypes.c_int]
+        L.pdmk_batch_eval.restype = ctypes.c_int
+        L.pdmk_batch_plan.argtypes = [P, ctypes.c_int]
+        L.pdmk_batch_plan.restype = P
+        L.pdmk_batch_destroy.argtypes = [P]
+        L.pdmk_batch_destroy.restype = None
         L.pdmk_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.pdmk_stage_times.restype = ctypes.c_int
         L.pdmk_get_info.argtypes = [P, ctypes.POINTER(Info)]
@@ -270,3 +280,84 @@ class Plan:
         ms = (ctypes.c_double * 32)()
         n = lib().pdmk_stage_times(self._h, names, ms, 32)
         return {names[i].decode(): ms[i] for i in range(max(n, 0))}
+
+
+class Batch:
+    """Many independent cells evaluated together (pdmk_batch_*): one plan per cell, one CUDA
+    graph per evaluation of all cells.  cells: list of (L, eps); every cell shares the options."""
+
+    def __init__(self, cells, *, precision: str = "fp64", kappa: float = 0.0, n_s: int = 0,
+                 neutrality: int = 1, stream=None):
+        Ls = [np.ascontiguousarray(np.asarray(L, dtype=np.float64)) for L, _ in cells]
+        self.dims = [L.shape[0] for L in Ls]
+        o = Opts()
+        lib().pdmk_default_opts(ctypes.byref(o))
+        o.kappa = kappa
+        o.n_s = n_s
+        o.precision = PDMK_MIXED if precision == "mixed" else PDMK_FP64
+        o.neutrality = neutrality
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        o.stream = stream or None
+        dd = np.asarray(self.dims, dtype=np.int32)
+        Lp = np.ascontiguousarray(np.concatenate([L.T.reshape(-1) for L in Ls]))  # column-major each
+        ee = np.asarray([float(e) for _, e in cells], dtype=np.float64)
+        h = ctypes.c_void_p()
+        rc = lib().pdmk_batch_create(len(cells), dd.ctypes.data, Lp.ctypes.data, ee.ctypes.data, ctypes.byref(o),
+                                     ctypes.byref(h))
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_batch_create")
+        self._h = h
+        self.counts = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().pdmk_batch_destroy(h)
+            except Exception:  # noqa: BLE001
+                pass
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    def set_sources(self, ys, qs):
+        """ys, qs: per-cell lists of host arrays (n_c x d_c positions, n_c charges)."""
+        self.counts = [len(q) for q in qs]
+        off = np.zeros(len(qs) + 1, dtype=np.int64)
+        off[1:] = np.cumsum(self.counts)
+        y = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1) for a in ys]))
+        q = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1) for a in qs]))
+        rc = lib().pdmk_batch_set_sources(self._h, off.ctypes.data, y.ctypes.data, q.ctypes.data, PDMK_HOST)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_batch_set_sources")
+        self._off = off
+
+    def eval(self):
+        """Host evaluation: per-cell lists of potentials and gradients."""
+        ntot = int(self._off[-1])
+        ytot = sum(c * d for c, d in zip(self.counts, self.dims))
+        pot = np.empty(ntot)
+        grad = np.empty(ytot)
+        rc = lib().pdmk_batch_eval(self._h, pot.ctypes.data, grad.ctypes.data, PDMK_HOST)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_batch_eval")
+        pots, grads, yo = [], [], 0
+        for c, (n, d) in enumerate(zip(self.counts, self.dims)):
+            pots.append(pot[self._off[c]:self._off[c + 1]])
+            grads.append(grad[yo:yo + n * d].reshape(n, d))
+            yo += n * d
+        return pots, grads
+
+    def eval_device(self, pot, grad=None):
+        """Device evaluation into packed float64 CUDA tensors (offsets / row layouts)."""
+        rc = lib().pdmk_batch_eval(self._h, pot.data_ptr(), grad.data_ptr() if grad is not None else None,
+                                   PDMK_DEVICE)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_batch_eval")

@@ -1474,3 +1474,186 @@ extern "C" int pdmk_eval_adjoint(pdmk_plan plan, const double* g_pot, const doub
     CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
     return PDMK_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Batches of independent cells: one plan per cell, one evaluation of all cells captured into
+// a single CUDA graph on the batch's stream (cells run concurrently as independent branches).
+struct pdmk_batch_s {
+    std::vector<pdmk_plan> plans;
+    std::vector<int> d;
+    std::vector<int64_t> n, off, yoff;  // per cell: sources, offset of its values, of its rows x d
+    int64_t ntot = 0, ytot = 0;
+    cudaStream_t stream = nullptr;      // the caller's
+    cudaStream_t bs = nullptr;          // the batch's own (graph capture needs a non-default stream)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    double* g_pot = nullptr;
+    double* g_grad = nullptr;
+    double* d_pot = nullptr;   // staging for host outputs
+    double* d_grad = nullptr;
+    int evals = 0;
+    bool ready = false;
+};
+
+extern "C" void pdmk_batch_destroy(pdmk_batch b) {
+    if (!b) return;
+    if (b->bs) cudaStreamSynchronize(b->bs);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (pdmk_plan p : b->plans) pdmk_plan_destroy(p);
+    if (b->d_pot) cudaFree(b->d_pot);
+    if (b->d_grad) cudaFree(b->d_grad);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->bs) cudaStreamDestroy(b->bs);
+    delete b;
+}
+
+extern "C" int pdmk_batch_create(int ncells, const int* d, const double* L, const double* eps, const pdmk_opts* opts,
+                                 pdmk_batch* out) {
+    if (!out || ncells <= 0 || !d || !L || !eps) return PDMK_ERR_BAD_ARG;
+    *out = nullptr;
+    pdmk_batch b = new (std::nothrow) pdmk_batch_s();
+    if (!b) return PDMK_ERR_OOM;
+    pdmk_opts o;
+    if (opts) o = *opts; else pdmk_default_opts(&o);
+    b->stream = static_cast<cudaStream_t>(o.stream);
+    if (cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        pdmk_batch_destroy(b);
+        return PDMK_ERR_CUDA;
+    }
+    size_t loff = 0;
+    for (int c = 0; c < ncells; ++c) {
+        if (d[c] != 2 && d[c] != 3) {
+            pdmk_batch_destroy(b);
+            return PDMK_ERR_BAD_ARG;
+        }
+        pdmk_plan p = nullptr;
+        const int r = pdmk_plan_create(d[c], L + loff, eps[c], &o, &p);
+        if (r != PDMK_OK) {
+            pdmk_batch_destroy(b);
+            return r;
+        }
+        b->plans.push_back(p);
+        b->d.push_back(d[c]);
+        loff += size_t(d[c]) * d[c];
+    }
+    *out = b;
+    return PDMK_OK;
+}
+
+extern "C" int pdmk_batch_set_sources(pdmk_batch b, const int64_t* offsets, const double* y, const double* q,
+                                      int where) {
+    if (!b || !offsets || offsets[0] != 0) return PDMK_ERR_BAD_ARG;
+    pdmk_plan plan = nullptr;
+    const int nc = int(b->plans.size());
+    b->ready = false;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->evals = 0;
+    b->n.assign(nc, 0);
+    b->off.assign(nc, 0);
+    b->yoff.assign(nc, 0);
+    int64_t yo = 0;
+    for (int c = 0; c < nc; ++c) {
+        if (offsets[c + 1] <= offsets[c]) return PDMK_ERR_BAD_ARG;  // every cell holds sources
+        b->n[c] = offsets[c + 1] - offsets[c];
+        b->off[c] = offsets[c];
+        b->yoff[c] = yo;
+        yo += b->n[c] * b->d[c];
+    }
+    b->ntot = offsets[nc];
+    b->ytot = yo;
+    for (int c = 0; c < nc; ++c) {
+        const int r = pdmk_set_sources(b->plans[c], b->n[c], y ? y + b->yoff[c] : nullptr,
+                                       q ? q + b->off[c] : nullptr, where);
+        if (r != PDMK_OK) return r;
+        b->plans[c]->count_pending = false;  // no pair counting inside a batch evaluation
+    }
+    if (b->d_pot) cudaFree(b->d_pot);
+    if (b->d_grad) cudaFree(b->d_grad);
+    b->d_pot = b->d_grad = nullptr;
+    CK(cudaMalloc(reinterpret_cast<void**>(&b->d_pot), size_t(std::max<int64_t>(b->ntot, 1)) * sizeof(double)));
+    CK(cudaMalloc(reinterpret_cast<void**>(&b->d_grad), size_t(std::max<int64_t>(b->ytot, 1)) * sizeof(double)));
+    b->ready = true;
+    return PDMK_OK;
+}
+
+// every cell's evaluation, forked from and joined to the batch stream
+static int batch_launch(pdmk_batch b, double* dp, double* dg) {
+    pdmk_plan plan = nullptr;
+    CK(cudaEventRecord(b->ev_fork, b->bs));
+    for (size_t c = 0; c < b->plans.size(); ++c) {
+        pdmk_plan p = b->plans[c];
+        if (b->n[c] == 0) continue;
+        CK(cudaStreamWaitEvent(p->ws, b->ev_fork, 0));
+        const bool saved_profile = p->opts.profile != 0;
+        p->opts.profile = 0;
+        const int r = launch_eval(p, dp + b->off[c], dg ? dg + b->yoff[c] : nullptr);
+        p->opts.profile = saved_profile ? 1 : 0;
+        if (r != PDMK_OK) return r;
+        CK(cudaEventRecord(p->ev_join, p->ws));
+        CK(cudaStreamWaitEvent(b->bs, p->ev_join, 0));
+    }
+    return PDMK_OK;
+}
+
+extern "C" int pdmk_batch_eval(pdmk_batch b, double* pot, double* grad, int where) {
+    if (!b || !pot) return PDMK_ERR_BAD_ARG;
+    if (!b->ready) return PDMK_ERR_NOT_READY;
+    pdmk_plan plan = nullptr;
+    for (pdmk_plan p : b->plans)
+        if (p->pw.h_err && *reinterpret_cast<volatile int*>(p->pw.h_err)) {
+            *p->pw.h_err = 0;
+            return PDMK_ERR_TIMEOUT;
+        }
+    double* dp = where == PDMK_DEVICE ? pot : b->d_pot;
+    double* dg = grad ? (where == PDMK_DEVICE ? grad : b->d_grad) : nullptr;
+    CK(cudaEventRecord(b->ev_join, b->stream));  // order after the caller's stream
+    CK(cudaStreamWaitEvent(b->bs, b->ev_join, 0));
+    if (b->evals == 0) {
+        const int r = batch_launch(b, dp, dg);  // first evaluation eagerly
+        if (r != PDMK_OK) return r;
+    } else {
+        if (!b->gexec || b->g_pot != dp || b->g_grad != dg) {
+            if (b->gexec) cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(b->bs, cudaStreamCaptureModeThreadLocal));
+            const int r = batch_launch(b, dp, dg);
+            const cudaError_t ce = cudaStreamEndCapture(b->bs, &graph);
+            if (r != PDMK_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return r;
+            }
+            CK(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ie);
+            b->g_pot = dp;
+            b->g_grad = dg;
+        }
+        CK(cudaGraphLaunch(b->gexec, b->bs));
+    }
+    ++b->evals;
+    if (where != PDMK_DEVICE) {
+        CK(cudaMemcpyAsync(pot, dp, size_t(b->ntot) * sizeof(double), cudaMemcpyDeviceToHost, b->bs));
+        if (grad) CK(cudaMemcpyAsync(grad, dg, size_t(b->ytot) * sizeof(double), cudaMemcpyDeviceToHost, b->bs));
+        CK(cudaStreamSynchronize(b->bs));
+        for (pdmk_plan p : b->plans)
+            if (p->pw.h_err && *reinterpret_cast<volatile int*>(p->pw.h_err)) {
+                *p->pw.h_err = 0;
+                return PDMK_ERR_TIMEOUT;
+            }
+    }
+    CK(cudaEventRecord(b->ev_join, b->bs));
+    CK(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
+    return PDMK_OK;
+}
+
+extern "C" pdmk_plan pdmk_batch_plan(pdmk_batch b, int cell) {
+    if (!b || cell < 0 || cell >= int(b->plans.size())) return nullptr;
+    return b->plans[cell];
+}
