@@ -101,6 +101,18 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
 int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, const double* q, int where);
 
 /*
+ * As pdmk_set_sources, with m >= 1 separate targets x (m x d, row-major, the caller's frame;
+ * wrapped into the cell like the sources): pdmk_eval then writes the potential and gradient
+ * at the m targets (m values, m x d), the sources' field only.  The plan is built on the union
+ * of sources and targets, the targets being points of charge 0: they add nothing to any stage
+ * and carry no self term, so the cost is that of evaluating the union.  A target that
+ * coincides exactly with a source is singular; the pair is skipped.  pdmk_set_charges still
+ * takes the n source charges.  Errors: as pdmk_set_sources.
+ */
+int pdmk_set_sources_targets(pdmk_plan plan, int64_t n, const double* y, const double* q, int64_t m, const double* x,
+                             int where);
+
+/*
  * Replaces the charges (n values, the same n and order as pdmk_set_sources) without
  * rebuilding the tree.  Errors: NOT_READY, NONFINITE, NON_NEUTRAL, CUDA.
  */
@@ -156,8 +168,12 @@ int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad);
  *     g_y = dLoss/dy = g grad Phi[q] + q grad Phi[g]    (n x d, row-major, caller's frame)
  * computed with two evaluations on the device (charges q, then charges g; neutrality of g is
  * not required) and a combine kernel; the plan's charges are the caller's again on return.
- * g_q or g_y may be NULL (not wanted).  g_grad (an upstream gradient on the returned field)
- * must be NULL: it would need second derivatives of the kernel.  g_x must be NULL: the targets
+ * With separate targets (pdmk_set_sources_targets) g_pot has one value per target and
+ *     g_q = (B^T g)  the sources' potential of charges g at the targets   (n values)
+ *     g_y = q grad Phi[g at x](y),   g_x = g grad Phi[q](x)                (n x d, m x d)
+ * from the same two evaluations over the union of points.  g_q, g_y or g_x may be NULL (not
+ * wanted).  g_grad (an upstream gradient on the returned field) must be NULL: it would need
+ * second derivatives of the kernel.  Without separate targets g_x must be NULL: the targets
  * are the sources, so their derivative is part of g_y.  where = PDMK_HOST / PDMK_DEVICE for
  * all pointers.  The first call after pdmk_set_sources allocates n (4 + 2 d) doubles of
  * scratch (kept until the next pdmk_set_sources or pdmk_plan_destroy).  Ordered after the
@@ -221,6 +237,8 @@ typedef struct {
     int pw_down_parents;       /* boxes whose local expansion is passed down   */
     int64_t pw_eval_targets;   /* targets evaluated from a leaf local expansion */
     int spread_subproblems;    /* spreading subproblems (tile, point range)     */
+    int64_t n_targets;         /* points written by pdmk_eval: the separate targets
+                                  of pdmk_set_sources_targets, else the sources  */
 } pdmk_info;
 int pdmk_get_info(pdmk_plan plan, pdmk_info* info);
 

@@ -45,7 +45,7 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("launches", ctypes.c_int),
                 ("pw_moment_sources", ctypes.c_int64), ("pw_merge_parents", ctypes.c_int),
                 ("pw_down_parents", ctypes.c_int), ("pw_eval_targets", ctypes.c_int64),
-                ("spread_subproblems", ctypes.c_int)]
+                ("spread_subproblems", ctypes.c_int), ("n_targets", ctypes.c_int64)]
 
 
 _lib = None
@@ -65,6 +65,8 @@ def lib():
         L.pdmk_plan_create.restype = ctypes.c_int
         L.pdmk_set_sources.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int]
         L.pdmk_set_sources.restype = ctypes.c_int
+        L.pdmk_set_sources_targets.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int64, P, ctypes.c_int]
+        L.pdmk_set_sources_targets.restype = ctypes.c_int
         L.pdmk_set_charges.argtypes = [P, P, ctypes.c_int]
         L.pdmk_set_charges.restype = ctypes.c_int
         L.pdmk_eval.argtypes = [P, P, P, ctypes.c_int]
@@ -166,6 +168,7 @@ class Plan:
             raise PdmkError(rc, "pdmk_plan_create")
         self._h = h
         self.n = 0
+        self.m = 0
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -179,21 +182,33 @@ class Plan:
     def close(self):
         self.__del__()
 
-    def set_sources(self, y, q):
-        if _is_torch(y):
+    def set_sources(self, y, q, x=None):
+        """Sources y (n x d) with charges q (n); optional separate targets x (m x d), else the
+        evaluation is at the sources.  numpy arrays (host) or CUDA tensors (device)."""
+        dev = _is_torch(y)
+        if dev:
             assert y.is_cuda and y.dtype.is_floating_point
             yy = y.contiguous().double()
             qq = q.contiguous().double()
-            rc = lib().pdmk_set_sources(self._h, yy.shape[0], yy.data_ptr(), qq.data_ptr(), PDMK_DEVICE)
-            n = yy.shape[0]
+            xx = x.contiguous().double() if x is not None else None
+            n, ptr = yy.shape[0], (lambda a: a.data_ptr())
         else:
             yy = np.ascontiguousarray(np.asarray(y, dtype=np.float64).reshape(-1, self.d))
             qq = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
-            n = yy.shape[0]
-            rc = lib().pdmk_set_sources(self._h, n, yy.ctypes.data, qq.ctypes.data, PDMK_HOST)
+            xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, self.d)) if x is not None else None
+            n, ptr = yy.shape[0], (lambda a: a.ctypes.data)
+        where = PDMK_DEVICE if dev else PDMK_HOST
+        if xx is None:
+            rc = lib().pdmk_set_sources(self._h, n, ptr(yy), ptr(qq), where)
+            m = n
+        else:
+            m = xx.shape[0]
+            rc = lib().pdmk_set_sources_targets(self._h, n, ptr(yy), ptr(qq), m, ptr(xx), where)
         if rc != 0:
             raise PdmkError(rc, "pdmk_set_sources")
         self.n = n
+        self.m = m
+        self.separate_targets = xx is not None
 
     def set_charges(self, q):
         if _is_torch(q):
@@ -211,16 +226,16 @@ class Plan:
         memory, e.g. a pinned torch tensor's .numpy(), makes the device-to-host copy a DMA)."""
         if out is not None:
             pot, g = out
-            ok = (isinstance(pot, np.ndarray) and pot.dtype == np.float64 and pot.shape == (self.n,)
+            ok = (isinstance(pot, np.ndarray) and pot.dtype == np.float64 and pot.shape == (self.m,)
                   and pot.flags.c_contiguous)
             if grad:
-                ok = ok and (isinstance(g, np.ndarray) and g.dtype == np.float64 and g.shape == (self.n, self.d)
+                ok = ok and (isinstance(g, np.ndarray) and g.dtype == np.float64 and g.shape == (self.m, self.d)
                              and g.flags.c_contiguous)
             if not ok:
-                raise ValueError("out must be C-contiguous float64 arrays of shapes (n,) and (n, d)")
+                raise ValueError("out must be C-contiguous float64 arrays of shapes (m,) and (m, d)")
         else:
-            pot = np.empty(self.n, dtype=np.float64)
-            g = np.empty((self.n, self.d), dtype=np.float64) if grad else None
+            pot = np.empty(self.m, dtype=np.float64)
+            g = np.empty((self.m, self.d), dtype=np.float64) if grad else None
         rc = lib().pdmk_eval(self._h, pot.ctypes.data, g.ctypes.data if grad else None, PDMK_HOST)
         if rc != 0:
             raise PdmkError(rc, "pdmk_eval")
@@ -241,28 +256,35 @@ class Plan:
         if rc != 0:
             raise PdmkError(rc, "pdmk_eval_noalloc")
 
-    def eval_adjoint(self, g_pot, want_q: bool = True, want_y: bool = True):
+    def eval_adjoint(self, g_pot, want_q: bool = True, want_y: bool = True, want_x: bool = None):
         """Vector-Jacobian product of the evaluation (pdmk_eval_adjoint): for the upstream
-        gradient g_pot = dLoss/dPhi (n values) returns (dLoss/dq, dLoss/dy) as numpy arrays for
-        numpy input, or CUDA float64 tensors for a CUDA tensor input (None where not wanted)."""
+        gradient g_pot = dLoss/dPhi (one value per evaluated point) returns (dLoss/dq, dLoss/dy)
+        and, with separate targets, (dLoss/dq, dLoss/dy, dLoss/dx); numpy arrays for numpy
+        input, CUDA float64 tensors for a CUDA tensor input (None where not wanted)."""
+        sep = getattr(self, "separate_targets", False)
+        if want_x is None:
+            want_x = sep
+        if want_x and not sep:
+            raise ValueError("without separate targets the target derivative is part of dLoss/dy")
         if _is_torch(g_pot):
             import torch
             g = g_pot.contiguous().to(torch.float64)
-            gq = torch.empty(self.n, dtype=torch.float64, device=g.device) if want_q else None
-            gy = torch.empty((self.n, self.d), dtype=torch.float64, device=g.device) if want_y else None
-            rc = lib().pdmk_eval_adjoint(self._h, g.data_ptr(), None, gq.data_ptr() if want_q else None,
-                                         gy.data_ptr() if want_y else None, None, PDMK_DEVICE)
+            mk = lambda *s: torch.empty(s, dtype=torch.float64, device=g.device)  # noqa: E731
+            ptr, where = (lambda a: a.data_ptr()), PDMK_DEVICE
         else:
             g = np.ascontiguousarray(np.asarray(g_pot, dtype=np.float64).reshape(-1))
-            if g.shape[0] != self.n:
-                raise ValueError("g_pot must have one value per source")
-            gq = np.empty(self.n, dtype=np.float64) if want_q else None
-            gy = np.empty((self.n, self.d), dtype=np.float64) if want_y else None
-            rc = lib().pdmk_eval_adjoint(self._h, g.ctypes.data, None, gq.ctypes.data if want_q else None,
-                                         gy.ctypes.data if want_y else None, None, PDMK_HOST)
+            mk = lambda *s: np.empty(s, dtype=np.float64)  # noqa: E731
+            ptr, where = (lambda a: a.ctypes.data), PDMK_HOST
+        if g.shape[0] != self.m:
+            raise ValueError("g_pot must have one value per evaluated point")
+        gq = mk(self.n) if want_q else None
+        gy = mk(self.n, self.d) if want_y else None
+        gx = mk(self.m, self.d) if want_x else None
+        rc = lib().pdmk_eval_adjoint(self._h, ptr(g), None, ptr(gq) if want_q else None,
+                                     ptr(gy) if want_y else None, ptr(gx) if want_x else None, where)
         if rc != 0:
             raise PdmkError(rc, "pdmk_eval_adjoint")
-        return gq, gy
+        return (gq, gy, gx) if sep else (gq, gy)
 
     def info(self) -> dict:
         inf = Info()

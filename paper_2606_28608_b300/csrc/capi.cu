@@ -119,6 +119,9 @@ struct pdmk_plan_s {
     void* d_slab = nullptr;
     void* slab_override = nullptr;  // set only for the duration of pdmk_eval_noalloc
     double* d_adj = nullptr;        // adjoint scratch (n (4 + 2 d) doubles), allocated on first use
+    int64_t n_src = 0;              // the caller's sources (n = n_src + separate targets)
+    int64_t out_first = 0;          // first caller-order point written by pdmk_eval
+    int64_t n_out = 0;              // points written by pdmk_eval
     int4* d_t_g0 = nullptr;
     void* d_t_dq = nullptr;
     double* d_pot_near = nullptr;
@@ -605,20 +608,33 @@ static int set_charges_device(pdmk_plan plan, bool check_neutral) {
     return pw_set_charges(&plan->pw, plan->ws);
 }
 
-extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, const double* q, int where) {
-    if (!plan || n < 0 || (n > 0 && (!y || !q))) return PDMK_ERR_BAD_ARG;
+// Sources (n_src, charges q) and, if m > 0, separate targets x (m points): the plan is built
+// on the union, the targets being points of charge 0 (they add nothing to any stage and have
+// no self term), and the evaluation writes the m target outputs only.
+static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const double* q, int64_t m, const double* x,
+                      int where) {
+    if (!plan || n_src < 0 || m < 0 || (n_src > 0 && (!y || !q)) || (m > 0 && !x)) return PDMK_ERR_BAD_ARG;
+    const int64_t n = n_src + m;
     if (n >= (int64_t(1) << 30)) return PDMK_ERR_TOO_LARGE;
     const int d = plan->d;
     plan->ready = false;
-    std::vector<double> hy(size_t(n) * d), hq(static_cast<size_t>(n));
-    if (n > 0) {
+    std::vector<double> hy(size_t(n) * d), hq(static_cast<size_t>(n), 0.0);
+    if (n_src > 0 || m > 0) {
         if (where == PDMK_DEVICE) {
             CK(cudaStreamSynchronize(plan->stream));
-            CK(cudaMemcpy(hy.data(), y, hy.size() * sizeof(double), cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(hq.data(), q, hq.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            if (n_src > 0) {
+                CK(cudaMemcpy(hy.data(), y, size_t(n_src) * d * sizeof(double), cudaMemcpyDeviceToHost));
+                CK(cudaMemcpy(hq.data(), q, size_t(n_src) * sizeof(double), cudaMemcpyDeviceToHost));
+            }
+            if (m > 0)
+                CK(cudaMemcpy(hy.data() + size_t(n_src) * d, x, size_t(m) * d * sizeof(double),
+                              cudaMemcpyDeviceToHost));
         } else {
-            std::memcpy(hy.data(), y, hy.size() * sizeof(double));
-            std::memcpy(hq.data(), q, hq.size() * sizeof(double));
+            if (n_src > 0) {
+                std::memcpy(hy.data(), y, size_t(n_src) * d * sizeof(double));
+                std::memcpy(hq.data(), q, size_t(n_src) * sizeof(double));
+            }
+            if (m > 0) std::memcpy(hy.data() + size_t(n_src) * d, x, size_t(m) * d * sizeof(double));
         }
     }
     double qs = 0, qa = 0;
@@ -914,8 +930,23 @@ extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, cons
     I.pw_eval_targets = plan->pw.active ? plan->pw.eval_targets : 0;
     I.spread_subproblems = plan->nsub;
     plan->count_pending = plan->opts.profile != 0;
+    plan->n_src = n_src;
+    plan->out_first = m > 0 ? n_src : 0;
+    plan->n_out = m > 0 ? m : n_src;
+    I.n = n_src;
+    I.n_targets = plan->n_out;
     plan->ready = true;
     return PDMK_OK;
+}
+
+extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, const double* q, int where) {
+    return set_points(plan, n, y, q, 0, nullptr, where);
+}
+
+extern "C" int pdmk_set_sources_targets(pdmk_plan plan, int64_t n, const double* y, const double* q, int64_t m,
+                                        const double* x, int where) {
+    if (m < 1 || !x) return PDMK_ERR_BAD_ARG;
+    return set_points(plan, n, y, q, m, x, where);
 }
 
 extern "C" int pdmk_set_charges(pdmk_plan plan, const double* q, int where) {
@@ -924,7 +955,7 @@ extern "C" int pdmk_set_charges(pdmk_plan plan, const double* q, int where) {
     // order after the caller's stream (device charges may still be in flight there)
     CK(cudaEventRecord(plan->ev_fork, plan->stream));
     CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
-    CK(cudaMemcpyAsync(plan->d_q_user, q, size_t(plan->n) * sizeof(double),
+    CK(cudaMemcpyAsync(plan->d_q_user, q, size_t(plan->n_src) * sizeof(double),
                        where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, plan->ws));
     int r = set_charges_device(plan, where == PDMK_HOST || plan->opts.neutrality == 0);
     if (r != PDMK_OK) return r;
@@ -944,7 +975,7 @@ static int stage_mark(pdmk_plan plan, const char* name) {
 }
 
 template <typename T, int D>
-static int run_eval(pdmk_plan plan, double* pot, double* grad) {
+static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first) {
     cudaStream_t s = plan->ws;
     const Geometry& g = plan->g;
     int r;
@@ -1211,6 +1242,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
             }
         aa.pot_out = pot;
         aa.grad_out = grad;
+        aa.out_first = out_first;
         int blocks = int(std::min<int64_t>((plan->ntgt + 255) / 256, 148 * 8));
         k_assemble<D, T><<<std::max(blocks, 1), 256, 0, s>>>(aa);
         ++plan->launches;
@@ -1220,10 +1252,13 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad) {
     return PDMK_OK;
 }
 
-static int launch_eval(pdmk_plan plan, double* dp, double* dg) {
+// out_first: the first caller-order point to write (points before it are computed but not
+// written; the outputs start at that point)
+static int launch_eval(pdmk_plan plan, double* dp, double* dg, int64_t out_first) {
     const bool mixed = plan->opts.precision == PDMK_MIXED;
-    if (plan->d == 2) return mixed ? run_eval<float, 2>(plan, dp, dg) : run_eval<double, 2>(plan, dp, dg);
-    return mixed ? run_eval<float, 3>(plan, dp, dg) : run_eval<double, 3>(plan, dp, dg);
+    if (plan->d == 2)
+        return mixed ? run_eval<float, 2>(plan, dp, dg, out_first) : run_eval<double, 2>(plan, dp, dg, out_first);
+    return mixed ? run_eval<float, 3>(plan, dp, dg, out_first) : run_eval<double, 3>(plan, dp, dg, out_first);
 }
 
 extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
@@ -1245,14 +1280,14 @@ extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
     // pair-counting evaluation run eagerly).
     const bool eager = plan->opts.profile || plan->count_pending || plan->evals_since_setup == 0;
     if (eager) {
-        r = launch_eval(plan, dp, dg);
+        r = launch_eval(plan, dp, dg, plan->out_first);
         if (r != PDMK_OK) return r;
     } else {
         if (!plan->gexec || plan->g_pot != dp || plan->g_grad != dg) {
             drop_graph(plan);
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(plan->ws, cudaStreamCaptureModeThreadLocal));
-            r = launch_eval(plan, dp, dg);
+            r = launch_eval(plan, dp, dg, plan->out_first);
             cudaError_t ce = cudaStreamEndCapture(plan->ws, &graph);
             if (r != PDMK_OK) {
                 if (graph) cudaGraphDestroy(graph);
@@ -1269,9 +1304,9 @@ extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
     }
     ++plan->evals_since_setup;
     if (where != PDMK_DEVICE) {
-        CK(cudaMemcpyAsync(pot, dp, size_t(plan->n) * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
+        CK(cudaMemcpyAsync(pot, dp, size_t(plan->n_out) * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
         if (grad)
-            CK(cudaMemcpyAsync(grad, dg, size_t(plan->n) * plan->d * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
+            CK(cudaMemcpyAsync(grad, dg, size_t(plan->n_out) * plan->d * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
         CK(cudaStreamSynchronize(plan->ws));
         if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
             *plan->pw.h_err = 0;
@@ -1379,7 +1414,7 @@ extern "C" int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad) {
     plan->opts.profile = 0;
     plan->count_pending = false;
     plan->slab_override = scratch;
-    const int r = launch_eval(plan, pot, grad);
+    const int r = launch_eval(plan, pot, grad, plan->out_first);
     plan->slab_override = nullptr;
     plan->opts.profile = saved_profile ? 1 : 0;
     plan->count_pending = saved_count;
@@ -1404,18 +1439,23 @@ __global__ void k_adjoint_combine(int64_t n, int d, const double* __restrict__ g
 
 extern "C" int pdmk_eval_adjoint(pdmk_plan plan, const double* g_pot, const double* g_grad, double* g_q, double* g_y,
                                  double* g_x, int where) {
-    if (!plan || !g_pot || (!g_q && !g_y)) return PDMK_ERR_BAD_ARG;
-    if (g_grad || g_x) {
-        plan_set_msg(plan, g_grad ? "upstream gradients on the returned field need second derivatives of the kernel"
-                                  : "the targets are the sources: their derivative is part of g_y");
+    if (!plan || !g_pot || (!g_q && !g_y && !g_x)) return PDMK_ERR_BAD_ARG;
+    if (g_grad) {
+        plan_set_msg(plan, "upstream gradients on the returned field need second derivatives of the kernel");
         return PDMK_ERR_BAD_ARG;
     }
     if (!plan->ready) return PDMK_ERR_NOT_READY;
+    if (g_x && plan->out_first == 0) {
+        plan_set_msg(plan, "the targets are the sources: their derivative is part of g_y");
+        return PDMK_ERR_BAD_ARG;
+    }
     if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
         *plan->pw.h_err = 0;
         return PDMK_ERR_TIMEOUT;
     }
-    const int64_t n = plan->n;
+    // over the plan's points: the sources [0, n_src) and, with separate targets, the targets
+    // [n_src, n); the upstream gradient lives on the evaluated points [out_first, n)
+    const int64_t n = plan->n, ns = plan->n_src, m = n - ns, first = plan->out_first;
     const int d = plan->d;
     if (n == 0) return PDMK_OK;
     if (!plan->d_adj) {
@@ -1434,19 +1474,20 @@ extern "C" int pdmk_eval_adjoint(pdmk_plan plan, const double* g_pot, const doub
     CK(cudaEventRecord(plan->ev_fork, plan->stream));
     CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
     CK(cudaMemcpyAsync(q_save, plan->d_q_user, nb, cudaMemcpyDeviceToDevice, plan->ws));
-    CK(cudaMemcpyAsync(gdev, g_pot, nb, where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                       plan->ws));
-    // both evaluations run eagerly: the plan's captured graph stays keyed to the caller's
-    // outputs of pdmk_eval
+    CK(cudaMemsetAsync(gdev, 0, nb, plan->ws));
+    CK(cudaMemcpyAsync(gdev + first, g_pot, size_t(n - first) * sizeof(double),
+                       where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, plan->ws));
+    // both evaluations run eagerly over every point: the plan's captured graph stays keyed
+    // to the caller's outputs of pdmk_eval
     const bool saved_profile = plan->opts.profile != 0, saved_count = plan->count_pending;
     plan->opts.profile = 0;
     plan->count_pending = false;
-    int r = launch_eval(plan, pot_q, grad_q);  // grad Phi[q]
+    int r = launch_eval(plan, pot_q, grad_q, 0);  // grad Phi[q]
     if (r == PDMK_OK) {
         CK(cudaMemcpyAsync(plan->d_q_user, gdev, nb, cudaMemcpyDeviceToDevice, plan->ws));
         r = set_charges_device(plan, false);
     }
-    if (r == PDMK_OK) r = launch_eval(plan, pot_g, grad_g);  // Phi[g] = A g, grad Phi[g]
+    if (r == PDMK_OK) r = launch_eval(plan, pot_g, grad_g, 0);  // Phi[g] = A g, grad Phi[g]
     // the caller's charges again, whatever happened above
     cudaMemcpyAsync(plan->d_q_user, q_save, nb, cudaMemcpyDeviceToDevice, plan->ws);
     const int r2 = set_charges_device(plan, false);
@@ -1454,15 +1495,17 @@ extern "C" int pdmk_eval_adjoint(pdmk_plan plan, const double* g_pot, const doub
     plan->count_pending = saved_count;
     if (r != PDMK_OK) return r;
     if (r2 != PDMK_OK) return r2;
-    double* gy_dev = (where == PDMK_DEVICE) ? g_y : grad_q;  // in place is safe: element-wise
-    if (g_y) {
+    // g grad Phi[q] + q grad Phi[g] at every point, in place (element-wise): the source rows
+    // are g_y, the target rows g_x
+    if (g_y || g_x) {
         const int blocks = int(std::min<int64_t>((n * d + 255) / 256, 148 * 8));
-        k_adjoint_combine<<<std::max(blocks, 1), 256, 0, plan->ws>>>(n, d, gdev, q_save, grad_q, grad_g, gy_dev);
+        k_adjoint_combine<<<std::max(blocks, 1), 256, 0, plan->ws>>>(n, d, gdev, q_save, grad_q, grad_g, grad_q);
         CK(cudaGetLastError());
     }
     const cudaMemcpyKind out_kind = where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (g_q) CK(cudaMemcpyAsync(g_q, pot_g, nb, out_kind, plan->ws));
-    if (g_y && where != PDMK_DEVICE) CK(cudaMemcpyAsync(g_y, gy_dev, nb * d, out_kind, plan->ws));
+    if (g_q) CK(cudaMemcpyAsync(g_q, pot_g, size_t(ns) * sizeof(double), out_kind, plan->ws));
+    if (g_y) CK(cudaMemcpyAsync(g_y, grad_q, size_t(ns) * d * sizeof(double), out_kind, plan->ws));
+    if (g_x) CK(cudaMemcpyAsync(g_x, grad_q + size_t(ns) * d, size_t(m) * d * sizeof(double), out_kind, plan->ws));
     if (where != PDMK_DEVICE) {
         CK(cudaStreamSynchronize(plan->ws));
         if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
@@ -1591,7 +1634,7 @@ static int batch_launch(pdmk_batch b, double* dp, double* dg) {
         CK(cudaStreamWaitEvent(p->ws, b->ev_fork, 0));
         const bool saved_profile = p->opts.profile != 0;
         p->opts.profile = 0;
-        const int r = launch_eval(p, dp + b->off[c], dg ? dg + b->yoff[c] : nullptr);
+        const int r = launch_eval(p, dp + b->off[c], dg ? dg + b->yoff[c] : nullptr, p->out_first);
         p->opts.profile = saved_profile ? 1 : 0;
         if (r != PDMK_OK) return r;
         CK(cudaEventRecord(p->ev_join, p->ws));

@@ -102,6 +102,7 @@ struct AssembleArgs {
     double Qt[9];            // Q^T: user-frame rotation (row-major d x d)
     double* pot_out;         // user order
     double* grad_out;        // user order, d per point, or null
+    int64_t out_first;       // caller-order points before this one are not written
 };
 
 // The potential (self term, mean correction, the 2D logarithmic cancellation between the
@@ -121,7 +122,8 @@ __global__ void __launch_bounds__(256) k_assemble(AssembleArgs a) {
          t += int64_t(gridDim.x) * blockDim.x) {
         double p = a.pot_near[t] + a.pot_far[t] - a.self_w[t] * a.q_tgt[t] - corr;
         if (a.pot_pw) p += a.pot_pw[t];
-        const int o = a.tgt_orig[t];
+        if (a.tgt_orig[t] < a.out_first) continue;
+        const int64_t o = a.tgt_orig[t] - a.out_first;
         a.pot_out[o] = p;
         if (a.grad_out) {
             GT gu[D], g[D];
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(256) k_assemble(AssembleArgs a) {
                 GT s = GT(0);
 #pragma unroll
                 for (int j = 0; j < D; ++j) s = fma(Qt[i * D + j], g[j], s);
-                a.grad_out[int64_t(o) * D + i] = double(s);
+                a.grad_out[o * D + i] = double(s);
             }
         }
     }
