@@ -168,6 +168,19 @@ STAGE_KERNELS = {
 }
 
 
+def replica_summary(t_local, n, steps, ws, pg, device):
+    """Replicas (one independent cell per rank, no collective on the data path): the timed
+    region is the slowest rank's, and the value is every rank's points over that time.
+    Returns (points/s over all ranks, ms per step, the slowest rank's seconds)."""
+    t_max = t_local
+    if pg is not None and ws > 1:
+        import torch
+        tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return ws * n * steps / t_max, 1e3 * t_max / steps, t_max
+
+
 def run_reference(args, ws, rank):
     """The oracle (plain FP64 Ewald on the host cores) on a bounded sample of targets."""
     if rank != 0:
@@ -265,13 +278,7 @@ def main():
     sampler = ClockSampler(local)
     t_total = timed(plan, args.steps, 0)
     clocks = sampler.stop()
-    t_max = t_total
-    if pg:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * n * args.steps / t_max
-    ms_per_step = 1e3 * t_max / args.steps
+    value, ms_per_step, t_max = replica_summary(t_total, n, args.steps, ws, pg, dev)
     pot_m = pot.cpu().numpy().copy()
     grad_m = grad.cpu().numpy().copy()
     info = plan.info()
