@@ -57,6 +57,7 @@ struct pdmk_plan_s {
     int near_nh = 0;             // > 0: warp near-field kernel with this many monomial terms
     std::vector<double> mW, mWd; // window F, dF as monomials in x = 2 s - 1
     bool far_halo = false;       // 2D FP32 halo-grid spreading / interpolation kernels
+    bool far_warp3d = false;     // 3D warp-per-target interpolation
     int B[3] = {1, 1, 1}, nbin[3] = {1, 1, 1}, P[3] = {1, 1, 1}, Ptot = 1;
     int whole_ctas = 0;  // > 0: 2D whole-grid spreading with this many CTAs (small grids)
     int64_t ncell = 1, nhalf = 1;
@@ -470,6 +471,11 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
         plan->far_halo = d == 2 && mixed && nh > 0 && int(plan->cW.size()) <= nh && int(plan->cWd.size()) <= nh &&
                          ampW <= 4.0 && ampWd <= 4.0 && plan->w - 1 <= std::min(plan->g.M[0], plan->g.M[1]) &&
                          (8 * Mp0 * Mp1 + 16 * plan->w) * 4 <= 112 * 1024;
+        // FP64 windows need longer series (eps-scaled fit): 24 terms cover eps >= 1e-9
+        const int nh3 = plan->w == 8 ? 16 : plan->w == 13 ? 20 : plan->w == 17 ? 24 : 0;
+        plan->far_warp3d = d == 3 && nh3 > 0 && int(plan->cW.size()) <= nh3 && int(plan->cWd.size()) <= nh3 &&
+                           ampW <= 4.0 && ampWd <= 4.0 &&
+                           plan->w - 1 <= std::min(plan->g.M[0], std::min(plan->g.M[1], plan->g.M[2]));
     }
     // plane-wave planning (proxy order, plane-wave counts, 1D operators)
     pw_plan_create(&plan->pw, d, eps, plan->c, plan->kt, plan->opts.n_proxy, plan->opts.n_pw, mixed);
@@ -1124,6 +1130,21 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         if (plan->w == 8) interp(k_interp_halo<T, 8, 12, 12>);
         else if (plan->w == 13) interp(k_interp_halo<T, 13, 16, 16>);
         else interp(k_interp_halo<T, 17, 20, 20>);
+        ++plan->launches;
+        CK(cudaGetLastError());
+    } else if (plan->ntgt > 0 && D == 3 && plan->far_warp3d && plan->ntgt < 50000) {
+        // (with many targets a thread per target already fills the GPU)
+        auto interp = [&](auto kern) {
+            const int warps = int(std::min<int64_t>(plan->ntgt, int64_t(148) * 64));
+            kern<<<(warps + 7) / 8, 256, 0, s>>>(static_cast<const T*>(plan->d_grid), plan->d_t_g0,
+                                                 static_cast<const T*>(plan->d_t_dq), int(plan->ntgt), g.M[0], g.M[1],
+                                                 g.M[2], hwi2, static_cast<const T*>(plan->d_monoW),
+                                                 static_cast<const T*>(plan->d_monoWd), plan->d_pot_far,
+                                                 plan->d_gradu_far);
+        };
+        if (plan->w == 8) interp(k_interp_warp3d<T, 8, 16, 16>);
+        else if (plan->w == 13) interp(k_interp_warp3d<T, 13, 20, 20>);
+        else interp(k_interp_warp3d<T, 17, 24, 24>);
         ++plan->launches;
         CK(cudaGetLastError());
     } else if (plan->ntgt > 0) {

@@ -568,3 +568,85 @@ k_interp_halo(const T* __restrict__ grid, const int4* __restrict__ t_g0, const T
 }
 
 }  // namespace pdmk
+
+namespace pdmk {
+
+// 3D interpolation of the potential and its grid-coordinate gradient, one warp per target
+// (small cells have few targets, and a thread per target left most of the GPU idle): lanes
+// evaluate the 3 W window values and derivatives (Horner sums of monomials in x = 2 s - 1),
+// then take the W^2 (y, z) rows in turn, each row a W-point contraction along x; a warp
+// reduction in a fixed order combines the lanes.  Window starts arrive wrapped into
+// [0, M_i); needs W - 1 <= min(M0, M1, M2).
+template <typename T, int W, int NH, int NHD>
+__global__ void __launch_bounds__(256)
+k_interp_warp3d(const T* __restrict__ grid, const int4* __restrict__ t_g0, const T* __restrict__ t_dq, int nt, int M0,
+                int M1, int M2, T half_w_inv2, const T* __restrict__ monoW, const T* __restrict__ monoWd,
+                double* __restrict__ pot, double* __restrict__ gradu) {
+    __shared__ T win[8][2][3][W];  // [warp][value, derivative][axis][j]
+    T cw[NH], cd[NHD];
+#pragma unroll
+    for (int k = 0; k < NH; ++k) cw[k] = monoW[k];
+#pragma unroll
+    for (int k = 0; k < NHD; ++k) cd[k] = monoWd[k];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += nw) {
+        const int4 g0 = t_g0[t];
+        for (int l = lane; l < 3 * W; l += 32) {
+            const int a = l / W, j = l - a * W;
+            const T z = t_dq[size_t(t) * 4 + a] - T(j);
+            const T s = z * z * half_w_inv2;
+            const bool in = s < T(1);
+            const T x = fma(T(2), s, T(-1));
+            T v = cw[NH - 1], dv = cd[NHD - 1];
+#pragma unroll
+            for (int k = NH - 2; k >= 0; --k) v = fma(v, x, cw[k]);
+#pragma unroll
+            for (int k = NHD - 2; k >= 0; --k) dv = fma(dv, x, cd[k]);
+            // phi(z) = F(2 s - 1), phi'(z) = dF(2 s - 1) 2 z / (w/2)^2
+            win[wp][0][a][j] = in ? v : T(0);
+            win[wp][1][a][j] = in ? dv * T(2) * z * half_w_inv2 : T(0);
+        }
+        __syncwarp();
+        T p = 0, gx = 0, gy = 0, gz = 0;
+        for (int r = lane; r < W * W; r += 32) {
+            const int iz = r / W, iy = r - iz * W;
+            int yy = g0.y + iy;
+            if (yy >= M1) yy -= M1;
+            int zz = g0.z + iz;
+            if (zz >= M2) zz -= M2;
+            const T* row = grid + (size_t(zz) * M1 + yy) * M0;
+            T sx = 0, sdx = 0;
+            int xx = g0.x;
+#pragma unroll
+            for (int ix = 0; ix < W; ++ix) {
+                const T v = __ldg(row + xx);
+                sx = fma(v, win[wp][0][0][ix], sx);
+                sdx = fma(v, win[wp][1][0][ix], sdx);
+                if (++xx == M0) xx = 0;
+            }
+            const T wy = win[wp][0][1][iy], dwy = win[wp][1][1][iy];
+            const T wz = win[wp][0][2][iz], dwz = win[wp][1][2][iz];
+            p = fma(sx, wy * wz, p);
+            gx = fma(sdx, wy * wz, gx);
+            gy = fma(sx, dwy * wz, gy);
+            gz = fma(sx, wy * dwz, gz);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_down_sync(0xffffffffu, p, o);
+            gx += __shfl_down_sync(0xffffffffu, gx, o);
+            gy += __shfl_down_sync(0xffffffffu, gy, o);
+            gz += __shfl_down_sync(0xffffffffu, gz, o);
+        }
+        if (lane == 0) {
+            pot[t] = double(p);
+            gradu[size_t(t) * 3 + 0] = double(gx);
+            gradu[size_t(t) * 3 + 1] = double(gy);
+            gradu[size_t(t) * 3 + 2] = double(gz);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace pdmk
