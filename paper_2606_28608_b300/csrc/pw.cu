@@ -206,6 +206,150 @@ __global__ void __launch_bounds__(128) k_down(const int* __restrict__ list, T* _
     }
 }
 
+// 3D with a compile-time order P: one block of P^2 threads per parent, thread (i, j) <-> the
+// positions (M1, M2) or (m1, m2) of a P x P slice.  The sum over the eight children factors by
+// axis (child c = (b0, b1, b2), bit k of c is b_k):
+//   merge: T_{b0 b1}[m1][M2] = sum_{b2, m2} S_b2[M2][m2] Q_c[m0][m1][m2]       (slice m0)
+//          U_{b0}[M1][M2]    = sum_{b1, m1} S_b1[M1][m1] T_{b0 b1}[m1][M2]
+//          Q_P[M0][M1][M2]  += sum_{b0} S_b0[M0][m0] U_{b0}[M1][M2]           (registers)
+//   down:  V_{b0}[M1][M2]    = sum_{M0} S_b0[M0][m0] a_P[M0][M1][M2]          (slice m0)
+//          W_{b0 b1}[m1][M2] = sum_{M1} S_b1[M1][m1] V_{b0}[M1][M2]
+//          a_c[m0][m1][m2]  += sum_{M2} S_b2[M2][m2] W_{b0 b1}[m1][M2]
+// 14 P^4 multiply-adds per parent (a child-by-child separable re-expansion takes 24 P^4).
+// S is stored as Sm[b][M][m] and transposed as St[b][m][M] (lanes along the contiguous index).
+template <typename T, int P>
+__global__ void __launch_bounds__(P * P) k_merge3d_p(const int* __restrict__ list, T* __restrict__ Q,
+                                                     const T* __restrict__ Sg) {
+    constexpr int PP = P * P, NP = PP * P;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Sm = reinterpret_cast<T*>(smraw);  // [2][P][P]
+    T* St = Sm + 2 * PP;                  // [2][P][P] transposed
+    T* in = St + 2 * PP;                  // [8][PP] child slices m0
+    T* Ts = in + 8 * PP;                  // [4][PP]
+    T* Us = Ts + 4 * PP;                  // [2][PP]
+    const int tid = threadIdx.x, i = tid / P, j = tid % P;
+    for (int k = tid; k < 2 * PP; k += blockDim.x) {
+        const T v = Sg[k];
+        Sm[k] = v;
+        const int b = k / PP, M = (k / P) % P, m = k % P;
+        St[(b * P + m) * P + M] = v;
+    }
+    const int* e = list + size_t(blockIdx.x) * 9;
+    int cs[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cs[c] = e[1 + c];
+    T acc[P];
+#pragma unroll
+    for (int M0 = 0; M0 < P; ++M0) acc[M0] = T(0);
+    for (int m0 = 0; m0 < P; ++m0) {
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) in[c * PP + tid] = cs[c] >= 0 ? Q[size_t(cs[c]) * NP + size_t(m0) * PP + tid] : T(0);
+        __syncthreads();
+        // T_{b0b1}[m1 = i][M2 = j]
+        {
+            T t4[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+                for (int m2 = 0; m2 < P; ++m2) {
+                    const T s = St[(b2 * P + m2) * P + j];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) t4[k] = fma(s, in[((b2 << 2) | k) * PP + i * P + m2], t4[k]);
+                }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Ts[k * PP + tid] = t4[k];
+        }
+        __syncthreads();
+        // U_{b0}[M1 = i][M2 = j]
+        {
+            T u0 = T(0), u1 = T(0);
+#pragma unroll
+            for (int b1 = 0; b1 < 2; ++b1)
+#pragma unroll
+                for (int m1 = 0; m1 < P; ++m1) {
+                    const T s = Sm[(b1 * P + i) * P + m1];
+                    u0 = fma(s, Ts[((b1 << 1) | 0) * PP + m1 * P + j], u0);
+                    u1 = fma(s, Ts[((b1 << 1) | 1) * PP + m1 * P + j], u1);
+                }
+            // Q_P[M0][i][j] += S_0[M0][m0] U_0 + S_1[M0][m0] U_1
+#pragma unroll
+            for (int M0 = 0; M0 < P; ++M0)
+                acc[M0] = fma(Sm[M0 * P + m0], u0, fma(Sm[(P + M0) * P + m0], u1, acc[M0]));
+        }
+    }
+    T* dst = Q + size_t(e[0]) * NP;
+#pragma unroll
+    for (int M0 = 0; M0 < P; ++M0) dst[size_t(M0) * PP + tid] = acc[M0];
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(P * P) k_down3d_p(const int* __restrict__ list, T* __restrict__ Lc,
+                                                    const T* __restrict__ Sg) {
+    constexpr int PP = P * P, NP = PP * P;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Sm = reinterpret_cast<T*>(smraw);  // [2][P][P]
+    T* St = Sm + 2 * PP;                  // [2][P][P] transposed
+    T* aP = St + 2 * PP;                  // [P][PP] parent coefficients
+    T* Vs = aP + NP;                      // [2][PP]
+    T* Ws = Vs + 2 * PP;                  // [4][PP]
+    const int tid = threadIdx.x, i = tid / P, j = tid % P;
+    for (int k = tid; k < 2 * PP; k += blockDim.x) {
+        const T v = Sg[k];
+        Sm[k] = v;
+        const int b = k / PP, M = (k / P) % P, m = k % P;
+        St[(b * P + m) * P + M] = v;
+    }
+    const int* e = list + size_t(blockIdx.x) * 9;
+    const T* src = Lc + size_t(e[0]) * NP;
+    for (int k = tid; k < NP; k += blockDim.x) aP[k] = src[k];
+    int cs[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cs[c] = e[1 + c];
+    for (int m0 = 0; m0 < P; ++m0) {
+        __syncthreads();
+        // V_{b0}[M1 = i][M2 = j]
+        {
+            T v0 = T(0), v1 = T(0);
+#pragma unroll
+            for (int M0 = 0; M0 < P; ++M0) {
+                const T a = aP[M0 * PP + tid];
+                v0 = fma(Sm[M0 * P + m0], a, v0);
+                v1 = fma(Sm[(P + M0) * P + m0], a, v1);
+            }
+            Vs[tid] = v0;
+            Vs[PP + tid] = v1;
+        }
+        __syncthreads();
+        // W_{b0b1}[m1 = i][M2 = j]
+        {
+            T w4[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int M1 = 0; M1 < P; ++M1) {
+                const T s0 = Sm[M1 * P + i], s1 = Sm[(P + M1) * P + i];
+                const T va = Vs[M1 * P + j], vb = Vs[PP + M1 * P + j];
+                w4[0] = fma(s0, va, w4[0]);  // (b0, b1) = (0, 0)
+                w4[1] = fma(s0, vb, w4[1]);  // (1, 0)
+                w4[2] = fma(s1, va, w4[2]);  // (0, 1)
+                w4[3] = fma(s1, vb, w4[3]);  // (1, 1)
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Ws[k * PP + tid] = w4[k];
+        }
+        __syncthreads();
+        // a_c[m0][m1 = i][m2 = j] += sum_{M2} S_b2[M2][m2] W_{b0b1}[m1][M2]
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (cs[c] < 0) continue;
+            const int b2 = c >> 2, k = c & 3;  // k = b0 | b1 << 1
+            T o = T(0);
+#pragma unroll
+            for (int M2 = 0; M2 < P; ++M2) o = fma(Sm[(b2 * P + M2) * P + j], Ws[k * PP + i * P + M2], o);
+            Lc[size_t(cs[c]) * NP + size_t(m0) * PP + tid] += o;
+        }
+    }
+}
+
 // 2D: the whole re-expansion of all children in two shared-memory phases per parent.
 // merge: Q_P[M0][M1] = sum_c sum_{m0<=M0} S_{b0}[M0][m0] sum_{m1<=M1} S_{b1}[M1][m1] Q_c[m0][m1]
 template <typename T>
@@ -1705,6 +1849,14 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                     case 32: launch_p(k_merge2d_p<T, 32>, 10 * 32 * 32, lst, Q); break;
                     default: k_merge2d<T><<<e - b, 256, sm_m2, s>>>(lst, Q, S, pd);
                 }
+            } else if (pd.p == 16 || pd.p == 24) {
+                auto m3 = [&](auto kern, int P) {
+                    const size_t smb = ts * 18 * P * P;
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+                    kern<<<e - b, P * P, smb, s>>>(lst, Q, S);
+                };
+                if (pd.p == 16) m3(k_merge3d_p<T, 16>, 16);
+                else m3(k_merge3d_p<T, 24>, 24);
             } else {
                 k_merge<T, D><<<e - b, 128, sm_re, s>>>(lst, Q, S, pd);
             }
@@ -1775,6 +1927,14 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                     case 32: launch_p(k_down2d_p<T, 32>, 5 * 32 * 32, lst, L); break;
                     default: k_down2d<T><<<e - b, 256, sm_d2, s>>>(lst, L, S, pd);
                 }
+            } else if (pd.p == 16 || pd.p == 24) {
+                auto d3 = [&](auto kern, int P) {
+                    const size_t smb = ts * (10 * P * P + P * P * P);
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+                    kern<<<e - b, P * P, smb, s>>>(lst, L, S);
+                };
+                if (pd.p == 16) d3(k_down3d_p<T, 16>, 16);
+                else d3(k_down3d_p<T, 24>, 24);
             } else {
                 k_down<T, D><<<e - b, 128, sm_re, s>>>(lst, L, S, pd);
             }
