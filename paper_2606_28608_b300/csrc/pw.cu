@@ -26,6 +26,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "k_pw.cuh"
@@ -106,6 +107,54 @@ __global__ void __launch_bounds__(128) k_leaf_moments(const int4* __restrict__ l
             Qb[e] += acc;
         }
     }
+}
+
+// 3D leaf moments with a compile-time order P: one block of P^2 threads per leaf, thread
+// (m1, m2) accumulates Q[m0][m1][m2] for every m0 in registers:
+//   Q[m0][m1][m2] = sum_s (q_s T_m1(t1_s) T_m2(t2_s)) T_m0(t0_s)
+// with the sources' Chebyshev rows staged in shared memory 32 at a time.
+template <typename T, int P>
+__global__ void __launch_bounds__(P * P, 1) k_leaf_moments3d_p(const int4* __restrict__ leaves,
+                                                            const T* __restrict__ src4, T* __restrict__ Q,
+                                                            double inv_rc) {
+    constexpr int PP = P * P, NB = 32;
+    __shared__ T basis[NB][3][P];
+    __shared__ T qv[NB];
+    const int4 lf = leaves[blockIdx.x];  // (first source, count, q slot, level)
+    const T scale = T(2.0 * inv_rc * double(1LL << lf.w));  // t = 2 (y - c)/h
+    const int tid = threadIdx.x, m1 = tid / P, m2 = tid % P;
+    T acc[P];
+#pragma unroll
+    for (int m0 = 0; m0 < P; ++m0) acc[m0] = T(0);
+    for (int s0 = 0; s0 < lf.y; s0 += NB) {
+        const int ns = min(NB, lf.y - s0);
+        __syncthreads();
+        if (tid < ns * 3) {
+            const int s = tid / 3, ax = tid - 3 * s;
+            const T* y = src4 + size_t(lf.x + s0 + s) * 4;
+            const T t = y[ax] * scale;
+            T tm1 = T(1), tm = t;
+            basis[s][ax][0] = T(1);
+            basis[s][ax][1] = t;
+#pragma unroll
+            for (int m = 2; m < P; ++m) {
+                const T tn = fma(T(2) * t, tm, -tm1);
+                basis[s][ax][m] = tn;
+                tm1 = tm;
+                tm = tn;
+            }
+            if (ax == 0) qv[s] = y[3];
+        }
+        __syncthreads();
+        for (int s = 0; s < ns; ++s) {
+            const T w = qv[s] * basis[s][1][m1] * basis[s][2][m2];
+#pragma unroll
+            for (int m0 = 0; m0 < P; ++m0) acc[m0] = fma(w, basis[s][0][m0], acc[m0]);
+        }
+    }
+    T* Qb = Q + size_t(lf.z) * (PP * P);
+#pragma unroll
+    for (int m0 = 0; m0 < P; ++m0) Qb[m0 * PP + tid] = acc[m0];
 }
 
 // ------------------------------------------------------------------ merge / downward
@@ -741,6 +790,112 @@ __global__ void __launch_bounds__(128) k_pw_in(const int* __restrict__ list, con
             a[it] += acc;
         }
         __syncthreads();
+    }
+}
+
+// 3D leaf evaluation with a compile-time order P: one warp per leaf, a thread per target.  The
+// z-axis T_m, T'_m sit in registers, the x- and y-axis ones in shared memory (interleaved by
+// thread), and the leaf's coefficient rows are read as vectors (all lanes read the same row:
+// one broadcast load per 4 (FP32) or 2 (FP64) coefficients).
+template <typename T, int P>
+__global__ void __launch_bounds__(32) k_leaf_eval3d_p(const int4* __restrict__ list, const T* __restrict__ Lc,
+                                                      const T* __restrict__ tgt4, double* __restrict__ pot,
+                                                      double* __restrict__ grad, double inv_rc) {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int VW = sizeof(V) / sizeof(T), NV = P / VW;
+    static_assert(P % VW == 0, "rows are whole vectors");
+    __shared__ T tab[4][P][32];  // [b0, d0, b1, d1][m][lane]
+    const int lane = threadIdx.x;
+    const int4 e = list[blockIdx.x];
+    const T* a = Lc + size_t(e.x) * (P * P * P);
+    const double sc = 2.0 * inv_rc * double(1LL << e.w);  // dt/dx = 2/h
+    for (int t0 = 0; t0 < e.z; t0 += 32) {
+        const int ti = t0 + lane;
+        const bool act = ti < e.z;
+        T tz[P], dz[P];
+        {
+            const T* x = tgt4 + size_t(e.y + (act ? ti : 0)) * 4;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const T t = T(double(x[ax]) * sc);
+                T tm1 = T(1), tm = t, um1 = T(1), um = T(2) * t;
+                T bv[P], dv[P];
+                bv[0] = T(1);
+                dv[0] = T(0);
+                bv[1] = t;
+                dv[1] = T(1);
+#pragma unroll
+                for (int m = 2; m < P; ++m) {
+                    const T tn = fma(T(2) * t, tm, -tm1);
+                    bv[m] = tn;
+                    dv[m] = T(m) * um;  // T'_m = m U_{m-1}
+                    const T un = fma(T(2) * t, um, -um1);
+                    tm1 = tm;
+                    tm = tn;
+                    um1 = um;
+                    um = un;
+                }
+#pragma unroll
+                for (int m = 0; m < P; ++m) {
+                    if (ax < 2) {
+                        tab[2 * ax][m][lane] = bv[m];
+                        tab[2 * ax + 1][m][lane] = dv[m];
+                    } else {
+                        tz[m] = bv[m];
+                        dz[m] = dv[m];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        T phi = 0, g0 = 0, g1 = 0, g2 = 0;
+#pragma unroll 1
+        for (int m0 = 0; m0 < P; ++m0) {
+            T s = 0, s1d = 0, s2d = 0;
+#pragma unroll 2
+            for (int m1 = 0; m1 < P; ++m1) {
+                const V* row = reinterpret_cast<const V*>(a + (m0 * P + m1) * P);
+                T u = 0, ud = 0;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const V v = __ldg(row + k);
+                    if constexpr (VW == 4) {
+                        u = fma(v.x, tz[4 * k], u);
+                        ud = fma(v.x, dz[4 * k], ud);
+                        u = fma(v.y, tz[4 * k + 1], u);
+                        ud = fma(v.y, dz[4 * k + 1], ud);
+                        u = fma(v.z, tz[4 * k + 2], u);
+                        ud = fma(v.z, dz[4 * k + 2], ud);
+                        u = fma(v.w, tz[4 * k + 3], u);
+                        ud = fma(v.w, dz[4 * k + 3], ud);
+                    } else {
+                        u = fma(v.x, tz[2 * k], u);
+                        ud = fma(v.x, dz[2 * k], ud);
+                        u = fma(v.y, tz[2 * k + 1], u);
+                        ud = fma(v.y, dz[2 * k + 1], ud);
+                    }
+                }
+                const T b1 = tab[2][m1][lane], d1 = tab[3][m1][lane];
+                s = fma(b1, u, s);
+                s1d = fma(d1, u, s1d);
+                s2d = fma(b1, ud, s2d);
+            }
+            const T b0 = tab[0][m0][lane], d0 = tab[1][m0][lane];
+            phi = fma(b0, s, phi);
+            g0 = fma(d0, s, g0);
+            g1 = fma(b0, s1d, g1);
+            g2 = fma(b0, s2d, g2);
+        }
+        if (act) {
+            const size_t o = size_t(e.y + ti);
+            pot[o] = double(phi);
+            if (grad) {
+                grad[o * 3 + 0] = double(g0) * sc;
+                grad[o * 3 + 1] = double(g1) * sc;
+                grad[o * 3 + 2] = double(g2) * sc;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -1816,8 +1971,12 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     }
     if (phase == 0 && I->nleafq > 0) {
         const T* s4 = static_cast<const T*>(pw->d_src4);
-        const size_t sm = ts * (32 * D * pd.p + 32);
-        k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, s4, Q, pd, inv_rc);
+        if (D == 3 && pd.p == 16) k_leaf_moments3d_p<T, 16><<<I->nleafq, 256, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
+        else if (D == 3 && pd.p == 24) k_leaf_moments3d_p<T, 24><<<I->nleafq, 576, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
+        else {
+            const size_t sm = ts * (32 * D * pd.p + 32);
+            k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, s4, Q, pd, inv_rc);
+        }
         ++pw->launches;
     }
     // compile-time-order 2D re-expansion kernels (dynamic shared memory of nel elements)
@@ -1942,7 +2101,13 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         }
     }
     // 6. leaf evaluation (folded into the downward launch for the compile-time 2D orders)
-    if (phase == 4 && I->neval > 0 && !fixed2d) {
+    if (phase == 4 && I->neval > 0 && D == 3 && (pd.p == 16 || pd.p == 24 || pd.p == 32)) {
+        const T* t4 = static_cast<const T*>(pw->d_tgt4);
+        if (pd.p == 16) k_leaf_eval3d_p<T, 16><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
+        else if (pd.p == 24) k_leaf_eval3d_p<T, 24><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
+        else k_leaf_eval3d_p<T, 32><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
+        ++pw->launches;
+    } else if (phase == 4 && I->neval > 0 && !fixed2d) {
         size_t sm = ts * 32 * 2 * D * pd.p;
         cudaFuncSetAttribute(k_leaf_eval<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_leaf_eval<T, D><<<I->neval, 32, sm, s>>>(I->d_eval, L, static_cast<const T*>(pw->d_tgt4), pw->d_pot,
