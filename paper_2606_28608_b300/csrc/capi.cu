@@ -96,6 +96,7 @@ struct pdmk_plan_s {
     // source-dependent device buffers
     int64_t n = 0, nimg = 0, ntgt = 0, nspread = 0;
     int nbox = 0, ntleaf = 0, nsub = 0, nbins_tot = 1;
+    int nnear = 0;  // near-field descriptors (target leaves cut into groups of 32 targets)
     void* d_src4 = nullptr;
     int* d_src_orig = nullptr;
     void* d_tgt4 = nullptr;
@@ -766,8 +767,24 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
             }
         }
     }
-    // the warp near-field kernel takes leaves in order of decreasing pair count (the long
-    // ones start first)
+    // the warp near-field kernel computes 32 targets at a time: a leaf with more targets
+    // becomes several descriptors over the same direct list (one warp each, so leaves of a
+    // few hundred targets do not leave the grid short of warps; every target is still summed
+    // by one lane in the same order). Descriptors are taken in order of decreasing pair
+    // count (the long ones start first).
+    if (plan->near_nh > 0) {
+        std::vector<TLeaf> split;
+        split.reserve(tl.size() * 2);
+        for (const TLeaf& L : tl)
+            for (int t0 = 0; t0 < std::max(L.tgt_count, 1); t0 += 32) {
+                TLeaf c = L;
+                c.tgt_begin = L.tgt_begin + t0;
+                c.tgt_count = std::min(32, L.tgt_count - t0);
+                split.push_back(c);
+            }
+        tl.swap(split);
+    }
+    plan->nnear = int(tl.size());
     {
         std::vector<int64_t> cost(tl.size(), 0);
         for (size_t k = 0; k < tl.size(); ++k) {
@@ -1177,10 +1194,10 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         if ((r = stage_mark(plan, pw_names[ph]))) return r;
     }
     plan->launches += plan->pw.launches;
-    if (plan->ntleaf > 0) {
+    if (plan->nnear > 0) {
         NearArgs<T> na;
         na.tleaf = plan->d_tleaf;
-        na.ntleaf = plan->ntleaf;
+        na.ntleaf = plan->nnear;
         na.list = plan->d_list;
         na.box_src_begin = plan->d_box_src_begin;
         na.box_src_count = plan->d_box_src_count;
@@ -1208,7 +1225,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         na.monoA = static_cast<const T*>(plan->d_monoA);
         na.monoB = static_cast<const T*>(plan->d_monoB);
         const int nc = std::max(na.nA, na.nB);
-        const int wb = (plan->ntleaf + kNearWarps - 1) / kNearWarps, wt = 32 * kNearWarps;
+        const int wb = (plan->nnear + kNearWarps - 1) / kNearWarps, wt = 32 * kNearWarps;
         // A is usually two terms shorter than B: its own compile-time length then
         const bool ash = na.nA <= plan->near_nh - 2;
 #define PDMK_NEAR(NH)                                                                         \
@@ -1222,13 +1239,13 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         else if (plan->near_nh == 20) PDMK_NEAR(20);
         else if (plan->near_nh == 24) PDMK_NEAR(24);
 #undef PDMK_NEAR
-        else if (nc <= 8) k_nearfield<T, D, 8><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 12) k_nearfield<T, D, 12><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 16) k_nearfield<T, D, 16><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 20) k_nearfield<T, D, 20><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 24) k_nearfield<T, D, 24><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 32) k_nearfield<T, D, 32><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
-        else k_nearfield<T, D, 40><<<plan->ntleaf, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 8) k_nearfield<T, D, 8><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 12) k_nearfield<T, D, 12><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 16) k_nearfield<T, D, 16><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 20) k_nearfield<T, D, 20><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 24) k_nearfield<T, D, 24><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
+        else if (nc <= 32) k_nearfield<T, D, 32><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
+        else k_nearfield<T, D, 40><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
         ++plan->launches;
         CK(cudaGetLastError());
     }
