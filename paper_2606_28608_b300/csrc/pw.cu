@@ -793,6 +793,230 @@ __global__ void __launch_bounds__(128) k_pw_in(const int* __restrict__ list, con
     }
 }
 
+// ------------------------------------------------------------------ 3D compile-time outgoing / incoming
+// The parity of the Chebyshev coefficients of exp(-i (pi/3) k t) makes every contraction with
+// Co real: Co[k][2j] = ce[|k|][j] (real, even in k), Co[k][2j+1] = i sgn(k) so[|k|][j].  So
+// each axis transform works on the half range k >= 0 and forms the pair of modes +-k at once.
+// Both kernels take one box per block of P^2 threads, thread (m1, m2), and walk the k0 axis
+// (the Hermitian half 0..K) slice by slice.
+
+// Outgoing waves of one box, out[k0][k1][k2] = sum_m Co[k0][m0] Co[k1][m1] Co[k2][m2] q[m]:
+//   A[m1][m2]  = sum_j ce[k0][j] q[2j][m1][m2] + i so[k0][j] q[2j+1][m1][m2]   (thread's own q)
+//   B[+-k1][m2] = E +- i O,  E = sum_j ce[k1][j] A[2j][m2],  O = sum_j so[k1][j] A[2j+1][m2]
+//   out[k0][k1][+-k2] = E' +- i O' over m2 in the same way.
+template <typename T, int P, int K>
+__global__ void __launch_bounds__(P * P) k_pw_out3d_p(const int2* __restrict__ list, const T* __restrict__ Q,
+                                                     C2<T>* __restrict__ out, const C2<T>* __restrict__ Cog) {
+    constexpr int H = P / 2, KH = K + 1, N1 = 2 * K + 1, PP = P * P, NPW = KH * N1 * N1;
+    __shared__ T ce[KH][H], so[KH][H];
+    __shared__ C2<T> A[PP];      // [m1][m2]
+    __shared__ C2<T> B[N1][P];   // [k1 + K][m2]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < KH * H; i += PP) {
+        const int k = i / H, j = i % H;
+        ce[k][j] = Cog[(k + K) * P + 2 * j].x;
+        so[k][j] = Cog[(k + K) * P + 2 * j + 1].y;
+    }
+    const int2 e = list[blockIdx.x];
+    const T* q = Q + size_t(e.x) * (PP * P);
+    C2<T>* o = out + size_t(e.y) * NPW;
+    T qr[P];
+#pragma unroll
+    for (int m0 = 0; m0 < P; ++m0) qr[m0] = q[m0 * PP + tid];
+    __syncthreads();
+    for (int k0 = 0; k0 <= K; ++k0) {
+        {
+            T ax = T(0), ay = T(0);
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                ax = fma(ce[k0][j], qr[2 * j], ax);
+                ay = fma(so[k0][j], qr[2 * j + 1], ay);
+            }
+            A[tid] = C2<T>{ax, ay};
+        }
+        __syncthreads();
+        if (tid < KH * P) {
+            const int k1 = tid / P, m2 = tid % P;
+            T ex = T(0), ey = T(0), ox = T(0), oy = T(0);
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                const C2<T> ae = A[(2 * j) * P + m2], ao = A[(2 * j + 1) * P + m2];
+                const T c = ce[k1][j], s = so[k1][j];
+                ex = fma(c, ae.x, ex);
+                ey = fma(c, ae.y, ey);
+                ox = fma(s, ao.x, ox);
+                oy = fma(s, ao.y, oy);
+            }
+            B[K + k1][m2] = C2<T>{ex - oy, ey + ox};  // E + i O
+            if (k1 > 0) B[K - k1][m2] = C2<T>{ex + oy, ey - ox};
+        }
+        __syncthreads();
+        C2<T>* os = o + size_t(k0) * (N1 * N1);
+        for (int it = tid; it < N1 * KH; it += PP) {
+            const int kk1 = it / KH, k2 = it % KH;
+            T ex = T(0), ey = T(0), ox = T(0), oy = T(0);
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                const C2<T> be = B[kk1][2 * j], bo = B[kk1][2 * j + 1];
+                const T c = ce[k2][j], s = so[k2][j];
+                ex = fma(c, be.x, ex);
+                ey = fma(c, be.y, ey);
+                ox = fma(s, bo.x, ox);
+                oy = fma(s, bo.y, oy);
+            }
+            os[kk1 * N1 + K + k2] = C2<T>{ex - oy, ey + ox};
+            if (k2 > 0) os[kk1 * N1 + K - k2] = C2<T>{ex + oy, ey - ox};
+        }
+        // the next slice rewrites A only: every thread is past the reads of A (barrier above),
+        // and B is rewritten only after the next barrier
+    }
+}
+
+// Translation + incoming of one in-box (list entry: local slot, level, 27 colleague out slots).
+// Per slice k0:
+//  1. thread (k1, k2 >= 0) sums the colleagues' waves at (k0, k1, +-k2) with the phases
+//     exp(-i (2 pi/3) k.delta), which factor by axis; along each axis the three colleagues
+//     combine as X_0 + Re(u) (X_+ + X_-) +- i Im(u) (X_+ - X_-), the sign following the mode.
+//     The weighted pair is kept as Sp = I(+k2) + I(-k2), Sm = I(+k2) - I(-k2).
+//  2. thread (k1 >= 0, m2): contraction over k2 with conj(Co) (ce Sp for even m2, -i so Sm
+//     for odd m2) for the rows +-k1, kept again as the sum Bp and the difference Bm.
+//  3. thread (m1, m2): contraction over k1 the same way, then
+//     a[2j][m1][m2] += w ce[k0][j] Re(.), a[2j+1][m1][m2] += w so[k0][j] Im(.),
+//     w = 1 for k0 = 0, else 2 (the Hermitian half of the k0 axis), in registers.
+// Each in-box has one entry: the coefficients are written, not added.
+template <typename T, int P, int K>
+__global__ void __launch_bounds__(P * P) k_pw_in3d_p(const int* __restrict__ list, const C2<T>* __restrict__ out,
+                                                    T* __restrict__ Lc, const C2<T>* __restrict__ Cog,
+                                                    const C2<T>* __restrict__ phg, const T* __restrict__ fk,
+                                                    double inv_rc) {
+    constexpr int H = P / 2, KH = K + 1, N1 = 2 * K + 1, PP = P * P, NK1 = N1 * N1, NPW = KH * NK1;
+    __shared__ T ce[KH][H], so[KH][H];
+    __shared__ C2<T> u[N1];                  // exp(-i (2 pi/3) k), k = -K..K
+    __shared__ C2<T> Sp[N1][KH], Sm[N1][KH];  // [k1 + K][k2]
+    __shared__ C2<T> Bp[KH][P], Bm[KH][P];    // [k1][m2]
+    __shared__ int coll[27];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < KH * H; i += PP) {
+        const int k = i / H, j = i % H;
+        ce[k][j] = Cog[(k + K) * P + 2 * j].x;
+        so[k][j] = Cog[(k + K) * P + 2 * j + 1].y;
+    }
+    for (int i = tid; i < N1; i += PP) u[i] = phg[2 * N1 + i];  // delta = +1
+    const int* e = list + size_t(blockIdx.x) * 29;
+    if (tid < 27) coll[tid] = e[2 + tid];
+    __syncthreads();
+    const int level = e[1];
+    // trapezoidal weight (1/(3h))^3 times the h^2 of D-hat_l(xi) = h^2 f(|k|)
+    const T wlev = T(double(1LL << level) * inv_rc / 27.0);
+    T acc[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) acc[m] = T(0);
+    const int m1 = tid / P, m2 = tid % P;
+    for (int k0 = 0; k0 <= K; ++k0) {
+        // 1. weighted sums over the colleagues, modes (k0, k1, +-k2)
+        for (int it = tid; it < N1 * KH; it += PP) {
+            const int kk1 = it / KH, k2 = it % KH;
+            const T fw = fk[size_t(k0) * NK1 + kk1 * N1 + K + k2] * wlev;
+            C2<T> ip{T(0), T(0)}, im{T(0), T(0)};
+            if (fw != T(0)) {
+                const C2<T> u2 = u[K + k2], u1 = u[kk1], u0 = u[K + k0];
+                const size_t op = size_t(k0) * NK1 + size_t(kk1) * N1 + K + k2;
+                const size_t om = op - 2 * k2;
+                const C2<T> z{T(0), T(0)};
+                C2<T> tp[3], tm[3];  // per delta0: sums over delta1, delta2
+#pragma unroll
+                for (int d0 = 0; d0 < 3; ++d0) {
+                    C2<T> rp[3], rm[3];  // per delta1: sums over delta2
+#pragma unroll
+                    for (int d1 = 0; d1 < 3; ++d1) {
+                        const int sM = coll[d0 + 3 * d1], s0 = coll[d0 + 3 * d1 + 9], sP = coll[d0 + 3 * d1 + 18];
+                        const C2<T> pP = sP >= 0 ? out[size_t(sP) * NPW + op] : z;
+                        const C2<T> pM = sM >= 0 ? out[size_t(sM) * NPW + op] : z;
+                        const C2<T> p0 = s0 >= 0 ? out[size_t(s0) * NPW + op] : z;
+                        const C2<T> mP = sP >= 0 ? out[size_t(sP) * NPW + om] : z;
+                        const C2<T> mM = sM >= 0 ? out[size_t(sM) * NPW + om] : z;
+                        const C2<T> m0 = s0 >= 0 ? out[size_t(s0) * NPW + om] : z;
+                        rp[d1].x = p0.x + u2.x * (pP.x + pM.x) - u2.y * (pP.y - pM.y);
+                        rp[d1].y = p0.y + u2.x * (pP.y + pM.y) + u2.y * (pP.x - pM.x);
+                        rm[d1].x = m0.x + u2.x * (mP.x + mM.x) + u2.y * (mP.y - mM.y);
+                        rm[d1].y = m0.y + u2.x * (mP.y + mM.y) - u2.y * (mP.x - mM.x);
+                    }
+                    // axis 1: the mode k1 is the same for both members of the pair
+                    tp[d0].x = rp[1].x + u1.x * (rp[2].x + rp[0].x) - u1.y * (rp[2].y - rp[0].y);
+                    tp[d0].y = rp[1].y + u1.x * (rp[2].y + rp[0].y) + u1.y * (rp[2].x - rp[0].x);
+                    tm[d0].x = rm[1].x + u1.x * (rm[2].x + rm[0].x) - u1.y * (rm[2].y - rm[0].y);
+                    tm[d0].y = rm[1].y + u1.x * (rm[2].y + rm[0].y) + u1.y * (rm[2].x - rm[0].x);
+                }
+                ip.x = fw * (tp[1].x + u0.x * (tp[2].x + tp[0].x) - u0.y * (tp[2].y - tp[0].y));
+                ip.y = fw * (tp[1].y + u0.x * (tp[2].y + tp[0].y) + u0.y * (tp[2].x - tp[0].x));
+                im.x = fw * (tm[1].x + u0.x * (tm[2].x + tm[0].x) - u0.y * (tm[2].y - tm[0].y));
+                im.y = fw * (tm[1].y + u0.x * (tm[2].y + tm[0].y) + u0.y * (tm[2].x - tm[0].x));
+            }
+            if (k2 == 0) {
+                Sp[kk1][0] = ip;  // the +-k2 modes coincide
+                Sm[kk1][0] = C2<T>{T(0), T(0)};
+            } else {
+                Sp[kk1][k2] = C2<T>{ip.x + im.x, ip.y + im.y};
+                Sm[kk1][k2] = C2<T>{ip.x - im.x, ip.y - im.y};
+            }
+        }
+        __syncthreads();
+        // 2. over k2, rows +-k1
+        if (tid < KH * P) {
+            const int k1 = tid / P, n2 = tid % P, j = n2 >> 1;
+            const bool odd = n2 & 1;
+            const T* tab = odd ? &so[0][j] : &ce[0][j];
+            const C2<T>* sP = odd ? &Sm[K + k1][0] : &Sp[K + k1][0];
+            const C2<T>* sN = odd ? &Sm[K - k1][0] : &Sp[K - k1][0];
+            T px = T(0), py = T(0), nx = T(0), ny = T(0);
+#pragma unroll
+            for (int k2 = 0; k2 < KH; ++k2) {
+                const T c = tab[k2 * H];
+                const C2<T> a = sP[k2], b = sN[k2];
+                px = fma(c, a.x, px);
+                py = fma(c, a.y, py);
+                nx = fma(c, b.x, nx);
+                ny = fma(c, b.y, ny);
+            }
+            // odd m2: times -i
+            C2<T> vp = odd ? C2<T>{py, -px} : C2<T>{px, py};
+            C2<T> vn = odd ? C2<T>{ny, -nx} : C2<T>{nx, ny};
+            if (k1 == 0) vn = C2<T>{T(0), T(0)};
+            Bp[k1][n2] = C2<T>{vp.x + vn.x, vp.y + vn.y};
+            Bm[k1][n2] = k1 == 0 ? C2<T>{T(0), T(0)} : C2<T>{vp.x - vn.x, vp.y - vn.y};
+        }
+        __syncthreads();
+        // 3. over k1 (thread's own (m1, m2)), then over k0 into the registers
+        {
+            const bool odd = m1 & 1;
+            const int j1 = m1 >> 1;
+            const T* tab = odd ? &so[0][j1] : &ce[0][j1];
+            const C2<T>* bb = odd ? &Bm[0][m2] : &Bp[0][m2];
+            T ax = T(0), ay = T(0);
+#pragma unroll
+            for (int k1 = 0; k1 < KH; ++k1) {
+                const T c = tab[k1 * H];
+                const C2<T> v = bb[k1 * P];
+                ax = fma(c, v.x, ax);
+                ay = fma(c, v.y, ay);
+            }
+            const T re = odd ? ay : ax, im_ = odd ? -ax : ay;  // odd m1: times -i
+            const T w = k0 == 0 ? T(1) : T(2);
+            const T wr = w * re, wi = w * im_;
+#pragma unroll
+            for (int j0 = 0; j0 < H; ++j0) {
+                acc[2 * j0] = fma(ce[k0][j0], wr, acc[2 * j0]);
+                acc[2 * j0 + 1] = fma(so[k0][j0], wi, acc[2 * j0 + 1]);
+            }
+        }
+        // the next slice rewrites Sp / Sm only (every thread is past step 2); Bp / Bm are
+        // rewritten after the next barrier
+    }
+    T* a = Lc + size_t(e[0]) * (PP * P);
+#pragma unroll
+    for (int m0 = 0; m0 < P; ++m0) a[m0 * PP + tid] = acc[m0];
+}
+
 // 3D leaf evaluation with a compile-time order P: one warp per leaf, a thread per target.  The
 // z-axis T_m, T'_m sit in registers, the x- and y-axis ones in shared memory (interleaved by
 // thread), and the leaf's coefficient rows are read as vectors (all lanes read the same row:
@@ -2024,7 +2248,12 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     }
     // 3. outgoing plane waves (all levels); fused into the moments launch for the compile-time
     //    2D orders
-    if (phase == 1 && I->nout > 0 && !fixed2d) {
+    const bool fixed3d = D == 3 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16));
+    if (phase == 1 && I->nout > 0 && fixed3d) {
+        if (pd.p == 16) k_pw_out3d_p<T, 16, 9><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co);
+        else k_pw_out3d_p<T, 24, 16><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co);
+        ++pw->launches;
+    } else if (phase == 1 && I->nout > 0 && !fixed2d) {
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + 2 * size_t(pd.n1) * pd.p);
         cudaFuncSetAttribute(k_pw_out<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_pw_out<T, D><<<I->nout, 128, sm, s>>>(I->d_outl, Q, out, Co, pd, std::min(I->KC, 16));
@@ -2038,6 +2267,12 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         if (pd.p == 16) k_pw_in2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
         else if (pd.p == 24) k_pw_in2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
         else k_pw_in2d_p<T, 32, 23><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
+        ++pw->launches;
+    } else if (phase == 2 && I->nin > 0 && fixed3d) {
+        const C2<T>* ph = static_cast<const C2<T>*>(I->d_ph);
+        const T* fk = static_cast<const T*>(I->d_f);
+        if (pd.p == 16) k_pw_in3d_p<T, 16, 9><<<I->nin, 256, 0, s>>>(I->d_inl, out, L, Co, ph, fk, inv_rc);
+        else k_pw_in3d_p<T, 24, 16><<<I->nin, 576, 0, s>>>(I->d_inl, out, L, Co, ph, fk, inv_rc);
         ++pw->launches;
     } else if (phase == 2 && I->nin > 0) {
         const int KC = std::min(I->KC, 16);
