@@ -134,14 +134,21 @@ int oracle_ewald(int d, const double* L, int64_t n, const double* y, const doubl
     double V = fabs(det);
     if (!(V > 0)) return -1;
 
-    /* fractional coordinates of sources, wrapped into [0,1) */
+    /* fractional coordinates of sources, wrapped into [0,1), and the whole lattice steps
+       the wrap took (w_j = floor(L^{-1} y_j)): v locates a source for the binning and the
+       structure factors, while a pair's displacement x - y_j - L n is formed from the
+       caller's coordinates with the integer shift n, so that nearby points keep their
+       exact difference */
     double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * d);
-    if (!v) return -1;
+    int* wj = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1) * d);
+    if (!v || !wj) { free(v); free(wj); return -1; }
     for (int64_t j = 0; j < n; ++j)
         for (int a = 0; a < d; ++a) {
             double s = 0;
             for (int b = 0; b < d; ++b) s += Li[a + b * d] * y[j * d + b];
-            v[j * d + a] = s - floor(s);
+            const double f = floor(s);
+            v[j * d + a] = s - f;
+            wj[j * d + a] = (int)f;
         }
 
     long double Qsum = 0;
@@ -165,7 +172,7 @@ int oracle_ewald(int d, const double* L, int64_t n, const double* y, const doubl
     int64_t* bstart = (int64_t*)calloc((size_t)nbins + 1, sizeof(int64_t));
     int64_t* border = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int64_t* bcur = (int64_t*)calloc((size_t)nbins + 1, sizeof(int64_t));
-    if (!bstart || !border || !bcur) { free(v); free(bstart); free(border); free(bcur); return -1; }
+    if (!bstart || !border || !bcur) { free(v); free(wj); free(bstart); free(border); free(bcur); return -1; }
 #define BIN_OF(uu, a) ((int)((uu) * nb[a]) >= nb[a] ? nb[a] - 1 : (int)((uu) * nb[a]))
     for (int64_t j = 0; j < n; ++j) {
         int64_t b = 0;
@@ -197,7 +204,7 @@ int oracle_ewald(int d, const double* L, int64_t n, const double* y, const doubl
     int* modes = (int*)malloc(sizeof(int) * (size_t)cap * 3);
     double* kvec = (double*)malloc(sizeof(double) * (size_t)cap * 3);
     double* gk = (double*)malloc(sizeof(double) * (size_t)cap);
-    if (!modes || !kvec || !gk) { free(v); free(bstart); free(border); free(modes); free(kvec); free(gk); return -1; }
+    if (!modes || !kvec || !gk) { free(v); free(wj); free(bstart); free(border); free(modes); free(kvec); free(gk); return -1; }
     int64_t nk = 0;
     int m2lo = (d == 3) ? -mmax[2] : 0, m2hi = (d == 3) ? mmax[2] : 0;
     for (int m0 = 0; m0 <= mmax[0]; ++m0)
@@ -232,7 +239,7 @@ int oracle_ewald(int d, const double* L, int64_t n, const double* y, const doubl
     for (int a = 0; a < d; ++a) tw += mmax[a] + 1;
     double* tab = (double*)malloc(sizeof(double) * (size_t)blk * tw * 2);
     if (!rho_re || !rho_im || !tab) {
-        free(v); free(bstart); free(border); free(modes); free(kvec); free(gk);
+        free(v); free(wj); free(bstart); free(border); free(modes); free(kvec); free(gk);
         free(rho_re); free(rho_im); free(tab); return -1;
     }
     int toff[3] = {0, 0, 0};
@@ -283,16 +290,12 @@ int oracle_ewald(int d, const double* L, int64_t n, const double* y, const doubl
         }
         /* wrapped target and the lattice shift that wraps it */
         double uw[3] = {0, 0, 0};
-        int tb[3] = {0, 0, 0};
+        int tb[3] = {0, 0, 0}, tw[3] = {0, 0, 0};
         for (int a = 0; a < d; ++a) {
-            uw[a] = u[a] - floor(u[a]);
+            const double f = floor(u[a]);
+            uw[a] = u[a] - f;
+            tw[a] = (int)f;
             tb[a] = BIN_OF(uw[a], a);
-        }
-        double xw[3] = {0, 0, 0};
-        for (int b = 0; b < d; ++b) {
-            double s = 0;
-            for (int a = 0; a < d; ++a) s += L[b + a * d] * uw[a];
-            xw[b] = s;
         }
         int64_t self = self_idx ? self_idx[i] : -1;
         long double phi = 0, g[3] = {0, 0, 0};
@@ -311,21 +314,19 @@ int oracle_ewald(int d, const double* L, int64_t n, const double* y, const doubl
                     }
                     int64_t bidx = 0;
                     for (int a = d - 1; a >= 0; --a) bidx = bidx * nb[a] + bb[a];
-                    double shift[3] = {0, 0, 0};
-                    for (int b = 0; b < d; ++b) {
-                        double s = 0;
-                        for (int a = 0; a < d; ++a) s += L[b + a * d] * sh[a];
-                        shift[b] = s;
-                    }
                     int zero_shift = 1;
                     for (int a = 0; a < d; ++a) zero_shift &= (sh[a] == 0);
                     for (int64_t t = bstart[bidx]; t < bstart[bidx + 1]; ++t) {
                         int64_t j = border[t];
+                        /* x - y_j - L n with n = tw - w_j + sh: the wrapped target minus the
+                           shifted wrapped source, written in the caller's coordinates */
+                        int nn[3] = {0, 0, 0};
+                        for (int a = 0; a < d; ++a) nn[a] = tw[a] - wj[j * d + a] + sh[a];
                         double dx[3] = {0, 0, 0}, r2 = 0;
                         for (int b = 0; b < d; ++b) {
-                            double yb = 0;
-                            for (int a = 0; a < d; ++a) yb += L[b + a * d] * v[j * d + a];
-                            dx[b] = xw[b] - (yb + shift[b]);
+                            double ln = 0;
+                            for (int a = 0; a < d; ++a) ln += L[b + a * d] * nn[a];
+                            dx[b] = (xi[b] - y[j * d + b]) - ln;
                             r2 += dx[b] * dx[b];
                         }
                         if (r2 > rc2) continue;
@@ -359,7 +360,7 @@ int oracle_ewald(int d, const double* L, int64_t n, const double* y, const doubl
             for (int b = 0; b < d; ++b) grad[i * d + b] = (double)g[b];
     }
 #undef BIN_OF
-    free(v); free(bstart); free(border); free(modes); free(kvec); free(gk);
+    free(v); free(wj); free(bstart); free(border); free(modes); free(kvec); free(gk);
     free(rho_re); free(rho_im);
     return err;
 }
