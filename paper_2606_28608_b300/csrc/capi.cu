@@ -86,6 +86,7 @@ struct pdmk_plan_s {
     void* d_monoWd = nullptr;
     double* d_weight = nullptr;
     void* d_grid = nullptr;
+    void* d_grid64 = nullptr;  // FP64 grid of the transforms (the grid itself for FP64 plans)
     void* d_spec = nullptr;
     double* d_qsums = nullptr;
     double* d_qsum_part = nullptr;  // [kSumBlocks][3] partial charge sums
@@ -512,7 +513,17 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
         PCHECK(upload(plan, plan->d_weight, wt));
         PCHECK(dalloc(plan, plan->plan_allocs, &p, ts * size_t(plan->ncell)));
         plan->d_grid = p;
-        PCHECK(dalloc(plan, plan->plan_allocs, &p, 2 * ts * size_t(plan->nhalf)));
+        // the transforms and the k-space scaling run in FP64 for both precisions: rounding
+        // that enters before the scaling is amplified by the window deconvolution near the
+        // band edge, and an FP32 transform's error (~1e-7 log N of the grid norm) would
+        // reach ~1e-6 of a far-field-dominated potential
+        if (mixed) {
+            PCHECK(dalloc(plan, plan->plan_allocs, &p, sizeof(double) * size_t(plan->ncell)));
+            plan->d_grid64 = p;
+        } else {
+            plan->d_grid64 = plan->d_grid;
+        }
+        PCHECK(dalloc(plan, plan->plan_allocs, &p, 2 * sizeof(double) * size_t(plan->nhalf)));
         plan->d_spec = p;
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsums, 4));
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsum_part, size_t(3 * kSumBlocks)));
@@ -520,7 +531,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     }
     {
         const Geometry& g = plan->g;
-        cufftType tf = mixed ? CUFFT_R2C : CUFFT_D2Z, ti = mixed ? CUFFT_C2R : CUFFT_Z2D;
+        const cufftType tf = CUFFT_D2Z, ti = CUFFT_Z2D;
         cufftResult fr;
         if (d == 2) {
             fr = cufftPlan2d(&plan->fft_fwd, g.M[1], g.M[0], tf);
@@ -700,14 +711,65 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     for (int b = 0; b < st.nboxes; ++b)
         if (tree.is_leaf(b))
             for (int64_t j = tree.src_begin[b]; j < tree.src_end[b]; ++j) leaf_of[j] = b;
-    // sorted sources: coordinates relative to their leaf centre (FP64 difference, then T)
+    // Leaf-relative coordinates, taken in the caller's frame.  Two nearby inputs differ
+    // exactly there, while their oriented, wrapped copies (ss.pos) carry roundings of the
+    // size of the cell's coordinates, which a pair 1e-4 of the cell apart would see at
+    // 1e-11.  So every leaf gets a caller-frame centre C_b = Q^T c_b (any fixed double
+    // vector serves), a copy of source o shifted by the lattice vector R m (tree frame) gets
+    //   rel = Q (y_o - Q^T (c_b - R m)),   which is y_o - C_b rotated when m = 0,
+    // and the leaf-to-leaf shifts of the direct lists are Q (C_s - C_t): for originals the
+    // pair displacement rel_t - rel_s - sh is Q (y_t - y_s) up to roundings of leaf-sized
+    // terms.  Pairs with an image keep the rounding of the lattice shift itself.
+    auto to_user = [&](const double* v, double* out) {  // Q^T v
+        for (int i = 0; i < d; ++i) {
+            double s = 0;
+            for (int k = 0; k < d; ++k) s += g.Q[k * d + i] * v[k];
+            out[i] = s;
+        }
+    };
+    auto to_tree = [&](const double* v, double* out) {  // Q v
+        for (int i = 0; i < d; ++i) {
+            double s = 0;
+            for (int k = 0; k < d; ++k) s += g.Q[i * d + k] * v[k];
+            out[i] = s;
+        }
+    };
+    std::vector<double> Cu(size_t(st.nboxes) * d);
+    for (int b = 0; b < st.nboxes; ++b) to_user(&tree.center[size_t(b) * d], &Cu[size_t(b) * d]);
+    std::vector<double> relv(size_t(plan->nimg) * d);
+    for (int64_t j = 0; j < plan->nimg; ++j) {
+        const int b = leaf_of[j];
+        const int64_t o = ss.orig[j];
+        double yo[3] = {0, 0, 0}, xo[3], m[3], D[3], E[3], du[3];
+        for (int a = 0; a < d; ++a) yo[a] = hy[size_t(o) * d + a];
+        to_tree(yo, xo);
+        bool shifted = false;
+        for (int i = 0; i < d; ++i) {
+            double f = 0;
+            for (int k = 0; k < d; ++k) f += g.Rinv[i * d + k] * (ss.pos[j * d + k] - xo[k]);
+            m[i] = std::nearbyint(f);
+            shifted |= m[i] != 0.0;
+        }
+        if (shifted) {
+            for (int i = 0; i < d; ++i) {
+                double s = 0;
+                for (int k = 0; k < d; ++k) s += g.R[i * d + k] * m[k];
+                D[i] = tree.center[size_t(b) * d + i] - s;
+            }
+            to_user(D, E);
+        } else {
+            for (int i = 0; i < d; ++i) E[i] = Cu[size_t(b) * d + i];
+        }
+        for (int a = 0; a < d; ++a) du[a] = yo[a] - E[a];
+        to_tree(du, &relv[size_t(j) * d]);
+    }
+    // sorted sources: coordinates relative to their leaf centre (FP64, then T)
     std::vector<unsigned char> src4(size_t(plan->nimg) * 4 * ts, 0);
     std::vector<int> src_orig(size_t(plan->nimg));
     std::vector<float> src_lo(mixed ? size_t(plan->nimg) * 4 : 0, 0.0f);
     for (int64_t j = 0; j < plan->nimg; ++j) {
-        int b = leaf_of[j];
         for (int a = 0; a < d; ++a) {
-            const double rel = ss.pos[j * d + a] - tree.center[size_t(b) * d + a];
+            const double rel = relv[size_t(j) * d + a];
             put(src4, size_t(j) * 4 + a, rel);
             if (mixed) src_lo[size_t(j) * 4 + a] = float(rel - double(float(rel)));
         }
@@ -724,7 +786,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         int b = leaf_of[j];
         tgt_leaf[t] = b;
         for (int a = 0; a < d; ++a) {
-            const double rel = ss.pos[j * d + a] - tree.center[size_t(b) * d + a];
+            const double rel = relv[size_t(j) * d + a];
             put(tgt4, size_t(t) * 4 + a, rel);
             if (mixed) tgt_lo[size_t(t) * 4 + a] = float(rel - double(float(rel)));
         }
@@ -760,8 +822,11 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         for (int64_t e = dl.list_begin[k]; e < dl.list_begin[k + 1]; ++e) {
             const int sb = dl.list[e];
             ent[e] = make_int2(bsb[sb], bsc[sb]);
+            double du[3] = {0, 0, 0}, sht[3];
+            for (int a = 0; a < d; ++a) du[a] = Cu[size_t(sb) * d + a] - Cu[size_t(tb) * d + a];
+            to_tree(du, sht);
             for (int a = 0; a < d; ++a) {
-                const double sh = tree.center[size_t(sb) * d + a] - tree.center[size_t(tb) * d + a];
+                const double sh = sht[a];
                 put(ent_sh, size_t(e) * 4 + a, sh);
                 if (mixed) ent_shlo[size_t(e) * 4 + a] = float(sh - double(float(sh)));
             }
@@ -1036,7 +1101,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         CK(cudaGetLastError());
         const int blocks = int((plan->ncell + 31) / 32);
         k_fold_whole<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<const T*>(slab), plan->whole_ctas,
-                                                            static_cast<T*>(plan->d_grid), int(plan->ncell));
+                                                            static_cast<double*>(plan->d_grid64), int(plan->ncell));
         ++plan->launches;
         CK(cudaGetLastError());
     } else if (D == 2 && plan->whole_ctas > 0) {
@@ -1068,7 +1133,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         CK(cudaGetLastError());
         const int blocks = int((plan->ncell + 31) / 32);
         k_fold_whole<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<const T*>(slab), plan->whole_ctas,
-                                                            static_cast<T*>(plan->d_grid), int(plan->ncell));
+                                                            static_cast<double*>(plan->d_grid64), int(plan->ncell));
         ++plan->launches;
         CK(cudaGetLastError());
     } else {
@@ -1096,7 +1161,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         FoldArgs<T> fa;
         fa.slab = static_cast<const T*>(slab);
         fa.bin_sub_begin = plan->d_bin_sub_begin;
-        fa.grid = static_cast<T*>(plan->d_grid);
+        fa.grid = static_cast<double*>(plan->d_grid64);
         fa.M0 = g.M[0]; fa.M1 = g.M[1]; fa.M2 = g.M[2];
         fa.nb0 = plan->nbin[0]; fa.nb1 = plan->nbin[1]; fa.nb2 = plan->nbin[2];
         fa.B0 = plan->B[0]; fa.B1 = plan->B[1]; fa.B2 = plan->B[2];
@@ -1109,26 +1174,27 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
     }
     }
     if ((r = stage_mark(plan, "spread"))) return r;
-    if (sizeof(T) == 4) {
-        CKFFT(cufftExecR2C(plan->fft_fwd, (cufftReal*)plan->d_grid, (cufftComplex*)plan->d_spec));
-    } else {
-        CKFFT(cufftExecD2Z(plan->fft_fwd, (cufftDoubleReal*)plan->d_grid, (cufftDoubleComplex*)plan->d_spec));
-    }
+    const int cblocks = int(std::max<int64_t>(1, std::min<int64_t>((plan->ncell + 255) / 256, 148 * 8)));
+    CKFFT(cufftExecD2Z(plan->fft_fwd, (cufftDoubleReal*)plan->d_grid64, (cufftDoubleComplex*)plan->d_spec));
     if ((r = stage_mark(plan, "fft_fwd"))) return r;
     {
         int blocks = int(std::min<int64_t>((plan->nhalf + 255) / 256, 148 * 8));
-        k_scale<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<T*>(plan->d_spec), plan->d_weight, plan->nhalf);
+        k_scale<double><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<double*>(plan->d_spec), plan->d_weight,
+                                                            plan->nhalf);
         ++plan->launches;
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "scale"))) return r;
-    if (sizeof(T) == 4) {
-        CKFFT(cufftExecC2R(plan->fft_inv, (cufftComplex*)plan->d_spec, (cufftReal*)plan->d_grid));
-    } else {
-        CKFFT(cufftExecZ2D(plan->fft_inv, (cufftDoubleComplex*)plan->d_spec, (cufftDoubleReal*)plan->d_grid));
+    CKFFT(cufftExecZ2D(plan->fft_inv, (cufftDoubleComplex*)plan->d_spec, (cufftDoubleReal*)plan->d_grid64));
+    const bool interp_halo = plan->ntgt > 0 && D == 2 && plan->far_halo && sizeof(T) == 4;
+    if (sizeof(T) == 4 && !interp_halo) {  // the halo interpolation reads the FP64 grid itself
+        k_convert<double, T><<<cblocks, 256, 0, s>>>(static_cast<const double*>(plan->d_grid64),
+                                                     static_cast<T*>(plan->d_grid), plan->ncell);
+        ++plan->launches;
+        CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "fft_inv"))) return r;
-    if (plan->ntgt > 0 && D == 2 && plan->far_halo && sizeof(T) == 4) {
+    if (interp_halo) {
         const int Mp0 = g.M[0] + plan->w - 1, Mp1 = g.M[1] + plan->w - 1;
         const size_t smem = sizeof(T) * size_t(Mp0) * Mp1;
         auto interp = [&](auto kern) {
@@ -1139,7 +1205,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
             const int grid = int(std::max<int64_t>(1, std::min<int64_t>((plan->ntgt + 255) / 256,
                                                                         int64_t(std::max(1, per_sm)) * nsm)));
-            kern<<<grid, 256, smem, s>>>(static_cast<const T*>(plan->d_grid), plan->d_t_g0,
+            kern<<<grid, 256, smem, s>>>(static_cast<const double*>(plan->d_grid64), plan->d_t_g0,
                                          static_cast<const T*>(plan->d_t_dq), int(plan->ntgt), g.M[0], g.M[1], hwi2,
                                          static_cast<const T*>(plan->d_monoW), static_cast<const T*>(plan->d_monoWd),
                                          plan->d_pot_far, plan->d_gradu_far);

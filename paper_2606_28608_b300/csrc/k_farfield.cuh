@@ -259,7 +259,7 @@ k_spread_whole_w(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, cons
 // Sum of the per-CTA slabs: a block takes 32 cells (one per lane); its eight warps split the
 // slabs, and warp 0 adds the eight partials in order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fold_whole(const T* __restrict__ slab, int nslab, T* __restrict__ grid,
+__global__ void __launch_bounds__(256) k_fold_whole(const T* __restrict__ slab, int nslab, double* __restrict__ grid,
                                                     int ncell) {
     __shared__ T part[8][32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256) k_fold_whole(const T* __restrict__ slab, 
     if (wp == 0 && c < ncell) {
         T t = part[0][lane];
         for (int k = 1; k < 8; ++k) t += part[k][lane];
-        grid[c] = t;
+        grid[c] = double(t);
     }
 }
 
@@ -310,7 +310,7 @@ __global__ void k_fold(FoldArgs<T> a) {
                     for (int s = a.bin_sub_begin[bin]; s < a.bin_sub_begin[bin + 1]; ++s)
                         acc += a.slab[size_t(s) * a.Ptot + idx];
                 }
-        a.grid[cell] = acc;
+        a.grid[cell] = double(acc);
     }
 }
 
@@ -324,6 +324,13 @@ __global__ void k_scale(T* spec /* interleaved complex */, const double* weight,
         spec[2 * i] = T(double(spec[2 * i]) * wgt);
         spec[2 * i + 1] = T(double(spec[2 * i + 1]) * wgt);
     }
+}
+
+// grid precision change around the FP64 transforms (grid-stride)
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = B(in[i]);
 }
 
 // interpolation at targets: potential and gradient w.r.t. the grid coordinates
@@ -514,7 +521,7 @@ k_spread_halo(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, const T
 // grid-stride loop (one target per thread).
 template <typename T, int W, int NH, int NHD>
 __global__ void __launch_bounds__(256, 2)
-k_interp_halo(const T* __restrict__ grid, const int4* __restrict__ t_g0, const T* __restrict__ t_dq, int nt, int M0,
+k_interp_halo(const double* __restrict__ grid, const int4* __restrict__ t_g0, const T* __restrict__ t_dq, int nt, int M0,
               int M1, T half_w_inv2, const T* __restrict__ monoW, const T* __restrict__ monoWd,
               double* __restrict__ pot, double* __restrict__ gradu) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -522,7 +529,7 @@ k_interp_halo(const T* __restrict__ grid, const int4* __restrict__ t_g0, const T
     T* gs = reinterpret_cast<T*>(smem_raw);  // [Mp1][Mp0]
     for (int y = threadIdx.x / 32; y < Mp1; y += blockDim.x / 32) {
         const int yy = y < M1 ? y : y - M1;
-        for (int x = threadIdx.x & 31; x < Mp0; x += 32) gs[y * Mp0 + x] = grid[yy * M0 + (x < M0 ? x : x - M0)];
+        for (int x = threadIdx.x & 31; x < Mp0; x += 32) gs[y * Mp0 + x] = T(grid[yy * M0 + (x < M0 ? x : x - M0)]);
     }
     T cw[NH], cd[NHD];
 #pragma unroll

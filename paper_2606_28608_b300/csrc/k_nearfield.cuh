@@ -68,7 +68,6 @@ k_nearfield(NearArgs<T> a) {
     const double hinv_d = a.inv_rc * double(1LL << L.level);
     const T hinv = T(hinv_d);
     const T h2inv = T(hinv_d * hinv_d);
-    const double* cB_centre = a.box_center + size_t(L.box) * D;
     const int nt = L.tgt_count;
     // targets per group: the smallest power of two >= nt (so the groups tile the block
     // exactly); the G = 64 / C groups split the source tiles, so small leaves still keep
@@ -106,14 +105,15 @@ k_nearfield(NearArgs<T> a) {
             const int ne = min(kNearMaxList, L.list_count - s0);
             __syncthreads();
             for (int e = tid; e < ne; e += kNearThreads) {
-                int box = a.list[L.list_begin + s0 + e];
-                e_begin[e] = a.box_src_begin[box];
-                e_pref[e + 1] = a.box_src_count[box];
-                const double* cs = a.box_center + size_t(box) * D;
+                // source range and the source leaf centre's shift into this leaf's frame
+                // (hi / lo in T), as the host formed them
+                const int ei = L.list_begin + s0 + e;
+                const int2 bc = a.ent[ei];
+                e_begin[e] = bc.x;
+                e_pref[e + 1] = bc.y;
                 for (int k = 0; k < D; ++k) {
-                    const double sh = cs[k] - cB_centre[k];
-                    e_shift[k][e] = T(sh);
-                    if constexpr (kLo) e_shlo[k][e] = T(sh - double(T(sh)));
+                    e_shift[k][e] = a.ent_sh[size_t(ei) * 4 + k];
+                    if constexpr (kLo) e_shlo[k][e] = a.ent_shlo[size_t(ei) * 4 + k];
                 }
             }
             __syncthreads();

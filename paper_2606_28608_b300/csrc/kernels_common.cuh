@@ -96,7 +96,7 @@ template <typename T>
 struct FoldArgs {
     const T* slab;
     const int* bin_sub_begin;  // per bin: first subproblem (nbin + 1 entries)
-    T* grid;                   // M0*M1*M2
+    double* grid;              // M0*M1*M2 (FP64: the transforms run in FP64)
     int M0, M1, M2;
     int nb0, nb1, nb2;
     int B0, B1, B2;

@@ -72,6 +72,19 @@ def test_fp64_parity(case, eps):
     assert eg <= 10 * eps
 
 
+@pytest.mark.parametrize("case", ["cube", "oblique2d", "triclinic3d", "oblique2d_deep", "triclinic3d_deep"])
+def test_fp64_parity_1e12(case):
+    """The eps = 1e-12 tier (the tightest tolerance of the paper's experiments)."""
+    g = dict(CASES[case](), case=case)
+    pref, gref = oracle_ref(g)
+    pot, grad, info = run(g, 1e-12, precision="fp64")
+    ep, eg = rel(pot, pref), rel(grad, gref)
+    print(f"{case} eps=1e-12: E_pot={ep:.2e} E_grad={eg:.2e} p={info['n_proxy']} K={info['n_pw']} "
+          f"w={info['window_w']} depth={info['depth']}")
+    assert ep <= 1e-12
+    assert eg <= 1e-11
+
+
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("eps", [1e-3, 1e-6])
 def test_mixed_parity(case, eps):
