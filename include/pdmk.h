@@ -252,8 +252,10 @@ const char* pdmk_strerror(int code);
  * Debug / verification access to the FP64 kernel tables (host only, no GPU needed).
  * kind: 0 = residual kernel R_1(t) (scale-free, t = r/h in (0, 1]), 1 = dR_1/dt,
  *       2 = hat-w(x) (transform of the smoothing density), 3 = bandwidth c (x ignored),
- *       4 = self value W_1(0) (3D: psi(0)/(4 pi c0); 2D: W_1(0)), 5 = window F(s),
- *       6 = window transform at grid frequency x.
+ *       4 = self value W_1(0) (3D: psi(0)/(4 pi c0); 2D: W_1(0)),
+ *       5 = integral of the residual kernel (hat-R_h(0) = value * h^2; x ignored),
+ *       6 = the default spreading window's F(s) at s = x in [0, 1] (window w = ceil(2c/pi) + 2),
+ *       7 = that window's Fourier transform at grid frequency x (cycles per grid point).
  * Returns 0 and writes *value, or a negative error.
  */
 int pdmk_kernel_table_eval(int d, double eps, int kind, double x, double* value);

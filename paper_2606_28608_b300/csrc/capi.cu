@@ -12,6 +12,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "host_plan.h"
@@ -86,7 +87,8 @@ struct pdmk_plan_s {
     void* d_monoWd = nullptr;
     double* d_weight = nullptr;
     void* d_grid = nullptr;
-    void* d_grid64 = nullptr;  // FP64 grid of the transforms (the grid itself for FP64 plans)
+    void* d_grid64 = nullptr;  // grid of the transforms (the grid itself unless FP64 transforms of a mixed plan)
+    bool fft32 = false;        // FP32 transforms (2D mixed plans)
     void* d_spec = nullptr;
     double* d_qsums = nullptr;
     double* d_qsum_part = nullptr;  // [kSumBlocks][3] partial charge sums
@@ -262,6 +264,46 @@ static void size_bins(pdmk_plan plan) {
     plan->whole_ctas = (d == 2 && size_t(plan->ncell) * ts * 8 <= size_t(96) * 1024) ? 2 * 148 : 0;
 }
 
+// Largest far-field weight over the one of the lowest nonzero mode.  Eq. (3.15) puts the
+// band edge of axis i at its Nyquist index; where the band's ellipse in index space reaches
+// the corners of the index box (strongly skewed cells), the window deconvolution of several
+// axes multiplies, and rounding in the spread grid is amplified by this ratio.
+static double far_amplification(pdmk_plan plan) {
+    const int d = plan->d;
+    const Geometry& g = plan->g;
+    std::vector<double> ph[3];
+    for (int i = 0; i < d; ++i) {
+        ph[i].resize(g.M[i] / 2 + 1);
+        for (int m = 0; m <= g.M[i] / 2; ++m) ph[i][m] = plan->wt.ft(double(m) / g.M[i]);
+    }
+    double wmax = 0, kmin = 1e300, wlow = 0;
+    const int h0 = g.M[0] / 2, h1 = g.M[1] / 2, h2 = d == 3 ? g.M[2] / 2 : 0;
+    for (int m2 = -h2 + (d == 3 ? 1 : 0); m2 < std::max(h2, 1); ++m2)
+        for (int m1 = -h1 + 1; m1 < h1; ++m1)
+            for (int m0 = 0; m0 < h0; ++m0) {
+                if (m0 == 0 && m1 == 0 && m2 == 0) continue;
+                const int m[3] = {m0, m1, m2};
+                double k2 = 0;
+                for (int b = 0; b < d; ++b) {
+                    double s = 0;
+                    for (int a = 0; a < d; ++a) s += g.Rinv[a * d + b] * m[a];
+                    s *= 2.0 * kPi;
+                    k2 += s * s;
+                }
+                const double kk = std::sqrt(k2);
+                if (kk * g.rc > plan->c) continue;
+                double den = 1;
+                for (int i = 0; i < d; ++i) {
+                    const double f = ph[i][std::abs(m[i])];
+                    den *= f * f;
+                }
+                const double wv = plan->kt.what(kk * g.rc) / k2 / den;
+                wmax = std::max(wmax, wv);
+                if (kk < kmin) { kmin = kk; wlow = wv; }
+            }
+    return wlow > 0 ? wmax / wlow : 1.0;
+}
+
 // FP64 far-field weights for the half spectrum (Eq. (3.14)-(3.15a) with the window
 // deconvolution of both NUFFT halves folded in); zero at m = 0 and on Nyquist planes
 static std::vector<double> far_weights(pdmk_plan plan) {
@@ -348,6 +390,18 @@ extern "C" int pdmk_kernel_table_eval(int d, double eps, int kind, double x, dou
         case 3: *value = kt.psi.c; return PDMK_OK;
         case 4: *value = kt.self_coef; return PDMK_OK;
         case 5: *value = kt.rhat0; return PDMK_OK;
+        case 6:
+        case 7: {
+            const int w = std::max(2, std::min(int(std::ceil(2.0 * kt.psi.c / kPi - 1e-9)) + 2, kMaxW));
+            const WindowTables wt = make_window(w, kPi * w / 2.0, std::max(eps * 1e-5, 1e-15));
+            if (kind == 6) {
+                if (!(x >= 0 && x <= 1)) return PDMK_ERR_BAD_ARG;
+                *value = wt.F.eval(x);
+            } else {
+                *value = wt.ft(x);
+            }
+            return PDMK_OK;
+        }
         default: return PDMK_ERR_BAD_ARG;
     }
 }
@@ -439,6 +493,24 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     plan->w = std::max(2, std::min(plan->w, kMaxW));
     plan->beta = kPi * plan->w / 2.0;  // window prolate bandwidth c_w
     plan->wt = make_window(plan->w, plan->beta, mixed ? 1e-9 : std::max(eps * 1e-5, 1e-15));
+    // FP32 far field: oversample the grid (about 5 % per step) until the window
+    // deconvolution amplifies grid rounding by at most 5e7 relative to the lowest mode; the
+    // band edge then moves off the Nyquist index, where the window's transform is smallest.
+    // Only strongly skewed cells need it (a 2D cell at 20 degrees: 3e15 before; the 60-degree
+    // bench cell is at 2.5e7 with E_pot 2e-7 at eps 1e-6, and keeps its grid).
+    if (mixed)
+        for (int it = 0; it < 16 && far_amplification(plan) > 5e7; ++it)
+            for (int i = 0; i < d; ++i) {
+                // next even size >= 1.05 M with prime factors <= 7 (fast transform lengths)
+                int M = 2 * int(std::ceil(0.525 * plan->g.M[i]));
+                auto smooth = [](int v) {
+                    for (int p : {2, 3, 5, 7})
+                        while (v % p == 0) v /= p;
+                    return v == 1;
+                };
+                while (!smooth(M)) M += 2;
+                plan->g.M[i] = M;
+            }
     size_bins(plan);
     // near-field coefficients
     plan->cA = plan->kt.A.coef;
@@ -513,17 +585,19 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
         PCHECK(upload(plan, plan->d_weight, wt));
         PCHECK(dalloc(plan, plan->plan_allocs, &p, ts * size_t(plan->ncell)));
         plan->d_grid = p;
-        // the transforms and the k-space scaling run in FP64 for both precisions: rounding
-        // that enters before the scaling is amplified by the window deconvolution near the
-        // band edge, and an FP32 transform's error (~1e-7 log N of the grid norm) would
-        // reach ~1e-6 of a far-field-dominated potential
-        if (mixed) {
+        // the transforms and the k-space scaling run in FP64 except for 2D mixed plans:
+        // rounding that enters before the scaling is amplified by the window deconvolution
+        // near the band edge (a per-axis factor), and in 3D an FP32 transform's error
+        // (~1e-7 log N of the grid norm) reached ~1e-6 of a far-field-dominated potential;
+        // the 2D grids are small and two axes amplify less
+        plan->fft32 = mixed && d == 2;
+        if (mixed && !plan->fft32) {
             PCHECK(dalloc(plan, plan->plan_allocs, &p, sizeof(double) * size_t(plan->ncell)));
             plan->d_grid64 = p;
         } else {
             plan->d_grid64 = plan->d_grid;
         }
-        PCHECK(dalloc(plan, plan->plan_allocs, &p, 2 * sizeof(double) * size_t(plan->nhalf)));
+        PCHECK(dalloc(plan, plan->plan_allocs, &p, 2 * (plan->fft32 ? 4 : 8) * size_t(plan->nhalf)));
         plan->d_spec = p;
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsums, 4));
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsum_part, size_t(3 * kSumBlocks)));
@@ -531,7 +605,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     }
     {
         const Geometry& g = plan->g;
-        const cufftType tf = CUFFT_D2Z, ti = CUFFT_Z2D;
+        const cufftType tf = plan->fft32 ? CUFFT_R2C : CUFFT_D2Z, ti = plan->fft32 ? CUFFT_C2R : CUFFT_Z2D;
         cufftResult fr;
         if (d == 2) {
             fr = cufftPlan2d(&plan->fft_fwd, g.M[1], g.M[0], tf);
@@ -1100,8 +1174,12 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         ++plan->launches;
         CK(cudaGetLastError());
         const int blocks = int((plan->ncell + 31) / 32);
-        k_fold_whole<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<const T*>(slab), plan->whole_ctas,
-                                                            static_cast<double*>(plan->d_grid64), int(plan->ncell));
+        if (plan->fft32)
+            k_fold_whole<T, float><<<std::max(blocks, 1), 256, 0, s>>>(
+                static_cast<const T*>(slab), plan->whole_ctas, static_cast<float*>(plan->d_grid64), int(plan->ncell));
+        else
+            k_fold_whole<T, double><<<std::max(blocks, 1), 256, 0, s>>>(
+                static_cast<const T*>(slab), plan->whole_ctas, static_cast<double*>(plan->d_grid64), int(plan->ncell));
         ++plan->launches;
         CK(cudaGetLastError());
     } else if (D == 2 && plan->whole_ctas > 0) {
@@ -1132,8 +1210,12 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         ++plan->launches;
         CK(cudaGetLastError());
         const int blocks = int((plan->ncell + 31) / 32);
-        k_fold_whole<T><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<const T*>(slab), plan->whole_ctas,
-                                                            static_cast<double*>(plan->d_grid64), int(plan->ncell));
+        if (plan->fft32)
+            k_fold_whole<T, float><<<std::max(blocks, 1), 256, 0, s>>>(
+                static_cast<const T*>(slab), plan->whole_ctas, static_cast<float*>(plan->d_grid64), int(plan->ncell));
+        else
+            k_fold_whole<T, double><<<std::max(blocks, 1), 256, 0, s>>>(
+                static_cast<const T*>(slab), plan->whole_ctas, static_cast<double*>(plan->d_grid64), int(plan->ncell));
         ++plan->launches;
         CK(cudaGetLastError());
     } else {
@@ -1158,36 +1240,52 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         CK(cudaGetLastError());
     }
     {
-        FoldArgs<T> fa;
+        auto fold = [&](auto* gridp) {
+        using G = std::remove_pointer_t<decltype(gridp)>;
+        FoldArgs<T, G> fa;
         fa.slab = static_cast<const T*>(slab);
         fa.bin_sub_begin = plan->d_bin_sub_begin;
-        fa.grid = static_cast<double*>(plan->d_grid64);
+        fa.grid = gridp;
         fa.M0 = g.M[0]; fa.M1 = g.M[1]; fa.M2 = g.M[2];
         fa.nb0 = plan->nbin[0]; fa.nb1 = plan->nbin[1]; fa.nb2 = plan->nbin[2];
         fa.B0 = plan->B[0]; fa.B1 = plan->B[1]; fa.B2 = plan->B[2];
         fa.P0 = plan->P[0]; fa.P1 = plan->P[1]; fa.P2 = plan->P[2]; fa.Ptot = plan->Ptot;
         fa.fw = plan->w / 2;
         int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 8));
-        k_fold<T, D><<<std::max(blocks, 1), 256, 0, s>>>(fa);
+        k_fold<T, D, G><<<std::max(blocks, 1), 256, 0, s>>>(fa);
+        };
+        if (plan->fft32) fold(static_cast<float*>(plan->d_grid64));
+        else fold(static_cast<double*>(plan->d_grid64));
         ++plan->launches;
         CK(cudaGetLastError());
     }
     }
     if ((r = stage_mark(plan, "spread"))) return r;
     const int cblocks = int(std::max<int64_t>(1, std::min<int64_t>((plan->ncell + 255) / 256, 148 * 8)));
-    CKFFT(cufftExecD2Z(plan->fft_fwd, (cufftDoubleReal*)plan->d_grid64, (cufftDoubleComplex*)plan->d_spec));
+    if (plan->fft32)
+        CKFFT(cufftExecR2C(plan->fft_fwd, (cufftReal*)plan->d_grid64, (cufftComplex*)plan->d_spec));
+    else
+        CKFFT(cufftExecD2Z(plan->fft_fwd, (cufftDoubleReal*)plan->d_grid64, (cufftDoubleComplex*)plan->d_spec));
     if ((r = stage_mark(plan, "fft_fwd"))) return r;
     {
         int blocks = int(std::min<int64_t>((plan->nhalf + 255) / 256, 148 * 8));
-        k_scale<double><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<double*>(plan->d_spec), plan->d_weight,
-                                                            plan->nhalf);
+        if (plan->fft32)
+            k_scale<float><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<float*>(plan->d_spec), plan->d_weight,
+                                                               plan->nhalf);
+        else
+            k_scale<double><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<double*>(plan->d_spec), plan->d_weight,
+                                                                plan->nhalf);
         ++plan->launches;
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "scale"))) return r;
-    CKFFT(cufftExecZ2D(plan->fft_inv, (cufftDoubleComplex*)plan->d_spec, (cufftDoubleReal*)plan->d_grid64));
+    if (plan->fft32)
+        CKFFT(cufftExecC2R(plan->fft_inv, (cufftComplex*)plan->d_spec, (cufftReal*)plan->d_grid64));
+    else
+        CKFFT(cufftExecZ2D(plan->fft_inv, (cufftDoubleComplex*)plan->d_spec, (cufftDoubleReal*)plan->d_grid64));
     const bool interp_halo = plan->ntgt > 0 && D == 2 && plan->far_halo && sizeof(T) == 4;
-    if (sizeof(T) == 4 && !interp_halo) {  // the halo interpolation reads the FP64 grid itself
+    // the halo interpolation reads the transform grid in its own precision; the others read T
+    if (sizeof(T) == 4 && !plan->fft32 && !interp_halo) {
         k_convert<double, T><<<cblocks, 256, 0, s>>>(static_cast<const double*>(plan->d_grid64),
                                                      static_cast<T*>(plan->d_grid), plan->ncell);
         ++plan->launches;
@@ -1197,7 +1295,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
     if (interp_halo) {
         const int Mp0 = g.M[0] + plan->w - 1, Mp1 = g.M[1] + plan->w - 1;
         const size_t smem = sizeof(T) * size_t(Mp0) * Mp1;
-        auto interp = [&](auto kern) {
+        auto interp = [&](auto kern, auto* gridp) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
             int per_sm = 0, nsm = 0, dev = 0;
             cudaGetDevice(&dev);
@@ -1205,14 +1303,22 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
             const int grid = int(std::max<int64_t>(1, std::min<int64_t>((plan->ntgt + 255) / 256,
                                                                         int64_t(std::max(1, per_sm)) * nsm)));
-            kern<<<grid, 256, smem, s>>>(static_cast<const double*>(plan->d_grid64), plan->d_t_g0,
+            kern<<<grid, 256, smem, s>>>(gridp, plan->d_t_g0,
                                          static_cast<const T*>(plan->d_t_dq), int(plan->ntgt), g.M[0], g.M[1], hwi2,
                                          static_cast<const T*>(plan->d_monoW), static_cast<const T*>(plan->d_monoWd),
                                          plan->d_pot_far, plan->d_gradu_far);
         };
-        if (plan->w == 8) interp(k_interp_halo<T, 8, 12, 12>);
-        else if (plan->w == 13) interp(k_interp_halo<T, 13, 16, 16>);
-        else interp(k_interp_halo<T, 17, 20, 20>);
+        if (plan->fft32) {
+            const float* gp = static_cast<const float*>(plan->d_grid64);
+            if (plan->w == 8) interp(k_interp_halo<T, 8, 12, 12, float>, gp);
+            else if (plan->w == 13) interp(k_interp_halo<T, 13, 16, 16, float>, gp);
+            else interp(k_interp_halo<T, 17, 20, 20, float>, gp);
+        } else {
+            const double* gp = static_cast<const double*>(plan->d_grid64);
+            if (plan->w == 8) interp(k_interp_halo<T, 8, 12, 12, double>, gp);
+            else if (plan->w == 13) interp(k_interp_halo<T, 13, 16, 16, double>, gp);
+            else interp(k_interp_halo<T, 17, 20, 20, double>, gp);
+        }
         ++plan->launches;
         CK(cudaGetLastError());
     } else if (plan->ntgt > 0 && D == 3 && plan->far_warp3d && plan->ntgt < 50000) {

@@ -258,8 +258,8 @@ k_spread_whole_w(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, cons
 
 // Sum of the per-CTA slabs: a block takes 32 cells (one per lane); its eight warps split the
 // slabs, and warp 0 adds the eight partials in order.
-template <typename T>
-__global__ void __launch_bounds__(256) k_fold_whole(const T* __restrict__ slab, int nslab, double* __restrict__ grid,
+template <typename T, typename G>
+__global__ void __launch_bounds__(256) k_fold_whole(const T* __restrict__ slab, int nslab, G* __restrict__ grid,
                                                     int ncell) {
     __shared__ T part[8][32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -272,13 +272,13 @@ __global__ void __launch_bounds__(256) k_fold_whole(const T* __restrict__ slab, 
     if (wp == 0 && c < ncell) {
         T t = part[0][lane];
         for (int k = 1; k < 8; ++k) t += part[k][lane];
-        grid[c] = double(t);
+        grid[c] = G(t);
     }
 }
 
 // fold: grid cell g gathers every subproblem tile that covers it (periodic wrap)
-template <typename T, int D>
-__global__ void k_fold(FoldArgs<T> a) {
+template <typename T, int D, typename G>
+__global__ void k_fold(FoldArgs<T, G> a) {
     const int64_t ncell = int64_t(a.M0) * a.M1 * (D == 3 ? a.M2 : 1);
     for (int64_t cell = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; cell < ncell;
          cell += int64_t(gridDim.x) * blockDim.x) {
@@ -310,7 +310,7 @@ __global__ void k_fold(FoldArgs<T> a) {
                     for (int s = a.bin_sub_begin[bin]; s < a.bin_sub_begin[bin + 1]; ++s)
                         acc += a.slab[size_t(s) * a.Ptot + idx];
                 }
-        a.grid[cell] = double(acc);
+        a.grid[cell] = G(acc);
     }
 }
 
@@ -519,9 +519,9 @@ k_spread_halo(const int4* __restrict__ t_g0, const T* __restrict__ t_dq, const T
 // Interpolation of the potential and its grid-coordinate gradient: each block copies the
 // periodic grid into a halo grid in shared memory once, then its threads take targets in a
 // grid-stride loop (one target per thread).
-template <typename T, int W, int NH, int NHD>
+template <typename T, int W, int NH, int NHD, typename G>
 __global__ void __launch_bounds__(256, 2)
-k_interp_halo(const double* __restrict__ grid, const int4* __restrict__ t_g0, const T* __restrict__ t_dq, int nt, int M0,
+k_interp_halo(const G* __restrict__ grid, const int4* __restrict__ t_g0, const T* __restrict__ t_dq, int nt, int M0,
               int M1, T half_w_inv2, const T* __restrict__ monoW, const T* __restrict__ monoWd,
               double* __restrict__ pot, double* __restrict__ gradu) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

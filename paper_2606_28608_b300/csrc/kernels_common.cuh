@@ -92,11 +92,11 @@ struct SpreadArgs {
     int nW;
 };
 
-template <typename T>
+template <typename T, typename G>
 struct FoldArgs {
     const T* slab;
     const int* bin_sub_begin;  // per bin: first subproblem (nbin + 1 entries)
-    double* grid;              // M0*M1*M2 (FP64: the transforms run in FP64)
+    G* grid;                   // M0*M1*M2, in the precision of the transforms
     int M0, M1, M2;
     int nb0, nb1, nb2;
     int B0, B1, B2;

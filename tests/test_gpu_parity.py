@@ -56,6 +56,10 @@ CASES = {
     # deep adaptive trees (clustered sources, small leaves): exercise every plane-wave pass
     "oblique2d_deep": lambda: W.oblique2d_clusters(20000),
     "triclinic3d_deep": lambda: W.triclinic3d_clusters(12000, nclusters=8),
+    # strongly skewed cells: the far-field band reaches the corners of the index box, where
+    # the window deconvolution is largest (the FP32 far field oversamples its grid there)
+    "skew2d": lambda: W.random_neutral(np.array([[1.0, 0.8], [0.0, 0.3]]), 20000, seed=11),
+    "skew3d": lambda: W.random_neutral(W.lattice_from_lengths_angles(1.0, 1.1, 0.9, 50, 60, 55), 6000, seed=12),
 }
 OPTS = {"triclinic3d_deep": dict(n_s=60), "cube": dict(n_s=20)}
 
