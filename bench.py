@@ -158,7 +158,7 @@ def stage_flops(info, d, leaf_folded, out_folded):
 # DRAM bytes (read + write) per launch of each stage's main kernel on this workload, from
 # one `ncu --set full` capture of the kernel as it stands (profiles/ holds the summaries);
 # None where no capture of the current kernel exists
-STAGE_TRAFFIC = {"nearfield": 17895424, "pw_upward": 6190336, "pw_downward": 13728768}
+STAGE_TRAFFIC = {"nearfield": 17922560, "pw_upward": 6190336, "pw_downward": 13728768}
 
 STAGE_KERNELS = {
     "spread": "k_spread_halo + k_fold_whole", "interp": "k_interp_halo", "nearfield": "k_near_warp",
