@@ -399,6 +399,137 @@ __global__ void __launch_bounds__(P * P) k_down3d_p(const int* __restrict__ list
     }
 }
 
+// 3D re-expansions split four ways per parent, by the children's first two axis bits
+// q = b0 | b1 << 1 (child c = b0 | b1 << 1 | b2 << 2): a block of P^2 threads, thread
+// (i, j) <-> positions (M1, M2) or (m1, m2) of a P x P slice, as in k_merge3d_p / k_down3d_p.
+// A parent's work is spread over four blocks instead of one: 16 P^4 multiply-adds instead of
+// 14 P^4, for four times the blocks, which the small upper levels of a deep tree need (one
+// block per parent left most SMs idle and made every level cost one block's latency).
+//   down:  V[M1][M2] = sum_{M0} S_b0[M0][m0] a_P[M0][M1][M2]          (slice m0)
+//          W[m1][M2] = sum_{M1} S_b1[M1][m1] V[M1][M2]
+//          a_c[m0][m1][m2] += sum_{M2} S_b2[M2][m2] W[m1][M2]        (b2 = 0, 1: two children)
+//   merge: T[m1][M2] = sum_{b2, m2} S_b2[M2][m2] Q_c[m0][m1][m2]       (slice m0, two children)
+//          U[M1][M2] = sum_{m1} S_b1[M1][m1] T[m1][M2]
+//          part_q[M0][M1][M2] += S_b0[M0][m0] U[M1][M2]              (registers)
+//          the block that completes a parent adds its four parts in the order q = 0..3.
+template <typename T, int P>
+__global__ void __launch_bounds__(P * P) k_down3d_q(const int* __restrict__ list, T* __restrict__ Lc,
+                                                    const T* __restrict__ Sg) {
+    constexpr int PP = P * P, NP = PP * P;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Sm = reinterpret_cast<T*>(smraw);  // [2][P][P]  S[b][M][m]
+    T* aP = Sm + 2 * PP;                  // [P][PP]   parent coefficients
+    T* Vs = aP + NP;                      // [PP]
+    T* Ws = Vs + PP;                      // [PP]
+    const int tid = threadIdx.x, i = tid / P, j = tid % P;
+    const int q = blockIdx.x & 3, b0 = q & 1, b1 = q >> 1;
+    const int* e = list + size_t(blockIdx.x >> 2) * 9;
+    const int c0 = e[1 + q], c1 = e[1 + (q | 4)];
+    if (c0 < 0 && c1 < 0) return;  // whole block: no child of this quadrant has targets
+    for (int k = tid; k < 2 * PP; k += blockDim.x) Sm[k] = Sg[k];
+    const T* src = Lc + size_t(e[0]) * NP;
+    for (int k = tid; k < NP; k += blockDim.x) aP[k] = src[k];
+    const T* S0 = Sm + b0 * PP;  // S_b0[M][m]
+    const T* S1 = Sm + b1 * PP;  // S_b1[M][m]
+    for (int m0 = 0; m0 < P; ++m0) {
+        __syncthreads();
+        {
+            T v = T(0);
+#pragma unroll
+            for (int M0 = 0; M0 < P; ++M0) v = fma(S0[M0 * P + m0], aP[M0 * PP + tid], v);
+            Vs[tid] = v;
+        }
+        __syncthreads();
+        {
+            T w = T(0);
+#pragma unroll
+            for (int M1 = 0; M1 < P; ++M1) w = fma(S1[M1 * P + i], Vs[M1 * P + j], w);
+            Ws[tid] = w;
+        }
+        __syncthreads();
+        T o0 = T(0), o1 = T(0);
+#pragma unroll
+        for (int M2 = 0; M2 < P; ++M2) {
+            const T wv = Ws[i * P + M2];
+            o0 = fma(Sm[M2 * P + j], wv, o0);
+            o1 = fma(Sm[PP + M2 * P + j], wv, o1);
+        }
+        if (c0 >= 0) Lc[size_t(c0) * NP + size_t(m0) * PP + tid] += o0;
+        if (c1 >= 0) Lc[size_t(c1) * NP + size_t(m0) * PP + tid] += o1;
+    }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(P * P) k_merge3d_q(const int* __restrict__ list, T* __restrict__ Q,
+                                                     const T* __restrict__ Sg, T* __restrict__ part,
+                                                     int* __restrict__ done) {
+    constexpr int PP = P * P, NP = PP * P;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Sm = reinterpret_cast<T*>(smraw);  // [2][P][P]  S[b][M][m]
+    T* St = Sm + 2 * PP;                  // [2][P][P]  transposed: St[b][m][M]
+    T* in = St + 2 * PP;                  // [2][PP]    the two children's slice m0
+    T* Ts = in + 2 * PP;                  // [PP]
+    __shared__ int s_last;
+    const int tid = threadIdx.x, i = tid / P, j = tid % P;
+    const int q = blockIdx.x & 3, b0 = q & 1, b1 = q >> 1;
+    const int ent = blockIdx.x >> 2;
+    const int* e = list + size_t(ent) * 9;
+    const int c0 = e[1 + q], c1 = e[1 + (q | 4)];
+    for (int k = tid; k < 2 * PP; k += blockDim.x) {
+        const T v = Sg[k];
+        Sm[k] = v;
+        const int b = k / PP, M = (k / P) % P, m = k % P;
+        St[(b * P + m) * P + M] = v;
+    }
+    T acc[P];
+#pragma unroll
+    for (int M0 = 0; M0 < P; ++M0) acc[M0] = T(0);
+    if (c0 >= 0 || c1 >= 0) {  // block-uniform
+        for (int m0 = 0; m0 < P; ++m0) {
+            __syncthreads();
+            in[tid] = c0 >= 0 ? Q[size_t(c0) * NP + size_t(m0) * PP + tid] : T(0);
+            in[PP + tid] = c1 >= 0 ? Q[size_t(c1) * NP + size_t(m0) * PP + tid] : T(0);
+            __syncthreads();
+            {
+                T t = T(0);
+#pragma unroll
+                for (int m2 = 0; m2 < P; ++m2) {
+                    t = fma(St[m2 * P + j], in[i * P + m2], t);
+                    t = fma(St[PP + m2 * P + j], in[PP + i * P + m2], t);
+                }
+                Ts[tid] = t;
+            }
+            __syncthreads();
+            T u = T(0);
+#pragma unroll
+            for (int m1 = 0; m1 < P; ++m1) u = fma(Sm[(b1 * P + i) * P + m1], Ts[m1 * P + j], u);
+#pragma unroll
+            for (int M0 = 0; M0 < P; ++M0) acc[M0] = fma(Sm[(b0 * P + M0) * P + m0], u, acc[M0]);
+        }
+    }
+    T* mine = part + (size_t(ent) * 4 + q) * NP;
+#pragma unroll
+    for (int M0 = 0; M0 < P; ++M0) mine[size_t(M0) * PP + tid] = acc[M0];
+    // the block that completes the parent adds the four parts in a fixed order (the counter
+    // only decides which block does it) and resets the counter for the next evaluation
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(done + ent, 1) == 3;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const T* p0 = part + size_t(ent) * 4 * NP;
+    T* dst = Q + size_t(e[0]) * NP;
+    for (int k = tid; k < NP; k += blockDim.x) {
+        T v = __ldcg(p0 + k);
+        v += __ldcg(p0 + NP + k);
+        v += __ldcg(p0 + 2 * NP + k);
+        v += __ldcg(p0 + 3 * NP + k);
+        dst[k] = v;
+    }
+    if (tid == 0) done[ent] = 0;
+}
+
 // 2D: the whole re-expansion of all children in two shared-memory phases per parent.
 // merge: Q_P[M0][M1] = sum_c sum_{m0<=M0} S_{b0}[M0][m0] sum_{m1<=M1} S_{b1}[M1][m1] Q_c[m0][m1]
 template <typename T>
@@ -1778,6 +1909,8 @@ struct PwImpl {
     int* d_src_leaf = nullptr;  // leaf box of every sorted source
     int4* d_bcoord = nullptr;   // (i0, i1, level, 0) per box
     void* d_part = nullptr;     // partial moments [nditems][p p]
+    void* d_part3 = nullptr;    // 3D four-way merges: parts [parents of the largest level][4][p^3]
+    int* d_done3 = nullptr;     //   and per parent the number of parts written (reset by the last)
     int4* d_obox = nullptr;     // per out slot: (first partial slot, segments, box, 0)
     int* d_seg_done = nullptr;  // per out slot: segments finished in this evaluation
     // single-launch downward pass with folded leaf evaluation (2D compile-time orders)
@@ -2141,6 +2274,17 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     I->d_out = p;
     if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nloc, 1)) * I->dims.np * ts))) return r;
     I->d_L = p;
+    if (d == 3 && (I->dims.p == 16 || I->dims.p == 24)) {
+        int maxlev = 1;
+        for (int l = 0; l < t.nlevels; ++l) {
+            const int np_l = I->merge_start[l + 1] - I->merge_start[l];
+            if (np_l < 148) maxlev = std::max(maxlev, np_l);  // levels the four-way merge takes
+        }
+        if ((r = pw_alloc(pw, &p, size_t(maxlev) * 4 * I->dims.np * ts))) return r;
+        I->d_part3 = p;
+        if ((r = pw_alloc(pw, &I->d_done3, size_t(maxlev)))) return r;
+        if (cudaMemsetAsync(I->d_done3, 0, size_t(maxlev) * sizeof(int), stream) != cudaSuccess) return PDMK_ERR_CUDA;
+    }
     if ((r = pw_alloc(pw, &pw->d_pot, size_t(std::max<int64_t>(ntg, 1))))) return r;
     if ((r = pw_alloc(pw, &pw->d_grad, size_t(std::max<int64_t>(ntg, 1)) * d))) return r;
     return PDMK_OK;
@@ -2232,6 +2376,16 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                     case 32: launch_p(k_merge2d_p<T, 32>, 10 * 32 * 32, lst, Q); break;
                     default: k_merge2d<T><<<e - b, 256, sm_m2, s>>>(lst, Q, S, pd);
                 }
+            } else if ((pd.p == 16 || pd.p == 24) && e - b < 148) {
+                // a level with fewer parents than SMs: four blocks per parent (k_merge3d_q);
+                // larger levels keep one block per parent, which issues fewer shared loads
+                auto m3 = [&](auto kern, int P) {
+                    const size_t smb = ts * 7 * P * P;
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+                    kern<<<4 * (e - b), P * P, smb, s>>>(lst, Q, S, static_cast<T*>(I->d_part3), I->d_done3);
+                };
+                if (pd.p == 16) m3(k_merge3d_q<T, 16>, 16);
+                else m3(k_merge3d_q<T, 24>, 24);
             } else if (pd.p == 16 || pd.p == 24) {
                 auto m3 = [&](auto kern, int P) {
                     const size_t smb = ts * 18 * P * P;
@@ -2322,13 +2476,14 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                     default: k_down2d<T><<<e - b, 256, sm_d2, s>>>(lst, L, S, pd);
                 }
             } else if (pd.p == 16 || pd.p == 24) {
+                // four blocks per parent (k_down3d_q)
                 auto d3 = [&](auto kern, int P) {
-                    const size_t smb = ts * (10 * P * P + P * P * P);
+                    const size_t smb = ts * (4 * P * P + P * P * P);
                     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
-                    kern<<<e - b, P * P, smb, s>>>(lst, L, S);
+                    kern<<<4 * (e - b), P * P, smb, s>>>(lst, L, S);
                 };
-                if (pd.p == 16) d3(k_down3d_p<T, 16>, 16);
-                else d3(k_down3d_p<T, 24>, 24);
+                if (pd.p == 16) d3(k_down3d_q<T, 16>, 16);
+                else d3(k_down3d_q<T, 24>, 24);
             } else {
                 k_down<T, D><<<e - b, 128, sm_re, s>>>(lst, L, S, pd);
             }
@@ -2374,7 +2529,7 @@ void pw_free_sources(PwPlan* pw) {
         I->d_down = nullptr; I->d_eval = nullptr; I->d_Q = I->d_out = I->d_L = nullptr;
         I->nleafq = I->nout = I->nin = I->neval = 0;
         I->d_ditems = nullptr; I->d_src_leaf = nullptr; I->d_bcoord = nullptr; I->d_part = nullptr;
-        I->d_obox = nullptr; I->d_seg_done = nullptr;
+        I->d_obox = nullptr; I->d_seg_done = nullptr; I->d_part3 = nullptr; I->d_done3 = nullptr;
         I->nditems = 0;
         I->d_down_items = nullptr; I->d_down_flags = nullptr;
         I->ndown_items = 0;
