@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(128) k_down(const int* __restrict__ list, T* _
 // 14 P^4 multiply-adds per parent (a child-by-child separable re-expansion takes 24 P^4).
 // S is stored as Sm[b][M][m] and transposed as St[b][m][M] (lanes along the contiguous index).
 template <typename T, int P>
-__global__ void __launch_bounds__(P * P) k_merge3d_p(const int* __restrict__ list, T* __restrict__ Q,
+__global__ void __launch_bounds__(P * P, sizeof(T) == 4 ? 2 : 1) k_merge3d_p(const int* __restrict__ list, T* __restrict__ Q,
                                                      const T* __restrict__ Sg) {
     constexpr int PP = P * P, NP = PP * P;
     extern __shared__ __align__(16) unsigned char smraw[];
