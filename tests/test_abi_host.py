@@ -93,3 +93,26 @@ def test_gradient_table_is_derivative(d):
         h = 1e-6
         fd = (P.kernel_table(d, eps, 0, t + h) - P.kernel_table(d, eps, 0, t - h)) / (2 * h)
         assert abs(fd - P.kernel_table(d, eps, 1, t)) < 1e-6 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_window_transform_matches_quadrature(eps):
+    """The spreading window phi(z) = F((2z/w)^2), |z| < w/2, and its Fourier transform at a grid
+    frequency nu (cycles per grid point): the host table against Gauss-Legendre quadrature of
+    F.  Also F(0) = 1 (normalised, to the Chebyshev fit's tolerance eps 1e-5) and the
+    transform is even and decreasing on [0, 1/2]."""
+    c = P.kernel_table(2, eps, 3)
+    w = min(int(math.ceil(2 * c / math.pi - 1e-9)) + 2, 20)
+    assert abs(P.kernel_table(2, eps, 6, 0.0) - 1.0) < 10 * max(eps * 1e-5, 1e-15)  # the fit's tolerance
+    xg, wg = np.polynomial.legendre.leggauss(200)
+    z = 0.5 * w * xg  # nodes on (-w/2, w/2)
+    F = np.array([P.kernel_table(2, eps, 6, min(1.0, (2 * zz / w) ** 2)) for zz in z])
+    prev = None
+    for nu in (0.0, 0.1, 0.25, 0.4, 0.5):
+        ref = 0.5 * w * np.sum(wg * F * np.cos(2 * math.pi * nu * z))
+        got = P.kernel_table(2, eps, 7, nu)
+        assert abs(got - ref) <= 1e-9 * abs(P.kernel_table(2, eps, 7, 0.0))
+        assert abs(P.kernel_table(2, eps, 7, -nu) - got) <= 1e-14 * abs(got) + 1e-300
+        if prev is not None:
+            assert got < prev
+        prev = got

@@ -228,3 +228,29 @@ def test_e1_against_scipy():
     for x in (1e-8, 1e-3, 0.3, 0.999, 1.0, 1.001, 2.5, 10.0, 35.0):
         ref = float(sp.exp1(x))
         assert abs(E.e1(x) - ref) <= 1e-14 * abs(ref) + 1e-300
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_close_pair_displacement_is_exact(d):
+    """The lattice sum's pair term G(x - y_j - L n) (Eq. (1.1)) at a neutral pair 1e-7 apart,
+    placed where its coordinates are ~0.6 in an oblique / triclinic cell.  The periodic kernel minus the
+    free-space one is even, so its gradient vanishes at the origin: the field at one charge is
+    the free-space pair term to O(1e-7) of the smooth part, i.e. ~1e-20 relative.  A pair
+    displacement taken from positions rounded to an ulp of the coordinates (~1e-16) would be
+    off by ~1e-9 relative."""
+    # oblique / triclinic cells: there, positions rebuilt as L frac(L^-1 y) differ from the
+    # inputs by rounding (with L = I the round trip is exact)
+    L = (np.array([[1.0, 0.45], [0.0, 0.85]]) if d == 2
+         else lattice_from_lengths_angles(1.0, 1.3, 0.8, 75.0, 95.0, 110.0))
+    delta = np.zeros(d)
+    delta[0], delta[1] = 6e-8, 8e-8  # |delta| = 1e-7
+    y0 = np.full(d, 0.6)
+    y = np.stack([y0, y0 + delta])
+    q = np.array([1.0, -1.0])
+    pot, grad = E.ewald(L, y, q, x=y[:1], self_idx=np.array([0]))
+    dx = y[0] - y[1]  # the inputs' own difference (exact: Sterbenz)
+    r = np.linalg.norm(dx)
+    # grad Phi at y_0 from the charge q_1 at y_1: q_1 grad G(y_0 - y_1)
+    want = q[1] * (-dx / (4 * math.pi * r ** 3) if d == 3 else -dx / (2 * math.pi * r ** 2))
+    g = grad[0]
+    assert np.linalg.norm(g - want) <= 1e-12 * np.linalg.norm(want)
