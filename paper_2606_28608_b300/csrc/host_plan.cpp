@@ -389,9 +389,18 @@ int make_geometry(int d, const double* Lc, double kappa, double c, Geometry* g) 
         g->m[i] = mi;
         g->nroot[i] = mi + 2;
         g->lo[i] = xminus - g->rc;
-        // Eq. (3.15)
-        g->M[i] = 2 * int(std::ceil(c * g->anorm[i] / (2.0 * kPi * g->rc) - 1e-9));
-        if (g->M[i] < 2) g->M[i] = 2;
+        // Eq. (3.15), rounded up to an even length whose prime factors are at most 13 (the
+        // transform's fast paths; the added modes lie outside the active ball and carry no
+        // weight)
+        int M = 2 * int(std::ceil(c * g->anorm[i] / (2.0 * kPi * g->rc) - 1e-9));
+        if (M < 2) M = 2;
+        auto smooth13 = [](int v) {
+            for (int p : {2, 3, 5, 7, 11, 13})
+                while (v % p == 0) v /= p;
+            return v == 1;
+        };
+        while (!smooth13(M)) M += 2;
+        g->M[i] = M;
     }
     return PDMK_OK;
 }
