@@ -255,17 +255,16 @@ __global__ void __launch_bounds__(128) k_down(const int* __restrict__ list, T* _
     }
 }
 
-// 3D with a compile-time order P: one block of P^2 threads per parent, thread (i, j) <-> the
-// positions (M1, M2) or (m1, m2) of a P x P slice.  The sum over the eight children factors by
-// axis (child c = (b0, b1, b2), bit k of c is b_k):
-//   merge: T_{b0 b1}[m1][M2] = sum_{b2, m2} S_b2[M2][m2] Q_c[m0][m1][m2]       (slice m0)
-//          U_{b0}[M1][M2]    = sum_{b1, m1} S_b1[M1][m1] T_{b0 b1}[m1][M2]
-//          Q_P[M0][M1][M2]  += sum_{b0} S_b0[M0][m0] U_{b0}[M1][M2]           (registers)
-//   down:  V_{b0}[M1][M2]    = sum_{M0} S_b0[M0][m0] a_P[M0][M1][M2]          (slice m0)
-//          W_{b0 b1}[m1][M2] = sum_{M1} S_b1[M1][m1] V_{b0}[M1][M2]
-//          a_c[m0][m1][m2]  += sum_{M2} S_b2[M2][m2] W_{b0 b1}[m1][M2]
+// 3D merge with a compile-time order P: one block of P^2 threads per parent, thread (i, j) <->
+// the positions (M1, M2) or (m1, m2) of a P x P slice.  The sum over the eight children
+// factors by axis (child c = (b0, b1, b2), bit k of c is b_k):
+//   T_{b0 b1}[m1][M2] = sum_{b2, m2} S_b2[M2][m2] Q_c[m0][m1][m2]       (slice m0)
+//   U_{b0}[M1][M2]    = sum_{b1, m1} S_b1[M1][m1] T_{b0 b1}[m1][M2]
+//   Q_P[M0][M1][M2]  += sum_{b0} S_b0[M0][m0] U_{b0}[M1][M2]           (registers)
 // 14 P^4 multiply-adds per parent (a child-by-child separable re-expansion takes 24 P^4).
 // S is stored as Sm[b][M][m] and transposed as St[b][m][M] (lanes along the contiguous index).
+// Levels with fewer parents than SMs take the four-way k_merge3d_q below; the downward pass
+// always runs four ways (k_down3d_q).
 template <typename T, int P>
 __global__ void __launch_bounds__(P * P, sizeof(T) == 4 ? 2 : 1) k_merge3d_p(const int* __restrict__ list, T* __restrict__ Q,
                                                      const T* __restrict__ Sg) {
@@ -332,76 +331,9 @@ __global__ void __launch_bounds__(P * P, sizeof(T) == 4 ? 2 : 1) k_merge3d_p(con
     for (int M0 = 0; M0 < P; ++M0) dst[size_t(M0) * PP + tid] = acc[M0];
 }
 
-template <typename T, int P>
-__global__ void __launch_bounds__(P * P) k_down3d_p(const int* __restrict__ list, T* __restrict__ Lc,
-                                                    const T* __restrict__ Sg) {
-    constexpr int PP = P * P, NP = PP * P;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* Sm = reinterpret_cast<T*>(smraw);  // [2][P][P]
-    T* St = Sm + 2 * PP;                  // [2][P][P] transposed
-    T* aP = St + 2 * PP;                  // [P][PP] parent coefficients
-    T* Vs = aP + NP;                      // [2][PP]
-    T* Ws = Vs + 2 * PP;                  // [4][PP]
-    const int tid = threadIdx.x, i = tid / P, j = tid % P;
-    for (int k = tid; k < 2 * PP; k += blockDim.x) {
-        const T v = Sg[k];
-        Sm[k] = v;
-        const int b = k / PP, M = (k / P) % P, m = k % P;
-        St[(b * P + m) * P + M] = v;
-    }
-    const int* e = list + size_t(blockIdx.x) * 9;
-    const T* src = Lc + size_t(e[0]) * NP;
-    for (int k = tid; k < NP; k += blockDim.x) aP[k] = src[k];
-    int cs[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) cs[c] = e[1 + c];
-    for (int m0 = 0; m0 < P; ++m0) {
-        __syncthreads();
-        // V_{b0}[M1 = i][M2 = j]
-        {
-            T v0 = T(0), v1 = T(0);
-#pragma unroll
-            for (int M0 = 0; M0 < P; ++M0) {
-                const T a = aP[M0 * PP + tid];
-                v0 = fma(Sm[M0 * P + m0], a, v0);
-                v1 = fma(Sm[(P + M0) * P + m0], a, v1);
-            }
-            Vs[tid] = v0;
-            Vs[PP + tid] = v1;
-        }
-        __syncthreads();
-        // W_{b0b1}[m1 = i][M2 = j]
-        {
-            T w4[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-            for (int M1 = 0; M1 < P; ++M1) {
-                const T s0 = Sm[M1 * P + i], s1 = Sm[(P + M1) * P + i];
-                const T va = Vs[M1 * P + j], vb = Vs[PP + M1 * P + j];
-                w4[0] = fma(s0, va, w4[0]);  // (b0, b1) = (0, 0)
-                w4[1] = fma(s0, vb, w4[1]);  // (1, 0)
-                w4[2] = fma(s1, va, w4[2]);  // (0, 1)
-                w4[3] = fma(s1, vb, w4[3]);  // (1, 1)
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) Ws[k * PP + tid] = w4[k];
-        }
-        __syncthreads();
-        // a_c[m0][m1 = i][m2 = j] += sum_{M2} S_b2[M2][m2] W_{b0b1}[m1][M2]
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            if (cs[c] < 0) continue;
-            const int b2 = c >> 2, k = c & 3;  // k = b0 | b1 << 1
-            T o = T(0);
-#pragma unroll
-            for (int M2 = 0; M2 < P; ++M2) o = fma(Sm[(b2 * P + M2) * P + j], Ws[k * PP + i * P + M2], o);
-            Lc[size_t(cs[c]) * NP + size_t(m0) * PP + tid] += o;
-        }
-    }
-}
-
 // 3D re-expansions split four ways per parent, by the children's first two axis bits
 // q = b0 | b1 << 1 (child c = b0 | b1 << 1 | b2 << 2): a block of P^2 threads, thread
-// (i, j) <-> positions (M1, M2) or (m1, m2) of a P x P slice, as in k_merge3d_p / k_down3d_p.
+// (i, j) <-> positions (M1, M2) or (m1, m2) of a P x P slice, as in k_merge3d_p.
 // A parent's work is spread over four blocks instead of one: 16 P^4 multiply-adds instead of
 // 14 P^4, for four times the blocks, which the small upper levels of a deep tree need (one
 // block per parent left most SMs idle and made every level cost one block's latency).
