@@ -57,7 +57,9 @@ extern "C" {
 #define PDMK_DEVICE 1
 
 #define PDMK_FP64 0  /* every stage in FP64                                         */
-#define PDMK_MIXED 1 /* FP32 bulk with compensated sums; FP64 set-up, scaling, assembly */
+#define PDMK_MIXED 1 /* FP32 bulk with compensated sums; FP64 set-up, scaling, assembly.
+                        FP32 rounding bounds its relative error near 1e-7: for eps below
+                        1e-6 use PDMK_FP64 (mixed plans are accepted but do not reach it) */
 
 typedef struct pdmk_plan_s* pdmk_plan;
 
@@ -66,7 +68,9 @@ typedef struct {
     double kappa;   /* root box side r_c = L_min / kappa (Algorithm 1 step 1); <= 0: Table 1 */
     int n_s;        /* leaf capacity (Algorithm 1 step 2); <= 0: Table 1                     */
     int precision;  /* PDMK_FP64 or PDMK_MIXED                                               */
-    int window_w;   /* spreading window width in grid points; <= 0: ceil(2 c / pi)           */
+    int window_w;   /* spreading window width in grid points; <= 0: ceil(2 c / pi) + 2,
+                       at most 20.  In mixed precision a wider window than the default
+                       amplifies FP32 rounding through the deconvolution (FP64 plans only) */
     int n_proxy;    /* Chebyshev proxy points per dimension p; <= 0: from eps                */
     int n_pw;       /* plane-wave half-width K (nodes -K..K per dimension); <= 0: from eps   */
     int max_depth;  /* deepest tree level; < 0: 30; 0: every root box is a leaf              */
