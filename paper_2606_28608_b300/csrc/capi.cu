@@ -980,8 +980,9 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         for (int i = 0; i < 3; ++i) put(pt_dq, size_t(k) * 4 + i, sp_del[j * 3 + i]);
         sp_orig[k] = int(j);
     }
-    // subproblems: chunks of at most max_pts points of one bin
-    const int max_pts = 512;
+    // subproblems: chunks of at most max_pts points of one bin (one spreading block each; in
+    // 3D the clustered bins hold most points, so smaller chunks give the grid enough blocks)
+    const int max_pts = d == 3 ? 128 : 512;
     std::vector<int4> subs;
     std::vector<int> bin_sub_begin(size_t(plan->nbins_tot) + 1, 0);
     {
