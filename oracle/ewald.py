@@ -46,6 +46,10 @@ def _load():
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P,
                                      ctypes.c_int]
         lib.oracle_ewald.restype = ctypes.c_int
+        lib.oracle_ewald_bloch.argtypes = [ctypes.c_int, P, ctypes.c_int64, P, P, ctypes.c_int64, P, PI, P,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P, P,
+                                           ctypes.c_int]
+        lib.oracle_ewald_bloch.restype = ctypes.c_int
         lib.oracle_e1.argtypes = [ctypes.c_double]
         lib.oracle_e1.restype = ctypes.c_double
         _lib = lib
@@ -113,6 +117,47 @@ def ewald(L, y, q, x=None, self_idx=None, *, tol: float = 1e-15, alpha: float | 
     if rc != 0:
         raise RuntimeError(f"oracle_ewald failed ({rc})")
     return pot, g
+
+
+def ewald_bloch(L, y, q, beta, x=None, self_idx=None, *, tol: float = 1e-15, alpha: float | None = None,
+                nthreads: int | None = None):
+    """Quasi-periodic (Bloch) potential and gradient at targets ``x``:
+    Phi(x) = sum_n sum_j' q_j e^{i beta.L n} G(x - y_j - L n), so that
+    Phi(x + L n) = e^{i beta.L n} Phi(x) (paper Sec. 3.7).  No neutrality is needed; beta
+    must not be a reciprocal-lattice vector.  Direct loops: for small N.
+    Returns (pot (m,) complex, grad (m, d) complex)."""
+    L = np.ascontiguousarray(np.asarray(L, dtype=np.float64))
+    d = L.shape[0]
+    y = np.ascontiguousarray(np.asarray(y, dtype=np.float64).reshape(-1, d))
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1))
+    beta = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(d))
+    n = y.shape[0]
+    if x is None:
+        x = y
+        sidx = np.arange(n, dtype=np.int64)
+    else:
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, d))
+        sidx = (np.full(x.shape[0], -1, dtype=np.int64) if self_idx is None
+                else np.ascontiguousarray(np.asarray(self_idx, dtype=np.int64)))
+    m = x.shape[0]
+    V = abs(np.linalg.det(L))
+    if alpha is None:
+        alpha = default_alpha(d, V, n, m)
+    s = math.sqrt(-math.log(tol))
+    rcut = s / alpha
+    kcut = 2.0 * alpha * s
+    Lc = np.ascontiguousarray(L.T)
+    pr, pi = np.zeros(m), np.zeros(m)
+    gr, gi = np.zeros((m, d)), np.zeros((m, d))
+    rc = _load().oracle_ewald_bloch(
+        d, _ptr(Lc), n, _ptr(y), _ptr(q), m, _ptr(x),
+        sidx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(beta), float(alpha), rcut, kcut,
+        _ptr(pr), _ptr(pi), _ptr(gr), _ptr(gi), int(nthreads or 0))
+    if rc == -2:
+        raise ValueError("beta is a reciprocal-lattice vector (the periodic case)")
+    if rc != 0:
+        raise RuntimeError(f"oracle_ewald_bloch failed ({rc})")
+    return pr + 1j * pi, gr + 1j * gi
 
 
 def nthreads_default() -> int:

@@ -29,6 +29,10 @@
  * and the gradient is the analytic derivative of every term.  All sums accumulate in
  * long double.  Cost is O(M * neighbours + (N + M) * modes); it is meant to be slow
  * and obviously correct, not fast.
+ *
+ * oracle_ewald_bloch (end of file) is the quasi-periodic counterpart (paper Sec. 3.7):
+ * image charges carry the Bloch phase e^{i beta.L n}, the reciprocal sum runs over the
+ * shifted modes k_m + beta with every mode kept, and no neutrality is needed.
  */
 #include <math.h>
 #include <stdint.h>
@@ -363,4 +367,167 @@ int oracle_ewald(int d, const double* L, int64_t n, const double* y, const doubl
     free(v); free(wj); free(bstart); free(border); free(modes); free(kvec); free(gk);
     free(rho_re); free(rho_im);
     return err;
+}
+
+/*
+ * oracle_ewald_bloch: quasi-periodic (Bloch) potential and gradient at m targets,
+ *
+ *   Phi(x) = sum_{n in Z^d} sum_j' q_j e^{i beta.L n} G(x - y_j - L n)
+ *
+ * (paper Sec. 3.7, the periodised kernel with the Bloch phase), which satisfies
+ * Phi(x + L n) = e^{i beta.L n} Phi(x).  Same Ewald split as oracle_ewald, with
+ *
+ *   real space:  sum_{n, r < rcut} q_j e^{i beta.L n} S(|x - y_j - L n|)
+ *   reciprocal:  (1/V) sum_m g(|k_m + beta|) e^{i (k_m + beta).x} sum_j q_j e^{-i (k_m + beta).y_j}
+ *                over every mode m (no half space, no mode dropped), |k_m + beta| < kcut
+ *   self:        - q_self S0
+ *
+ * by Poisson summation of sum_n f(z - L n) e^{i beta.L n}.  No neutrality is needed; beta
+ * must not be a reciprocal-lattice vector (some k_m + beta = 0): then it returns -2.
+ * Written as direct loops over sources, shifts and modes: meant for small N.
+ * The potential and gradient are complex: pot_re/pot_im (m), grad_re/grad_im (m*d) or NULL.
+ */
+int oracle_ewald_bloch(int d, const double* L, int64_t n, const double* y, const double* q, int64_t m,
+                       const double* x, const int64_t* self_idx, const double* beta, double alpha,
+                       double rcut, double kcut, double* pot_re, double* pot_im, double* grad_re,
+                       double* grad_im, int nthreads) {
+    if ((d != 2 && d != 3) || n < 0 || m < 0 || alpha <= 0 || rcut <= 0 || kcut <= 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    double Li[9];
+    double det = orc_inv(d, L, Li);
+    double V = fabs(det);
+    if (!(V > 0)) return -1;
+    /* shifts: |n_a - nearest| <= R_a covers r < rcut (plane spacing 1/|row a of L^{-1}|) */
+    int R[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+        double rn = 0;
+        for (int b = 0; b < d; ++b) rn += Li[a + b * d] * Li[a + b * d];
+        R[a] = (int)ceil(rcut * sqrt(rn)) + 1;
+    }
+    /* modes: |m_a| <= (kcut + |beta|) |a_a| / (2 pi) */
+    double bn = 0;
+    for (int b = 0; b < d; ++b) bn += beta[b] * beta[b];
+    bn = sqrt(bn);
+    int mmax[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+        double an = 0;
+        for (int b = 0; b < d; ++b) an += L[b + a * d] * L[b + a * d];
+        mmax[a] = (int)ceil((kcut + bn) * sqrt(an) / (2.0 * ORC_PI));
+    }
+    int64_t cap = 1;
+    for (int a = 0; a < d; ++a) cap *= (2 * mmax[a] + 1);
+    double* kv = (double*)malloc(sizeof(double) * (size_t)cap * 3);
+    double* gk = (double*)malloc(sizeof(double) * (size_t)cap);
+    long double* sre = (long double*)calloc((size_t)cap, sizeof(long double));
+    long double* sim = (long double*)calloc((size_t)cap, sizeof(long double));
+    if (!kv || !gk || !sre || !sim) { free(kv); free(gk); free(sre); free(sim); return -1; }
+    int64_t nk = 0;
+    int bad = 0;
+    int m2lo = (d == 3) ? -mmax[2] : 0, m2hi = (d == 3) ? mmax[2] : 0;
+    for (int m0 = -mmax[0]; m0 <= mmax[0]; ++m0)
+        for (int m1 = -mmax[1]; m1 <= mmax[1]; ++m1)
+            for (int m2 = m2lo; m2 <= m2hi; ++m2) {
+                int mm[3] = {m0, m1, m2};
+                double k[3] = {0, 0, 0}, k2 = 0;
+                for (int b = 0; b < d; ++b) {
+                    double s = 0;
+                    for (int a = 0; a < d; ++a) s += Li[a + b * d] * mm[a];
+                    k[b] = 2.0 * ORC_PI * s + beta[b];
+                    k2 += k[b] * k[b];
+                }
+                if (k2 > kcut * kcut) continue;
+                if (!(k2 > 1e-24 * kcut * kcut)) { bad = 1; continue; }
+                for (int b = 0; b < 3; ++b) kv[nk * 3 + b] = b < d ? k[b] : 0.0;
+                gk[nk] = exp(-k2 / (4.0 * alpha * alpha)) / k2;
+                ++nk;
+            }
+    if (bad) { free(kv); free(gk); free(sre); free(sim); return -2; }
+    /* structure factors S(k) = sum_j q_j e^{-i k.y_j}, k = k_m + beta */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t ik = 0; ik < nk; ++ik) {
+        long double sr = 0, si = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            double ph = 0;
+            for (int b = 0; b < d; ++b) ph += kv[ik * 3 + b] * y[j * d + b];
+            sr += (long double)q[j] * cos(ph);
+            si -= (long double)q[j] * sin(ph);
+        }
+        sre[ik] = sr;
+        sim[ik] = si;
+    }
+    const double rc2 = rcut * rcut;
+    const double S0 = (d == 3) ? alpha / (2.0 * ORC_PI * sqrt(ORC_PI))
+                               : (ORC_EULER_GAMMA + 2.0 * log(alpha)) / (4.0 * ORC_PI);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < m; ++i) {
+        const double* xi = x + i * d;
+        const int64_t self = self_idx ? self_idx[i] : -1;
+        long double pr = 0, pim = 0, gr[3] = {0, 0, 0}, gi[3] = {0, 0, 0};
+        /* real space */
+        for (int64_t j = 0; j < n; ++j) {
+            double d0[3] = {0, 0, 0}, f[3] = {0, 0, 0};
+            for (int b = 0; b < d; ++b) d0[b] = xi[b] - y[j * d + b];
+            int nc[3] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) {
+                for (int b = 0; b < d; ++b) f[a] += Li[a + b * d] * d0[b];
+                nc[a] = (int)floor(f[a] + 0.5);
+            }
+            int lo2 = (d == 3) ? -R[2] : 0, hi2 = (d == 3) ? R[2] : 0;
+            for (int o0 = -R[0]; o0 <= R[0]; ++o0)
+                for (int o1 = -R[1]; o1 <= R[1]; ++o1)
+                    for (int o2 = lo2; o2 <= hi2; ++o2) {
+                        int nn[3] = {nc[0] + o0, nc[1] + o1, d == 3 ? nc[2] + o2 : 0};
+                        double dx[3] = {0, 0, 0}, r2 = 0, phase = 0;
+                        for (int b = 0; b < d; ++b) {
+                            double ln = 0;
+                            for (int a = 0; a < d; ++a) ln += L[b + a * d] * nn[a];
+                            dx[b] = d0[b] - ln;
+                            r2 += dx[b] * dx[b];
+                            phase += beta[b] * ln;
+                        }
+                        if (r2 > rc2) continue;
+                        int zero = (nn[0] == 0 && nn[1] == 0 && nn[2] == 0);
+                        if (zero && j == self) continue;
+                        if (r2 == 0.0) continue;
+                        double r = sqrt(r2), s, ds;
+                        orc_short(d, alpha, r, &s, &ds);
+                        double c = cos(phase), sn = sin(phase);
+                        pr += (long double)q[j] * s * c;
+                        pim += (long double)q[j] * s * sn;
+                        for (int b = 0; b < d; ++b) {
+                            gr[b] += (long double)q[j] * ds * dx[b] / r * c;
+                            gi[b] += (long double)q[j] * ds * dx[b] / r * sn;
+                        }
+                    }
+        }
+        /* reciprocal space: g(k) e^{i k.x} S(k) */
+        for (int64_t ik = 0; ik < nk; ++ik) {
+            double ph = 0;
+            for (int b = 0; b < d; ++b) ph += kv[ik * 3 + b] * xi[b];
+            double c = cos(ph), sn = sin(ph);
+            long double re = sre[ik] * c - sim[ik] * sn; /* Re[S e^{ikx}] */
+            long double im = sre[ik] * sn + sim[ik] * c; /* Im[S e^{ikx}] */
+            pr += gk[ik] * re / V;
+            pim += gk[ik] * im / V;
+            /* grad: i k g S e^{ikx} -> Re = -k g Im, Im = k g Re */
+            for (int b = 0; b < d; ++b) {
+                gr[b] += -kv[ik * 3 + b] * gk[ik] * im / V;
+                gi[b] += kv[ik * 3 + b] * gk[ik] * re / V;
+            }
+        }
+        if (self >= 0) pr -= (long double)q[self] * S0;
+        pot_re[i] = (double)pr;
+        pot_im[i] = (double)pim;
+        if (grad_re && grad_im)
+            for (int b = 0; b < d; ++b) {
+                grad_re[i * d + b] = (double)gr[b];
+                grad_im[i * d + b] = (double)gi[b];
+            }
+    }
+    free(kv); free(gk); free(sre); free(sim);
+    return 0;
 }

@@ -254,3 +254,82 @@ def test_close_pair_displacement_is_exact(d):
     want = q[1] * (-dx / (4 * math.pi * r ** 3) if d == 3 else -dx / (2 * math.pi * r ** 2))
     g = grad[0]
     assert np.linalg.norm(g - want) <= 1e-12 * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------- quasi-periodic (Bloch) oracle
+def _bloch_case(d, n=24, seed=7):
+    rng = np.random.default_rng(seed)
+    L = (np.array([[1.0, 0.35], [0.0, 0.9]]) if d == 2
+         else lattice_from_lengths_angles(1.0, 1.2, 0.9, 80.0, 100.0, 110.0))
+    y = rng.random((n, d)) @ L.T
+    q = rng.uniform(-1.0, 1.0, n)  # not neutral: the Bloch sum needs no neutrality
+    kr = 2 * math.pi * np.linalg.inv(L).T  # columns: reciprocal vectors
+    beta = kr @ rng.uniform(0.1, 0.4, d)
+    return L, y, q, beta
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_bloch_alpha_independence(d):
+    """Real- and reciprocal-space parts of the quasi-periodic Ewald sum (Sec. 3.7) are
+    consistent: the result does not depend on the splitting parameter."""
+    L, y, q, beta = _bloch_case(d)
+    a0 = E.default_alpha(d, abs(np.linalg.det(L)), len(q), len(q))
+    p1, g1 = E.ewald_bloch(L, y, q, beta, alpha=0.7 * a0)
+    p2, g2 = E.ewald_bloch(L, y, q, beta, alpha=1.5 * a0)
+    assert np.abs(p1 - p2).max() <= 1e-12 * np.abs(p1).max()
+    assert np.abs(g1 - g2).max() <= 1e-11 * np.abs(g1).max()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_bloch_property_and_reciprocity(d):
+    """Phi(x + L n) = e^{i beta.L n} Phi(x) (Eq. of Sec. 3.7), and the kernel is Hermitian:
+    the potential at x of a unit charge at y is the conjugate of that at y of one at x."""
+    L, y, q, beta = _bloch_case(d)
+    rng = np.random.default_rng(3)
+    x = rng.random((5, d)) @ L.T
+    p0, g0 = E.ewald_bloch(L, y, q, beta, x=x)
+    for a in range(d):
+        shift = L[:, a]
+        p1, g1 = E.ewald_bloch(L, y, q, beta, x=x + shift)
+        ph = np.exp(1j * beta @ shift)
+        assert np.abs(p1 - ph * p0).max() <= 1e-12 * np.abs(p0).max()
+        assert np.abs(g1 - ph * g0).max() <= 1e-11 * np.abs(g0).max()
+    xa, xb = x[0], x[1]
+    pab, _ = E.ewald_bloch(L, xb[None], [1.0], beta, x=xa[None])
+    pba, _ = E.ewald_bloch(L, xa[None], [1.0], beta, x=xb[None])
+    assert abs(pab[0] - np.conj(pba[0])) <= 1e-12 * abs(pab[0])
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_bloch_half_reciprocal_vector_is_doubled_cell(d):
+    """At beta = k_1 / 2 the Bloch phase is (-1)^{n_1}: the quasi-periodic sum is the periodic
+    sum on the doubled cell (2 a_1, a_2, ...) holding q_j at y_j and -q_j at y_j + a_1 (that
+    system is neutral and its even modes, k = 0 included, vanish).  The periodic oracle is
+    pinned independently (Madelung constants, closed forms)."""
+    L, y, q, _ = _bloch_case(d, n=16, seed=11)
+    beta = math.pi * np.linalg.inv(L).T[:, 0]  # k_1 / 2
+    pb, gb = E.ewald_bloch(L, y, q, beta)
+    L2 = L.copy()
+    L2[:, 0] *= 2.0
+    y2 = np.concatenate([y, y + L[:, 0]])
+    q2 = np.concatenate([q, -q])
+    idx = np.arange(len(q))
+    pp, gp = E.ewald(L2, y2, q2, x=y, self_idx=idx)
+    assert np.abs(pb.imag).max() <= 1e-12 * np.abs(pp).max()
+    assert np.abs(pb.real - pp).max() <= 1e-12 * np.abs(pp).max()
+    assert np.abs(gb.real - gp).max() <= 1e-11 * np.abs(gp).max()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_bloch_gradient_finite_difference(d):
+    L, y, q, beta = _bloch_case(d)
+    x = (np.random.default_rng(5).random((3, d)) @ L.T)
+    _, g = E.ewald_bloch(L, y, q, beta, x=x)
+    h = 1e-5
+    for b in range(d):
+        e = np.zeros(d)
+        e[b] = h
+        pp, _ = E.ewald_bloch(L, y, q, beta, x=x + e)
+        pm, _ = E.ewald_bloch(L, y, q, beta, x=x - e)
+        fd = (pp - pm) / (2 * h)
+        assert np.abs(fd - g[:, b]).max() <= 1e-6 * np.abs(g).max()
