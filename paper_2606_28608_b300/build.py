@@ -24,10 +24,10 @@ def _newest_input():
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
-    cmd = ["nvcc", "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O3",
+    cmd = ["nvcc", "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O3,-fopenmp",
            "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-shared", "-o", LIB]
     cmd += [os.path.join(CSRC, s) for s in SOURCES]
-    cmd += ["-lcufft"]
+    cmd += ["-lcufft", "-lgomp"]  # OpenMP: the host planner's per-point and per-box loops
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)

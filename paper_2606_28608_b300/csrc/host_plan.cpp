@@ -1,5 +1,8 @@
 // host_plan.cpp -- FP64 host planning: prolates, kernel tables, geometry, images, tree.
 #include "host_plan.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include <algorithm>
 #include <cmath>
@@ -466,7 +469,13 @@ struct Builder {
     int d;
     const Geometry* g;
     std::vector<double> pos;  // d per image
+    std::vector<double> tsc;  // d per working position: (pos - lo) / r_c of image idx[j];
+                              // (pos - lo) / h_L = 2^L tsc exactly
+    std::vector<double> tsct; // split scratch
     std::vector<int64_t> idx; // working permutation of images
+    std::vector<int> lab;     // split scratch
+    std::vector<int> split_log;  // boxes split since the log was last cleared
+    std::vector<int64_t> tmp;
     std::vector<TmpBox> boxes;
     std::unordered_map<BoxKey, int, BoxKeyHash> map;
     int max_level = 0;
@@ -483,13 +492,15 @@ struct Builder {
     void split(int bi) {
         TmpBox B = boxes[bi];
         int L = B.level + 1;
-        double h = g->rc / double(1LL << L);
+        const double s2 = double(1LL << L);
         int nc = nchild();
-        std::vector<int64_t> cnt(nc + 1, 0);
-        auto child_of = [&](int64_t img) {
+        int64_t cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        auto child_of = [&](int64_t j) {  // working position j
             int ch = 0;
             for (int i = 0; i < d; ++i) {
-                double x = (pos[img * d + i] - g->lo[i]) / h;
+                // (pos - lo) / (r_c 2^-L) = 2^L (pos - lo) / r_c, rounding included: scaling
+                // by a power of two commutes with rounding
+                double x = tsc[j * d + i] * s2;
                 int64_t ci = int64_t(std::floor(x));
                 int64_t base = B.c[i] * 2;
                 int bit = int(ci - base);
@@ -499,18 +510,27 @@ struct Builder {
             }
             return ch;
         };
-        std::vector<int> lab(B.e - B.b);
+        const int64_t m = B.e - B.b;
+        lab.resize(size_t(m));
+        tmp.resize(size_t(m));
+        tsct.resize(size_t(m) * d);
         for (int64_t j = B.b; j < B.e; ++j) {
-            lab[j - B.b] = child_of(idx[j]);
+            lab[j - B.b] = child_of(j);
             cnt[lab[j - B.b] + 1]++;
         }
         for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
-        std::vector<int64_t> tmp(B.e - B.b);
-        std::vector<int64_t> cur(cnt.begin(), cnt.end() - 1);
-        for (int64_t j = B.b; j < B.e; ++j) tmp[cur[lab[j - B.b]]++] = idx[j];
-        std::copy(tmp.begin(), tmp.end(), idx.begin() + B.b);
+        int64_t cur[8];
+        for (int k = 0; k < nc; ++k) cur[k] = cnt[k];
+        for (int64_t j = B.b; j < B.e; ++j) {
+            const int64_t o = cur[lab[j - B.b]]++;
+            tmp[o] = idx[j];
+            for (int i = 0; i < d; ++i) tsct[size_t(o) * d + i] = tsc[size_t(j) * d + i];
+        }
+        std::copy(tmp.begin(), tmp.begin() + m, idx.begin() + B.b);
+        std::copy(tsct.begin(), tsct.begin() + m * d, tsc.begin() + B.b * d);
         int first = int(boxes.size());
         boxes[bi].child0 = first;
+        split_log.push_back(bi);
         for (int k = 0; k < nc; ++k) {
             TmpBox C;
             C.level = L;
@@ -590,45 +610,85 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
         nvec[lev] = 0;
     };
     rec(d - 1);
+    // per shift (in order), the points whose shifted copy lies in the box, in point order:
+    // each thread counts and then writes one contiguous chunk of points
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    const int64_t chunk = (n + nthr - 1) / std::max(nthr, 1);
+    std::vector<int64_t> ccount(size_t(nthr) + 1);
     for (const auto& sh : shifts) {
         double tr[3] = {0, 0, 0};
         for (int a = 0; a < d; ++a)
             for (int k = a; k < d; ++k) tr[a] += g.R[a * d + k] * sh[k];
         bool zero = true;
         for (int k = 0; k < d; ++k) zero &= (sh[k] == 0);
-        for (int64_t j = 0; j < n; ++j) {
+        auto inside = [&](int64_t j) {
             bool in = true;
-            double p[3];
             for (int a = 0; a < d; ++a) {
-                p[a] = x[j * d + a] + tr[a];
-                in &= (p[a] >= g.lo[a] && p[a] < hi[a]);
+                const double p = x[j * d + a] + tr[a];
+                in &= (p >= g.lo[a] && p < hi[a]);
             }
-            if (zero && !in) return PDMK_ERR_INTERNAL;  // the cell lies inside the inner block
-            if (!in) continue;
-            img_orig.push_back(zero ? j : -(j + 1));
-            for (int a = 0; a < d; ++a) bld.pos.push_back(p[a]);
+            return in;
+        };
+        bool missing = false;
+#pragma omp parallel for schedule(static, 1) reduction(|| : missing)
+        for (int c = 0; c < nthr; ++c) {
+            int64_t k = 0;
+            for (int64_t j = c * chunk; j < std::min(n, (c + 1) * chunk); ++j) {
+                const bool in = inside(j);
+                if (zero && !in) missing = true;
+                k += in;
+            }
+            ccount[c + 1] = k;
+        }
+        if (missing) return PDMK_ERR_INTERNAL;  // the cell lies inside the inner block
+        ccount[0] = int64_t(img_orig.size());
+        for (int c = 0; c < nthr; ++c) ccount[c + 1] += ccount[c];
+        img_orig.resize(size_t(ccount[nthr]));
+        bld.pos.resize(size_t(ccount[nthr]) * d);
+#pragma omp parallel for schedule(static, 1)
+        for (int c = 0; c < nthr; ++c) {
+            int64_t o = ccount[c];
+            for (int64_t j = c * chunk; j < std::min(n, (c + 1) * chunk); ++j) {
+                if (!inside(j)) continue;
+                img_orig[o] = zero ? j : -(j + 1);
+                for (int a = 0; a < d; ++a) bld.pos[size_t(o) * d + a] = x[j * d + a] + tr[a];
+                ++o;
+            }
         }
     }
     const int64_t nimg = int64_t(img_orig.size());
+    bld.tsc.resize(size_t(nimg) * d);
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < nimg; ++j)
+        for (int a = 0; a < d; ++a) bld.tsc[size_t(j) * d + a] = (bld.pos[size_t(j) * d + a] - g.lo[a]) / g.rc;
+    bld.map.reserve(size_t(std::max<int64_t>(1024, 4 * nimg / std::max(n_s, 1))));
     // ---- root boxes: counting sort by root cell ----
     int64_t nroot_tot = 1;
     for (int a = 0; a < d; ++a) nroot_tot *= g.nroot[a];
     std::vector<int64_t> rcell(nimg), rcnt(nroot_tot + 1, 0);
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < nimg; ++j) {
         int64_t cell = 0;
         for (int a = d - 1; a >= 0; --a) {
-            int64_t ci = int64_t(std::floor((bld.pos[j * d + a] - g.lo[a]) / g.rc));
+            int64_t ci = int64_t(std::floor(bld.tsc[j * d + a]));
             ci = std::min<int64_t>(std::max<int64_t>(ci, 0), g.nroot[a] - 1);
             cell = cell * g.nroot[a] + ci;
         }
         rcell[j] = cell;
-        rcnt[cell + 1]++;
     }
+    for (int64_t j = 0; j < nimg; ++j) rcnt[rcell[j] + 1]++;
     for (int64_t k = 0; k < nroot_tot; ++k) rcnt[k + 1] += rcnt[k];
     bld.idx.resize(nimg);
     {
         std::vector<int64_t> cur(rcnt.begin(), rcnt.end() - 1);
         for (int64_t j = 0; j < nimg; ++j) bld.idx[cur[rcell[j]]++] = j;
+        std::vector<double> tw(size_t(nimg) * d);
+        for (int64_t k = 0; k < nimg; ++k)
+            for (int a = 0; a < d; ++a) tw[size_t(k) * d + a] = bld.tsc[size_t(bld.idx[k]) * d + a];
+        bld.tsc.swap(tw);
     }
     for (int64_t cell = 0; cell < nroot_tot; ++cell) {
         TmpBox B;
@@ -653,11 +713,13 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     }
     // ---- level restriction: every colleague of the parent of a non-leaf box is non-leaf.
     // This keeps the leaves that meet a leaf's colleague neighbourhood within one level of it.
-    bool changed = true;
-    while (changed) {
-        changed = false;
-        size_t nb = bld.boxes.size();
-        for (size_t bi = 0; bi < nb; ++bi) {
+    // The rule's closure is unique and the renumbering below is canonical, so only boxes that
+    // became non-leaf since the last sweep need checking: all of them first, then the log.
+    std::vector<int> work;
+    for (size_t bi = 0; bi < bld.boxes.size(); ++bi) work.push_back(int(bi));
+    while (!work.empty()) {
+        bld.split_log.clear();
+        for (int bi : work) {
             const TmpBox Y = bld.boxes[bi];
             if (Y.level < 1 || Y.child0 < 0) continue;
             const TmpBox P = bld.boxes[Y.parent];
@@ -676,9 +738,9 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
                 int X = bld.find(P.level, c);
                 if (X >= 0 && bld.boxes[X].child0 >= 0) continue;
                 bld.ensure_nonleaf(P.level, c);
-                changed = true;
             }
         }
+        work.swap(bld.split_log);
     }
     // ---- renumber in level order (children of consecutive parents stay contiguous) ----
     const int nbtot = int(bld.boxes.size());
@@ -731,6 +793,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     int nn = 1;
     for (int a = 0; a < d; ++a) nn *= 3;
     t->colleague.assign(size_t(nbtot) * nn, -1);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < nbtot; ++k) {
         const TmpBox& B = bld.boxes[order[k]];
         for (int o = 0; o < nn; ++o) {
@@ -753,16 +816,22 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     std::vector<int64_t> is_tgt_prefix(nimg + 1, 0);
     s->tgt_of.clear();
     s->tgt_orig.clear();
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < nimg; ++j) {
         int64_t im = bld.idx[j];
         int64_t o = img_orig[im];
-        bool original = o >= 0;
-        s->orig[j] = original ? o : -(o + 1);
+        s->orig[j] = o >= 0 ? o : -(o + 1);
         for (int a = 0; a < d; ++a) s->pos[size_t(j) * d + a] = bld.pos[size_t(im) * d + a];
-        is_tgt_prefix[j + 1] = is_tgt_prefix[j] + (original ? 1 : 0);
-        if (original) {
-            s->tgt_of.push_back(j);
-            s->tgt_orig.push_back(o);
+    }
+    for (int64_t j = 0; j < nimg; ++j) is_tgt_prefix[j + 1] = is_tgt_prefix[j] + (img_orig[bld.idx[j]] >= 0 ? 1 : 0);
+    s->tgt_of.resize(size_t(is_tgt_prefix[nimg]));
+    s->tgt_orig.resize(size_t(is_tgt_prefix[nimg]));
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < nimg; ++j) {
+        const int64_t o = img_orig[bld.idx[j]];
+        if (o >= 0) {
+            s->tgt_of[is_tgt_prefix[j]] = j;
+            s->tgt_orig[is_tgt_prefix[j]] = o;
         }
     }
     t->tgt_begin.resize(nbtot);
