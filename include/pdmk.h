@@ -90,7 +90,10 @@ void pdmk_default_opts(pdmk_opts* opts);
  * Creates a plan for lattice L (d x d, column-major, host memory) and target relative L2
  * precision eps in [1e-12, 1e-2].  Orients L to upper-triangular form (Sec. 3.2, Eq. (3.4)),
  * picks r_c and n_s, sizes the root grid (Eq. (3.10), (3.12)) and the Fourier grid
- * (Eq. (3.15)), and computes the prolate tables in FP64.  opts may be NULL (defaults).
+ * (Eq. (3.15), each length rounded up to an even size with prime factors <= 13; mixed plans
+ * of strongly skewed cells enlarge it further so that FP32 rounding is not amplified by the
+ * window deconvolution; pdmk_get_info reports the sizes as M), and computes the prolate
+ * tables in FP64.  opts may be NULL (defaults).
  * Errors: BAD_ARG, BAD_EPS, SINGULAR_LATTICE, NONFINITE, CUDA, OOM.
  */
 int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, pdmk_plan* out);
