@@ -181,3 +181,20 @@ def test_eval_into_caller_arrays():
     with pytest.raises(ValueError):
         plan.eval(out=(np.empty(n + 1), go))
     plan.close()
+
+
+@pytest.mark.parametrize("case", ["random2d", "triclinic3d"])
+def test_split_parameters_leave_result_unchanged(case):
+    """The splitting radius r_c = L_min / kappa and the leaf capacity n_s change how the work
+    is divided (Algorithm 1 steps 1-2), not the result: every choice matches the oracle to
+    eps and the default plan to 2 eps."""
+    g = dict(CASES[case](), case=case)
+    pref, gref = oracle_ref(g)
+    eps = 1e-6
+    p0, g0, _ = run(g, eps, precision="fp64")
+    for kw in (dict(kappa=4.0), dict(kappa=10.0), dict(n_s=20), dict(n_s=200)):
+        pot, grad, info = run(g, eps, precision="fp64", **kw)
+        print(f"{case} {kw}: E_pot={rel(pot, pref):.2e} vs default {rel(pot, p0):.2e} M={info['M']} depth={info['depth']}")
+        assert rel(pot, pref) <= eps
+        assert rel(grad, gref) <= 10 * eps
+        assert rel(pot, p0) <= 2 * eps
