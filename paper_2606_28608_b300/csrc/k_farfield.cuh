@@ -301,16 +301,17 @@ __global__ void k_fold(FoldArgs<T, G> a) {
         collect(g1, a.M1, a.B1, a.P1, a.nb1, cb1, lo1, n1);
         if (D == 3) collect(g2, a.M2, a.B2, a.P2, a.nb2, cb2, lo2, n2);
         else { cb2[0] = 0; lo2[0] = 0; n2 = 1; }
-        T acc = T(0);
+        // the slabs are added in the grid's precision (FP64 for the FP64 transforms)
+        G acc = G(0);
         for (int i2 = 0; i2 < n2; ++i2)
             for (int i1 = 0; i1 < n1; ++i1)
                 for (int i0 = 0; i0 < n0; ++i0) {
                     const int bin = (cb2[i2] * a.nb1 + cb1[i1]) * a.nb0 + cb0[i0];
                     const int idx = (lo2[i2] * a.P1 + lo1[i1]) * a.P0 + lo0[i0];
                     for (int s = a.bin_sub_begin[bin]; s < a.bin_sub_begin[bin + 1]; ++s)
-                        acc += a.slab[size_t(s) * a.Ptot + idx];
+                        acc += G(a.slab[size_t(s) * a.Ptot + idx]);
                 }
-        a.grid[cell] = G(acc);
+        a.grid[cell] = acc;
     }
 }
 
