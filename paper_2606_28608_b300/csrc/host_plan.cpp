@@ -566,6 +566,74 @@ struct Builder {
         if (boxes[a].child0 < 0) split(a);
     }
 };
+
+// One root box's subtree, refined independently of the others (the splits of a root box only
+// permute its own range of the working arrays): its boxes (local index 0 = the root), and
+// the keys to enter in the builder's map once the subtrees are merged.
+struct LocalTree {
+    std::vector<TmpBox> boxes;
+    std::vector<std::pair<BoxKey, int>> keys;
+    std::vector<int> lab;
+    std::vector<int64_t> tmp;
+    std::vector<double> tsct;
+    int max_level = 0;
+};
+
+// Builder::split for a box of a local subtree (same arithmetic, same child order)
+static void split_local(Builder& bld, LocalTree& lt, int bi) {
+    const int d = bld.d;
+    TmpBox B = lt.boxes[bi];
+    int L = B.level + 1;
+    const double s2 = double(1LL << L);
+    int nc = bld.nchild();
+    int64_t cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    auto child_of = [&](int64_t j) {
+        int ch = 0;
+        for (int i = 0; i < d; ++i) {
+            double x = bld.tsc[j * d + i] * s2;
+            int64_t ci = int64_t(std::floor(x));
+            int64_t base = B.c[i] * 2;
+            int bit = int(ci - base);
+            if (bit < 0) bit = 0;
+            if (bit > 1) bit = 1;
+            ch |= bit << i;
+        }
+        return ch;
+    };
+    const int64_t m = B.e - B.b;
+    lt.lab.resize(size_t(m));
+    lt.tmp.resize(size_t(m));
+    lt.tsct.resize(size_t(m) * d);
+    for (int64_t j = B.b; j < B.e; ++j) {
+        lt.lab[j - B.b] = child_of(j);
+        cnt[lt.lab[j - B.b] + 1]++;
+    }
+    for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
+    int64_t cur[8];
+    for (int k = 0; k < nc; ++k) cur[k] = cnt[k];
+    for (int64_t j = B.b; j < B.e; ++j) {
+        const int64_t o = cur[lt.lab[j - B.b]]++;
+        lt.tmp[o] = bld.idx[j];
+        for (int i = 0; i < d; ++i) lt.tsct[size_t(o) * d + i] = bld.tsc[size_t(j) * d + i];
+    }
+    std::copy(lt.tmp.begin(), lt.tmp.begin() + m, bld.idx.begin() + B.b);
+    std::copy(lt.tsct.begin(), lt.tsct.begin() + m * d, bld.tsc.begin() + B.b * d);
+    int first = int(lt.boxes.size());
+    lt.boxes[bi].child0 = first;
+    for (int k = 0; k < nc; ++k) {
+        TmpBox C;
+        C.level = L;
+        C.c[0] = C.c[1] = C.c[2] = 0;
+        for (int i = 0; i < d; ++i) C.c[i] = B.c[i] * 2 + ((k >> i) & 1);
+        C.parent = bi;
+        C.child0 = -1;
+        C.b = B.b + cnt[k];
+        C.e = B.b + cnt[k + 1];
+        lt.boxes.push_back(C);
+        lt.keys.push_back({BoxKey{L, {C.c[0], C.c[1], C.c[2]}}, first + k});
+    }
+    if (L > lt.max_level) lt.max_level = L;
+}
 }  // namespace
 
 int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_depth, Tree* t,
@@ -610,53 +678,107 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
         nvec[lev] = 0;
     };
     rec(d - 1);
-    // per shift (in order), the points whose shifted copy lies in the box, in point order:
-    // each thread counts and then writes one contiguous chunk of points
+    // Images in shift order, and within a shift in point order.  Each point's admissible
+    // shifts are enumerated from the in-box bounds of the triangular frame (axis by axis from
+    // the last, with a small slack against rounding) and then accepted by the same test with
+    // the same arithmetic as a scan of every listed shift; listed shifts only.
+    const int ns = int(shifts.size());
+    int Bx[3] = {0, 0, 0};
+    for (const auto& sh : shifts)
+        for (int a = 0; a < d; ++a) Bx[a] = std::max(Bx[a], std::abs(sh[a]));
+    int64_t dimx[3] = {1, 1, 1}, ntab = 1;
+    for (int a = 0; a < d; ++a) { dimx[a] = 2 * Bx[a] + 1; ntab *= dimx[a]; }
+    auto flat = [&](const int* nv) {
+        int64_t f = 0;
+        for (int a = d - 1; a >= 0; --a) f = f * dimx[a] + (nv[a] + Bx[a]);
+        return f;
+    };
+    std::vector<int> sidx(static_cast<size_t>(ntab), -1);
+    std::vector<double> trs(size_t(ns) * 3, 0.0);
+    for (int k = 0; k < ns; ++k) {
+        sidx[size_t(flat(shifts[k].data()))] = k;
+        for (int a = 0; a < d; ++a)
+            for (int kk = a; kk < d; ++kk) trs[size_t(k) * 3 + a] += g.R[a * d + kk] * shifts[k][kk];
+    }
     int nthr = 1;
 #ifdef _OPENMP
     nthr = omp_get_max_threads();
 #endif
     const int64_t chunk = (n + nthr - 1) / std::max(nthr, 1);
-    std::vector<int64_t> ccount(size_t(nthr) + 1);
-    for (const auto& sh : shifts) {
-        double tr[3] = {0, 0, 0};
-        for (int a = 0; a < d; ++a)
-            for (int k = a; k < d; ++k) tr[a] += g.R[a * d + k] * sh[k];
-        bool zero = true;
-        for (int k = 0; k < d; ++k) zero &= (sh[k] == 0);
-        auto inside = [&](int64_t j) {
-            bool in = true;
-            for (int a = 0; a < d; ++a) {
-                const double p = x[j * d + a] + tr[a];
-                in &= (p >= g.lo[a] && p < hi[a]);
-            }
-            return in;
-        };
-        bool missing = false;
+    std::vector<std::vector<std::pair<int, int64_t>>> acc(static_cast<size_t>(nthr));
+    bool missing = false;
 #pragma omp parallel for schedule(static, 1) reduction(|| : missing)
-        for (int c = 0; c < nthr; ++c) {
-            int64_t k = 0;
-            for (int64_t j = c * chunk; j < std::min(n, (c + 1) * chunk); ++j) {
-                const bool in = inside(j);
-                if (zero && !in) missing = true;
-                k += in;
+    for (int c = 0; c < nthr; ++c) {
+        auto& out = acc[size_t(c)];
+        for (int64_t j = c * chunk; j < std::min(n, (c + 1) * chunk); ++j) {
+            const double* xj = &x[size_t(j) * d];
+            auto accept = [&](int k) {
+                bool in = true;
+                for (int a = 0; a < d; ++a) {
+                    const double p = xj[a] + trs[size_t(k) * 3 + a];
+                    in &= (p >= g.lo[a] && p < hi[a]);
+                }
+                return in;
+            };
+            if (!accept(0)) { missing = true; continue; }  // the cell lies inside the inner block
+            // nested intervals, axis by axis from the last: the bounds carry a slack of 1e-9
+            // (far above their rounding) and every candidate then takes the exact test
+            auto range = [&](int a, const int* nv, int* lo_n, int* hi_n) {
+                double off = 0;
+                for (int k = a + 1; k < d; ++k) off += g.R[a * d + k] * nv[k];
+                const double raa = g.R[a * d + a];
+                const double l = (g.lo[a] - xj[a] - off) / raa, h = (hi[a] - xj[a] - off) / raa;
+                const double sl = 1e-9 * (1.0 + std::fabs(l)), sh = 1e-9 * (1.0 + std::fabs(h));
+                *lo_n = std::max(-Bx[a], int(std::ceil(l - sl)));
+                *hi_n = std::min(Bx[a], int(std::floor(h + sh)));
+            };
+            int nv[3] = {0, 0, 0};
+            int l2 = 0, h2 = 0, l1 = 0, h1 = 0, l0 = 0, h0 = 0;
+            if (d == 3) range(2, nv, &l2, &h2);
+            for (int v2 = l2; v2 <= h2; ++v2) {
+                nv[2] = d == 3 ? v2 : 0;
+                range(1, nv, &l1, &h1);
+                for (int v1 = l1; v1 <= h1; ++v1) {
+                    nv[1] = v1;
+                    range(0, nv, &l0, &h0);
+                    for (int v0 = l0; v0 <= h0; ++v0) {
+                        nv[0] = v0;
+                        const int k = sidx[size_t(flat(nv))];
+                        if (k > 0 && accept(k)) out.push_back({k, j});
+                    }
+                }
             }
-            ccount[c + 1] = k;
         }
-        if (missing) return PDMK_ERR_INTERNAL;  // the cell lies inside the inner block
-        ccount[0] = int64_t(img_orig.size());
-        for (int c = 0; c < nthr; ++c) ccount[c + 1] += ccount[c];
-        img_orig.resize(size_t(ccount[nthr]));
-        bld.pos.resize(size_t(ccount[nthr]) * d);
-#pragma omp parallel for schedule(static, 1)
+    }
+    if (missing) return PDMK_ERR_INTERNAL;
+    // offsets: shift 0 holds the originals in point order; then shift by shift, thread
+    // chunks in order (points in increasing order within each)
+    std::vector<int64_t> cnt(size_t(ns) * nthr, 0);
+    for (int c = 0; c < nthr; ++c)
+        for (const auto& pr : acc[size_t(c)]) cnt[size_t(pr.first) * nthr + c]++;
+    std::vector<int64_t> off(size_t(ns) * nthr, 0);
+    int64_t run = n;
+    for (int k = 1; k < ns; ++k)
         for (int c = 0; c < nthr; ++c) {
-            int64_t o = ccount[c];
-            for (int64_t j = c * chunk; j < std::min(n, (c + 1) * chunk); ++j) {
-                if (!inside(j)) continue;
-                img_orig[o] = zero ? j : -(j + 1);
-                for (int a = 0; a < d; ++a) bld.pos[size_t(o) * d + a] = x[j * d + a] + tr[a];
-                ++o;
-            }
+            off[size_t(k) * nthr + c] = run;
+            run += cnt[size_t(k) * nthr + c];
+        }
+    img_orig.resize(size_t(run));
+    bld.pos.resize(size_t(run) * d);
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j) {
+        img_orig[size_t(j)] = j;
+        for (int a = 0; a < d; ++a) bld.pos[size_t(j) * d + a] = x[size_t(j) * d + a] + trs[a];
+    }
+#pragma omp parallel for schedule(static, 1)
+    for (int c = 0; c < nthr; ++c) {
+        std::vector<int64_t> o(static_cast<size_t>(ns));
+        for (int k = 1; k < ns; ++k) o[size_t(k)] = off[size_t(k) * nthr + c];
+        for (const auto& pr : acc[size_t(c)]) {
+            const int64_t w = o[size_t(pr.first)]++;
+            img_orig[size_t(w)] = -(pr.second + 1);
+            for (int a = 0; a < d; ++a)
+                bld.pos[size_t(w) * d + a] = x[size_t(pr.second) * d + a] + trs[size_t(pr.first) * 3 + a];
         }
     }
     const int64_t nimg = int64_t(img_orig.size());
@@ -683,8 +805,27 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     for (int64_t k = 0; k < nroot_tot; ++k) rcnt[k + 1] += rcnt[k];
     bld.idx.resize(nimg);
     {
-        std::vector<int64_t> cur(rcnt.begin(), rcnt.end() - 1);
-        for (int64_t j = 0; j < nimg; ++j) bld.idx[cur[rcell[j]]++] = j;
+        // stable counting sort, in parallel: thread chunks of images in order
+        int nt = 1;
+#ifdef _OPENMP
+        nt = omp_get_max_threads();
+#endif
+        const int64_t ch = (nimg + nt - 1) / std::max(nt, 1);
+        std::vector<int64_t> tc(size_t(nt) * size_t(nroot_tot), 0);
+#pragma omp parallel for schedule(static, 1)
+        for (int c = 0; c < nt; ++c)
+            for (int64_t j = c * ch; j < std::min(nimg, (c + 1) * ch); ++j) tc[size_t(c) * nroot_tot + rcell[j]]++;
+        for (int64_t cell = 0; cell < nroot_tot; ++cell) {
+            int64_t o = rcnt[cell];
+            for (int c = 0; c < nt; ++c) {
+                const int64_t v = tc[size_t(c) * nroot_tot + cell];
+                tc[size_t(c) * nroot_tot + cell] = o;
+                o += v;
+            }
+        }
+#pragma omp parallel for schedule(static, 1)
+        for (int c = 0; c < nt; ++c)
+            for (int64_t j = c * ch; j < std::min(nimg, (c + 1) * ch); ++j) bld.idx[tc[size_t(c) * nroot_tot + rcell[j]]++] = j;
         std::vector<double> tw(size_t(nimg) * d);
         for (int64_t k = 0; k < nimg; ++k)
             for (int a = 0; a < d; ++a) tw[size_t(k) * d + a] = bld.tsc[size_t(bld.idx[k]) * d + a];
@@ -707,9 +848,34 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
         bld.map[BoxKey{0, {B.c[0], B.c[1], B.c[2]}}] = int(cell);
     }
     // ---- refine boxes holding more than n_s sources (Algorithm 1, step 2) ----
-    for (size_t bi = 0; bi < bld.boxes.size(); ++bi) {
-        if (bld.boxes[bi].e - bld.boxes[bi].b > n_s && bld.boxes[bi].level < max_depth)
-            bld.split(int(bi));
+    // Root boxes refine independently (in parallel); their subtrees are then appended in
+    // root order.  Box numbering here does not matter: the tree is renumbered canonically
+    // (level order, children in order) below.
+    {
+        std::vector<LocalTree> locals(static_cast<size_t>(nroot_tot));
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t r = 0; r < nroot_tot; ++r) {
+            LocalTree& lt = locals[size_t(r)];
+            lt.boxes.push_back(bld.boxes[size_t(r)]);
+            for (size_t bi = 0; bi < lt.boxes.size(); ++bi)
+                if (lt.boxes[bi].e - lt.boxes[bi].b > n_s && lt.boxes[bi].level < max_depth)
+                    split_local(bld, lt, int(bi));
+        }
+        for (int64_t r = 0; r < nroot_tot; ++r) {
+            LocalTree& lt = locals[size_t(r)];
+            const int base = int(bld.boxes.size());
+            auto gid = [&](int l) { return l == 0 ? int(r) : base + l - 1; };
+            bld.boxes[size_t(r)].child0 = lt.boxes[0].child0 < 0 ? -1 : gid(lt.boxes[0].child0);
+            for (size_t l = 1; l < lt.boxes.size(); ++l) {
+                TmpBox B = lt.boxes[l];
+                B.parent = gid(B.parent);
+                B.child0 = B.child0 < 0 ? -1 : gid(B.child0);
+                bld.boxes.push_back(B);
+            }
+            for (const auto& kv : lt.keys) bld.map[kv.first] = gid(kv.second);
+            bld.max_level = std::max(bld.max_level, lt.max_level);
+            LocalTree().boxes.swap(lt.boxes);
+        }
     }
     // ---- level restriction: every colleague of the parent of a non-leaf box is non-leaf.
     // This keeps the leaves that meet a leaf's colleague neighbourhood within one level of it.
@@ -717,29 +883,55 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     // became non-leaf since the last sweep need checking: all of them first, then the log.
     std::vector<int> work;
     for (size_t bi = 0; bi < bld.boxes.size(); ++bi) work.push_back(int(bi));
+    struct Need {
+        int level;
+        int64_t c[3];
+    };
+    int nthb = 1;
+#ifdef _OPENMP
+    nthb = omp_get_max_threads();
+#endif
+    std::vector<std::vector<Need>> need(static_cast<size_t>(nthb));
     while (!work.empty()) {
         bld.split_log.clear();
-        for (int bi : work) {
-            const TmpBox Y = bld.boxes[bi];
-            if (Y.level < 1 || Y.child0 < 0) continue;
-            const TmpBox P = bld.boxes[Y.parent];
-            int nn = 1;
-            for (int a = 0; a < d; ++a) nn *= 3;
-            for (int o = 0; o < nn; ++o) {
-                int64_t c[3] = {0, 0, 0};
-                int r = o;
-                bool ok = true;
-                for (int a = 0; a < d; ++a) {
-                    c[a] = P.c[a] + (r % 3) - 1;
-                    r /= 3;
-                    ok &= (c[a] >= 0 && c[a] < bld.dim_at(a, P.level));
+        // find the violations in parallel (read-only), then repair them in order
+#pragma omp parallel
+        {
+            int tid = 0;
+#ifdef _OPENMP
+            tid = omp_get_thread_num();
+#endif
+            auto& mine = need[size_t(tid)];
+            mine.clear();
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t w = 0; w < int64_t(work.size()); ++w) {
+                const TmpBox& Y = bld.boxes[size_t(work[size_t(w)])];
+                if (Y.level < 1 || Y.child0 < 0) continue;
+                const TmpBox& P = bld.boxes[size_t(Y.parent)];
+                int nn = 1;
+                for (int a = 0; a < d; ++a) nn *= 3;
+                for (int o = 0; o < nn; ++o) {
+                    int64_t c[3] = {0, 0, 0};
+                    int r = o;
+                    bool ok = true;
+                    for (int a = 0; a < d; ++a) {
+                        c[a] = P.c[a] + (r % 3) - 1;
+                        r /= 3;
+                        ok &= (c[a] >= 0 && c[a] < bld.dim_at(a, P.level));
+                    }
+                    if (!ok) continue;
+                    int X = bld.find(P.level, c);
+                    if (X >= 0 && bld.boxes[size_t(X)].child0 >= 0) continue;
+                    mine.push_back(Need{P.level, {c[0], c[1], c[2]}});
                 }
-                if (!ok) continue;
-                int X = bld.find(P.level, c);
-                if (X >= 0 && bld.boxes[X].child0 >= 0) continue;
-                bld.ensure_nonleaf(P.level, c);
             }
         }
+        for (const auto& list : need)
+            for (const Need& nd : list) {
+                int X = bld.find(nd.level, nd.c);
+                if (X >= 0 && bld.boxes[size_t(X)].child0 >= 0) continue;
+                bld.ensure_nonleaf(nd.level, nd.c);
+            }
         work.swap(bld.split_log);
     }
     // ---- renumber in level order (children of consecutive parents stay contiguous) ----
