@@ -116,3 +116,28 @@ def test_window_transform_matches_quadrature(eps):
         if prev is not None:
             assert got < prev
         prev = got
+
+
+def test_plan_create_rejects_bad_arguments():
+    """pdmk_plan_create validates its arguments before any device work: dimension and
+    pointers (BAD_ARG), eps outside [1e-12, 1e-2] (BAD_EPS), non-finite lattice entries
+    (NONFINITE) and an unknown precision (BAD_ARG); the output handle stays NULL."""
+    lib = P.lib()
+    L2 = np.ascontiguousarray(np.array([[1.0, 0.3], [0.0, 0.9]]).T)  # column-major
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out = ctypes.c_void_p(1234)
+    assert lib.pdmk_plan_create(4, ptr(L2), ctypes.c_double(1e-6), None, ctypes.byref(out)) == -1
+    assert lib.pdmk_plan_create(2, None, ctypes.c_double(1e-6), None, ctypes.byref(out)) == -1
+    out = ctypes.c_void_p(1234)
+    assert lib.pdmk_plan_create(2, ptr(L2), ctypes.c_double(1e-13), None, ctypes.byref(out)) == -4
+    assert not out.value
+    assert lib.pdmk_plan_create(2, ptr(L2), ctypes.c_double(0.5), None, ctypes.byref(out)) == -4
+    bad = L2.copy()
+    bad[1] = np.nan
+    assert lib.pdmk_plan_create(2, ptr(bad), ctypes.c_double(1e-6), None, ctypes.byref(out)) == -5
+    o = P.Opts()
+    lib.pdmk_default_opts(ctypes.byref(o))
+    o.precision = 7
+    assert lib.pdmk_plan_create(2, ptr(L2), ctypes.c_double(1e-6), ctypes.byref(o), ctypes.byref(out)) == -1
+    with pytest.raises(P.PdmkError):
+        P.Plan(np.eye(2), 1e-13)
