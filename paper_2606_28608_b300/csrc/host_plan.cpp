@@ -465,6 +465,65 @@ struct TmpBox {
     int64_t b, e;  // range in the working index array
 };
 
+// Splits box bi of `boxes` into its 2^d children: the box's range of the working arrays
+// (idx, and tsc, d scaled coordinates per position) is reordered child by child (a stable
+// counting sort), the children are appended to `boxes`, and on_child(key, index) is called
+// for each.  (pos - lo) / h_L = 2^L tsc exactly: scaling by a power of two commutes with
+// rounding.
+template <class OnChild>
+static void split_box(int d, std::vector<int64_t>& idx, std::vector<double>& tsc, std::vector<TmpBox>& boxes,
+                      int bi, std::vector<int>& lab, std::vector<int64_t>& tmp, std::vector<double>& tsct,
+                      OnChild on_child) {
+    TmpBox B = boxes[bi];
+    const int L = B.level + 1;
+    const double s2 = double(1LL << L);
+    const int nc = 1 << d;
+    int64_t cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    auto child_of = [&](int64_t j) {  // working position j
+        int ch = 0;
+        for (int i = 0; i < d; ++i) {
+            const int64_t ci = int64_t(std::floor(tsc[j * d + i] * s2));
+            int bit = int(ci - B.c[i] * 2);
+            if (bit < 0) bit = 0;
+            if (bit > 1) bit = 1;
+            ch |= bit << i;
+        }
+        return ch;
+    };
+    const int64_t m = B.e - B.b;
+    lab.resize(size_t(m));
+    tmp.resize(size_t(m));
+    tsct.resize(size_t(m) * d);
+    for (int64_t j = B.b; j < B.e; ++j) {
+        lab[j - B.b] = child_of(j);
+        cnt[lab[j - B.b] + 1]++;
+    }
+    for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
+    int64_t cur[8];
+    for (int k = 0; k < nc; ++k) cur[k] = cnt[k];
+    for (int64_t j = B.b; j < B.e; ++j) {
+        const int64_t o = cur[lab[j - B.b]]++;
+        tmp[o] = idx[j];
+        for (int i = 0; i < d; ++i) tsct[size_t(o) * d + i] = tsc[size_t(j) * d + i];
+    }
+    std::copy(tmp.begin(), tmp.begin() + m, idx.begin() + B.b);
+    std::copy(tsct.begin(), tsct.begin() + m * d, tsc.begin() + B.b * d);
+    const int first = int(boxes.size());
+    boxes[bi].child0 = first;
+    for (int k = 0; k < nc; ++k) {
+        TmpBox C;
+        C.level = L;
+        C.c[0] = C.c[1] = C.c[2] = 0;
+        for (int i = 0; i < d; ++i) C.c[i] = B.c[i] * 2 + ((k >> i) & 1);
+        C.parent = bi;
+        C.child0 = -1;
+        C.b = B.b + cnt[k];
+        C.e = B.b + cnt[k + 1];
+        boxes.push_back(C);
+        on_child(BoxKey{L, {C.c[0], C.c[1], C.c[2]}}, first + k);
+    }
+}
+
 struct Builder {
     int d;
     const Geometry* g;
@@ -490,60 +549,9 @@ struct Builder {
     }
 
     void split(int bi) {
-        TmpBox B = boxes[bi];
-        int L = B.level + 1;
-        const double s2 = double(1LL << L);
-        int nc = nchild();
-        int64_t cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        auto child_of = [&](int64_t j) {  // working position j
-            int ch = 0;
-            for (int i = 0; i < d; ++i) {
-                // (pos - lo) / (r_c 2^-L) = 2^L (pos - lo) / r_c, rounding included: scaling
-                // by a power of two commutes with rounding
-                double x = tsc[j * d + i] * s2;
-                int64_t ci = int64_t(std::floor(x));
-                int64_t base = B.c[i] * 2;
-                int bit = int(ci - base);
-                if (bit < 0) bit = 0;
-                if (bit > 1) bit = 1;
-                ch |= bit << i;
-            }
-            return ch;
-        };
-        const int64_t m = B.e - B.b;
-        lab.resize(size_t(m));
-        tmp.resize(size_t(m));
-        tsct.resize(size_t(m) * d);
-        for (int64_t j = B.b; j < B.e; ++j) {
-            lab[j - B.b] = child_of(j);
-            cnt[lab[j - B.b] + 1]++;
-        }
-        for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
-        int64_t cur[8];
-        for (int k = 0; k < nc; ++k) cur[k] = cnt[k];
-        for (int64_t j = B.b; j < B.e; ++j) {
-            const int64_t o = cur[lab[j - B.b]]++;
-            tmp[o] = idx[j];
-            for (int i = 0; i < d; ++i) tsct[size_t(o) * d + i] = tsc[size_t(j) * d + i];
-        }
-        std::copy(tmp.begin(), tmp.begin() + m, idx.begin() + B.b);
-        std::copy(tsct.begin(), tsct.begin() + m * d, tsc.begin() + B.b * d);
-        int first = int(boxes.size());
-        boxes[bi].child0 = first;
+        split_box(d, idx, tsc, boxes, bi, lab, tmp, tsct, [&](const BoxKey& k, int id) { map[k] = id; });
         split_log.push_back(bi);
-        for (int k = 0; k < nc; ++k) {
-            TmpBox C;
-            C.level = L;
-            C.c[0] = C.c[1] = C.c[2] = 0;
-            for (int i = 0; i < d; ++i) C.c[i] = B.c[i] * 2 + ((k >> i) & 1);
-            C.parent = bi;
-            C.child0 = -1;
-            C.b = B.b + cnt[k];
-            C.e = B.b + cnt[k + 1];
-            boxes.push_back(C);
-            map[BoxKey{L, {C.c[0], C.c[1], C.c[2]}}] = first + k;
-        }
-        if (L > max_level) max_level = L;
+        max_level = std::max(max_level, boxes[bi].level + 1);
     }
 
     // make the box at (level, c) exist and have children
@@ -579,60 +587,11 @@ struct LocalTree {
     int max_level = 0;
 };
 
-// Builder::split for a box of a local subtree (same arithmetic, same child order)
+// Builder::split for a box of a local subtree (the same split_box)
 static void split_local(Builder& bld, LocalTree& lt, int bi) {
-    const int d = bld.d;
-    TmpBox B = lt.boxes[bi];
-    int L = B.level + 1;
-    const double s2 = double(1LL << L);
-    int nc = bld.nchild();
-    int64_t cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    auto child_of = [&](int64_t j) {
-        int ch = 0;
-        for (int i = 0; i < d; ++i) {
-            double x = bld.tsc[j * d + i] * s2;
-            int64_t ci = int64_t(std::floor(x));
-            int64_t base = B.c[i] * 2;
-            int bit = int(ci - base);
-            if (bit < 0) bit = 0;
-            if (bit > 1) bit = 1;
-            ch |= bit << i;
-        }
-        return ch;
-    };
-    const int64_t m = B.e - B.b;
-    lt.lab.resize(size_t(m));
-    lt.tmp.resize(size_t(m));
-    lt.tsct.resize(size_t(m) * d);
-    for (int64_t j = B.b; j < B.e; ++j) {
-        lt.lab[j - B.b] = child_of(j);
-        cnt[lt.lab[j - B.b] + 1]++;
-    }
-    for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
-    int64_t cur[8];
-    for (int k = 0; k < nc; ++k) cur[k] = cnt[k];
-    for (int64_t j = B.b; j < B.e; ++j) {
-        const int64_t o = cur[lt.lab[j - B.b]]++;
-        lt.tmp[o] = bld.idx[j];
-        for (int i = 0; i < d; ++i) lt.tsct[size_t(o) * d + i] = bld.tsc[size_t(j) * d + i];
-    }
-    std::copy(lt.tmp.begin(), lt.tmp.begin() + m, bld.idx.begin() + B.b);
-    std::copy(lt.tsct.begin(), lt.tsct.begin() + m * d, bld.tsc.begin() + B.b * d);
-    int first = int(lt.boxes.size());
-    lt.boxes[bi].child0 = first;
-    for (int k = 0; k < nc; ++k) {
-        TmpBox C;
-        C.level = L;
-        C.c[0] = C.c[1] = C.c[2] = 0;
-        for (int i = 0; i < d; ++i) C.c[i] = B.c[i] * 2 + ((k >> i) & 1);
-        C.parent = bi;
-        C.child0 = -1;
-        C.b = B.b + cnt[k];
-        C.e = B.b + cnt[k + 1];
-        lt.boxes.push_back(C);
-        lt.keys.push_back({BoxKey{L, {C.c[0], C.c[1], C.c[2]}}, first + k});
-    }
-    if (L > lt.max_level) lt.max_level = L;
+    split_box(bld.d, bld.idx, bld.tsc, lt.boxes, bi, lt.lab, lt.tmp, lt.tsct,
+              [&](const BoxKey& k, int id) { lt.keys.push_back({k, id}); });
+    lt.max_level = std::max(lt.max_level, lt.boxes[bi].level + 1);
 }
 }  // namespace
 
