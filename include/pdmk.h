@@ -160,7 +160,10 @@ int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where);
  *    needs to start at zero.
  *  - Launches are eager (never replayed from a captured graph) and on the plan's stream
  *    order, asynchronous like pdmk_eval with device pointers.
- * Errors: BAD_ARG, NOT_READY, TOO_LARGE, CUDA.
+ * Errors: BAD_ARG, NOT_READY, TOO_LARGE, CUDA, TIMEOUT.  TIMEOUT: as for pdmk_eval; the call
+ * does not synchronise, so a bounded wait that expires during it is reported by the plan's
+ * next call (pdmk_eval, pdmk_eval_noalloc or pdmk_eval_adjoint), and an expiry left by an
+ * earlier evaluation is reported by this call before it launches anything.
  */
 int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad);
 

@@ -42,7 +42,16 @@ using namespace pdmk;
         }                                                    \
     } while (0)
 
-constexpr int kSumBlocks = 2 * 148;  // blocks of the two-stage charge sums
+// streaming multiprocessors of the current device (grid sizing)
+static int device_sms() {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || nsm <= 0) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nsm;
+}
 
 struct pdmk_plan_s {
     int d = 3;
@@ -91,7 +100,9 @@ struct pdmk_plan_s {
     bool fft32 = false;        // FP32 transforms (2D mixed plans)
     void* d_spec = nullptr;
     double* d_qsums = nullptr;
-    double* d_qsum_part = nullptr;  // [kSumBlocks][3] partial charge sums
+    double* d_qsum_part = nullptr;  // [sum_blocks][3] partial charge sums
+    int nsm = 1;                    // SMs of the plan's device
+    int sum_blocks = 2;             // blocks of the two-stage charge sums (2 per SM)
     unsigned long long* d_count = nullptr;
     bool count_pending = false;
     cufftHandle fft_fwd = 0, fft_inv = 0;
@@ -261,7 +272,7 @@ static void size_bins(pdmk_plan plan) {
     plan->nbins_tot = plan->nbin[0] * plan->nbin[1] * plan->nbin[2];
     // 2D grids whose 8 per-warp copies fit in ~96 KB of shared memory use whole-grid spreading
     const size_t ts = plan->opts.precision == PDMK_MIXED ? 4 : 8;
-    plan->whole_ctas = (d == 2 && size_t(plan->ncell) * ts * 8 <= size_t(96) * 1024) ? 2 * 148 : 0;
+    plan->whole_ctas = (d == 2 && size_t(plan->ncell) * ts * 8 <= size_t(96) * 1024) ? 2 * plan->nsm : 0;
 }
 
 // Largest far-field weight over the one of the lowest nonzero mode.  Eq. (3.15) puts the
@@ -443,8 +454,9 @@ static double cheb_to_mono(const std::vector<double>& c, std::vector<double>* a)
 }
 
 int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, pdmk_plan* out) {
-    if (!out || !L || (d != 2 && d != 3)) return PDMK_ERR_BAD_ARG;
+    if (!out) return PDMK_ERR_BAD_ARG;
     *out = nullptr;
+    if (!L || (d != 2 && d != 3)) return PDMK_ERR_BAD_ARG;
     if (!(eps >= 1e-12 && eps <= 1e-2)) return PDMK_ERR_BAD_EPS;
     for (int i = 0; i < d * d; ++i)
         if (!std::isfinite(L[i])) return PDMK_ERR_NONFINITE;
@@ -458,6 +470,9 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     plan->d = d;
     plan->eps = eps;
     plan->stream = static_cast<cudaStream_t>(plan->opts.stream);
+    plan->nsm = device_sms();
+    plan->sum_blocks = 2 * plan->nsm;
+    plan->pw.nsm = plan->nsm;
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (cudaStreamCreateWithFlags(&plan->ws, cudaStreamNonBlocking) != cudaSuccess ||
@@ -600,7 +615,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
         PCHECK(dalloc(plan, plan->plan_allocs, &p, 2 * (plan->fft32 ? 4 : 8) * size_t(plan->nhalf)));
         plan->d_spec = p;
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsums, 4));
-        PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsum_part, size_t(3 * kSumBlocks)));
+        PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_qsum_part, size_t(3 * plan->sum_blocks)));
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_count, 2));
     }
     {
@@ -676,7 +691,7 @@ static int gather_charges(pdmk_plan plan) {
     a.tgt4 = static_cast<T*>(plan->d_tgt4);
     a.q_tgt = plan->d_q_tgt;
     int64_t mx = std::max(plan->nimg, std::max(plan->nspread, plan->ntgt));
-    int blocks = int(std::min<int64_t>((mx + 255) / 256, 148 * 16));
+    int blocks = int(std::min<int64_t>((mx + 255) / 256, int64_t(plan->nsm) * 16));
     k_gather_charges<T><<<std::max(blocks, 1), 256, 0, plan->ws>>>(a);
     CK(cudaGetLastError());
     return PDMK_OK;
@@ -684,7 +699,7 @@ static int gather_charges(pdmk_plan plan) {
 
 static int set_charges_device(pdmk_plan plan, bool check_neutral) {
     // deterministic two-stage sums over many SMs (FP64 on one SM would take ~0.2 ms)
-    const int nb = int(std::max<int64_t>(1, std::min<int64_t>(kSumBlocks, (plan->n + 1023) / 1024)));
+    const int nb = int(std::max<int64_t>(1, std::min<int64_t>(plan->sum_blocks, (plan->n + 1023) / 1024)));
     k_charge_sums_part<<<nb, kSumThreads, 0, plan->ws>>>(plan->d_q_user, plan->n, plan->d_qsum_part);
     k_charge_sums_final<<<1, kSumThreads, 0, plan->ws>>>(plan->d_qsum_part, nb, plan->d_qsums);
     CK(cudaGetLastError());
@@ -1146,6 +1161,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
     for (auto e : plan->ev) cudaEventDestroy(e);
     plan->ev.clear();
     plan->stage_names.clear();
+    plan->stage_ms.clear();
     if ((r = stage_mark(plan, "start"))) return r;
     // Three independent branches until assembly: far field on ws, plane-wave passes on
     // ws_pw, near-field sum on ws_near (one stream when profiling per stage).
@@ -1252,7 +1268,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         fa.B0 = plan->B[0]; fa.B1 = plan->B[1]; fa.B2 = plan->B[2];
         fa.P0 = plan->P[0]; fa.P1 = plan->P[1]; fa.P2 = plan->P[2]; fa.Ptot = plan->Ptot;
         fa.fw = plan->w / 2;
-        int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, 148 * 8));
+        int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, int64_t(plan->nsm) * 8));
         k_fold<T, D, G><<<std::max(blocks, 1), 256, 0, s>>>(fa);
         };
         if (plan->fft32) fold(static_cast<float*>(plan->d_grid64));
@@ -1262,14 +1278,14 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
     }
     }
     if ((r = stage_mark(plan, "spread"))) return r;
-    const int cblocks = int(std::max<int64_t>(1, std::min<int64_t>((plan->ncell + 255) / 256, 148 * 8)));
+    const int cblocks = int(std::max<int64_t>(1, std::min<int64_t>((plan->ncell + 255) / 256, int64_t(plan->nsm) * 8)));
     if (plan->fft32)
         CKFFT(cufftExecR2C(plan->fft_fwd, (cufftReal*)plan->d_grid64, (cufftComplex*)plan->d_spec));
     else
         CKFFT(cufftExecD2Z(plan->fft_fwd, (cufftDoubleReal*)plan->d_grid64, (cufftDoubleComplex*)plan->d_spec));
     if ((r = stage_mark(plan, "fft_fwd"))) return r;
     {
-        int blocks = int(std::min<int64_t>((plan->nhalf + 255) / 256, 148 * 8));
+        int blocks = int(std::min<int64_t>((plan->nhalf + 255) / 256, int64_t(plan->nsm) * 8));
         if (plan->fft32)
             k_scale<float><<<std::max(blocks, 1), 256, 0, s>>>(static_cast<float*>(plan->d_spec), plan->d_weight,
                                                                plan->nhalf);
@@ -1325,7 +1341,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
     } else if (plan->ntgt > 0 && D == 3 && plan->far_warp3d && plan->ntgt < 50000) {
         // (with many targets a thread per target already fills the GPU)
         auto interp = [&](auto kern) {
-            const int warps = int(std::min<int64_t>(plan->ntgt, int64_t(148) * 64));
+            const int warps = int(std::min<int64_t>(plan->ntgt, int64_t(plan->nsm) * 64));
             kern<<<(warps + 7) / 8, 256, 0, s>>>(static_cast<const T*>(plan->d_grid), plan->d_t_g0,
                                                  static_cast<const T*>(plan->d_t_dq), int(plan->ntgt), g.M[0], g.M[1],
                                                  g.M[2], hwi2, static_cast<const T*>(plan->d_monoW),
@@ -1454,7 +1470,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         aa.pot_out = pot;
         aa.grad_out = grad;
         aa.out_first = out_first;
-        int blocks = int(std::min<int64_t>((plan->ntgt + 255) / 256, 148 * 8));
+        int blocks = int(std::min<int64_t>((plan->ntgt + 255) / 256, int64_t(plan->nsm) * 8));
         k_assemble<D, T><<<std::max(blocks, 1), 256, 0, s>>>(aa);
         ++plan->launches;
         CK(cudaGetLastError());
@@ -1547,7 +1563,7 @@ extern "C" int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where) {
 
 extern "C" int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, int cap) {
     if (!plan) return PDMK_ERR_BAD_ARG;
-    int n = int(plan->stage_ms.size()) - 1;
+    int n = int(std::min(plan->stage_ms.size(), plan->stage_names.size())) - 1;
     if (n < 0) n = 0;
     for (int i = 0; i < n && i < cap; ++i) {
         if (names) names[i] = plan->stage_names[i + 1].c_str();
@@ -1709,7 +1725,7 @@ extern "C" int pdmk_eval_adjoint(pdmk_plan plan, const double* g_pot, const doub
     // g grad Phi[q] + q grad Phi[g] at every point, in place (element-wise): the source rows
     // are g_y, the target rows g_x
     if (g_y || g_x) {
-        const int blocks = int(std::min<int64_t>((n * d + 255) / 256, 148 * 8));
+        const int blocks = int(std::min<int64_t>((n * d + 255) / 256, int64_t(plan->nsm) * 8));
         k_adjoint_combine<<<std::max(blocks, 1), 256, 0, plan->ws>>>(n, d, gdev, q_save, grad_q, grad_g, grad_q);
         CK(cudaGetLastError());
     }
@@ -1764,8 +1780,9 @@ extern "C" void pdmk_batch_destroy(pdmk_batch b) {
 
 extern "C" int pdmk_batch_create(int ncells, const int* d, const double* L, const double* eps, const pdmk_opts* opts,
                                  pdmk_batch* out) {
-    if (!out || ncells <= 0 || !d || !L || !eps) return PDMK_ERR_BAD_ARG;
+    if (!out) return PDMK_ERR_BAD_ARG;
     *out = nullptr;
+    if (ncells <= 0 || !d || !L || !eps) return PDMK_ERR_BAD_ARG;
     pdmk_batch b = new (std::nothrow) pdmk_batch_s();
     if (!b) return PDMK_ERR_OOM;
     pdmk_opts o;

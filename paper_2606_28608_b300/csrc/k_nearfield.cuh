@@ -18,6 +18,12 @@ namespace pdmk {
 constexpr int kNearThreads = 64;
 constexpr int kNearTile = 64;
 constexpr int kNearMaxList = 256;
+// The target groups below must tile the block exactly: a group size C above the block gives
+// G = kNearThreads / C = 0 groups, and the source loop (j += G) would never advance; a C that
+// does not divide the block leaves threads outside every group.  C is the smallest power of
+// two >= the leaf's target count, capped at the block, so a power-of-two block is required.
+static_assert(kNearThreads > 0 && (kNearThreads & (kNearThreads - 1)) == 0, "block must be a power of two");
+static_assert(kNearTile == kNearThreads, "one staged source per thread");
 
 // Clenshaw with a compile-time number of terms (coefficients zero-padded) and coefficients
 // in registers: fully unrolled.
@@ -74,7 +80,7 @@ k_nearfield(NearArgs<T> a) {
     // most lanes busy
     int C = 1;
     while (C < nt && C < kNearThreads) C <<= 1;
-    const int G = kNearThreads / C;
+    const int G = kNearThreads / C;  // >= 1, and G * C == kNearThreads (power-of-two C <= block)
     const int lt = tid % C;
     const int grp = tid / C;
     const bool ingrp = grp < G;

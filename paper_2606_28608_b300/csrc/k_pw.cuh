@@ -30,6 +30,7 @@ struct PwPlan {
     int* h_err = nullptr;   // host-mapped flag: a bounded device wait expired (sticky)
     int* d_err = nullptr;   // its device address
     int wait_test = 0;      // test hook: make the first dependent downward item wait forever
+    int nsm = 1;            // SMs of the plan's device (grid sizing)
     std::vector<void*> allocs;
     void* impl = nullptr;
 };

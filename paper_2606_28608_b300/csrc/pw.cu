@@ -2210,7 +2210,7 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         int maxlev = 1;
         for (int l = 0; l < t.nlevels; ++l) {
             const int np_l = I->merge_start[l + 1] - I->merge_start[l];
-            if (np_l < 148) maxlev = std::max(maxlev, np_l);  // levels the four-way merge takes
+            if (np_l < pw->nsm) maxlev = std::max(maxlev, np_l);  // levels the four-way merge takes
         }
         if ((r = pw_alloc(pw, &p, size_t(maxlev) * 4 * I->dims.np * ts))) return r;
         I->d_part3 = p;
@@ -2308,7 +2308,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                     case 32: launch_p(k_merge2d_p<T, 32>, 10 * 32 * 32, lst, Q); break;
                     default: k_merge2d<T><<<e - b, 256, sm_m2, s>>>(lst, Q, S, pd);
                 }
-            } else if ((pd.p == 16 || pd.p == 24) && e - b < 148) {
+            } else if ((pd.p == 16 || pd.p == 24) && e - b < pw->nsm) {
                 // a level with fewer parents than SMs: four blocks per parent (k_merge3d_q);
                 // larger levels keep one block per parent, which issues fewer shared loads
                 auto m3 = [&](auto kern, int P) {

@@ -126,18 +126,22 @@ def test_plan_create_rejects_bad_arguments():
     L2 = np.ascontiguousarray(np.array([[1.0, 0.3], [0.0, 0.9]]).T)  # column-major
     ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     out = ctypes.c_void_p(1234)
-    assert lib.pdmk_plan_create(4, ptr(L2), ctypes.c_double(1e-6), None, ctypes.byref(out)) == -1
-    assert lib.pdmk_plan_create(2, None, ctypes.c_double(1e-6), None, ctypes.byref(out)) == -1
-    out = ctypes.c_void_p(1234)
-    assert lib.pdmk_plan_create(2, ptr(L2), ctypes.c_double(1e-13), None, ctypes.byref(out)) == -4
-    assert not out.value
-    assert lib.pdmk_plan_create(2, ptr(L2), ctypes.c_double(0.5), None, ctypes.byref(out)) == -4
+
+    def rejected(code, *args):
+        out.value = 1234  # a non-NULL sentinel before every call
+        assert lib.pdmk_plan_create(*args, ctypes.byref(out)) == code
+        assert not out.value
+
+    rejected(-1, 4, ptr(L2), ctypes.c_double(1e-6), None)
+    rejected(-1, 2, None, ctypes.c_double(1e-6), None)
+    rejected(-4, 2, ptr(L2), ctypes.c_double(1e-13), None)
+    rejected(-4, 2, ptr(L2), ctypes.c_double(0.5), None)
     bad = L2.copy()
     bad[1] = np.nan
-    assert lib.pdmk_plan_create(2, ptr(bad), ctypes.c_double(1e-6), None, ctypes.byref(out)) == -5
+    rejected(-5, 2, ptr(bad), ctypes.c_double(1e-6), None)
     o = P.Opts()
     lib.pdmk_default_opts(ctypes.byref(o))
     o.precision = 7
-    assert lib.pdmk_plan_create(2, ptr(L2), ctypes.c_double(1e-6), ctypes.byref(o), ctypes.byref(out)) == -1
+    rejected(-1, 2, ptr(L2), ctypes.c_double(1e-6), ctypes.byref(o))
     with pytest.raises(P.PdmkError):
         P.Plan(np.eye(2), 1e-13)
