@@ -1,20 +1,28 @@
-"""Benchmark: periodic potential + gradient throughput on the 2D oblique clustered workload.
+"""Benchmark: periodic potential + gradient throughput, mixed precision against FP64.
 
-Workload: oblique cell a1 = (1, 0), a2 = (0.45, 0.85), N = 200,000 sources in 16 Gaussian
-clusters (sigma log-uniform in [1e-4, 1e-2] of the cell), balanced +/-1 charges, eps = 1e-6,
-evaluation at every source (self term excluded).  One step = one full evaluation
-(far field: spread, FFT, scale, inverse FFT, interpolate; near field: plane-wave passes and
+Headline workload (the largest single-GPU configuration): 3D triclinic cell
+a1 = (1, 0, 0), a2 = (0.3, 2, 0), a3 = (0.5, 0.7, 17) (longest edge ~17x the shortest),
+N = 4,000,000 sources in 64 anisotropic Gaussian clusters (sigma 1e-4..1e-2 of the cell per
+fractional axis, randomly rotated, wrapped), q ~ U(-1, 1) minus the mean, eps = 1e-6,
+evaluation at every source (self term excluded).  One step = one full evaluation (far
+field: spread, FFT, scale, inverse FFT, interpolate; near field: the plane-wave passes and
 the residual direct sum; assembly) with the sources already set.
 
+The line also carries: the same cell in FP64 (`fp64`), the end-to-end figure through the C
+ABI with host buffers (`e2e`: positions and charges in, tree build, evaluation, potential and
+gradient out, every step), the accuracy against stored oracle values, per-stage roofline
+accounting, the oracle timed on the host cores (`cpu_baseline`), and secondary lines for
+the 2D oblique 200k cell and a batch of 3D cells.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank evaluates its own replica of the workload (independent cells: weak
-scaling, no collective on the data path); value = total points/s over ranks.
+                       [--workload triclinic3d_4m|oblique2d_200k]
+Under torchrun each rank evaluates its own replica (independent cells: weak scaling, no
+collective on the data path); value = total points/s over ranks.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -29,12 +37,21 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 EPS = 1e-6
-N_POINTS = 200_000
-WORKLOAD = "oblique2d_clusters: a1=(1,0) a2=(0.45,0.85), N=200000, 16 gaussian clusters sigma in [1e-4,1e-2], +/-1 charges"
 METRIC = "points/s (potential+force) at 1e-6 rel err"
 CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+WORKLOADS = {
+    "triclinic3d_4m": dict(
+        make=lambda: W.triclinic3d_clusters(4_000_000), golden="triclinic3d_4m",
+        desc="triclinic3d_clusters: a1=(1,0,0) a2=(0.3,2,0) a3=(0.5,0.7,17), N=4000000, 64 anisotropic "
+             "gaussian clusters sigma in [1e-4,1e-2] of the cell, q~U(-1,1) minus mean"),
+    "oblique2d_200k": dict(
+        make=lambda: W.oblique2d_clusters(200_000), golden=None,
+        desc="oblique2d_clusters: a1=(1,0) a2=(0.45,0.85), N=200000, 16 gaussian clusters sigma in "
+             "[1e-4,1e-2], +/-1 charges"),
+}
 
 
 def load_peaks():
@@ -102,10 +119,20 @@ def dist_env():
 
 
 def oracle_sample(g, idx, nthreads=None):
+    """The oracle (plain FP64 Ewald) at the sampled sources, one call: its reciprocal-space
+    structure factors run over every source, whatever the sample size."""
     from oracle import ewald as E
     t0 = time.perf_counter()
     pot, grad = E.ewald(g["L"], g["y"], g["q"], x=g["y"][idx], self_idx=idx, nthreads=nthreads)
     return pot, grad, time.perf_counter() - t0
+
+
+def golden_sample(name):
+    """Stored oracle values at seeded targets of a full-size workload (written by the oracle
+    alone, tests/golden/make_fullsize.py)."""
+    with open(os.path.join(ROOT, "tests", "golden", f"fullsize_{name}.json")) as f:
+        c = json.load(f)["cells"][0]
+    return np.asarray(c["idx"]), np.asarray(c["pot"]), np.asarray(c["grad"])
 
 
 def stage_flops(info, d, leaf_folded, out_folded):
@@ -116,56 +143,76 @@ def stage_flops(info, d, leaf_folded, out_folded):
       nearfield   per visited pair 5 (2D) / 7 (3D); per pair inside the support two
                   residual series of n_A, n_B terms (2 flops/term) + 16 (2D) / 22 (3D)
       pw_upward   per (out box, source) pair: the p^d moment outer product (2 flops each) and
-                  2 d p Chebyshev recurrence flops; per merge parent (generic path) 12 p^3 (2D)
-                  or 8 * 3 * 2 p^{d+1} (3D separable re-expansion)
+                  2 d p Chebyshev recurrence flops; per merge parent 12 p^3 (2D generic) or
+                  28 p^4 (3D: the eight children summed axis by axis, 14 p^4 multiply-adds)
       pw_out      per box (2D parity form): 2 (K+1) p^2 + 4 (K+1)^2 p; credited to pw_upward
-                  where the moments launch computes the outgoing waves itself
-      pw_translate_in per box (2D parity form): ~100 (K+1)^2 (nine phased colleagues, both
-                  k1 signs) + 4 (K+1)^2 p + 2 (K+1) p^2
-      pw_downward per parent 12 p^3 (2D) or 8 * 3 * 2 p^{d+1} (3D), plus the leaf evaluation
-                  (4 p^d per target) where the single-launch pass folds it in
-      pw_leaf_eval per target 4 p^d
+                  where the moments launch computes the outgoing waves itself;
+                  3D parity form: 2 (K+1) p^3 + 4 (K+1)^2 p^2 + 4 (K+1)^2 (2K+1) p
+      pw_translate_in per box (2D parity form): ~100 (K+1)^2 + 4 (K+1)^2 p + 2 (K+1) p^2;
+                  3D: 27 phased colleagues over the (K+1)(2K+1)^2 half-space modes (14 flops
+                  each) + the three transposed axis contractions
+      pw_downward per parent 12 p^3 (2D) or 32 p^4 (3D, four blocks of 4 p^4 multiply-adds
+                  per two children), plus the leaf evaluation (4 p^d per target) where the
+                  single-launch pass folds it in
+      pw_leaf_eval per target 2 (p^d + 3 p^{d-1} ... ) ~ 4 p^d (value and three derivatives)
     """
     w, p, K = info["window_w"], info["n_proxy"], info["n_pw"]
     n1 = 2 * K + 1
-    npw = (K + 1) * n1 ** (d - 1)
     nW = 15
-    n = info["n"]
+    n = info["n_targets"] or info["n"]
     out = {}
-    out["spread"] = n * (2 * w ** d + 2 * d * w * nW)
+    out["spread"] = info["n"] * (2 * w ** d + 2 * d * w * nW)
     out["interp"] = n * (4 * w ** d + 2 * d * w * 2 * nW)
     visit, inside = (5, 2 * (12 + 14) + 16) if d == 2 else (7, 2 * (13 + 14) + 22)
     out["nearfield"] = info["near_pairs"] * visit + info["near_pairs_in"] * inside
-    merge_unit = 12 * p ** 3 if d == 2 else 8 * 3 * 2 * p ** (d + 1)
+    merge_unit = 12 * p ** 3 if d == 2 else 28 * p ** 4
+    down_unit = 12 * p ** 3 if d == 2 else 32 * p ** 4
     out["pw_upward"] = info["pw_moment_sources"] * (2 * p ** d + 2 * d * p) + info["pw_merge_parents"] * merge_unit
     if d == 2:
         out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** 2 + 4 * (K + 1) ** 2 * p)
         out["pw_translate_in"] = info["n_pw_boxes_in"] * (100 * (K + 1) ** 2 + 4 * (K + 1) ** 2 * p
                                                           + 2 * (K + 1) * p ** 2)
     else:
-        out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** d + 8 * (K + 1) * n1 * p ** (d - 1) * (d - 1))
-        out["pw_translate_in"] = info["n_pw_boxes_in"] * (3 ** d * 14 * npw + 8 * (K + 1) * n1 * p ** (d - 1) * (d - 1)
-                                                          + 3 * (K + 1) * p ** d)
+        out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** 3 + 4 * (K + 1) ** 2 * p ** 2
+                                                  + 4 * (K + 1) ** 2 * n1 * p)
+        out["pw_translate_in"] = info["n_pw_boxes_in"] * (27 * 14 * (K + 1) * n1 * n1
+                                                          + 2 * (K + 1) * p ** 3 + 4 * (K + 1) ** 2 * p ** 2
+                                                          + 4 * (K + 1) ** 2 * n1 * p)
     if out_folded:
         out["pw_upward"] += out["pw_out"]
         out["pw_out"] = 0
     leaf = info["pw_eval_targets"] * 4 * p ** d
-    out["pw_downward"] = info["pw_down_parents"] * merge_unit + (leaf if leaf_folded else 0)
+    out["pw_downward"] = info["pw_down_parents"] * down_unit + (leaf if leaf_folded else 0)
     out["pw_leaf_eval"] = 0 if leaf_folded else leaf
     return out
 
 
-# DRAM bytes (read + write) per launch of each stage's main kernel on this workload, from
-# one `ncu --set full` capture of the kernel as it stands (profiles/ holds the summaries);
-# None where no capture of the current kernel exists
-STAGE_TRAFFIC = {"nearfield": 17922560, "pw_upward": 6190336, "pw_downward": 13728768}
+# DRAM bytes (read + write) per launch of each stage's main kernel, per workload, from one
+# `ncu` capture of the kernel as it stands (profiles/ holds the summaries); absent where no
+# capture of the current kernel exists
+STAGE_TRAFFIC = {
+    "oblique2d_200k": {"nearfield": 17922560, "pw_upward": 6190336, "pw_downward": 13728768},
+    "triclinic3d_4m": {},
+}
 
 STAGE_KERNELS = {
-    "spread": "k_spread_halo + k_fold_whole", "interp": "k_interp_halo", "nearfield": "k_near_warp",
-    "pw_upward": "k_moments_direct2d (outgoing waves folded in)", "pw_out": "k_pw_out",
-    "pw_translate_in": "k_pw_in2d_p",
-    "pw_downward": "k_down_persist2d (leaf evaluation folded in)", "pw_leaf_eval": "k_leaf_eval",
+    2: {"spread": "k_spread_halo + k_fold_whole", "interp": "k_interp_halo", "nearfield": "k_near_warp",
+        "pw_upward": "k_moments_direct2d (outgoing waves folded in)", "pw_out": "k_pw_out",
+        "pw_translate_in": "k_pw_in2d_p",
+        "pw_downward": "k_down_persist2d (leaf evaluation folded in)", "pw_leaf_eval": "k_leaf_eval"},
+    3: {"spread": "k_spread + k_fold", "interp": "k_interp", "nearfield": "k_near_warp",
+        "pw_upward": "k_leaf_moments3d_p + k_merge3d_p / k_merge3d_q", "pw_out": "k_pw_out3d_p",
+        "pw_translate_in": "k_pw_in3d_p", "pw_downward": "k_down3d_q", "pw_leaf_eval": "k_leaf_eval3d_p"},
 }
+
+
+def fp32_peak_tflops(peaks):
+    """FP32 FMA pipe peak of this device: SMs x 128 lanes x 2 flops x the maximum SM clock
+    (no FP32 figure is measured; the SM count is the device's own)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    return nsm * 128 * 2 * sm_mhz * 1e6 / 1e12, nsm, sm_mhz
 
 
 def replica_summary(t_local, n, steps, ws, pg, device):
@@ -184,64 +231,129 @@ def replica_summary(t_local, n, steps, ws, pg, device):
 def batched_line(P, torch, stream, ncells=16, nmax=20_000, steps=20):
     """Batched cells (the 3D batched workload's shape, bounded to ncells cells of at most nmax
     sources so that the host tree builds stay short): points/s of one graph-replayed batch
-    evaluation with device outputs, timed with CUDA events."""
+    evaluation with device outputs, timed with CUDA events, mixed and FP64 on the same cells."""
     cells = W.batched_cells(ncells, nmax=nmax)
-    b = P.Batch([(c["L"], EPS) for c in cells], precision="mixed", stream=stream.cuda_stream)
-    t0 = time.perf_counter()
-    b.set_sources([c["y"] for c in cells], [c["q"] for c in cells])
-    t_set = time.perf_counter() - t0
-    ntot = sum(len(c["q"]) for c in cells)
-    bp = torch.empty(ntot, dtype=torch.float64, device="cuda")
-    bg = torch.empty(3 * ntot, dtype=torch.float64, device="cuda")
-    for _ in range(3):
-        b.eval_device(bp, bg)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        b.eval_device(bp, bg)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    b.close()
-    return {"cells": ncells, "points": ntot, "value": ntot / (ms * 1e-3), "unit": "points/s", "ms_per_eval": ms,
-            "t_set_sources_s": t_set, "workload": f"batched_cells({ncells}, nmax={nmax}): 3D triclinic, edges U(1,4), "
-                                                  "angles U(60,120), uniform or 4-cluster, +/-1 charges, eps 1e-6, mixed"}
+    out = {"cells": ncells, "workload": f"batched_cells({ncells}, nmax={nmax}): 3D triclinic, edges U(1,4), "
+                                        "angles U(60,120), uniform or 4-cluster, +/-1 charges, eps 1e-6"}
+    for prec in ("mixed", "fp64"):
+        b = P.Batch([(c["L"], EPS) for c in cells], precision=prec, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        b.set_sources([c["y"] for c in cells], [c["q"] for c in cells])
+        t_set = time.perf_counter() - t0
+        ntot = sum(len(c["q"]) for c in cells)
+        bp = torch.empty(ntot, dtype=torch.float64, device="cuda")
+        bg = torch.empty(3 * ntot, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            b.eval_device(bp, bg)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ns = steps if prec == "mixed" else max(3, steps // 4)
+        e0.record(stream)
+        for _ in range(ns):
+            b.eval_device(bp, bg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / ns
+        b.close()
+        out["points"] = ntot
+        out[prec] = {"value": ntot / (ms * 1e-3), "unit": "points/s", "ms_per_eval": ms, "t_set_sources_s": t_set}
+    out["value"] = out["mixed"]["value"]
+    out["unit"] = "points/s"
+    return out
 
 
 def run_reference(args, ws, rank):
-    """The oracle (plain FP64 Ewald on the host cores) on a bounded sample of targets."""
+    """The oracle (plain FP64 Ewald on the host cores) on the headline workload.  A step is a
+    sample of `per_step` targets; each oracle call pays the reciprocal-space structure factors
+    over all N sources once, so the warm-up steps run as one call and the K timed steps as one
+    call over their K samples (a bounded run: two calls)."""
     if rank != 0:
         return
-    g = W.oblique2d_clusters(N_POINTS)
+    wl = WORKLOADS[args.workload]
+    g = wl["make"]()
+    n = len(g["q"])
     rng = np.random.default_rng(7)
-    nsamp = 64
-    times = []
+    per_step = 2 if n > 1_000_000 else 16
     ncores = os.cpu_count() or 1
-    for k in range(args.warmup + args.steps):
-        idx = np.sort(rng.choice(N_POINTS, nsamp, replace=False))
-        _, _, dt = oracle_sample(g, idx, nthreads=ncores)
-        if k >= args.warmup:
-            times.append(dt)
-    value = nsamp * len(times) / sum(times)
+    idx_w = np.sort(rng.choice(n, per_step * args.warmup, replace=False))
+    oracle_sample(g, idx_w, nthreads=ncores)
+    idx = np.sort(rng.choice(n, per_step * args.steps, replace=False))
+    _, _, dt = oracle_sample(g, idx, nthreads=ncores)
+    value = len(idx) / dt
+    sample = (f"{per_step} random targets per step, the {args.steps} timed steps in one oracle call "
+              f"(its full-N reciprocal sums paid once per call)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "eps": EPS},
-            "cpu_baseline": {"value": value, "unit": "points/s", "cores": ncores, "kind": "oracle",
-                             "sample": f"{nsamp} random targets per step, full-N structure factors"},
+            "data": "synthetic", "config": {"workload": wl["desc"], "eps": EPS},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": ncores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def timed_device(pl, pot, grad, stream, flush, steps, warmup):
+    """Seconds of `steps` device evaluations (CUDA events on the caller's stream around each,
+    L2 flushed by a 256 MB write before each, outside the events)."""
+    import torch
+    for _ in range(warmup):
+        pl.eval_device(pot, grad)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.eval_device(pot, grad)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / 1e3
+
+
+def stage_profile(P, g, prec, stream, pot, grad, flush, nprof=3):
+    """Per-stage device times (CUDA events between the stages, which then run one after
+    another on one stream) and the plan's work counts."""
+    import torch
+    pl = P.Plan(g["L"], EPS, precision=prec, profile=True, stream=stream.cuda_stream)
+    pl.set_sources(g["y"], g["q"])
+    pl.eval_device(pot, grad)  # counts the pairs inside the support
+    torch.cuda.synchronize()
+    acc = {}
+    for _ in range(nprof):
+        flush.fill_(1.0)
+        pl.eval_device(pot, grad)
+        torch.cuda.synchronize()
+        for k, v in pl.stage_times().items():
+            acc[k] = acc.get(k, 0.0) + v / nprof
+    info = pl.info()
+    pl.close()
+    return acc, info
+
+
+def stage_roofline(acc, info, d, peak):
+    leaf_folded = acc.get("pw_leaf_eval", 0.0) < 0.05 * acc.get("pw_downward", 0.0)
+    out_folded = acc.get("pw_out", 0.0) < 0.05 * acc.get("pw_upward", 0.0)
+    fl = stage_flops(info, d, leaf_folded, out_folded)
+    per = {}
+    for k, f in fl.items():
+        t = acc.get(k, 0.0) / 1e3
+        if t > 0:
+            per[k] = {"ms": round(1e3 * t, 4), "gflop": round(f / 1e9, 4), "tflops": round(f / t / 1e12, 4),
+                      "frac": round(f / t / 1e12 / peak, 5), "kernels": STAGE_KERNELS[d].get(k)}
+    return per
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="triclinic3d_4m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 2D and batched secondary lines")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the mixed plan, warm-up + steps evaluations, no other work")
     args = ap.parse_args()
@@ -262,13 +374,14 @@ def main():
         pg = dist
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    g = W.oblique2d_clusters(N_POINTS)
+    wl = WORKLOADS[args.workload]
+    g = wl["make"]()
     n, d = g["y"].shape
     peaks, peak_kind = load_peaks()
 
-    def make(prec, profile=False):
-        pl = P.Plan(g["L"], EPS, precision=prec, profile=profile, stream=stream.cuda_stream)
-        pl.set_sources(g["y"], g["q"])
+    def make(prec, gg=g):
+        pl = P.Plan(gg["L"], EPS, precision=prec, stream=stream.cuda_stream)
+        pl.set_sources(gg["y"], gg["q"])
         return pl
 
     pot = torch.empty(n, dtype=torch.float64, device=dev)
@@ -278,26 +391,12 @@ def main():
         for _ in range(args.warmup + args.steps):
             plan.eval_device(pot, grad)
         torch.cuda.synchronize()
-        print(json.dumps({"ncu_run": True, "evals": args.warmup + args.steps, "launches_per_eval": plan.info()["launches"]}))
+        print(json.dumps({"ncu_run": True, "evals": args.warmup + args.steps,
+                          "launches_per_eval": plan.info()["launches"]}))
         return
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    def timed(pl, steps, warmup):
-        for _ in range(warmup):
-            pl.eval_device(pot, grad)
-        torch.cuda.synchronize()
-        evs = []
-        for _ in range(steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pl.eval_device(pot, grad)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs) / 1e3  # seconds
-
+    # ---- headline: mixed precision, device outputs, graph-replayed evaluations ----
     t_set0 = time.perf_counter()
     plan = make("mixed")
     torch.cuda.synchronize()
@@ -308,112 +407,159 @@ def main():
         pg.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
-    t_total = timed(plan, args.steps, 0)
+    t_total = timed_device(plan, pot, grad, stream, flush, args.steps, 0)
     clocks = sampler.stop()
-    value, ms_per_step, t_max = replica_summary(t_total, n, args.steps, ws, pg, dev)
+    value, ms_per_step, _ = replica_summary(t_total, n, args.steps, ws, pg, dev)
     pot_m = pot.cpu().numpy().copy()
     grad_m = grad.cpu().numpy().copy()
     info = plan.info()
 
-    # FP64 comparator (same workload, fewer steps)
-    plan64 = make("fp64")
-    t64 = timed(plan64, max(2, args.steps // 4), 2)
-    pts64 = n * max(2, args.steps // 4) / t64
-    pot_64 = pot.cpu().numpy().copy()
-    del plan64
-
-    # per-stage device times (CUDA events on the plan's stream) for the roofline
-    pprof = make("mixed", profile=True)
-    pprof.eval_device(pot, grad)  # counts pairs inside the support
-    torch.cuda.synchronize()
-    stage_acc = {}
-    nprof = 5
-    for _ in range(nprof):
-        flush.fill_(1.0)
-        pprof.eval_device(pot, grad)
-        torch.cuda.synchronize()
-        for k, v in pprof.stage_times().items():
-            stage_acc[k] = stage_acc.get(k, 0.0) + v / nprof
-    pinfo = pprof.info()
-    del pprof
-
-    # end-to-end through the C ABI with host buffers: charges in, potential+gradient out
-    q_host = torch.from_numpy(g["q"]).pin_memory()
+    # ---- end to end through the C ABI with host buffers, every step: positions and charges
+    # in (page-locked), tree build and device layouts, evaluation, potential + gradient out
+    y_host = torch.from_numpy(np.ascontiguousarray(g["y"])).pin_memory().numpy()
+    q_host = torch.from_numpy(np.ascontiguousarray(g["q"])).pin_memory().numpy()
     pot_host = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
     grad_host = torch.empty((n, d), dtype=torch.float64).pin_memory().numpy()
-    reps = max(3, args.steps // 2)
-    plan.set_charges(q_host.numpy())
+    reps = 2
+    plan.set_sources(y_host, q_host)
+    plan.eval(out=(pot_host, grad_host))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        plan.set_sources(y_host, q_host)
+        plan.eval(out=(pot_host, grad_host))
+    e2e_t = (time.perf_counter() - t0) / reps
+    e2e = {"value": ws * n / e2e_t, "unit": "points/s", "h2d_bytes_per_step": 8 * n * (d + 1),
+           "d2h_bytes_per_step": 8 * n * (1 + d),
+           "per_step": "pdmk_set_sources (positions + charges from pinned host memory, tree build, device "
+                       "layouts) + pdmk_eval into pinned host arrays"}
+    # the same with fixed positions: charges in, potential + gradient out
+    reps_c = max(3, args.steps // 2)
+    plan.set_charges(q_host)
     plan.eval(out=(pot_host, grad_host))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(reps):
-        plan.set_charges(q_host.numpy())
+    for _ in range(reps_c):
+        plan.set_charges(q_host)
         plan.eval(out=(pot_host, grad_host))
-    e2e_t = (time.perf_counter() - t0) / reps
-    e2e = {"value": ws * n / e2e_t, "unit": "points/s", "h2d_bytes_per_step": 8 * n,
-           "d2h_bytes_per_step": 8 * n * (1 + d)}
+    e2e_c = (time.perf_counter() - t0) / reps_c
+    e2e_charges = {"value": ws * n / e2e_c, "unit": "points/s", "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": 8 * n * (1 + d),
+                   "per_step": "pdmk_set_charges from pinned host memory + pdmk_eval into pinned host arrays"}
+    plan.close()
+    del plan
+
+    # ---- FP64 comparator on the same workload ----
+    plan64 = make("fp64")
+    s64 = max(2, args.steps // 4)
+    t64 = timed_device(plan64, pot, grad, stream, flush, s64, 2)
+    pts64 = n * s64 / t64
+    pot_64 = pot.cpu().numpy().copy()
+    grad_64 = grad.cpu().numpy().copy()
+    plan64.close()
+    del plan64
+
+    # ---- per-stage device times for the roofline ----
+    stage_acc, pinfo = stage_profile(P, g, "mixed", stream, pot, grad, flush)
 
     out = None
     if rank == 0:
-        # accuracy against the oracle on sampled targets (full-N structure factors)
-        rng = np.random.default_rng(11)
-        idx = np.sort(rng.choice(n, 128, replace=False))
+        # accuracy against the oracle: stored values at seeded targets (full-size workloads), or
+        # a fresh oracle sample
         cpu_line = None
-        pref, gref, dt = oracle_sample(g, idx, nthreads=os.cpu_count())
-        e_pot = float(np.linalg.norm(pot_m[idx] - pref) / np.linalg.norm(pref))
-        e_grad = float(np.linalg.norm(grad_m[idx] - gref) / np.linalg.norm(gref))
-        e_pot64 = float(np.linalg.norm(pot_64[idx] - pref) / np.linalg.norm(pref))
+        if wl["golden"]:
+            idx, pref, gref = golden_sample(wl["golden"])
+            acc_sample = f"{len(idx)} seeded targets, stored oracle values (tests/golden/fullsize_{wl['golden']}.json)"
+        else:
+            rng = np.random.default_rng(11)
+            idx = np.sort(rng.choice(n, 128, replace=False))
+            pref, gref, _ = oracle_sample(g, idx, nthreads=os.cpu_count())
+            acc_sample = f"{len(idx)} random targets, oracle with full-N structure factors"
+        rel = lambda a, b: float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+        accuracy = {"E_pot_mixed": rel(pot_m[idx], pref), "E_grad_mixed": rel(grad_m[idx], gref),
+                    "E_pot_fp64": rel(pot_64[idx], pref), "E_grad_fp64": rel(grad_64[idx], gref),
+                    "sample": acc_sample}
         if not args.no_cpu_baseline:
-            cpu_line = {"value": len(idx) / dt, "unit": "points/s", "cores": os.cpu_count(),
-                        "kind": "oracle",
-                        "sample": f"{len(idx)} random targets of the workload, full-N structure factors"}
-        # roofline: every timed stage is bound by the FP32 ALU pipes (tiny byte counts; the
-        # working set stays in L2); report each and pick the dominant one
-        sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-        fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
-        # the single-launch downward pass evaluates the leaves itself (its leaf stage is empty)
-        leaf_folded = stage_acc.get("pw_leaf_eval", 0.0) < 0.05 * stage_acc.get("pw_downward", 0.0)
-        # likewise the moments launch computes the outgoing waves (its outgoing stage is empty)
-        out_folded = stage_acc.get("pw_out", 0.0) < 0.05 * stage_acc.get("pw_upward", 0.0)
-        fl = stage_flops(pinfo, d, leaf_folded, out_folded)
-        stages = {k: round(v, 4) for k, v in stage_acc.items()}
-        per_stage = {}
-        for k, f in fl.items():
-            t = stage_acc.get(k, 0.0) / 1e3
-            if t > 0:
-                per_stage[k] = {"ms": round(1e3 * t, 4), "gflop": round(f / 1e9, 4),
-                                "tflops": round(f / t / 1e12, 4), "frac": round(f / t / 1e12 / fp32_peak, 5),
-                                "kernels": STAGE_KERNELS.get(k)}
+            rng = np.random.default_rng(12)
+            ns = 16 if n > 1_000_000 else 128
+            cidx = np.sort(rng.choice(n, ns, replace=False))
+            _, _, dt = oracle_sample(g, cidx, nthreads=os.cpu_count())
+            cpu_line = {"value": ns / dt, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                        "sample": f"{ns} random targets of the workload in one oracle call, including its "
+                                  f"full-N reciprocal-space structure factors ({dt:.1f} s)"}
+        fp32_peak, nsm, sm_mhz = fp32_peak_tflops(peaks)
+        per_stage = stage_roofline(stage_acc, pinfo, d, fp32_peak)
         dominant = max(per_stage, key=lambda k: per_stage[k]["ms"]) if per_stage else None
         achieved = per_stage[dominant]["tflops"] if dominant else None
         out = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "eps": EPS, "precision": "mixed", "l2": "flushed (256 MB write) between steps",
+            "config": {"workload": wl["desc"], "eps": EPS, "precision": "mixed",
+                       "l2": "flushed (256 MB write) between steps; inputs also exceed L2",
                        "depth": info["depth"], "n_images": info["n_images"], "M": info["M"][:d],
-                       "near_pairs": pinfo["near_pairs"], "near_pairs_in": pinfo["near_pairs_in"]},
-            "accuracy": {"E_pot_mixed": e_pot, "E_grad_mixed": e_grad, "E_pot_fp64": e_pot64,
-                         "sample": len(idx)},
-            "fp64": {"value": pts64, "unit": "points/s"},
-            "stages_ms": stages, "dominant_stage": dominant, "stage_roofline": per_stage,
+                       "near_pairs": pinfo["near_pairs"], "near_pairs_in": pinfo["near_pairs_in"],
+                       "n_proxy": info["n_proxy"], "n_pw": info["n_pw"], "n_s": info["n_s"],
+                       "kappa": info["kappa"], "device_bytes": info["device_bytes"]},
+            "accuracy": accuracy,
+            "fp64": {"value": pts64, "unit": "points/s", "ms_per_eval": 1e3 * t64 / s64,
+                     "mixed_over_fp64": value / (ws * pts64)},
+            "stages_ms": {k: round(v, 4) for k, v in stage_acc.items()}, "dominant_stage": dominant,
+            "stage_roofline": per_stage,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": (achieved / fp32_peak) if achieved else None,
-                         "traffic": STAGE_TRAFFIC.get(dominant),
-                         "kernel": STAGE_KERNELS.get(dominant), "stage": dominant,
-                         "peak_note": f"FP32 FMA pipes: 148 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
-                                      "(recipe unit counts at the maximum clock; no measured FP32 peak exists)"},
-            "cpu_baseline": cpu_line, "e2e": e2e,
-            "gpu_launches": None, "clocks": clocks,
+                         "traffic": STAGE_TRAFFIC.get(args.workload, {}).get(dominant),
+                         "kernel": STAGE_KERNELS[d].get(dominant), "stage": dominant,
+                         "peak_note": f"FP32 FMA pipes: {nsm} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                                      "(unit counts at the maximum clock; no measured FP32 peak exists)"},
+            "cpu_baseline": cpu_line, "e2e": e2e, "e2e_fixed_positions": e2e_charges,
+            "t_set_sources_s": t_set_sources,
+            "gpu_launches": int(info["launches"]) * args.steps, "clocks": clocks,
         }
-        out["t_set_sources_s"] = t_set_sources
-        out["batched"] = batched_line(P, torch, stream)
-        out["gpu_launches"] = int(info["launches"]) * args.steps
         out["config"]["launches_per_step"] = int(info["launches"])
+        if not args.no_secondary:
+            out["secondary"] = secondary_lines(P, torch, stream, flush, args, peaks)
         print(json.dumps(out))
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def secondary_lines(P, torch, stream, flush, args, peaks):
+    """The 2D oblique 200k cell (mixed and FP64, accuracy on 128 oracle targets) and a bounded
+    batch of 3D cells."""
+    out = {}
+    if args.workload != "oblique2d_200k":
+        g = WORKLOADS["oblique2d_200k"]["make"]()
+        n, d = g["y"].shape
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        grad = torch.empty((n, d), dtype=torch.float64, device="cuda")
+        line = {"workload": WORKLOADS["oblique2d_200k"]["desc"]}
+        res = {}
+        for prec in ("mixed", "fp64"):
+            pl = P.Plan(g["L"], EPS, precision=prec, stream=stream.cuda_stream)
+            t0 = time.perf_counter()
+            pl.set_sources(g["y"], g["q"])
+            torch.cuda.synchronize()
+            t_set = time.perf_counter() - t0
+            steps = args.steps if prec == "mixed" else max(2, args.steps // 4)
+            t = timed_device(pl, pot, grad, stream, flush, steps, 3)
+            res[prec] = (pot.cpu().numpy().copy(), grad.cpu().numpy().copy())
+            line[prec] = {"value": n * steps / t, "unit": "points/s", "ms_per_eval": 1e3 * t / steps,
+                          "t_set_sources_s": t_set}
+            pl.close()
+        rng = np.random.default_rng(11)
+        idx = np.sort(rng.choice(n, 128, replace=False))
+        pref, gref, _ = oracle_sample(g, idx, nthreads=os.cpu_count())
+        rel = lambda a, b: float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+        line["accuracy"] = {f"E_pot_{p}": rel(res[p][0][idx], pref) for p in res}
+        line["accuracy"].update({f"E_grad_{p}": rel(res[p][1][idx], gref) for p in res})
+        acc, pinfo = stage_profile(P, g, "mixed", stream, pot, grad, flush)
+        fp32_peak, _, _ = fp32_peak_tflops(peaks)
+        line["stages_ms"] = {k: round(v, 4) for k, v in acc.items()}
+        line["stage_roofline"] = stage_roofline(acc, pinfo, d, fp32_peak)
+        out["oblique2d_200k"] = line
+    out["batched"] = batched_line(P, torch, stream)
+    return out
 
 
 if __name__ == "__main__":
