@@ -228,13 +228,22 @@ def replica_summary(t_local, n, steps, ws, pg, device):
     return ws * n * steps / t_max, 1e3 * t_max / steps, t_max
 
 
-def batched_line(P, torch, stream, ncells=16, nmax=20_000, steps=20):
+def batched_line(P, torch, stream, ncells=16, nmax=20_000, steps=20, ws=1, rank=0, pg=None):
     """Batched cells (the 3D batched workload's shape, bounded to ncells cells of at most nmax
     sources so that the host tree builds stay short): points/s of one graph-replayed batch
-    evaluation with device outputs, timed with CUDA events, mixed and FP64 on the same cells."""
-    cells = W.batched_cells(ncells, nmax=nmax)
+    evaluation with device outputs, timed with CUDA events, mixed and FP64 on the same cells.
+    With several ranks the cells are split by estimated work (pdmk_partition_cells, the same
+    partition computed on every rank, no exchange); the value is all ranks' points over the
+    slowest rank's time."""
+    all_cells = W.batched_cells(ncells, nmax=nmax)
+    work = [P.cell_work(c["L"], EPS, len(c["q"])) for c in all_cells]
+    owner = P.partition_cells(work, ws)
+    cells = [c for c, r in zip(all_cells, owner) if r == rank]
     out = {"cells": ncells, "workload": f"batched_cells({ncells}, nmax={nmax}): 3D triclinic, edges U(1,4), "
-                                        "angles U(60,120), uniform or 4-cluster, +/-1 charges, eps 1e-6"}
+                                        "angles U(60,120), uniform or 4-cluster, +/-1 charges, eps 1e-6",
+           "partition": "cells split over ranks by estimated work" if ws > 1 else "one rank"}
+    if not cells:
+        return out
     for prec in ("mixed", "fp64"):
         b = P.Batch([(c["L"], EPS) for c in cells], precision=prec, stream=stream.cuda_stream)
         t0 = time.perf_counter()
@@ -256,8 +265,14 @@ def batched_line(P, torch, stream, ncells=16, nmax=20_000, steps=20):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / ns
         b.close()
-        out["points"] = ntot
-        out[prec] = {"value": ntot / (ms * 1e-3), "unit": "points/s", "ms_per_eval": ms, "t_set_sources_s": t_set}
+        tot = float(ntot)
+        if pg is not None and ws > 1:
+            tt = torch.tensor([ms, tot], device="cuda", dtype=torch.float64)
+            pg.all_reduce(tt[:1], op=pg.ReduceOp.MAX)
+            pg.all_reduce(tt[1:], op=pg.ReduceOp.SUM)
+            ms, tot = float(tt[0].item()), float(tt[1].item())
+        out["points"] = int(tot)
+        out[prec] = {"value": tot / (ms * 1e-3), "unit": "points/s", "ms_per_eval": ms, "t_set_sources_s": t_set}
     out["value"] = out["mixed"]["value"]
     out["unit"] = "points/s"
     return out
@@ -518,6 +533,12 @@ def main():
         out["config"]["launches_per_step"] = int(info["launches"])
         if not args.no_secondary:
             out["secondary"] = secondary_lines(P, torch, stream, flush, args, peaks)
+    if not args.no_secondary:
+        # every rank takes part in the batched line (its share of the cells)
+        bl = batched_line(P, torch, stream, ws=ws, rank=rank, pg=pg)
+        if out is not None:
+            out.setdefault("secondary", {})["batched"] = bl
+    if out is not None:
         print(json.dumps(out))
     if pg:
         pg.barrier()
@@ -558,7 +579,6 @@ def secondary_lines(P, torch, stream, flush, args, peaks):
         line["stages_ms"] = {k: round(v, 4) for k, v in acc.items()}
         line["stage_roofline"] = stage_roofline(acc, pinfo, d, fp32_peak)
         out["oblique2d_200k"] = line
-    out["batched"] = batched_line(P, torch, stream)
     return out
 
 

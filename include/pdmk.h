@@ -221,6 +221,23 @@ int pdmk_batch_eval(pdmk_batch batch, double* pot, double* grad, int where);
 pdmk_plan pdmk_batch_plan(pdmk_batch batch, int cell);
 void pdmk_batch_destroy(pdmk_batch batch);
 
+/*
+ * Multi-GPU runs over independent cells.  The cells of a batch share nothing, so ranks split
+ * them and exchange nothing on the data path.  The paper has no counterpart (its runs use one
+ * CPU thread); the estimate follows the cost of Algorithm 1's steps.  Host only; neither call
+ * touches a GPU.
+ * pdmk_cell_work: estimated flops of one evaluation of a cell of n sources with lattice L
+ *   (d x d column-major), precision eps and options opts (NULL: defaults), from the plan's
+ *   parameters alone (no tree): n (10 3^d n_s + 4 p^d + 6 w^d) + 10 prod(M) log2 prod(M).
+ *   Errors: BAD_ARG, BAD_EPS, NONFINITE, SINGULAR_LATTICE.
+ * pdmk_partition_cells: assigns each of ncells cells (work[c] >= 0) to one of nranks ranks,
+ *   rank_of_cell[c] in [0, nranks): cells by decreasing work (ties by index) each go to the
+ *   least-loaded rank (ties to the lowest).  Deterministic: every rank computes the same
+ *   partition locally.  Errors: BAD_ARG.
+ */
+int pdmk_cell_work(int d, const double* L, double eps, const pdmk_opts* opts, int64_t n, double* work);
+int pdmk_partition_cells(int ncells, const double* work, int nranks, int* rank_of_cell);
+
 /* Per-stage device times (ms) of the last pdmk_eval when opts.profile = 1.  names/ms
  * receive up to cap entries; returns the number of stages (or a negative error).     */
 int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, int cap);

@@ -93,6 +93,11 @@ def lib():
         L.pdmk_plan_destroy.restype = None
         L.pdmk_strerror.argtypes = [ctypes.c_int]
         L.pdmk_strerror.restype = ctypes.c_char_p
+        L.pdmk_cell_work.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Opts), ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_double)]
+        L.pdmk_cell_work.restype = ctypes.c_int
+        L.pdmk_partition_cells.argtypes = [ctypes.c_int, P, ctypes.c_int, P]
+        L.pdmk_partition_cells.restype = ctypes.c_int
         L.pdmk_kernel_table_eval.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_double)]
         L.pdmk_kernel_table_eval.restype = ctypes.c_int
@@ -121,6 +126,27 @@ def kernel_table(d: int, eps: float, kind: int, x: float = 0.0) -> float:
     if rc != 0:
         raise PdmkError(rc, "pdmk_kernel_table_eval")
     return v.value
+
+
+def cell_work(L, eps: float, n: int) -> float:
+    """Estimated flops of one evaluation of a cell (pdmk_cell_work; host only)."""
+    L = np.ascontiguousarray(np.asarray(L, dtype=np.float64))
+    Lc = np.ascontiguousarray(L.T)
+    v = ctypes.c_double()
+    rc = lib().pdmk_cell_work(L.shape[0], Lc.ctypes.data, float(eps), None, int(n), ctypes.byref(v))
+    if rc != 0:
+        raise PdmkError(rc, "pdmk_cell_work")
+    return v.value
+
+
+def partition_cells(work, nranks: int):
+    """Rank of every cell (pdmk_partition_cells: decreasing work to the least-loaded rank)."""
+    w = np.ascontiguousarray(np.asarray(work, dtype=np.float64))
+    out = np.empty(len(w), dtype=np.int32)
+    rc = lib().pdmk_partition_cells(len(w), w.ctypes.data, int(nranks), out.ctypes.data)
+    if rc != 0:
+        raise PdmkError(rc, "pdmk_partition_cells")
+    return out
 
 
 def _is_torch(x):

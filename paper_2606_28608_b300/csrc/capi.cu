@@ -68,6 +68,7 @@ struct pdmk_plan_s {
     std::vector<double> mW, mWd; // window F, dF as monomials in x = 2 s - 1
     bool far_halo = false;       // 2D FP32 halo-grid spreading / interpolation kernels
     bool far_warp3d = false;     // 3D warp-per-target interpolation
+    bool spread_reg3d = false;   // 3D spreading with the padded tile in registers (k_spread3d_reg)
     int B[3] = {1, 1, 1}, nbin[3] = {1, 1, 1}, P[3] = {1, 1, 1}, Ptot = 1;
     int whole_ctas = 0;  // > 0: 2D whole-grid spreading with this many CTAs (small grids)
     int64_t ncell = 1, nhalf = 1;
@@ -369,6 +370,69 @@ static std::vector<double> far_weights(pdmk_plan plan) {
     return wt;
 }
 
+// ---------------------------------------------------------------------------------------
+// Work estimate of one cell and the partition of independent cells over ranks (host only).
+// Cells of a batch share nothing, so the ranks of a multi-GPU run split the cells and
+// exchange nothing on the data path.  The estimate counts flops per source of the three
+// parts of an evaluation from the plan's parameters (no tree needed): near-field pairs
+// ~ 3^d n_s per target at ~10 flops each, the plane-wave moments and leaf evaluation 4 p^d,
+// spreading and interpolation 6 w^d, and the two transforms 10 prod(M) log2 prod(M).
+extern "C" int pdmk_cell_work(int d, const double* L, double eps, const pdmk_opts* opts, int64_t n, double* work) {
+    if (!L || !work || (d != 2 && d != 3) || n < 0) return PDMK_ERR_BAD_ARG;
+    if (!(eps >= 1e-12 && eps <= 1e-2)) return PDMK_ERR_BAD_EPS;
+    for (int i = 0; i < d * d; ++i)
+        if (!std::isfinite(L[i])) return PDMK_ERR_NONFINITE;
+    pdmk_opts o;
+    if (opts) o = *opts; else pdmk_default_opts(&o);
+    static std::mutex mu;
+    static std::map<double, double> ccache;  // bandwidth c per eps (a root search)
+    double c;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = ccache.find(eps);
+        if (it == ccache.end()) it = ccache.emplace(eps, pswf_calibrate(eps)).first;
+        c = it->second;
+    }
+    Geometry tmp, g;
+    int rc = make_geometry(d, L, 1.0, c, &tmp);
+    if (rc != PDMK_OK) return rc;
+    double kappa;
+    int ns;
+    table1_defaults(d, eps, &tmp, L, &kappa, &ns);
+    if (o.kappa > 0) kappa = o.kappa;
+    if (o.n_s > 0) ns = o.n_s;
+    rc = make_geometry(d, L, kappa, c, &g);
+    if (rc != PDMK_OK) return rc;
+    const int p = o.n_proxy > 0 ? o.n_proxy : ((int(std::ceil(c)) + 6 + 3) / 4) * 4;
+    const int w = o.window_w > 0 ? o.window_w : int(std::ceil(2.0 * c / kPi - 1e-9)) + 2;
+    double ncell = 1;
+    for (int i = 0; i < d; ++i) ncell *= g.M[i];
+    const double per_src = 10.0 * std::pow(3.0, d) * ns + 4.0 * std::pow(double(p), d) + 6.0 * std::pow(double(w), d);
+    *work = double(n) * per_src + 10.0 * ncell * std::log2(std::max(ncell, 2.0));
+    return PDMK_OK;
+}
+
+// Longest-processing-time assignment: cells in order of decreasing work (ties by index) go
+// to the rank with the least work so far (ties to the lowest rank).  Deterministic, so every
+// rank computes the same partition without communicating.
+extern "C" int pdmk_partition_cells(int ncells, const double* work, int nranks, int* rank_of_cell) {
+    if (ncells < 0 || nranks < 1 || (ncells > 0 && (!work || !rank_of_cell))) return PDMK_ERR_BAD_ARG;
+    for (int c = 0; c < ncells; ++c)
+        if (!std::isfinite(work[c]) || work[c] < 0) return PDMK_ERR_BAD_ARG;
+    std::vector<int> ord(static_cast<size_t>(ncells));
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<double> load(static_cast<size_t>(nranks), 0.0);
+    for (int c : ord) {
+        int best = 0;
+        for (int r = 1; r < nranks; ++r)
+            if (load[r] < load[best]) best = r;
+        rank_of_cell[c] = best;
+        load[best] += work[c];
+    }
+    return PDMK_OK;
+}
+
 extern "C" int pdmk_kernel_table_eval(int d, double eps, int kind, double x, double* value) {
     if ((d != 2 && d != 3) || !value) return PDMK_ERR_BAD_ARG;
     if (!(eps >= 1e-12 && eps <= 1e-2)) return PDMK_ERR_BAD_EPS;
@@ -527,6 +591,11 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
                 plan->g.M[i] = M;
             }
     size_bins(plan);
+    // register-tile 3D spreading: FP32 tiles, cubic 8-cell bins and a compiled window width
+    // (an FP64 tile of P^2 columns needs twice the registers and ran slower than the
+    // shared-memory kernel on B300's FP64 pipe: 73 against 65 ms on the 4M-point cell)
+    plan->spread_reg3d = d == 3 && mixed && plan->B[0] == 8 && plan->B[1] == 8 && plan->B[2] == 8 &&
+                         (plan->w == 8 || plan->w == 13 || plan->w == 17);
     // near-field coefficients
     plan->cA = plan->kt.A.coef;
     plan->cB = plan->kt.B.coef;
@@ -997,7 +1066,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     }
     // subproblems: chunks of at most max_pts points of one bin (one spreading block each; in
     // 3D the clustered bins hold most points, so smaller chunks give the grid enough blocks)
-    const int max_pts = d == 3 ? 128 : 512;
+    const int max_pts = plan->spread_reg3d ? 1024 : (d == 3 ? 128 : 512);
     std::vector<int4> subs;
     std::vector<int> bin_sub_begin(size_t(plan->nbins_tot) + 1, 0);
     {
@@ -1249,10 +1318,25 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         sa.half_w_inv2 = hwi2;
         sa.coefW = static_cast<const T*>(plan->d_coefW);
         sa.nW = int(plan->cW.size());
-        size_t smem = sizeof(T) * (size_t(plan->Ptot) + size_t(kSpreadChunk) * 3 * plan->w + kSpreadChunk) +
-                      sizeof(int) * kSpreadChunk * 3;
-        CK(cudaFuncSetAttribute(k_spread<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_spread<T, D><<<plan->nsub, kSpreadThreads, smem, s>>>(sa);
+        if (D == 3 && plan->spread_reg3d) {
+            auto reg = [&](auto kern, size_t smem, int nt) -> int {
+                CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+                kern<<<plan->nsub, nt, smem, s>>>(sa);
+                return PDMK_OK;
+            };
+            int rr = PDMK_ERR_INTERNAL;
+            if constexpr (sizeof(T) == 4) {
+                if (plan->w == 8) rr = reg(k_spread3d_reg<T, 8, 128, 4>, spread3d_reg_smem<T, 8, 128>(), 128);
+                else if (plan->w == 13) rr = reg(k_spread3d_reg<T, 13, 128, 3>, spread3d_reg_smem<T, 13, 128>(), 128);
+                else rr = reg(k_spread3d_reg<T, 17, 128, 2>, spread3d_reg_smem<T, 17, 128>(), 128);
+            }
+            if (rr != PDMK_OK) return rr;
+        } else {
+            size_t smem = sizeof(T) * (size_t(plan->Ptot) + size_t(kSpreadChunk) * 3 * plan->w + kSpreadChunk) +
+                          sizeof(int) * kSpreadChunk * 3;
+            CK(cudaFuncSetAttribute(k_spread<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            k_spread<T, D><<<plan->nsub, kSpreadThreads, smem, s>>>(sa);
+        }
         ++plan->launches;
         CK(cudaGetLastError());
     }

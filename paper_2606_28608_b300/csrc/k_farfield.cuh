@@ -131,6 +131,98 @@ k_spread(SpreadArgs<T> a) {
     for (int i = tid; i < a.Ptot; i += kSpreadThreads) out[i] = tile[i];
 }
 
+// 3D spreading with the padded tile in registers (cubic tiles, P = B + W - 1 per dimension,
+// compile-time W).  Thread t owns the tile columns (X, Y) = (c % P, c / P) for c = t + NT k
+// and keeps their P cells along Z in registers.  Per point the host-computed window offset
+// places the w window values of each axis inside a zero-padded row of P values (shared
+// memory), and every thread adds  q wx[X] wy[Y] wz[Z]  to its cells: P FMAs per owned column,
+// skipped where the column lies outside the point's footprint.  A cell is only ever updated by
+// its owner, in point order (deterministic, no atomics).  Clustered bins put hundreds of
+// thousands of points into a few tiles; with the tile in registers a CTA takes subproblems
+// of up to a thousand points, so the fold adds far fewer slabs per grid cell.
+// dynamic shared memory: windows [NT][3][PR] | q [NT]
+template <typename T, int W, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+k_spread3d_reg(SpreadArgs<T> a) {
+    constexpr int P = 8 + W - 1;                 // B = 8 per dimension
+    constexpr int PP = P * P;
+    constexpr int NCOL = (PP + NT - 1) / NT;     // columns per thread
+    constexpr int PR = (P * int(sizeof(T)) % 16 == 0) ? P : ((P * int(sizeof(T)) + 15) / 16) * 16 / int(sizeof(T));
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T cw[kMaxCheb];
+    T* win = reinterpret_cast<T*>(smem_raw);     // [NT][3][PR]
+    T* qv = win + NT * 3 * PR;                   // [NT]
+    const int tid = threadIdx.x;
+    if (tid < a.nW) cw[tid] = a.coefW[tid];
+    const int4 sp = a.sub[blockIdx.x];
+    const int begin = sp.y, count = sp.z;
+    int colx[NCOL], coly[NCOL];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+        const int col = tid + c * NT;
+        colx[c] = col < PP ? col % P : 0;
+        coly[c] = col < PP ? col / P : -1;       // -1: no column (past the tile)
+    }
+    T acc[NCOL][P];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+        for (int z = 0; z < P; ++z) acc[c][z] = T(0);
+    __syncthreads();
+    for (int c0 = 0; c0 < count; c0 += NT) {
+        const int np = min(NT, count - c0);
+        if (tid < np) {
+            const int pi = begin + c0 + tid;
+            const int4 g = a.pt_g0[pi];           // window start inside the tile, [0, B) per axis
+            const T* dq = a.pt_dq + size_t(pi) * 4;
+            const int ko[3] = {g.x, g.y, g.z};
+            T* row = win + tid * 3 * PR;
+            for (int k = 0; k < 3; ++k) {
+                const T del = dq[k];             // M u - g0 (first node's distance), grid units
+                T* r = row + k * PR;
+                for (int x = 0; x < P; ++x) {
+                    const int j = x - ko[k];
+                    r[x] = (j >= 0 && j < W) ? pswf_window(del - T(j), a.half_w_inv2, cw, a.nW) : T(0);
+                }
+            }
+            qv[tid] = dq[3];
+        }
+        __syncthreads();
+        for (int p = 0; p < np; ++p) {
+            const T* row = win + p * 3 * PR;
+            const T q = qv[p];
+            T wz[P];
+#pragma unroll
+            for (int z = 0; z < P; ++z) wz[z] = row[2 * PR + z];
+#pragma unroll
+            for (int c = 0; c < NCOL; ++c) {
+                if (coly[c] < 0) continue;
+                const T wxy = q * row[colx[c]] * row[PR + coly[c]];
+                if (wxy != T(0)) {
+#pragma unroll
+                    for (int z = 0; z < P; ++z) acc[c][z] = fma(wxy, wz[z], acc[c][z]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    T* out = a.slab + size_t(blockIdx.x) * (PP * P);
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+        if (coly[c] < 0) continue;
+        const int col = tid + c * NT;
+#pragma unroll
+        for (int z = 0; z < P; ++z) out[z * PP + col] = acc[c][z];
+    }
+}
+
+template <typename T, int W, int NT>
+constexpr size_t spread3d_reg_smem() {
+    constexpr int P = 8 + W - 1;
+    constexpr int PR = (P * int(sizeof(T)) % 16 == 0) ? P : ((P * int(sizeof(T)) + 15) / 16) * 16 / int(sizeof(T));
+    return sizeof(T) * (size_t(NT) * 3 * PR + NT);
+}
+
 // Small 2D grids: every warp keeps a private copy of the whole periodic grid in shared memory
 // and spreads its own contiguous run of points into it (lanes over the w x w footprint, one
 // point at a time: no two lanes touch one cell, every cell is updated in point order).  The

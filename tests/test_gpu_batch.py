@@ -62,3 +62,27 @@ def test_batch_against_oracle():
         assert np.linalg.norm(pots[c] - pref) <= 1e-6 * np.linalg.norm(pref)
         assert np.linalg.norm(grads[c] - gref) <= 1e-5 * np.linalg.norm(gref)
     b.close()
+
+
+def test_rank_shares_equal_the_whole_batch():
+    """Cells split over two ranks by estimated work (pdmk_partition_cells): each rank's batch of
+    its own cells gives, cell for cell, the single-process batch's results bit for bit.  The
+    two ranks' batches run one after the other on this GPU (nothing is exchanged between
+    ranks, so running them in sequence is the multi-GPU run's arithmetic)."""
+    P, torch = _cuda()
+    cells = _cells()
+    work = [P.cell_work(g["L"], 1e-6, len(g["q"])) for g in cells]
+    owner = P.partition_cells(work, 2)
+    assert set(owner.tolist()) == {0, 1}
+    whole = P.Batch([(g["L"], 1e-6) for g in cells], precision="mixed")
+    whole.set_sources([g["y"] for g in cells], [g["q"] for g in cells])
+    wp, wg = whole.eval()
+    whole.close()
+    for r in (0, 1):
+        mine = [c for c in range(len(cells)) if owner[c] == r]
+        b = P.Batch([(cells[c]["L"], 1e-6) for c in mine], precision="mixed")
+        b.set_sources([cells[c]["y"] for c in mine], [cells[c]["q"] for c in mine])
+        pp, gg = b.eval()
+        b.close()
+        for k, c in enumerate(mine):
+            assert np.array_equal(pp[k], wp[c]) and np.array_equal(gg[k], wg[c])
