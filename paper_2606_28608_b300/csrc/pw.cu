@@ -157,6 +157,87 @@ __global__ void __launch_bounds__(P * P, 1) k_leaf_moments3d_p(const int4* __res
     for (int m0 = 0; m0 < P; ++m0) Qb[m0 * PP + tid] = acc[m0];
 }
 
+// 3D leaf moments as a small GEMM per leaf (the transpose of k_leaf_eval3d_gemm): one block of
+// 256 threads per leaf, sources taken 16 at a time.  For a chunk, X[s][m0] = T_m0(t0_s) and
+// B[s][m1 m2] = q_s T_m1(t1_s) T_m2(t2_s) are staged in shared memory (B formed by all threads,
+// two products per element), and
+//     Q[m0][m1 m2] += sum_s X[s][m0] B[s][m1 m2]          (P^3 multiply-adds per source)
+// with a register tile of P/4 rows x P^2/64 columns per thread (columns strided by 64).
+template <typename T, int P>
+constexpr size_t leaf_moments3d_gemm_smem() {
+    return sizeof(T) * (size_t(16) * P * P + size_t(16) * 3 * P + 16);
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_leaf_moments3d_gemm(const int4* __restrict__ leaves,
+                                                             const T* __restrict__ src4, T* __restrict__ Q,
+                                                             double inv_rc) {
+    constexpr int PP = P * P, RT = P / 4, CT = PP / 64, NS = 16;
+    static_assert(P % 4 == 0 && PP % 64 == 0, "tile split");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Bs = reinterpret_cast<T*>(smraw);  // [NS][PP]
+    T* Tb = Bs + NS * PP;                 // [NS][3][P]  T_m of the three axes
+    T* qv = Tb + NS * 3 * P;              // [NS]
+    const int tid = threadIdx.x, rg = tid >> 6, cg = tid & 63;
+    const int4 lf = leaves[blockIdx.x];   // (first source, count, q slot, level)
+    const T scale = T(2.0 * inv_rc * double(1LL << lf.w));  // t = 2 (y - c)/h
+    T acc[RT][CT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int k = 0; k < CT; ++k) acc[i][k] = T(0);
+    for (int s0 = 0; s0 < lf.y; s0 += NS) {
+        const int ns = min(NS, lf.y - s0);
+        __syncthreads();  // the previous chunk's B and tables are consumed
+        if (tid < 3 * NS) {
+            const int sidx = tid / 3, ax = tid - 3 * sidx;
+            T t = T(0), q = T(0);
+            if (sidx < ns) {
+                const T* y = src4 + size_t(lf.x + s0 + sidx) * 4;
+                t = y[ax] * scale;
+                q = y[3];
+            }
+            T* row = Tb + (sidx * 3 + ax) * P;
+            T tm1 = T(1), tm = t;
+            row[0] = T(1);
+            row[1] = t;
+#pragma unroll
+            for (int m = 2; m < P; ++m) {
+                const T tn = fma(T(2) * t, tm, -tm1);
+                row[m] = tn;
+                tm1 = tm;
+                tm = tn;
+            }
+            if (ax == 0) qv[sidx] = q;  // zero for absent sources: their B rows vanish
+        }
+        __syncthreads();
+        for (int e = tid; e < NS * PP; e += 256) {
+            const int sidx = e / PP, col = e - sidx * PP, m1 = col / P, m2 = col - m1 * P;
+            const T* tr = Tb + sidx * 3 * P;
+            Bs[e] = qv[sidx] * tr[P + m1] * tr[2 * P + m2];
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int sidx = 0; sidx < NS; ++sidx) {
+            T xr[RT];
+#pragma unroll
+            for (int i = 0; i < RT; ++i) xr[i] = Tb[sidx * 3 * P + rg * RT + i];
+            const T* brow = Bs + sidx * PP + cg;
+#pragma unroll
+            for (int k = 0; k < CT; ++k) {
+                const T b = brow[64 * k];
+#pragma unroll
+                for (int i = 0; i < RT; ++i) acc[i][k] = fma(xr[i], b, acc[i][k]);
+            }
+        }
+    }
+    T* Qb = Q + size_t(lf.z) * (PP * P);
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int k = 0; k < CT; ++k) Qb[(rg * RT + i) * PP + cg + 64 * k] = acc[i][k];
+}
+
 // ------------------------------------------------------------------ merge / downward
 // Re-expansion of one box's Chebyshev array into another's, one axis at a time (slices of
 // the first axis through shared memory).  mode 0 (merge): contract the child index m against
@@ -460,6 +541,207 @@ __global__ void __launch_bounds__(P * P) k_merge3d_q(const int* __restrict__ lis
         dst[k] = v;
     }
     if (tid == 0) done[ent] = 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// 3D re-expansions with register accumulators and the triangular shift matrices.
+// S_b[M][m] (coefficient of T_m in T_M((t -/+ 1)/2)) vanishes for m > M, so every axis
+// contraction below runs over the lower triangle only: 7 P^4 multiply-adds per parent in all
+// (the full separable form takes 14 P^4).  A thread owns one P x P slice position and keeps P
+// accumulators in registers; the contracted operand is one shared (or coalesced global) load
+// per P/2 multiply-adds on average, and the matrix rows are read as broadcast vectors.
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<float> { using V = float4; static constexpr int W = 4; };
+template <>
+struct VecOf<double> { using V = double2; static constexpr int W = 2; };
+
+// acc[m] += row[m] * x for m in [LO, HI]  (row 16-byte aligned; LO, HI compile-time after
+// unrolling)
+template <typename T, int P>
+__device__ __forceinline__ void tri_axpy(T (&acc)[P], const T* __restrict__ row, T x, int lo, int hi) {
+    using V = typename VecOf<T>::V;
+    constexpr int VW = VecOf<T>::W;
+#pragma unroll
+    for (int k = 0; k < P / VW; ++k) {
+        if (VW * k + VW - 1 < lo || VW * k > hi) continue;
+        const V v = reinterpret_cast<const V*>(row)[k];
+        const T* vv = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+            const int m = VW * k + j;
+            if (m >= lo && m <= hi) acc[m] = fma(vv[j], x, acc[m]);
+        }
+    }
+}
+
+// downward pass, two blocks per parent (one per first-axis child bit b0):
+//   V[m0][M1 M2]  = sum_{M0 >= m0} S_b0[M0][m0] a_P[M0][M1 M2]      thread (M1 M2)
+//   W[m0][m1 M2]  = sum_{M1 >= m1} S_b1[M1][m1] V[m0][M1 M2]        thread (m0 M2), per b1
+//   a_c[m0 m1][m2] += sum_{M2 >= m2} S_b2[M2][m2] W[m0 m1][M2]      thread (m0 m1), per b2
+template <typename T, int P>
+__global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list, T* __restrict__ Lc,
+                                                    const T* __restrict__ Sg) {
+    constexpr int PP = P * P, NP = PP * P;
+    using V = typename VecOf<T>::V;
+    constexpr int VW = VecOf<T>::W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Sm = reinterpret_cast<T*>(smraw);  // [2][P][P]  S[b][M][m]
+    T* Vs = Sm + 2 * PP;                  // [P][PP]
+    T* Ws = Vs + NP;                      // [P][PP]
+    const int tid = threadIdx.x, b0 = blockIdx.x & 1;
+    const int* e = list + size_t(blockIdx.x >> 1) * 9;
+    int ch[2][2];
+#pragma unroll
+    for (int b1 = 0; b1 < 2; ++b1)
+#pragma unroll
+        for (int b2 = 0; b2 < 2; ++b2) ch[b1][b2] = e[1 + (b0 | (b1 << 1) | (b2 << 2))];
+    if (ch[0][0] < 0 && ch[0][1] < 0 && ch[1][0] < 0 && ch[1][1] < 0) return;  // block-uniform
+    for (int k = tid; k < 2 * PP; k += PP) Sm[k] = Sg[k];
+    __syncthreads();
+    {
+        const T* aP = Lc + size_t(e[0]) * NP;
+        T v[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) v[m] = T(0);
+#pragma unroll
+        for (int M0 = 0; M0 < P; ++M0) tri_axpy<T, P>(v, Sm + (b0 * P + M0) * P, aP[M0 * PP + tid], 0, M0);
+#pragma unroll
+        for (int m0 = 0; m0 < P; ++m0) Vs[m0 * PP + tid] = v[m0];
+    }
+    __syncthreads();
+    const int i = tid / P, j = tid - (tid / P) * P;
+    for (int b1 = 0; b1 < 2; ++b1) {
+        if (ch[b1][0] < 0 && ch[b1][1] < 0) continue;  // block-uniform
+        {
+            // thread (m0 = i, M2 = j)
+            T w[P];
+#pragma unroll
+            for (int m = 0; m < P; ++m) w[m] = T(0);
+#pragma unroll
+            for (int M1 = 0; M1 < P; ++M1) tri_axpy<T, P>(w, Sm + (b1 * P + M1) * P, Vs[i * PP + M1 * P + j], 0, M1);
+#pragma unroll
+            for (int m1 = 0; m1 < P; ++m1) Ws[i * PP + m1 * P + j] = w[m1];
+        }
+        __syncthreads();
+        {
+            // thread (m0 m1) = tid: its W row over M2
+            T wr[P];
+#pragma unroll
+            for (int k = 0; k < P / VW; ++k) {
+                const V v = reinterpret_cast<const V*>(Ws + tid * P)[k];
+#pragma unroll
+                for (int jj = 0; jj < VW; ++jj) wr[VW * k + jj] = reinterpret_cast<const T*>(&v)[jj];
+            }
+#pragma unroll
+            for (int b2 = 0; b2 < 2; ++b2) {
+                const int c = ch[b1][b2];
+                if (c < 0) continue;
+                T o[P];
+#pragma unroll
+                for (int m = 0; m < P; ++m) o[m] = T(0);
+#pragma unroll
+                for (int M2 = 0; M2 < P; ++M2) tri_axpy<T, P>(o, Sm + (b2 * P + M2) * P, wr[M2], 0, M2);
+                V* dst = reinterpret_cast<V*>(Lc + size_t(c) * NP + size_t(tid) * P);
+#pragma unroll
+                for (int k = 0; k < P / VW; ++k) {
+                    V d = dst[k];
+                    T* dd = reinterpret_cast<T*>(&d);
+#pragma unroll
+                    for (int jj = 0; jj < VW; ++jj) dd[jj] += o[VW * k + jj];
+                    dst[k] = d;
+                }
+            }
+        }
+        __syncthreads();  // W is rewritten for the next b1
+    }
+}
+
+// upward merge, one block per parent, three P^3 buffers A, B, C in shared memory:
+//   U_{b0 b1}[m0 m1][M2] = sum_{b2} sum_{m2 <= M2} S_b2[M2][m2] Q_c[m0 m1][m2]   thread (m0 m1)
+//   V_{b0}[m0][M1 M2]    = sum_{b1} sum_{m1 <= M1} S_b1[M1][m1] U_{b0 b1}[m0][m1 M2]   thread (m0 M2)
+//   Q_P[M0][M1 M2]       = sum_{b0} sum_{m0 <= M0} S_b0[M0][m0] V_{b0}[m0][M1 M2]  thread (M1 M2)
+// V_{b0} overwrites U_{b0 0} in place (a thread rewrites exactly the (m0, M2) slice it read).
+// b0 = 0 uses buffers (A, B) and leaves V_0 in A; b0 = 1 uses (B, C) and leaves V_1 in B.
+template <typename T, int P>
+__global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ list, T* __restrict__ Q,
+                                                     const T* __restrict__ Sg) {
+    constexpr int PP = P * P, NP = PP * P;
+    using V = typename VecOf<T>::V;
+    constexpr int VW = VecOf<T>::W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* St = reinterpret_cast<T*>(smraw);  // [2][P][P]  St[b][m][M] = S_b[M][m]
+    T* buf = St + 2 * PP;                 // [3][NP]
+    const int tid = threadIdx.x, i = tid / P, j = tid - (tid / P) * P;
+    const int* e = list + size_t(blockIdx.x) * 9;
+    for (int k = tid; k < 2 * PP; k += PP) {
+        const int b = k / PP, M = (k / P) % P, m = k % P;
+        St[(b * P + m) * P + M] = Sg[k];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int b0 = 0; b0 < 2; ++b0) {
+        T* Ub[2] = {buf + size_t(b0) * NP, buf + size_t(b0 + 1) * NP};
+#pragma unroll 1
+        for (int b1 = 0; b1 < 2; ++b1) {
+            // thread (m0 m1) = tid
+            T u[P];
+#pragma unroll
+            for (int m = 0; m < P; ++m) u[m] = T(0);
+#pragma unroll 1
+            for (int b2 = 0; b2 < 2; ++b2) {
+                const int c = e[1 + (b0 | (b1 << 1) | (b2 << 2))];
+                if (c < 0) continue;
+                const V* qrow = reinterpret_cast<const V*>(Q + size_t(c) * NP + size_t(tid) * P);
+#pragma unroll
+                for (int k = 0; k < P / VW; ++k) {
+                    const V qv = __ldg(qrow + k);
+#pragma unroll
+                    for (int jj = 0; jj < VW; ++jj) {
+                        const int m2 = VW * k + jj;
+                        tri_axpy<T, P>(u, St + (b2 * P + m2) * P, reinterpret_cast<const T*>(&qv)[jj], m2, P - 1);
+                    }
+                }
+            }
+            V* ud = reinterpret_cast<V*>(Ub[b1] + size_t(tid) * P);
+#pragma unroll
+            for (int k = 0; k < P / VW; ++k) {
+                V v;
+#pragma unroll
+                for (int jj = 0; jj < VW; ++jj) reinterpret_cast<T*>(&v)[jj] = u[VW * k + jj];
+                ud[k] = v;
+            }
+        }
+        __syncthreads();
+        {
+            // thread (m0 = i, M2 = j)
+            T v[P];
+#pragma unroll
+            for (int m = 0; m < P; ++m) v[m] = T(0);
+#pragma unroll 1
+            for (int b1 = 0; b1 < 2; ++b1)
+#pragma unroll
+                for (int m1 = 0; m1 < P; ++m1)
+                    tri_axpy<T, P>(v, St + (b1 * P + m1) * P, Ub[b1][i * PP + m1 * P + j], m1, P - 1);
+#pragma unroll
+            for (int M1 = 0; M1 < P; ++M1) Ub[0][i * PP + M1 * P + j] = v[M1];
+        }
+        __syncthreads();
+    }
+    // thread (M1 M2) = tid
+    T q[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) q[m] = T(0);
+#pragma unroll 1
+    for (int b0 = 0; b0 < 2; ++b0) {
+        const T* Vb = buf + size_t(b0) * NP;
+#pragma unroll
+        for (int m0 = 0; m0 < P; ++m0) tri_axpy<T, P>(q, St + (b0 * P + m0) * P, Vb[m0 * PP + tid], m0, P - 1);
+    }
+    T* dst = Q + size_t(e[0]) * NP;
+#pragma unroll
+    for (int M0 = 0; M0 < P; ++M0) dst[size_t(M0) * PP + tid] = q[M0];
 }
 
 // 2D: the whole re-expansion of all children in two shared-memory phases per parent.
@@ -1183,6 +1465,148 @@ __global__ void __launch_bounds__(32) k_leaf_eval3d_p(const int4* __restrict__ l
             }
         }
         __syncwarp();
+    }
+}
+
+// 3D leaf evaluation as a small GEMM per leaf: one block of 256 threads per target leaf, the
+// leaf's P^3 local coefficients a[m0][m1 m2] staged once in shared memory, its targets taken
+// 16 at a time.  For a chunk the rows X = [T_m0(x_t); T'_m0(x_t)] (32 rows) multiply the
+// coefficients viewed as a P x P^2 matrix:
+//     A[r][m1 m2] = sum_m0 X[r][m0] a[m0][m1 m2]                    (2 P^3 multiply-adds per target)
+// with a register tile of 8 rows x P^2/64 columns per thread (columns strided by 64, so the
+// shared loads of a row are conflict-free and the 8 row values are broadcasts).  Then every
+// thread weights its columns by T_m1(y_t) T_m2(z_t) and the derivative tables, and the 64
+// threads sharing a target's rows add their partials by a fixed shuffle tree (deterministic).
+//     phi  = sum A[T row] Ty Tz,  g_x = sum A[T' row] Ty Tz,
+//     g_y  = sum A[T row] Ty' Tz, g_z = sum A[T row] Ty Tz'        (times dt/dx = 2/h)
+template <typename T, int P>
+constexpr size_t leaf_eval3d_gemm_smem() {
+    return sizeof(T) * (size_t(P) * P * P + size_t(P) * 32 + size_t(16) * 4 * P) + sizeof(double) * 4 * 2 * 16;
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_leaf_eval3d_gemm(const int4* __restrict__ list, const T* __restrict__ Lc,
+                                                          const T* __restrict__ tgt4, double* __restrict__ pot,
+                                                          double* __restrict__ grad, double inv_rc) {
+    constexpr int PP = P * P, NP = PP * P, CT = PP / 64, RT = 8;
+    static_assert(PP % 64 == 0, "columns split over 64 threads");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* La = reinterpret_cast<T*>(smraw);  // [P][PP]
+    T* X = La + NP;                       // [P][32]  X[m0][r], r = 2 t + (0: T, 1: T')
+    T* TB = X + P * 32;                   // [16][4][P]  (Ty, Ty', Tz, Tz') per target
+    double* red = reinterpret_cast<double*>(TB + 16 * 4 * P);  // [4 row groups][2 warps][16]
+    const int tid = threadIdx.x, rg = tid >> 6, cg = tid & 63, lane = tid & 31, half = (tid >> 5) & 1;
+    const int4 e = list[blockIdx.x];      // (local slot, first target, target count, level)
+    const double sc = 2.0 * inv_rc * double(1LL << e.w);  // dt/dx = 2/h
+    {
+        const T* a = Lc + size_t(e.x) * NP;
+        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        constexpr int VW = sizeof(V) / sizeof(T);
+        const V* av = reinterpret_cast<const V*>(a);
+        V* lv = reinterpret_cast<V*>(La);
+        for (int k = tid; k < NP / VW; k += 256) lv[k] = __ldg(av + k);
+    }
+    for (int t0 = 0; t0 < e.z; t0 += 16) {
+        const int nt = min(16, e.z - t0);
+        __syncthreads();  // previous chunk done with X, TB, red
+        if (tid < 48) {
+            const int t = tid / 3, ax = tid - 3 * t;
+            T tv = T(0);
+            if (t < nt) tv = T(double(tgt4[size_t(e.y + t0 + t) * 4 + ax]) * sc);
+            T tm1 = T(1), tm = tv, um1 = T(1), um = T(2) * tv;
+            const T live = t < nt ? T(1) : T(0);  // rows of absent targets are zero
+            auto put = [&](int m, T b, T d) {
+                if (ax == 0) {
+                    X[m * 32 + 2 * t] = b * live;
+                    X[m * 32 + 2 * t + 1] = d * live;
+                } else {
+                    TB[(t * 4 + 2 * (ax - 1)) * P + m] = b;
+                    TB[(t * 4 + 2 * (ax - 1) + 1) * P + m] = d;
+                }
+            };
+            put(0, T(1), T(0));
+            put(1, tv, T(1));
+#pragma unroll
+            for (int m = 2; m < P; ++m) {
+                const T tn = fma(T(2) * tv, tm, -tm1);
+                put(m, tn, T(m) * um);  // T'_m = m U_{m-1}
+                const T un = fma(T(2) * tv, um, -um1);
+                tm1 = tm;
+                tm = tn;
+                um1 = um;
+                um = un;
+            }
+        }
+        __syncthreads();
+        T acc[RT][CT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int k = 0; k < CT; ++k) acc[i][k] = T(0);
+#pragma unroll 2
+        for (int m0 = 0; m0 < P; ++m0) {
+            T xr[RT];
+#pragma unroll
+            for (int i = 0; i < RT; ++i) xr[i] = X[m0 * 32 + rg * RT + i];
+            const T* lrow = La + m0 * PP + cg;
+#pragma unroll
+            for (int k = 0; k < CT; ++k) {
+                const T l = lrow[64 * k];
+#pragma unroll
+                for (int i = 0; i < RT; ++i) acc[i][k] = fma(xr[i], l, acc[i][k]);
+            }
+        }
+        // weights of the columns and partial sums for this thread's four targets (the tree
+        // over the 64 column threads stays in T: B300's FP64 pipe is a small fraction of FP32)
+        T part[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const T* tb = TB + (rg * 4 + j) * 4 * P;
+            T sp = T(0), sx = T(0), sy = T(0), sz = T(0);
+#pragma unroll
+            for (int k = 0; k < CT; ++k) {
+                const int col = cg + 64 * k, m1 = col / P, m2 = col - m1 * P;
+                const T ty = tb[m1], dy = tb[P + m1], tz = tb[2 * P + m2], dz = tb[3 * P + m2];
+                const T a0 = acc[2 * j][k], a1 = acc[2 * j + 1][k];
+                const T w = ty * tz;
+                sp = fma(a0, w, sp);
+                sx = fma(a1, w, sx);
+                sy = fma(a0, dy * tz, sy);
+                sz = fma(a0, ty * dz, sz);
+            }
+            part[j][0] = sp;
+            part[j][1] = sx;
+            part[j][2] = sy;
+            part[j][3] = sz;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) part[j][q] += __shfl_xor_sync(0xffffffffu, part[j][q], o);
+        if (lane == 0)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) red[(rg * 2 + half) * 16 + j * 4 + q] = double(part[j][q]);
+        __syncthreads();
+        if (tid < 16) {
+            const int t = tid;  // target of the chunk: row group t / 4, slot t % 4
+            const int g = t >> 2, j = t & 3;
+            if (t < nt) {
+                double v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = red[(g * 2) * 16 + j * 4 + q] + red[(g * 2 + 1) * 16 + j * 4 + q];
+                const size_t o = size_t(e.y + t0 + t);
+                pot[o] = v[0];
+                if (grad) {
+                    grad[o * 3 + 0] = v[1] * sc;
+                    grad[o * 3 + 1] = v[2] * sc;
+                    grad[o * 3 + 2] = v[3] * sc;
+                }
+            }
+        }
     }
 }
 
@@ -2271,9 +2695,15 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     }
     if (phase == 0 && I->nleafq > 0) {
         const T* s4 = static_cast<const T*>(pw->d_src4);
-        if (D == 3 && pd.p == 16) k_leaf_moments3d_p<T, 16><<<I->nleafq, 256, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
-        else if (D == 3 && pd.p == 24) k_leaf_moments3d_p<T, 24><<<I->nleafq, 576, 0, s>>>(I->d_leafq, s4, Q, inv_rc);
-        else {
+        auto gemm = [&](auto kern, size_t smb) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+            kern<<<I->nleafq, 256, smb, s>>>(I->d_leafq, s4, Q, inv_rc);
+        };
+        if (D == 3 && pd.p == 16) gemm(k_leaf_moments3d_gemm<T, 16>, leaf_moments3d_gemm_smem<T, 16>());
+        else if (D == 3 && pd.p == 24) gemm(k_leaf_moments3d_gemm<T, 24>, leaf_moments3d_gemm_smem<T, 24>());
+        else if (D == 3 && pd.p == 32 && sizeof(T) == 4) {
+            if constexpr (sizeof(T) == 4) gemm(k_leaf_moments3d_gemm<T, 32>, leaf_moments3d_gemm_smem<T, 32>());
+        } else {
             const size_t sm = ts * (32 * D * pd.p + 32);
             k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, s4, Q, pd, inv_rc);
         }
@@ -2308,6 +2738,16 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                     case 32: launch_p(k_merge2d_p<T, 32>, 10 * 32 * 32, lst, Q); break;
                     default: k_merge2d<T><<<e - b, 256, sm_m2, s>>>(lst, Q, S, pd);
                 }
+            } else if ((sizeof(T) == 4 && (pd.p == 16 || pd.p == 24)) || (sizeof(T) == 8 && pd.p == 16)) {
+                // register accumulators over the triangular shift matrices (three P^3
+                // shared buffers: FP32 up to P = 24, FP64 P = 16)
+                auto mr = [&](auto kern, int P) {
+                    const size_t smb = ts * (2 * P * P + 3 * P * P * P);
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+                    kern<<<e - b, P * P, smb, s>>>(lst, Q, S);
+                };
+                if (pd.p == 16) mr(k_merge3d_r<T, 16>, 16);
+                else if constexpr (sizeof(T) == 4) mr(k_merge3d_r<T, 24>, 24);
             } else if ((pd.p == 16 || pd.p == 24) && e - b < pw->nsm) {
                 // a level with fewer parents than SMs: four blocks per parent (k_merge3d_q);
                 // larger levels keep one block per parent, which issues fewer shared loads
@@ -2407,6 +2847,16 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                     case 32: launch_p(k_down2d_p<T, 32>, 5 * 32 * 32, lst, L); break;
                     default: k_down2d<T><<<e - b, 256, sm_d2, s>>>(lst, L, S, pd);
                 }
+            } else if ((sizeof(T) == 4 && (pd.p == 16 || pd.p == 24)) || (sizeof(T) == 8 && pd.p == 16)) {
+                // two blocks per parent, register accumulators over the triangular shift
+                // matrices (two P^3 shared buffers)
+                auto dr = [&](auto kern, int P) {
+                    const size_t smb = ts * (2 * P * P + 2 * P * P * P);
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+                    kern<<<2 * (e - b), P * P, smb, s>>>(lst, L, S);
+                };
+                if (pd.p == 16) dr(k_down3d_r<T, 16>, 16);
+                else if constexpr (sizeof(T) == 4) dr(k_down3d_r<T, 24>, 24);
             } else if (pd.p == 16 || pd.p == 24) {
                 // four blocks per parent (k_down3d_q)
                 auto d3 = [&](auto kern, int P) {
@@ -2423,11 +2873,20 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         }
     }
     // 6. leaf evaluation (folded into the downward launch for the compile-time 2D orders)
-    if (phase == 4 && I->neval > 0 && D == 3 && (pd.p == 16 || pd.p == 24 || pd.p == 32)) {
+    if (phase == 4 && I->neval > 0 && D == 3 && (pd.p == 16 || pd.p == 24 || (pd.p == 32 && sizeof(T) == 4))) {
         const T* t4 = static_cast<const T*>(pw->d_tgt4);
-        if (pd.p == 16) k_leaf_eval3d_p<T, 16><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
-        else if (pd.p == 24) k_leaf_eval3d_p<T, 24><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
-        else k_leaf_eval3d_p<T, 32><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
+        auto gemm = [&](auto kern, size_t smb) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+            kern<<<I->neval, 256, smb, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
+        };
+        if (pd.p == 16) gemm(k_leaf_eval3d_gemm<T, 16>, leaf_eval3d_gemm_smem<T, 16>());
+        else if (pd.p == 24) gemm(k_leaf_eval3d_gemm<T, 24>, leaf_eval3d_gemm_smem<T, 24>());
+        else if constexpr (sizeof(T) == 4) gemm(k_leaf_eval3d_gemm<T, 32>, leaf_eval3d_gemm_smem<T, 32>());
+        ++pw->launches;
+    } else if (phase == 4 && I->neval > 0 && D == 3 && pd.p == 32) {
+        // FP64 order 32: the coefficients (256 KB) do not fit in shared memory
+        const T* t4 = static_cast<const T*>(pw->d_tgt4);
+        k_leaf_eval3d_p<T, 32><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
         ++pw->launches;
     } else if (phase == 4 && I->neval > 0 && !fixed2d) {
         size_t sm = ts * 32 * 2 * D * pd.p;
