@@ -360,6 +360,59 @@ def stage_roofline(acc, info, d, peak):
     return per
 
 
+SWEEP_REGIMES = [
+    ("ring2d_a1", lambda n: W.wavy_ring2d(n, aspect=1.0)),
+    ("ring2d_a10", lambda n: W.wavy_ring2d(n, aspect=10.0)),
+    ("ring2d_a100", lambda n: W.wavy_ring2d(n, aspect=100.0)),
+    ("sphere3d_rect_iso", lambda n: W.wavy_sphere3d(n, (1, 1, 1), triclinic=False)),
+    ("sphere3d_rect_rod", lambda n: W.wavy_sphere3d(n, (1, 1, 10), triclinic=False)),
+    ("sphere3d_rect_slab", lambda n: W.wavy_sphere3d(n, (1, 10, 10), triclinic=False)),
+    ("sphere3d_tri_iso", lambda n: W.wavy_sphere3d(n, (1, 1, 1), triclinic=True)),
+    ("sphere3d_tri_rod", lambda n: W.wavy_sphere3d(n, (1, 1, 10), triclinic=True)),
+    ("sphere3d_tri_slab", lambda n: W.wavy_sphere3d(n, (1, 10, 10), triclinic=True)),
+]
+SWEEP_RUNS = [("mixed", 1e-3), ("mixed", 1e-6), ("fp64", 1e-6), ("fp64", 1e-9), ("fp64", 1e-12)]
+
+
+def run_sweep(args):
+    """The paper's experiment grid (Sec. 6, Tables 2-4) on this GPU: wavy rings in oblique 2D
+    cells of aspect 1, 10, 100 and wavy sphere shells in rectangular and triclinic 3D cells
+    (iso / rod / slab), at eps 1e-3 .. 1e-12.  Per (regime, precision, eps): the set-up time
+    (tree build and layouts: the paper's t_build), the evaluation time (device, potential and
+    gradient at every source), points/s, and E_rel of the potential against the oracle on
+    sampled targets.  One JSON line per run."""
+    import torch
+    import paper_2606_28608_b300 as P
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.sweep_n
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for name, make in SWEEP_REGIMES:
+        g = make(n)
+        d = g["y"].shape[1]
+        rng = np.random.default_rng(31)
+        idx = np.sort(rng.choice(n, args.sweep_samples, replace=False))
+        pref, _, t_or = oracle_sample(g, idx, nthreads=os.cpu_count())
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        grad = torch.empty((n, d), dtype=torch.float64, device="cuda")
+        for prec, eps in SWEEP_RUNS:
+            t0 = time.perf_counter()
+            pl = P.Plan(g["L"], eps, precision=prec, stream=stream.cuda_stream)
+            pl.set_sources(g["y"], g["q"])
+            torch.cuda.synchronize()
+            t_build = time.perf_counter() - t0
+            steps = 5 if prec == "mixed" else 2
+            t = timed_device(pl, pot, grad, stream, flush, steps, 2)
+            p = pot.cpu().numpy()
+            info = pl.info()
+            pl.close()
+            e = float(np.linalg.norm(p[idx] - pref) / np.linalg.norm(pref))
+            print(json.dumps({"sweep": name, "n": n, "precision": prec, "eps": eps, "t_build_s": round(t_build, 4),
+                              "t_eval_s": t / steps, "points_per_s": n * steps / t, "E_pot": e,
+                              "depth": info["depth"], "n_images": info["n_images"], "M": info["M"][:d],
+                              "oracle_s": round(t_or, 2), "oracle_samples": len(idx)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,11 +422,19 @@ def main():
     ap.add_argument("--workload", default="triclinic3d_4m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 2D and batched secondary lines")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the paper's wavy ring / sphere grid (Tables 2-4 shapes) instead of the benchmark")
+    ap.add_argument("--sweep-n", type=int, default=1_000_000)
+    ap.add_argument("--sweep-samples", type=int, default=32)
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the mixed plan, warm-up + steps evaluations, no other work")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return

@@ -81,6 +81,14 @@ typedef struct {
                        single-launch downward pass waits on a flag that nothing sets, so its
                        bounded wait (about 1 s) expires and the evaluation reports
                        PDMK_ERR_TIMEOUT (2D compile-time orders only; no effect elsewhere) */
+    int autotune;   /* 0: kappa and n_s from Table 1 (or as given).  1: pdmk_set_sources times
+                       candidate (kappa, n_s) pairs around the Table 1 values (those not given
+                       explicitly) on the given sources with temporary plans, keeps the fastest
+                       evaluation and rebuilds the plan with it (the paper's Sec. 5 sweep of
+                       kappa and n_s, done at run time).  The choice, as ratios to the Table 1
+                       values, is cached per (d, precision, eps, floor(log2 n)) for the process,
+                       so later plans of similar size reuse it without timing.  The chosen values
+                       are reported by pdmk_get_info. */
 } pdmk_opts;
 
 /* Fills *opts with the defaults (all fields "auto", FP64, neutrality allowed). */
@@ -136,6 +144,46 @@ int pdmk_set_charges(pdmk_plan plan, const double* q, int where);
  * not synchronise, so its timeout is reported by the next pdmk_eval of the plan.
  */
 int pdmk_eval(pdmk_plan plan, double* pot, double* grad, int where);
+
+/*
+ * pdmk_eval_targets -- the potential (pot, m values) and, if grad is not NULL, its gradient
+ * (grad, m x d row-major) of the plan's sources at m targets x (m x d row-major, the caller's
+ * frame; any position: wrapped into the cell since Phi is periodic), evaluated against the
+ * tree built by pdmk_set_sources: no rebuild (Algorithm 1 returns Phi at the targets it is
+ * given; here the targets may change on every call while the sources stay).
+ * Each target is located in the source tree on the host.  Its plane-wave part comes from the
+ * deepest box on its path that holds a complete local expansion, and its residual sum runs
+ * over the source leaves meeting the neighbourhood of that box's child containing it (the
+ * level restriction of Algorithm 1 step 2 makes this the same telescoped interaction as at
+ * the plan's own targets); the far field is interpolated at the target.  A target whose
+ * wrapped fractional coordinates equal a source's bitwise excludes that source's self term,
+ * as pdmk_eval does at the sources.  The plan's charges are those of the last
+ * pdmk_set_sources / pdmk_set_charges.  where: PDMK_HOST or PDMK_DEVICE for x, pot and grad.
+ * Each call recomputes the sources' far-field grid and local expansions, and keeps an
+ * m-sized device scratch (grown on demand, freed by pdmk_set_sources / pdmk_plan_destroy).
+ * Ordered after the plan's stream like pdmk_eval; a host call returns after the copies.
+ * Errors: BAD_ARG, NOT_READY, NONFINITE, TOO_LARGE (m >= 2^30), OOM, CUDA, TIMEOUT, INTERNAL.
+ */
+int pdmk_eval_targets(pdmk_plan plan, int64_t m, const double* x, double* pot, double* grad, int where);
+
+/*
+ * pdmk_eval_bloch -- the quasi-periodic lattice sum of Sec. 3.7 at the plan's points: for a
+ * Bloch wave vector beta (d values, the caller's frame; not a reciprocal-lattice vector, which
+ * is the periodic case of pdmk_eval)
+ *     Phi(x) = sum_n sum_j q_j e^{i beta.L n} G(x - y_j - L n),   Phi(x + L n) = e^{i beta.L n} Phi(x),
+ * self term excluded, no neutrality requirement (every Fourier mode k_m + beta is kept; none
+ * vanishes).  Complex results: pot (2 values per point: real, imaginary) and, if grad is not
+ * NULL, grad (2 d values per point: for each axis real, imaginary), in the caller's order and
+ * frame.  The near field runs the plan's real kernels twice, on the real and imaginary parts
+ * of the phased image charges q_j e^{i beta.L n}; the smooth part spreads q_j e^{-i beta.y_j},
+ * transforms the full grid (complex, FP64), scales by hat-W_0(|k_m + beta|), transforms back,
+ * interpolates and multiplies by e^{i beta.x}.  The first call after pdmk_set_sources makes
+ * its buffers (about 7 grid sizes and 12 values per point of FP64, kept until the next
+ * pdmk_set_sources).  where as pdmk_eval; the plan's charges are unchanged on return.
+ * Errors: BAD_ARG (also beta a reciprocal-lattice vector), NOT_READY, NONFINITE, OOM, CUDA,
+ * TIMEOUT.
+ */
+int pdmk_eval_bloch(pdmk_plan plan, const double* beta, double* pot, double* grad, int where);
 
 /*
  * pdmk_eval_noalloc -- the evaluation of pdmk_eval (device outputs) for callers that cannot
@@ -274,6 +322,10 @@ void pdmk_plan_destroy(pdmk_plan plan);
 
 /* Static message for an error code. */
 const char* pdmk_strerror(int code);
+
+/* Detail of the plan's last failure (the CUDA or cuFFT error text, or the violated condition),
+ * "" if none; owned by the plan, valid until its next call. */
+const char* pdmk_plan_message(pdmk_plan plan);
 
 /*
  * Debug / verification access to the FP64 kernel tables (host only, no GPU needed).

@@ -30,7 +30,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_double), ("n_s", ctypes.c_int), ("precision", ctypes.c_int),
                 ("window_w", ctypes.c_int), ("n_proxy", ctypes.c_int), ("n_pw", ctypes.c_int),
                 ("max_depth", ctypes.c_int), ("neutrality", ctypes.c_int), ("profile", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("wait_test", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("wait_test", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -71,6 +71,10 @@ def lib():
         L.pdmk_set_charges.restype = ctypes.c_int
         L.pdmk_eval.argtypes = [P, P, P, ctypes.c_int]
         L.pdmk_eval.restype = ctypes.c_int
+        L.pdmk_eval_bloch.argtypes = [P, P, P, P, ctypes.c_int]
+        L.pdmk_eval_bloch.restype = ctypes.c_int
+        L.pdmk_eval_targets.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int]
+        L.pdmk_eval_targets.restype = ctypes.c_int
         L.pdmk_eval_noalloc.argtypes = [P, P, P]
         L.pdmk_eval_noalloc.restype = ctypes.c_int
         L.pdmk_eval_adjoint.argtypes = [P, P, P, P, P, P, ctypes.c_int]
@@ -91,6 +95,8 @@ def lib():
         L.pdmk_get_info.restype = ctypes.c_int
         L.pdmk_plan_destroy.argtypes = [P]
         L.pdmk_plan_destroy.restype = None
+        L.pdmk_plan_message.argtypes = [P]
+        L.pdmk_plan_message.restype = ctypes.c_char_p
         L.pdmk_strerror.argtypes = [ctypes.c_int]
         L.pdmk_strerror.restype = ctypes.c_char_p
         L.pdmk_cell_work.argtypes = [ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Opts), ctypes.c_int64,
@@ -162,7 +168,8 @@ class Plan:
 
     def __init__(self, L, eps: float, *, precision: str = "fp64", kappa: float = 0.0, n_s: int = 0,
                  window_w: int = 0, n_proxy: int = 0, n_pw: int = 0, max_depth: int = -1,
-                 neutrality: int = 1, profile: bool = False, stream=None, wait_test: int = 0):
+                 neutrality: int = 1, profile: bool = False, stream=None, wait_test: int = 0,
+                 autotune: bool = False):
         L = np.ascontiguousarray(np.asarray(L, dtype=np.float64))
         self.d = L.shape[0]
         self._L = L
@@ -186,6 +193,7 @@ class Plan:
                 stream = None
         o.stream = stream or None
         o.wait_test = int(wait_test)
+        o.autotune = 1 if autotune else 0
         self.opts = o
         Lc = np.ascontiguousarray(L.T)  # column-major
         h = ctypes.c_void_p()
@@ -272,6 +280,46 @@ class Plan:
         rc = lib().pdmk_eval(self._h, pot.data_ptr(), grad.data_ptr() if grad is not None else None, PDMK_DEVICE)
         if rc != 0:
             raise PdmkError(rc, "pdmk_eval")
+
+    def eval_targets(self, x, grad: bool = True, out=None):
+        """Potential (and gradient) of the plan's sources at targets x (m x d), evaluated per call
+        against the existing source tree (pdmk_eval_targets).  x: numpy array (host results as
+        numpy) or CUDA tensor (results written into out=(pot, grad) CUDA tensors, or new ones)."""
+        if _is_torch(x):
+            import torch
+            xx = x.contiguous().double()
+            m = xx.shape[0]
+            if out is None:
+                pot = torch.empty(m, dtype=torch.float64, device=xx.device)
+                g = torch.empty((m, self.d), dtype=torch.float64, device=xx.device) if grad else None
+            else:
+                pot, g = out
+            rc = lib().pdmk_eval_targets(self._h, m, xx.data_ptr(), pot.data_ptr(),
+                                         g.data_ptr() if g is not None else None, PDMK_DEVICE)
+        else:
+            xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, self.d))
+            m = xx.shape[0]
+            pot = np.empty(m, dtype=np.float64)
+            g = np.empty((m, self.d), dtype=np.float64) if grad else None
+            rc = lib().pdmk_eval_targets(self._h, m, xx.ctypes.data, pot.ctypes.data,
+                                         g.ctypes.data if g is not None else None, PDMK_HOST)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_eval_targets")
+        return pot, g
+
+    def eval_bloch(self, beta, grad: bool = True):
+        """Quasi-periodic potential (and gradient) at the plan's points for the Bloch wave vector
+        beta (pdmk_eval_bloch): complex numpy arrays of shapes (m,) and (m, d)."""
+        b = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(self.d))
+        pot = np.empty(2 * self.m, dtype=np.float64)
+        g = np.empty(2 * self.m * self.d, dtype=np.float64) if grad else None
+        rc = lib().pdmk_eval_bloch(self._h, b.ctypes.data, pot.ctypes.data, g.ctypes.data if grad else None,
+                                   PDMK_HOST)
+        if rc != 0:
+            raise PdmkError(rc, "pdmk_eval_bloch: " + lib().pdmk_plan_message(self._h).decode())
+        pc = pot[0::2] + 1j * pot[1::2]
+        gc = (g[0::2] + 1j * g[1::2]).reshape(self.m, self.d) if grad else None
+        return pc, gc
 
     def eval_noalloc(self, pot, grad=None):
         """Device evaluation into caller-owned torch CUDA tensors (float64) without any device

@@ -17,6 +17,7 @@
 
 #include "host_plan.h"
 #include "k_assemble.cuh"
+#include "k_bloch.cuh"
 #include "k_farfield.cuh"
 #include "k_nearfield.cuh"
 #include "k_pw.cuh"
@@ -56,6 +57,7 @@ static int device_sms() {
 struct pdmk_plan_s {
     int d = 3;
     double eps = 1e-6;
+    double Lc[9] = {0};  // the caller's lattice (column-major), kept for autotuning
     pdmk_opts opts{};
     double c = 0, kappa = 0, beta = 0;
     int n_s = 0, w = 0, max_depth = 0;
@@ -149,6 +151,24 @@ struct pdmk_plan_s {
     double* d_pot_out = nullptr;
     double* d_grad_out = nullptr;
     PwPlan pw;  // plane-wave (difference-kernel) passes
+    // host copies kept after set_sources for evaluations at new targets (pdmk_eval_targets)
+    Tree h_tree;
+    std::vector<double> h_u;                   // fractional coordinates of the plan's points (n x d)
+    std::vector<int64_t> h_src_orig;           // sorted source -> point index
+    std::vector<unsigned char> h_src_is_orig;  // the sorted source is the point itself, not an image
+    std::vector<double> h_Cu;                  // caller-frame centre of every box (d per box)
+    std::vector<double> h_y;                   // the caller's positions (n x d)
+    std::vector<double> h_src_disp;            // per sorted source: caller-frame lattice vector from
+                                               // its point's given position to this copy (d each)
+    // quasi-periodic evaluation (pdmk_eval_bloch): buffers made on first use
+    bool bl_ready = false;
+    double* bl_buf = nullptr;     // device block: displacements, positions, grids, weights, results
+    cufftHandle bl_fft = 0;       // complex-to-complex transform of the full grid (FP64)
+    bool bl_have_fft = false;
+    double* bl_tab = nullptr;     // device: quadrature of the smoothing transform and window tables
+    // per-call target scratch of pdmk_eval_targets (grown on demand, kept until set_sources)
+    void* tq_buf = nullptr;
+    size_t tq_cap = 0;
     // profiling
     std::vector<cudaEvent_t> ev;
     std::vector<std::string> stage_names;
@@ -222,6 +242,7 @@ extern "C" void pdmk_default_opts(pdmk_opts* o) {
     o->profile = 0;
     o->stream = nullptr;
     o->wait_test = 0;
+    o->autotune = 0;
 }
 
 extern "C" const char* pdmk_strerror(int code) {
@@ -533,6 +554,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     }
     plan->d = d;
     plan->eps = eps;
+    for (int i = 0; i < d * d; ++i) plan->Lc[i] = L[i];
     plan->stream = static_cast<cudaStream_t>(plan->opts.stream);
     plan->nsm = device_sms();
     plan->sum_blocks = 2 * plan->nsm;
@@ -728,11 +750,13 @@ extern "C" void pdmk_plan_destroy(pdmk_plan plan) {
     drop_graph(plan);
     free_list(plan->src_allocs, &plan->device_bytes);
     free_list(plan->plan_allocs, &plan->device_bytes);
+    if (plan->tq_buf) cudaFree(plan->tq_buf);
     pw_free(&plan->pw);
     if (plan->have_fft) {
         cufftDestroy(plan->fft_fwd);
         cufftDestroy(plan->fft_inv);
     }
+    if (plan->bl_have_fft) cufftDestroy(plan->bl_fft);
     for (auto e : plan->ev) cudaEventDestroy(e);
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
@@ -852,6 +876,9 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     plan->evals_since_setup = 0;
     free_list(plan->src_allocs, &plan->device_bytes);
     plan->d_adj = nullptr;
+    if (plan->tq_buf) cudaFree(plan->tq_buf);
+    plan->tq_buf = nullptr;
+    plan->tq_cap = 0;
     pw_free_sources(&plan->pw);
     const bool mixed = plan->opts.precision == PDMK_MIXED;
     const size_t ts = tsize(plan);
@@ -895,6 +922,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     std::vector<double> Cu(size_t(st.nboxes) * d);
     for (int b = 0; b < st.nboxes; ++b) to_user(&tree.center[size_t(b) * d], &Cu[size_t(b) * d]);
     std::vector<double> relv(size_t(plan->nimg) * d);
+    std::vector<double> src_disp(size_t(plan->nimg) * d, 0.0);
     for (int64_t j = 0; j < plan->nimg; ++j) {
         const int b = leaf_of[j];
         const int64_t o = ss.orig[j];
@@ -909,12 +937,15 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
             shifted |= m[i] != 0.0;
         }
         if (shifted) {
+            double Rm[3] = {0, 0, 0};
             for (int i = 0; i < d; ++i) {
                 double s = 0;
                 for (int k = 0; k < d; ++k) s += g.R[i * d + k] * m[k];
+                Rm[i] = s;
                 D[i] = tree.center[size_t(b) * d + i] - s;
             }
             to_user(D, E);
+            to_user(Rm, &src_disp[size_t(j) * d]);
         } else {
             for (int i = 0; i < d; ++i) E[i] = Cu[size_t(b) * d + i];
         }
@@ -1182,11 +1213,161 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     plan->n_out = m > 0 ? m : n_src;
     I.n = n_src;
     I.n_targets = plan->n_out;
+    // host copies for evaluations at new targets
+    plan->h_u.swap(u);
+    plan->h_src_orig.assign(ss.orig.begin(), ss.orig.end());
+    plan->h_src_is_orig.assign(size_t(plan->nimg), 0);
+    for (int64_t tt = 0; tt < int64_t(ss.tgt_of.size()); ++tt) plan->h_src_is_orig[size_t(ss.tgt_of[tt])] = 1;
+    plan->h_Cu.swap(Cu);
+    plan->h_y.swap(hy);
+    plan->h_src_disp.swap(src_disp);
+    plan->bl_ready = false;
+    plan->bl_buf = nullptr;  // freed with the source buffers
+    plan->h_tree = std::move(tree);
     plan->ready = true;
     return PDMK_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Autotuning of (kappa, n_s) (pdmk_opts.autotune): candidate pairs around the Table 1 values
+// are timed on the caller's sources with temporary plans; the fastest wins.  A coordinate
+// search: n_s in {n0, n0/2, 2 n0} at kappa0, then kappa in {3/4, 4/3} x kappa0 at the best
+// n_s (five timed plans).  Each candidate is timed on its third evaluation (the first runs
+// eagerly, the second captures the graph).  Choices are cached as ratios to the Table 1
+// values.
+namespace {
+struct TuneKey {
+    int d, precision, logn;
+    double eps;
+    bool operator<(const TuneKey& o) const {
+        if (d != o.d) return d < o.d;
+        if (precision != o.precision) return precision < o.precision;
+        if (logn != o.logn) return logn < o.logn;
+        return eps < o.eps;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<double, double>> g_tune;  // (kappa / kappa0, n_s / n0)
+}  // namespace
+
+static int time_candidate(pdmk_plan plan, double kappa, int ns, int64_t n, const double* y, const double* q,
+                          int where, double* dp, double* dg, float* ms) {
+    pdmk_opts o = plan->opts;
+    o.kappa = kappa;
+    o.n_s = ns;
+    o.autotune = 0;
+    o.profile = 0;
+    pdmk_plan tmp = nullptr;
+    int r = pdmk_plan_create(plan->d, plan->Lc, plan->eps, &o, &tmp);
+    if (r != PDMK_OK) return r;
+    r = pdmk_set_sources(tmp, n, y, q, where);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (r == PDMK_OK) {
+        for (int k = 0; k < 2 && r == PDMK_OK; ++k) r = pdmk_eval(tmp, dp, dg, PDMK_DEVICE);
+    }
+    if (r == PDMK_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) r = PDMK_ERR_CUDA;
+    if (r == PDMK_OK) {
+        cudaEventRecord(e0, plan->stream);
+        r = pdmk_eval(tmp, dp, dg, PDMK_DEVICE);
+        cudaEventRecord(e1, plan->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) r = PDMK_ERR_CUDA;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGetLastError();
+    pdmk_plan_destroy(tmp);
+    return r;
+}
+
+static int autotune_plan(pdmk_plan plan, int64_t n, const double* y, const double* q, int where) {
+    const bool kfix = plan->opts.kappa > 0, nfix = plan->opts.n_s > 0;
+    if (kfix && nfix) return PDMK_OK;
+    double kappa0;
+    int n0;
+    {
+        Geometry tmp;
+        int rc = make_geometry(plan->d, plan->Lc, 1.0, plan->c, &tmp);
+        if (rc != PDMK_OK) return rc;
+        table1_defaults(plan->d, plan->eps, &tmp, plan->Lc, &kappa0, &n0);
+    }
+    if (kfix) kappa0 = plan->opts.kappa;
+    if (nfix) n0 = plan->opts.n_s;
+    const TuneKey key{plan->d, plan->opts.precision, int(std::floor(std::log2(double(std::max<int64_t>(n, 1))))),
+                      plan->eps};
+    double kr = 1.0, nr = 1.0;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            kr = it->second.first;
+            nr = it->second.second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        double* buf = nullptr;
+        if (cudaMalloc(&buf, sizeof(double) * size_t(std::max<int64_t>(n, 1)) * (1 + plan->d)) != cudaSuccess) {
+            cudaGetLastError();
+            return PDMK_ERR_OOM;
+        }
+        double* dp = buf;
+        double* dg = buf + n;
+        float best = 0;
+        auto trial = [&](double k, double nrat) -> int {
+            const int ns = std::max(4, int(std::lround(n0 * nrat)));
+            float ms = 0;
+            const int r = time_candidate(plan, kappa0 * k, ns, n, y, q, where, dp, dg, &ms);
+            if (r != PDMK_OK) return r;
+            if (best == 0 || ms < best) {
+                best = ms;
+                kr = k;
+                nr = nrat;
+            }
+            return PDMK_OK;
+        };
+        int r = trial(1.0, 1.0);
+        if (!nfix) {
+            if (r == PDMK_OK) r = trial(1.0, 0.5);
+            if (r == PDMK_OK) r = trial(1.0, 2.0);
+        }
+        const double nbest = nr;
+        if (!kfix) {
+            if (r == PDMK_OK) r = trial(0.75, nbest);
+            if (r == PDMK_OK) r = trial(4.0 / 3.0, nbest);
+        }
+        cudaFree(buf);
+        if (r != PDMK_OK) return r;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = {kr, nr};
+    }
+    const double kappa = kfix ? plan->opts.kappa : kappa0 * kr;
+    const int ns = nfix ? plan->opts.n_s : std::max(4, int(std::lround(n0 * nr)));
+    if (std::fabs(kappa - plan->kappa) > 1e-12 * kappa) {
+        // a new root box size changes the geometry: rebuild the plan and take its contents
+        pdmk_opts o = plan->opts;
+        o.kappa = kappa;
+        o.n_s = ns;
+        o.autotune = 0;
+        pdmk_plan fresh = nullptr;
+        const int r = pdmk_plan_create(plan->d, plan->Lc, plan->eps, &o, &fresh);
+        if (r != PDMK_OK) return r;
+        fresh->opts.autotune = plan->opts.autotune;
+        fresh->opts.kappa = plan->opts.kappa;
+        fresh->opts.n_s = plan->opts.n_s;
+        if (plan->ws) cudaStreamSynchronize(plan->ws);
+        std::swap(*plan, *fresh);
+        pdmk_plan_destroy(fresh);  // the old contents
+    }
+    plan->n_s = ns;
+    return PDMK_OK;
+}
+
 extern "C" int pdmk_set_sources(pdmk_plan plan, int64_t n, const double* y, const double* q, int where) {
+    if (plan && plan->opts.autotune && n > 0 && y && q) {
+        const int r = autotune_plan(plan, n, y, q, where);
+        if (r != PDMK_OK) return r;
+    }
     return set_points(plan, n, y, q, 0, nullptr, where);
 }
 
@@ -1221,27 +1402,42 @@ static int stage_mark(pdmk_plan plan, const char* name) {
     return PDMK_OK;
 }
 
+// The residual direct sum over ndesc target descriptors (near-field arguments filled in).
 template <typename T, int D>
-static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first) {
-    cudaStream_t s = plan->ws;
+static void near_launch(pdmk_plan plan, const NearArgs<T>& na, int ndesc, cudaStream_t st) {
+    const int nc = std::max(na.nA, na.nB);
+    const int wb = (ndesc + kNearWarps - 1) / kNearWarps, wt = 32 * kNearWarps;
+    // A is usually two terms shorter than B: its own compile-time length then
+    const bool ash = na.nA <= plan->near_nh - 2;
+#define PDMK_NEAR(NH)                                                                         \
+(ash ? k_near_warp<T, D, NH, NH - 2><<<wb, wt, 0, st>>>(na)                            \
+     : k_near_warp<T, D, NH, NH><<<wb, wt, 0, st>>>(na))
+    if (plan->near_nh == 8) PDMK_NEAR(8);
+    else if (plan->near_nh == 10) PDMK_NEAR(10);
+    else if (plan->near_nh == 12) PDMK_NEAR(12);
+    else if (plan->near_nh == 14) PDMK_NEAR(14);
+    else if (plan->near_nh == 16) PDMK_NEAR(16);
+    else if (plan->near_nh == 20) PDMK_NEAR(20);
+    else if (plan->near_nh == 24) PDMK_NEAR(24);
+#undef PDMK_NEAR
+    else if (nc <= 8) k_nearfield<T, D, 8><<<ndesc, kNearThreads, 0, st>>>(na);
+    else if (nc <= 12) k_nearfield<T, D, 12><<<ndesc, kNearThreads, 0, st>>>(na);
+    else if (nc <= 16) k_nearfield<T, D, 16><<<ndesc, kNearThreads, 0, st>>>(na);
+    else if (nc <= 20) k_nearfield<T, D, 20><<<ndesc, kNearThreads, 0, st>>>(na);
+    else if (nc <= 24) k_nearfield<T, D, 24><<<ndesc, kNearThreads, 0, st>>>(na);
+    else if (nc <= 32) k_nearfield<T, D, 32><<<ndesc, kNearThreads, 0, st>>>(na);
+    else k_nearfield<T, D, 40><<<ndesc, kNearThreads, 0, st>>>(na);
+}
+
+// The far field up to the potential grid: spread, fold, FFT, scale, inverse FFT (and the
+// narrowing copy a mixed 3D plan's interpolation reads).  Afterwards the grid in the
+// plan's precision (d_grid) holds the smooth periodic potential on the Fourier grid, except
+// for the 2D halo interpolation, which reads the transform grid itself.
+// Spreading (type-1 half) and the fold of the subproblem or per-CTA slabs into a real grid
+// out (FP32 if out_f32, else FP64).
+template <typename T, int D>
+static int spread_fold(pdmk_plan plan, cudaStream_t s, void* out, bool out_f32) {
     const Geometry& g = plan->g;
-    int r;
-    plan->launches = 0;
-    for (auto e : plan->ev) cudaEventDestroy(e);
-    plan->ev.clear();
-    plan->stage_names.clear();
-    plan->stage_ms.clear();
-    if ((r = stage_mark(plan, "start"))) return r;
-    // Three independent branches until assembly: far field on ws, plane-wave passes on
-    // ws_pw, near-field sum on ws_near (one stream when profiling per stage).
-    const bool branches = !plan->opts.profile;
-    cudaStream_t s_pw = branches ? plan->ws_pw : s, s_near = branches ? plan->ws_near : s;
-    if (branches) {
-        CK(cudaEventRecord(plan->ev_s, s));
-        CK(cudaStreamWaitEvent(s_pw, plan->ev_s, 0));
-        CK(cudaStreamWaitEvent(s_near, plan->ev_s, 0));
-    }
-    // ---- far field: spread, fold, FFT, scale, inverse FFT, interpolate ----
     const T hwi2 = T(4.0 / (double(plan->w) * plan->w));
     void* slab = plan->slab_override ? plan->slab_override : plan->d_slab;
     if (D == 2 && plan->whole_ctas > 0 && plan->far_halo && sizeof(T) == 4) {
@@ -1260,12 +1456,12 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         ++plan->launches;
         CK(cudaGetLastError());
         const int blocks = int((plan->ncell + 31) / 32);
-        if (plan->fft32)
+        if (out_f32)
             k_fold_whole<T, float><<<std::max(blocks, 1), 256, 0, s>>>(
-                static_cast<const T*>(slab), plan->whole_ctas, static_cast<float*>(plan->d_grid64), int(plan->ncell));
+                static_cast<const T*>(slab), plan->whole_ctas, static_cast<float*>(out), int(plan->ncell));
         else
             k_fold_whole<T, double><<<std::max(blocks, 1), 256, 0, s>>>(
-                static_cast<const T*>(slab), plan->whole_ctas, static_cast<double*>(plan->d_grid64), int(plan->ncell));
+                static_cast<const T*>(slab), plan->whole_ctas, static_cast<double*>(out), int(plan->ncell));
         ++plan->launches;
         CK(cudaGetLastError());
     } else if (D == 2 && plan->whole_ctas > 0) {
@@ -1296,12 +1492,12 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         ++plan->launches;
         CK(cudaGetLastError());
         const int blocks = int((plan->ncell + 31) / 32);
-        if (plan->fft32)
+        if (out_f32)
             k_fold_whole<T, float><<<std::max(blocks, 1), 256, 0, s>>>(
-                static_cast<const T*>(slab), plan->whole_ctas, static_cast<float*>(plan->d_grid64), int(plan->ncell));
+                static_cast<const T*>(slab), plan->whole_ctas, static_cast<float*>(out), int(plan->ncell));
         else
             k_fold_whole<T, double><<<std::max(blocks, 1), 256, 0, s>>>(
-                static_cast<const T*>(slab), plan->whole_ctas, static_cast<double*>(plan->d_grid64), int(plan->ncell));
+                static_cast<const T*>(slab), plan->whole_ctas, static_cast<double*>(out), int(plan->ncell));
         ++plan->launches;
         CK(cudaGetLastError());
     } else {
@@ -1355,12 +1551,19 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         int blocks = int(std::min<int64_t>((plan->ncell + 255) / 256, int64_t(plan->nsm) * 8));
         k_fold<T, D, G><<<std::max(blocks, 1), 256, 0, s>>>(fa);
         };
-        if (plan->fft32) fold(static_cast<float*>(plan->d_grid64));
-        else fold(static_cast<double*>(plan->d_grid64));
+        if (out_f32) fold(static_cast<float*>(out));
+        else fold(static_cast<double*>(out));
         ++plan->launches;
         CK(cudaGetLastError());
     }
     }
+    return PDMK_OK;
+}
+
+template <typename T, int D>
+static int far_grid(pdmk_plan plan, cudaStream_t s, bool interp_halo) {
+    int r;
+    if ((r = spread_fold<T, D>(plan, s, plan->d_grid64, plan->fft32))) return r;
     if ((r = stage_mark(plan, "spread"))) return r;
     const int cblocks = int(std::max<int64_t>(1, std::min<int64_t>((plan->ncell + 255) / 256, int64_t(plan->nsm) * 8)));
     if (plan->fft32)
@@ -1384,7 +1587,6 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         CKFFT(cufftExecC2R(plan->fft_inv, (cufftComplex*)plan->d_spec, (cufftReal*)plan->d_grid64));
     else
         CKFFT(cufftExecZ2D(plan->fft_inv, (cufftDoubleComplex*)plan->d_spec, (cufftDoubleReal*)plan->d_grid64));
-    const bool interp_halo = plan->ntgt > 0 && D == 2 && plan->far_halo && sizeof(T) == 4;
     // the halo interpolation reads the transform grid in its own precision; the others read T
     if (sizeof(T) == 4 && !plan->fft32 && !interp_halo) {
         k_convert<double, T><<<cblocks, 256, 0, s>>>(static_cast<const double*>(plan->d_grid64),
@@ -1393,6 +1595,33 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         CK(cudaGetLastError());
     }
     if ((r = stage_mark(plan, "fft_inv"))) return r;
+    return PDMK_OK;
+}
+
+template <typename T, int D>
+static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first) {
+    cudaStream_t s = plan->ws;
+    const Geometry& g = plan->g;
+    int r;
+    plan->launches = 0;
+    for (auto e : plan->ev) cudaEventDestroy(e);
+    plan->ev.clear();
+    plan->stage_names.clear();
+    plan->stage_ms.clear();
+    if ((r = stage_mark(plan, "start"))) return r;
+    // Three independent branches until assembly: far field on ws, plane-wave passes on
+    // ws_pw, near-field sum on ws_near (one stream when profiling per stage).
+    const bool branches = !plan->opts.profile;
+    cudaStream_t s_pw = branches ? plan->ws_pw : s, s_near = branches ? plan->ws_near : s;
+    if (branches) {
+        CK(cudaEventRecord(plan->ev_s, s));
+        CK(cudaStreamWaitEvent(s_pw, plan->ev_s, 0));
+        CK(cudaStreamWaitEvent(s_near, plan->ev_s, 0));
+    }
+    // ---- far field: spread, fold, FFT, scale, inverse FFT, interpolate ----
+    const T hwi2 = T(4.0 / (double(plan->w) * plan->w));
+    const bool interp_halo = plan->ntgt > 0 && D == 2 && plan->far_halo && sizeof(T) == 4;
+    if ((r = far_grid<T, D>(plan, s, interp_halo))) return r;
     if (interp_halo) {
         const int Mp0 = g.M[0] + plan->w - 1, Mp1 = g.M[1] + plan->w - 1;
         const size_t smem = sizeof(T) * size_t(Mp0) * Mp1;
@@ -1497,28 +1726,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         na.ent_shlo = static_cast<const T*>(plan->d_ent_shlo);
         na.monoA = static_cast<const T*>(plan->d_monoA);
         na.monoB = static_cast<const T*>(plan->d_monoB);
-        const int nc = std::max(na.nA, na.nB);
-        const int wb = (plan->nnear + kNearWarps - 1) / kNearWarps, wt = 32 * kNearWarps;
-        // A is usually two terms shorter than B: its own compile-time length then
-        const bool ash = na.nA <= plan->near_nh - 2;
-#define PDMK_NEAR(NH)                                                                         \
-    (ash ? k_near_warp<T, D, NH, NH - 2><<<wb, wt, 0, s_near>>>(na)                            \
-         : k_near_warp<T, D, NH, NH><<<wb, wt, 0, s_near>>>(na))
-        if (plan->near_nh == 8) PDMK_NEAR(8);
-        else if (plan->near_nh == 10) PDMK_NEAR(10);
-        else if (plan->near_nh == 12) PDMK_NEAR(12);
-        else if (plan->near_nh == 14) PDMK_NEAR(14);
-        else if (plan->near_nh == 16) PDMK_NEAR(16);
-        else if (plan->near_nh == 20) PDMK_NEAR(20);
-        else if (plan->near_nh == 24) PDMK_NEAR(24);
-#undef PDMK_NEAR
-        else if (nc <= 8) k_nearfield<T, D, 8><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 12) k_nearfield<T, D, 12><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 16) k_nearfield<T, D, 16><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 20) k_nearfield<T, D, 20><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 24) k_nearfield<T, D, 24><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
-        else if (nc <= 32) k_nearfield<T, D, 32><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
-        else k_nearfield<T, D, 40><<<plan->nnear, kNearThreads, 0, s_near>>>(na);
+        near_launch<T, D>(plan, na, plan->nnear, s_near);
         ++plan->launches;
         CK(cudaGetLastError());
     }
@@ -1656,6 +1864,10 @@ extern "C" int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, 
     return n;
 }
 
+extern "C" const char* pdmk_plan_message(pdmk_plan plan) {
+    return plan ? plan->msg.c_str() : "";
+}
+
 extern "C" int pdmk_get_info(pdmk_plan plan, pdmk_info* info) {
     if (!plan || !info) return PDMK_ERR_BAD_ARG;
     *info = plan->info;
@@ -1729,6 +1941,769 @@ extern "C" int pdmk_eval_noalloc(pdmk_plan plan, double* pot, double* grad) {
     plan->slab_override = nullptr;
     plan->opts.profile = saved_profile ? 1 : 0;
     plan->count_pending = saved_count;
+    if (r != PDMK_OK) return r;
+    CK(cudaEventRecord(plan->ev_join, plan->ws));
+    CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
+    return PDMK_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Evaluation at new targets against the existing source tree (Algorithm 1's RETURN at points
+// given per call).  A target x takes the deepest box A on its path whose complete local
+// expansion is stored (the receiving boxes of the plane-wave passes; in 3D also the target
+// leaves) and the virtual leaf B' = A's child containing x (A itself when A is x's leaf; the
+// root box when no ancestor has one).  With L' the level of B':
+//     near(x) = local_A(x)  [= sum_{l < L'} D_l, the telescoped plane-wave part]
+//             + sum over the source leaves meeting B''s neighbourhood of R_{L'}(x - y) q
+// which is the interaction rule of the plan's own targets with B' in place of the leaf: by
+// the level restriction no coarser leaf meets the neighbourhood of a non-leaf B'.  The far
+// field is interpolated at x; a target that equals a source bitwise (the same wrapped
+// fractional coordinates) excludes that source's self pair and has W_{L'}(0) q removed.
+__global__ void k_self_charges(int64_t m, const int* __restrict__ self_pt, const double* __restrict__ q,
+                               double* __restrict__ q_tgt) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
+        q_tgt[i] = self_pt[i] >= 0 ? q[self_pt[i]] : 0.0;
+}
+
+namespace {
+// host-side layout of one call: the targets in evaluation order and their descriptors
+struct TargetLayout {
+    int64_t m = 0;
+    std::vector<unsigned char> tgt4, tgt4a, t_dq;  // T-sized records (4 per target)
+    std::vector<float> tgt_lo;
+    std::vector<int4> t_g0;
+    std::vector<double> self_w;
+    std::vector<int> self_pt, tgt_orig;
+    std::vector<TLeaf> desc;
+    std::vector<int2> ent;
+    std::vector<unsigned char> ent_sh;
+    std::vector<float> ent_shlo;
+    std::vector<int4> evl;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+}  // namespace
+
+static int build_target_layout(pdmk_plan plan, int64_t m, const double* hx, TargetLayout* out) {
+    const int d = plan->d;
+    const Geometry& g = plan->g;
+    const Tree& t = plan->h_tree;
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    const size_t ts = tsize(plan);
+    const int depth = t.nlevels - 1;
+    const double cscale = double(1LL << depth) / g.rc;
+    const std::vector<unsigned char>& full = plan->pw.local_full;
+    std::vector<double> tu(size_t(m) * d), tsh(size_t(m) * d);
+    std::vector<int> leaf(static_cast<size_t>(m)), vb(static_cast<size_t>(m)), ab(static_cast<size_t>(m));
+    std::vector<int> selfp(static_cast<size_t>(m), -1);
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t j = 0; j < m; ++j) {
+        double xo[3] = {0, 0, 0}, u[3] = {0, 0, 0}, pos[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i)
+            for (int k = 0; k < d; ++k) xo[i] += g.Q[i * d + k] * hx[j * d + k];
+        for (int i = 0; i < d; ++i) {
+            double sv = 0;
+            for (int k = 0; k < d; ++k) sv += g.Rinv[i * d + k] * xo[k];
+            double f = sv - std::floor(sv);
+            if (f >= 1.0) f = 0.0;
+            u[i] = f;
+            tu[size_t(j) * d + i] = f;
+            tsh[size_t(j) * d + i] = std::nearbyint(f - sv);  // pos = Q x + R shift
+        }
+        int64_t c[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i) {
+            for (int k = i; k < d; ++k) pos[i] += g.R[i * d + k] * u[k];
+            const int64_t cmax = int64_t(g.nroot[i]) << depth;
+            c[i] = std::min<int64_t>(cmax - 1, std::max<int64_t>(0, int64_t(std::floor((pos[i] - g.lo[i]) * cscale))));
+        }
+        const int B = t.locate(depth, c);
+        if (B < 0) { ++bad; continue; }
+        leaf[j] = B;
+        // a source that is this very point: an original copy (not an image) in the leaf with
+        // bitwise-equal fractional coordinates
+        for (int64_t s = t.src_begin[B]; s < t.src_end[B]; ++s) {
+            if (!plan->h_src_is_orig[size_t(s)]) continue;
+            const int64_t o = plan->h_src_orig[size_t(s)];
+            bool eq = true;
+            for (int i = 0; i < d; ++i) eq &= plan->h_u[size_t(o) * d + i] == u[i];
+            if (eq) {
+                selfp[j] = int(o);
+                break;
+            }
+        }
+        int a = B;
+        while (a >= 0 && !(size_t(a) < full.size() && full[a])) a = t.parent[a];
+        int v = B;
+        if (a < 0) {
+            while (t.parent[v] >= 0) v = t.parent[v];  // the root box
+        } else if (a != B) {
+            while (t.parent[v] != a) v = t.parent[v];  // A's child on the path
+        }
+        vb[j] = v;
+        ab[j] = a;
+    }
+    if (bad) return PDMK_ERR_INTERNAL;
+    // evaluation order: by (virtual leaf, real leaf), then by target index
+    std::vector<int64_t> ord(static_cast<size_t>(m));
+    std::iota(ord.begin(), ord.end(), int64_t(0));
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
+        return vb[x] != vb[y] ? vb[x] < vb[y] : leaf[x] < leaf[y];
+    });
+    TargetLayout& L = *out;
+    L.m = m;
+    L.tgt4.assign(size_t(m) * 4 * ts, 0);
+    L.tgt4a.assign(size_t(m) * 4 * ts, 0);
+    L.t_dq.assign(size_t(m) * 4 * ts, 0);
+    L.tgt_lo.assign(mixed ? size_t(m) * 4 : 0, 0.0f);
+    L.t_g0.resize(static_cast<size_t>(m));
+    L.self_w.resize(static_cast<size_t>(m));
+    L.self_pt.resize(static_cast<size_t>(m));
+    L.tgt_orig.resize(static_cast<size_t>(m));
+    auto put = [&](std::vector<unsigned char>& buf, size_t idx, double v) {
+        if (mixed) { float f = float(v); std::memcpy(&buf[idx * 4], &f, 4); }
+        else std::memcpy(&buf[idx * 8], &v, 8);
+    };
+    // coordinates relative to a box centre, formed in the caller's frame (as the sources'):
+    // Q (x - Q^T (c_b - R shift))
+    auto rel = [&](int64_t j, int b, double* r) {
+        double D[3] = {0, 0, 0}, E[3] = {0, 0, 0}, du[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i) {
+            double sR = 0;
+            for (int k = 0; k < d; ++k) sR += g.R[i * d + k] * tsh[size_t(j) * d + k];
+            D[i] = t.center[size_t(b) * d + i] - sR;
+        }
+        for (int i = 0; i < d; ++i)
+            for (int k = 0; k < d; ++k) E[i] += g.Q[k * d + i] * D[k];
+        for (int a = 0; a < d; ++a) du[a] = hx[j * d + a] - E[a];
+        for (int i = 0; i < d; ++i) {
+            double sv = 0;
+            for (int k = 0; k < d; ++k) sv += g.Q[i * d + k] * du[k];
+            r[i] = sv;
+        }
+    };
+    const int fw = plan->w / 2;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < m; ++k) {
+        const int64_t j = ord[size_t(k)];
+        double r[3];
+        // near field: relative to the real leaf (a coincident source then cancels exactly)
+        rel(j, leaf[j], r);
+        for (int a = 0; a < d; ++a) {
+            put(L.tgt4, size_t(k) * 4 + a, r[a]);
+            if (mixed) L.tgt_lo[size_t(k) * 4 + a] = float(r[a] - double(float(r[a])));
+        }
+        if (ab[j] >= 0) {
+            rel(j, ab[j], r);
+            for (int a = 0; a < d; ++a) put(L.tgt4a, size_t(k) * 4 + a, r[a]);
+        }
+        int gg[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i) {
+            const int M = g.M[i];
+            const double Mu = M * tu[size_t(j) * d + i];
+            int g0 = int(std::ceil(Mu - 0.5 * plan->w));
+            const double del = Mu - g0;
+            const int key = g0 + fw;
+            const int wrap = key >= 0 ? key / M : -((-key + M - 1) / M);
+            g0 -= wrap * M;
+            gg[i] = ((g0 % M) + M) % M;
+            put(L.t_dq, size_t(k) * 4 + i, del);
+        }
+        L.t_g0[size_t(k)] = make_int4(gg[0], gg[1], gg[2], 0);
+        const double h = g.rc / double(1LL << t.level[vb[j]]);
+        L.self_w[size_t(k)] = (d == 3) ? plan->kt.self_coef / h : plan->kt.self_coef - std::log(h) / (2.0 * kPi);
+        L.self_pt[size_t(k)] = selfp[j];
+        L.tgt_orig[size_t(k)] = int(j);
+    }
+    // near-field descriptors: one group per (virtual leaf, real leaf), the virtual leaf's
+    // list, shifts into the real leaf's frame; groups cut to 32 targets for the warp kernel
+    std::vector<int> lst;
+    for (int64_t k0 = 0; k0 < m;) {
+        const int64_t j0 = ord[size_t(k0)];
+        int64_t k1 = k0;
+        while (k1 < m && vb[ord[size_t(k1)]] == vb[j0] && leaf[ord[size_t(k1)]] == leaf[j0]) ++k1;
+        const int v = vb[j0], B = leaf[j0];
+        box_direct_list(t, v, &lst);
+        const int lb = int(L.ent.size());
+        for (int S : lst) {
+            L.ent.push_back(make_int2(int(t.src_begin[S]), int(t.src_end[S] - t.src_begin[S])));
+            double du[3] = {0, 0, 0}, sht[3] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) du[a] = plan->h_Cu[size_t(S) * d + a] - plan->h_Cu[size_t(B) * d + a];
+            for (int i = 0; i < d; ++i)
+                for (int kk = 0; kk < d; ++kk) sht[i] += g.Q[i * d + kk] * du[kk];
+            const size_t e = L.ent.size() - 1;
+            L.ent_sh.resize(L.ent.size() * 4 * ts, 0);
+            if (mixed) L.ent_shlo.resize(L.ent.size() * 4, 0.0f);
+            for (int a = 0; a < d; ++a) {
+                put(L.ent_sh, e * 4 + a, sht[a]);
+                if (mixed) L.ent_shlo[e * 4 + a] = float(sht[a] - double(float(sht[a])));
+            }
+        }
+        const int cut = plan->near_nh > 0 ? 32 : int(k1 - k0);
+        for (int64_t c0 = k0; c0 < k1; c0 += cut) {
+            TLeaf tl;
+            tl.tgt_begin = int(c0);
+            tl.tgt_count = int(std::min<int64_t>(cut, k1 - c0));
+            tl.list_begin = lb;
+            tl.list_count = int(lst.size());
+            tl.level = t.level[v];
+            tl.box = v;
+            tl.pad0 = tl.pad1 = 0;
+            L.desc.push_back(tl);
+        }
+        k0 = k1;
+    }
+    if (L.ent.empty()) {  // keep the device pointers valid
+        L.ent.push_back(make_int2(0, 0));
+        L.ent_sh.assign(4 * ts, 0);
+        if (mixed) L.ent_shlo.assign(4, 0.0f);
+    }
+    // local-expansion evaluation: runs of equal box A in evaluation order
+    for (int64_t k0 = 0; k0 < m;) {
+        const int a = ab[ord[size_t(k0)]];
+        int64_t k1 = k0;
+        while (k1 < m && ab[ord[size_t(k1)]] == a) ++k1;
+        if (a >= 0) L.evl.push_back(make_int4(plan->pw.lslot[a], int(k0), int(k1 - k0), t.level[a]));
+        k0 = k1;
+    }
+    return PDMK_OK;
+}
+
+template <typename T, int D>
+static int run_eval_targets(pdmk_plan plan, const TargetLayout& L, char* buf, double* dp, double* dg) {
+    cudaStream_t s = plan->ws;
+    const Geometry& g = plan->g;
+    const int64_t m = L.m;
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    const size_t ts = sizeof(T);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = buf + off;
+        off += align256(std::max<size_t>(bytes, 1));
+        return static_cast<void*>(p);
+    };
+    auto up = [&](void* dst, const void* src, size_t bytes) -> int {
+        if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        return PDMK_OK;
+    };
+    T* tgt4 = static_cast<T*>(take(size_t(m) * 4 * ts));
+    T* tgt4a = static_cast<T*>(take(size_t(m) * 4 * ts));
+    float* tgt_lo = static_cast<float*>(take(size_t(m) * 4 * 4));
+    int4* t_g0 = static_cast<int4*>(take(size_t(m) * sizeof(int4)));
+    T* t_dq = static_cast<T*>(take(size_t(m) * 4 * ts));
+    double* self_w = static_cast<double*>(take(size_t(m) * 8));
+    int* self_pt = static_cast<int*>(take(size_t(m) * 4));
+    int* tgt_orig = static_cast<int*>(take(size_t(m) * 4));
+    double* q_tgt = static_cast<double*>(take(size_t(m) * 8));
+    double* pot_near = static_cast<double*>(take(size_t(m) * 8));
+    double* grad_near = static_cast<double*>(take(size_t(m) * D * 8));
+    double* pot_pw = static_cast<double*>(take(size_t(m) * 8));
+    double* grad_pw = static_cast<double*>(take(size_t(m) * D * 8));
+    double* pot_far = static_cast<double*>(take(size_t(m) * 8));
+    double* gradu_far = static_cast<double*>(take(size_t(m) * D * 8));
+    TLeaf* desc = static_cast<TLeaf*>(take(L.desc.size() * sizeof(TLeaf)));
+    int2* ent = static_cast<int2*>(take(L.ent.size() * sizeof(int2)));
+    T* ent_sh = static_cast<T*>(take(L.ent_sh.size()));
+    float* ent_shlo = static_cast<float*>(take(L.ent_shlo.size() * 4));
+    int4* evl = static_cast<int4*>(take(L.evl.size() * sizeof(int4)));
+    int r;
+    if ((r = up(tgt4, L.tgt4.data(), L.tgt4.size()))) return r;
+    if ((r = up(tgt4a, L.tgt4a.data(), L.tgt4a.size()))) return r;
+    if ((r = up(tgt_lo, L.tgt_lo.data(), L.tgt_lo.size() * 4))) return r;
+    if ((r = up(t_g0, L.t_g0.data(), L.t_g0.size() * sizeof(int4)))) return r;
+    if ((r = up(t_dq, L.t_dq.data(), L.t_dq.size()))) return r;
+    if ((r = up(self_w, L.self_w.data(), L.self_w.size() * 8))) return r;
+    if ((r = up(self_pt, L.self_pt.data(), L.self_pt.size() * 4))) return r;
+    if ((r = up(tgt_orig, L.tgt_orig.data(), L.tgt_orig.size() * 4))) return r;
+    if ((r = up(desc, L.desc.data(), L.desc.size() * sizeof(TLeaf)))) return r;
+    if ((r = up(ent, L.ent.data(), L.ent.size() * sizeof(int2)))) return r;
+    if ((r = up(ent_sh, L.ent_sh.data(), L.ent_sh.size()))) return r;
+    if ((r = up(ent_shlo, L.ent_shlo.data(), L.ent_shlo.size() * 4))) return r;
+    if ((r = up(evl, L.evl.data(), L.evl.size() * sizeof(int4)))) return r;
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, int64_t(plan->nsm) * 8)));
+    // sources' side: the far-field grid and the stored local expansions
+    if ((r = far_grid<T, D>(plan, s, false))) return r;
+    for (int ph = 0; ph < 4; ++ph)
+        if ((r = pw_eval(&plan->pw, s, ph)) != PDMK_OK) return r;
+    // far field at the targets
+    {
+        InterpArgs<T> ia;
+        ia.grid = static_cast<const T*>(plan->d_grid);
+        ia.t_g0 = t_g0;
+        ia.t_dq = t_dq;
+        ia.nt = int(m);
+        ia.M0 = g.M[0]; ia.M1 = g.M[1]; ia.M2 = g.M[2];
+        ia.w = plan->w;
+        ia.half_w_inv2 = T(4.0 / (double(plan->w) * plan->w));
+        ia.coefW = static_cast<const T*>(plan->d_coefW);
+        ia.coefWd = static_cast<const T*>(plan->d_coefWd);
+        ia.nW = int(plan->cW.size());
+        ia.nWd = int(plan->cWd.size());
+        ia.pot = pot_far;
+        ia.gradu = gradu_far;
+        const size_t smem = sizeof(T) * 128 * 2 * D * plan->w;
+        CK(cudaFuncSetAttribute(k_interp<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_interp<T, D><<<int((m + 127) / 128), 128, smem, s>>>(ia);
+        CK(cudaGetLastError());
+    }
+    // plane-wave part: the stored local expansions at the targets
+    CK(cudaMemsetAsync(pot_pw, 0, size_t(m) * 8, s));
+    CK(cudaMemsetAsync(grad_pw, 0, size_t(m) * D * 8, s));
+    if ((r = pw_eval_points(&plan->pw, s, evl, int(L.evl.size()), tgt4a, pot_pw, grad_pw)) != PDMK_OK) return r;
+    // residual direct sum over each virtual leaf's neighbourhood
+    CK(cudaMemsetAsync(pot_near, 0, size_t(m) * 8, s));
+    CK(cudaMemsetAsync(grad_near, 0, size_t(m) * D * 8, s));
+    if (!L.desc.empty()) {
+        NearArgs<T> na;
+        na.tleaf = desc;
+        na.ntleaf = int(L.desc.size());
+        na.list = nullptr;
+        na.box_src_begin = plan->d_box_src_begin;
+        na.box_src_count = plan->d_box_src_count;
+        na.box_center = plan->d_box_center;
+        na.src4 = static_cast<const T*>(plan->d_src4);
+        na.tgt4 = tgt4;
+        na.pot = pot_near;
+        na.grad = grad_near;
+        na.inv_rc = 1.0 / g.rc;
+        na.coefA = static_cast<const T*>(plan->d_coefA);
+        na.coefB = static_cast<const T*>(plan->d_coefB);
+        na.nA = int(plan->cA.size());
+        na.nB = int(plan->cB.size());
+        na.count_in = nullptr;
+        na.src_lo = static_cast<const T*>(plan->d_src_lo);
+        na.tgt_lo = reinterpret_cast<const T*>(tgt_lo);
+        na.close_s = T(0.04);  // r < 0.2 h
+        na.ent = ent;
+        na.ent_sh = ent_sh;
+        na.ent_shlo = reinterpret_cast<const T*>(ent_shlo);
+        na.monoA = static_cast<const T*>(plan->d_monoA);
+        na.monoB = static_cast<const T*>(plan->d_monoB);
+        near_launch<T, D>(plan, na, int(L.desc.size()), s);
+        CK(cudaGetLastError());
+    }
+    (void)mixed;
+    // assembly in the caller's order
+    k_self_charges<<<blocks, 256, 0, s>>>(m, self_pt, plan->d_q_user, q_tgt);
+    CK(cudaGetLastError());
+    AssembleArgs aa;
+    aa.nt = m;
+    aa.d = D;
+    aa.tgt_orig = tgt_orig;
+    aa.self_w = self_w;
+    aa.q_tgt = q_tgt;
+    aa.pot_near = pot_near;
+    aa.grad_near = grad_near;
+    aa.pot_pw = pot_pw;
+    aa.grad_pw = grad_pw;
+    aa.pot_far = pot_far;
+    aa.gradu_far = gradu_far;
+    aa.qsum = plan->d_qsums;
+    aa.mean_coef = plan->kt.rhat0 * g.rc * g.rc / g.V;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            aa.G[i * D + j] = g.Rinv[j * D + i] * g.M[j];
+            aa.Qt[i * D + j] = g.Q[j * D + i];
+        }
+    aa.pot_out = dp;
+    aa.grad_out = dg;
+    aa.out_first = 0;
+    k_assemble<D, T><<<blocks, 256, 0, s>>>(aa);
+    CK(cudaGetLastError());
+    return PDMK_OK;
+}
+
+extern "C" int pdmk_eval_targets(pdmk_plan plan, int64_t m, const double* x, double* pot, double* grad, int where) {
+    if (!plan || m < 0 || (m > 0 && (!x || !pot))) return PDMK_ERR_BAD_ARG;
+    if (where != PDMK_HOST && where != PDMK_DEVICE) return PDMK_ERR_BAD_ARG;
+    if (!plan->ready) return PDMK_ERR_NOT_READY;
+    if (m == 0) return PDMK_OK;
+    if (m >= (int64_t(1) << 30)) return PDMK_ERR_TOO_LARGE;
+    if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+        *plan->pw.h_err = 0;
+        return PDMK_ERR_TIMEOUT;
+    }
+    const int d = plan->d;
+    std::vector<double> hx(size_t(m) * d);
+    if (where == PDMK_DEVICE) {
+        CK(cudaStreamSynchronize(plan->stream));
+        CK(cudaMemcpy(hx.data(), x, hx.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(hx.data(), x, hx.size() * sizeof(double));
+    }
+    for (double v : hx)
+        if (!std::isfinite(v)) return PDMK_ERR_NONFINITE;
+    TargetLayout L;
+    int r = build_target_layout(plan, m, hx.data(), &L);
+    if (r != PDMK_OK) return r;
+    // device scratch for this call (kept and reused while large enough)
+    const size_t ts = tsize(plan);
+    size_t need = 0;
+    auto add = [&](size_t b) { need += align256(std::max<size_t>(b, 1)); };
+    for (int k = 0; k < 3; ++k) add(size_t(m) * 4 * ts);  // tgt4, tgt4a, (t_dq below)
+    add(size_t(m) * 16);                                   // tgt_lo
+    add(size_t(m) * sizeof(int4));                         // t_g0
+    add(size_t(m) * 8);                                    // self_w
+    add(size_t(m) * 4);                                    // self_pt
+    add(size_t(m) * 4);                                    // tgt_orig
+    add(size_t(m) * 8);                                    // q_tgt
+    for (int k = 0; k < 3; ++k) { add(size_t(m) * 8); add(size_t(m) * d * 8); }  // near, pw, far
+    add(L.desc.size() * sizeof(TLeaf));
+    add(L.ent.size() * sizeof(int2));
+    add(L.ent_sh.size());
+    add(L.ent_shlo.size() * 4);
+    add(L.evl.size() * sizeof(int4));
+    const size_t out_bytes = where == PDMK_DEVICE ? 0 : size_t(m) * (1 + d) * 8;
+    need += align256(out_bytes + 1);
+    if (need > plan->tq_cap) {
+        CK(cudaStreamSynchronize(plan->ws));
+        if (plan->tq_buf) cudaFree(plan->tq_buf);
+        plan->tq_buf = nullptr;
+        plan->tq_cap = 0;
+        if (cudaMalloc(&plan->tq_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return PDMK_ERR_OOM;
+        }
+        plan->tq_cap = need;
+    }
+    char* buf = static_cast<char*>(plan->tq_buf);
+    double* dp = pot;
+    double* dg = grad;
+    if (where != PDMK_DEVICE) {
+        dp = reinterpret_cast<double*>(buf + need - align256(out_bytes + 1));
+        dg = grad ? dp + m : nullptr;
+    }
+    CK(cudaEventRecord(plan->ev_fork, plan->stream));
+    CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
+    const bool saved_profile = plan->opts.profile != 0;
+    plan->opts.profile = 0;  // eager launches, no stage events
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    if (d == 2)
+        r = mixed ? run_eval_targets<float, 2>(plan, L, buf, dp, dg) : run_eval_targets<double, 2>(plan, L, buf, dp, dg);
+    else
+        r = mixed ? run_eval_targets<float, 3>(plan, L, buf, dp, dg) : run_eval_targets<double, 3>(plan, L, buf, dp, dg);
+    plan->opts.profile = saved_profile ? 1 : 0;
+    if (r != PDMK_OK) return r;
+    if (where != PDMK_DEVICE) {
+        CK(cudaMemcpyAsync(pot, dp, size_t(m) * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
+        if (grad) CK(cudaMemcpyAsync(grad, dg, size_t(m) * d * sizeof(double), cudaMemcpyDeviceToHost, plan->ws));
+        CK(cudaStreamSynchronize(plan->ws));
+        if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+            *plan->pw.h_err = 0;
+            return PDMK_ERR_TIMEOUT;
+        }
+    }
+    CK(cudaEventRecord(plan->ev_join, plan->ws));
+    CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));
+    return PDMK_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Quasi-periodic (Bloch) evaluation at the plan's points (Sec. 3.7); kernels and the reading
+// of the method in k_bloch.cuh.  Buffers are made on the first call after pdmk_set_sources.
+namespace {
+struct BlochBufs {
+    double *disp, *y, *tdisp, *beta, *gre, *gim, *cg, *w, *tre, *tim, *res;
+};
+// sub-buffers start on 256-byte boundaries (the complex grid needs at least 16 for cuFFT)
+size_t pad32(size_t v) { return (v + 31) & ~size_t(31); }
+BlochBufs bloch_layout(pdmk_plan plan) {
+    BlochBufs b;
+    const int d = plan->d;
+    double* p = plan->bl_buf;
+    b.disp = p; p += pad32(size_t(plan->nimg) * d);
+    b.y = p; p += pad32(size_t(plan->n) * d);
+    b.tdisp = p; p += pad32(size_t(plan->ntgt) * d);
+    b.beta = p; p += 32;
+    b.gre = p; p += pad32(size_t(plan->ncell));
+    b.gim = p; p += pad32(size_t(plan->ncell));
+    b.cg = p; p += pad32(2 * size_t(plan->ncell));
+    b.w = p; p += pad32(size_t(plan->ncell));
+    b.tre = p; p += pad32(size_t(plan->ncell));
+    b.tim = p; p += pad32(size_t(plan->ncell));
+    b.res = p;  // 6 x (ntgt + ntgt d): near, plane-wave and far parts, real and imaginary
+    return b;
+}
+size_t bloch_doubles(pdmk_plan plan) {
+    const int d = plan->d;
+    return pad32(size_t(plan->nimg) * d) + pad32(size_t(plan->n) * d) + pad32(size_t(plan->ntgt) * d) + 32 +
+           5 * pad32(size_t(plan->ncell)) + pad32(2 * size_t(plan->ncell)) + 6 * size_t(plan->ntgt) * (1 + d);
+}
+}  // namespace
+
+static int bloch_setup(pdmk_plan plan) {
+    if (plan->bl_ready) return PDMK_OK;
+    const int d = plan->d;
+    const Geometry& g = plan->g;
+    double* p = nullptr;
+    int r = dalloc(plan, plan->src_allocs, &p, bloch_doubles(plan));
+    if (r != PDMK_OK) return r;
+    plan->bl_buf = p;
+    BlochBufs b = bloch_layout(plan);
+    std::vector<double> tdisp(size_t(plan->ntgt) * d);
+    // the copy of each target's own point: the original's position in the sorted sources
+    {
+        std::vector<int64_t> copy_of(static_cast<size_t>(plan->n), -1);
+        for (int64_t j = 0; j < plan->nimg; ++j)
+            if (plan->h_src_is_orig[size_t(j)]) copy_of[size_t(plan->h_src_orig[size_t(j)])] = j;
+        std::vector<int> torig(static_cast<size_t>(plan->ntgt));
+        CK(cudaMemcpy(torig.data(), plan->d_tgt_orig, torig.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int64_t t = 0; t < plan->ntgt; ++t) {
+            const int64_t j = copy_of[size_t(torig[size_t(t)])];
+            for (int a = 0; a < d; ++a) tdisp[size_t(t) * d + a] = j >= 0 ? plan->h_src_disp[size_t(j) * d + a] : 0.0;
+        }
+    }
+    CK(cudaMemcpy(b.disp, plan->h_src_disp.data(), plan->h_src_disp.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.y, plan->h_y.data(), plan->h_y.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b.tdisp, tdisp.data(), tdisp.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (!plan->bl_tab) {
+        // the smoothing transform's quadrature (hat-w(x) = sum glw cos(x glx)) and the window's
+        // transform at every index of each axis
+        std::vector<double> tab;
+        const KernelTables& kt = plan->kt;
+        for (size_t i = 0; i < kt.gl_x.size(); ++i) tab.push_back(kt.gl_x[i]);
+        for (size_t i = 0; i < kt.gl_x.size(); ++i) tab.push_back(kt.gl_w[i] * kt.gl_psi[i] / kt.psi.c0);
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < g.M[i]; ++j) {
+                const int m = j <= g.M[i] / 2 ? j : j - g.M[i];
+                tab.push_back(plan->wt.ft(double(m) / g.M[i]));
+            }
+        double* t = nullptr;
+        if ((r = dalloc(plan, plan->plan_allocs, &t, tab.size())) != PDMK_OK) return r;
+        CK(cudaMemcpy(t, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+        plan->bl_tab = t;
+    }
+    if (!plan->bl_have_fft) {
+        cufftResult fr = d == 2 ? cufftPlan2d(&plan->bl_fft, g.M[1], g.M[0], CUFFT_Z2Z)
+                                : cufftPlan3d(&plan->bl_fft, g.M[2], g.M[1], g.M[0], CUFFT_Z2Z);
+        if (fr != CUFFT_SUCCESS) {
+            plan_set_msg(plan, "cufft plan failure");
+            return PDMK_ERR_CUDA;
+        }
+        plan->bl_have_fft = true;
+    }
+    CKFFT(cufftSetStream(plan->bl_fft, plan->ws));
+    plan->bl_ready = true;
+    return PDMK_OK;
+}
+
+template <typename T, int D>
+static int run_eval_bloch(pdmk_plan plan, const double* beta_host, double* dp, double* dg) {
+    cudaStream_t s = plan->ws;
+    const Geometry& g = plan->g;
+    int r;
+    if ((r = bloch_setup(plan)) != PDMK_OK) return r;
+    BlochBufs b = bloch_layout(plan);
+    const int64_t nt = plan->ntgt;
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((std::max(plan->nimg, plan->ncell) + 255) / 256,
+                                                                  int64_t(plan->nsm) * 16)));
+    CK(cudaMemcpyAsync(b.beta, beta_host, D * sizeof(double), cudaMemcpyHostToDevice, s));
+    // weights at the shifted modes
+    {
+        BlochWeightArgs wa;
+        wa.d = D;
+        wa.M0 = g.M[0]; wa.M1 = g.M[1]; wa.M2 = g.M[2];
+        for (int i = 0; i < D * D; ++i) wa.Rinv[i] = g.Rinv[i];
+        for (int i = 0; i < 3; ++i) {
+            wa.beta_o[i] = 0;
+            if (i < D)
+                for (int k = 0; k < D; ++k) wa.beta_o[i] += g.Q[i * D + k] * beta_host[k];
+        }
+        wa.rc = g.rc;
+        wa.c = plan->c;
+        wa.V = g.V;
+        wa.ngl = int(plan->kt.gl_x.size());
+        wa.glx = plan->bl_tab;
+        wa.glw = plan->bl_tab + wa.ngl;
+        wa.ph = plan->bl_tab + 2 * wa.ngl;
+        k_bloch_weights<<<blocks, 256, 0, s>>>(wa, b.w);
+        CK(cudaGetLastError());
+    }
+    double* res = b.res;
+    const size_t sp = size_t(nt), sg = size_t(nt) * D;
+    double* pn[2] = {res, res + sp};
+    double* gn[2] = {res + 2 * sp, res + 2 * sp + sg};
+    double* pp[2] = {res + 2 * sp + 2 * sg, res + 3 * sp + 2 * sg};
+    double* gp[2] = {res + 4 * sp + 2 * sg, res + 4 * sp + 3 * sg};
+    double* pf[2] = {res + 4 * sp + 4 * sg, res + 5 * sp + 4 * sg};
+    double* gf[2] = {res + 6 * sp + 4 * sg, res + 6 * sp + 5 * sg};
+    T* src4 = static_cast<T*>(plan->d_src4);
+    T* sdq = static_cast<T*>(plan->d_pt_dq);
+    for (int part = 0; part < 2; ++part) {
+        k_bloch_charges<T><<<blocks, 256, 0, s>>>(part, D, plan->d_q_user, b.beta, plan->nimg, plan->d_src_orig,
+                                                   b.disp, src4, plan->nspread, plan->d_spread_orig, b.y, sdq,
+                                                   plan->ntgt, plan->d_tgt_orig, static_cast<T*>(plan->d_tgt4));
+        CK(cudaGetLastError());
+        // far field: spread this part of the complex strengths
+        if ((r = spread_fold<T, D>(plan, s, part == 0 ? b.gre : b.gim, false))) return r;
+        // near field with this part of the phased copies: plane waves and the residual sum
+        for (int ph = 0; ph < 5; ++ph)
+            if ((r = pw_eval(&plan->pw, s, ph)) != PDMK_OK) return r;
+        if (plan->pw.active) {
+            CK(cudaMemcpyAsync(pp[part], plan->pw.d_pot, sp * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(gp[part], plan->pw.d_grad, sg * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        CK(cudaMemsetAsync(pn[part], 0, sp * sizeof(double), s));
+        CK(cudaMemsetAsync(gn[part], 0, sg * sizeof(double), s));
+        if (plan->nnear > 0) {
+            NearArgs<T> na;
+            na.tleaf = plan->d_tleaf;
+            na.ntleaf = plan->nnear;
+            na.list = plan->d_list;
+            na.box_src_begin = plan->d_box_src_begin;
+            na.box_src_count = plan->d_box_src_count;
+            na.box_center = plan->d_box_center;
+            na.src4 = src4;
+            na.tgt4 = static_cast<const T*>(plan->d_tgt4);
+            na.pot = pn[part];
+            na.grad = gn[part];
+            na.inv_rc = 1.0 / g.rc;
+            na.coefA = static_cast<const T*>(plan->d_coefA);
+            na.coefB = static_cast<const T*>(plan->d_coefB);
+            na.nA = int(plan->cA.size());
+            na.nB = int(plan->cB.size());
+            na.count_in = nullptr;
+            na.src_lo = static_cast<const T*>(plan->d_src_lo);
+            na.tgt_lo = static_cast<const T*>(plan->d_tgt_lo);
+            na.close_s = T(0.04);
+            na.ent = plan->d_ent;
+            na.ent_sh = static_cast<const T*>(plan->d_ent_sh);
+            na.ent_shlo = static_cast<const T*>(plan->d_ent_shlo);
+            na.monoA = static_cast<const T*>(plan->d_monoA);
+            na.monoB = static_cast<const T*>(plan->d_monoB);
+            near_launch<T, D>(plan, na, plan->nnear, s);
+            CK(cudaGetLastError());
+        }
+    }
+    // the smooth part: complex transform, scaling at k_m + beta, inverse, interpolation
+    k_bloch_interleave<<<blocks, 256, 0, s>>>(b.gre, b.gim, b.cg, plan->ncell);
+    CK(cudaGetLastError());
+    CKFFT(cufftExecZ2Z(plan->bl_fft, (cufftDoubleComplex*)b.cg, (cufftDoubleComplex*)b.cg, CUFFT_FORWARD));
+    k_bloch_scale<<<blocks, 256, 0, s>>>(b.cg, b.w, plan->ncell);
+    CK(cudaGetLastError());
+    CKFFT(cufftExecZ2Z(plan->bl_fft, (cufftDoubleComplex*)b.cg, (cufftDoubleComplex*)b.cg, CUFFT_INVERSE));
+    T* tre = reinterpret_cast<T*>(b.tre);
+    T* tim = reinterpret_cast<T*>(b.tim);
+    k_bloch_deinterleave<T><<<blocks, 256, 0, s>>>(b.cg, tre, tim, plan->ncell);
+    CK(cudaGetLastError());
+    for (int part = 0; part < 2 && nt > 0; ++part) {
+        InterpArgs<T> ia;
+        ia.grid = part == 0 ? tre : tim;
+        ia.t_g0 = plan->d_t_g0;
+        ia.t_dq = static_cast<const T*>(plan->d_t_dq);
+        ia.nt = int(nt);
+        ia.M0 = g.M[0]; ia.M1 = g.M[1]; ia.M2 = g.M[2];
+        ia.w = plan->w;
+        ia.half_w_inv2 = T(4.0 / (double(plan->w) * plan->w));
+        ia.coefW = static_cast<const T*>(plan->d_coefW);
+        ia.coefWd = static_cast<const T*>(plan->d_coefWd);
+        ia.nW = int(plan->cW.size());
+        ia.nWd = int(plan->cWd.size());
+        ia.pot = pf[part];
+        ia.gradu = gf[part];
+        const size_t smem = sizeof(T) * 128 * 2 * D * plan->w;
+        CK(cudaFuncSetAttribute(k_interp<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_interp<T, D><<<int((nt + 127) / 128), 128, smem, s>>>(ia);
+        CK(cudaGetLastError());
+    }
+    // the plan's own (real) charges again for later evaluations
+    if ((r = set_charges_device(plan, false)) != PDMK_OK) return r;
+    BlochAssembleArgs aa;
+    aa.nt = nt;
+    aa.tgt_orig = plan->d_tgt_orig;
+    aa.self_w = plan->d_self_w;
+    aa.q = plan->d_q_user;
+    aa.tdisp = b.tdisp;
+    aa.y = b.y;
+    aa.beta = b.beta;
+    for (int part = 0; part < 2; ++part) {
+        aa.pn[part] = pn[part];
+        aa.gn[part] = gn[part];
+        aa.pp[part] = plan->pw.active ? pp[part] : nullptr;
+        aa.gp[part] = plan->pw.active ? gp[part] : nullptr;
+        aa.pf[part] = pf[part];
+        aa.gf[part] = gf[part];
+    }
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            aa.G[i * D + j] = g.Rinv[j * D + i] * g.M[j];
+            aa.Qt[i * D + j] = g.Q[j * D + i];
+        }
+    aa.pot_out = dp;
+    aa.grad_out = dg;
+    aa.out_first = plan->out_first;
+    k_assemble_bloch<D><<<blocks, 256, 0, s>>>(aa);
+    CK(cudaGetLastError());
+    return PDMK_OK;
+}
+
+extern "C" int pdmk_eval_bloch(pdmk_plan plan, const double* beta, double* pot, double* grad, int where) {
+    if (!plan || !beta || !pot) return PDMK_ERR_BAD_ARG;
+    if (where != PDMK_HOST && where != PDMK_DEVICE) return PDMK_ERR_BAD_ARG;
+    if (!plan->ready) return PDMK_ERR_NOT_READY;
+    const int d = plan->d;
+    for (int a = 0; a < d; ++a)
+        if (!std::isfinite(beta[a])) return PDMK_ERR_NONFINITE;
+    {
+        // beta must not be a reciprocal-lattice vector (the periodic case, where k = 0 is singular)
+        const Geometry& g = plan->g;
+        double bo[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i)
+            for (int k = 0; k < d; ++k) bo[i] += g.Q[i * d + k] * beta[k];
+        bool integral = true;
+        for (int i = 0; i < d; ++i) {
+            double mi = 0;  // beta = 2 pi R^{-T} m  <=>  m = R^T beta / (2 pi)
+            for (int k = 0; k < d; ++k) mi += g.R[k * d + i] * bo[k];
+            mi /= 2.0 * kPi;
+            integral &= std::fabs(mi - std::nearbyint(mi)) < 1e-9;
+        }
+        if (integral) {
+            plan_set_msg(plan, "beta is a reciprocal-lattice vector: use pdmk_eval (periodic)");
+            return PDMK_ERR_BAD_ARG;
+        }
+    }
+    if (plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+        *plan->pw.h_err = 0;
+        return PDMK_ERR_TIMEOUT;
+    }
+    const int64_t m = plan->n_out;
+    double* dp = pot;
+    double* dg = grad;
+    double* stage = nullptr;
+    if (where != PDMK_DEVICE) {
+        if (cudaMalloc(&stage, sizeof(double) * size_t(std::max<int64_t>(m, 1)) * 2 * (1 + d)) != cudaSuccess) {
+            cudaGetLastError();
+            return PDMK_ERR_OOM;
+        }
+        dp = stage;
+        dg = grad ? stage + 2 * m : nullptr;
+    }
+    CK(cudaEventRecord(plan->ev_fork, plan->stream));
+    CK(cudaStreamWaitEvent(plan->ws, plan->ev_fork, 0));
+    const bool saved_profile = plan->opts.profile != 0, saved_count = plan->count_pending;
+    plan->opts.profile = 0;
+    plan->count_pending = false;
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    int r;
+    if (d == 2) r = mixed ? run_eval_bloch<float, 2>(plan, beta, dp, dg) : run_eval_bloch<double, 2>(plan, beta, dp, dg);
+    else r = mixed ? run_eval_bloch<float, 3>(plan, beta, dp, dg) : run_eval_bloch<double, 3>(plan, beta, dp, dg);
+    plan->opts.profile = saved_profile ? 1 : 0;
+    plan->count_pending = saved_count;
+    if (r == PDMK_OK && where != PDMK_DEVICE) {
+        if (cudaMemcpyAsync(pot, dp, size_t(m) * 2 * sizeof(double), cudaMemcpyDeviceToHost, plan->ws) != cudaSuccess ||
+            (grad && cudaMemcpyAsync(grad, dg, size_t(m) * 2 * d * sizeof(double), cudaMemcpyDeviceToHost,
+                                     plan->ws) != cudaSuccess) ||
+            cudaStreamSynchronize(plan->ws) != cudaSuccess)
+            r = PDMK_ERR_CUDA;
+        if (r == PDMK_OK && plan->pw.h_err && *reinterpret_cast<volatile int*>(plan->pw.h_err)) {
+            *plan->pw.h_err = 0;
+            r = PDMK_ERR_TIMEOUT;
+        }
+    }
+    if (stage) {
+        cudaStreamSynchronize(plan->ws);
+        cudaFree(stage);
+    }
     if (r != PDMK_OK) return r;
     CK(cudaEventRecord(plan->ev_join, plan->ws));
     CK(cudaStreamWaitEvent(plan->stream, plan->ev_join, 0));

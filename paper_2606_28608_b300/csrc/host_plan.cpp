@@ -1003,46 +1003,52 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     return PDMK_OK;
 }
 
-void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
+void box_direct_list(const Tree& t, int b, std::vector<int>* out) {
     const int d = t.d;
     int nn = 1;
     for (int a = 0; a < d; ++a) nn *= 3;
+    std::vector<int>& lst = *out;
+    lst.clear();
+    auto add_leaves_below = [&](int x, auto&& self) -> void {
+        if (t.is_leaf(x)) {
+            if (t.src_end[x] > t.src_begin[x]) lst.push_back(x);
+            return;
+        }
+        for (int c = 0; c < (1 << d); ++c) self(t.child0[x] + c, self);
+    };
+    // box lookup by (level, coords) through the colleague structure: walk from the box's
+    // ancestors, which always exist
+    for (int o = 0; o < nn; ++o) {
+        int X = t.colleague[size_t(b) * nn + o];
+        if (X >= 0) {
+            add_leaves_below(X, add_leaves_below);
+            continue;
+        }
+        // no same-level box here: the region is covered by a coarser leaf
+        int64_t c[3] = {0, 0, 0};
+        int r = o;
+        for (int a = 0; a < d; ++a) {
+            c[a] = t.coord[size_t(b) * d + a] + (r % 3) - 1;
+            r /= 3;
+        }
+        int found = t.locate(t.level[b], c);
+        if (found >= 0 && !t.is_leaf(found)) found = -1;
+        if (found >= 0 && t.src_end[found] > t.src_begin[found]) lst.push_back(found);
+    }
+    std::sort(lst.begin(), lst.end());
+    lst.erase(std::unique(lst.begin(), lst.end()), lst.end());
+}
+
+void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
     dl->tleaf.clear();
     dl->list_begin.assign(1, 0);
     dl->list.clear();
     int64_t np = 0;
-    // box lookup by (level, coords) through the colleague structure: walk from the leaf's
-    // ancestors, which always exist
+    std::vector<int> lst;
     for (int b = 0; b < int(t.level.size()); ++b) {
         if (!t.is_leaf(b) || t.tgt_end[b] == t.tgt_begin[b]) continue;
         dl->tleaf.push_back(b);
-        std::vector<int> lst;
-        auto add_leaves_below = [&](int x, auto&& self) -> void {
-            if (t.is_leaf(x)) {
-                if (t.src_end[x] > t.src_begin[x]) lst.push_back(x);
-                return;
-            }
-            for (int c = 0; c < (1 << d); ++c) self(t.child0[x] + c, self);
-        };
-        for (int o = 0; o < nn; ++o) {
-            int X = t.colleague[size_t(b) * nn + o];
-            if (X >= 0) {
-                add_leaves_below(X, add_leaves_below);
-                continue;
-            }
-            // no same-level box here: the region is covered by a coarser leaf
-            int64_t c[3] = {0, 0, 0};
-            int r = o;
-            for (int a = 0; a < d; ++a) {
-                c[a] = t.coord[size_t(b) * d + a] + (r % 3) - 1;
-                r /= 3;
-            }
-            int found = t.locate(t.level[b], c);
-            if (found >= 0 && !t.is_leaf(found)) found = -1;
-            if (found >= 0 && t.src_end[found] > t.src_begin[found]) lst.push_back(found);
-        }
-        std::sort(lst.begin(), lst.end());
-        lst.erase(std::unique(lst.begin(), lst.end()), lst.end());
+        box_direct_list(t, b, &lst);
         int64_t nsrc = 0;
         for (int x : lst) nsrc += t.src_end[x] - t.src_begin[x];
         np += nsrc * (t.tgt_end[b] - t.tgt_begin[b]);

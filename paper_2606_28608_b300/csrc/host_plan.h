@@ -138,6 +138,8 @@ struct DirectLists {
     std::vector<int> list;            // source leaf box ids
 };
 void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs);
+// the source leaves meeting the 3^d neighbourhood of box b (any box, leaf or not), sorted
+void box_direct_list(const Tree& t, int b, std::vector<int>* out);
 
 // default (kappa, n_s) from the paper's Table 1
 void table1_defaults(int d, double eps, const Geometry* g_or_null, const double* Lcol,

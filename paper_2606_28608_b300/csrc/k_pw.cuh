@@ -31,6 +31,11 @@ struct PwPlan {
     int* d_err = nullptr;   // its device address
     int wait_test = 0;      // test hook: make the first dependent downward item wait forever
     int nsm = 1;            // SMs of the plan's device (grid sizing)
+    std::vector<int> lslot;  // per box: slot of its local expansion in the local array, or -1
+    std::vector<unsigned char> local_full;  // per box: the slot holds its complete local expansion
+                                            // after the downward pass (every receiving non-leaf box,
+                                            // and the target leaves unless the 2D single-launch pass
+                                            // keeps theirs in shared memory)
     std::vector<void*> allocs;
     void* impl = nullptr;
 };
@@ -44,6 +49,12 @@ int pw_set_charges(PwPlan* pw, cudaStream_t stream);
 // phase 0: leaf moments + upward merges; 1: outgoing plane waves; 2: translation +
 // incoming; 3: downward pass; 4: evaluation at leaf targets
 int pw_eval(PwPlan* pw, cudaStream_t stream, int phase);
+// Evaluation of stored local expansions at arbitrary points (after phases 0-3 of pw_eval):
+// list entries (local slot, first point, count, level of the box) over points given relative
+// to their box's centre (d_pts4: 4 values of the plan's precision per point); writes pot (one
+// per point) and grad (d per point).
+int pw_eval_points(PwPlan* pw, cudaStream_t stream, const int4* d_list, int nlist, const void* d_pts4, double* pot,
+                   double* grad);
 void pw_free_sources(PwPlan* pw);
 void pw_free(PwPlan* pw);
 

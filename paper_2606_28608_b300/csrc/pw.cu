@@ -109,54 +109,6 @@ __global__ void __launch_bounds__(128) k_leaf_moments(const int4* __restrict__ l
     }
 }
 
-// 3D leaf moments with a compile-time order P: one block of P^2 threads per leaf, thread
-// (m1, m2) accumulates Q[m0][m1][m2] for every m0 in registers:
-//   Q[m0][m1][m2] = sum_s (q_s T_m1(t1_s) T_m2(t2_s)) T_m0(t0_s)
-// with the sources' Chebyshev rows staged in shared memory 32 at a time.
-template <typename T, int P>
-__global__ void __launch_bounds__(P * P, 1) k_leaf_moments3d_p(const int4* __restrict__ leaves,
-                                                            const T* __restrict__ src4, T* __restrict__ Q,
-                                                            double inv_rc) {
-    constexpr int PP = P * P, NB = 32;
-    __shared__ T basis[NB][3][P];
-    __shared__ T qv[NB];
-    const int4 lf = leaves[blockIdx.x];  // (first source, count, q slot, level)
-    const T scale = T(2.0 * inv_rc * double(1LL << lf.w));  // t = 2 (y - c)/h
-    const int tid = threadIdx.x, m1 = tid / P, m2 = tid % P;
-    T acc[P];
-#pragma unroll
-    for (int m0 = 0; m0 < P; ++m0) acc[m0] = T(0);
-    for (int s0 = 0; s0 < lf.y; s0 += NB) {
-        const int ns = min(NB, lf.y - s0);
-        __syncthreads();
-        if (tid < ns * 3) {
-            const int s = tid / 3, ax = tid - 3 * s;
-            const T* y = src4 + size_t(lf.x + s0 + s) * 4;
-            const T t = y[ax] * scale;
-            T tm1 = T(1), tm = t;
-            basis[s][ax][0] = T(1);
-            basis[s][ax][1] = t;
-#pragma unroll
-            for (int m = 2; m < P; ++m) {
-                const T tn = fma(T(2) * t, tm, -tm1);
-                basis[s][ax][m] = tn;
-                tm1 = tm;
-                tm = tn;
-            }
-            if (ax == 0) qv[s] = y[3];
-        }
-        __syncthreads();
-        for (int s = 0; s < ns; ++s) {
-            const T w = qv[s] * basis[s][1][m1] * basis[s][2][m2];
-#pragma unroll
-            for (int m0 = 0; m0 < P; ++m0) acc[m0] = fma(w, basis[s][0][m0], acc[m0]);
-        }
-    }
-    T* Qb = Q + size_t(lf.z) * (PP * P);
-#pragma unroll
-    for (int m0 = 0; m0 < P; ++m0) Qb[m0 * PP + tid] = acc[m0];
-}
-
 // 3D leaf moments as a small GEMM per leaf (the transpose of k_leaf_eval3d_gemm): one block of
 // 256 threads per leaf, sources taken 16 at a time.  For a chunk, X[s][m0] = T_m0(t0_s) and
 // B[s][m1 m2] = q_s T_m1(t1_s) T_m2(t2_s) are staged in shared memory (B formed by all threads,
@@ -2450,6 +2402,11 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         const bool inbox = !t.is_leaf(b) && has_tgt(b);
         if (inbox || (t.level[b] >= 1 && has_tgt(b))) lslot[b] = nloc++;
     }
+    pw->lslot = lslot;
+    pw->local_full.assign(size_t(nb), 0);
+    const bool leaves_in_smem = d == 2 && direct2d_orders(I->dims, pw->mixed);
+    for (int b = 0; b < nb; ++b)
+        pw->local_full[b] = lslot[b] >= 0 && (!t.is_leaf(b) || !leaves_in_smem);
     for (int b = 0; b < nb; ++b) {
         if (t.is_leaf(b) || !has_tgt(b)) continue;
         inl.push_back(lslot[b]);
@@ -2906,7 +2863,33 @@ int pw_eval(PwPlan* pw, cudaStream_t s, int phase) {
     return pw->mixed ? pw_eval_t<float, 3>(pw, s, phase) : pw_eval_t<double, 3>(pw, s, phase);
 }
 
+int pw_eval_points(PwPlan* pw, cudaStream_t s, const int4* d_list, int nlist, const void* d_pts4, double* pot,
+                   double* grad) {
+    if (!pw->active || nlist <= 0) return PDMK_OK;
+    PwImpl* I = impl(pw);
+    const PwDims& pd = I->dims;
+    const double inv_rc = 1.0 / I->rc;
+    auto run = [&](auto tag, auto dtag) {
+        using T = decltype(tag);
+        constexpr int D = decltype(dtag)::value;
+        const size_t sm = sizeof(T) * 32 * 2 * D * pd.p;
+        cudaFuncSetAttribute(k_leaf_eval<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        k_leaf_eval<T, D><<<nlist, 32, sm, s>>>(d_list, static_cast<const T*>(I->d_L), static_cast<const T*>(d_pts4),
+                                                pot, grad, pd, inv_rc);
+    };
+    if (pw->d == 2) {
+        if (pw->mixed) run(float(), std::integral_constant<int, 2>());
+        else run(double(), std::integral_constant<int, 2>());
+    } else {
+        if (pw->mixed) run(float(), std::integral_constant<int, 3>());
+        else run(double(), std::integral_constant<int, 3>());
+    }
+    return cudaGetLastError() == cudaSuccess ? PDMK_OK : PDMK_ERR_CUDA;
+}
+
 void pw_free_sources(PwPlan* pw) {
+    pw->lslot.clear();
+    pw->local_full.clear();
     for (void* p : pw->allocs) cudaFree(p);
     pw->allocs.clear();
     pw->device_bytes = 0;

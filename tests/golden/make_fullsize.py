@@ -2,7 +2,7 @@
 potential and gradient at a seeded sample of targets of each full-size synthetic workload.
 It calls only the oracle and the seeded input generators.
 
-    python tests/golden/make_fullsize.py [triclinic3d_4m] [water_333k] [batched_256]
+    python tests/golden/make_fullsize.py [triclinic3d_4m] [water_333k] [batched_256] [oblique2d_200k]
 
 Each output file holds, besides the values, the sampled indices and the sampled inputs
 (positions and charges), which the tests compare against a fresh generation to make sure
@@ -52,14 +52,21 @@ def water_333k():
 
 
 def batched_256():
+    # 64 seeded targets per cell: enough to hold every cell's relative L2 error to eps
     cells = W.batched_cells(256)
     out = []
     for c, g in enumerate(cells):
-        out.append(one_cell(g, sample(len(g["q"]), 8, 1000 + c)))
+        out.append(one_cell(g, sample(len(g["q"]), 64, 1000 + c)))
     return dict(workload="batched_cells(256)", oracle="ewald, tol 1e-15", cells=out)
 
 
-MAKERS = {"triclinic3d_4m": triclinic3d_4m, "water_333k": water_333k, "batched_256": batched_256}
+def oblique2d_200k():
+    g = W.oblique2d_clusters(200_000)
+    return dict(workload="oblique2d_clusters(200_000)", oracle="ewald, tol 1e-15", cells=[one_cell(g, sample(len(g["q"]), 64, 23))])
+
+
+MAKERS = {"triclinic3d_4m": triclinic3d_4m, "water_333k": water_333k, "batched_256": batched_256,
+          "oblique2d_200k": oblique2d_200k}
 
 if __name__ == "__main__":
     names = sys.argv[1:] or list(MAKERS)
