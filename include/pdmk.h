@@ -89,6 +89,12 @@ typedef struct {
                        values, is cached per (d, precision, eps, floor(log2 n)) for the process,
                        so later plans of similar size reuse it without timing.  The chosen values
                        are reported by pdmk_get_info. */
+    int root_mode;  /* 0: a cubic (square) cell with an integer kappa >= 3 takes the periodic root
+                       of Remark 3.3: the root grid is the cell itself, no image sources are
+                       made, and neighbours across the faces are virtual copies shifted by
+                       L n, n in {-1, 0, 1}^d (pdmk_get_info reports n_images = n).  Any other
+                       cell takes the multi-cube root with its halo of images (Sec. 3.3-3.4).
+                       1: always the multi-cube root with images. */
 } pdmk_opts;
 
 /* Fills *opts with the defaults (all fields "auto", FP64, neutrality allowed). */

@@ -30,7 +30,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_double), ("n_s", ctypes.c_int), ("precision", ctypes.c_int),
                 ("window_w", ctypes.c_int), ("n_proxy", ctypes.c_int), ("n_pw", ctypes.c_int),
                 ("max_depth", ctypes.c_int), ("neutrality", ctypes.c_int), ("profile", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("wait_test", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("wait_test", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("root_mode", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -169,7 +170,7 @@ class Plan:
     def __init__(self, L, eps: float, *, precision: str = "fp64", kappa: float = 0.0, n_s: int = 0,
                  window_w: int = 0, n_proxy: int = 0, n_pw: int = 0, max_depth: int = -1,
                  neutrality: int = 1, profile: bool = False, stream=None, wait_test: int = 0,
-                 autotune: bool = False):
+                 autotune: bool = False, root_mode: int = 0):
         L = np.ascontiguousarray(np.asarray(L, dtype=np.float64))
         self.d = L.shape[0]
         self._L = L
@@ -194,6 +195,7 @@ class Plan:
         o.stream = stream or None
         o.wait_test = int(wait_test)
         o.autotune = 1 if autotune else 0
+        o.root_mode = int(root_mode)
         self.opts = o
         Lc = np.ascontiguousarray(L.T)  # column-major
         h = ctypes.c_void_p()

@@ -243,6 +243,7 @@ extern "C" void pdmk_default_opts(pdmk_opts* o) {
     o->stream = nullptr;
     o->wait_test = 0;
     o->autotune = 0;
+    o->root_mode = 0;
 }
 
 extern "C" const char* pdmk_strerror(int code) {
@@ -588,6 +589,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     plan->max_depth = plan->opts.max_depth < 0 ? 30 : std::min(plan->opts.max_depth, 30);
     rc = make_geometry(d, L, plan->kappa, plan->c, &plan->g);
     if (rc != PDMK_OK) { delete plan; return rc; }
+    if (plan->opts.root_mode == 0) make_periodic_root(&plan->g, plan->kappa);  // cubic cells
     // window width: ceil(2c/pi) makes the window's transform at the band edge equal its own
     // edge value; two more points keep the far-field gradient (a derivative) within eps too
     plan->w = plan->opts.window_w > 0 ? plan->opts.window_w : int(std::ceil(2.0 * plan->c / kPi - 1e-9)) + 2;
@@ -808,6 +810,20 @@ static int set_charges_device(pdmk_plan plan, bool check_neutral) {
     return pw_set_charges(&plan->pw, plan->ws);
 }
 
+// the caller-frame lattice vector L n of a direct-list shift code (zero without a periodic root)
+static void lattice_shift(const Geometry& g, int code, double* out) {
+    const int d = g.d;
+    int n[3];
+    shift_of(code, n);
+    double v[3] = {0, 0, 0};
+    for (int i = 0; i < d; ++i)
+        for (int k = 0; k < d; ++k) v[i] += g.R[i * d + k] * n[k];
+    for (int i = 0; i < d; ++i) {
+        out[i] = 0;
+        for (int k = 0; k < d; ++k) out[i] += g.Q[k * d + i] * v[k];
+    }
+}
+
 // Sources (n_src, charges q) and, if m > 0, separate targets x (m points): the plan is built
 // on the union, the targets being points of charge 0 (they add nothing to any stage and have
 // no self term), and the evaluation writes the m target outputs only.
@@ -1011,8 +1027,9 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         for (int64_t e = dl.list_begin[k]; e < dl.list_begin[k + 1]; ++e) {
             const int sb = dl.list[e];
             ent[e] = make_int2(bsb[sb], bsc[sb]);
-            double du[3] = {0, 0, 0}, sht[3];
-            for (int a = 0; a < d; ++a) du[a] = Cu[size_t(sb) * d + a] - Cu[size_t(tb) * d + a];
+            double du[3] = {0, 0, 0}, sht[3], Ln[3] = {0, 0, 0};
+            lattice_shift(g, dl.shift[e], Ln);
+            for (int a = 0; a < d; ++a) du[a] = Cu[size_t(sb) * d + a] + Ln[a] - Cu[size_t(tb) * d + a];
             to_tree(du, sht);
             for (int a = 0; a < d; ++a) {
                 const double sh = sht[a];
@@ -2117,18 +2134,21 @@ static int build_target_layout(pdmk_plan plan, int64_t m, const double* hx, Targ
     }
     // near-field descriptors: one group per (virtual leaf, real leaf), the virtual leaf's
     // list, shifts into the real leaf's frame; groups cut to 32 targets for the warp kernel
-    std::vector<int> lst;
+    std::vector<int> lst, lsh;
     for (int64_t k0 = 0; k0 < m;) {
         const int64_t j0 = ord[size_t(k0)];
         int64_t k1 = k0;
         while (k1 < m && vb[ord[size_t(k1)]] == vb[j0] && leaf[ord[size_t(k1)]] == leaf[j0]) ++k1;
         const int v = vb[j0], B = leaf[j0];
-        box_direct_list(t, v, &lst);
+        box_direct_list(t, v, &lst, &lsh);
         const int lb = int(L.ent.size());
-        for (int S : lst) {
+        for (size_t li = 0; li < lst.size(); ++li) {
+            const int S = lst[li];
             L.ent.push_back(make_int2(int(t.src_begin[S]), int(t.src_end[S] - t.src_begin[S])));
-            double du[3] = {0, 0, 0}, sht[3] = {0, 0, 0};
-            for (int a = 0; a < d; ++a) du[a] = plan->h_Cu[size_t(S) * d + a] - plan->h_Cu[size_t(B) * d + a];
+            double du[3] = {0, 0, 0}, sht[3] = {0, 0, 0}, Ln[3] = {0, 0, 0};
+            lattice_shift(g, lsh[li], Ln);
+            for (int a = 0; a < d; ++a)
+                du[a] = plan->h_Cu[size_t(S) * d + a] + Ln[a] - plan->h_Cu[size_t(B) * d + a];
             for (int i = 0; i < d; ++i)
                 for (int kk = 0; kk < d; ++kk) sht[i] += g.Q[i * d + kk] * du[kk];
             const size_t e = L.ent.size() - 1;

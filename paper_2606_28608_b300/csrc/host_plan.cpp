@@ -408,6 +408,25 @@ int make_geometry(int d, const double* Lc, double kappa, double c, Geometry* g) 
     return PDMK_OK;
 }
 
+bool make_periodic_root(Geometry* g, double kappa) {
+    const int d = g->d;
+    const double a = g->R[0];
+    if (!(kappa >= 3.0) || std::fabs(kappa - std::nearbyint(kappa)) > 1e-12) return false;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            const double want = i == j ? a : 0.0;
+            if (std::fabs(g->R[i * d + j] - want) > 1e-13 * a) return false;
+        }
+    const int m = int(std::nearbyint(kappa));
+    for (int i = 0; i < d; ++i) {
+        g->m[i] = m;
+        g->nroot[i] = m;
+        g->lo[i] = 0.0;
+    }
+    g->periodic_root = true;
+    return true;
+}
+
 void table1_defaults(int d, double eps, const Geometry* g, const double* Lc, double* kappa, int* n_s) {
     // paper Table 1 rows: eps = 1e-3, 1e-6, 1e-9, 1e-12
     static const double row_eps[4] = {1e-3, 1e-6, 1e-9, 1e-12};
@@ -636,7 +655,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
         }
         nvec[lev] = 0;
     };
-    rec(d - 1);
+    if (!g.periodic_root) rec(d - 1);  // a periodic root holds the originals only
     // Images in shift order, and within a shift in point order.  Each point's admissible
     // shifts are enumerated from the in-box bounds of the triangular frame (axis by axis from
     // the last, with a small slack against rounding) and then accepted by the same test with
@@ -876,7 +895,9 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
                     for (int a = 0; a < d; ++a) {
                         c[a] = P.c[a] + (r % 3) - 1;
                         r /= 3;
-                        ok &= (c[a] >= 0 && c[a] < bld.dim_at(a, P.level));
+                        const int64_t dim = bld.dim_at(a, P.level);
+                        if (g.periodic_root) c[a] = (c[a] + dim) % dim;  // neighbours across the faces
+                        ok &= (c[a] >= 0 && c[a] < dim);
                     }
                     if (!ok) continue;
                     int X = bld.find(P.level, c);
@@ -918,6 +939,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     for (int k = 0; k < nbtot; ++k) newid[order[k]] = k;
     t->d = d;
     for (int a = 0; a < 3; ++a) t->nroot[a] = a < d ? g.nroot[a] : 1;
+    t->periodic = g.periodic_root;
     t->nlevels = int(lstart.size()) - 1;
     t->level_start = lstart;
     t->level.resize(nbtot);
@@ -954,7 +976,9 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
             for (int a = 0; a < d; ++a) {
                 c[a] = B.c[a] + (r % 3) - 1;
                 r /= 3;
-                ok &= (c[a] >= 0 && c[a] < bld.dim_at(a, B.level));
+                const int64_t dim = bld.dim_at(a, B.level);
+                if (g.periodic_root) c[a] = (c[a] + dim) % dim;
+                ok &= (c[a] >= 0 && c[a] < dim);
             }
             if (!ok) continue;
             int X = bld.find(B.level, c);
@@ -1003,40 +1027,44 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     return PDMK_OK;
 }
 
-void box_direct_list(const Tree& t, int b, std::vector<int>* out) {
+void box_direct_list(const Tree& t, int b, std::vector<int>* out, std::vector<int>* shift) {
     const int d = t.d;
     int nn = 1;
     for (int a = 0; a < d; ++a) nn *= 3;
-    std::vector<int>& lst = *out;
-    lst.clear();
-    auto add_leaves_below = [&](int x, auto&& self) -> void {
+    std::vector<std::pair<int, int>> lst;  // (leaf, shift code)
+    auto add_leaves_below = [&](int x, int code, auto&& self) -> void {
         if (t.is_leaf(x)) {
-            if (t.src_end[x] > t.src_begin[x]) lst.push_back(x);
+            if (t.src_end[x] > t.src_begin[x]) lst.push_back({x, code});
             return;
         }
-        for (int c = 0; c < (1 << d); ++c) self(t.child0[x] + c, self);
+        for (int c = 0; c < (1 << d); ++c) self(t.child0[x] + c, code, self);
     };
-    // box lookup by (level, coords) through the colleague structure: walk from the box's
-    // ancestors, which always exist
     for (int o = 0; o < nn; ++o) {
-        int X = t.colleague[size_t(b) * nn + o];
-        if (X >= 0) {
-            add_leaves_below(X, add_leaves_below);
-            continue;
-        }
-        // no same-level box here: the region is covered by a coarser leaf
         int64_t c[3] = {0, 0, 0};
         int r = o;
         for (int a = 0; a < d; ++a) {
             c[a] = t.coord[size_t(b) * d + a] + (r % 3) - 1;
             r /= 3;
         }
+        const int code = t.wrap(t.level[b], c);
+        int X = t.colleague[size_t(b) * nn + o];
+        if (X >= 0) {
+            add_leaves_below(X, code, add_leaves_below);
+            continue;
+        }
+        // no same-level box here: the region is covered by a coarser leaf
         int found = t.locate(t.level[b], c);
         if (found >= 0 && !t.is_leaf(found)) found = -1;
-        if (found >= 0 && t.src_end[found] > t.src_begin[found]) lst.push_back(found);
+        if (found >= 0 && t.src_end[found] > t.src_begin[found]) lst.push_back({found, code});
     }
     std::sort(lst.begin(), lst.end());
     lst.erase(std::unique(lst.begin(), lst.end()), lst.end());
+    out->resize(lst.size());
+    if (shift) shift->resize(lst.size());
+    for (size_t k = 0; k < lst.size(); ++k) {
+        (*out)[k] = lst[k].first;
+        if (shift) (*shift)[k] = lst[k].second;
+    }
 }
 
 void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
@@ -1044,15 +1072,17 @@ void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
     dl->list_begin.assign(1, 0);
     dl->list.clear();
     int64_t np = 0;
-    std::vector<int> lst;
+    dl->shift.clear();
+    std::vector<int> lst, sh;
     for (int b = 0; b < int(t.level.size()); ++b) {
         if (!t.is_leaf(b) || t.tgt_end[b] == t.tgt_begin[b]) continue;
         dl->tleaf.push_back(b);
-        box_direct_list(t, b, &lst);
+        box_direct_list(t, b, &lst, &sh);
         int64_t nsrc = 0;
         for (int x : lst) nsrc += t.src_end[x] - t.src_begin[x];
         np += nsrc * (t.tgt_end[b] - t.tgt_begin[b]);
         dl->list.insert(dl->list.end(), lst.begin(), lst.end());
+        dl->shift.insert(dl->shift.end(), sh.begin(), sh.end());
         dl->list_begin.push_back(int64_t(dl->list.size()));
     }
     if (pairs) *pairs = np;
@@ -1062,7 +1092,24 @@ void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
 }  // namespace pdmk
 
 namespace pdmk {
-int Tree::locate(int L, const int64_t* c) const {
+int Tree::wrap(int L, int64_t* c) const {
+    if (!periodic) return 13;
+    int code = 0, mul = 1;
+    for (int a = 0; a < d; ++a) {
+        const int64_t dim = nroot[a] << L;
+        int n = 0;
+        while (c[a] < 0) { c[a] += dim; --n; }
+        while (c[a] >= dim) { c[a] -= dim; ++n; }
+        code += (n + 1) * mul;
+        mul *= 3;
+    }
+    for (int a = d; a < 3; ++a) { code += mul; mul *= 3; }
+    return code;
+}
+
+int Tree::locate(int L, const int64_t* cin) const {
+    int64_t c[3] = {cin[0], d > 1 ? cin[1] : 0, d > 2 ? cin[2] : 0};
+    wrap(L, c);
     int64_t root = 0;
     for (int a = d - 1; a >= 0; --a) {
         int64_t ca = c[a] >> L;

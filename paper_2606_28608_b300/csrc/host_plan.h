@@ -89,7 +89,14 @@ struct Geometry {
     int nroot[3] = {1, 1, 1};    // extended domain m + 2
     double lo[3] = {0, 0, 0};    // lower corner of the extended domain
     int M[3] = {1, 1, 1};        // Fourier grid
+    // cubic cell (Remark 3.3): the root grid is the cell itself, tiled by m cubes per axis,
+    // with no halo and no image sources; neighbours across the cell's faces are the boxes on
+    // the opposite side, shifted by a lattice vector (periodic box coordinates)
+    bool periodic_root = false;
 };
+// switches a cubic (square) cell with an integer kappa >= 3 to the periodic root; returns
+// whether it did (the cell's oriented matrix must be a multiple of the identity to 1e-13)
+bool make_periodic_root(Geometry* g, double kappa);
 // returns 0 or a negative PDMK error code
 int make_geometry(int d, const double* Lcolmajor, double kappa, double c, Geometry* g);
 
@@ -109,8 +116,14 @@ struct Tree {
     double h(int l, double rc) const { return rc / double(1LL << l); }
     bool is_leaf(int b) const { return child0[b] < 0; }
     int64_t nroot[3] = {1, 1, 1};
-    // deepest existing box of level <= L containing the level-L cell c, or -1 outside
+    bool periodic = false;  // box coordinates wrap (cubic cell, Remark 3.3)
+    // deepest existing box of level <= L containing the level-L cell c, or -1 outside (with
+    // periodic coordinates, c is wrapped first)
     int locate(int L, const int64_t* c) const;
+    // the shift code (n_0 + 1) + 3 (n_1 + 1) + 9 (n_2 + 1) of the lattice vector that brings the
+    // level-L cell c into the root grid (periodic coordinates), with c replaced by the wrapped
+    // cell; 13 (no shift) otherwise
+    int wrap(int L, int64_t* c) const;
 };
 
 // A source record after image enumeration and sorting.
@@ -136,10 +149,19 @@ struct DirectLists {
     std::vector<int> tleaf;           // target leaves (boxes with targets that are leaves)
     std::vector<int64_t> list_begin;  // CSR over tleaf
     std::vector<int> list;            // source leaf box ids
+    std::vector<int> shift;           // per entry: shift code of the lattice vector added to the
+                                      // source leaf (13 = none; periodic roots only)
 };
 void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs);
-// the source leaves meeting the 3^d neighbourhood of box b (any box, leaf or not), sorted
-void box_direct_list(const Tree& t, int b, std::vector<int>* out);
+// the source leaves meeting the 3^d neighbourhood of box b (any box, leaf or not), sorted,
+// with the shift code of each (a leaf may appear once per distinct shift)
+void box_direct_list(const Tree& t, int b, std::vector<int>* out, std::vector<int>* shift);
+// lattice shift n (integer per axis) of a shift code
+inline void shift_of(int code, int* n) {
+    n[0] = code % 3 - 1;
+    n[1] = (code / 3) % 3 - 1;
+    n[2] = code / 9 - 1;
+}
 
 // default (kappa, n_s) from the paper's Table 1
 void table1_defaults(int d, double eps, const Geometry* g_or_null, const double* Lcol,
