@@ -865,6 +865,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     const Geometry& g = plan->g;
     // orient, then fractional coordinates wrapped into [0, 1)
     std::vector<double> u(size_t(n) * d);
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) {
         double xo[3] = {0, 0, 0};
         for (int i = 0; i < d; ++i)
@@ -909,6 +910,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     };
     // leaf of every sorted source
     std::vector<int> leaf_of(size_t(plan->nimg), -1);
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < st.nboxes; ++b)
         if (tree.is_leaf(b))
             for (int64_t j = tree.src_begin[b]; j < tree.src_end[b]; ++j) leaf_of[j] = b;
@@ -936,9 +938,11 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         }
     };
     std::vector<double> Cu(size_t(st.nboxes) * d);
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < st.nboxes; ++b) to_user(&tree.center[size_t(b) * d], &Cu[size_t(b) * d]);
     std::vector<double> relv(size_t(plan->nimg) * d);
     std::vector<double> src_disp(size_t(plan->nimg) * d, 0.0);
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < plan->nimg; ++j) {
         const int b = leaf_of[j];
         const int64_t o = ss.orig[j];
@@ -972,6 +976,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     std::vector<unsigned char> src4(size_t(plan->nimg) * 4 * ts, 0);
     std::vector<int> src_orig(size_t(plan->nimg));
     std::vector<float> src_lo(mixed ? size_t(plan->nimg) * 4 : 0, 0.0f);
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < plan->nimg; ++j) {
         for (int a = 0; a < d; ++a) {
             const double rel = relv[size_t(j) * d + a];
@@ -986,6 +991,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     std::vector<double> self_w(size_t(plan->ntgt));
     std::vector<int> tgt_leaf(size_t(plan->ntgt));
     std::vector<float> tgt_lo(mixed ? size_t(plan->ntgt) * 4 : 0, 0.0f);
+#pragma omp parallel for schedule(static)
     for (int64_t t = 0; t < plan->ntgt; ++t) {
         int64_t j = ss.tgt_of[t];
         int b = leaf_of[j];
@@ -1022,7 +1028,8 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     std::vector<int2> ent(dl.list.size());
     std::vector<unsigned char> ent_sh(dl.list.size() * 4 * ts, 0);
     std::vector<float> ent_shlo(mixed ? dl.list.size() * 4 : 0, 0.0f);
-    for (size_t k = 0; k < dl.tleaf.size(); ++k) {
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t k = 0; k < int64_t(dl.tleaf.size()); ++k) {
         const int tb = dl.tleaf[k];
         for (int64_t e = dl.list_begin[k]; e < dl.list_begin[k + 1]; ++e) {
             const int sb = dl.list[e];
@@ -1085,6 +1092,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     std::vector<int64_t> sp_bin(static_cast<size_t>(n));
     std::vector<int> sp_g0(size_t(n) * 3, 0);
     std::vector<double> sp_del(size_t(n) * 3, 0.0);
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) {
         int64_t bin = 0;
         for (int i = d - 1; i >= 0; --i) {
@@ -1099,13 +1107,19 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         }
         sp_bin[j] = bin;
     }
+    // points in bin order, stable within a bin (a counting sort over the bins)
     std::vector<int64_t> sp_order(static_cast<size_t>(n));
-    std::iota(sp_order.begin(), sp_order.end(), 0);
-    std::stable_sort(sp_order.begin(), sp_order.end(), [&](int64_t a, int64_t b) { return sp_bin[a] < sp_bin[b]; });
+    {
+        std::vector<int64_t> start(size_t(plan->nbins_tot) + 1, 0);
+        for (int64_t j = 0; j < n; ++j) ++start[size_t(sp_bin[j]) + 1];
+        for (int b = 0; b < plan->nbins_tot; ++b) start[size_t(b) + 1] += start[size_t(b)];
+        for (int64_t j = 0; j < n; ++j) sp_order[size_t(start[size_t(sp_bin[j])]++)] = j;
+    }
     plan->nspread = n;
     std::vector<int4> pt_g0(static_cast<size_t>(n));
     std::vector<unsigned char> pt_dq(size_t(n) * 4 * ts, 0);
     std::vector<int> sp_orig(static_cast<size_t>(n));
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n; ++k) {
         int64_t j = sp_order[k];
         pt_g0[k] = make_int4(sp_g0[j * 3], sp_g0[j * 3 + 1], sp_g0[j * 3 + 2], 0);
@@ -1132,6 +1146,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     // interpolation targets (sorted target order)
     std::vector<int4> t_g0(size_t(plan->ntgt));
     std::vector<unsigned char> t_dq(size_t(plan->ntgt) * 4 * ts, 0);
+#pragma omp parallel for schedule(static)
     for (int64_t t = 0; t < plan->ntgt; ++t) {
         int64_t j = ss.tgt_orig[t];
         int gg[3] = {0, 0, 0};

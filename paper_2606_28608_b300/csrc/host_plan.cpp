@@ -1073,17 +1073,27 @@ void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
     dl->list.clear();
     int64_t np = 0;
     dl->shift.clear();
-    std::vector<int> lst, sh;
-    for (int b = 0; b < int(t.level.size()); ++b) {
-        if (!t.is_leaf(b) || t.tgt_end[b] == t.tgt_begin[b]) continue;
-        dl->tleaf.push_back(b);
-        box_direct_list(t, b, &lst, &sh);
+    for (int b = 0; b < int(t.level.size()); ++b)
+        if (t.is_leaf(b) && t.tgt_end[b] > t.tgt_begin[b]) dl->tleaf.push_back(b);
+    // each target leaf's list on its own (in parallel), then concatenated in leaf order
+    const int64_t nl = int64_t(dl->tleaf.size());
+    std::vector<std::vector<int>> lists(static_cast<size_t>(nl)), shifts(static_cast<size_t>(nl));
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : np)
+    for (int64_t k = 0; k < nl; ++k) {
+        const int b = dl->tleaf[size_t(k)];
+        box_direct_list(t, b, &lists[size_t(k)], &shifts[size_t(k)]);
         int64_t nsrc = 0;
-        for (int x : lst) nsrc += t.src_end[x] - t.src_begin[x];
+        for (int x : lists[size_t(k)]) nsrc += t.src_end[x] - t.src_begin[x];
         np += nsrc * (t.tgt_end[b] - t.tgt_begin[b]);
-        dl->list.insert(dl->list.end(), lst.begin(), lst.end());
-        dl->shift.insert(dl->shift.end(), sh.begin(), sh.end());
-        dl->list_begin.push_back(int64_t(dl->list.size()));
+    }
+    dl->list_begin.resize(size_t(nl) + 1);
+    for (int64_t k = 0; k < nl; ++k) dl->list_begin[size_t(k) + 1] = dl->list_begin[size_t(k)] + int64_t(lists[size_t(k)].size());
+    dl->list.resize(size_t(dl->list_begin[size_t(nl)]));
+    dl->shift.resize(dl->list.size());
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nl; ++k) {
+        std::copy(lists[size_t(k)].begin(), lists[size_t(k)].end(), dl->list.begin() + dl->list_begin[size_t(k)]);
+        std::copy(shifts[size_t(k)].begin(), shifts[size_t(k)].end(), dl->shift.begin() + dl->list_begin[size_t(k)]);
     }
     if (pairs) *pairs = np;
 }
