@@ -107,3 +107,35 @@ def test_eval_adjoint_device_matches_host_and_rejects_field_gradients():
                                    P.PDMK_HOST)
     assert rc == -1 and not out.any()
     plan.close()
+
+
+def test_plan_reuse_across_steps():
+    """A molecular-dynamics-like loop (PeriodicPotential module): positions move every step,
+    the plans come from the pool (no new plan once one is free), and every step's energy
+    gradient matches a fresh computation with its own plan."""
+    torch, pp = _torch()
+    from paper_2606_28608_b300.autograd import POOL, PeriodicPotential
+    import paper_2606_28608_b300 as P
+    g = W.triclinic3d_clusters(3000, seed=19, nclusters=4)
+    mod = PeriodicPotential(g["L"], eps=1e-6, precision="mixed")
+    rng = np.random.default_rng(2)
+    y0 = g["y"].copy()
+    for step in range(3):
+        y = torch.tensor(y0 + 1e-3 * rng.standard_normal(y0.shape), device="cuda", requires_grad=True)
+        q = torch.tensor(g["q"], device="cuda")
+        pot, _ = mod(y, q)
+        (0.5 * (q * pot).sum()).backward()
+        free_after = POOL.size()
+        assert free_after >= 1  # the plan went back to the pool after backward
+        plan = P.Plan(g["L"], 1e-6, precision="mixed")
+        plan.set_sources(y.detach(), q)
+        p_ref, g_ref = plan.eval()
+        plan.close()
+        dy = y.grad.cpu().numpy()
+        want = g["q"][:, None] * g_ref
+        assert np.linalg.norm(dy - want) <= 1e-6 * np.linalg.norm(want)
+    # without a graph the plan returns to the pool at once
+    with torch.no_grad():
+        before = POOL.size()
+        mod(torch.tensor(y0, device="cuda"), torch.tensor(g["q"], device="cuda"))
+        assert POOL.size() == before
