@@ -1713,9 +1713,19 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         ia.nWd = int(plan->cWd.size());
         ia.pot = plan->d_pot_far;
         ia.gradu = plan->d_gradu_far;
-        size_t smem = sizeof(T) * 128 * 2 * D * plan->w;
-        CK(cudaFuncSetAttribute(k_interp<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        k_interp<T, D><<<int((plan->ntgt + 127) / 128), 128, smem, s>>>(ia);
+        // compile-time widths in FP32 (their per-thread y/z windows fit the static shared limit)
+        if (D == 3 && sizeof(T) == 4 && (plan->w == 8 || plan->w == 13 || plan->w == 17)) {
+            if constexpr (sizeof(T) == 4) {
+                const int nb = int((plan->ntgt + 127) / 128);
+                if (plan->w == 8) k_interp3d_w<T, 8><<<nb, 128, 0, s>>>(ia);
+                else if (plan->w == 13) k_interp3d_w<T, 13><<<nb, 128, 0, s>>>(ia);
+                else k_interp3d_w<T, 17><<<nb, 128, 0, s>>>(ia);
+            }
+        } else {
+            size_t smem = sizeof(T) * 128 * 2 * D * plan->w;
+            CK(cudaFuncSetAttribute(k_interp<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            k_interp<T, D><<<int((plan->ntgt + 127) / 128), 128, smem, s>>>(ia);
+        }
         ++plan->launches;
         CK(cudaGetLastError());
     }

@@ -426,6 +426,82 @@ __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t
         out[i] = B(in[i]);
 }
 
+// 3D interpolation with a compile-time window width W, a thread per target: the x-axis
+// window values, their derivatives and the wrapped x indices sit in registers, the y and z
+// ones in shared memory (one read per grid row), and the rows' offsets are wrapped once per
+// target, so each grid value costs one load and two multiply-adds.
+template <typename T, int W>
+__global__ void __launch_bounds__(128)
+k_interp3d_w(InterpArgs<T> a) {
+    __shared__ T cw[kMaxCheb], cd[kMaxCheb];
+    __shared__ T wyz[4][W][128];  // (value, derivative) x (y, z) per thread
+    if (threadIdx.x < a.nW) cw[threadIdx.x] = a.coefW[threadIdx.x];
+    if (threadIdx.x < a.nWd) cd[threadIdx.x] = a.coefWd[threadIdx.x];
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.nt) return;
+    const int tx = threadIdx.x;
+    const int4 g = a.t_g0[t];
+    const T* dq = a.t_dq + size_t(t) * 4;
+    T wx[W], dwx[W];
+    int xi[W];
+    {
+        const T del = dq[0];
+        int xx = g.x % a.M0;
+        if (xx < 0) xx += a.M0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            pswf_window_d(del - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &wx[j], &dwx[j]);
+            xi[j] = xx;
+            if (++xx == a.M0) xx = 0;
+        }
+    }
+    for (int k = 1; k < 3; ++k) {
+        const T del = dq[k];
+        for (int j = 0; j < W; ++j) {
+            T v, dv;
+            pswf_window_d(del - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &v, &dv);
+            wyz[2 * (k - 1)][j][tx] = v;
+            wyz[2 * (k - 1) + 1][j][tx] = dv;
+        }
+    }
+    T pot = 0, gx = 0, gy = 0, gz = 0;
+    int zz = g.z % a.M2;
+    if (zz < 0) zz += a.M2;
+    int yy0 = g.y % a.M1;
+    if (yy0 < 0) yy0 += a.M1;
+    for (int iz = 0; iz < W; ++iz) {
+        const T wz = wyz[2][iz][tx], dwz = wyz[3][iz][tx];
+        const T* plane = a.grid + size_t(zz) * a.M1 * a.M0;
+        int yy = yy0;
+        T py = 0, gxy = 0, gyy = 0;
+        for (int iy = 0; iy < W; ++iy) {
+            const T* row = plane + size_t(yy) * a.M0;
+            T sx = 0, sdx = 0;
+#pragma unroll
+            for (int ix = 0; ix < W; ++ix) {
+                const T v = __ldg(row + xi[ix]);
+                sx = fma(v, wx[ix], sx);
+                sdx = fma(v, dwx[ix], sdx);
+            }
+            const T wy = wyz[0][iy][tx], dwy = wyz[1][iy][tx];
+            py = fma(sx, wy, py);
+            gxy = fma(sdx, wy, gxy);
+            gyy = fma(sx, dwy, gyy);
+            if (++yy == a.M1) yy = 0;
+        }
+        pot = fma(py, wz, pot);
+        gx = fma(gxy, wz, gx);
+        gy = fma(gyy, wz, gy);
+        gz = fma(py, dwz, gz);
+        if (++zz == a.M2) zz = 0;
+    }
+    a.pot[t] = double(pot);
+    a.gradu[size_t(t) * 3 + 0] = double(gx);
+    a.gradu[size_t(t) * 3 + 1] = double(gy);
+    a.gradu[size_t(t) * 3 + 2] = double(gz);
+}
+
 // interpolation at targets: potential and gradient w.r.t. the grid coordinates
 template <typename T, int D>
 __global__ void __launch_bounds__(128)

@@ -163,10 +163,17 @@ __global__ void __launch_bounds__(256) k_leaf_moments3d_gemm(const int4* __restr
             if (ax == 0) qv[sidx] = q;  // zero for absent sources: their B rows vanish
         }
         __syncthreads();
-        for (int e = tid; e < NS * PP; e += 256) {
-            const int sidx = e / PP, col = e - sidx * PP, m1 = col / P, m2 = col - m1 * P;
-            const T* tr = Tb + sidx * 3 * P;
-            Bs[e] = qv[sidx] * tr[P + m1] * tr[2 * P + m2];
+#pragma unroll
+        for (int c = 0; c < (PP + 255) / 256; ++c) {
+            const int col = tid + 256 * c;
+            if (col < PP) {
+                const int m1 = col / P, m2 = col - (col / P) * P;
+#pragma unroll 4
+                for (int sidx = 0; sidx < NS; ++sidx) {
+                    const T* tr = Tb + sidx * 3 * P;
+                    Bs[sidx * PP + col] = qv[sidx] * tr[P + m1] * tr[2 * P + m2];
+                }
+            }
         }
         __syncthreads();
 #pragma unroll 2
@@ -1433,7 +1440,7 @@ __global__ void __launch_bounds__(32) k_leaf_eval3d_p(const int4* __restrict__ l
 //     g_y  = sum A[T row] Ty' Tz, g_z = sum A[T row] Ty Tz'        (times dt/dx = 2/h)
 template <typename T, int P>
 constexpr size_t leaf_eval3d_gemm_smem() {
-    return sizeof(T) * (size_t(P) * P * P + size_t(P) * 32 + size_t(16) * 4 * P) + sizeof(double) * 4 * 2 * 16;
+    return sizeof(T) * (size_t(P) * P * P + size_t(P) * 32 + size_t(16) * 4 * (P + 1)) + sizeof(double) * 4 * 2 * 16;
 }
 
 template <typename T, int P>
@@ -1445,8 +1452,9 @@ __global__ void __launch_bounds__(256) k_leaf_eval3d_gemm(const int4* __restrict
     extern __shared__ __align__(16) unsigned char smraw[];
     T* La = reinterpret_cast<T*>(smraw);  // [P][PP]
     T* X = La + NP;                       // [P][32]  X[m0][r], r = 2 t + (0: T, 1: T')
-    T* TB = X + P * 32;                   // [16][4][P]  (Ty, Ty', Tz, Tz') per target
-    double* red = reinterpret_cast<double*>(TB + 16 * 4 * P);  // [4 row groups][2 warps][16]
+    constexpr int PS = P + 1;             // odd row stride: the 16 targets' rows fall in distinct banks
+    T* TB = X + P * 32;                   // [16][4][PS]  (Ty, Ty', Tz, Tz') per target
+    double* red = reinterpret_cast<double*>(TB + 16 * 4 * PS);  // [4 row groups][2 warps][16]
     const int tid = threadIdx.x, rg = tid >> 6, cg = tid & 63, lane = tid & 31, half = (tid >> 5) & 1;
     const int4 e = list[blockIdx.x];      // (local slot, first target, target count, level)
     const double sc = 2.0 * inv_rc * double(1LL << e.w);  // dt/dx = 2/h
@@ -1472,8 +1480,8 @@ __global__ void __launch_bounds__(256) k_leaf_eval3d_gemm(const int4* __restrict
                     X[m * 32 + 2 * t] = b * live;
                     X[m * 32 + 2 * t + 1] = d * live;
                 } else {
-                    TB[(t * 4 + 2 * (ax - 1)) * P + m] = b;
-                    TB[(t * 4 + 2 * (ax - 1) + 1) * P + m] = d;
+                    TB[(t * 4 + 2 * (ax - 1)) * PS + m] = b;
+                    TB[(t * 4 + 2 * (ax - 1) + 1) * PS + m] = d;
                 }
             };
             put(0, T(1), T(0));
@@ -1513,12 +1521,12 @@ __global__ void __launch_bounds__(256) k_leaf_eval3d_gemm(const int4* __restrict
         T part[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const T* tb = TB + (rg * 4 + j) * 4 * P;
+            const T* tb = TB + (rg * 4 + j) * 4 * PS;
             T sp = T(0), sx = T(0), sy = T(0), sz = T(0);
 #pragma unroll
             for (int k = 0; k < CT; ++k) {
                 const int col = cg + 64 * k, m1 = col / P, m2 = col - m1 * P;
-                const T ty = tb[m1], dy = tb[P + m1], tz = tb[2 * P + m2], dz = tb[3 * P + m2];
+                const T ty = tb[m1], dy = tb[PS + m1], tz = tb[2 * PS + m2], dz = tb[3 * PS + m2];
                 const T a0 = acc[2 * j][k], a1 = acc[2 * j + 1][k];
                 const T w = ty * tz;
                 sp = fma(a0, w, sp);
