@@ -95,6 +95,14 @@ typedef struct {
                        L n, n in {-1, 0, 1}^d (pdmk_get_info reports n_images = n).  Any other
                        cell takes the multi-cube root with its halo of images (Sec. 3.3-3.4).
                        1: always the multi-cube root with images. */
+    int build_mode; /* where pdmk_set_sources builds the tree and the per-point records:
+                       0: on the device, falling back to the host for inputs the device build
+                       does not take (trees deeper than its 64-bit point keys hold, about 16
+                       levels in 3D and 25 in 2D, or 2^30 images or more); 1: on the host;
+                       2: on the device only (PDMK_ERR_TOO_LARGE otherwise); 3: both, compared
+                       array by array (a check of the device build: PDMK_ERR_INTERNAL with
+                       pdmk_plan_message naming the first array that differs).  Both builds
+                       give the same tree, order and records, bit for bit. */
 } pdmk_opts;
 
 /* Fills *opts with the defaults (all fields "auto", FP64, neutrality allowed). */
@@ -295,6 +303,16 @@ int pdmk_partition_cells(int ncells, const double* work, int nranks, int* rank_o
 /* Per-stage device times (ms) of the last pdmk_eval when opts.profile = 1.  names/ms
  * receive up to cap entries; returns the number of stages (or a negative error).     */
 int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, int cap);
+
+/* Host wall-clock times (ms) of the phases of the last pdmk_set_sources (or
+ * pdmk_set_sources_targets) of the plan: reading and checking the inputs, the tree build's
+ * phases (images, root sort, refinement, level restriction, renumbering and colleagues,
+ * sorted outputs), the direct lists, the per-point records, the near-field entries, the far
+ * field's layout, the device uploads and the plane-wave layouts.  Recorded on every call,
+ * whatever opts.profile.  names/ms (either may be NULL) receive up to cap entries; the names
+ * are static strings.  Returns the number of phases (0 before the first set-up), or
+ * PDMK_ERR_BAD_ARG for a NULL plan or cap < 0. */
+int pdmk_setup_times(pdmk_plan plan, const char** names, double* ms, int cap);
 
 /* Plan facts (sizes, counts) for reporting and roofline accounting. */
 typedef struct {

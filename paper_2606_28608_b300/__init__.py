@@ -31,7 +31,7 @@ class Opts(ctypes.Structure):
                 ("window_w", ctypes.c_int), ("n_proxy", ctypes.c_int), ("n_pw", ctypes.c_int),
                 ("max_depth", ctypes.c_int), ("neutrality", ctypes.c_int), ("profile", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("wait_test", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("root_mode", ctypes.c_int)]
+                ("root_mode", ctypes.c_int), ("build_mode", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -92,6 +92,8 @@ def lib():
         L.pdmk_batch_destroy.restype = None
         L.pdmk_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.pdmk_stage_times.restype = ctypes.c_int
+        L.pdmk_setup_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.pdmk_setup_times.restype = ctypes.c_int
         L.pdmk_get_info.argtypes = [P, ctypes.POINTER(Info)]
         L.pdmk_get_info.restype = ctypes.c_int
         L.pdmk_plan_destroy.argtypes = [P]
@@ -170,7 +172,7 @@ class Plan:
     def __init__(self, L, eps: float, *, precision: str = "fp64", kappa: float = 0.0, n_s: int = 0,
                  window_w: int = 0, n_proxy: int = 0, n_pw: int = 0, max_depth: int = -1,
                  neutrality: int = 1, profile: bool = False, stream=None, wait_test: int = 0,
-                 autotune: bool = False, root_mode: int = 0):
+                 autotune: bool = False, root_mode: int = 0, build: str = "auto"):
         L = np.ascontiguousarray(np.asarray(L, dtype=np.float64))
         self.d = L.shape[0]
         self._L = L
@@ -196,6 +198,7 @@ class Plan:
         o.wait_test = int(wait_test)
         o.autotune = 1 if autotune else 0
         o.root_mode = int(root_mode)
+        o.build_mode = {"auto": 0, "host": 1, "device": 2, "compare": 3}[build]
         self.opts = o
         Lc = np.ascontiguousarray(L.T)  # column-major
         h = ctypes.c_void_p()
@@ -241,7 +244,7 @@ class Plan:
             m = xx.shape[0]
             rc = lib().pdmk_set_sources_targets(self._h, n, ptr(yy), ptr(qq), m, ptr(xx), where)
         if rc != 0:
-            raise PdmkError(rc, "pdmk_set_sources")
+            raise PdmkError(rc, "pdmk_set_sources: " + self.message())
         self.n = n
         self.m = m
         self.separate_targets = xx is not None
@@ -378,6 +381,18 @@ class Plan:
         ms = (ctypes.c_double * 32)()
         n = lib().pdmk_stage_times(self._h, names, ms, 32)
         return {names[i].decode(): ms[i] for i in range(max(n, 0))}
+
+    def message(self) -> str:
+        """Detail of the plan's last error or check (pdmk_plan_message)."""
+        m = lib().pdmk_plan_message(self._h)
+        return m.decode() if m else ""
+
+    def setup_times(self) -> dict:
+        """Host wall-clock ms of the phases of the last set_sources (pdmk_setup_times)."""
+        names = (ctypes.c_char_p * 32)()
+        ms = (ctypes.c_double * 32)()
+        n = lib().pdmk_setup_times(self._h, names, ms, 32)
+        return {names[i].decode(): ms[i] for i in range(max(min(n, 32), 0))}
 
 
 class Batch:

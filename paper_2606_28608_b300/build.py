@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpdmk.so")
-SOURCES = ["capi.cu", "pw.cu", "host_plan.cpp"]
+SOURCES = ["capi.cu", "pw.cu", "gpu_build.cu", "host_plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -4,6 +4,7 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "gpu_build.h"
 #include "host_plan.h"
 #include "k_assemble.cuh"
 #include "k_bloch.cuh"
@@ -173,6 +175,17 @@ struct pdmk_plan_s {
     std::vector<cudaEvent_t> ev;
     std::vector<std::string> stage_names;
     std::vector<double> stage_ms;
+    // device set-up (gpu_build.cu): the per-point host copies are downloaded on first use
+    bool setup_device = false;
+    bool host_copies = true;
+    double* d_u_keep = nullptr;     // fractional coordinates (n x d)
+    double* d_y_keep = nullptr;     // the caller's positions (n x d)
+    double* d_src_disp = nullptr;   // per sorted source: caller-frame lattice vector (d)
+    int* d_tgt_of_keep = nullptr;   // per sorted target: sorted source index
+    int64_t nlist = 0;              // direct-list entries
+    // host phases of the last pdmk_set_sources (milliseconds, wall clock)
+    std::vector<const char*> setup_names;
+    std::vector<double> setup_ms;
     pdmk_info info{};
     int64_t device_bytes = 0;
     int launches = 0;  // kernels launched by the last eval (this library's own)
@@ -244,6 +257,7 @@ extern "C" void pdmk_default_opts(pdmk_opts* o) {
     o->wait_test = 0;
     o->autotune = 0;
     o->root_mode = 0;
+    o->build_mode = 0;
 }
 
 extern "C" const char* pdmk_strerror(int code) {
@@ -827,13 +841,389 @@ static void lattice_shift(const Geometry& g, int code, double* out) {
 // Sources (n_src, charges q) and, if m > 0, separate targets x (m points): the plan is built
 // on the union, the targets being points of charge 0 (they add nothing to any stage and have
 // no self term), and the evaluation writes the m target outputs only.
+// ---- source set-up -------------------------------------------------------------------
+// The set-up runs on the host (build_tree and the per-point passes below) or on the device
+// (gpu_build.cu); both produce the same tree, order and records, bit for bit.  The per-box
+// passes (direct lists, near-field entries, spreading subproblems, plane-wave layouts) run on
+// the host in both.
+
+// near-field leaf descriptors and direct-list entries (per box)
+static void near_layout(pdmk_plan plan, const Tree& tree, const DirectLists& dl, const std::vector<double>& Cu,
+                        std::vector<TLeaf>* tl_out, std::vector<int2>* ent_out, std::vector<unsigned char>* ent_sh_out,
+                        std::vector<float>* ent_shlo_out, std::vector<int>* bsb_out, std::vector<int>* bsc_out) {
+    const int d = plan->d;
+    const Geometry& g = plan->g;
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    const size_t ts = tsize(plan);
+    const int nb = int(tree.level.size());
+    auto put = [&](std::vector<unsigned char>& buf, size_t idx, double v) {
+        if (mixed) { float f = float(v); std::memcpy(&buf[idx * 4], &f, 4); }
+        else std::memcpy(&buf[idx * 8], &v, 8);
+    };
+    auto to_tree = [&](const double* v, double* out) {  // Q v
+        for (int i = 0; i < d; ++i) {
+            double s = 0;
+            for (int k = 0; k < d; ++k) s += g.Q[i * d + k] * v[k];
+            out[i] = s;
+        }
+    };
+    std::vector<TLeaf>& tl = *tl_out;
+    tl.assign(dl.tleaf.size(), TLeaf{});
+    for (size_t k = 0; k < dl.tleaf.size(); ++k) {
+        int b = dl.tleaf[k];
+        tl[k].tgt_begin = int(tree.tgt_begin[b]);
+        tl[k].tgt_count = int(tree.tgt_end[b] - tree.tgt_begin[b]);
+        tl[k].list_begin = int(dl.list_begin[k]);
+        tl[k].list_count = int(dl.list_begin[k + 1] - dl.list_begin[k]);
+        tl[k].level = tree.level[b];
+        tl[k].box = b;
+        tl[k].pad0 = tl[k].pad1 = 0;
+    }
+    std::vector<int>& bsb = *bsb_out;
+    std::vector<int>& bsc = *bsc_out;
+    bsb.resize(nb);
+    bsc.resize(nb);
+    for (int b = 0; b < nb; ++b) {
+        bsb[b] = int(tree.src_begin[b]);
+        bsc[b] = int(tree.src_end[b] - tree.src_begin[b]);
+    }
+    // per direct-list entry: source range and the source leaf centre's shift into the target
+    // leaf's frame (FP64 difference, then hi / lo in T)
+    std::vector<int2>& ent = *ent_out;
+    std::vector<unsigned char>& ent_sh = *ent_sh_out;
+    std::vector<float>& ent_shlo = *ent_shlo_out;
+    ent.assign(dl.list.size(), int2{0, 0});
+    ent_sh.assign(dl.list.size() * 4 * ts, 0);
+    ent_shlo.assign(mixed ? dl.list.size() * 4 : 0, 0.0f);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t k = 0; k < int64_t(dl.tleaf.size()); ++k) {
+        const int tb = dl.tleaf[k];
+        for (int64_t e = dl.list_begin[k]; e < dl.list_begin[k + 1]; ++e) {
+            const int sb = dl.list[e];
+            ent[e] = make_int2(bsb[sb], bsc[sb]);
+            double du[3] = {0, 0, 0}, sht[3], Ln[3] = {0, 0, 0};
+            lattice_shift(g, dl.shift[e], Ln);
+            for (int a = 0; a < d; ++a) du[a] = Cu[size_t(sb) * d + a] + Ln[a] - Cu[size_t(tb) * d + a];
+            to_tree(du, sht);
+            for (int a = 0; a < d; ++a) {
+                const double sh = sht[a];
+                put(ent_sh, size_t(e) * 4 + a, sh);
+                if (mixed) ent_shlo[size_t(e) * 4 + a] = float(sh - double(float(sh)));
+            }
+        }
+    }
+    // the warp near-field kernel computes 32 targets at a time: a leaf with more targets
+    // becomes several descriptors over the same direct list (one warp each, so leaves of a
+    // few hundred targets do not leave the grid short of warps; every target is still summed
+    // by one lane in the same order). Descriptors are taken in order of decreasing pair
+    // count (the long ones start first).
+    if (plan->near_nh > 0) {
+        std::vector<TLeaf> split;
+        split.reserve(tl.size() * 2);
+        for (const TLeaf& L : tl)
+            for (int t0 = 0; t0 < std::max(L.tgt_count, 1); t0 += 32) {
+                TLeaf c = L;
+                c.tgt_begin = L.tgt_begin + t0;
+                c.tgt_count = std::min(32, L.tgt_count - t0);
+                split.push_back(c);
+            }
+        tl.swap(split);
+    }
+    std::vector<int64_t> cost(tl.size(), 0);
+    for (size_t k = 0; k < tl.size(); ++k) {
+        int64_t ns = 0;
+        for (int e = tl[k].list_begin; e < tl[k].list_begin + tl[k].list_count; ++e) ns += ent[e].y;
+        cost[k] = ns * int64_t(tl[k].tgt_count);
+    }
+    std::vector<size_t> ord(tl.size());
+    std::iota(ord.begin(), ord.end(), size_t(0));
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<TLeaf> tl2(tl.size());
+    for (size_t k = 0; k < ord.size(); ++k) tl2[k] = tl[ord[k]];
+    tl.swap(tl2);
+}
+
+// spreading subproblems: chunks of at most max_pts points of one bin (one spreading block
+// each; in 3D the clustered bins hold most points, so smaller chunks give the grid enough
+// blocks), from the points per bin in bin order
+static void spread_subproblems(pdmk_plan plan, const std::vector<int64_t>& bin_count, std::vector<int4>* subs,
+                               std::vector<int>* bin_sub_begin) {
+    const int max_pts = plan->spread_reg3d ? 1024 : (plan->d == 3 ? 128 : 512);
+    subs->clear();
+    bin_sub_begin->assign(size_t(plan->nbins_tot) + 1, 0);
+    int64_t k = 0;
+    for (int bin = 0; bin < plan->nbins_tot; ++bin) {
+        (*bin_sub_begin)[bin] = int(subs->size());
+        const int64_t k0 = k;
+        k += bin_count[size_t(bin)];
+        for (int64_t s0 = k0; s0 < k; s0 += max_pts)
+            subs->push_back(make_int4(bin, int(s0), int(std::min<int64_t>(max_pts, k - s0)), 0));
+    }
+    (*bin_sub_begin)[plan->nbins_tot] = int(subs->size());
+}
+
+// drop the previous set-up's buffers and graph
+static void release_sources(pdmk_plan plan) {
+    cudaStreamSynchronize(plan->ws);
+    drop_graph(plan);
+    plan->evals_since_setup = 0;
+    free_list(plan->src_allocs, &plan->device_bytes);
+    plan->d_adj = nullptr;
+    if (plan->tq_buf) cudaFree(plan->tq_buf);
+    plan->tq_buf = nullptr;
+    plan->tq_cap = 0;
+    pw_free_sources(&plan->pw);
+    plan->d_u_keep = nullptr;
+    plan->d_y_keep = nullptr;
+    plan->d_src_disp = nullptr;
+    plan->d_tgt_of_keep = nullptr;
+    plan->host_copies = true;
+}
+
+// the per-point device arrays of a set-up (sizes from the plan's counts)
+static int alloc_sources(pdmk_plan plan, size_t nleafdesc, size_t nlist) {
+    auto& L = plan->src_allocs;
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    const size_t ts = tsize(plan);
+    const int d = plan->d;
+    const int64_t n = plan->n;
+    DALLOC(L, plan->d_src4, unsigned char, size_t(plan->nimg) * 4 * ts);
+    DALLOC(L, plan->d_src_orig, int, plan->nimg);
+    DALLOC(L, plan->d_tgt4, unsigned char, size_t(plan->ntgt) * 4 * ts);
+    DALLOC(L, plan->d_tgt_orig, int, plan->ntgt);
+    DALLOC(L, plan->d_src_lo, float, mixed ? size_t(plan->nimg) * 4 : 0);
+    DALLOC(L, plan->d_tgt_lo, float, mixed ? size_t(plan->ntgt) * 4 : 0);
+    DALLOC(L, plan->d_q_tgt, double, plan->ntgt);
+    DALLOC(L, plan->d_self_w, double, plan->ntgt);
+    DALLOC(L, plan->d_tleaf, TLeaf, nleafdesc);
+    DALLOC(L, plan->d_list, int, nlist);
+    DALLOC(L, plan->d_ent, int2, nlist);
+    DALLOC(L, plan->d_ent_sh, unsigned char, nlist * 4 * ts);
+    DALLOC(L, plan->d_ent_shlo, float, mixed ? nlist * 4 : 0);
+    DALLOC(L, plan->d_box_src_begin, int, plan->nbox);
+    DALLOC(L, plan->d_box_src_count, int, plan->nbox);
+    DALLOC(L, plan->d_box_center, double, size_t(plan->nbox) * d);
+    DALLOC(L, plan->d_pt_g0, int4, n);
+    DALLOC(L, plan->d_pt_dq, unsigned char, size_t(n) * 4 * ts);
+    DALLOC(L, plan->d_spread_orig, int, n);
+    DALLOC(L, plan->d_t_g0, int4, plan->ntgt);
+    DALLOC(L, plan->d_t_dq, unsigned char, size_t(plan->ntgt) * 4 * ts);
+    DALLOC(L, plan->d_pot_near, double, plan->ntgt);
+    DALLOC(L, plan->d_grad_near, double, plan->ntgt * d);
+    DALLOC(L, plan->d_pot_far, double, plan->ntgt);
+    DALLOC(L, plan->d_gradu_far, double, plan->ntgt * d);
+    DALLOC(L, plan->d_q_user, double, n);
+    DALLOC(L, plan->d_pot_out, double, n);
+    DALLOC(L, plan->d_grad_out, double, n * d);
+    return PDMK_OK;
+}
+
+// the spreading subproblems and their scratch (plan->nsub set)
+static int alloc_subs(pdmk_plan plan, size_t nsub) {
+    auto& L = plan->src_allocs;
+    DALLOC(L, plan->d_sub, int4, nsub);
+    DALLOC(L, plan->d_bin_sub_begin, int, size_t(plan->nbins_tot) + 1);
+    DALLOC(L, plan->d_slab, unsigned char, slab_bytes(plan));
+    return PDMK_OK;
+}
+
+// plan facts after a set-up
+static void finish_info(pdmk_plan plan, const BuildStats& st, int64_t pairs, int64_t n_src, int64_t m) {
+    const Geometry& g = plan->g;
+    const int d = plan->d;
+    pdmk_info& I = plan->info;
+    std::memset(&I, 0, sizeof(I));
+    I.d = d; I.eps = plan->eps; I.c = plan->c; I.rc = g.rc; I.V = g.V; I.kappa = plan->kappa;
+    I.n_s = plan->n_s; I.window_w = plan->w; I.n_proxy = plan->pw.p; I.n_pw = plan->pw.K;
+    I.precision = plan->opts.precision;
+    for (int i = 0; i < 3; ++i) { I.M[i] = g.M[i]; I.nroot[i] = i < d ? g.nroot[i] : 1; }
+    I.n = plan->n; I.n_images = plan->nimg; I.nboxes = st.nboxes; I.nleaves = st.nleaves; I.depth = st.depth;
+    I.ntarget_leaves = plan->ntleaf; I.near_pairs = pairs;
+    I.n_pw_boxes_out = plan->pw.nout; I.n_pw_boxes_in = plan->pw.nin;
+    I.pw_moment_sources = plan->pw.active ? plan->pw.moment_sources : 0;
+    I.pw_merge_parents = plan->pw.active ? plan->pw.merge_parents : 0;
+    I.pw_down_parents = plan->pw.active ? plan->pw.down_parents : 0;
+    I.pw_eval_targets = plan->pw.active ? plan->pw.eval_targets : 0;
+    I.spread_subproblems = plan->nsub;
+    plan->count_pending = plan->opts.profile != 0;
+    plan->n_src = n_src;
+    plan->out_first = m > 0 ? n_src : 0;
+    plan->n_out = m > 0 ? m : n_src;
+    I.n = n_src;
+    I.n_targets = plan->n_out;
+}
+
+// the host copies of a device set-up (used by evaluations at new targets and Bloch sums)
+static int ensure_host_copies(pdmk_plan plan) {
+    if (plan->host_copies) return PDMK_OK;
+    const int d = plan->d;
+    CK(cudaStreamSynchronize(plan->ws));
+    plan->h_u.resize(size_t(plan->n) * d);
+    plan->h_y.resize(size_t(plan->n) * d);
+    plan->h_src_disp.resize(size_t(plan->nimg) * d);
+    std::vector<int> so(size_t(plan->nimg)), tof(size_t(plan->ntgt));
+    CK(cudaMemcpy(plan->h_u.data(), plan->d_u_keep, plan->h_u.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(plan->h_y.data(), plan->d_y_keep, plan->h_y.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(plan->h_src_disp.data(), plan->d_src_disp, plan->h_src_disp.size() * sizeof(double),
+                  cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(so.data(), plan->d_src_orig, so.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tof.data(), plan->d_tgt_of_keep, tof.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    plan->h_src_orig.assign(so.begin(), so.end());
+    plan->h_src_is_orig.assign(size_t(plan->nimg), 0);
+    for (int j : tof) plan->h_src_is_orig[size_t(j)] = 1;
+    plan->host_copies = true;
+    return PDMK_OK;
+}
+
+static int set_points_host(pdmk_plan plan, int64_t n_src, const double* y, const double* q, int64_t m,
+                           const double* x, int where);
+static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, const double* q, int64_t m,
+                             const double* x, int where);
+
+// every array a set-up leaves, for the comparison of the two builds (name, bytes)
+static int setup_snapshot(pdmk_plan plan, std::vector<std::pair<std::string, std::vector<unsigned char>>>* out) {
+    out->clear();
+    CK(cudaStreamSynchronize(plan->ws));
+    const size_t ts = tsize(plan);
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    const int d = plan->d;
+    auto dev = [&](const char* name, const void* p, size_t bytes) -> int {
+        std::vector<unsigned char> v(bytes);
+        if (bytes) CK(cudaMemcpy(v.data(), p, bytes, cudaMemcpyDeviceToHost));
+        out->push_back({name, std::move(v)});
+        return PDMK_OK;
+    };
+    auto host = [&](const char* name, const void* p, size_t bytes) {
+        std::vector<unsigned char> v(bytes);
+        if (bytes) std::memcpy(v.data(), p, bytes);
+        out->push_back({name, std::move(v)});
+    };
+    int64_t counts[8] = {plan->n, plan->nimg, plan->ntgt, plan->nspread, plan->nbox, plan->ntleaf, plan->nsub,
+                         plan->nnear};
+    host("counts", counts, sizeof(counts));
+    int r;
+    if ((r = dev("list", plan->d_list, size_t(plan->nlist) * 4))) return r;
+    if ((r = dev("ent", plan->d_ent, size_t(plan->nlist) * 8))) return r;
+    if ((r = dev("ent_sh", plan->d_ent_sh, size_t(plan->nlist) * 4 * ts))) return r;
+    if (mixed && (r = dev("ent_shlo", plan->d_ent_shlo, size_t(plan->nlist) * 16))) return r;
+    if ((r = dev("src4", plan->d_src4, size_t(plan->nimg) * 4 * ts))) return r;
+    if ((r = dev("src_orig", plan->d_src_orig, size_t(plan->nimg) * 4))) return r;
+    if ((r = dev("tgt4", plan->d_tgt4, size_t(plan->ntgt) * 4 * ts))) return r;
+    if ((r = dev("tgt_orig", plan->d_tgt_orig, size_t(plan->ntgt) * 4))) return r;
+    if (mixed) {
+        if ((r = dev("src_lo", plan->d_src_lo, size_t(plan->nimg) * 16))) return r;
+        if ((r = dev("tgt_lo", plan->d_tgt_lo, size_t(plan->ntgt) * 16))) return r;
+    }
+    if ((r = dev("self_w", plan->d_self_w, size_t(plan->ntgt) * 8))) return r;
+    if ((r = dev("tleaf", plan->d_tleaf, size_t(plan->nnear) * sizeof(TLeaf)))) return r;
+    if ((r = dev("box_src_begin", plan->d_box_src_begin, size_t(plan->nbox) * 4))) return r;
+    if ((r = dev("box_src_count", plan->d_box_src_count, size_t(plan->nbox) * 4))) return r;
+    if ((r = dev("box_center", plan->d_box_center, size_t(plan->nbox) * d * 8))) return r;
+    if ((r = dev("pt_g0", plan->d_pt_g0, size_t(plan->nspread) * 16))) return r;
+    if ((r = dev("pt_dq", plan->d_pt_dq, size_t(plan->nspread) * 4 * ts))) return r;
+    if ((r = dev("spread_orig", plan->d_spread_orig, size_t(plan->nspread) * 4))) return r;
+    if ((r = dev("sub", plan->d_sub, size_t(plan->nsub) * 16))) return r;
+    if ((r = dev("bin_sub_begin", plan->d_bin_sub_begin, size_t(plan->nbins_tot + 1) * 4))) return r;
+    if ((r = dev("t_g0", plan->d_t_g0, size_t(plan->ntgt) * 16))) return r;
+    if ((r = dev("t_dq", plan->d_t_dq, size_t(plan->ntgt) * 4 * ts))) return r;
+    if ((r = dev("q_user", plan->d_q_user, size_t(plan->n) * 8))) return r;
+    const Tree& t = plan->h_tree;
+    host("tree.level_start", t.level_start.data(), t.level_start.size() * 4);
+    host("tree.level", t.level.data(), t.level.size() * 4);
+    host("tree.coord", t.coord.data(), t.coord.size() * 8);
+    host("tree.parent", t.parent.data(), t.parent.size() * 4);
+    host("tree.child0", t.child0.data(), t.child0.size() * 4);
+    host("tree.src_begin", t.src_begin.data(), t.src_begin.size() * 8);
+    host("tree.src_end", t.src_end.data(), t.src_end.size() * 8);
+    host("tree.tgt_begin", t.tgt_begin.data(), t.tgt_begin.size() * 8);
+    host("tree.tgt_end", t.tgt_end.data(), t.tgt_end.size() * 8);
+    host("tree.colleague", t.colleague.data(), t.colleague.size() * 4);
+    host("tree.center", t.center.data(), t.center.size() * 8);
+    if ((r = ensure_host_copies(plan))) return r;
+    host("h_u", plan->h_u.data(), plan->h_u.size() * 8);
+    host("h_src_orig", plan->h_src_orig.data(), plan->h_src_orig.size() * 8);
+    host("h_src_is_orig", plan->h_src_is_orig.data(), plan->h_src_is_orig.size());
+    host("h_Cu", plan->h_Cu.data(), plan->h_Cu.size() * 8);
+    host("h_y", plan->h_y.data(), plan->h_y.size() * 8);
+    host("h_src_disp", plan->h_src_disp.data(), plan->h_src_disp.size() * 8);
+    int64_t facts[8] = {plan->info.n_images, plan->info.nboxes, plan->info.nleaves, plan->info.depth,
+                        plan->info.near_pairs, plan->info.pw_merge_parents, plan->info.pw_down_parents,
+                        plan->info.n_pw_boxes_in};
+    host("info", facts, sizeof(facts));
+    return PDMK_OK;
+}
+
 static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const double* q, int64_t m, const double* x,
                       int where) {
     if (!plan || n_src < 0 || m < 0 || (n_src > 0 && (!y || !q)) || (m > 0 && !x)) return PDMK_ERR_BAD_ARG;
     const int64_t n = n_src + m;
     if (n >= (int64_t(1) << 30)) return PDMK_ERR_TOO_LARGE;
-    const int d = plan->d;
     plan->ready = false;
+    plan->setup_names.clear();
+    plan->setup_ms.clear();
+    plan->setup_device = false;
+    const int mode = plan->opts.build_mode;
+    if (mode == 1 || n == 0) return set_points_host(plan, n_src, y, q, m, x, where);
+    if (mode == 3) {
+        // both builds, compared array by array (a check of the device build)
+        int r = set_points_host(plan, n_src, y, q, m, x, where);
+        if (r != PDMK_OK) return r;
+        std::vector<std::pair<std::string, std::vector<unsigned char>>> a, b;
+        if ((r = setup_snapshot(plan, &a))) return r;
+        plan->ready = false;
+        r = set_points_device(plan, n_src, y, q, m, x, where);
+        if (r == kGpuBuildUnsupported) {
+            plan_set_msg(plan, "device set-up unsupported for these inputs (host build kept)");
+            return set_points_host(plan, n_src, y, q, m, x, where);
+        }
+        if (r != PDMK_OK) return r;
+        if ((r = setup_snapshot(plan, &b))) return r;
+        for (size_t k = 0; k < a.size() && k < b.size(); ++k)
+            if (a[k].first != b[k].first || a[k].second != b[k].second) {
+                plan->ready = false;
+                std::string msg = "device and host set-up differ in " + a[k].first + " (" +
+                                  std::to_string(a[k].second.size()) + " vs " + std::to_string(b[k].second.size()) +
+                                  " bytes)";
+                for (size_t i = 0; i < std::min(a[k].second.size(), b[k].second.size()); ++i)
+                    if (a[k].second[i] != b[k].second[i]) {
+                        msg += ", first at byte " + std::to_string(i);
+                        break;
+                    }
+                plan->msg = msg;
+                return PDMK_ERR_INTERNAL;
+            }
+        if (a.size() != b.size()) {
+            plan->ready = false;
+            plan_set_msg(plan, "device and host set-up differ in their array lists");
+            return PDMK_ERR_INTERNAL;
+        }
+        plan->msg = "device and host set-up identical";
+        return PDMK_OK;
+    }
+    int r = set_points_device(plan, n_src, y, q, m, x, where);
+    if (r == kGpuBuildUnsupported) {
+        if (mode == 2) {
+            plan_set_msg(plan, "device set-up unsupported for these inputs");
+            return PDMK_ERR_TOO_LARGE;
+        }
+        plan->setup_names.clear();
+        plan->setup_ms.clear();
+        return set_points_host(plan, n_src, y, q, m, x, where);
+    }
+    return r;
+}
+
+static int set_points_host(pdmk_plan plan, int64_t n_src, const double* y, const double* q, int64_t m,
+                           const double* x, int where) {
+    const int64_t n = n_src + m;
+    const int d = plan->d;
+    auto clk = std::chrono::steady_clock::now();
+    auto lap = [&](const char* name) {
+        const auto now = std::chrono::steady_clock::now();
+        plan->setup_names.push_back(name);
+        plan->setup_ms.push_back(std::chrono::duration<double, std::milli>(now - clk).count());
+        clk = now;
+    };
     std::vector<double> hy(size_t(n) * d), hq(static_cast<size_t>(n), 0.0);
     if (n_src > 0 || m > 0) {
         if (where == PDMK_DEVICE) {
@@ -878,25 +1268,24 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
             u[j * d + i] = s;
         }
     }
+    lap("read_check_orient");
     Tree tree;
     SortedSources ss;
     BuildStats st;
     const int maxd = pw_supported(&plan->pw) ? plan->max_depth : 0;
     int rc = build_tree(g, n, u.data(), plan->n_s, maxd, &tree, &ss, &st);
     if (rc != PDMK_OK) return rc;
+    for (int k = 0; k < 6; ++k) {
+        plan->setup_names.push_back(kBuildPhases[k]);
+        plan->setup_ms.push_back(st.phase_ms[k]);
+    }
+    clk = std::chrono::steady_clock::now();
     DirectLists dl;
     int64_t pairs = 0;
     build_direct_lists(tree, &dl, &pairs);
+    lap("direct_lists");
     // ---- release old buffers, allocate new ----
-    cudaStreamSynchronize(plan->ws);
-    drop_graph(plan);
-    plan->evals_since_setup = 0;
-    free_list(plan->src_allocs, &plan->device_bytes);
-    plan->d_adj = nullptr;
-    if (plan->tq_buf) cudaFree(plan->tq_buf);
-    plan->tq_buf = nullptr;
-    plan->tq_cap = 0;
-    pw_free_sources(&plan->pw);
+    release_sources(plan);
     const bool mixed = plan->opts.precision == PDMK_MIXED;
     const size_t ts = tsize(plan);
     plan->n = n;
@@ -972,6 +1361,7 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         for (int a = 0; a < d; ++a) du[a] = yo[a] - E[a];
         to_tree(du, &relv[size_t(j) * d]);
     }
+    lap("leaf_relative_coordinates");
     // sorted sources: coordinates relative to their leaf centre (FP64, then T)
     std::vector<unsigned char> src4(size_t(plan->nimg) * 4 * ts, 0);
     std::vector<int> src_orig(size_t(plan->nimg));
@@ -1006,77 +1396,16 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         const double h = g.rc / double(1LL << L);
         self_w[t] = (d == 3) ? plan->kt.self_coef / h : plan->kt.self_coef - std::log(h) / (2.0 * kPi);
     }
-    // near-field leaf descriptors
-    std::vector<TLeaf> tl(dl.tleaf.size());
-    for (size_t k = 0; k < dl.tleaf.size(); ++k) {
-        int b = dl.tleaf[k];
-        tl[k].tgt_begin = int(tree.tgt_begin[b]);
-        tl[k].tgt_count = int(tree.tgt_end[b] - tree.tgt_begin[b]);
-        tl[k].list_begin = int(dl.list_begin[k]);
-        tl[k].list_count = int(dl.list_begin[k + 1] - dl.list_begin[k]);
-        tl[k].level = tree.level[b];
-        tl[k].box = b;
-        tl[k].pad0 = tl[k].pad1 = 0;
-    }
-    std::vector<int> bsb(st.nboxes), bsc(st.nboxes);
-    for (int b = 0; b < st.nboxes; ++b) {
-        bsb[b] = int(tree.src_begin[b]);
-        bsc[b] = int(tree.src_end[b] - tree.src_begin[b]);
-    }
-    // per direct-list entry: source range and the source leaf centre's shift into the target
-    // leaf's frame (FP64 difference, then hi / lo in T)
-    std::vector<int2> ent(dl.list.size());
-    std::vector<unsigned char> ent_sh(dl.list.size() * 4 * ts, 0);
-    std::vector<float> ent_shlo(mixed ? dl.list.size() * 4 : 0, 0.0f);
-#pragma omp parallel for schedule(dynamic, 256)
-    for (int64_t k = 0; k < int64_t(dl.tleaf.size()); ++k) {
-        const int tb = dl.tleaf[k];
-        for (int64_t e = dl.list_begin[k]; e < dl.list_begin[k + 1]; ++e) {
-            const int sb = dl.list[e];
-            ent[e] = make_int2(bsb[sb], bsc[sb]);
-            double du[3] = {0, 0, 0}, sht[3], Ln[3] = {0, 0, 0};
-            lattice_shift(g, dl.shift[e], Ln);
-            for (int a = 0; a < d; ++a) du[a] = Cu[size_t(sb) * d + a] + Ln[a] - Cu[size_t(tb) * d + a];
-            to_tree(du, sht);
-            for (int a = 0; a < d; ++a) {
-                const double sh = sht[a];
-                put(ent_sh, size_t(e) * 4 + a, sh);
-                if (mixed) ent_shlo[size_t(e) * 4 + a] = float(sh - double(float(sh)));
-            }
-        }
-    }
-    // the warp near-field kernel computes 32 targets at a time: a leaf with more targets
-    // becomes several descriptors over the same direct list (one warp each, so leaves of a
-    // few hundred targets do not leave the grid short of warps; every target is still summed
-    // by one lane in the same order). Descriptors are taken in order of decreasing pair
-    // count (the long ones start first).
-    if (plan->near_nh > 0) {
-        std::vector<TLeaf> split;
-        split.reserve(tl.size() * 2);
-        for (const TLeaf& L : tl)
-            for (int t0 = 0; t0 < std::max(L.tgt_count, 1); t0 += 32) {
-                TLeaf c = L;
-                c.tgt_begin = L.tgt_begin + t0;
-                c.tgt_count = std::min(32, L.tgt_count - t0);
-                split.push_back(c);
-            }
-        tl.swap(split);
-    }
+    lap("source_target_records");
+    std::vector<TLeaf> tl;
+    std::vector<int2> ent;
+    std::vector<unsigned char> ent_sh;
+    std::vector<float> ent_shlo;
+    std::vector<int> bsb, bsc;
+    near_layout(plan, tree, dl, Cu, &tl, &ent, &ent_sh, &ent_shlo, &bsb, &bsc);
     plan->nnear = int(tl.size());
-    {
-        std::vector<int64_t> cost(tl.size(), 0);
-        for (size_t k = 0; k < tl.size(); ++k) {
-            int64_t ns = 0;
-            for (int e = tl[k].list_begin; e < tl[k].list_begin + tl[k].list_count; ++e) ns += ent[e].y;
-            cost[k] = ns * int64_t(tl[k].tgt_count);
-        }
-        std::vector<size_t> ord(tl.size());
-        std::iota(ord.begin(), ord.end(), size_t(0));
-        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
-        std::vector<TLeaf> tl2(tl.size());
-        for (size_t k = 0; k < ord.size(); ++k) tl2[k] = tl[ord[k]];
-        tl.swap(tl2);
-    }
+    plan->nlist = int64_t(dl.list.size());
+    lap("near_field_entries");
     // far field: originals sorted by spreading bin, window start and offsets in FP64
     const int fw = plan->w / 2;
     auto grid_coord = [&](double uu, int i, int* g0, double* del) {
@@ -1126,22 +1455,11 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         for (int i = 0; i < 3; ++i) put(pt_dq, size_t(k) * 4 + i, sp_del[j * 3 + i]);
         sp_orig[k] = int(j);
     }
-    // subproblems: chunks of at most max_pts points of one bin (one spreading block each; in
-    // 3D the clustered bins hold most points, so smaller chunks give the grid enough blocks)
-    const int max_pts = plan->spread_reg3d ? 1024 : (d == 3 ? 128 : 512);
+    std::vector<int64_t> bin_count(size_t(plan->nbins_tot), 0);
+    for (int64_t j = 0; j < n; ++j) ++bin_count[size_t(sp_bin[j])];
     std::vector<int4> subs;
-    std::vector<int> bin_sub_begin(size_t(plan->nbins_tot) + 1, 0);
-    {
-        int64_t k = 0;
-        for (int bin = 0; bin < plan->nbins_tot; ++bin) {
-            bin_sub_begin[bin] = int(subs.size());
-            int64_t k0 = k;
-            while (k < n && sp_bin[sp_order[k]] == bin) ++k;
-            for (int64_t s0 = k0; s0 < k; s0 += max_pts)
-                subs.push_back(make_int4(bin, int(s0), int(std::min<int64_t>(max_pts, k - s0)), 0));
-        }
-        bin_sub_begin[plan->nbins_tot] = int(subs.size());
-    }
+    std::vector<int> bin_sub_begin;
+    spread_subproblems(plan, bin_count, &subs, &bin_sub_begin);
     plan->nsub = int(subs.size());
     // interpolation targets (sorted target order)
     std::vector<int4> t_g0(size_t(plan->ntgt));
@@ -1159,39 +1477,13 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
         for (int i = 0; i < d; ++i) gg[i] = ((gg[i] % g.M[i]) + g.M[i]) % g.M[i];
         t_g0[t] = make_int4(gg[0], gg[1], gg[2], 0);
     }
+    lap("far_field_layout");
     // ---- device allocations and uploads ----
-    auto& L = plan->src_allocs;
-    DALLOC(L, plan->d_src4, unsigned char, src4.size());
-    DALLOC(L, plan->d_src_orig, int, src_orig.size());
-    DALLOC(L, plan->d_tgt4, unsigned char, tgt4.size());
-    DALLOC(L, plan->d_tgt_orig, int, tgt_orig.size());
-    DALLOC(L, plan->d_src_lo, float, src_lo.size());
-    DALLOC(L, plan->d_tgt_lo, float, tgt_lo.size());
-    DALLOC(L, plan->d_q_tgt, double, plan->ntgt);
-    DALLOC(L, plan->d_self_w, double, plan->ntgt);
-    DALLOC(L, plan->d_tleaf, TLeaf, tl.size());
-    DALLOC(L, plan->d_list, int, dl.list.size());
-    DALLOC(L, plan->d_ent, int2, ent.size());
-    DALLOC(L, plan->d_ent_sh, unsigned char, ent_sh.size());
-    DALLOC(L, plan->d_ent_shlo, float, ent_shlo.size());
-    DALLOC(L, plan->d_box_src_begin, int, bsb.size());
-    DALLOC(L, plan->d_box_src_count, int, bsc.size());
-    DALLOC(L, plan->d_box_center, double, tree.center.size());
-    DALLOC(L, plan->d_pt_g0, int4, pt_g0.size());
-    DALLOC(L, plan->d_pt_dq, unsigned char, pt_dq.size());
-    DALLOC(L, plan->d_spread_orig, int, sp_orig.size());
-    DALLOC(L, plan->d_sub, int4, subs.size());
-    DALLOC(L, plan->d_bin_sub_begin, int, bin_sub_begin.size());
-    DALLOC(L, plan->d_slab, unsigned char, slab_bytes(plan));
-    DALLOC(L, plan->d_t_g0, int4, t_g0.size());
-    DALLOC(L, plan->d_t_dq, unsigned char, t_dq.size());
-    DALLOC(L, plan->d_pot_near, double, plan->ntgt);
-    DALLOC(L, plan->d_grad_near, double, plan->ntgt * d);
-    DALLOC(L, plan->d_pot_far, double, plan->ntgt);
-    DALLOC(L, plan->d_gradu_far, double, plan->ntgt * d);
-    DALLOC(L, plan->d_q_user, double, n);
-    DALLOC(L, plan->d_pot_out, double, n);
-    DALLOC(L, plan->d_grad_out, double, n * d);
+    {
+        int ra = alloc_sources(plan, tl.size(), dl.list.size());
+        if (ra == PDMK_OK) ra = alloc_subs(plan, subs.size());
+        if (ra != PDMK_OK) return ra;
+    }
     int r;
     if ((r = upload(plan, plan->d_src4, src4))) return r;
     if ((r = upload(plan, plan->d_src_orig, src_orig))) return r;
@@ -1216,35 +1508,17 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     if ((r = upload(plan, plan->d_t_g0, t_g0))) return r;
     if ((r = upload(plan, plan->d_t_dq, t_dq))) return r;
     if ((r = upload(plan, plan->d_q_user, hq))) return r;
+    lap("device_alloc_upload");
     // plane-wave passes (proxy, translation and local-expansion layouts)
     plan->pw.d_src4 = plan->d_src4;
     plan->pw.d_tgt4 = plan->d_tgt4;
-    r = pw_set_sources(&plan->pw, tree, ss, leaf_of, tgt_leaf, g, plan->ws);
+    r = pw_set_sources(&plan->pw, tree, ss, leaf_of, tgt_leaf, g, plan->ws, nullptr, plan->nimg);
     if (r != PDMK_OK) return r;
     r = set_charges_device(plan, false);
     if (r != PDMK_OK) return r;
     CK(cudaStreamSynchronize(plan->ws));
-    // info
-    pdmk_info& I = plan->info;
-    std::memset(&I, 0, sizeof(I));
-    I.d = d; I.eps = plan->eps; I.c = plan->c; I.rc = g.rc; I.V = g.V; I.kappa = plan->kappa;
-    I.n_s = plan->n_s; I.window_w = plan->w; I.n_proxy = plan->pw.p; I.n_pw = plan->pw.K;
-    I.precision = plan->opts.precision;
-    for (int i = 0; i < 3; ++i) { I.M[i] = g.M[i]; I.nroot[i] = i < d ? g.nroot[i] : 1; }
-    I.n = n; I.n_images = plan->nimg; I.nboxes = st.nboxes; I.nleaves = st.nleaves; I.depth = st.depth;
-    I.ntarget_leaves = plan->ntleaf; I.near_pairs = pairs;
-    I.n_pw_boxes_out = plan->pw.nout; I.n_pw_boxes_in = plan->pw.nin;
-    I.pw_moment_sources = plan->pw.active ? plan->pw.moment_sources : 0;
-    I.pw_merge_parents = plan->pw.active ? plan->pw.merge_parents : 0;
-    I.pw_down_parents = plan->pw.active ? plan->pw.down_parents : 0;
-    I.pw_eval_targets = plan->pw.active ? plan->pw.eval_targets : 0;
-    I.spread_subproblems = plan->nsub;
-    plan->count_pending = plan->opts.profile != 0;
-    plan->n_src = n_src;
-    plan->out_first = m > 0 ? n_src : 0;
-    plan->n_out = m > 0 ? m : n_src;
-    I.n = n_src;
-    I.n_targets = plan->n_out;
+    lap("plane_wave_layout_charges");
+    finish_info(plan, st, pairs, n_src, m);
     // host copies for evaluations at new targets
     plan->h_u.swap(u);
     plan->h_src_orig.assign(ss.orig.begin(), ss.orig.end());
@@ -1256,8 +1530,267 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
     plan->bl_ready = false;
     plan->bl_buf = nullptr;  // freed with the source buffers
     plan->h_tree = std::move(tree);
+    lap("host_copies");
     plan->ready = true;
     return PDMK_OK;
+}
+
+static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, const double* q, int64_t m,
+                             const double* x, int where) {
+    const int64_t n = n_src + m;
+    const int d = plan->d;
+    const Geometry& g = plan->g;
+    const bool mixed = plan->opts.precision == PDMK_MIXED;
+    const size_t ts = tsize(plan);
+    cudaStream_t s = plan->ws;
+    auto clk = std::chrono::steady_clock::now();
+    auto lap = [&](const char* name) {
+        const auto now = std::chrono::steady_clock::now();
+        plan->setup_names.push_back(name);
+        plan->setup_ms.push_back(std::chrono::duration<double, std::milli>(now - clk).count());
+        clk = now;
+    };
+    // scratch of this call (freed on every return, after the stream has drained)
+    struct Scratch {
+        cudaStream_t s;
+        std::vector<void*> p;
+        GpuBuild gb;
+        ~Scratch() {
+            cudaStreamSynchronize(s);
+            for (void* x : p) cudaFree(x);
+            gpu_build_free(&gb);
+        }
+    } scr{s, {}, {}};
+    auto salloc = [&](void** out, size_t bytes) -> int {
+        *out = nullptr;
+        if (cudaMalloc(out, std::max<size_t>(bytes, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            plan_set_msg(plan, "device allocation failed (set-up)");
+            return PDMK_ERR_OOM;
+        }
+        scr.p.push_back(*out);
+        return PDMK_OK;
+    };
+#define SALLOC(ptr, type, count)                                                          \
+    do {                                                                                  \
+        void* v_ = nullptr;                                                               \
+        int rc_ = salloc(&v_, size_t(count) * sizeof(type));                              \
+        if (rc_ != PDMK_OK) return rc_;                                                   \
+        ptr = static_cast<type*>(v_);                                                     \
+    } while (0)
+    if (where == PDMK_DEVICE) CK(cudaStreamSynchronize(plan->stream));
+    release_sources(plan);
+    auto& AL = plan->src_allocs;
+    DALLOC(AL, plan->d_y_keep, double, size_t(n) * d);
+    DALLOC(AL, plan->d_u_keep, double, size_t(n) * d);
+    double *d_q, *d_part;
+    int* d_flag;
+    const int nblk = std::max(1, plan->sum_blocks);
+    SALLOC(d_q, double, n);
+    SALLOC(d_part, double, size_t(nblk) * 2);
+    SALLOC(d_flag, int, 1);
+    const cudaMemcpyKind kind = where == PDMK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (n_src > 0) {
+        CK(cudaMemcpyAsync(plan->d_y_keep, y, size_t(n_src) * d * sizeof(double), kind, s));
+        CK(cudaMemcpyAsync(d_q, q, size_t(n_src) * sizeof(double), kind, s));
+    }
+    if (m > 0) {
+        CK(cudaMemcpyAsync(plan->d_y_keep + size_t(n_src) * d, x, size_t(m) * d * sizeof(double), kind, s));
+        CK(cudaMemsetAsync(d_q + n_src, 0, size_t(m) * sizeof(double), s));
+    }
+    CK(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+    gpu_check_inputs(n, d, plan->d_y_keep, d_q, d_flag, d_part, nblk, s);
+    std::vector<double> part(size_t(nblk) * 2);
+    int bad = 0;
+    CK(cudaMemcpyAsync(part.data(), d_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&bad, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (bad) return PDMK_ERR_NONFINITE;
+    double qs = 0, qa = 0;
+    for (int b = 0; b < nblk; ++b) {
+        qs += part[size_t(b) * 2];
+        qa += part[size_t(b) * 2 + 1];
+    }
+    if (plan->opts.neutrality == 0 && std::fabs(qs) > 1e-12 * qa) return PDMK_ERR_NON_NEUTRAL;
+    gpu_orient(g, n, plan->d_y_keep, plan->d_u_keep, s);
+    CK(cudaGetLastError());
+    lap("read_check_orient");
+    // ---- tree (device), lists (host) ----
+    GpuBuild& gb = scr.gb;
+    gb.d_u = plan->d_u_keep;
+    Tree tree;
+    BuildStats st;
+    const int maxd = pw_supported(&plan->pw) ? plan->max_depth : 0;
+    std::string msg;
+    int r = gpu_build_tree(g, n, plan->n_s, maxd, s, &gb, &tree, &st, &msg);
+    if (r == kGpuBuildUnsupported) return r;
+    if (r != PDMK_OK) {
+        plan->msg = msg;
+        return r;
+    }
+    lap("tree_device");
+    DirectLists dl;
+    int64_t pairs = 0;
+    build_direct_lists(tree, &dl, &pairs);
+    lap("direct_lists");
+    plan->n = n;
+    plan->nimg = st.n_images;
+    plan->ntgt = gb.ntgt;
+    plan->nbox = st.nboxes;
+    plan->ntleaf = int(dl.tleaf.size());
+    // caller-frame box centres, as the host build
+    std::vector<double> Cu(size_t(st.nboxes) * d);
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < st.nboxes; ++b)
+        for (int i = 0; i < d; ++i) {
+            double sum = 0;
+            for (int k = 0; k < d; ++k) sum += g.Q[k * d + i] * tree.center[size_t(b) * d + k];
+            Cu[size_t(b) * d + i] = sum;
+        }
+    std::vector<TLeaf> tl;
+    std::vector<int2> ent;
+    std::vector<unsigned char> ent_sh;
+    std::vector<float> ent_shlo;
+    std::vector<int> bsb, bsc;
+    near_layout(plan, tree, dl, Cu, &tl, &ent, &ent_sh, &ent_shlo, &bsb, &bsc);
+    plan->nnear = int(tl.size());
+    plan->nlist = int64_t(dl.list.size());
+    lap("near_field_entries");
+    // ---- per-point records (device) ----
+    if ((r = alloc_sources(plan, tl.size(), dl.list.size()))) return r;
+    DALLOC(AL, plan->d_src_disp, double, size_t(plan->nimg) * d);
+    DALLOC(AL, plan->d_tgt_of_keep, int, plan->ntgt);
+    CK(cudaMemsetAsync(plan->d_src4, 0, size_t(plan->nimg) * 4 * ts, s));
+    CK(cudaMemsetAsync(plan->d_tgt4, 0, size_t(plan->ntgt) * 4 * ts, s));
+    if (mixed) {
+        CK(cudaMemsetAsync(plan->d_src_lo, 0, size_t(plan->nimg) * 4 * sizeof(float), s));
+        CK(cudaMemsetAsync(plan->d_tgt_lo, 0, size_t(plan->ntgt) * 4 * sizeof(float), s));
+    }
+    if ((r = upload(plan, plan->d_box_center, tree.center))) return r;
+    double *d_Cu, *d_selfw_level;
+    int *d_level, *d_tgt_leaf;
+    SALLOC(d_Cu, double, Cu.size());
+    SALLOC(d_level, int, tree.level.size());
+    SALLOC(d_tgt_leaf, int, plan->ntgt);
+    std::vector<double> selfw_level(size_t(tree.nlevels));
+    for (int L = 0; L < tree.nlevels; ++L) {
+        const double h = g.rc / double(1LL << L);
+        selfw_level[size_t(L)] = (d == 3) ? plan->kt.self_coef / h : plan->kt.self_coef - std::log(h) / (2.0 * kPi);
+    }
+    SALLOC(d_selfw_level, double, selfw_level.size());
+    if ((r = upload(plan, d_Cu, Cu))) return r;
+    if ((r = upload(plan, d_level, tree.level))) return r;
+    if ((r = upload(plan, d_selfw_level, selfw_level))) return r;
+    RecordArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.d = d;
+    ra.mixed = mixed ? 1 : 0;
+    ra.nimg = plan->nimg;
+    ra.ntgt = plan->ntgt;
+    std::memcpy(ra.Q, g.Q, sizeof(ra.Q));
+    std::memcpy(ra.R, g.R, sizeof(ra.R));
+    std::memcpy(ra.Rinv, g.Rinv, sizeof(ra.Rinv));
+    ra.y = plan->d_y_keep;
+    ra.orig = gb.d_orig;
+    ra.pos = gb.d_pos;
+    ra.leaf = gb.d_leaf;
+    ra.center = plan->d_box_center;
+    ra.Cu = d_Cu;
+    ra.tgt_of = gb.d_tgt_of;
+    ra.tgt_orig = gb.d_tgt_orig;
+    ra.box_level = d_level;
+    ra.self_w_level = d_selfw_level;
+    ra.src4 = plan->d_src4;
+    ra.src_lo = static_cast<float*>(plan->d_src_lo);
+    ra.src_orig = plan->d_src_orig;
+    ra.src_disp = plan->d_src_disp;
+    ra.tgt4 = plan->d_tgt4;
+    ra.tgt_lo = static_cast<float*>(plan->d_tgt_lo);
+    ra.tgt_orig_out = plan->d_tgt_orig;
+    ra.self_w = plan->d_self_w;
+    ra.tgt_leaf = d_tgt_leaf;
+    gpu_records(ra, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(plan->d_tgt_of_keep, gb.d_tgt_of, size_t(plan->ntgt) * sizeof(int), cudaMemcpyDeviceToDevice,
+                       s));
+    CK(cudaStreamSynchronize(s));
+    lap("source_target_records");
+    // ---- far field (device), subproblems (host) ----
+    plan->nspread = n;
+    int* d_bin_count;
+    SALLOC(d_bin_count, int, plan->nbins_tot);
+    FarLayoutArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
+    fa.d = d;
+    fa.mixed = mixed ? 1 : 0;
+    fa.n = n;
+    fa.ntgt = plan->ntgt;
+    for (int i = 0; i < 3; ++i) {
+        fa.M[i] = g.M[i];
+        fa.B[i] = plan->B[i];
+        fa.nbin[i] = plan->nbin[i];
+    }
+    fa.w = plan->w;
+    fa.nbins_tot = plan->nbins_tot;
+    fa.u = plan->d_u_keep;
+    fa.tgt_orig = gb.d_tgt_orig;
+    fa.pt_g0 = plan->d_pt_g0;
+    fa.pt_dq = plan->d_pt_dq;
+    fa.sp_orig = plan->d_spread_orig;
+    fa.bin_count = d_bin_count;
+    fa.t_g0 = plan->d_t_g0;
+    fa.t_dq = plan->d_t_dq;
+    if ((r = gpu_far_layout(fa, s, &msg)) != PDMK_OK) {
+        plan->msg = msg;
+        return r;
+    }
+    std::vector<int> bc(size_t(plan->nbins_tot));
+    CK(cudaMemcpy(bc.data(), d_bin_count, bc.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> bin_count(bc.begin(), bc.end());
+    std::vector<int4> subs;
+    std::vector<int> bin_sub_begin;
+    spread_subproblems(plan, bin_count, &subs, &bin_sub_begin);
+    plan->nsub = int(subs.size());
+    if ((r = alloc_subs(plan, subs.size()))) return r;
+    lap("far_field_layout");
+    // ---- per-box uploads ----
+    if ((r = upload(plan, plan->d_tleaf, tl))) return r;
+    if ((r = upload(plan, plan->d_list, dl.list))) return r;
+    if ((r = upload(plan, plan->d_box_src_begin, bsb))) return r;
+    if ((r = upload(plan, plan->d_box_src_count, bsc))) return r;
+    if ((r = upload(plan, plan->d_ent, ent))) return r;
+    if ((r = upload(plan, plan->d_ent_sh, ent_sh))) return r;
+    if ((r = upload(plan, plan->d_ent_shlo, ent_shlo))) return r;
+    if ((r = upload(plan, plan->d_sub, subs))) return r;
+    if ((r = upload(plan, plan->d_bin_sub_begin, bin_sub_begin))) return r;
+    CK(cudaMemcpyAsync(plan->d_q_user, d_q, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    lap("device_alloc_upload");
+    plan->pw.d_src4 = plan->d_src4;
+    plan->pw.d_tgt4 = plan->d_tgt4;
+    SortedSources ss_unused;
+    std::vector<int> none;
+    r = pw_set_sources(&plan->pw, tree, ss_unused, none, none, g, s, gb.d_leaf, plan->nimg);
+    if (r != PDMK_OK) return r;
+    r = set_charges_device(plan, false);
+    if (r != PDMK_OK) return r;
+    CK(cudaStreamSynchronize(s));
+    lap("plane_wave_layout_charges");
+    finish_info(plan, st, pairs, n_src, m);
+    plan->h_Cu.swap(Cu);
+    plan->h_tree = std::move(tree);
+    plan->h_u.clear();
+    plan->h_y.clear();
+    plan->h_src_disp.clear();
+    plan->h_src_orig.clear();
+    plan->h_src_is_orig.clear();
+    plan->host_copies = false;
+    plan->bl_ready = false;
+    plan->bl_buf = nullptr;  // freed with the source buffers
+    plan->setup_device = true;
+    lap("host_copies");
+    plan->ready = true;
+    return PDMK_OK;
+#undef SALLOC
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1906,6 +2439,16 @@ extern "C" int pdmk_stage_times(pdmk_plan plan, const char** names, double* ms, 
     return n;
 }
 
+extern "C" int pdmk_setup_times(pdmk_plan plan, const char** names, double* ms, int cap) {
+    if (!plan || cap < 0) return PDMK_ERR_BAD_ARG;
+    const int n = int(std::min(plan->setup_ms.size(), plan->setup_names.size()));
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (names) names[i] = plan->setup_names[i];
+        if (ms) ms[i] = plan->setup_ms[i];
+    }
+    return n;
+}
+
 extern "C" const char* pdmk_plan_message(pdmk_plan plan) {
     return plan ? plan->msg.c_str() : "";
 }
@@ -2378,8 +2921,10 @@ extern "C" int pdmk_eval_targets(pdmk_plan plan, int64_t m, const double* x, dou
     }
     for (double v : hx)
         if (!std::isfinite(v)) return PDMK_ERR_NONFINITE;
+    int r = ensure_host_copies(plan);
+    if (r != PDMK_OK) return r;
     TargetLayout L;
-    int r = build_target_layout(plan, m, hx.data(), &L);
+    r = build_target_layout(plan, m, hx.data(), &L);
     if (r != PDMK_OK) return r;
     // device scratch for this call (kept and reused while large enough)
     const size_t ts = tsize(plan);
@@ -2480,8 +3025,10 @@ static int bloch_setup(pdmk_plan plan) {
     if (plan->bl_ready) return PDMK_OK;
     const int d = plan->d;
     const Geometry& g = plan->g;
+    int r = ensure_host_copies(plan);
+    if (r != PDMK_OK) return r;
     double* p = nullptr;
-    int r = dalloc(plan, plan->src_allocs, &p, bloch_doubles(plan));
+    r = dalloc(plan, plan->src_allocs, &p, bloch_doubles(plan));
     if (r != PDMK_OK) return r;
     plan->bl_buf = p;
     BlochBufs b = bloch_layout(plan);

@@ -1,0 +1,986 @@
+// gpu_build.cu -- the source set-up on the device (Algorithm 1, steps 1-2; images of Sec. 3.4).
+//
+// Every point copy gets a 64-bit key: its root cell (axis 0 fastest, as the host's root
+// sort), then the interleaved bits of its cell at a fixed deep level K (axis a at bit a of
+// each d-bit digit, the coarsest digit first).  Sorted by key, the points of any box at level
+// L <= K form one contiguous run: the key prefix of the box.  The tree then follows from runs:
+//   * refinement: the boxes with more than n_s points below max_depth are the runs of more
+//     than n_s keys at each level (their ancestors are such runs too, so they exist);
+//   * level restriction (every colleague of the parent of a non-leaf box is non-leaf): one
+//     sweep from the deepest level up, adding the parent's colleagues of every non-leaf box
+//     of level L to the non-leaf set of level L - 1.  A forced split only makes leaves (a
+//     child with more than n_s points would have split its parent already), so one sweep
+//     reaches the closure;
+//   * the boxes of level L are the 2^d children of the non-leaf boxes of level L - 1, in key
+//     order, which is the host's level order (children of consecutive parents, in order).
+// The final order of the sources is by leaf and, within a leaf, by image index (a stable sort
+// of the image-ordered copies by their leaf's first position), the order the host's stable
+// splits leave.  All FP64 arithmetic is written with explicit round-to-nearest operations so
+// that no multiply-add is contracted: every coordinate, bound and record equals the host's.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+#include <cub/device/device_select.cuh>
+
+#include <algorithm>
+#include <cstring>
+
+#include "gpu_build.h"
+#include "pdmk.h"
+
+namespace pdmk {
+namespace {
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+constexpr int kThreads = 256;
+inline int blocks_for(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 1 << 20))); }
+
+struct Geo {
+    int d;
+    int periodic;
+    double Q[9], R[9], Rinv[9];
+    double lo[3], hi[3], rc;
+    int nroot[3];
+};
+
+Geo make_geo(const Geometry& g) {
+    Geo o;
+    std::memset(&o, 0, sizeof(o));
+    o.d = g.d;
+    o.periodic = g.periodic_root ? 1 : 0;
+    std::memcpy(o.Q, g.Q, sizeof(o.Q));
+    std::memcpy(o.R, g.R, sizeof(o.R));
+    std::memcpy(o.Rinv, g.Rinv, sizeof(o.Rinv));
+    for (int i = 0; i < 3; ++i) {
+        o.lo[i] = g.lo[i];
+        o.hi[i] = i < g.d ? g.lo[i] + g.nroot[i] * g.rc : 0.0;  // as the host build
+        o.nroot[i] = i < g.d ? g.nroot[i] : 1;
+    }
+    o.rc = g.rc;
+    return o;
+}
+
+struct ImgTab {
+    int ns;
+    int Bx[3];
+    long long dimx[3];
+    const int* sidx;
+    const double* trs;
+};
+
+// ---------------------------------------------------------------------------------------
+// orientation and wrapping; input checks
+
+__global__ void k_orient(Geo g, int64_t n, const double* __restrict__ y, double* __restrict__ u) {
+    const int d = g.d;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        double xo[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i)
+            for (int k = 0; k < d; ++k) xo[i] = dadd(xo[i], dmul(g.Q[i * d + k], y[j * d + k]));
+        for (int i = 0; i < d; ++i) {
+            double s = 0;
+            for (int k = 0; k < d; ++k) s = dadd(s, dmul(g.Rinv[i * d + k], xo[k]));
+            s = dsub(s, floor(s));
+            if (s >= 1.0) s = 0.0;
+            u[j * d + i] = s;
+        }
+    }
+}
+
+__global__ void k_check(int64_t n, int d, const double* __restrict__ y, const double* __restrict__ q,
+                        int* __restrict__ nonfinite, double* __restrict__ part) {
+    __shared__ double sh[2][kThreads];
+    double s = 0, a = 0;
+    bool bad = false;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        for (int k = 0; k < d; ++k) bad |= !isfinite(y[j * d + k]);
+        const double v = q[j];
+        bad |= !isfinite(v);
+        s += v;
+        a += fabs(v);
+    }
+    if (bad) atomicOr(nonfinite, 1);
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = a;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sh[0][0];
+        part[2 * blockIdx.x + 1] = sh[1][0];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// images (Sec. 3.4): the host's candidate ranges and in-box test, arithmetic for arithmetic
+
+__device__ __forceinline__ void frac_to_tree(const Geo& g, const double* uj, double* x) {
+    const int d = g.d;
+    for (int i = 0; i < d; ++i) {
+        double v = 0;
+        for (int k = i; k < d; ++k) v = dadd(v, dmul(g.R[i * d + k], uj[k]));
+        x[i] = v;
+    }
+}
+
+__device__ __forceinline__ bool in_domain(const Geo& g, const ImgTab& t, const double* x, int k) {
+    bool in = true;
+    for (int a = 0; a < g.d; ++a) {
+        const double p = dadd(x[a], t.trs[k * 3 + a]);
+        in &= (p >= g.lo[a] && p < g.hi[a]);
+    }
+    return in;
+}
+
+__device__ __forceinline__ void shift_range(const Geo& g, const ImgTab& t, const double* x, int a, const int* nv,
+                                            int* lo_n, int* hi_n) {
+    const int d = g.d;
+    double off = 0;
+    for (int k = a + 1; k < d; ++k) off = dadd(off, dmul(g.R[a * d + k], double(nv[k])));
+    const double raa = g.R[a * d + a];
+    const double l = ddiv(dsub(dsub(g.lo[a], x[a]), off), raa);
+    const double h = ddiv(dsub(dsub(g.hi[a], x[a]), off), raa);
+    const double sl = dmul(1e-9, dadd(1.0, fabs(l))), sh = dmul(1e-9, dadd(1.0, fabs(h)));
+    *lo_n = max(-t.Bx[a], int(ceil(dsub(l, sl))));
+    *hi_n = min(t.Bx[a], int(floor(dadd(h, sh))));
+}
+
+// calls f(k) for every accepted shift k > 0 in the host's loop order; false if the point
+// itself lies outside the extended domain
+template <class F>
+__device__ bool for_images(const Geo& g, const ImgTab& t, const double* x, F f) {
+    const int d = g.d;
+    if (!in_domain(g, t, x, 0)) return false;
+    int nv[3] = {0, 0, 0};
+    int l2 = 0, h2 = 0, l1 = 0, h1 = 0, l0 = 0, h0 = 0;
+    if (d == 3) shift_range(g, t, x, 2, nv, &l2, &h2);
+    for (int v2 = l2; v2 <= h2; ++v2) {
+        nv[2] = d == 3 ? v2 : 0;
+        shift_range(g, t, x, 1, nv, &l1, &h1);
+        for (int v1 = l1; v1 <= h1; ++v1) {
+            nv[1] = v1;
+            shift_range(g, t, x, 0, nv, &l0, &h0);
+            for (int v0 = l0; v0 <= h0; ++v0) {
+                nv[0] = v0;
+                long long fl = 0;
+                for (int a = d - 1; a >= 0; --a) fl = fl * t.dimx[a] + (nv[a] + t.Bx[a]);
+                const int k = t.sidx[fl];
+                if (k > 0 && in_domain(g, t, x, k)) f(k);
+            }
+        }
+    }
+    return true;
+}
+
+__global__ void k_image_count(Geo g, ImgTab t, int64_t n, const double* __restrict__ u, int* __restrict__ cnt,
+                              int* __restrict__ missing) {
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        double x[3];
+        frac_to_tree(g, u + j * g.d, x);
+        int c = 0;
+        if (!for_images(g, t, x, [&](int) { ++c; })) atomicOr(missing, 1);
+        cnt[j] = c;
+    }
+}
+
+__global__ void k_image_write(Geo g, ImgTab t, int64_t n, const double* __restrict__ u, const int* __restrict__ off,
+                              int* __restrict__ pk, int* __restrict__ pj) {
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        double x[3];
+        frac_to_tree(g, u + j * g.d, x);
+        int w = off[j];
+        for_images(g, t, x, [&](int k) {
+            pk[w] = k;
+            pj[w] = int(j);
+            ++w;
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// keys
+
+__device__ __forceinline__ unsigned long long morton(const long long* w, int d, int levels) {
+    unsigned long long m = 0;
+    for (int b = 0; b < levels; ++b)
+        for (int a = 0; a < d; ++a) m |= (unsigned long long)((w[a] >> b) & 1) << (d * b + a);
+    return m;
+}
+__device__ __forceinline__ void unmorton(unsigned long long m, int d, int levels, long long* w) {
+    for (int a = 0; a < d; ++a) w[a] = 0;
+    for (int b = 0; b < levels; ++b)
+        for (int a = 0; a < d; ++a) w[a] |= (long long)((m >> (d * b + a)) & 1) << b;
+}
+// box key of the level-L cell c (in range) and its inverse
+__device__ __forceinline__ unsigned long long box_key(const Geo& g, int L, const long long* c) {
+    long long root = 0, w[3] = {0, 0, 0};
+    for (int a = g.d - 1; a >= 0; --a) root = root * g.nroot[a] + (c[a] >> L);
+    for (int a = 0; a < g.d; ++a) w[a] = c[a] & ((1LL << L) - 1);
+    return ((unsigned long long)root << (g.d * L)) | morton(w, g.d, L);
+}
+__device__ __forceinline__ void box_cell(const Geo& g, int L, unsigned long long key, long long* c) {
+    long long root = (long long)(key >> (g.d * L));
+    long long w[3];
+    unmorton(key & ((1ULL << (g.d * L)) - 1), g.d, L, w);
+    for (int a = 0; a < g.d; ++a) {
+        const long long rc = root % g.nroot[a];
+        root /= g.nroot[a];
+        c[a] = (rc << L) | w[a];
+    }
+}
+
+// positions of the copies in image order, and their keys
+__global__ void k_image_pos(Geo g, ImgTab t, int64_t n, int64_t nimg, int K, const double* __restrict__ u,
+                            const int* __restrict__ pk, const int* __restrict__ pj, double* __restrict__ pos,
+                            unsigned long long* __restrict__ key, int* __restrict__ val) {
+    const int d = g.d;
+    const double scale = ldexp(1.0, K);
+    for (int64_t im = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; im < nimg; im += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t j = im < n ? im : pj[im - n];
+        const int k = im < n ? 0 : pk[im - n];
+        double x[3];
+        frac_to_tree(g, u + j * d, x);
+        long long root = 0, w[3] = {0, 0, 0};
+        long long rcell[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) {
+            const double p = dadd(x[a], t.trs[k * 3 + a]);
+            pos[im * d + a] = p;
+            const double tsc = ddiv(dsub(p, g.lo[a]), g.rc);
+            long long ci = (long long)floor(tsc);
+            ci = min(max(ci, 0LL), (long long)g.nroot[a] - 1);
+            rcell[a] = ci;
+            long long cK = (long long)floor(dmul(tsc, scale));
+            cK = min(max(cK, 0LL), ((long long)g.nroot[a] << K) - 1);
+            w[a] = cK & ((1LL << K) - 1);
+        }
+        for (int a = d - 1; a >= 0; --a) root = root * g.nroot[a] + rcell[a];
+        key[im] = ((unsigned long long)root << (d * K)) | morton(w, d, K);
+        val[im] = int(im);
+    }
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long* a, int64_t lo, int64_t hi,
+                                                   unsigned long long v) {
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// level-L runs of more than n_s keys (refinement, Algorithm 1 step 2)
+__global__ void k_runs(int64_t nimg, const unsigned long long* __restrict__ key, int shift, int n_s,
+                       unsigned long long* __restrict__ pref_out, unsigned char* __restrict__ flag) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nimg; i += int64_t(gridDim.x) * blockDim.x) {
+        const unsigned long long p = key[i] >> shift;
+        unsigned char f = 0;
+        if (i == 0 || (key[i - 1] >> shift) != p) {
+            const int64_t e = lower_bound_u64(key, i, nimg, (p + 1) << shift);
+            f = (e - i) > n_s;
+        }
+        pref_out[i] = p;
+        flag[i] = f;
+    }
+}
+
+// the parent's colleagues of every non-leaf box of level L (keys at level L - 1; invalid:
+// all ones)
+__global__ void k_restrict_cands(Geo g, int L, const unsigned long long* __restrict__ nl, int64_t cnt,
+                                 unsigned long long* __restrict__ out) {
+    const int d = g.d;
+    int nn = 1;
+    for (int a = 0; a < d; ++a) nn *= 3;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cnt; i += int64_t(gridDim.x) * blockDim.x) {
+        const unsigned long long P = nl[i] >> d;
+        long long c[3];
+        box_cell(g, L - 1, P, c);
+        for (int o = 0; o < nn; ++o) {
+            long long c2[3] = {0, 0, 0};
+            int r = o;
+            bool ok = true;
+            for (int a = 0; a < d; ++a) {
+                c2[a] = c[a] + (r % 3) - 1;
+                r /= 3;
+                const long long dim = (long long)g.nroot[a] << (L - 1);
+                if (g.periodic) c2[a] = (c2[a] + dim) % dim;
+                ok &= (c2[a] >= 0 && c2[a] < dim);
+            }
+            out[i * nn + o] = ok ? box_key(g, L - 1, c2) : ~0ULL;
+        }
+    }
+}
+
+__global__ void k_iota_u64(unsigned long long* __restrict__ a, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        a[i] = (unsigned long long)i;
+}
+__global__ void k_iota_int(int* __restrict__ a, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        a[i] = int(i);
+}
+__global__ void k_expand(const unsigned long long* __restrict__ nl, int64_t cnt, int d,
+                         unsigned long long* __restrict__ out) {
+    const int nc = 1 << d;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cnt * nc; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = (nl[i / nc] << d) | (unsigned long long)(i % nc);
+}
+
+struct BoxOut {
+    int* level;
+    long long* coord;
+    int* parent;
+    int* child0;
+    long long* src_b;
+    long long* src_e;
+    double* center;
+    int* colleague;
+};
+
+__global__ void k_boxes(Geo g, int L, int K, const unsigned long long* __restrict__ keys, int64_t nL, int baseL,
+                        const unsigned long long* __restrict__ keysUp, int64_t nUp, int baseUp,
+                        const unsigned long long* __restrict__ nlUp, const unsigned long long* __restrict__ nlL,
+                        int64_t nnlL, int baseDown, const unsigned long long* __restrict__ skey, int64_t nimg,
+                        BoxOut o) {
+    const int d = g.d;
+    int nn = 1;
+    for (int a = 0; a < d; ++a) nn *= 3;
+    const double h = ddiv(g.rc, double(1LL << L));
+    const int shift = d * (K - L);
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nL; i += int64_t(gridDim.x) * blockDim.x) {
+        const unsigned long long key = keys[i];
+        const int64_t b = baseL + i;
+        long long c[3] = {0, 0, 0};
+        box_cell(g, L, key, c);
+        o.level[b] = L;
+        for (int a = 0; a < d; ++a) {
+            o.coord[b * d + a] = c[a];
+            o.center[b * d + a] = dadd(g.lo[a], dmul(dadd(double(c[a]), 0.5), h));
+        }
+        if (L == 0) {
+            o.parent[b] = -1;
+        } else {
+            const unsigned long long pk = nlUp[i >> d];
+            o.parent[b] = baseUp + int(lower_bound_u64(keysUp, 0, nUp, pk));
+        }
+        const int64_t ci = lower_bound_u64(nlL, 0, nnlL, key);
+        o.child0[b] = (ci < nnlL && nlL[ci] == key) ? int(baseDown + ci * (1 << d)) : -1;
+        o.src_b[b] = lower_bound_u64(skey, 0, nimg, key << shift);
+        o.src_e[b] = lower_bound_u64(skey, 0, nimg, (key + 1) << shift);
+        for (int oo = 0; oo < nn; ++oo) {
+            long long c2[3] = {0, 0, 0};
+            int r = oo;
+            bool ok = true;
+            for (int a = 0; a < d; ++a) {
+                c2[a] = c[a] + (r % 3) - 1;
+                r /= 3;
+                const long long dim = (long long)g.nroot[a] << L;
+                if (g.periodic) c2[a] = (c2[a] + dim) % dim;
+                ok &= (c2[a] >= 0 && c2[a] < dim);
+            }
+            int X = -1;
+            if (ok) {
+                const unsigned long long k2 = box_key(g, L, c2);
+                const int64_t x = lower_bound_u64(keys, 0, nL, k2);
+                if (x < nL && keys[x] == k2) X = baseL + int(x);
+            }
+            o.colleague[b * nn + oo] = X;
+        }
+    }
+}
+
+// leaf of every key-sorted copy, and its leaf's first position per image
+__global__ void k_leaf_descent(int d, int K, int64_t nimg, const unsigned long long* __restrict__ skey,
+                               const int* __restrict__ sval, const int* __restrict__ child0,
+                               const long long* __restrict__ src_b, int* __restrict__ leaf_pos,
+                               int* __restrict__ lkey_img) {
+    const unsigned long long mask = (1ULL << d) - 1;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nimg; i += int64_t(gridDim.x) * blockDim.x) {
+        const unsigned long long key = skey[i];
+        int b = int(key >> (d * K));
+        int L = 0;
+        while (child0[b] >= 0) {
+            ++L;
+            b = child0[b] + int((key >> (d * (K - L))) & mask);
+        }
+        leaf_pos[i] = b;
+        lkey_img[sval[i]] = int(src_b[b]);
+    }
+}
+
+__global__ void k_sorted(int d, int64_t n, int64_t nimg, const int* __restrict__ simg, const int* __restrict__ pj,
+                         const double* __restrict__ pos_img, int* __restrict__ orig, double* __restrict__ pos,
+                         int* __restrict__ is_tgt) {
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < nimg; j += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t im = simg[j];
+        orig[j] = im < n ? int(im) : pj[im - n];
+        for (int a = 0; a < d; ++a) pos[j * d + a] = pos_img[im * d + a];
+        is_tgt[j] = im < n ? 1 : 0;
+    }
+}
+
+__global__ void k_targets_of(int64_t nimg, const int* __restrict__ is_tgt, const int* __restrict__ tpos,
+                             const int* __restrict__ orig, int* __restrict__ tgt_of, int* __restrict__ tgt_orig) {
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < nimg; j += int64_t(gridDim.x) * blockDim.x)
+        if (is_tgt[j]) {
+            tgt_of[tpos[j]] = int(j);
+            tgt_orig[tpos[j]] = orig[j];
+        }
+}
+
+__global__ void k_box_tgt(int64_t nb, const long long* __restrict__ sb, const long long* __restrict__ se,
+                          const int* __restrict__ tpos, long long* __restrict__ tb, long long* __restrict__ te) {
+    for (int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; b < nb; b += int64_t(gridDim.x) * blockDim.x) {
+        tb[b] = tpos[sb[b]];
+        te[b] = tpos[se[b]];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// records (the host build's per-point passes)
+
+template <typename T>
+__device__ __forceinline__ void put_rec(void* buf, int64_t idx, double v) {
+    static_cast<T*>(buf)[idx] = T(v);
+}
+
+__device__ __forceinline__ void mat_vec(int d, const double* M, const double* v, double* out, bool transpose) {
+    for (int i = 0; i < d; ++i) {
+        double s = 0;
+        for (int k = 0; k < d; ++k) s = dadd(s, dmul(transpose ? M[k * d + i] : M[i * d + k], v[k]));
+        out[i] = s;
+    }
+}
+
+// leaf-relative position of sorted source j, in the tree frame, and the caller-frame lattice
+// vector of its copy (zero for the point itself)
+__device__ void relative_of(const RecordArgs& a, int64_t j, double* rel, double* disp) {
+    const int d = a.d;
+    const int b = a.leaf[j];
+    const int64_t o = a.orig[j];
+    double yo[3] = {0, 0, 0}, xo[3], m[3], D[3], E[3], du[3];
+    for (int k = 0; k < d; ++k) yo[k] = a.y[o * d + k];
+    mat_vec(d, a.Q, yo, xo, false);
+    bool shifted = false;
+    for (int i = 0; i < d; ++i) {
+        double f = 0;
+        for (int k = 0; k < d; ++k) f = dadd(f, dmul(a.Rinv[i * d + k], dsub(a.pos[j * d + k], xo[k])));
+        m[i] = nearbyint(f);
+        shifted |= m[i] != 0.0;
+    }
+    for (int k = 0; k < d; ++k) disp[k] = 0.0;
+    if (shifted) {
+        double Rm[3];
+        for (int i = 0; i < d; ++i) {
+            double s = 0;
+            for (int k = 0; k < d; ++k) s = dadd(s, dmul(a.R[i * d + k], m[k]));
+            Rm[i] = s;
+            D[i] = dsub(a.center[int64_t(b) * d + i], s);
+        }
+        mat_vec(d, a.Q, D, E, true);
+        mat_vec(d, a.Q, Rm, disp, true);
+    } else {
+        for (int i = 0; i < d; ++i) E[i] = a.Cu[int64_t(b) * d + i];
+    }
+    for (int k = 0; k < d; ++k) du[k] = dsub(yo[k], E[k]);
+    mat_vec(d, a.Q, du, rel, false);
+}
+
+template <typename T>
+__global__ void k_src_records(RecordArgs a) {
+    const int d = a.d;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < a.nimg; j += int64_t(gridDim.x) * blockDim.x) {
+        double rel[3], disp[3];
+        relative_of(a, j, rel, disp);
+        for (int k = 0; k < d; ++k) {
+            put_rec<T>(a.src4, j * 4 + k, rel[k]);
+            if (a.mixed) a.src_lo[j * 4 + k] = float(rel[k] - double(float(rel[k])));
+            a.src_disp[j * d + k] = disp[k];
+        }
+        a.src_orig[j] = a.orig[j];
+    }
+}
+
+template <typename T>
+__global__ void k_tgt_records(RecordArgs a) {
+    const int d = a.d;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < a.ntgt; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t j = a.tgt_of[t];
+        const int b = a.leaf[j];
+        double rel[3], disp[3];
+        relative_of(a, j, rel, disp);
+        a.tgt_leaf[t] = b;
+        for (int k = 0; k < d; ++k) {
+            put_rec<T>(a.tgt4, t * 4 + k, rel[k]);
+            if (a.mixed) a.tgt_lo[t * 4 + k] = float(rel[k] - double(float(rel[k])));
+        }
+        a.tgt_orig_out[t] = a.tgt_orig[t];
+        a.self_w[t] = a.self_w_level[a.box_level[b]];
+    }
+}
+
+__global__ void k_box_cu(int nb, int d, Geo g, const double* __restrict__ center, double* __restrict__ Cu) {
+    for (int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; b < nb; b += int64_t(gridDim.x) * blockDim.x)
+        mat_vec(d, g.Q, center + b * d, Cu + b * d, true);
+}
+
+// ---------------------------------------------------------------------------------------
+// far-field layout (window starts in FP64, as the host build)
+
+__device__ __forceinline__ void grid_coord(double uu, int M, int w, int* g0, double* del) {
+    const double Mu = dmul(double(M), uu);
+    int gg = int(ceil(dsub(Mu, 0.5 * w)));
+    *del = dsub(Mu, double(gg));
+    const int fw = w / 2;
+    const int key = gg + fw;
+    const int wrap = key >= 0 ? key / M : -((-key + M - 1) / M);
+    gg -= wrap * M;
+    *g0 = gg;
+}
+
+__global__ void k_far_bins(FarLayoutArgs a, int* __restrict__ bin, int4* __restrict__ g0o,
+                           double* __restrict__ del3, int* __restrict__ vals, int* __restrict__ bin_count) {
+    const int fw = a.w / 2;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < a.n; j += int64_t(gridDim.x) * blockDim.x) {
+        int64_t bb = 0;
+        int off[3] = {0, 0, 0};
+        double dl[3] = {0, 0, 0};
+        for (int i = a.d - 1; i >= 0; --i) {
+            int g0;
+            double del;
+            grid_coord(a.u[j * a.d + i], a.M[i], a.w, &g0, &del);
+            const int key = g0 + fw;
+            const int bi = key / a.B[i];
+            off[i] = key - bi * a.B[i];
+            dl[i] = del;
+            bb = bb * a.nbin[i] + bi;
+        }
+        bin[j] = int(bb);
+        g0o[j] = make_int4(off[0], off[1], off[2], 0);
+        for (int i = 0; i < 3; ++i) del3[j * 3 + i] = dl[i];
+        vals[j] = int(j);
+        atomicAdd(&bin_count[bb], 1);
+    }
+}
+
+template <typename T>
+__global__ void k_far_points(FarLayoutArgs a, const int* __restrict__ order, const int4* __restrict__ g0o,
+                             const double* __restrict__ del3) {
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < a.n; k += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t j = order[k];
+        a.pt_g0[k] = g0o[j];
+        for (int i = 0; i < 3; ++i) put_rec<T>(a.pt_dq, k * 4 + i, del3[j * 3 + i]);
+        put_rec<T>(a.pt_dq, k * 4 + 3, 0.0);
+        a.sp_orig[k] = int(j);
+    }
+}
+
+template <typename T>
+__global__ void k_far_targets(FarLayoutArgs a) {
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < a.ntgt; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t j = a.tgt_orig[t];
+        int gg[3] = {0, 0, 0};
+        double dl[4] = {0, 0, 0, 0};
+        for (int i = 0; i < a.d; ++i) grid_coord(a.u[j * a.d + i], a.M[i], a.w, &gg[i], &dl[i]);
+        for (int i = 0; i < 4; ++i) put_rec<T>(a.t_dq, t * 4 + i, dl[i]);
+        for (int i = 0; i < a.d; ++i) gg[i] = ((gg[i] % a.M[i]) + a.M[i]) % a.M[i];
+        a.t_g0[t] = make_int4(gg[0], gg[1], gg[2], 0);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host helpers
+
+struct Scratch {
+    std::vector<void*> ptrs;
+    ~Scratch() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <class X>
+    X* get(size_t count) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return static_cast<X*>(p);
+    }
+};
+
+int bits_for(uint64_t v) {  // bits to hold values < v
+    int b = 0;
+    while (b < 64 && (uint64_t(1) << b) < v) ++b;
+    return b;
+}
+
+#define GB_CK(call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) {                                 \
+            if (msg) *msg = cudaGetErrorString(e_);              \
+            return PDMK_ERR_CUDA;                                \
+        }                                                        \
+    } while (0)
+#define GB_ALLOC(ptr, X, count)                                  \
+    do {                                                         \
+        ptr = scr.get<X>(count);                                 \
+        if (!ptr) {                                              \
+            if (msg) *msg = "device allocation failed (set-up)"; \
+            return PDMK_ERR_CUDA;                                \
+        }                                                        \
+    } while (0)
+
+template <class X>
+int own(GpuBuild* b, X** out, size_t count, std::string* msg) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) {
+        cudaGetLastError();
+        if (msg) *msg = "device allocation failed (set-up)";
+        return PDMK_ERR_CUDA;
+    }
+    b->allocs.push_back(p);
+    *out = static_cast<X*>(p);
+    return PDMK_OK;
+}
+
+}  // namespace
+
+void gpu_build_free(GpuBuild* b) {
+    for (void* p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+    b->d_u = nullptr;
+    b->d_orig = nullptr;
+    b->d_pos = nullptr;
+    b->d_leaf = nullptr;
+    b->d_tgt_of = nullptr;
+    b->d_tgt_orig = nullptr;
+}
+
+void gpu_orient(const Geometry& g, int64_t n, const double* y, double* u, cudaStream_t s) {
+    if (n > 0) k_orient<<<blocks_for(n), kThreads, 0, s>>>(make_geo(g), n, y, u);
+}
+
+void gpu_check_inputs(int64_t n, int d, const double* y, const double* q, int* d_nonfinite, double* d_part, int nblk,
+                      cudaStream_t s) {
+    k_check<<<nblk, kThreads, 0, s>>>(n, d, y, q, d_nonfinite, d_part);
+}
+
+int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStream_t s, GpuBuild* bo, Tree* t,
+                   BuildStats* st, std::string* msg) {
+    const int d = g.d;
+    const Geo geo = make_geo(g);
+    Scratch scr;
+    // ---- images ----
+    ImageShifts tab;
+    image_shifts(g, &tab);
+    ImgTab it;
+    it.ns = tab.ns;
+    for (int a = 0; a < 3; ++a) {
+        it.Bx[a] = tab.Bx[a];
+        it.dimx[a] = tab.dimx[a];
+    }
+    int* d_sidx;
+    double* d_trs;
+    GB_ALLOC(d_sidx, int, tab.sidx.size());
+    GB_ALLOC(d_trs, double, tab.trs.size());
+    GB_CK(cudaMemcpyAsync(d_sidx, tab.sidx.data(), tab.sidx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    GB_CK(cudaMemcpyAsync(d_trs, tab.trs.data(), tab.trs.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    it.sidx = d_sidx;
+    it.trs = d_trs;
+    int *d_cnt, *d_off, *d_flag;
+    GB_ALLOC(d_cnt, int, n + 1);
+    GB_ALLOC(d_off, int, n + 1);
+    GB_ALLOC(d_flag, int, 1);
+    GB_CK(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+    GB_CK(cudaMemsetAsync(d_cnt + n, 0, sizeof(int), s));
+    k_image_count<<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_cnt, d_flag);
+    size_t tb = 0;
+    GB_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, d_cnt, d_off, int(n + 1), s));
+    void* d_tmp = nullptr;
+    size_t tmp_bytes = 0;
+    auto tmp = [&](size_t need) -> void* {
+        if (need > tmp_bytes) {
+            d_tmp = scr.get<unsigned char>(need);
+            tmp_bytes = d_tmp ? need : 0;
+        }
+        return d_tmp;
+    };
+    if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+    GB_CK(cub::DeviceScan::ExclusiveSum(d_tmp, tb, d_cnt, d_off, int(n + 1), s));
+    int h_flag = 0, h_nextra = 0;
+    GB_CK(cudaMemcpyAsync(&h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(&h_nextra, d_off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaStreamSynchronize(s));
+    if (h_flag) {
+        if (msg) *msg = "a point lies outside the extended domain";
+        return PDMK_ERR_INTERNAL;
+    }
+    const int64_t nx = h_nextra;
+    const int64_t nimg = n + nx;
+    if (nimg >= (int64_t(1) << 30)) return kGpuBuildUnsupported;
+    int *d_pk, *d_pj, *d_pk2, *d_pj2;
+    GB_ALLOC(d_pk, int, nx);
+    GB_ALLOC(d_pj, int, nx);
+    GB_ALLOC(d_pk2, int, nx);
+    GB_ALLOC(d_pj2, int, nx);
+    if (nx > 0) {
+        k_image_write<<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_off, d_pk, d_pj);
+        const int kb = std::max(1, bits_for(uint64_t(tab.ns)));
+        GB_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, d_pk, d_pk2, d_pj, d_pj2, int(nx), 0, kb, s));
+        if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+        GB_CK(cub::DeviceRadixSort::SortPairs(d_tmp, tb, d_pk, d_pk2, d_pj, d_pj2, int(nx), 0, kb, s));
+    }
+    // ---- keys ----
+    int64_t nroot_tot = 1;
+    for (int a = 0; a < d; ++a) nroot_tot *= g.nroot[a];
+    const int rbits = bits_for(uint64_t(nroot_tot));
+    const int K = std::min((63 - rbits) / d, 30);
+    if (K < 1) return kGpuBuildUnsupported;
+    double* d_posimg;
+    unsigned long long *d_key, *d_key2;
+    int *d_val, *d_val2;
+    GB_ALLOC(d_posimg, double, size_t(nimg) * d);
+    GB_ALLOC(d_key, unsigned long long, nimg);
+    GB_ALLOC(d_key2, unsigned long long, nimg);
+    GB_ALLOC(d_val, int, nimg);
+    GB_ALLOC(d_val2, int, nimg);
+    k_image_pos<<<blocks_for(nimg), kThreads, 0, s>>>(geo, it, n, nimg, K, bo->d_u, d_pk2, d_pj2, d_posimg, d_key,
+                                                      d_val);
+    const int keybits = rbits + d * K;
+    GB_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, d_key, d_key2, d_val, d_val2, int(nimg), 0, keybits, s));
+    if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+    GB_CK(cub::DeviceRadixSort::SortPairs(d_tmp, tb, d_key, d_key2, d_val, d_val2, int(nimg), 0, keybits, s));
+    const unsigned long long* skey = d_key2;
+    const int* sval = d_val2;
+    // ---- refinement: non-leaf boxes per level ----
+    std::vector<unsigned long long*> nl;  // device arrays per level
+    std::vector<int64_t> nnl;
+    unsigned long long* d_pref;
+    unsigned char* d_rflag;
+    int64_t* d_nsel;
+    GB_ALLOC(d_pref, unsigned long long, nimg);
+    GB_ALLOC(d_rflag, unsigned char, nimg);
+    GB_ALLOC(d_nsel, int64_t, 1);
+    for (int L = 0;; ++L) {
+        if (L >= max_depth) break;
+        if (L > K) return kGpuBuildUnsupported;
+        k_runs<<<blocks_for(nimg), kThreads, 0, s>>>(nimg, skey, d * (K - L), n_s, d_pref, d_rflag);
+        unsigned long long* out;
+        GB_ALLOC(out, unsigned long long, nimg);
+        GB_CK(cub::DeviceSelect::Flagged(nullptr, tb, d_pref, d_rflag, out, d_nsel, nimg, s));
+        if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+        GB_CK(cub::DeviceSelect::Flagged(d_tmp, tb, d_pref, d_rflag, out, d_nsel, nimg, s));
+        int64_t h_n = 0;
+        GB_CK(cudaMemcpyAsync(&h_n, d_nsel, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GB_CK(cudaStreamSynchronize(s));
+        if (h_n == 0) break;
+        if (L == K) return kGpuBuildUnsupported;  // a box of the deepest key level would split
+        nl.push_back(out);
+        nnl.push_back(h_n);
+    }
+    // ---- level restriction, deepest level first ----
+    int nn = 1;
+    for (int a = 0; a < d; ++a) nn *= 3;
+    for (int L = int(nl.size()) - 1; L >= 1; --L) {
+        const int64_t nc = nnl[L] * nn, tot = nnl[L - 1] + nc;
+        unsigned long long *cat, *cat2, *uq;
+        GB_ALLOC(cat, unsigned long long, tot);
+        GB_ALLOC(cat2, unsigned long long, tot);
+        GB_ALLOC(uq, unsigned long long, tot);
+        GB_CK(cudaMemcpyAsync(cat, nl[L - 1], nnl[L - 1] * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+        k_restrict_cands<<<blocks_for(nnl[L]), kThreads, 0, s>>>(geo, L, nl[L], nnl[L], cat + nnl[L - 1]);
+        GB_CK(cub::DeviceRadixSort::SortKeys(nullptr, tb, cat, cat2, int(tot), 0, 64, s));
+        if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+        GB_CK(cub::DeviceRadixSort::SortKeys(d_tmp, tb, cat, cat2, int(tot), 0, 64, s));
+        GB_CK(cub::DeviceSelect::Unique(nullptr, tb, cat2, uq, d_nsel, tot, s));
+        if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+        GB_CK(cub::DeviceSelect::Unique(d_tmp, tb, cat2, uq, d_nsel, tot, s));
+        int64_t h_n = 0;
+        unsigned long long last = 0;
+        GB_CK(cudaMemcpyAsync(&h_n, d_nsel, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GB_CK(cudaStreamSynchronize(s));
+        GB_CK(cudaMemcpy(&last, uq + (h_n - 1), sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        if (last == ~0ULL) --h_n;
+        nl[L - 1] = uq;
+        nnl[L - 1] = h_n;
+    }
+    // ---- boxes per level ----
+    const int nlev = int(nl.size()) + 1;
+    std::vector<unsigned long long*> lk(nlev);
+    std::vector<int64_t> nlk(nlev);
+    GB_ALLOC(lk[0], unsigned long long, nroot_tot);
+    nlk[0] = nroot_tot;
+    k_iota_u64<<<blocks_for(nroot_tot), kThreads, 0, s>>>(lk[0], nroot_tot);
+    for (int L = 1; L < nlev; ++L) {
+        nlk[L] = nnl[L - 1] << d;
+        GB_ALLOC(lk[L], unsigned long long, nlk[L]);
+        k_expand<<<blocks_for(nlk[L]), kThreads, 0, s>>>(nl[L - 1], nnl[L - 1], d, lk[L]);
+    }
+    std::vector<int> lstart(nlev + 1, 0);
+    for (int L = 0; L < nlev; ++L) {
+        if (int64_t(lstart[L]) + nlk[L] >= (int64_t(1) << 31)) return kGpuBuildUnsupported;
+        lstart[L + 1] = lstart[L] + int(nlk[L]);
+    }
+    const int nb = lstart[nlev];
+    BoxOut bx;
+    GB_ALLOC(bx.level, int, nb);
+    GB_ALLOC(bx.coord, long long, size_t(nb) * d);
+    GB_ALLOC(bx.parent, int, nb);
+    GB_ALLOC(bx.child0, int, nb);
+    GB_ALLOC(bx.src_b, long long, nb);
+    GB_ALLOC(bx.src_e, long long, nb);
+    GB_ALLOC(bx.center, double, size_t(nb) * d);
+    GB_ALLOC(bx.colleague, int, size_t(nb) * nn);
+    for (int L = 0; L < nlev; ++L) {
+        const bool has_down = L < int(nl.size());
+        k_boxes<<<blocks_for(nlk[L]), kThreads, 0, s>>>(
+            geo, L, K, lk[L], nlk[L], lstart[L], L > 0 ? lk[L - 1] : nullptr, L > 0 ? nlk[L - 1] : 0,
+            L > 0 ? lstart[L - 1] : 0, L > 0 ? nl[L - 1] : nullptr, has_down ? nl[L] : nullptr,
+            has_down ? nnl[L] : 0, L + 1 <= nlev ? lstart[std::min(L + 1, nlev)] : 0, skey, nimg, bx);
+    }
+    // ---- final order: by leaf, then by image index ----
+    int *d_leafpos, *d_lkey, *d_lkey2, *d_iota, *d_simg;
+    GB_ALLOC(d_leafpos, int, nimg);
+    GB_ALLOC(d_lkey, int, nimg);
+    GB_ALLOC(d_lkey2, int, nimg);
+    GB_ALLOC(d_iota, int, nimg);
+    GB_ALLOC(d_simg, int, nimg);
+    k_leaf_descent<<<blocks_for(nimg), kThreads, 0, s>>>(d, K, nimg, skey, sval, bx.child0, bx.src_b, d_leafpos,
+                                                         d_lkey);
+    k_iota_int<<<blocks_for(nimg), kThreads, 0, s>>>(d_iota, nimg);
+    const int lb = std::max(1, bits_for(uint64_t(nimg)));
+    GB_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, d_lkey, d_lkey2, d_iota, d_simg, int(nimg), 0, lb, s));
+    if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+    GB_CK(cub::DeviceRadixSort::SortPairs(d_tmp, tb, d_lkey, d_lkey2, d_iota, d_simg, int(nimg), 0, lb, s));
+    // ---- sorted outputs ----
+    int r;
+    if ((r = own(bo, &bo->d_orig, nimg, msg))) return r;
+    if ((r = own(bo, &bo->d_pos, size_t(nimg) * d, msg))) return r;
+    if ((r = own(bo, &bo->d_tgt_of, n, msg))) return r;
+    if ((r = own(bo, &bo->d_tgt_orig, n, msg))) return r;
+    if ((r = own(bo, &bo->d_leaf, nimg, msg))) return r;
+    int *d_istgt, *d_tpos;
+    GB_ALLOC(d_istgt, int, nimg + 1);
+    GB_ALLOC(d_tpos, int, nimg + 1);
+    GB_CK(cudaMemsetAsync(d_istgt + nimg, 0, sizeof(int), s));
+    k_sorted<<<blocks_for(nimg), kThreads, 0, s>>>(d, n, nimg, d_simg, d_pj2, d_posimg, bo->d_orig, bo->d_pos,
+                                                   d_istgt);
+    GB_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, d_istgt, d_tpos, int(nimg + 1), s));
+    if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+    GB_CK(cub::DeviceScan::ExclusiveSum(d_tmp, tb, d_istgt, d_tpos, int(nimg + 1), s));
+    k_targets_of<<<blocks_for(nimg), kThreads, 0, s>>>(nimg, d_istgt, d_tpos, bo->d_orig, bo->d_tgt_of,
+                                                       bo->d_tgt_orig);
+    long long *d_tb, *d_te;
+    GB_ALLOC(d_tb, long long, nb);
+    GB_ALLOC(d_te, long long, nb);
+    k_box_tgt<<<blocks_for(nb), kThreads, 0, s>>>(nb, bx.src_b, bx.src_e, d_tpos, d_tb, d_te);
+    // the key-sorted and the final order share every leaf's range
+    GB_CK(cudaMemcpyAsync(bo->d_leaf, d_leafpos, size_t(nimg) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    int h_ntgt = 0;
+    GB_CK(cudaMemcpyAsync(&h_ntgt, d_tpos + nimg, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // ---- the host tree ----
+    t->d = d;
+    for (int a = 0; a < 3; ++a) t->nroot[a] = a < d ? g.nroot[a] : 1;
+    t->periodic = g.periodic_root;
+    t->nlevels = nlev;
+    t->level_start = lstart;
+    t->level.resize(nb);
+    t->coord.resize(size_t(nb) * d);
+    t->parent.resize(nb);
+    t->child0.resize(nb);
+    t->src_begin.resize(nb);
+    t->src_end.resize(nb);
+    t->tgt_begin.resize(nb);
+    t->tgt_end.resize(nb);
+    t->center.resize(size_t(nb) * d);
+    t->colleague.resize(size_t(nb) * nn);
+    static_assert(sizeof(long long) == sizeof(int64_t), "64-bit box arrays");
+    GB_CK(cudaMemcpyAsync(t->level.data(), bx.level, size_t(nb) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->coord.data(), bx.coord, size_t(nb) * d * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->parent.data(), bx.parent, size_t(nb) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->child0.data(), bx.child0, size_t(nb) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->src_begin.data(), bx.src_b, size_t(nb) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->src_end.data(), bx.src_e, size_t(nb) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->tgt_begin.data(), d_tb, size_t(nb) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->tgt_end.data(), d_te, size_t(nb) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->center.data(), bx.center, size_t(nb) * d * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(t->colleague.data(), bx.colleague, size_t(nb) * nn * sizeof(int), cudaMemcpyDeviceToHost,
+                          s));
+    GB_CK(cudaStreamSynchronize(s));
+    bo->n = n;
+    bo->nimg = nimg;
+    bo->ntgt = h_ntgt;
+    bo->key_levels = K;
+    if (st) {
+        st->n = n;
+        st->n_images = nimg;
+        st->nboxes = nb;
+        int nlv = 0;
+        for (int k = 0; k < nb; ++k) nlv += t->child0[k] < 0;
+        st->nleaves = nlv;
+        st->depth = nlev - 1;
+    }
+    return PDMK_OK;
+}
+
+void gpu_box_cu(int nb, int d, const double* Q, const double* center, double* Cu, cudaStream_t s) {
+    Geo g;
+    std::memset(&g, 0, sizeof(g));
+    g.d = d;
+    std::memcpy(g.Q, Q, sizeof(g.Q));
+    if (nb > 0) k_box_cu<<<blocks_for(nb), kThreads, 0, s>>>(nb, d, g, center, Cu);
+}
+
+void gpu_records(const RecordArgs& a, cudaStream_t s) {
+    if (a.nimg > 0) {
+        if (a.mixed) k_src_records<float><<<blocks_for(a.nimg), kThreads, 0, s>>>(a);
+        else k_src_records<double><<<blocks_for(a.nimg), kThreads, 0, s>>>(a);
+    }
+    if (a.ntgt > 0) {
+        if (a.mixed) k_tgt_records<float><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
+        else k_tgt_records<double><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
+    }
+}
+
+int gpu_far_layout(const FarLayoutArgs& a, cudaStream_t s, std::string* msg) {
+    Scratch scr;
+    int *d_bin, *d_bin2, *d_vals, *d_order;
+    int4* d_g0;
+    double* d_del;
+    GB_ALLOC(d_bin, int, a.n);
+    GB_ALLOC(d_bin2, int, a.n);
+    GB_ALLOC(d_vals, int, a.n);
+    GB_ALLOC(d_order, int, a.n);
+    GB_ALLOC(d_g0, int4, a.n);
+    GB_ALLOC(d_del, double, size_t(a.n) * 3);
+    GB_CK(cudaMemsetAsync(a.bin_count, 0, size_t(a.nbins_tot) * sizeof(int), s));
+    if (a.n > 0) {
+        k_far_bins<<<blocks_for(a.n), kThreads, 0, s>>>(a, d_bin, d_g0, d_del, d_vals, a.bin_count);
+        size_t tb = 0;
+        const int kb = std::max(1, bits_for(uint64_t(a.nbins_tot)));
+        GB_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, d_bin, d_bin2, d_vals, d_order, int(a.n), 0, kb, s));
+        void* d_tmp;
+        GB_ALLOC(d_tmp, unsigned char, tb);
+        GB_CK(cub::DeviceRadixSort::SortPairs(d_tmp, tb, d_bin, d_bin2, d_vals, d_order, int(a.n), 0, kb, s));
+        if (a.mixed) k_far_points<float><<<blocks_for(a.n), kThreads, 0, s>>>(a, d_order, d_g0, d_del);
+        else k_far_points<double><<<blocks_for(a.n), kThreads, 0, s>>>(a, d_order, d_g0, d_del);
+    }
+    if (a.ntgt > 0) {
+        if (a.mixed) k_far_targets<float><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
+        else k_far_targets<double><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
+    }
+    GB_CK(cudaGetLastError());
+    GB_CK(cudaStreamSynchronize(s));  // the scratch is freed on return
+    return PDMK_OK;
+}
+
+}  // namespace pdmk

@@ -1,0 +1,103 @@
+// gpu_build.h -- the source set-up on the device (Algorithm 1, steps 1-2, and Sec. 3.4):
+// orientation and wrapping, image enumeration, the adaptive tree with its level restriction,
+// the sorted order of sources and targets, and the per-point records of the near field, the
+// plane-wave passes and the far field.  It produces exactly the tree, order and records of
+// the host build (host_plan.cpp): the same arithmetic in the same order (FP64, no
+// contraction), images in shift order, boxes in level order with children in order, and
+// sources sorted by leaf and then by image index.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "host_plan.h"
+
+namespace pdmk {
+
+// device arrays of one build, freed by gpu_build_free
+struct GpuBuild {
+    int64_t n = 0, nimg = 0, ntgt = 0;
+    int key_levels = 0;         // depth of the point keys (levels a tree may reach)
+    double* d_u = nullptr;      // n x d fractional coordinates of the points in [0, 1)
+    int* d_orig = nullptr;      // per sorted source: point index
+    double* d_pos = nullptr;    // per sorted source: oriented position (d)
+    int* d_leaf = nullptr;      // per sorted source: leaf box
+    int* d_tgt_of = nullptr;    // per sorted target: sorted source index of the point
+    int* d_tgt_orig = nullptr;  // per sorted target: point index
+    std::vector<void*> allocs;
+};
+void gpu_build_free(GpuBuild* b);
+
+// Returned when the tree would need more levels than the 64-bit point keys hold (or more
+// images than 32-bit indices): the host build serves these inputs.
+constexpr int kGpuBuildUnsupported = 1;
+
+// u (device, n x d) must already hold the wrapped fractional coordinates.  Fills the host
+// tree t (every per-box array, as build_tree does), the device arrays of b and st.
+int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStream_t s, GpuBuild* b, Tree* t,
+                   BuildStats* st, std::string* msg);
+
+// ---- per-point passes (launchers; all arrays on the device) ----
+// the caller's positions (n x d) to wrapped fractional coordinates u (the orientation Q, then
+// R^{-1}, minus the floor)
+void gpu_orient(const Geometry& g, int64_t n, const double* y, double* u, cudaStream_t s);
+// nonfinite inputs (flag), and per-block partial sums of q and |q| (nblk x 2, summed by the
+// caller in block order)
+void gpu_check_inputs(int64_t n, int d, const double* y, const double* q, int* d_nonfinite, double* d_part,
+                      int nblk, cudaStream_t s);
+
+// leaf-relative records of the sorted sources and of the targets (the host build's
+// "leaf-relative coordinates": caller-frame leaf centres Cu, lattice-shift displacement of
+// every copy, hi/lo split in mixed precision)
+struct RecordArgs {
+    int d;
+    int mixed;
+    int64_t nimg, ntgt;
+    double Q[9], R[9], Rinv[9];
+    const double* y;        // caller positions (n x d)
+    const int* orig;        // per sorted source
+    const double* pos;      // per sorted source (oriented, d)
+    const int* leaf;        // per sorted source
+    const double* center;   // per box (tree frame, d)
+    const double* Cu;       // per box (caller frame, d)
+    const int* tgt_of;      // per sorted target
+    const int* tgt_orig;    // per sorted target
+    const int* box_level;   // per box
+    const double* self_w_level;  // W_{h_L}(0) per level
+    void* src4;             // out: 4 T per sorted source
+    float* src_lo;          // out (mixed): 4 per sorted source
+    int* src_orig;          // out
+    double* src_disp;       // out: caller-frame lattice vector per sorted source (d)
+    void* tgt4;             // out
+    float* tgt_lo;          // out (mixed)
+    int* tgt_orig_out;      // out
+    double* self_w;         // out: per sorted target
+    int* tgt_leaf;          // out: per sorted target
+};
+void gpu_records(const RecordArgs& a, cudaStream_t s);
+// caller-frame box centres Cu = Q^T c_b
+void gpu_box_cu(int nb, int d, const double* Q, const double* center, double* Cu, cudaStream_t s);
+
+// far-field layout: window starts, offsets and bins of every point, the points in bin order
+// (stable), and the interpolation records of the targets
+struct FarLayoutArgs {
+    int d;
+    int mixed;
+    int64_t n, ntgt;
+    int M[3], B[3], nbin[3];
+    int w;
+    int nbins_tot;
+    const double* u;       // n x d
+    const int* tgt_orig;   // per sorted target
+    int4* pt_g0;           // out: per point in bin order
+    void* pt_dq;           // out: 4 T per point in bin order
+    int* sp_orig;          // out: point index per position in bin order
+    int* bin_count;        // out: points per bin (nbins_tot)
+    int4* t_g0;            // out: per sorted target
+    void* t_dq;            // out
+};
+int gpu_far_layout(const FarLayoutArgs& a, cudaStream_t s, std::string* msg);
+
+}  // namespace pdmk

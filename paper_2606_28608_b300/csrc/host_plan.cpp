@@ -1,5 +1,7 @@
 // host_plan.cpp -- FP64 host planning: prolates, kernel tables, geometry, images, tree.
 #include "host_plan.h"
+
+#include <chrono>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -614,23 +616,8 @@ static void split_local(Builder& bld, LocalTree& lt, int bi) {
 }
 }  // namespace
 
-int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_depth, Tree* t,
-               SortedSources* s, BuildStats* st) {
+void image_shifts(const Geometry& g, ImageShifts* out) {
     const int d = g.d;
-    Builder bld;
-    bld.d = d;
-    bld.g = &g;
-    // ---- images (Sec. 3.4): shifts within the bounds of Eq. (3.13), in-box test ----
-    std::vector<int64_t> img_orig;
-    double hi[3];
-    for (int i = 0; i < d; ++i) hi[i] = g.lo[i] + g.nroot[i] * g.rc;
-    std::vector<double> x(n * d);
-    for (int64_t j = 0; j < n; ++j)
-        for (int i = 0; i < d; ++i) {
-            double v = 0;
-            for (int k = i; k < d; ++k) v += g.R[i * d + k] * u[j * d + k];
-            x[j * d + i] = v;
-        }
     // the originals first (shift 0), then every other admissible shift
     std::vector<std::vector<int>> shifts;
     shifts.push_back(std::vector<int>(d, 0));
@@ -656,28 +643,72 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
         nvec[lev] = 0;
     };
     if (!g.periodic_root) rec(d - 1);  // a periodic root holds the originals only
+    const int ns = int(shifts.size());
+    out->ns = ns;
+    for (int a = 0; a < 3; ++a) {
+        out->Bx[a] = 0;
+        out->dimx[a] = 1;
+    }
+    for (const auto& sh : shifts)
+        for (int a = 0; a < d; ++a) out->Bx[a] = std::max(out->Bx[a], std::abs(sh[a]));
+    int64_t ntab = 1;
+    for (int a = 0; a < d; ++a) {
+        out->dimx[a] = 2 * out->Bx[a] + 1;
+        ntab *= out->dimx[a];
+    }
+    auto flat = [&](const int* nv) {
+        int64_t f = 0;
+        for (int a = d - 1; a >= 0; --a) f = f * out->dimx[a] + (nv[a] + out->Bx[a]);
+        return f;
+    };
+    out->sidx.assign(static_cast<size_t>(ntab), -1);
+    out->trs.assign(size_t(ns) * 3, 0.0);
+    for (int k = 0; k < ns; ++k) {
+        out->sidx[size_t(flat(shifts[k].data()))] = k;
+        for (int a = 0; a < d; ++a)
+            for (int kk = a; kk < d; ++kk) out->trs[size_t(k) * 3 + a] += g.R[a * d + kk] * shifts[k][kk];
+    }
+}
+
+int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_depth, Tree* t,
+               SortedSources* s, BuildStats* st) {
+    const int d = g.d;
+    Builder bld;
+    bld.d = d;
+    bld.g = &g;
+    auto clk = std::chrono::steady_clock::now();
+    auto lap = [&](int k) {
+        const auto now = std::chrono::steady_clock::now();
+        if (st) st->phase_ms[k] = std::chrono::duration<double, std::milli>(now - clk).count();
+        clk = now;
+    };
+    // ---- images (Sec. 3.4): shifts within the bounds of Eq. (3.13), in-box test ----
+    std::vector<int64_t> img_orig;
+    double hi[3];
+    for (int i = 0; i < d; ++i) hi[i] = g.lo[i] + g.nroot[i] * g.rc;
+    std::vector<double> x(n * d);
+    for (int64_t j = 0; j < n; ++j)
+        for (int i = 0; i < d; ++i) {
+            double v = 0;
+            for (int k = i; k < d; ++k) v += g.R[i * d + k] * u[j * d + k];
+            x[j * d + i] = v;
+        }
     // Images in shift order, and within a shift in point order.  Each point's admissible
     // shifts are enumerated from the in-box bounds of the triangular frame (axis by axis from
     // the last, with a small slack against rounding) and then accepted by the same test with
     // the same arithmetic as a scan of every listed shift; listed shifts only.
-    const int ns = int(shifts.size());
-    int Bx[3] = {0, 0, 0};
-    for (const auto& sh : shifts)
-        for (int a = 0; a < d; ++a) Bx[a] = std::max(Bx[a], std::abs(sh[a]));
-    int64_t dimx[3] = {1, 1, 1}, ntab = 1;
-    for (int a = 0; a < d; ++a) { dimx[a] = 2 * Bx[a] + 1; ntab *= dimx[a]; }
+    ImageShifts tab;
+    image_shifts(g, &tab);
+    const int ns = tab.ns;
+    const int* Bx = tab.Bx;
+    const int64_t* dimx = tab.dimx;
     auto flat = [&](const int* nv) {
         int64_t f = 0;
         for (int a = d - 1; a >= 0; --a) f = f * dimx[a] + (nv[a] + Bx[a]);
         return f;
     };
-    std::vector<int> sidx(static_cast<size_t>(ntab), -1);
-    std::vector<double> trs(size_t(ns) * 3, 0.0);
-    for (int k = 0; k < ns; ++k) {
-        sidx[size_t(flat(shifts[k].data()))] = k;
-        for (int a = 0; a < d; ++a)
-            for (int kk = a; kk < d; ++kk) trs[size_t(k) * 3 + a] += g.R[a * d + kk] * shifts[k][kk];
-    }
+    const std::vector<int>& sidx = tab.sidx;
+    const std::vector<double>& trs = tab.trs;
     int nthr = 1;
 #ifdef _OPENMP
     nthr = omp_get_max_threads();
@@ -765,6 +796,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     for (int64_t j = 0; j < nimg; ++j)
         for (int a = 0; a < d; ++a) bld.tsc[size_t(j) * d + a] = (bld.pos[size_t(j) * d + a] - g.lo[a]) / g.rc;
     bld.map.reserve(size_t(std::max<int64_t>(1024, 4 * nimg / std::max(n_s, 1))));
+    lap(0);
     // ---- root boxes: counting sort by root cell ----
     int64_t nroot_tot = 1;
     for (int a = 0; a < d; ++a) nroot_tot *= g.nroot[a];
@@ -825,6 +857,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
         bld.boxes.push_back(B);
         bld.map[BoxKey{0, {B.c[0], B.c[1], B.c[2]}}] = int(cell);
     }
+    lap(1);
     // ---- refine boxes holding more than n_s sources (Algorithm 1, step 2) ----
     // Root boxes refine independently (in parallel); their subtrees are then appended in
     // root order.  Box numbering here does not matter: the tree is renumbered canonically
@@ -855,6 +888,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
             LocalTree().boxes.swap(lt.boxes);
         }
     }
+    lap(2);
     // ---- level restriction: every colleague of the parent of a non-leaf box is non-leaf.
     // This keeps the leaves that meet a leaf's colleague neighbourhood within one level of it.
     // The rule's closure is unique and the renumbering below is canonical, so only boxes that
@@ -914,6 +948,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
             }
         work.swap(bld.split_log);
     }
+    lap(3);
     // ---- renumber in level order (children of consecutive parents stay contiguous) ----
     const int nbtot = int(bld.boxes.size());
     std::vector<int> order;
@@ -985,6 +1020,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
             t->colleague[size_t(k) * nn + o] = X < 0 ? -1 : newid[X];
         }
     }
+    lap(4);
     // ---- sorted sources and targets (the originals, in sorted order) ----
     s->orig.resize(nimg);
     s->pos.resize(size_t(nimg) * d);
@@ -1015,6 +1051,7 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
         t->tgt_begin[k] = is_tgt_prefix[t->src_begin[k]];
         t->tgt_end[k] = is_tgt_prefix[t->src_end[k]];
     }
+    lap(5);
     if (st) {
         st->n = n;
         st->n_images = nimg;

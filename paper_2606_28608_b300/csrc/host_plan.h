@@ -138,7 +138,25 @@ struct BuildStats {
     int64_t n = 0, n_images = 0;
     int nboxes = 0, nleaves = 0, depth = 0;
     int64_t near_pairs = 0;
+    // host milliseconds of the phases of build_tree, in the order of kBuildPhases
+    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
 };
+constexpr const char* kBuildPhases[6] = {"tree_images", "tree_root_sort", "tree_refine",
+                                         "tree_level_restriction", "tree_renumber_colleagues",
+                                         "tree_sorted_outputs"};
+
+// The lattice shifts n of the images (Sec. 3.4, bounds of Eq. (3.13)): index 0 is no shift,
+// then the nested loops with n_d outermost; none for a periodic root.  sidx maps the flat
+// index of n + Bx (axis 0 fastest, extents dimx) to the shift's index or -1; trs holds R n
+// (3 per shift).
+struct ImageShifts {
+    int ns = 1;
+    int Bx[3] = {0, 0, 0};
+    int64_t dimx[3] = {1, 1, 1};
+    std::vector<int> sidx;
+    std::vector<double> trs;
+};
+void image_shifts(const Geometry& g, ImageShifts* out);
 
 // Images + tree + sort.  u: n*d fractional coordinates of the originals in [0,1).
 int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_depth, Tree* t,

@@ -43,8 +43,11 @@ struct PwPlan {
 void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables& kt, int n_proxy, int n_pw,
                     bool mixed);
 bool pw_supported(const PwPlan* pw);
+// leaf_of: the leaf of every sorted source on the host, or empty with d_leaf_of (nimg entries)
+// on the device
 int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& s, const std::vector<int>& leaf_of,
-                   const std::vector<int>& tgt_leaf, const Geometry& g, cudaStream_t stream);
+                   const std::vector<int>& tgt_leaf, const Geometry& g, cudaStream_t stream,
+                   const int* d_leaf_of, int64_t nimg);
 int pw_set_charges(PwPlan* pw, cudaStream_t stream);
 // phase 0: leaf moments + upward merges; 1: outgoing plane waves; 2: translation +
 // incoming; 3: downward pass; 4: evaluation at leaf targets

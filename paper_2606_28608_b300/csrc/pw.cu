@@ -2383,7 +2383,8 @@ static bool direct2d_orders(const PwDims& pd, bool mixed) {
 }
 
 int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const std::vector<int>& leaf_of,
-                   const std::vector<int>& /*tgt_leaf*/, const Geometry& g, cudaStream_t stream) {
+                   const std::vector<int>& /*tgt_leaf*/, const Geometry& g, cudaStream_t stream,
+                   const int* d_leaf_of, int64_t nimg) {
     PwImpl* I = impl(pw);
     const int d = t.d;
     const int nb = int(t.level.size());
@@ -2582,7 +2583,14 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         if ((r = pw_upload(pw, &I->d_ditems, ditems, stream))) return r;
         if ((r = pw_upload(pw, &I->d_obox, obox, stream))) return r;
         if ((r = pw_alloc(pw, &I->d_seg_done, size_t(std::max(nout, 1))))) return r;
-        if ((r = pw_upload(pw, &I->d_src_leaf, src_leaf, stream))) return r;
+        if (!src_leaf.empty() || !d_leaf_of) {
+            if ((r = pw_upload(pw, &I->d_src_leaf, src_leaf, stream))) return r;
+        } else {
+            if ((r = pw_alloc(pw, &I->d_src_leaf, size_t(std::max<int64_t>(nimg, 1))))) return r;
+            if (cudaMemcpyAsync(I->d_src_leaf, d_leaf_of, size_t(nimg) * sizeof(int), cudaMemcpyDeviceToDevice,
+                                stream) != cudaSuccess)
+                return PDMK_ERR_CUDA;
+        }
         if ((r = pw_upload(pw, &I->d_bcoord, bcoord, stream))) return r;
         if ((r = pw_alloc(pw, &p, size_t(std::max(I->nditems, 1)) * I->dims.np * ts))) return r;
         I->d_part = p;
