@@ -47,6 +47,11 @@ WORKLOADS = {
         make=lambda: W.triclinic3d_clusters(4_000_000), golden="triclinic3d_4m",
         desc="triclinic3d_clusters: a1=(1,0,0) a2=(0.3,2,0) a3=(0.5,0.7,17), N=4000000, 64 anisotropic "
              "gaussian clusters sigma in [1e-4,1e-2] of the cell, q~U(-1,1) minus mean"),
+    # the headline cell's shape at 1/8 of the points (profiling captures: a few GB on the device)
+    "triclinic3d_500k": dict(
+        make=lambda: W.triclinic3d_clusters(500_000), golden=None,
+        desc="triclinic3d_clusters: a1=(1,0,0) a2=(0.3,2,0) a3=(0.5,0.7,17), N=500000, 64 anisotropic "
+             "gaussian clusters sigma in [1e-4,1e-2] of the cell, q~U(-1,1) minus mean"),
     "oblique2d_200k": dict(
         make=lambda: W.oblique2d_clusters(200_000), golden=None,
         desc="oblique2d_clusters: a1=(1,0) a2=(0.45,0.85), N=200000, 16 gaussian clusters sigma in "
@@ -142,10 +147,11 @@ def stage_flops(info, d, leaf_folded, out_folded):
       interp      per target: 2 w^d FMAs (value, x-derivative) + d*w window series (value, derivative)
       nearfield   per visited pair 5 (2D) / 7 (3D); per pair inside the support two
                   residual series of n_A, n_B terms (2 flops/term) + 16 (2D) / 22 (3D)
-      pw_upward   per (out box, source) pair: the p^d moment outer product (2 flops each) and
-                  2 d p Chebyshev recurrence flops; per merge parent 12 p^3 (2D generic) or
-                  28 p^4 (3D: the eight children summed axis by axis, 14 p^4 multiply-adds)
-      pw_out      per box (2D parity form): 2 (K+1) p^2 + 4 (K+1)^2 p; credited to pw_upward
+      pw_moments  per (out box, source) pair: the p^d moment outer product (2 flops each) and
+                  2 d p Chebyshev recurrence flops
+      pw_merge    per merge parent 12 p^3 (2D generic) or 28 p^4 (3D: the eight children summed
+                  axis by axis, 14 p^4 multiply-adds)
+      pw_out      per box (2D parity form): 2 (K+1) p^2 + 4 (K+1)^2 p; credited to pw_moments
                   where the moments launch computes the outgoing waves itself;
                   3D parity form: 2 (K+1) p^3 + 4 (K+1)^2 p^2 + 4 (K+1)^2 (2K+1) p
       pw_translate_in per box (2D parity form): ~100 (K+1)^2 + 4 (K+1)^2 p + 2 (K+1) p^2;
@@ -167,7 +173,8 @@ def stage_flops(info, d, leaf_folded, out_folded):
     out["nearfield"] = info["near_pairs"] * visit + info["near_pairs_in"] * inside
     merge_unit = 12 * p ** 3 if d == 2 else 28 * p ** 4
     down_unit = 12 * p ** 3 if d == 2 else 32 * p ** 4
-    out["pw_upward"] = info["pw_moment_sources"] * (2 * p ** d + 2 * d * p) + info["pw_merge_parents"] * merge_unit
+    out["pw_moments"] = info["pw_moment_sources"] * (2 * p ** d + 2 * d * p)
+    out["pw_merge"] = info["pw_merge_parents"] * merge_unit
     if d == 2:
         out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** 2 + 4 * (K + 1) ** 2 * p)
         out["pw_translate_in"] = info["n_pw_boxes_in"] * (100 * (K + 1) ** 2 + 4 * (K + 1) ** 2 * p
@@ -179,7 +186,7 @@ def stage_flops(info, d, leaf_folded, out_folded):
                                                           + 2 * (K + 1) * p ** 3 + 4 * (K + 1) ** 2 * p ** 2
                                                           + 4 * (K + 1) ** 2 * n1 * p)
     if out_folded:
-        out["pw_upward"] += out["pw_out"]
+        out["pw_moments"] += out["pw_out"]
         out["pw_out"] = 0
     leaf = info["pw_eval_targets"] * 4 * p ** d
     out["pw_downward"] = info["pw_down_parents"] * down_unit + (leaf if leaf_folded else 0)
@@ -191,18 +198,18 @@ def stage_flops(info, d, leaf_folded, out_folded):
 # `ncu` capture of the kernel as it stands (profiles/ holds the summaries); absent where no
 # capture of the current kernel exists
 STAGE_TRAFFIC = {
-    "oblique2d_200k": {"nearfield": 17922560, "pw_upward": 6190336, "pw_downward": 13728768},
-    "triclinic3d_4m": {},
+    "oblique2d_200k": {"nearfield": 17922560, "pw_moments": 6190336, "pw_downward": 13728768},
+    "triclinic3d_4m": {"nearfield": 2306000000},  # 2.17 GB read + 0.136 GB written (k_near_warp)
 }
 
 STAGE_KERNELS = {
     2: {"spread": "k_spread_halo + k_fold_whole", "interp": "k_interp_halo", "nearfield": "k_near_warp",
-        "pw_upward": "k_moments_direct2d (outgoing waves folded in)", "pw_out": "k_pw_out",
-        "pw_translate_in": "k_pw_in2d_p",
+        "pw_moments": "k_moments_direct2d (outgoing waves folded in)", "pw_merge": "k_merge2d_p",
+        "pw_out": "k_pw_out", "pw_translate_in": "k_pw_in2d_p",
         "pw_downward": "k_down_persist2d (leaf evaluation folded in)", "pw_leaf_eval": "k_leaf_eval"},
-    3: {"spread": "k_spread + k_fold", "interp": "k_interp", "nearfield": "k_near_warp",
-        "pw_upward": "k_leaf_moments3d_p + k_merge3d_p / k_merge3d_q", "pw_out": "k_pw_out3d_p",
-        "pw_translate_in": "k_pw_in3d_p", "pw_downward": "k_down3d_q", "pw_leaf_eval": "k_leaf_eval3d_p"},
+    3: {"spread": "k_spread3d_reg + k_fold", "interp": "k_interp3d_w", "nearfield": "k_near_warp",
+        "pw_moments": "k_leaf_moments3d_gemm", "pw_merge": "k_merge3d_r", "pw_out": "k_pw_out3d_p",
+        "pw_translate_in": "k_pw_in3d_p", "pw_downward": "k_down3d_r", "pw_leaf_eval": "k_leaf_eval3d_gemm"},
 }
 
 
@@ -349,7 +356,7 @@ def stage_profile(P, g, prec, stream, pot, grad, flush, nprof=3):
 
 def stage_roofline(acc, info, d, peak):
     leaf_folded = acc.get("pw_leaf_eval", 0.0) < 0.05 * acc.get("pw_downward", 0.0)
-    out_folded = acc.get("pw_out", 0.0) < 0.05 * acc.get("pw_upward", 0.0)
+    out_folded = acc.get("pw_out", 0.0) < 0.05 * acc.get("pw_moments", 0.0)
     fl = stage_flops(info, d, leaf_folded, out_folded)
     per = {}
     for k, f in fl.items():
@@ -476,7 +483,7 @@ def main():
     t_set0 = time.perf_counter()
     plan = make("mixed")
     torch.cuda.synchronize()
-    t_set_sources = time.perf_counter() - t_set0  # plan + host tree build + device layouts
+    t_set_sources = time.perf_counter() - t_set0  # plan + device tree build + layouts
     for _ in range(args.warmup):
         plan.eval_device(pot, grad)
     if pg:
@@ -491,12 +498,12 @@ def main():
     info = plan.info()
 
     # ---- end to end through the C ABI with host buffers, every step: positions and charges
-    # in (page-locked), tree build and device layouts, evaluation, potential + gradient out
+    # in (page-locked), tree build and layouts, evaluation, potential + gradient out
     y_host = torch.from_numpy(np.ascontiguousarray(g["y"])).pin_memory().numpy()
     q_host = torch.from_numpy(np.ascontiguousarray(g["q"])).pin_memory().numpy()
     pot_host = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
     grad_host = torch.empty((n, d), dtype=torch.float64).pin_memory().numpy()
-    reps = 2
+    reps = 5
     plan.set_sources(y_host, q_host)
     plan.eval(out=(pot_host, grad_host))
     t0 = time.perf_counter()
@@ -504,10 +511,12 @@ def main():
         plan.set_sources(y_host, q_host)
         plan.eval(out=(pot_host, grad_host))
     e2e_t = (time.perf_counter() - t0) / reps
+    setup_phases = {k: round(v, 2) for k, v in plan.setup_times().items()}
     e2e = {"value": ws * n / e2e_t, "unit": "points/s", "h2d_bytes_per_step": 8 * n * (d + 1),
            "d2h_bytes_per_step": 8 * n * (1 + d),
-           "per_step": "pdmk_set_sources (positions + charges from pinned host memory, tree build, device "
-                       "layouts) + pdmk_eval into pinned host arrays"}
+           "per_step": "pdmk_set_sources (positions + charges from pinned host memory, tree build and "
+                       "layouts on the device, lists on the host) + pdmk_eval into pinned host arrays",
+           "set_sources_phases_ms": setup_phases}
     # the same with fixed positions: charges in, potential + gradient out
     reps_c = max(3, args.steps // 2)
     plan.set_charges(q_host)

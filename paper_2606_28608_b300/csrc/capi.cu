@@ -848,9 +848,11 @@ static void lattice_shift(const Geometry& g, int code, double* out) {
 // the host in both.
 
 // near-field leaf descriptors and direct-list entries (per box)
+// (with_entries false: the entries are left to the device, gpu_near_entries)
 static void near_layout(pdmk_plan plan, const Tree& tree, const DirectLists& dl, const std::vector<double>& Cu,
                         std::vector<TLeaf>* tl_out, std::vector<int2>* ent_out, std::vector<unsigned char>* ent_sh_out,
-                        std::vector<float>* ent_shlo_out, std::vector<int>* bsb_out, std::vector<int>* bsc_out) {
+                        std::vector<float>* ent_shlo_out, std::vector<int>* bsb_out, std::vector<int>* bsc_out,
+                        bool with_entries) {
     const int d = plan->d;
     const Geometry& g = plan->g;
     const bool mixed = plan->opts.precision == PDMK_MIXED;
@@ -892,11 +894,11 @@ static void near_layout(pdmk_plan plan, const Tree& tree, const DirectLists& dl,
     std::vector<int2>& ent = *ent_out;
     std::vector<unsigned char>& ent_sh = *ent_sh_out;
     std::vector<float>& ent_shlo = *ent_shlo_out;
-    ent.assign(dl.list.size(), int2{0, 0});
-    ent_sh.assign(dl.list.size() * 4 * ts, 0);
-    ent_shlo.assign(mixed ? dl.list.size() * 4 : 0, 0.0f);
+    ent.assign(with_entries ? dl.list.size() : 0, int2{0, 0});
+    ent_sh.assign(with_entries ? dl.list.size() * 4 * ts : 0, 0);
+    ent_shlo.assign(with_entries && mixed ? dl.list.size() * 4 : 0, 0.0f);
 #pragma omp parallel for schedule(dynamic, 256)
-    for (int64_t k = 0; k < int64_t(dl.tleaf.size()); ++k) {
+    for (int64_t k = 0; k < (with_entries ? int64_t(dl.tleaf.size()) : 0); ++k) {
         const int tb = dl.tleaf[k];
         for (int64_t e = dl.list_begin[k]; e < dl.list_begin[k + 1]; ++e) {
             const int sb = dl.list[e];
@@ -932,7 +934,7 @@ static void near_layout(pdmk_plan plan, const Tree& tree, const DirectLists& dl,
     std::vector<int64_t> cost(tl.size(), 0);
     for (size_t k = 0; k < tl.size(); ++k) {
         int64_t ns = 0;
-        for (int e = tl[k].list_begin; e < tl[k].list_begin + tl[k].list_count; ++e) ns += ent[e].y;
+        for (int e = tl[k].list_begin; e < tl[k].list_begin + tl[k].list_count; ++e) ns += bsc[dl.list[e]];
         cost[k] = ns * int64_t(tl[k].tgt_count);
     }
     std::vector<size_t> ord(tl.size());
@@ -1402,7 +1404,7 @@ static int set_points_host(pdmk_plan plan, int64_t n_src, const double* y, const
     std::vector<unsigned char> ent_sh;
     std::vector<float> ent_shlo;
     std::vector<int> bsb, bsc;
-    near_layout(plan, tree, dl, Cu, &tl, &ent, &ent_sh, &ent_shlo, &bsb, &bsc);
+    near_layout(plan, tree, dl, Cu, &tl, &ent, &ent_sh, &ent_shlo, &bsb, &bsc, true);
     plan->nnear = int(tl.size());
     plan->nlist = int64_t(dl.list.size());
     lap("near_field_entries");
@@ -1652,10 +1654,10 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     std::vector<unsigned char> ent_sh;
     std::vector<float> ent_shlo;
     std::vector<int> bsb, bsc;
-    near_layout(plan, tree, dl, Cu, &tl, &ent, &ent_sh, &ent_shlo, &bsb, &bsc);
+    near_layout(plan, tree, dl, Cu, &tl, &ent, &ent_sh, &ent_shlo, &bsb, &bsc, false);
     plan->nnear = int(tl.size());
     plan->nlist = int64_t(dl.list.size());
-    lap("near_field_entries");
+    lap("near_field_descriptors");
     // ---- per-point records (device) ----
     if ((r = alloc_sources(plan, tl.size(), dl.list.size()))) return r;
     DALLOC(AL, plan->d_src_disp, double, size_t(plan->nimg) * d);
@@ -1758,13 +1760,45 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     if ((r = upload(plan, plan->d_list, dl.list))) return r;
     if ((r = upload(plan, plan->d_box_src_begin, bsb))) return r;
     if ((r = upload(plan, plan->d_box_src_count, bsc))) return r;
-    if ((r = upload(plan, plan->d_ent, ent))) return r;
-    if ((r = upload(plan, plan->d_ent_sh, ent_sh))) return r;
-    if ((r = upload(plan, plan->d_ent_shlo, ent_shlo))) return r;
     if ((r = upload(plan, plan->d_sub, subs))) return r;
     if ((r = upload(plan, plan->d_bin_sub_begin, bin_sub_begin))) return r;
     CK(cudaMemcpyAsync(plan->d_q_user, d_q, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    lap("device_alloc_upload");
+    // near-field entries (device): source ranges and leaf-to-leaf shifts
+    if (plan->nlist > 0) {
+        int *d_tleafb, *d_shift;
+        long long* d_lb;
+        SALLOC(d_tleafb, int, dl.tleaf.size());
+        SALLOC(d_lb, long long, dl.list_begin.size());
+        SALLOC(d_shift, int, dl.shift.size());
+        static_assert(sizeof(long long) == sizeof(int64_t), "64-bit list offsets");
+        if ((r = upload(plan, d_tleafb, dl.tleaf))) return r;
+        CK(cudaMemcpyAsync(d_lb, dl.list_begin.data(), dl.list_begin.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           s));
+        if ((r = upload(plan, d_shift, dl.shift))) return r;
+        CK(cudaMemsetAsync(plan->d_ent_sh, 0, size_t(plan->nlist) * 4 * ts, s));
+        if (mixed) CK(cudaMemsetAsync(plan->d_ent_shlo, 0, size_t(plan->nlist) * 4 * sizeof(float), s));
+        EntryArgs ea;
+        std::memset(&ea, 0, sizeof(ea));
+        ea.d = d;
+        ea.mixed = mixed ? 1 : 0;
+        ea.nlist = plan->nlist;
+        ea.ntleaf = int(dl.tleaf.size());
+        std::memcpy(ea.Q, g.Q, sizeof(ea.Q));
+        for (int code = 0; code < 27; ++code) lattice_shift(g, code, &ea.Ln[code * 3]);
+        ea.tleaf = d_tleafb;
+        ea.list_begin = d_lb;
+        ea.list = plan->d_list;
+        ea.shift = d_shift;
+        ea.bsb = plan->d_box_src_begin;
+        ea.bsc = plan->d_box_src_count;
+        ea.Cu = d_Cu;
+        ea.ent = plan->d_ent;
+        ea.ent_sh = plan->d_ent_sh;
+        ea.ent_shlo = static_cast<float*>(plan->d_ent_shlo);
+        gpu_near_entries(ea, s);
+        CK(cudaGetLastError());
+    }
+    lap("device_alloc_upload_entries");
     plan->pw.d_src4 = plan->d_src4;
     plan->pw.d_tgt4 = plan->d_tgt4;
     SortedSources ss_unused;
@@ -2264,8 +2298,9 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
     }
     if ((r = stage_mark(plan, "interp"))) return r;
     // ---- near field: plane-wave passes, then the direct residual sum ----
-    static const char* pw_names[5] = {"pw_upward", "pw_out", "pw_translate_in", "pw_downward", "pw_leaf_eval"};
-    for (int ph = 0; ph < 5; ++ph) {
+    static const char* pw_names[kPwPhases] = {"pw_moments", "pw_merge",    "pw_out",
+                                              "pw_translate_in", "pw_downward", "pw_leaf_eval"};
+    for (int ph = 0; ph < kPwPhases; ++ph) {
         r = pw_eval(&plan->pw, s_pw, ph);
         if (r != PDMK_OK) return r;
         if ((r = stage_mark(plan, pw_names[ph]))) return r;
@@ -2811,7 +2846,7 @@ static int run_eval_targets(pdmk_plan plan, const TargetLayout& L, char* buf, do
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, int64_t(plan->nsm) * 8)));
     // sources' side: the far-field grid and the stored local expansions
     if ((r = far_grid<T, D>(plan, s, false))) return r;
-    for (int ph = 0; ph < 4; ++ph)
+    for (int ph = 0; ph < kPwPhases - 1; ++ph)  // every phase but the evaluation at leaf targets
         if ((r = pw_eval(&plan->pw, s, ph)) != PDMK_OK) return r;
     // far field at the targets
     {
@@ -3129,7 +3164,7 @@ static int run_eval_bloch(pdmk_plan plan, const double* beta_host, double* dp, d
         // far field: spread this part of the complex strengths
         if ((r = spread_fold<T, D>(plan, s, part == 0 ? b.gre : b.gim, false))) return r;
         // near field with this part of the phased copies: plane waves and the residual sum
-        for (int ph = 0; ph < 5; ++ph)
+        for (int ph = 0; ph < kPwPhases; ++ph)
             if ((r = pw_eval(&plan->pw, s, ph)) != PDMK_OK) return r;
         if (plan->pw.active) {
             CK(cudaMemcpyAsync(pp[part], plan->pw.d_pot, sp * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -597,6 +597,35 @@ __global__ void k_far_targets(FarLayoutArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// near-field entries
+
+template <typename T>
+__global__ void k_entries(EntryArgs a) {
+    const int d = a.d;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < a.nlist; e += int64_t(gridDim.x) * blockDim.x) {
+        // target leaf k of entry e: the last k with list_begin[k] <= e
+        int lo = 0, hi = a.ntleaf;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.list_begin[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        const int tb = a.tleaf[lo];
+        const int sb = a.list[e];
+        a.ent[e] = make_int2(a.bsb[sb], a.bsc[sb]);
+        const double* Ln = a.Ln + a.shift[e] * 3;
+        double du[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) du[k] = dsub(dadd(a.Cu[int64_t(sb) * d + k], Ln[k]), a.Cu[int64_t(tb) * d + k]);
+        for (int i = 0; i < d; ++i) {
+            double sh = 0;
+            for (int k = 0; k < d; ++k) sh = dadd(sh, dmul(a.Q[i * d + k], du[k]));
+            put_rec<T>(a.ent_sh, e * 4 + i, sh);
+            if (a.mixed) a.ent_shlo[e * 4 + i] = float(sh - double(float(sh)));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // host helpers
 
 struct Scratch {
@@ -949,6 +978,12 @@ void gpu_records(const RecordArgs& a, cudaStream_t s) {
         if (a.mixed) k_tgt_records<float><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
         else k_tgt_records<double><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
     }
+}
+
+void gpu_near_entries(const EntryArgs& a, cudaStream_t s) {
+    if (a.nlist <= 0) return;
+    if (a.mixed) k_entries<float><<<blocks_for(a.nlist), kThreads, 0, s>>>(a);
+    else k_entries<double><<<blocks_for(a.nlist), kThreads, 0, s>>>(a);
 }
 
 int gpu_far_layout(const FarLayoutArgs& a, cudaStream_t s, std::string* msg) {

@@ -100,4 +100,27 @@ struct FarLayoutArgs {
 };
 int gpu_far_layout(const FarLayoutArgs& a, cudaStream_t s, std::string* msg);
 
+// near-field entries: per direct-list entry e of target leaf k (list_begin[k] <= e <
+// list_begin[k + 1]), the source leaf's range and the shift Q (Cu_s + L n - Cu_t) of its
+// centre into the target leaf's frame (hi / lo split in mixed precision), as the host build
+struct EntryArgs {
+    int d;
+    int mixed;
+    int64_t nlist;
+    int ntleaf;
+    double Q[9];
+    double Ln[27 * 3];          // caller-frame lattice vector of every shift code
+    const int* tleaf;           // target leaf boxes
+    const long long* list_begin;  // ntleaf + 1
+    const int* list;            // source leaf per entry
+    const int* shift;           // shift code per entry
+    const int* bsb;             // per box: first sorted source
+    const int* bsc;             // per box: source count
+    const double* Cu;           // per box: caller-frame centre (d)
+    int2* ent;                  // out
+    void* ent_sh;               // out: 4 T per entry (zeroed by the caller)
+    float* ent_shlo;            // out (mixed; zeroed by the caller)
+};
+void gpu_near_entries(const EntryArgs& a, cudaStream_t s);
+
 }  // namespace pdmk

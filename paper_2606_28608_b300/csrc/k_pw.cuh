@@ -49,10 +49,12 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& s, const std:
                    const std::vector<int>& tgt_leaf, const Geometry& g, cudaStream_t stream,
                    const int* d_leaf_of, int64_t nimg);
 int pw_set_charges(PwPlan* pw, cudaStream_t stream);
-// phase 0: leaf moments + upward merges; 1: outgoing plane waves; 2: translation +
-// incoming; 3: downward pass; 4: evaluation at leaf targets
+// phase 0: leaf moments (in 2D compile-time orders: moments and outgoing waves straight
+// from the sources); 1: upward merges; 2: outgoing plane waves; 3: translation + incoming;
+// 4: downward pass; 5: evaluation at leaf targets
+constexpr int kPwPhases = 6;
 int pw_eval(PwPlan* pw, cudaStream_t stream, int phase);
-// Evaluation of stored local expansions at arbitrary points (after phases 0-3 of pw_eval):
+// Evaluation of stored local expansions at arbitrary points (after phases 0-4 of pw_eval):
 // list entries (local slot, first point, count, level of the box) over points given relative
 // to their box's centre (d_pts4: 4 values of the plan's precision per point); writes pot (one
 // per point) and grad (d per point).

@@ -539,9 +539,12 @@ __device__ __forceinline__ void tri_axpy(T (&acc)[P], const T* __restrict__ row,
 //   V[m0][M1 M2]  = sum_{M0 >= m0} S_b0[M0][m0] a_P[M0][M1 M2]      thread (M1 M2)
 //   W[m0][m1 M2]  = sum_{M1 >= m1} S_b1[M1][m1] V[m0][M1 M2]        thread (m0 M2), per b1
 //   a_c[m0 m1][m2] += sum_{M2 >= m2} S_b2[M2][m2] W[m0 m1][M2]      thread (m0 m1), per b2
+// The child's coefficients are added to those its own incoming waves wrote (in-boxes,
+// add[c] = 1) or written (leaves, whose only contribution this is), so the local array needs
+// no clearing.
 template <typename T, int P>
 __global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list, T* __restrict__ Lc,
-                                                    const T* __restrict__ Sg) {
+                                                    const T* __restrict__ Sg, const unsigned char* __restrict__ add) {
     constexpr int PP = P * P, NP = PP * P;
     using V = typename VecOf<T>::V;
     constexpr int VW = VecOf<T>::W;
@@ -603,13 +606,24 @@ __global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list
 #pragma unroll
                 for (int M2 = 0; M2 < P; ++M2) tri_axpy<T, P>(o, Sm + (b2 * P + M2) * P, wr[M2], 0, M2);
                 V* dst = reinterpret_cast<V*>(Lc + size_t(c) * NP + size_t(tid) * P);
+                if (add[c]) {
 #pragma unroll
-                for (int k = 0; k < P / VW; ++k) {
-                    V d = dst[k];
-                    T* dd = reinterpret_cast<T*>(&d);
+                    for (int k = 0; k < P / VW; ++k) {
+                        V d = dst[k];
+                        T* dd = reinterpret_cast<T*>(&d);
 #pragma unroll
-                    for (int jj = 0; jj < VW; ++jj) dd[jj] += o[VW * k + jj];
-                    dst[k] = d;
+                        for (int jj = 0; jj < VW; ++jj) dd[jj] += o[VW * k + jj];
+                        dst[k] = d;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < P / VW; ++k) {
+                        V d;
+                        T* dd = reinterpret_cast<T*>(&d);
+#pragma unroll
+                        for (int jj = 0; jj < VW; ++jj) dd[jj] = o[VW * k + jj];
+                        dst[k] = d;
+                    }
                 }
             }
         }
@@ -2227,6 +2241,7 @@ struct PwImpl {
     void* d_part = nullptr;     // partial moments [nditems][p p]
     void* d_part3 = nullptr;    // 3D four-way merges: parts [parents of the largest level][4][p^3]
     int* d_done3 = nullptr;     //   and per parent the number of parts written (reset by the last)
+    unsigned char* d_ladd = nullptr;  // per local slot: 1 for in-boxes (the downward pass adds), 0 for leaves
     int4* d_obox = nullptr;     // per out slot: (first partial slot, segments, box, 0)
     int* d_seg_done = nullptr;  // per out slot: segments finished in this evaluation
     // single-launch downward pass with folded leaf evaluation (2D compile-time orders)
@@ -2568,6 +2583,14 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     if ((r = pw_upload(pw, &I->d_inl, inl, stream))) return r;
     if ((r = pw_upload(pw, &I->d_down, down, stream))) return r;
     if ((r = pw_upload(pw, &I->d_eval, ev, stream))) return r;
+    {
+        // per local slot: does the downward pass add (in-boxes, written by the incoming
+        // waves) or write (leaves)
+        std::vector<unsigned char> ladd(size_t(std::max(nloc, 1)), 0);
+        for (int b = 0; b < nb; ++b)
+            if (lslot[b] >= 0 && !t.is_leaf(b) && has_tgt(b)) ladd[size_t(lslot[b])] = 1;
+        if ((r = pw_upload(pw, &I->d_ladd, ladd, stream))) return r;
+    }
     unsigned char* p = nullptr;
     if (I->direct2d) {
         if (!pw->h_err) {
@@ -2630,8 +2653,13 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     // compile-time 2D orders: direct moments, incoming written (not added) per in-box, and the
     // single-launch downward pass; no per-box moment or local arrays to clear
     const bool fixed2d = D == 2 && I->direct2d;
+    // 3D register-tiled path (leaf moments, merges and downward pass over the triangular shift
+    // matrices): every moment and local slot is written before it is read, so neither array is
+    // cleared (the moments and merges write their boxes; the downward pass writes the leaves
+    // and adds into the in-boxes, which the incoming waves wrote)
+    const bool rpath3d = D == 3 && ((sizeof(T) == 4 && (pd.p == 16 || pd.p == 24)) || (sizeof(T) == 8 && pd.p == 16));
     if (phase == 0) {
-    if (!fixed2d) {
+    if (!fixed2d && !rpath3d) {
     if (cudaMemsetAsync(I->d_Q, 0, size_t(std::max<int64_t>(I->nq, 1)) * pd.np * ts, s) != cudaSuccess) return PDMK_ERR_CUDA;
     if (cudaMemsetAsync(I->d_L, 0, size_t(std::max<int64_t>(I->nloc, 1)) * pd.np * ts, s) != cudaSuccess) return PDMK_ERR_CUDA;
     }
@@ -2697,7 +2725,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         cudaFuncSetAttribute(k_merge<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_re));
         cudaFuncSetAttribute(k_down<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_re));
     }
-    for (int l = I->nlevels - 1; phase == 0 && l >= 0; --l) {
+    for (int l = I->nlevels - 1; phase == 1 && l >= 0; --l) {
         const int b = I->merge_start[l], e = I->merge_start[l + 1];
         if (e > b) {
             const int* lst = I->d_merge + size_t(b) * (1 + (1 << D));
@@ -2748,18 +2776,18 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     // 3. outgoing plane waves (all levels); fused into the moments launch for the compile-time
     //    2D orders
     const bool fixed3d = D == 3 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16));
-    if (phase == 1 && I->nout > 0 && fixed3d) {
+    if (phase == 2 && I->nout > 0 && fixed3d) {
         if (pd.p == 16) k_pw_out3d_p<T, 16, 9><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co);
         else k_pw_out3d_p<T, 24, 16><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co);
         ++pw->launches;
-    } else if (phase == 1 && I->nout > 0 && !fixed2d) {
+    } else if (phase == 2 && I->nout > 0 && !fixed2d) {
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + 2 * size_t(pd.n1) * pd.p);
         cudaFuncSetAttribute(k_pw_out<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_pw_out<T, D><<<I->nout, 128, sm, s>>>(I->d_outl, Q, out, Co, pd, std::min(I->KC, 16));
         ++pw->launches;
     }
     // 4. translation + incoming (all levels)
-    if (phase == 2 && I->nin > 0 && fixed2d) {
+    if (phase == 3 && I->nin > 0 && fixed2d) {
         const int g = I->nin;  // one block per box
         const C2<T>* ph = static_cast<const C2<T>*>(I->d_ph);
         const T* fk = static_cast<const T*>(I->d_f);
@@ -2767,13 +2795,13 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         else if (pd.p == 24) k_pw_in2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
         else k_pw_in2d_p<T, 32, 23><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
         ++pw->launches;
-    } else if (phase == 2 && I->nin > 0 && fixed3d) {
+    } else if (phase == 3 && I->nin > 0 && fixed3d) {
         const C2<T>* ph = static_cast<const C2<T>*>(I->d_ph);
         const T* fk = static_cast<const T*>(I->d_f);
         if (pd.p == 16) k_pw_in3d_p<T, 16, 9><<<I->nin, 256, 0, s>>>(I->d_inl, out, L, Co, ph, fk, inv_rc);
         else k_pw_in3d_p<T, 24, 16><<<I->nin, 576, 0, s>>>(I->d_inl, out, L, Co, ph, fk, inv_rc);
         ++pw->launches;
-    } else if (phase == 2 && I->nin > 0) {
+    } else if (phase == 3 && I->nin > 0) {
         const int KC = std::min(I->KC, 16);
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + 3 * size_t(pd.n1) + size_t(KC) * pd.nk1 + size_t(KC) * pd.pd1 +
                               size_t(pd.n1) * pd.p);
@@ -2784,7 +2812,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     }
     // 5. downward, root first (by parent level); the compile-time 2D orders in one launch
     //    that also evaluates the target leaves
-    if (phase == 3 && fixed2d && I->ndown_items > 0) {
+    if (phase == 4 && fixed2d && I->ndown_items > 0) {
         if (cudaMemsetAsync(I->d_down_flags, 0, (size_t(I->ndown_items) + 3) * sizeof(int), s) != cudaSuccess)
             return PDMK_ERR_CUDA;
         const T* t4 = static_cast<const T*>(pw->d_tgt4);
@@ -2806,7 +2834,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         else persist(k_down_persist2d<T, 32>, 32);
         ++pw->launches;
     }
-    for (int l = 0; phase == 3 && !fixed2d && l + 1 < I->nlevels; ++l) {
+    for (int l = 0; phase == 4 && !fixed2d && l + 1 < I->nlevels; ++l) {
         const int b = I->down_start[l], e = I->down_start[l + 1];
         if (e > b) {
             const int* lst = I->d_down + size_t(b) * (1 + (1 << D));
@@ -2826,7 +2854,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                 auto dr = [&](auto kern, int P) {
                     const size_t smb = ts * (2 * P * P + 2 * P * P * P);
                     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
-                    kern<<<2 * (e - b), P * P, smb, s>>>(lst, L, S);
+                    kern<<<2 * (e - b), P * P, smb, s>>>(lst, L, S, I->d_ladd);
                 };
                 if (pd.p == 16) dr(k_down3d_r<T, 16>, 16);
                 else if constexpr (sizeof(T) == 4) dr(k_down3d_r<T, 24>, 24);
@@ -2846,7 +2874,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         }
     }
     // 6. leaf evaluation (folded into the downward launch for the compile-time 2D orders)
-    if (phase == 4 && I->neval > 0 && D == 3 && (pd.p == 16 || pd.p == 24 || (pd.p == 32 && sizeof(T) == 4))) {
+    if (phase == 5 && I->neval > 0 && D == 3 && (pd.p == 16 || pd.p == 24 || (pd.p == 32 && sizeof(T) == 4))) {
         const T* t4 = static_cast<const T*>(pw->d_tgt4);
         auto gemm = [&](auto kern, size_t smb) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
@@ -2856,12 +2884,12 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         else if (pd.p == 24) gemm(k_leaf_eval3d_gemm<T, 24>, leaf_eval3d_gemm_smem<T, 24>());
         else if constexpr (sizeof(T) == 4) gemm(k_leaf_eval3d_gemm<T, 32>, leaf_eval3d_gemm_smem<T, 32>());
         ++pw->launches;
-    } else if (phase == 4 && I->neval > 0 && D == 3 && pd.p == 32) {
+    } else if (phase == 5 && I->neval > 0 && D == 3 && pd.p == 32) {
         // FP64 order 32: the coefficients (256 KB) do not fit in shared memory
         const T* t4 = static_cast<const T*>(pw->d_tgt4);
         k_leaf_eval3d_p<T, 32><<<I->neval, 32, 0, s>>>(I->d_eval, L, t4, pw->d_pot, pw->d_grad, inv_rc);
         ++pw->launches;
-    } else if (phase == 4 && I->neval > 0 && !fixed2d) {
+    } else if (phase == 5 && I->neval > 0 && !fixed2d) {
         size_t sm = ts * 32 * 2 * D * pd.p;
         cudaFuncSetAttribute(k_leaf_eval<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         k_leaf_eval<T, D><<<I->neval, 32, sm, s>>>(I->d_eval, L, static_cast<const T*>(pw->d_tgt4), pw->d_pot,
@@ -2920,6 +2948,7 @@ void pw_free_sources(PwPlan* pw) {
         I->nleafq = I->nout = I->nin = I->neval = 0;
         I->d_ditems = nullptr; I->d_src_leaf = nullptr; I->d_bcoord = nullptr; I->d_part = nullptr;
         I->d_obox = nullptr; I->d_seg_done = nullptr; I->d_part3 = nullptr; I->d_done3 = nullptr;
+        I->d_ladd = nullptr;
         I->nditems = 0;
         I->d_down_items = nullptr; I->d_down_flags = nullptr;
         I->ndown_items = 0;
