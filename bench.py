@@ -47,6 +47,13 @@ WORKLOADS = {
         make=lambda: W.triclinic3d_clusters(4_000_000), golden="triclinic3d_4m",
         desc="triclinic3d_clusters: a1=(1,0,0) a2=(0.3,2,0) a3=(0.5,0.7,17), N=4000000, 64 anisotropic "
              "gaussian clusters sigma in [1e-4,1e-2] of the cell, q~U(-1,1) minus mean"),
+    "cube_2k": dict(
+        make=lambda: W.cube_uniform(2000), golden=None,
+        desc="cube_uniform: L = I, N=2000 uniform sources, q~N(0,1) minus mean"),
+    "water_333k": dict(
+        make=lambda: W.water_box(333_000), golden="water_333k",
+        desc="water_box: triclinic cell edges (3.1,3.3,9.8) angles (85,95,100), 333000 rigid 3-site "
+             "molecules (999000 charges -0.834/+0.417/+0.417)"),
     # the headline cell's shape at 1/8 of the points (profiling captures: a few GB on the device)
     "triclinic3d_500k": dict(
         make=lambda: W.triclinic3d_clusters(500_000), golden=None,
@@ -209,7 +216,8 @@ STAGE_KERNELS = {
         "pw_downward": "k_down_persist2d (leaf evaluation folded in)", "pw_leaf_eval": "k_leaf_eval"},
     3: {"spread": "k_spread3d_reg + k_fold", "interp": "k_interp3d_w", "nearfield": "k_near_warp",
         "pw_moments": "k_leaf_moments3d_gemm", "pw_merge": "k_merge3d_r", "pw_out": "k_pw_out3d_p",
-        "pw_translate_in": "k_pw_in3d_p", "pw_downward": "k_down3d_r", "pw_leaf_eval": "k_leaf_eval3d_gemm"},
+        "pw_translate_in": "k_pw_in3d_p", "pw_downward": "k_down3d_r",
+        "pw_leaf_eval": "k_leaf_eval3d_tc (tcgen05 kind::tf32, split operands)"},
 }
 
 
@@ -236,8 +244,9 @@ def replica_summary(t_local, n, steps, ws, pg, device):
 
 
 def batched_line(P, torch, stream, ncells=16, nmax=20_000, steps=20, ws=1, rank=0, pg=None):
-    """Batched cells (the 3D batched workload's shape, bounded to ncells cells of at most nmax
-    sources so that the host tree builds stay short): points/s of one graph-replayed batch
+    """Batched cells (the 3D batched workload's shape; by default bounded to 16 cells of at most
+    20,000 sources, --batch-cells 256 --batch-nmax 200000 for the full workload): points/s of one
+    graph-replayed batch
     evaluation with device outputs, timed with CUDA events, mixed and FP64 on the same cells.
     With several ranks the cells are split by estimated work (pdmk_partition_cells, the same
     partition computed on every rank, no exchange); the value is all ranks' points over the
@@ -428,6 +437,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="triclinic3d_4m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-cells", type=int, default=16, help="cells of the batched secondary line")
+    ap.add_argument("--batch-nmax", type=int, default=20_000, help="largest cell of the batched line")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 2D and batched secondary lines")
     ap.add_argument("--sweep", action="store_true",
                     help="run the paper's wavy ring / sphere grid (Tables 2-4 shapes) instead of the benchmark")
@@ -605,7 +616,7 @@ def main():
             out["secondary"] = secondary_lines(P, torch, stream, flush, args, peaks)
     if not args.no_secondary:
         # every rank takes part in the batched line (its share of the cells)
-        bl = batched_line(P, torch, stream, ws=ws, rank=rank, pg=pg)
+        bl = batched_line(P, torch, stream, ncells=args.batch_cells, nmax=args.batch_nmax, ws=ws, rank=rank, pg=pg)
         if out is not None:
             out.setdefault("secondary", {})["batched"] = bl
     if out is not None:

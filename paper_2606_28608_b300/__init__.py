@@ -31,7 +31,7 @@ class Opts(ctypes.Structure):
                 ("window_w", ctypes.c_int), ("n_proxy", ctypes.c_int), ("n_pw", ctypes.c_int),
                 ("max_depth", ctypes.c_int), ("neutrality", ctypes.c_int), ("profile", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("wait_test", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("root_mode", ctypes.c_int), ("build_mode", ctypes.c_int)]
+                ("root_mode", ctypes.c_int), ("build_mode", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -172,7 +172,7 @@ class Plan:
     def __init__(self, L, eps: float, *, precision: str = "fp64", kappa: float = 0.0, n_s: int = 0,
                  window_w: int = 0, n_proxy: int = 0, n_pw: int = 0, max_depth: int = -1,
                  neutrality: int = 1, profile: bool = False, stream=None, wait_test: int = 0,
-                 autotune: bool = False, root_mode: int = 0, build: str = "auto"):
+                 autotune: bool = False, root_mode: int = 0, build: str = "auto", tensor_cores: bool = True):
         L = np.ascontiguousarray(np.asarray(L, dtype=np.float64))
         self.d = L.shape[0]
         self._L = L
@@ -199,6 +199,7 @@ class Plan:
         o.autotune = 1 if autotune else 0
         o.root_mode = int(root_mode)
         o.build_mode = {"auto": 0, "host": 1, "device": 2, "compare": 3}[build]
+        o.tensor_cores = 0 if tensor_cores else 1
         self.opts = o
         Lc = np.ascontiguousarray(L.T)  # column-major
         h = ctypes.c_void_p()

@@ -258,6 +258,7 @@ extern "C" void pdmk_default_opts(pdmk_opts* o) {
     o->autotune = 0;
     o->root_mode = 0;
     o->build_mode = 0;
+    o->tensor_cores = 0;
 }
 
 extern "C" const char* pdmk_strerror(int code) {
@@ -675,6 +676,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     }
     // plane-wave planning (proxy order, plane-wave counts, 1D operators)
     pw_plan_create(&plan->pw, d, eps, plan->c, plan->kt, plan->opts.n_proxy, plan->opts.n_pw, mixed);
+    plan->pw.tensor_cores = plan->opts.tensor_cores == 0;
     plan->pw.wait_test = plan->opts.wait_test;
     // device: coefficient arrays, far weights, grid, spectrum, FFT plans
     const size_t ts = tsize(plan);

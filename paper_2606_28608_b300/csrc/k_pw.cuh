@@ -31,6 +31,7 @@ struct PwPlan {
     int* d_err = nullptr;   // its device address
     int wait_test = 0;      // test hook: make the first dependent downward item wait forever
     int nsm = 1;            // SMs of the plan's device (grid sizing)
+    bool tensor_cores = true;  // 3D leaf evaluation of FP32 plans on tcgen05 (3xTF32)
     std::vector<int> lslot;  // per box: slot of its local expansion in the local array, or -1
     std::vector<unsigned char> local_full;  // per box: the slot holds its complete local expansion
                                             // after the downward pass (every receiving non-leaf box,

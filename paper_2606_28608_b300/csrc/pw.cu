@@ -29,6 +29,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "k_leaf_tc.cuh"
 #include "k_pw.cuh"
 #include "kernels_common.cuh"
 #include "pdmk.h"
@@ -2592,6 +2593,16 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         if ((r = pw_upload(pw, &I->d_ladd, ladd, stream))) return r;
     }
     unsigned char* p = nullptr;
+    const bool leaf_tc = d == 3 && pw->mixed && pw->tensor_cores && (I->dims.p == 16 || I->dims.p == 24);
+    if (leaf_tc && !pw->h_err) {
+        // the tensor-core leaf evaluation's bounded wait reports through the same flag
+        if (cudaHostAlloc(reinterpret_cast<void**>(&pw->h_err), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void**>(&pw->d_err), pw->h_err, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return PDMK_ERR_CUDA;
+        }
+        *pw->h_err = 0;
+    }
     if (I->direct2d) {
         if (!pw->h_err) {
             if (cudaHostAlloc(reinterpret_cast<void**>(&pw->h_err), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
@@ -2874,7 +2885,21 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         }
     }
     // 6. leaf evaluation (folded into the downward launch for the compile-time 2D orders)
-    if (phase == 5 && I->neval > 0 && D == 3 && (pd.p == 16 || pd.p == 24 || (pd.p == 32 && sizeof(T) == 4))) {
+    const bool leaf_tc = D == 3 && sizeof(T) == 4 && pw->tensor_cores && (pd.p == 16 || pd.p == 24);
+    if (phase == 5 && I->neval > 0 && leaf_tc) {
+        // tensor cores (tcgen05, 3xTF32): persistent, two CTAs per SM
+        if constexpr (sizeof(T) == 4) {
+            const float* t4 = static_cast<const float*>(pw->d_tgt4);
+            const int grid = std::max(1, std::min(I->neval, 2 * pw->nsm));
+            auto tc = [&](auto kern, size_t smb) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+                kern<<<grid, 128, smb, s>>>(I->d_eval, I->neval, L, t4, pw->d_pot, pw->d_grad, inv_rc, pw->d_err);
+            };
+            if (pd.p == 16) tc(k_leaf_eval3d_tc<16>, LeafTcLayout<16>::total);
+            else tc(k_leaf_eval3d_tc<24>, LeafTcLayout<24>::total);
+        }
+        ++pw->launches;
+    } else if (phase == 5 && I->neval > 0 && D == 3 && (pd.p == 16 || pd.p == 24 || (pd.p == 32 && sizeof(T) == 4))) {
         const T* t4 = static_cast<const T*>(pw->d_tgt4);
         auto gemm = [&](auto kern, size_t smb) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
