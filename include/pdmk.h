@@ -105,7 +105,7 @@ typedef struct {
                        give the same tree, order and records, bit for bit. */
     int tensor_cores; /* 0: the 3D leaf evaluation of mixed plans (orders 16 and 24) runs on the
                        tensor cores (tcgen05, TF32 with each operand split in two, FP32
-                       accumulation: the accuracy of FP32); 1: on the FP32 FMA pipes. */
+                       accumulation: about the accuracy of FP32); 1: on the FP32 FMA pipes. */
 } pdmk_opts;
 
 /* Fills *opts with the defaults (all fields "auto", FP64, neutrality allowed). */

@@ -212,17 +212,27 @@ __global__ void __launch_bounds__(128, 2)
                 }
             }
             float accP = 0.f, accX = 0.f, accY = 0.f, accZ = 0.f;
-            float tz[P], tzd[P];
 #pragma unroll 1
             for (int c = 0; c < NCH; ++c) {
                 // ---- the chunk's coefficients: column n <-> (m1 = 8 c + n / P, m2 = n % P); task
-                //      (n, g) moves a[4g .. 4g+3][NC c + n] as one K-group of hi and of lo
-                for (int task = tid; task < NC * (P / 4); task += 128) {
-                    const int n = task % NC, g = task / NC;
+                //      (n, g) moves a[4g .. 4g+3][NC c + n] as one K-group of hi and of lo.  Every
+                //      thread's loads are issued before the first is used.
+                constexpr int TASKS = NC * (P / 4) / 128;
+                static_assert(TASKS * 128 == NC * (P / 4), "tasks split evenly over the block");
+                float xs[TASKS][4];
+#pragma unroll
+                for (int i = 0; i < TASKS; ++i) {
+                    const int task = tid + 128 * i, n = task % NC, g = task / NC;
                     const float* src = a + size_t(4 * g) * PP + NC * c + n;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) xs[i][j] = __ldg(src + j * PP);
+                }
+#pragma unroll
+                for (int i = 0; i < TASKS; ++i) {
+                    const int task = tid + 128 * i, n = task % NC, g = task / NC;
                     float h[4], l[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) tcg::split_tf32(__ldg(src + j * PP), h[j], l[j]);
+                    for (int j = 0; j < 4; ++j) tcg::split_tf32(xs[i][j], h[j], l[j]);
                     const uint32_t off = kmajor_off<P>(n, 4 * g);
                     *reinterpret_cast<float4*>(Bh + off) = make_float4(h[0], h[1], h[2], h[3]);
                     *reinterpret_cast<float4*>(Bl + off) = make_float4(l[0], l[1], l[2], l[3]);
@@ -231,13 +241,6 @@ __global__ void __launch_bounds__(128, 2)
                 tcg::fence_before();
                 __syncthreads();
                 tcg::fence_after();
-                if (c == 0) {
-#pragma unroll
-                    for (int m = 0; m < P; ++m) {
-                        tz[m] = TB[(2 * P + m) * 64 + t];
-                        tzd[m] = TB[(3 * P + m) * 64 + t];
-                    }
-                }
                 if (tid == 0) {
                     const uint32_t ah = tcg::smem_addr(Ah), al = tcg::smem_addr(Al);
                     const uint32_t bh = tcg::smem_addr(Bh), bl = tcg::smem_addr(Bl);
@@ -261,6 +264,12 @@ __global__ void __launch_bounds__(128, 2)
                 }
                 tcg::fence_after();
                 // ---- this thread's row of the chunk: sums over m2 per m1, then over m1
+                float tz[P], tzd[P];
+#pragma unroll
+                for (int m = 0; m < P; ++m) {
+                    tz[m] = TB[(2 * P + m) * 64 + t];
+                    tzd[m] = vrow ? TB[(3 * P + m) * 64 + t] : 0.f;
+                }
                 float u[8], v[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) u[j] = v[j] = 0.f;
@@ -318,5 +327,6 @@ __global__ void __launch_bounds__(128, 2)
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
+
 
 }  // namespace pdmk

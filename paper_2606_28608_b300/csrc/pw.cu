@@ -1124,7 +1124,7 @@ __global__ void __launch_bounds__(128) k_pw_in(const int* __restrict__ list, con
 //   B[+-k1][m2] = E +- i O,  E = sum_j ce[k1][j] A[2j][m2],  O = sum_j so[k1][j] A[2j+1][m2]
 //   out[k0][k1][+-k2] = E' +- i O' over m2 in the same way.
 template <typename T, int P, int K>
-__global__ void __launch_bounds__(P * P) k_pw_out3d_p(const int2* __restrict__ list, const T* __restrict__ Q,
+__global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 1) k_pw_out3d_p(const int2* __restrict__ list, const T* __restrict__ Q,
                                                      C2<T>* __restrict__ out, const C2<T>* __restrict__ Cog) {
     constexpr int H = P / 2, KH = K + 1, N1 = 2 * K + 1, PP = P * P, NPW = KH * N1 * N1;
     __shared__ T ce[KH][H], so[KH][H];
