@@ -175,6 +175,9 @@ struct pdmk_plan_s {
     std::vector<cudaEvent_t> ev;
     std::vector<std::string> stage_names;
     std::vector<double> stage_ms;
+    // page-locked staging of the device set-up's downloads (kept for the plan's next set-up)
+    unsigned char* h_stage = nullptr;
+    size_t stage_cap = 0;
     // device set-up (gpu_build.cu): the per-point host copies are downloaded on first use
     bool setup_device = false;
     bool host_copies = true;
@@ -769,6 +772,7 @@ extern "C" void pdmk_plan_destroy(pdmk_plan plan) {
     free_list(plan->src_allocs, &plan->device_bytes);
     free_list(plan->plan_allocs, &plan->device_bytes);
     if (plan->tq_buf) cudaFree(plan->tq_buf);
+    if (plan->h_stage) cudaFreeHost(plan->h_stage);
     pw_free(&plan->pw);
     if (plan->have_fft) {
         cufftDestroy(plan->fft_fwd);
@@ -933,17 +937,18 @@ static void near_layout(pdmk_plan plan, const Tree& tree, const DirectLists& dl,
             }
         tl.swap(split);
     }
-    std::vector<int64_t> cost(tl.size(), 0);
-    for (size_t k = 0; k < tl.size(); ++k) {
+    // (decreasing cost, then increasing index: the order a stable sort by cost gives)
+    std::vector<std::pair<int64_t, int64_t>> key(tl.size());
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < int64_t(tl.size()); ++k) {
         int64_t ns = 0;
         for (int e = tl[k].list_begin; e < tl[k].list_begin + tl[k].list_count; ++e) ns += bsc[dl.list[e]];
-        cost[k] = ns * int64_t(tl[k].tgt_count);
+        key[size_t(k)] = {-ns * int64_t(tl[k].tgt_count), k};
     }
-    std::vector<size_t> ord(tl.size());
-    std::iota(ord.begin(), ord.end(), size_t(0));
-    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::sort(key.begin(), key.end());
     std::vector<TLeaf> tl2(tl.size());
-    for (size_t k = 0; k < ord.size(); ++k) tl2[k] = tl[ord[k]];
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < int64_t(key.size()); ++k) tl2[size_t(k)] = tl[size_t(key[size_t(k)].second)];
     tl.swap(tl2);
 }
 
@@ -1622,7 +1627,19 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     // ---- tree (device), lists (host) ----
     GpuBuild& gb = scr.gb;
     gb.d_u = plan->d_u_keep;
-    Tree tree;
+    if (!plan->h_stage) {
+        void* hs = nullptr;
+        if (cudaHostAlloc(&hs, size_t(64) << 20, cudaHostAllocDefault) == cudaSuccess) {
+            plan->h_stage = static_cast<unsigned char*>(hs);
+            plan->stage_cap = size_t(64) << 20;
+        } else {
+            cudaGetLastError();  // without staging the downloads go straight to the host arrays
+        }
+    }
+    gb.h_stage = plan->h_stage;
+    gb.stage_cap = plan->stage_cap;
+    // the previous set-up's host tree lends its arrays' capacity (no new pages to fault in)
+    Tree tree = std::move(plan->h_tree);
     BuildStats st;
     const int maxd = pw_supported(&plan->pw) ? plan->max_depth : 0;
     std::string msg;
@@ -1632,7 +1649,11 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
         plan->msg = msg;
         return r;
     }
-    lap("tree_device");
+    for (int k = 0; k < 6; ++k) {
+        plan->setup_names.push_back(kDeviceBuildPhases[k]);
+        plan->setup_ms.push_back(st.phase_ms[k]);
+    }
+    clk = std::chrono::steady_clock::now();
     DirectLists dl;
     int64_t pairs = 0;
     build_direct_lists(tree, &dl, &pairs);
@@ -1642,8 +1663,9 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     plan->ntgt = gb.ntgt;
     plan->nbox = st.nboxes;
     plan->ntleaf = int(dl.tleaf.size());
-    // caller-frame box centres, as the host build
-    std::vector<double> Cu(size_t(st.nboxes) * d);
+    // caller-frame box centres, as the host build (in the previous set-up's array)
+    std::vector<double> Cu = std::move(plan->h_Cu);
+    Cu.resize(size_t(st.nboxes) * d);
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < st.nboxes; ++b)
         for (int i = 0; i < d; ++i) {

@@ -22,6 +22,7 @@
 #include <cub/device/device_select.cuh>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 
 #include "gpu_build.h"
@@ -708,6 +709,15 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     const int d = g.d;
     const Geo geo = make_geo(g);
     Scratch scr;
+    // host wall clock of the phases (kDeviceBuildPhases), the stream drained at each boundary
+    auto clk = std::chrono::steady_clock::now();
+    auto lap = [&](int k) -> int {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return PDMK_ERR_CUDA;
+        const auto now = std::chrono::steady_clock::now();
+        if (st) st->phase_ms[k] = std::chrono::duration<double, std::milli>(now - clk).count();
+        clk = now;
+        return PDMK_OK;
+    };
     // ---- images ----
     ImageShifts tab;
     image_shifts(g, &tab);
@@ -768,6 +778,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
         if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
         GB_CK(cub::DeviceRadixSort::SortPairs(d_tmp, tb, d_pk, d_pk2, d_pj, d_pj2, int(nx), 0, kb, s));
     }
+    if (lap(0)) return PDMK_ERR_CUDA;
     // ---- keys ----
     int64_t nroot_tot = 1;
     for (int a = 0; a < d; ++a) nroot_tot *= g.nroot[a];
@@ -790,6 +801,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     GB_CK(cub::DeviceRadixSort::SortPairs(d_tmp, tb, d_key, d_key2, d_val, d_val2, int(nimg), 0, keybits, s));
     const unsigned long long* skey = d_key2;
     const int* sval = d_val2;
+    if (lap(1)) return PDMK_ERR_CUDA;
     // ---- refinement: non-leaf boxes per level ----
     std::vector<unsigned long long*> nl;  // device arrays per level
     std::vector<int64_t> nnl;
@@ -816,6 +828,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
         nl.push_back(out);
         nnl.push_back(h_n);
     }
+    if (lap(2)) return PDMK_ERR_CUDA;
     // ---- level restriction, deepest level first ----
     int nn = 1;
     for (int a = 0; a < d; ++a) nn *= 3;
@@ -842,6 +855,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
         nl[L - 1] = uq;
         nnl[L - 1] = h_n;
     }
+    if (lap(3)) return PDMK_ERR_CUDA;
     // ---- boxes per level ----
     const int nlev = int(nl.size()) + 1;
     std::vector<unsigned long long*> lk(nlev);
@@ -916,6 +930,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     GB_CK(cudaMemcpyAsync(bo->d_leaf, d_leafpos, size_t(nimg) * sizeof(int), cudaMemcpyDeviceToDevice, s));
     int h_ntgt = 0;
     GB_CK(cudaMemcpyAsync(&h_ntgt, d_tpos + nimg, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (lap(4)) return PDMK_ERR_CUDA;
     // ---- the host tree ----
     t->d = d;
     for (int a = 0; a < 3; ++a) t->nroot[a] = a < d ? g.nroot[a] : 1;
@@ -933,18 +948,45 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     t->center.resize(size_t(nb) * d);
     t->colleague.resize(size_t(nb) * nn);
     static_assert(sizeof(long long) == sizeof(int64_t), "64-bit box arrays");
-    GB_CK(cudaMemcpyAsync(t->level.data(), bx.level, size_t(nb) * sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->coord.data(), bx.coord, size_t(nb) * d * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->parent.data(), bx.parent, size_t(nb) * sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->child0.data(), bx.child0, size_t(nb) * sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->src_begin.data(), bx.src_b, size_t(nb) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->src_end.data(), bx.src_e, size_t(nb) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->tgt_begin.data(), d_tb, size_t(nb) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->tgt_end.data(), d_te, size_t(nb) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->center.data(), bx.center, size_t(nb) * d * sizeof(double), cudaMemcpyDeviceToHost, s));
-    GB_CK(cudaMemcpyAsync(t->colleague.data(), bx.colleague, size_t(nb) * nn * sizeof(int), cudaMemcpyDeviceToHost,
-                          s));
+    // through the caller's page-locked staging buffer when it has one (chunked, the copy into
+    // the host arrays in parallel), else straight into the host arrays
+    auto download = [&](void* dst, const void* src, size_t bytes) -> int {
+        if (!bo->h_stage || bo->stage_cap < (size_t(1) << 20)) {
+            if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PDMK_ERR_CUDA;
+            return PDMK_OK;
+        }
+        for (size_t off = 0; off < bytes; off += bo->stage_cap) {
+            const size_t len = std::min(bo->stage_cap, bytes - off);
+            if (cudaMemcpyAsync(bo->h_stage, static_cast<const unsigned char*>(src) + off, len, cudaMemcpyDeviceToHost,
+                                s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return PDMK_ERR_CUDA;
+            const int64_t npiece = int64_t((len + (size_t(1) << 20) - 1) >> 20);
+#pragma omp parallel for schedule(static)
+            for (int64_t k = 0; k < npiece; ++k) {
+                const size_t o = size_t(k) << 20, l = std::min(size_t(1) << 20, len - o);
+                std::memcpy(static_cast<unsigned char*>(dst) + off + o, bo->h_stage + o, l);
+            }
+        }
+        return PDMK_OK;
+    };
+    int rd = PDMK_OK;
+    if (!rd) rd = download(t->level.data(), bx.level, size_t(nb) * sizeof(int));
+    if (!rd) rd = download(t->coord.data(), bx.coord, size_t(nb) * d * sizeof(int64_t));
+    if (!rd) rd = download(t->parent.data(), bx.parent, size_t(nb) * sizeof(int));
+    if (!rd) rd = download(t->child0.data(), bx.child0, size_t(nb) * sizeof(int));
+    if (!rd) rd = download(t->src_begin.data(), bx.src_b, size_t(nb) * sizeof(int64_t));
+    if (!rd) rd = download(t->src_end.data(), bx.src_e, size_t(nb) * sizeof(int64_t));
+    if (!rd) rd = download(t->tgt_begin.data(), d_tb, size_t(nb) * sizeof(int64_t));
+    if (!rd) rd = download(t->tgt_end.data(), d_te, size_t(nb) * sizeof(int64_t));
+    if (!rd) rd = download(t->center.data(), bx.center, size_t(nb) * d * sizeof(double));
+    if (!rd) rd = download(t->colleague.data(), bx.colleague, size_t(nb) * nn * sizeof(int));
+    if (rd) {
+        if (msg) *msg = cudaGetErrorString(cudaGetLastError());
+        return PDMK_ERR_CUDA;
+    }
     GB_CK(cudaStreamSynchronize(s));
+    if (lap(5)) return PDMK_ERR_CUDA;
     bo->n = n;
     bo->nimg = nimg;
     bo->ntgt = h_ntgt;

@@ -27,6 +27,8 @@ struct GpuBuild {
     int* d_tgt_of = nullptr;    // per sorted target: sorted source index of the point
     int* d_tgt_orig = nullptr;  // per sorted target: point index
     std::vector<void*> allocs;
+    unsigned char* h_stage = nullptr;  // optional page-locked staging buffer of the caller
+    size_t stage_cap = 0;              // its bytes (used when at least 1 MiB)
 };
 void gpu_build_free(GpuBuild* b);
 
@@ -35,7 +37,11 @@ void gpu_build_free(GpuBuild* b);
 constexpr int kGpuBuildUnsupported = 1;
 
 // u (device, n x d) must already hold the wrapped fractional coordinates.  Fills the host
-// tree t (every per-box array, as build_tree does), the device arrays of b and st.
+// tree t (every per-box array, as build_tree does), the device arrays of b and st (whose
+// phase_ms take the phases below, host wall clock with the stream drained at each boundary).
+constexpr const char* kDeviceBuildPhases[6] = {"tree_device_images",      "tree_device_keys_sort",
+                                               "tree_device_refinement",  "tree_device_level_restriction",
+                                               "tree_device_boxes_order", "tree_device_download"};
 int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStream_t s, GpuBuild* b, Tree* t,
                    BuildStats* st, std::string* msg);
 

@@ -63,7 +63,7 @@ def test_device_build_equals_host_build(case, prec):
     plan = P.Plan(g["L"], 1e-6, precision=prec, build="compare", **opts)
     plan.set_sources(g["y"], g["q"])  # raises if any array differs
     assert plan.message() == "device and host set-up identical"
-    assert "tree_device" in plan.setup_times()
+    assert "tree_device_images" in plan.setup_times()
     info = plan.info()
     print(f"{case} {prec}: identical; depth={info['depth']} boxes={info['nboxes']} images={info['n_images']}")
     plan.close()
@@ -103,7 +103,7 @@ def test_device_build_device_inputs_and_default_mode():
     y = torch.tensor(g["y"], device="cuda")
     q = torch.tensor(g["q"], device="cuda")
     plan.set_sources(y, q)
-    assert "tree_device" in plan.setup_times()
+    assert "tree_device_images" in plan.setup_times()
     pot, grad = plan.eval()
     rng = np.random.default_rng(3)
     idx = rng.choice(len(g["q"]), 64, replace=False)
