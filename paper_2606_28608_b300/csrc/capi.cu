@@ -2331,7 +2331,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
     }
     plan->launches += plan->pw.launches;
     if (plan->nnear > 0) {
-        NearArgs<T> na;
+        NearArgs<T> na{};
         na.tleaf = plan->d_tleaf;
         na.ntleaf = plan->nnear;
         na.list = plan->d_list;
@@ -2901,7 +2901,7 @@ static int run_eval_targets(pdmk_plan plan, const TargetLayout& L, char* buf, do
     CK(cudaMemsetAsync(pot_near, 0, size_t(m) * 8, s));
     CK(cudaMemsetAsync(grad_near, 0, size_t(m) * D * 8, s));
     if (!L.desc.empty()) {
-        NearArgs<T> na;
+        NearArgs<T> na{};
         na.tleaf = desc;
         na.ntleaf = int(L.desc.size());
         na.list = nullptr;
@@ -3197,7 +3197,7 @@ static int run_eval_bloch(pdmk_plan plan, const double* beta_host, double* dp, d
         CK(cudaMemsetAsync(pn[part], 0, sp * sizeof(double), s));
         CK(cudaMemsetAsync(gn[part], 0, sg * sizeof(double), s));
         if (plan->nnear > 0) {
-            NearArgs<T> na;
+            NearArgs<T> na{};
             na.tleaf = plan->d_tleaf;
             na.ntleaf = plan->nnear;
             na.list = plan->d_list;
