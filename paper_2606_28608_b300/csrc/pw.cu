@@ -1124,26 +1124,30 @@ __global__ void __launch_bounds__(128) k_pw_in(const int* __restrict__ list, con
 //   B[+-k1][m2] = E +- i O,  E = sum_j ce[k1][j] A[2j][m2],  O = sum_j so[k1][j] A[2j+1][m2]
 //   out[k0][k1][+-k2] = E' +- i O' over m2 in the same way.
 template <typename T, int P, int K>
-__global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 1) k_pw_out3d_p(const int2* __restrict__ list, const T* __restrict__ Q,
-                                                     C2<T>* __restrict__ out, const C2<T>* __restrict__ Cog) {
-    constexpr int H = P / 2, KH = K + 1, N1 = 2 * K + 1, PP = P * P, NPW = KH * N1 * N1;
+__global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 1)
+    k_pw_out3d_p(const int2* __restrict__ list, const T* __restrict__ Q, C2<T>* __restrict__ out,
+                 const C2<T>* __restrict__ Cog, const int2* __restrict__ rowg) {
+    constexpr int H = P / 2, KH = K + 1, N1 = 2 * K + 1, PP = P * P;
     __shared__ T ce[KH][H], so[KH][H];
     __shared__ C2<T> A[PP];      // [m1][m2]
     __shared__ C2<T> B[N1][P];   // [k1 + K][m2]
+    __shared__ int2 row[KH][N1];  // (unused offset, m): the ball's rows k2 = -m .. m
     const int tid = threadIdx.x;
     for (int i = tid; i < KH * H; i += PP) {
         const int k = i / H, j = i % H;
         ce[k][j] = Cog[(k + K) * P + 2 * j].x;
         so[k][j] = Cog[(k + K) * P + 2 * j + 1].y;
     }
+    for (int i = tid; i < KH * N1; i += PP) row[i / N1][i % N1] = rowg[i];
     const int2 e = list[blockIdx.x];
     const T* q = Q + size_t(e.x) * (PP * P);
-    C2<T>* o = out + size_t(e.y) * NPW;
+    C2<T>* o = out + size_t(e.y) * (KH * N1 * N1);
     T qr[P];
 #pragma unroll
     for (int m0 = 0; m0 < P; ++m0) qr[m0] = q[m0 * PP + tid];
     __syncthreads();
     for (int k0 = 0; k0 <= K; ++k0) {
+        if (row[k0][K].y < 0) break;  // this slice and the later ones lie outside the ball
         {
             T ax = T(0), ay = T(0);
 #pragma unroll
@@ -1154,7 +1158,7 @@ __global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 
             A[tid] = C2<T>{ax, ay};
         }
         __syncthreads();
-        if (tid < KH * P) {
+        if (tid < KH * P && row[k0][K + tid / P].y >= 0) {  // rows +-k1 that meet the ball
             const int k1 = tid / P, m2 = tid % P;
             T ex = T(0), ey = T(0), ox = T(0), oy = T(0);
 #pragma unroll
@@ -1170,9 +1174,10 @@ __global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 
             if (k1 > 0) B[K - k1][m2] = C2<T>{ex + oy, ey - ox};
         }
         __syncthreads();
-        C2<T>* os = o + size_t(k0) * (N1 * N1);
         for (int it = tid; it < N1 * KH; it += PP) {
             const int kk1 = it / KH, k2 = it % KH;
+            const int2 rw = row[k0][kk1];
+            if (k2 > rw.y) continue;  // outside the ball: never read
             T ex = T(0), ey = T(0), ox = T(0), oy = T(0);
 #pragma unroll
             for (int j = 0; j < H; ++j) {
@@ -1183,8 +1188,9 @@ __global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 
                 ox = fma(s, bo.x, ox);
                 oy = fma(s, bo.y, oy);
             }
-            os[kk1 * N1 + K + k2] = C2<T>{ex - oy, ey + ox};
-            if (k2 > 0) os[kk1 * N1 + K - k2] = C2<T>{ex + oy, ey - ox};
+            C2<T>* os = o + size_t(k0) * (N1 * N1) + kk1 * N1 + K;
+            os[k2] = C2<T>{ex - oy, ey + ox};
+            if (k2 > 0) os[-k2] = C2<T>{ex + oy, ey - ox};
         }
         // the next slice rewrites A only: every thread is past the reads of A (barrier above),
         // and B is rewritten only after the next barrier
@@ -2219,6 +2225,14 @@ struct PwImpl {
     void* d_S = nullptr;   // 2 p p
     void* d_ph = nullptr;  // 3 n1 complex
     void* d_f = nullptr;   // (K+1) n1^{d-1}
+    // 3D compile-time orders: the modes inside the ball |k| <= 3c/pi (where f is nonzero), row
+    // by row: for (k0, k1) the modes k2 = -m .. m, row[k0][k1 + K] = (offset in a compact
+    // layout, m), m = -1 for an empty row; npwc modes in all.  The outgoing kernel computes and
+    // stores only these modes (at their places in the full layout), and both kernels stop at
+    // the first empty k0 slice.
+    int2* d_row = nullptr;
+    std::vector<int2> host_row;
+    int npwc = 0;
     // lists
     int4* d_leafq = nullptr;
     int nleafq = 0;
@@ -2383,6 +2397,22 @@ void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables&
             }
             I->host_f[size_t(k0) * D.nk1 + r] = f;
         }
+    if (d == 3) {
+        I->host_row.assign(size_t(K + 1) * D.n1, make_int2(0, -1));
+        int off = 0;
+        for (int k0 = 0; k0 <= K; ++k0)
+            for (int kk1 = 0; kk1 < D.n1; ++kk1) {
+                const int k1 = kk1 - K;
+                int m = -1;
+                for (int k2 = 0; k2 <= K; ++k2) {
+                    const double kk = std::sqrt(double(k0) * k0 + double(k1) * k1 + double(k2) * k2);
+                    if (kk <= kball) m = k2;  // the same test as f: the ball is convex along k2
+                }
+                I->host_row[size_t(k0) * D.n1 + kk1] = make_int2(off, m);
+                off += m >= 0 ? 2 * m + 1 : 0;
+            }
+        I->npwc = off;
+    }
     // k0 chunk: the [KC][p^{d-1}] complex slices must fit next to the tables in shared memory
     const size_t ts = mixed ? 4 : 8;
     const size_t per = size_t(D.pd1) * 2 * ts + size_t(D.nk1) * 2 * ts;
@@ -2633,8 +2663,10 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     }
     if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nq, 1)) * I->dims.np * ts))) return r;
     I->d_Q = p;
+    const bool fixed3d_sz = d == 3 && ((I->dims.p == 16 && I->dims.K == 9) || (I->dims.p == 24 && I->dims.K == 16));
     if ((r = pw_alloc(pw, &p, size_t(std::max(nout, 1)) * I->dims.npw * 2 * ts))) return r;
     I->d_out = p;
+    if (fixed3d_sz && (r = pw_upload(pw, &I->d_row, I->host_row, stream))) return r;
     if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nloc, 1)) * I->dims.np * ts))) return r;
     I->d_L = p;
     if (d == 3 && (I->dims.p == 16 || I->dims.p == 24)) {
@@ -2788,8 +2820,8 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     //    2D orders
     const bool fixed3d = D == 3 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16));
     if (phase == 2 && I->nout > 0 && fixed3d) {
-        if (pd.p == 16) k_pw_out3d_p<T, 16, 9><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co);
-        else k_pw_out3d_p<T, 24, 16><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co);
+        if (pd.p == 16) k_pw_out3d_p<T, 16, 9><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co, I->d_row);
+        else k_pw_out3d_p<T, 24, 16><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co, I->d_row);
         ++pw->launches;
     } else if (phase == 2 && I->nout > 0 && !fixed2d) {
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + 2 * size_t(pd.n1) * pd.p);
@@ -2809,8 +2841,10 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     } else if (phase == 3 && I->nin > 0 && fixed3d) {
         const C2<T>* ph = static_cast<const C2<T>*>(I->d_ph);
         const T* fk = static_cast<const T*>(I->d_f);
-        if (pd.p == 16) k_pw_in3d_p<T, 16, 9><<<I->nin, 256, 0, s>>>(I->d_inl, out, L, Co, ph, fk, inv_rc);
-        else k_pw_in3d_p<T, 24, 16><<<I->nin, 576, 0, s>>>(I->d_inl, out, L, Co, ph, fk, inv_rc);
+        if (pd.p == 16)
+            k_pw_in3d_p<T, 16, 9><<<I->nin, 256, 0, s>>>(I->d_inl, out, L, Co, ph, fk, inv_rc);
+        else
+            k_pw_in3d_p<T, 24, 16><<<I->nin, 576, 0, s>>>(I->d_inl, out, L, Co, ph, fk, inv_rc);
         ++pw->launches;
     } else if (phase == 3 && I->nin > 0) {
         const int KC = std::min(I->KC, 16);
@@ -2968,6 +3002,7 @@ void pw_free_sources(PwPlan* pw) {
     PwImpl* I = impl(pw);
     if (I) {
         I->d_Co = I->d_S = I->d_ph = I->d_f = nullptr;
+        I->d_row = nullptr;
         I->d_leafq = nullptr; I->d_merge = nullptr; I->d_outl = nullptr; I->d_inl = nullptr;
         I->d_down = nullptr; I->d_eval = nullptr; I->d_Q = I->d_out = I->d_L = nullptr;
         I->nleafq = I->nout = I->nin = I->neval = 0;
