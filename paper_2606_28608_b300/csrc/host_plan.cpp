@@ -1068,7 +1068,8 @@ void box_direct_list(const Tree& t, int b, std::vector<int>* out, std::vector<in
     const int d = t.d;
     int nn = 1;
     for (int a = 0; a < d; ++a) nn *= 3;
-    std::vector<std::pair<int, int>> lst;  // (leaf, shift code)
+    thread_local std::vector<std::pair<int, int>> lst;  // (leaf, shift code), reused per thread
+    lst.clear();
     auto add_leaves_below = [&](int x, int code, auto&& self) -> void {
         if (t.is_leaf(x)) {
             if (t.src_end[x] > t.src_begin[x]) lst.push_back({x, code});
@@ -1108,33 +1109,54 @@ void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
     dl->tleaf.clear();
     dl->list_begin.assign(1, 0);
     dl->list.clear();
-    int64_t np = 0;
     dl->shift.clear();
     for (int b = 0; b < int(t.level.size()); ++b)
         if (t.is_leaf(b) && t.tgt_end[b] > t.tgt_begin[b]) dl->tleaf.push_back(b);
-    // each target leaf's list on its own (in parallel), then concatenated in leaf order
+    // each thread builds the lists of a contiguous range of target leaves into its own flat
+    // buffers (in leaf order); the buffers are then concatenated in thread order
     const int64_t nl = int64_t(dl->tleaf.size());
-    std::vector<std::vector<int>> lists(static_cast<size_t>(nl)), shifts(static_cast<size_t>(nl));
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : np)
-    for (int64_t k = 0; k < nl; ++k) {
-        const int b = dl->tleaf[size_t(k)];
-        box_direct_list(t, b, &lists[size_t(k)], &shifts[size_t(k)]);
-        int64_t nsrc = 0;
-        for (int x : lists[size_t(k)]) nsrc += t.src_end[x] - t.src_begin[x];
-        np += nsrc * (t.tgt_end[b] - t.tgt_begin[b]);
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    std::vector<std::vector<int>> tlist(static_cast<size_t>(nthr)), tshift(static_cast<size_t>(nthr));
+    std::vector<int64_t> count(static_cast<size_t>(nl) + 1, 0);
+    std::vector<int64_t> tpairs(static_cast<size_t>(nthr), 0);
+#pragma omp parallel num_threads(nthr)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        const int64_t k0 = nl * tid / nthr, k1 = nl * (tid + 1) / nthr;
+        std::vector<int> lst, sh;
+        int64_t np = 0;
+        for (int64_t k = k0; k < k1; ++k) {
+            const int b = dl->tleaf[size_t(k)];
+            box_direct_list(t, b, &lst, &sh);
+            int64_t nsrc = 0;
+            for (int x : lst) nsrc += t.src_end[x] - t.src_begin[x];
+            np += nsrc * (t.tgt_end[b] - t.tgt_begin[b]);
+            count[size_t(k) + 1] = int64_t(lst.size());
+            tlist[size_t(tid)].insert(tlist[size_t(tid)].end(), lst.begin(), lst.end());
+            tshift[size_t(tid)].insert(tshift[size_t(tid)].end(), sh.begin(), sh.end());
+        }
+        tpairs[size_t(tid)] = np;
     }
     dl->list_begin.resize(size_t(nl) + 1);
-    for (int64_t k = 0; k < nl; ++k) dl->list_begin[size_t(k) + 1] = dl->list_begin[size_t(k)] + int64_t(lists[size_t(k)].size());
+    for (int64_t k = 0; k < nl; ++k) dl->list_begin[size_t(k) + 1] = dl->list_begin[size_t(k)] + count[size_t(k) + 1];
     dl->list.resize(size_t(dl->list_begin[size_t(nl)]));
     dl->shift.resize(dl->list.size());
-#pragma omp parallel for schedule(static)
-    for (int64_t k = 0; k < nl; ++k) {
-        std::copy(lists[size_t(k)].begin(), lists[size_t(k)].end(), dl->list.begin() + dl->list_begin[size_t(k)]);
-        std::copy(shifts[size_t(k)].begin(), shifts[size_t(k)].end(), dl->shift.begin() + dl->list_begin[size_t(k)]);
+    int64_t np = 0;
+    for (int c = 0; c < nthr; ++c) np += tpairs[size_t(c)];
+#pragma omp parallel for schedule(static, 1) num_threads(nthr)
+    for (int c = 0; c < nthr; ++c) {
+        const int64_t base = dl->list_begin[size_t(nl * c / nthr)];
+        std::copy(tlist[size_t(c)].begin(), tlist[size_t(c)].end(), dl->list.begin() + base);
+        std::copy(tshift[size_t(c)].begin(), tshift[size_t(c)].end(), dl->shift.begin() + base);
     }
     if (pairs) *pairs = np;
 }
-
 
 }  // namespace pdmk
 
