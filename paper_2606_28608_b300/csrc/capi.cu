@@ -2308,9 +2308,13 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         if (D == 3 && sizeof(T) == 4 && (plan->w == 8 || plan->w == 13 || plan->w == 17)) {
             if constexpr (sizeof(T) == 4) {
                 const int nb = int((plan->ntgt + 127) / 128);
-                if (plan->w == 8) k_interp3d_w<T, 8><<<nb, 128, 0, s>>>(ia);
-                else if (plan->w == 13) k_interp3d_w<T, 13><<<nb, 128, 0, s>>>(ia);
-                else k_interp3d_w<T, 17><<<nb, 128, 0, s>>>(ia);
+                auto iw = [&](auto kern, size_t smb) {
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
+                    kern<<<nb, 128, smb, s>>>(ia);
+                };
+                if (plan->w == 8) iw(k_interp3d_w<T, 8>, interp3d_w_smem<T, 8>());
+                else if (plan->w == 13) iw(k_interp3d_w<T, 13>, interp3d_w_smem<T, 13>());
+                else iw(k_interp3d_w<T, 17>, interp3d_w_smem<T, 17>());
             }
         } else {
             size_t smem = sizeof(T) * 128 * 2 * D * plan->w;

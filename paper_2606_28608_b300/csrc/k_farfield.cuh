@@ -427,74 +427,137 @@ __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t
 }
 
 // 3D interpolation with a compile-time window width W, a thread per target: the x-axis
-// window values, their derivatives and the wrapped x indices sit in registers, the y and z
-// ones in shared memory (one read per grid row), and the rows' offsets are wrapped once per
-// target, so each grid value costs one load and two multiply-adds.
+// window values and their derivatives sit in registers, the y and z ones in shared memory
+// (one read per grid row).  The block's targets are consecutive in the sorted order and
+// usually close together: when the union of their windows fits kInterpTile cells, the block
+// copies that part of the grid into shared memory once (coalesced along x, indices wrapped on
+// the way in) and every thread reads its window there; otherwise each thread reads the grid
+// through the read-only cache with its rows' offsets wrapped once.  Each grid value costs one
+// load and two multiply-adds either way.
+constexpr int kInterpTile = 8192;  // grid values of the shared tile
+template <typename T, int W>
+constexpr size_t interp3d_w_smem() {
+    return sizeof(T) * (size_t(4) * W * 128 + kInterpTile);
+}
+
 template <typename T, int W>
 __global__ void __launch_bounds__(128)
 k_interp3d_w(InterpArgs<T> a) {
     __shared__ T cw[kMaxCheb], cd[kMaxCheb];
-    __shared__ T wyz[4][W][128];  // (value, derivative) x (y, z) per thread
+    __shared__ int bmin[3], bmax[3];
+    extern __shared__ __align__(16) unsigned char smi[];
+    T (*wyz)[W][128] = reinterpret_cast<T (*)[W][128]>(smi);  // [4][W][128]: (value, derivative) x (y, z)
+    T* tile = reinterpret_cast<T*>(smi) + 4 * W * 128;
     if (threadIdx.x < a.nW) cw[threadIdx.x] = a.coefW[threadIdx.x];
     if (threadIdx.x < a.nWd) cd[threadIdx.x] = a.coefWd[threadIdx.x];
+    if (threadIdx.x < 3) {
+        bmin[threadIdx.x] = 0x7fffffff;
+        bmax[threadIdx.x] = -1;
+    }
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.nt) return;
+    const bool valid = t < a.nt;
     const int tx = threadIdx.x;
-    const int4 g = a.t_g0[t];
-    const T* dq = a.t_dq + size_t(t) * 4;
+    int4 g = make_int4(0, 0, 0, 0);
     T wx[W], dwx[W];
-    int xi[W];
-    {
-        const T del = dq[0];
-        int xx = g.x % a.M0;
-        if (xx < 0) xx += a.M0;
+    if (valid) {
+        g = a.t_g0[t];  // window starts wrapped into [0, M)
+        const T* dq = a.t_dq + size_t(t) * 4;
 #pragma unroll
-        for (int j = 0; j < W; ++j) {
-            pswf_window_d(del - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &wx[j], &dwx[j]);
-            xi[j] = xx;
-            if (++xx == a.M0) xx = 0;
-        }
-    }
-    for (int k = 1; k < 3; ++k) {
-        const T del = dq[k];
-        for (int j = 0; j < W; ++j) {
-            T v, dv;
-            pswf_window_d(del - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &v, &dv);
-            wyz[2 * (k - 1)][j][tx] = v;
-            wyz[2 * (k - 1) + 1][j][tx] = dv;
-        }
-    }
-    T pot = 0, gx = 0, gy = 0, gz = 0;
-    int zz = g.z % a.M2;
-    if (zz < 0) zz += a.M2;
-    int yy0 = g.y % a.M1;
-    if (yy0 < 0) yy0 += a.M1;
-    for (int iz = 0; iz < W; ++iz) {
-        const T wz = wyz[2][iz][tx], dwz = wyz[3][iz][tx];
-        const T* plane = a.grid + size_t(zz) * a.M1 * a.M0;
-        int yy = yy0;
-        T py = 0, gxy = 0, gyy = 0;
-        for (int iy = 0; iy < W; ++iy) {
-            const T* row = plane + size_t(yy) * a.M0;
-            T sx = 0, sdx = 0;
-#pragma unroll
-            for (int ix = 0; ix < W; ++ix) {
-                const T v = __ldg(row + xi[ix]);
-                sx = fma(v, wx[ix], sx);
-                sdx = fma(v, dwx[ix], sdx);
+        for (int j = 0; j < W; ++j) pswf_window_d(dq[0] - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &wx[j], &dwx[j]);
+        for (int k = 1; k < 3; ++k) {
+            const T del = dq[k];
+            for (int j = 0; j < W; ++j) {
+                T v, dv;
+                pswf_window_d(del - T(j), a.half_w_inv2, cw, a.nW, cd, a.nWd, &v, &dv);
+                wyz[2 * (k - 1)][j][tx] = v;
+                wyz[2 * (k - 1) + 1][j][tx] = dv;
             }
-            const T wy = wyz[0][iy][tx], dwy = wyz[1][iy][tx];
-            py = fma(sx, wy, py);
-            gxy = fma(sdx, wy, gxy);
-            gyy = fma(sx, dwy, gyy);
-            if (++yy == a.M1) yy = 0;
         }
-        pot = fma(py, wz, pot);
-        gx = fma(gxy, wz, gx);
-        gy = fma(gyy, wz, gy);
-        gz = fma(py, dwz, gz);
-        if (++zz == a.M2) zz = 0;
+        atomicMin(&bmin[0], g.x);
+        atomicMax(&bmax[0], g.x);
+        atomicMin(&bmin[1], g.y);
+        atomicMax(&bmax[1], g.y);
+        atomicMin(&bmin[2], g.z);
+        atomicMax(&bmax[2], g.z);
+    }
+    __syncthreads();
+    const int ex = bmax[0] - bmin[0] + W, ey = bmax[1] - bmin[1] + W, ez = bmax[2] - bmin[2] + W;
+    const bool use_tile = bmax[0] >= 0 && ex * ey * ez <= kInterpTile;  // block-uniform
+    if (use_tile) {
+        for (int i = tx; i < ex * ey * ez; i += 128) {
+            const int ix = i % ex, iy = (i / ex) % ey, iz = i / (ex * ey);
+            int gx = bmin[0] + ix, gy = bmin[1] + iy, gz = bmin[2] + iz;
+            while (gx >= a.M0) gx -= a.M0;
+            while (gy >= a.M1) gy -= a.M1;
+            while (gz >= a.M2) gz -= a.M2;
+            tile[i] = __ldg(a.grid + (size_t(gz) * a.M1 + gy) * a.M0 + gx);
+        }
+        __syncthreads();
+    }
+    if (!valid) return;
+    T pot = 0, gx = 0, gy = 0, gz = 0;
+    if (use_tile) {
+        const int ox = g.x - bmin[0], oy = g.y - bmin[1], oz = g.z - bmin[2];
+        for (int iz = 0; iz < W; ++iz) {
+            const T wz = wyz[2][iz][tx], dwz = wyz[3][iz][tx];
+            T py = 0, gxy = 0, gyy = 0;
+            for (int iy = 0; iy < W; ++iy) {
+                const T* row = tile + ((oz + iz) * ey + (oy + iy)) * ex + ox;
+                T sx = 0, sdx = 0;
+#pragma unroll
+                for (int ix = 0; ix < W; ++ix) {
+                    const T v = row[ix];
+                    sx = fma(v, wx[ix], sx);
+                    sdx = fma(v, dwx[ix], sdx);
+                }
+                const T wy = wyz[0][iy][tx], dwy = wyz[1][iy][tx];
+                py = fma(sx, wy, py);
+                gxy = fma(sdx, wy, gxy);
+                gyy = fma(sx, dwy, gyy);
+            }
+            pot = fma(py, wz, pot);
+            gx = fma(gxy, wz, gx);
+            gy = fma(gyy, wz, gy);
+            gz = fma(py, dwz, gz);
+        }
+    } else {
+        int xi[W];
+        {
+            int xx = g.x;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                xi[j] = xx;
+                if (++xx == a.M0) xx = 0;
+            }
+        }
+        int zz = g.z, yy0 = g.y;
+        for (int iz = 0; iz < W; ++iz) {
+            const T wz = wyz[2][iz][tx], dwz = wyz[3][iz][tx];
+            const T* plane = a.grid + size_t(zz) * a.M1 * a.M0;
+            int yy = yy0;
+            T py = 0, gxy = 0, gyy = 0;
+            for (int iy = 0; iy < W; ++iy) {
+                const T* row = plane + size_t(yy) * a.M0;
+                T sx = 0, sdx = 0;
+#pragma unroll
+                for (int ix = 0; ix < W; ++ix) {
+                    const T v = __ldg(row + xi[ix]);
+                    sx = fma(v, wx[ix], sx);
+                    sdx = fma(v, dwx[ix], sdx);
+                }
+                const T wy = wyz[0][iy][tx], dwy = wyz[1][iy][tx];
+                py = fma(sx, wy, py);
+                gxy = fma(sdx, wy, gxy);
+                gyy = fma(sx, dwy, gyy);
+                if (++yy == a.M1) yy = 0;
+            }
+            pot = fma(py, wz, pot);
+            gx = fma(gxy, wz, gx);
+            gy = fma(gyy, wz, gy);
+            gz = fma(py, dwz, gz);
+            if (++zz == a.M2) zz = 0;
+        }
     }
     a.pot[t] = double(pot);
     a.gradu[size_t(t) * 3 + 0] = double(gx);
