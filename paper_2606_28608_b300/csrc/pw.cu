@@ -1123,15 +1123,18 @@ __global__ void __launch_bounds__(128) k_pw_in(const int* __restrict__ list, con
 //   A[m1][m2]  = sum_j ce[k0][j] q[2j][m1][m2] + i so[k0][j] q[2j+1][m1][m2]   (thread's own q)
 //   B[+-k1][m2] = E +- i O,  E = sum_j ce[k1][j] A[2j][m2],  O = sum_j so[k1][j] A[2j+1][m2]
 //   out[k0][k1][+-k2] = E' +- i O' over m2 in the same way.
-template <typename T, int P, int K>
+// HALF: the waves are stored over the half ball k2 >= 0 only, as the pair (E', O') of each mode
+// at its compact index (row offset + k2, rows as in rowg), nhalf modes per box; otherwise the
+// two modes +-k2 at their places in the full (K + 1) (2K + 1)^2 layout.
+template <typename T, int P, int K, bool HALF>
 __global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 1)
     k_pw_out3d_p(const int2* __restrict__ list, const T* __restrict__ Q, C2<T>* __restrict__ out,
-                 const C2<T>* __restrict__ Cog, const int2* __restrict__ rowg) {
+                 const C2<T>* __restrict__ Cog, const int2* __restrict__ rowg, int nhalf) {
     constexpr int H = P / 2, KH = K + 1, N1 = 2 * K + 1, PP = P * P;
     __shared__ T ce[KH][H], so[KH][H];
     __shared__ C2<T> A[PP];      // [m1][m2]
     __shared__ C2<T> B[N1][P];   // [k1 + K][m2]
-    __shared__ int2 row[KH][N1];  // (unused offset, m): the ball's rows k2 = -m .. m
+    __shared__ int2 row[KH][N1];  // (half-ball offset, m): the ball's rows k2 = -m .. m
     const int tid = threadIdx.x;
     for (int i = tid; i < KH * H; i += PP) {
         const int k = i / H, j = i % H;
@@ -1188,9 +1191,19 @@ __global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 
                 ox = fma(s, bo.x, ox);
                 oy = fma(s, bo.y, oy);
             }
-            C2<T>* os = o + size_t(k0) * (N1 * N1) + kk1 * N1 + K;
-            os[k2] = C2<T>{ex - oy, ey + ox};
-            if (k2 > 0) os[-k2] = C2<T>{ex + oy, ey - ox};
+            if constexpr (HALF) {
+                C2<T>* oh = out + (size_t(e.y) * nhalf + rw.x + k2) * 2;
+                if constexpr (sizeof(T) == 4) {
+                    *reinterpret_cast<float4*>(oh) = make_float4(ex, ey, ox, oy);
+                } else {
+                    oh[0] = C2<T>{ex, ey};
+                    oh[1] = C2<T>{ox, oy};
+                }
+            } else {
+                C2<T>* os = o + size_t(k0) * (N1 * N1) + kk1 * N1 + K;
+                os[k2] = C2<T>{ex - oy, ey + ox};
+                if (k2 > 0) os[-k2] = C2<T>{ex + oy, ey - ox};
+            }
         }
         // the next slice rewrites A only: every thread is past the reads of A (barrier above),
         // and B is rewritten only after the next barrier
@@ -1338,6 +1351,188 @@ __global__ void __launch_bounds__(P * P) k_pw_in3d_p(const int* __restrict__ lis
         // rewritten after the next barrier
     }
     T* a = Lc + size_t(e[0]) * (PP * P);
+#pragma unroll
+    for (int m0 = 0; m0 < P; ++m0) a[m0 * PP + tid] = acc[m0];
+}
+
+// Translation + incoming of one in-box over the half ball (FP32, the outgoing waves stored as
+// (E, O) pairs: out(+-k2) = E +- i O at the compact index of the mode, k2 >= 0).  Four phases,
+// each over all of the box's modes at once (one barrier between phases):
+//  A. thread per mode (k0, k1, k2 >= 0): the 27 colleagues' pairs, one 16-byte load each.  With
+//     u = exp(-i (2 pi/3) k2) = a + i b, the axis-2 neighbours of a row combine into
+//       Xe = E_0 + a (E_+ + E_-) - b (O_+ - O_-),   Xo = O_0 + a (O_+ + O_-) + b (E_+ - E_-),
+//     which are (I(+k2) + I(-k2)) / 2 and (I(+k2) - I(-k2)) / 2i for the axis-2 sums I; axes 1
+//     and 0 apply the same complex phase to both.  The weight f(|k|) (doubled for k2 > 0, where
+//     the two modes are folded into one pair) gives Sp = 2 Xe f, Sm = 2 Xo f (the -i that the
+//     odd Chebyshev coefficients carry is absorbed into Sm).
+//  B. thread per (row k0, k1 >= 0; four j): the k2 contraction of the rows +-k1,
+//       even n2 = 2j: ce[k2][j] Sp,  odd n2 = 2j + 1: so[k2][j] Sm,
+//     kept as the sum Bp and the difference Bm of the two rows (row k1 = 0 alone: Bm = 0).
+//  C. thread per (k0, m2; four j): the k1 contraction, even m1: ce Bp, odd m1: -i so Bm, times
+//     w = 1 for k0 = 0 and 2 otherwise (the Hermitian half of the k0 axis).
+//  D. thread (m1, m2): the k0 contraction into P registers, a[2j] += ce[k0][j] Re, a[2j+1] +=
+//     so[k0][j] Im, written (each in-box has one entry).
+// Shared memory: the modes' (Sp, Sm) [nhalf], reused for C [nk0][P][P] (region 1 of r1 floats),
+// then B [rows][P] (region 2).
+template <int P, int K>
+__global__ void __launch_bounds__(P * P, P <= 16 ? 2 : 1)
+    k_pw_in3d_h(const int* __restrict__ list, const float4* __restrict__ out, float* __restrict__ Lc,
+                const C2<float>* __restrict__ Cog, const C2<float>* __restrict__ phg, const int* __restrict__ item,
+                const float* __restrict__ fh, const int4* __restrict__ rowb, const int2* __restrict__ k0rows,
+                int nhalf, int nk0, int nrowb, int r1, double inv_rc) {
+    constexpr int H = P / 2, KH = K + 1, N1 = 2 * K + 1, PP = P * P, NQ = H / 4;
+    static_assert(H % 4 == 0, "the j axis is taken four at a time");
+    __shared__ __align__(16) float ce[KH][H];
+    __shared__ __align__(16) float so[KH][H];
+    __shared__ C2<float> u[N1];  // exp(-i (2 pi/3) k), k = -K..K
+    __shared__ int coll[27];
+    __shared__ int2 krow[KH];    // per k0: first row of the k2 contraction, rows (k1 = 0, 1, ..)
+    extern __shared__ __align__(16) float dsm[];
+    float4* Sx = reinterpret_cast<float4*>(dsm);       // [nhalf] (Sp, Sm)
+    float2* Cx = reinterpret_cast<float2*>(dsm);       // [nk0][P][P] (after phase B)
+    float4* Bx = reinterpret_cast<float4*>(dsm + r1);  // [nrowb][P] (Bp, Bm)
+    const int tid = threadIdx.x;
+    for (int i = tid; i < KH * H; i += PP) {
+        const int k = i / H, j = i % H;
+        ce[k][j] = Cog[(k + K) * P + 2 * j].x;
+        so[k][j] = Cog[(k + K) * P + 2 * j + 1].y;
+    }
+    for (int i = tid; i < N1; i += PP) u[i] = phg[2 * N1 + i];  // delta = +1
+    for (int i = tid; i < KH; i += PP) krow[i] = k0rows[i];
+    const int* e = list + size_t(blockIdx.x) * 29;
+    if (tid < 27) coll[tid] = e[2 + tid];
+    __syncthreads();
+    // trapezoidal weight (1/(3h))^3 times the h^2 of D-hat_l(xi) = h^2 f(|k|)
+    const float wlev = float(double(1LL << e[1]) * inv_rc / 27.0);
+    // A. translation
+    for (int i = tid; i < nhalf; i += PP) {
+        const int it = __ldg(item + i);
+        const int k0 = it & 255, kk1 = (it >> 8) & 255, k2 = it >> 16;
+        const float fw = __ldg(fh + i) * wlev;
+        const C2<float> u2 = u[K + k2], u1 = u[kk1], u0 = u[K + k0];
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 t[3];  // per delta0: (Xe, Xo) summed over delta1, delta2
+#pragma unroll
+        for (int d0 = 0; d0 < 3; ++d0) {
+            float4 r[3];  // per delta1: summed over delta2
+#pragma unroll
+            for (int d1 = 0; d1 < 3; ++d1) {
+                const int sM = coll[d0 + 3 * d1], s0 = coll[d0 + 3 * d1 + 9], sP = coll[d0 + 3 * d1 + 18];
+                const float4 pP = sP >= 0 ? __ldg(out + size_t(sP) * nhalf + i) : z;
+                const float4 pM = sM >= 0 ? __ldg(out + size_t(sM) * nhalf + i) : z;
+                const float4 p0 = s0 >= 0 ? __ldg(out + size_t(s0) * nhalf + i) : z;
+                r[d1].x = p0.x + u2.x * (pP.x + pM.x) - u2.y * (pP.z - pM.z);
+                r[d1].y = p0.y + u2.x * (pP.y + pM.y) - u2.y * (pP.w - pM.w);
+                r[d1].z = p0.z + u2.x * (pP.z + pM.z) + u2.y * (pP.x - pM.x);
+                r[d1].w = p0.w + u2.x * (pP.w + pM.w) + u2.y * (pP.y - pM.y);
+            }
+            // axis 1: X_0 + u X_+ + conj(u) X_-, for Xe (x, y) and Xo (z, w)
+            t[d0].x = r[1].x + u1.x * (r[2].x + r[0].x) - u1.y * (r[2].y - r[0].y);
+            t[d0].y = r[1].y + u1.x * (r[2].y + r[0].y) + u1.y * (r[2].x - r[0].x);
+            t[d0].z = r[1].z + u1.x * (r[2].z + r[0].z) - u1.y * (r[2].w - r[0].w);
+            t[d0].w = r[1].w + u1.x * (r[2].w + r[0].w) + u1.y * (r[2].z - r[0].z);
+        }
+        float4 v;
+        v.x = fw * (t[1].x + u0.x * (t[2].x + t[0].x) - u0.y * (t[2].y - t[0].y));
+        v.y = fw * (t[1].y + u0.x * (t[2].y + t[0].y) + u0.y * (t[2].x - t[0].x));
+        v.z = fw * (t[1].z + u0.x * (t[2].z + t[0].z) - u0.y * (t[2].w - t[0].w));
+        v.w = fw * (t[1].w + u0.x * (t[2].w + t[0].w) + u0.y * (t[2].z - t[0].z));
+        Sx[i] = v;
+    }
+    __syncthreads();
+    // B. over k2, rows +-k1 (four j per thread)
+    for (int t = tid; t < nrowb * NQ; t += PP) {
+        const int q = t % NQ, rb = t / NQ;
+        const int4 rw = __ldg(rowb + rb);  // (k0 | k1 << 8 | m << 16, row +k1, row -k1, 0)
+        const int k1 = (rw.x >> 8) & 255, m = rw.x >> 16;
+        const float4* sp = Sx + rw.y;
+        const float4* sn = Sx + rw.z;
+        float ep[4][2], en[4][2], op[4][2], on[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ep[j][0] = ep[j][1] = en[j][0] = en[j][1] = op[j][0] = op[j][1] = on[j][0] = on[j][1] = 0.f;
+        for (int k2 = 0; k2 <= m; ++k2) {
+            const float4 a = sp[k2], b = sn[k2];
+            const float4 c4 = *reinterpret_cast<const float4*>(&ce[k2][4 * q]);
+            const float4 s4 = *reinterpret_cast<const float4*>(&so[k2][4 * q]);
+            const float cv[4] = {c4.x, c4.y, c4.z, c4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ep[j][0] = fmaf(cv[j], a.x, ep[j][0]);
+                ep[j][1] = fmaf(cv[j], a.y, ep[j][1]);
+                en[j][0] = fmaf(cv[j], b.x, en[j][0]);
+                en[j][1] = fmaf(cv[j], b.y, en[j][1]);
+                op[j][0] = fmaf(sv[j], a.z, op[j][0]);
+                op[j][1] = fmaf(sv[j], a.w, op[j][1]);
+                on[j][0] = fmaf(sv[j], b.z, on[j][0]);
+                on[j][1] = fmaf(sv[j], b.w, on[j][1]);
+            }
+        }
+        float4* bo = Bx + size_t(rb) * P + 8 * q;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (k1 == 0) {
+                bo[2 * j] = make_float4(ep[j][0], ep[j][1], 0.f, 0.f);
+                bo[2 * j + 1] = make_float4(op[j][0], op[j][1], 0.f, 0.f);
+            } else {
+                bo[2 * j] = make_float4(ep[j][0] + en[j][0], ep[j][1] + en[j][1], ep[j][0] - en[j][0], ep[j][1] - en[j][1]);
+                bo[2 * j + 1] =
+                    make_float4(op[j][0] + on[j][0], op[j][1] + on[j][1], op[j][0] - on[j][0], op[j][1] - on[j][1]);
+            }
+        }
+    }
+    __syncthreads();
+    // C. over k1 (four j per thread: m1 = 2j even, 2j + 1 odd), into region 1
+    for (int t = tid; t < nk0 * P * NQ; t += PP) {
+        const int q = t % NQ, m2 = (t / NQ) % P, k0 = t / (NQ * P);
+        const int2 kr = krow[k0];
+        float ex[4], ey[4], ox[4], oy[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ex[j] = ey[j] = ox[j] = oy[j] = 0.f;
+        const float4* bb = Bx + size_t(kr.x) * P + m2;
+        for (int k1 = 0; k1 < kr.y; ++k1) {
+            const float4 b = bb[size_t(k1) * P];
+            const float4 c4 = *reinterpret_cast<const float4*>(&ce[k1][4 * q]);
+            const float4 s4 = *reinterpret_cast<const float4*>(&so[k1][4 * q]);
+            const float cv[4] = {c4.x, c4.y, c4.z, c4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ex[j] = fmaf(cv[j], b.x, ex[j]);
+                ey[j] = fmaf(cv[j], b.y, ey[j]);
+                ox[j] = fmaf(sv[j], b.z, ox[j]);
+                oy[j] = fmaf(sv[j], b.w, oy[j]);
+            }
+        }
+        const float w = k0 == 0 ? 1.f : 2.f;
+        float2* cc = Cx + size_t(k0) * PP + m2;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m1 = 2 * (4 * q + j);
+            cc[m1 * P] = make_float2(w * ex[j], w * ey[j]);
+            cc[(m1 + 1) * P] = make_float2(w * oy[j], -w * ox[j]);  // odd m1: times -i
+        }
+    }
+    __syncthreads();
+    // D. over k0 into registers, thread (m1, m2)
+    float acc[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) acc[m] = 0.f;
+    for (int k0 = 0; k0 < nk0; ++k0) {
+        const float2 c = Cx[size_t(k0) * PP + tid];
+#pragma unroll
+        for (int j4 = 0; j4 < H; j4 += 4) {
+            const float4 c4 = *reinterpret_cast<const float4*>(&ce[k0][j4]);
+            const float4 s4 = *reinterpret_cast<const float4*>(&so[k0][j4]);
+            acc[2 * j4 + 0] = fmaf(c4.x, c.x, acc[2 * j4 + 0]);
+            acc[2 * j4 + 1] = fmaf(s4.x, c.y, acc[2 * j4 + 1]);
+            acc[2 * j4 + 2] = fmaf(c4.y, c.x, acc[2 * j4 + 2]);
+            acc[2 * j4 + 3] = fmaf(s4.y, c.y, acc[2 * j4 + 3]);
+            acc[2 * j4 + 4] = fmaf(c4.z, c.x, acc[2 * j4 + 4]);
+            acc[2 * j4 + 5] = fmaf(s4.z, c.y, acc[2 * j4 + 5]);
+            acc[2 * j4 + 6] = fmaf(c4.w, c.x, acc[2 * j4 + 6]);
+            acc[2 * j4 + 7] = fmaf(s4.w, c.y, acc[2 * j4 + 7]);
+        }
+    }
+    float* a = Lc + size_t(e[0]) * (PP * P);
 #pragma unroll
     for (int m0 = 0; m0 < P; ++m0) a[m0 * PP + tid] = acc[m0];
 }
@@ -2226,13 +2421,26 @@ struct PwImpl {
     void* d_ph = nullptr;  // 3 n1 complex
     void* d_f = nullptr;   // (K+1) n1^{d-1}
     // 3D compile-time orders: the modes inside the ball |k| <= 3c/pi (where f is nonzero), row
-    // by row: for (k0, k1) the modes k2 = -m .. m, row[k0][k1 + K] = (offset in a compact
-    // layout, m), m = -1 for an empty row; npwc modes in all.  The outgoing kernel computes and
-    // stores only these modes (at their places in the full layout), and both kernels stop at
-    // the first empty k0 slice.
+    // by row: for (k0, k1) the modes k2 = -m .. m, row[k0][k1 + K] = (offset of the row's
+    // modes k2 = 0 .. m in the half-ball layout, m), m = -1 for an empty row.  The outgoing
+    // kernel computes only these modes and stops at the first empty k0 slice.
     int2* d_row = nullptr;
     std::vector<int2> host_row;
-    int npwc = 0;
+    // FP32 compile-time 3D orders: the outgoing waves over the half ball k2 >= 0 only, one pair
+    // (E, O) per mode (out(+-k2) = E +- i O), at offset row[k0][k1 + K].x + k2 of the box's nhalf;
+    // the per-mode, per-row and per-k0 tables of k_pw_in3d_h
+    int nhalf = 0;
+    bool half3d = false;
+    int nk0 = 0, nrowb = 0, in3d_r1 = 0;
+    size_t in3d_smem = 0;
+    std::vector<int> host_item;
+    std::vector<double> host_fh;
+    std::vector<int4> host_rowb;
+    std::vector<int2> host_k0rows;
+    int* d_item = nullptr;
+    void* d_fh = nullptr;
+    int4* d_rowb = nullptr;
+    int2* d_k0rows = nullptr;
     // lists
     int4* d_leafq = nullptr;
     int nleafq = 0;
@@ -2409,9 +2617,51 @@ void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables&
                     if (kk <= kball) m = k2;  // the same test as f: the ball is convex along k2
                 }
                 I->host_row[size_t(k0) * D.n1 + kk1] = make_int2(off, m);
-                off += m >= 0 ? 2 * m + 1 : 0;
+                off += m + 1;
             }
-        I->npwc = off;
+        I->nhalf = off;
+        // the half-ball modes in that order: (k0, k1 + K, k2) and f(|k|), doubled for k2 > 0
+        I->host_item.clear();
+        I->host_fh.clear();
+        for (int k0 = 0; k0 <= K; ++k0)
+            for (int kk1 = 0; kk1 < D.n1; ++kk1)
+                for (int k2 = 0; k2 <= I->host_row[size_t(k0) * D.n1 + kk1].y; ++k2) {
+                    I->host_item.push_back(k0 | (kk1 << 8) | (k2 << 16));
+                    const double f = I->host_f[size_t(k0) * D.nk1 + size_t(kk1) * D.n1 + K + k2];
+                    I->host_fh.push_back(k2 > 0 ? 2.0 * f : f);
+                }
+        // rows (k0, k1 >= 0) of the k2 contraction: per k0 the rows k1 = 0, 1, .. that meet the
+        // ball (a contiguous range, the ball being convex), as (k0 | k1 << 8 | m << 16, offset of
+        // row +k1, offset of row -k1, 0); per k0 (first row, count); nk0 slices meet the ball
+        I->host_rowb.clear();
+        I->host_k0rows.assign(size_t(K + 1), make_int2(0, 0));
+        I->nk0 = 0;
+        for (int k0 = 0; k0 <= K; ++k0) {
+            I->host_k0rows[k0].x = int(I->host_rowb.size());
+            for (int k1 = 0; k1 <= K; ++k1) {
+                const int2 rp = I->host_row[size_t(k0) * D.n1 + K + k1];
+                const int2 rn = I->host_row[size_t(k0) * D.n1 + K - k1];
+                if (rp.y < 0) break;
+                I->host_rowb.push_back(make_int4(k0 | (k1 << 8) | (rp.y << 16), rp.x, rn.x, 0));
+            }
+            I->host_k0rows[k0].y = int(I->host_rowb.size()) - I->host_k0rows[k0].x;
+            if (I->host_k0rows[k0].y > 0) I->nk0 = k0 + 1;
+        }
+        I->nrowb = int(I->host_rowb.size());
+        // FP32 plans of the compile-time orders keep the waves over the half ball when the
+        // incoming kernel's shared memory fits
+        if (mixed && ((p == 16 && K == 9) || (p == 24 && K == 16))) {
+            const size_t r1 = std::max(size_t(I->nhalf) * 4, size_t(I->nk0) * p * p * 2);  // floats
+            const size_t smem = (r1 + size_t(I->nrowb) * p * 4) * sizeof(float);
+            int dev = 0, optin = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            if (smem + 8192 <= size_t(optin)) {
+                I->half3d = true;
+                I->in3d_r1 = int(r1);
+                I->in3d_smem = smem;
+            }
+        }
     }
     // k0 chunk: the [KC][p^{d-1}] complex slices must fit next to the tables in shared memory
     const size_t ts = mixed ? 4 : 8;
@@ -2664,9 +2914,16 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nq, 1)) * I->dims.np * ts))) return r;
     I->d_Q = p;
     const bool fixed3d_sz = d == 3 && ((I->dims.p == 16 && I->dims.K == 9) || (I->dims.p == 24 && I->dims.K == 16));
-    if ((r = pw_alloc(pw, &p, size_t(std::max(nout, 1)) * I->dims.npw * 2 * ts))) return r;
+    const size_t out_modes = I->half3d ? size_t(I->nhalf) * 2 : size_t(I->dims.npw);  // complex values per box
+    if ((r = pw_alloc(pw, &p, size_t(std::max(nout, 1)) * out_modes * 2 * ts))) return r;
     I->d_out = p;
     if (fixed3d_sz && (r = pw_upload(pw, &I->d_row, I->host_row, stream))) return r;
+    if (I->half3d) {
+        if ((r = pw_upload(pw, &I->d_item, I->host_item, stream))) return r;
+        if ((r = pw_upload_typed(pw, &I->d_fh, I->host_fh, stream))) return r;
+        if ((r = pw_upload(pw, &I->d_rowb, I->host_rowb, stream))) return r;
+        if ((r = pw_upload(pw, &I->d_k0rows, I->host_k0rows, stream))) return r;
+    }
     if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nloc, 1)) * I->dims.np * ts))) return r;
     I->d_L = p;
     if (d == 3 && (I->dims.p == 16 || I->dims.p == 24)) {
@@ -2820,8 +3077,13 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     //    2D orders
     const bool fixed3d = D == 3 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16));
     if (phase == 2 && I->nout > 0 && fixed3d) {
-        if (pd.p == 16) k_pw_out3d_p<T, 16, 9><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co, I->d_row);
-        else k_pw_out3d_p<T, 24, 16><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co, I->d_row);
+        if (I->half3d) {
+            if (pd.p == 16) k_pw_out3d_p<T, 16, 9, true><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co, I->d_row, I->nhalf);
+            else k_pw_out3d_p<T, 24, 16, true><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co, I->d_row, I->nhalf);
+        } else {
+            if (pd.p == 16) k_pw_out3d_p<T, 16, 9, false><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co, I->d_row, 0);
+            else k_pw_out3d_p<T, 24, 16, false><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co, I->d_row, 0);
+        }
         ++pw->launches;
     } else if (phase == 2 && I->nout > 0 && !fixed2d) {
         size_t sm = ts * 2 * (size_t(pd.n1) * pd.p + size_t(I->KC) * pd.pd1 + 2 * size_t(pd.n1) * pd.p);
@@ -2837,6 +3099,20 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
         if (pd.p == 16) k_pw_in2d_p<T, 16, 9><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
         else if (pd.p == 24) k_pw_in2d_p<T, 24, 16><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
         else k_pw_in2d_p<T, 32, 23><<<g, 128, 0, s>>>(I->d_inl, I->nin, out, L, Co, ph, fk);
+        ++pw->launches;
+    } else if (phase == 3 && I->nin > 0 && fixed3d && I->half3d) {
+        if constexpr (sizeof(T) == 4) {
+            const C2<float>* ph = static_cast<const C2<float>*>(I->d_ph);
+            const float4* o4 = reinterpret_cast<const float4*>(I->d_out);
+            auto hin = [&](auto kern, int P) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(I->in3d_smem));
+                kern<<<I->nin, P * P, I->in3d_smem, s>>>(I->d_inl, o4, L, Co, ph, I->d_item,
+                                                         static_cast<const float*>(I->d_fh), I->d_rowb, I->d_k0rows,
+                                                         I->nhalf, I->nk0, I->nrowb, I->in3d_r1, inv_rc);
+            };
+            if (pd.p == 16) hin(k_pw_in3d_h<16, 9>, 16);
+            else hin(k_pw_in3d_h<24, 16>, 24);
+        }
         ++pw->launches;
     } else if (phase == 3 && I->nin > 0 && fixed3d) {
         const C2<T>* ph = static_cast<const C2<T>*>(I->d_ph);
@@ -3003,6 +3279,7 @@ void pw_free_sources(PwPlan* pw) {
     if (I) {
         I->d_Co = I->d_S = I->d_ph = I->d_f = nullptr;
         I->d_row = nullptr;
+        I->d_item = nullptr; I->d_fh = nullptr; I->d_rowb = nullptr; I->d_k0rows = nullptr;
         I->d_leafq = nullptr; I->d_merge = nullptr; I->d_outl = nullptr; I->d_inl = nullptr;
         I->d_down = nullptr; I->d_eval = nullptr; I->d_Q = I->d_out = I->d_L = nullptr;
         I->nleafq = I->nout = I->nin = I->neval = 0;
