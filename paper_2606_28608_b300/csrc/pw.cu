@@ -1123,18 +1123,16 @@ __global__ void __launch_bounds__(128) k_pw_in(const int* __restrict__ list, con
 //   A[m1][m2]  = sum_j ce[k0][j] q[2j][m1][m2] + i so[k0][j] q[2j+1][m1][m2]   (thread's own q)
 //   B[+-k1][m2] = E +- i O,  E = sum_j ce[k1][j] A[2j][m2],  O = sum_j so[k1][j] A[2j+1][m2]
 //   out[k0][k1][+-k2] = E' +- i O' over m2 in the same way.
-// HALF: the waves are stored over the half ball k2 >= 0 only, as the pair (E', O') of each mode
-// at its compact index (row offset + k2, rows as in rowg), nhalf modes per box; otherwise the
-// two modes +-k2 at their places in the full (K + 1) (2K + 1)^2 layout.
-template <typename T, int P, int K, bool HALF>
+// The modes are stored at their places in the full (K + 1) (2K + 1)^2 layout.
+template <typename T, int P, int K>
 __global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 1)
     k_pw_out3d_p(const int2* __restrict__ list, const T* __restrict__ Q, C2<T>* __restrict__ out,
-                 const C2<T>* __restrict__ Cog, const int2* __restrict__ rowg, int nhalf) {
+                 const C2<T>* __restrict__ Cog, const int2* __restrict__ rowg) {
     constexpr int H = P / 2, KH = K + 1, N1 = 2 * K + 1, PP = P * P;
     __shared__ T ce[KH][H], so[KH][H];
     __shared__ C2<T> A[PP];      // [m1][m2]
     __shared__ C2<T> B[N1][P];   // [k1 + K][m2]
-    __shared__ int2 row[KH][N1];  // (half-ball offset, m): the ball's rows k2 = -m .. m
+    __shared__ int2 row[KH][N1];  // (unused offset, m): the ball's rows k2 = -m .. m
     const int tid = threadIdx.x;
     for (int i = tid; i < KH * H; i += PP) {
         const int k = i / H, j = i % H;
@@ -1191,22 +1189,147 @@ __global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P * P <= 576) ? 2 : 
                 ox = fma(s, bo.x, ox);
                 oy = fma(s, bo.y, oy);
             }
-            if constexpr (HALF) {
-                C2<T>* oh = out + (size_t(e.y) * nhalf + rw.x + k2) * 2;
-                if constexpr (sizeof(T) == 4) {
-                    *reinterpret_cast<float4*>(oh) = make_float4(ex, ey, ox, oy);
-                } else {
-                    oh[0] = C2<T>{ex, ey};
-                    oh[1] = C2<T>{ox, oy};
-                }
-            } else {
-                C2<T>* os = o + size_t(k0) * (N1 * N1) + kk1 * N1 + K;
-                os[k2] = C2<T>{ex - oy, ey + ox};
-                if (k2 > 0) os[-k2] = C2<T>{ex + oy, ey - ox};
-            }
+            C2<T>* os = o + size_t(k0) * (N1 * N1) + kk1 * N1 + K;
+            os[k2] = C2<T>{ex - oy, ey + ox};
+            if (k2 > 0) os[-k2] = C2<T>{ex + oy, ey - ox};
         }
         // the next slice rewrites A only: every thread is past the reads of A (barrier above),
         // and B is rewritten only after the next barrier
+    }
+}
+
+// Outgoing waves of one box over the half ball (FP32; the pairs (E, O) of k_pw_in3d_h's layout),
+// the same three contractions as k_pw_out3d_p, each over all of the box's modes at once:
+//  1. thread (m1, m2): A[k0][m1][m2] = sum_j ce[k0][j] q[2j][m1][m2] + i so[k0][j] q[2j+1][m1][m2]
+//     for every slice k0 that meets the ball (its q in registers);
+//  2. thread per (k0, m2; eight k1 >= 0): E = sum_j ce[k1][j] A[2j], O = sum_j so[k1][j] A[2j+1],
+//     kept as the pair of rows +-k1 (B(+-k1) = E +- i O);
+//  3. thread per (row k0, k1 >= 0; four k2 >= 0): E' = sum_j ce[k2][j] B[2j], O' = sum_j so[k2][j]
+//     B[2j+1] for both rows +-k1, stored as (E', O') at the modes' compact indices.
+// The tables are transposed (j major, the k axis padded to a multiple of eight) so that one
+// 16-byte load gives four k.  Shared memory: A [nk0][P][P] in region 1 (r1 floats), the row pairs
+// [rows][P + 1] in region 2, as in k_pw_in3d_h.
+template <int P, int K>
+__global__ void __launch_bounds__(P * P, P <= 16 ? 2 : 1)
+    k_pw_out3d_h(const int2* __restrict__ list, const float* __restrict__ Q, float4* __restrict__ out,
+                 const C2<float>* __restrict__ Cog, const int4* __restrict__ rowb, const int2* __restrict__ k0rows,
+                 int nhalf, int nk0, int nrowb, int r1) {
+    constexpr int H = P / 2, KH = K + 1, PP = P * P, KQ = (KH + 3) / 4, KT = 8 * ((KH + 7) / 8), KE = KT / 8;
+    __shared__ __align__(16) float ce[KH][H];
+    __shared__ __align__(16) float so[KH][H];
+    __shared__ __align__(16) float ceT[H][KT];
+    __shared__ __align__(16) float soT[H][KT];
+    __shared__ int2 krow[KH];
+    extern __shared__ __align__(16) float dsm[];
+    float2* Ax = reinterpret_cast<float2*>(dsm);       // [nk0][P][P]
+    float4* Bx = reinterpret_cast<float4*>(dsm + r1);  // [nrowb][P + 1] (E, O); the pad spreads rows over banks
+    const int tid = threadIdx.x;
+    for (int i = tid; i < KH * H; i += PP) {
+        const int k = i / H, j = i % H;
+        ce[k][j] = Cog[(k + K) * P + 2 * j].x;
+        so[k][j] = Cog[(k + K) * P + 2 * j + 1].y;
+    }
+    for (int i = tid; i < H * KT; i += PP) {
+        const int j = i / KT, k = i % KT;
+        ceT[j][k] = k < KH ? Cog[(k + K) * P + 2 * j].x : 0.f;
+        soT[j][k] = k < KH ? Cog[(k + K) * P + 2 * j + 1].y : 0.f;
+    }
+    for (int i = tid; i < KH; i += PP) krow[i] = k0rows[i];
+    const int2 e = list[blockIdx.x];
+    const float* q = Q + size_t(e.x) * (PP * P);
+    float qr[P];
+#pragma unroll
+    for (int m0 = 0; m0 < P; ++m0) qr[m0] = q[m0 * PP + tid];
+    __syncthreads();
+    // 1. over m0, every slice
+    for (int k0 = 0; k0 < nk0; ++k0) {
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int j4 = 0; j4 < H; j4 += 4) {
+            const float4 c4 = *reinterpret_cast<const float4*>(&ce[k0][j4]);
+            const float4 s4 = *reinterpret_cast<const float4*>(&so[k0][j4]);
+            ax = fmaf(c4.x, qr[2 * j4 + 0], ax);
+            ay = fmaf(s4.x, qr[2 * j4 + 1], ay);
+            ax = fmaf(c4.y, qr[2 * j4 + 2], ax);
+            ay = fmaf(s4.y, qr[2 * j4 + 3], ay);
+            ax = fmaf(c4.z, qr[2 * j4 + 4], ax);
+            ay = fmaf(s4.z, qr[2 * j4 + 5], ay);
+            ax = fmaf(c4.w, qr[2 * j4 + 6], ax);
+            ay = fmaf(s4.w, qr[2 * j4 + 7], ay);
+        }
+        Ax[size_t(k0) * PP + tid] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    // 2. over m1, eight k1 per thread (m2 fastest across threads)
+    for (int t = tid; t < nk0 * P * KE; t += PP) {
+        const int m2 = t % P, ke = (t / P) % KE, k0 = t / (KE * P);
+        const int2 kr = krow[k0];
+        if (8 * ke >= kr.y) continue;
+        float ex[8], ey[8], ox[8], oy[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ex[i] = ey[i] = ox[i] = oy[i] = 0.f;
+        const float2* a = Ax + size_t(k0) * PP + m2;
+#pragma unroll 2
+        for (int j = 0; j < H; ++j) {
+            const float2 ae = a[(2 * j) * P], ao = a[(2 * j + 1) * P];
+            const float4 c0 = *reinterpret_cast<const float4*>(&ceT[j][8 * ke]);
+            const float4 c1 = *reinterpret_cast<const float4*>(&ceT[j][8 * ke + 4]);
+            const float4 s0 = *reinterpret_cast<const float4*>(&soT[j][8 * ke]);
+            const float4 s1 = *reinterpret_cast<const float4*>(&soT[j][8 * ke + 4]);
+            const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                ex[i] = fmaf(cv[i], ae.x, ex[i]);
+                ey[i] = fmaf(cv[i], ae.y, ey[i]);
+                ox[i] = fmaf(sv[i], ao.x, ox[i]);
+                oy[i] = fmaf(sv[i], ao.y, oy[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (8 * ke + i < kr.y) Bx[size_t(kr.x + 8 * ke + i) * (P + 1) + m2] = make_float4(ex[i], ey[i], ox[i], oy[i]);
+    }
+    __syncthreads();
+    // 3. over m2, four k2 per thread, rows +k1 and -k1
+    float4* o = out + size_t(e.y) * nhalf;
+    for (int t = tid; t < nrowb * KQ; t += PP) {
+        const int kq = t % KQ, rb = t / KQ;
+        const int4 rw = __ldg(rowb + rb);  // (k0 | k1 << 8 | m << 16, row +k1, row -k1, 0)
+        const int k1 = (rw.x >> 8) & 255, m = rw.x >> 16;
+        if (4 * kq > m) continue;
+        float pe[4][2], po[4][2], ne[4][2], no[4][2];  // (E', O') of rows +k1 / -k1 per k2
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pe[i][0] = pe[i][1] = po[i][0] = po[i][1] = ne[i][0] = ne[i][1] = no[i][0] = no[i][1] = 0.f;
+        const float4* b = Bx + size_t(rb) * (P + 1);
+#pragma unroll 4
+        for (int j = 0; j < H; ++j) {
+            const float4 be = b[2 * j], bo = b[2 * j + 1];  // (E, O) at n2 = 2j, 2j + 1
+            // B(+k1) = E + i O, B(-k1) = E - i O
+            const float bpe_x = be.x - be.w, bpe_y = be.y + be.z, bne_x = be.x + be.w, bne_y = be.y - be.z;
+            const float bpo_x = bo.x - bo.w, bpo_y = bo.y + bo.z, bno_x = bo.x + bo.w, bno_y = bo.y - bo.z;
+            const float4 c4 = *reinterpret_cast<const float4*>(&ceT[j][4 * kq]);
+            const float4 s4 = *reinterpret_cast<const float4*>(&soT[j][4 * kq]);
+            const float cv[4] = {c4.x, c4.y, c4.z, c4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                pe[i][0] = fmaf(cv[i], bpe_x, pe[i][0]);
+                pe[i][1] = fmaf(cv[i], bpe_y, pe[i][1]);
+                po[i][0] = fmaf(sv[i], bpo_x, po[i][0]);
+                po[i][1] = fmaf(sv[i], bpo_y, po[i][1]);
+                ne[i][0] = fmaf(cv[i], bne_x, ne[i][0]);
+                ne[i][1] = fmaf(cv[i], bne_y, ne[i][1]);
+                no[i][0] = fmaf(sv[i], bno_x, no[i][0]);
+                no[i][1] = fmaf(sv[i], bno_y, no[i][1]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k2 = 4 * kq + i;
+            if (k2 > m) break;
+            o[rw.y + k2] = make_float4(pe[i][0], pe[i][1], po[i][0], po[i][1]);
+            if (k1 > 0) o[rw.z + k2] = make_float4(ne[i][0], ne[i][1], no[i][0], no[i][1]);
+        }
     }
 }
 
@@ -1373,7 +1496,7 @@ __global__ void __launch_bounds__(P * P) k_pw_in3d_p(const int* __restrict__ lis
 //  D. thread (m1, m2): the k0 contraction into P registers, a[2j] += ce[k0][j] Re, a[2j+1] +=
 //     so[k0][j] Im, written (each in-box has one entry).
 // Shared memory: the modes' (Sp, Sm) [nhalf], reused for C [nk0][P][P] (region 1 of r1 floats),
-// then B [rows][P] (region 2).
+// then B [rows][P + 1] (region 2).
 template <int P, int K>
 __global__ void __launch_bounds__(P * P, P <= 16 ? 2 : 1)
     k_pw_in3d_h(const int* __restrict__ list, const float4* __restrict__ out, float* __restrict__ Lc,
@@ -1390,7 +1513,7 @@ __global__ void __launch_bounds__(P * P, P <= 16 ? 2 : 1)
     extern __shared__ __align__(16) float dsm[];
     float4* Sx = reinterpret_cast<float4*>(dsm);       // [nhalf] (Sp, Sm)
     float2* Cx = reinterpret_cast<float2*>(dsm);       // [nk0][P][P] (after phase B)
-    float4* Bx = reinterpret_cast<float4*>(dsm + r1);  // [nrowb][P] (Bp, Bm)
+    float4* Bx = reinterpret_cast<float4*>(dsm + r1);  // [nrowb][P + 1] (Bp, Bm); the pad spreads rows over banks
     const int tid = threadIdx.x;
     for (int i = tid; i < KH * H; i += PP) {
         const int k = i / H, j = i % H;
@@ -1467,7 +1590,7 @@ __global__ void __launch_bounds__(P * P, P <= 16 ? 2 : 1)
                 on[j][1] = fmaf(sv[j], b.w, on[j][1]);
             }
         }
-        float4* bo = Bx + size_t(rb) * P + 8 * q;
+        float4* bo = Bx + size_t(rb) * (P + 1) + 8 * q;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (k1 == 0) {
@@ -1488,9 +1611,9 @@ __global__ void __launch_bounds__(P * P, P <= 16 ? 2 : 1)
         float ex[4], ey[4], ox[4], oy[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) ex[j] = ey[j] = ox[j] = oy[j] = 0.f;
-        const float4* bb = Bx + size_t(kr.x) * P + m2;
+        const float4* bb = Bx + size_t(kr.x) * (P + 1) + m2;
         for (int k1 = 0; k1 < kr.y; ++k1) {
-            const float4 b = bb[size_t(k1) * P];
+            const float4 b = bb[size_t(k1) * (P + 1)];
             const float4 c4 = *reinterpret_cast<const float4*>(&ce[k1][4 * q]);
             const float4 s4 = *reinterpret_cast<const float4*>(&so[k1][4 * q]);
             const float cv[4] = {c4.x, c4.y, c4.z, c4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
@@ -2652,7 +2775,7 @@ void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables&
         // incoming kernel's shared memory fits
         if (mixed && ((p == 16 && K == 9) || (p == 24 && K == 16))) {
             const size_t r1 = std::max(size_t(I->nhalf) * 4, size_t(I->nk0) * p * p * 2);  // floats
-            const size_t smem = (r1 + size_t(I->nrowb) * p * 4) * sizeof(float);
+            const size_t smem = (r1 + size_t(I->nrowb) * (p + 1) * 4) * sizeof(float);
             int dev = 0, optin = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -3078,11 +3201,19 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
     const bool fixed3d = D == 3 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16));
     if (phase == 2 && I->nout > 0 && fixed3d) {
         if (I->half3d) {
-            if (pd.p == 16) k_pw_out3d_p<T, 16, 9, true><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co, I->d_row, I->nhalf);
-            else k_pw_out3d_p<T, 24, 16, true><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co, I->d_row, I->nhalf);
+            if constexpr (sizeof(T) == 4) {
+                float4* o4 = reinterpret_cast<float4*>(I->d_out);
+                auto hout = [&](auto kern, int P) {
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(I->in3d_smem));
+                    kern<<<I->nout, P * P, I->in3d_smem, s>>>(I->d_outl, Q, o4, Co, I->d_rowb, I->d_k0rows, I->nhalf,
+                                                              I->nk0, I->nrowb, I->in3d_r1);
+                };
+                if (pd.p == 16) hout(k_pw_out3d_h<16, 9>, 16);
+                else hout(k_pw_out3d_h<24, 16>, 24);
+            }
         } else {
-            if (pd.p == 16) k_pw_out3d_p<T, 16, 9, false><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co, I->d_row, 0);
-            else k_pw_out3d_p<T, 24, 16, false><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co, I->d_row, 0);
+            if (pd.p == 16) k_pw_out3d_p<T, 16, 9><<<I->nout, 256, 0, s>>>(I->d_outl, Q, out, Co, I->d_row);
+            else k_pw_out3d_p<T, 24, 16><<<I->nout, 576, 0, s>>>(I->d_outl, Q, out, Co, I->d_row);
         }
         ++pw->launches;
     } else if (phase == 2 && I->nout > 0 && !fixed2d) {
