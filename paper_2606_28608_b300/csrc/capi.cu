@@ -95,8 +95,6 @@ struct pdmk_plan_s {
     void* d_coefB = nullptr;
     void* d_coefW = nullptr;
     void* d_coefWd = nullptr;
-    void* d_monoA = nullptr;
-    void* d_monoB = nullptr;
     void* d_monoW = nullptr;
     void* d_monoWd = nullptr;
     double* d_weight = nullptr;
@@ -703,8 +701,6 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
         PCHECK(coef_upload(plan->cB, &plan->d_coefB));
         PCHECK(coef_upload(plan->cW, &plan->d_coefW));
         PCHECK(coef_upload(plan->cWd, &plan->d_coefWd));
-        PCHECK(coef_upload(plan->mA, &plan->d_monoA));
-        PCHECK(coef_upload(plan->mB, &plan->d_monoB));
         PCHECK(coef_upload(plan->mW, &plan->d_monoW));
         PCHECK(coef_upload(plan->mWd, &plan->d_monoWd));
         PCHECK(dalloc(plan, plan->plan_allocs, &plan->d_weight, size_t(plan->nhalf)));
@@ -2025,6 +2021,15 @@ static int stage_mark(pdmk_plan plan, const char* name) {
     return PDMK_OK;
 }
 
+// The warp kernel's residual series (monomials in 2 s - 1, zero-padded) into its arguments.
+template <typename T>
+static void near_coefs(pdmk_plan plan, NearArgs<T>* na) {
+    for (int k = 0; k < kNearMono; ++k) {
+        na->cmA[k] = k < int(plan->mA.size()) ? T(plan->mA[k]) : T(0);
+        na->cmB[k] = k < int(plan->mB.size()) ? T(plan->mB[k]) : T(0);
+    }
+}
+
 // The residual direct sum over ndesc target descriptors (near-field arguments filled in).
 template <typename T, int D>
 static void near_launch(pdmk_plan plan, const NearArgs<T>& na, int ndesc, cudaStream_t st) {
@@ -2362,8 +2367,7 @@ static int run_eval(pdmk_plan plan, double* pot, double* grad, int64_t out_first
         na.ent = plan->d_ent;
         na.ent_sh = static_cast<const T*>(plan->d_ent_sh);
         na.ent_shlo = static_cast<const T*>(plan->d_ent_shlo);
-        na.monoA = static_cast<const T*>(plan->d_monoA);
-        na.monoB = static_cast<const T*>(plan->d_monoB);
+        near_coefs(plan, &na);
         near_launch<T, D>(plan, na, plan->nnear, s_near);
         ++plan->launches;
         CK(cudaGetLastError());
@@ -2928,8 +2932,7 @@ static int run_eval_targets(pdmk_plan plan, const TargetLayout& L, char* buf, do
         na.ent = ent;
         na.ent_sh = ent_sh;
         na.ent_shlo = reinterpret_cast<const T*>(ent_shlo);
-        na.monoA = static_cast<const T*>(plan->d_monoA);
-        na.monoB = static_cast<const T*>(plan->d_monoB);
+        near_coefs(plan, &na);
         near_launch<T, D>(plan, na, int(L.desc.size()), s);
         CK(cudaGetLastError());
     }
@@ -3224,8 +3227,7 @@ static int run_eval_bloch(pdmk_plan plan, const double* beta_host, double* dp, d
             na.ent = plan->d_ent;
             na.ent_sh = static_cast<const T*>(plan->d_ent_sh);
             na.ent_shlo = static_cast<const T*>(plan->d_ent_shlo);
-            na.monoA = static_cast<const T*>(plan->d_monoA);
-            na.monoB = static_cast<const T*>(plan->d_monoB);
+            near_coefs(plan, &na);
             near_launch<T, D>(plan, na, plan->nnear, s);
             CK(cudaGetLastError());
         }

@@ -295,7 +295,7 @@ struct NearWarpSmem {
 
 // NH: padded length of the B series; NA <= NH: of the A series (usually two terms shorter)
 template <typename T, int D, int NH, int NA>
-__global__ void __launch_bounds__(32 * kNearWarps)
+__global__ void __launch_bounds__(32 * kNearWarps, sizeof(T) == 4 ? 8 : 1)
 k_near_warp(NearArgs<T> a) {
     constexpr int kLo = NearWarpSmem<T, D>::kLo;
     constexpr unsigned kFull = 0xffffffffu;
@@ -303,13 +303,9 @@ k_near_warp(NearArgs<T> a) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li = blockIdx.x * kNearWarps + w;
     if (li >= a.ntleaf) return;  // whole warp; the kernel has no block-wide barrier
+    static_assert(NH <= kNearMono && NA <= NH, "series lengths");
     NearWarpSmem<T, D>& S = smem[w];
     const TLeaf L = a.tleaf[li];
-    T cA[NA], cB[NH];
-#pragma unroll
-    for (int k = 0; k < NA; ++k) cA[k] = a.monoA[k];
-#pragma unroll
-    for (int k = 0; k < NH; ++k) cB[k] = a.monoB[k];
     const double hinv_d = a.inv_rc * double(1LL << L.level);
     const T hinv = T(hinv_d);
     const T h2inv = T(hinv_d * hinv_d);
@@ -448,11 +444,11 @@ k_near_warp(NearArgs<T> a) {
                     if (a.count_in) ++nin;
                     const T q = S.sq[j];
                     const T xc = fma(T(2), s, T(-1));
-                    T fa = cA[NA - 1], fb = cB[NH - 1];
+                    T fa = a.cmA[NA - 1], fb = a.cmB[NH - 1];
 #pragma unroll
                     for (int m = NH - 2; m >= 0; --m) {
-                        if (m < NA - 1) fa = fma(fa, xc, cA[m]);
-                        fb = fma(fb, xc, cB[m]);
+                        if (m < NA - 1) fa = fma(fa, xc, a.cmA[m]);
+                        fb = fma(fb, xc, a.cmB[m]);
                     }
                     if constexpr (D == 3) {
                         // R = (1 - t A)/(4 pi r); grad R = -(1 - t A + t B) dr / (4 pi r^3)

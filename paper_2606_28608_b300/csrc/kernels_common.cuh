@@ -8,6 +8,7 @@
 namespace pdmk {
 
 constexpr int kMaxCheb = 40;  // Chebyshev terms held per kernel function
+constexpr int kNearMono = 24;  // monomial terms of the warp near-field kernel's series (its longest instance)
 
 // Chebyshev series in x in [-1, 1] by Clenshaw's recurrence (stable in FP32).
 template <typename T>
@@ -71,9 +72,10 @@ struct NearArgs {
     const int2* ent;
     const T* ent_sh;
     const T* ent_shlo;
-    // warp kernel: A and B as monomials in x = 2 s - 1 (zero-padded)
-    const T* monoA;
-    const T* monoB;
+    // warp kernel: A and B as monomials in x = 2 s - 1 (zero-padded), by value: the kernel's
+    // Horner steps take them as constant operands instead of holding them in registers
+    T cmA[kNearMono];
+    T cmB[kNearMono];
 };
 
 // -------- far field -----------------------------------------------------------------
