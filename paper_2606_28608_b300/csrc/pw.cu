@@ -198,6 +198,85 @@ __global__ void __launch_bounds__(256) k_leaf_moments3d_gemm(const int4* __restr
         for (int k = 0; k < CT; ++k) Qb[(rg * RT + i) * PP + cg + 64 * k] = acc[i][k];
 }
 
+// 3D leaf moments (FP32) with a three-way register tile: thread (a, b, c) owns
+// Q[TA a + i][4 b + j][4 c + k], i < TA, j, k < 4.  Sources are taken 32 at a time; per chunk the
+// rows q T_m0(t0), T_m1(t1), T_m2(t2) of every source are formed once in shared memory (thread
+// per source and axis, the three-term recurrence), and per source a thread forms its 4 TA
+// products of the first two rows and adds each times its four third-row values:
+//     Q[m0][m1][m2] += (q T_m0(t0_s) T_m1(t1_s)) T_m2(t2_s)      (P^3 multiply-adds per source)
+// with three 16-byte (or 8-byte) shared loads per source.  The chunk loop runs over the sources
+// present only.
+template <int P, int TA>
+__global__ void __launch_bounds__((P / TA) * (P / 4) * (P / 4))
+    k_leaf_moments3d_t(const int4* __restrict__ leaves, const float* __restrict__ src4, float* __restrict__ Q,
+                       double inv_rc) {
+    constexpr int NA = P / TA, NB = P / 4, NT = NA * NB * NB, PP = P * P, NS = 32;
+    static_assert(P % 4 == 0 && P % TA == 0 && (TA == 2 || TA == 4), "tile split");
+    __shared__ __align__(16) float Tt[NS][3][P];  // [source][axis][m]; the charge in the axis-0 row
+    const int tid = threadIdx.x;
+    const int c = tid % NB, b = (tid / NB) % NB, a = tid / (NB * NB);
+    const int4 lf = leaves[blockIdx.x];  // (first source, count, q slot, level)
+    const float scale = float(2.0 * inv_rc * double(1LL << lf.w));  // t = 2 (y - c)/h
+    float acc[TA][4][4];
+#pragma unroll
+    for (int i = 0; i < TA; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    for (int s0 = 0; s0 < lf.y; s0 += NS) {
+        const int ns = min(NS, lf.y - s0);
+        __syncthreads();  // the previous chunk's rows are consumed
+        for (int r = tid; r < 3 * ns; r += NT) {
+            const int sidx = r / 3, ax = r - 3 * sidx;
+            const float* y = src4 + size_t(lf.x + s0 + sidx) * 4;
+            const float t = y[ax] * scale;
+            const float f = ax == 0 ? y[3] : 1.f;
+            float* row = &Tt[sidx][ax][0];
+            float tm1 = 1.f, tm = t;
+            row[0] = f;
+            row[1] = f * t;
+#pragma unroll
+            for (int m = 2; m < P; ++m) {
+                const float tn = fmaf(2.f * t, tm, -tm1);
+                row[m] = f * tn;
+                tm1 = tm;
+                tm = tn;
+            }
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int sidx = 0; sidx < ns; ++sidx) {
+            float xv[TA];
+            if constexpr (TA == 4) {
+                const float4 x4 = *reinterpret_cast<const float4*>(&Tt[sidx][0][4 * a]);
+                xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
+            } else {
+                const float2 x2 = *reinterpret_cast<const float2*>(&Tt[sidx][0][2 * a]);
+                xv[0] = x2.x; xv[1] = x2.y;
+            }
+            const float4 y4 = *reinterpret_cast<const float4*>(&Tt[sidx][1][4 * b]);
+            const float4 z4 = *reinterpret_cast<const float4*>(&Tt[sidx][2][4 * c]);
+            const float yv[4] = {y4.x, y4.y, y4.z, y4.w}, zv[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+            for (int i = 0; i < TA; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float xy = xv[i] * yv[j];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[i][j][k] = fmaf(xy, zv[k], acc[i][j][k]);
+                }
+        }
+    }
+    float* Qb = Q + size_t(lf.z) * (PP * P);
+#pragma unroll
+    for (int i = 0; i < TA; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4*>(Qb + size_t(TA * a + i) * PP + (4 * b + j) * P + 4 * c) =
+                make_float4(acc[i][j][0], acc[i][j][1], acc[i][j][2], acc[i][j][3]);
+}
+
 // ------------------------------------------------------------------ merge / downward
 // Re-expansion of one box's Chebyshev array into another's, one axis at a time (slices of
 // the first axis through shared memory).  mode 0 (merge): contract the child index m against
@@ -653,12 +732,24 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
         const int b = k / PP, M = (k / P) % P, m = k % P;
         St[(b * P + m) * P + M] = Sg[k];
     }
+    // children present per quarter (b0, b1) and per half b0: absent quarters and halves are
+    // skipped (block-uniform)
+    bool quarter[2][2], half[2];
+#pragma unroll
+    for (int b0 = 0; b0 < 2; ++b0) {
+#pragma unroll
+        for (int b1 = 0; b1 < 2; ++b1)
+            quarter[b0][b1] = e[1 + (b0 | (b1 << 1))] >= 0 || e[1 + (b0 | (b1 << 1) | 4)] >= 0;
+        half[b0] = quarter[b0][0] || quarter[b0][1];
+    }
     __syncthreads();
 #pragma unroll 1
     for (int b0 = 0; b0 < 2; ++b0) {
+        if (!half[b0]) continue;
         T* Ub[2] = {buf + size_t(b0) * NP, buf + size_t(b0 + 1) * NP};
 #pragma unroll 1
         for (int b1 = 0; b1 < 2; ++b1) {
+            if (!quarter[b0][b1]) continue;
             // thread (m0 m1) = tid
             T u[P];
 #pragma unroll
@@ -694,10 +785,12 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
 #pragma unroll
             for (int m = 0; m < P; ++m) v[m] = T(0);
 #pragma unroll 1
-            for (int b1 = 0; b1 < 2; ++b1)
+            for (int b1 = 0; b1 < 2; ++b1) {
+                if (!quarter[b0][b1]) continue;
 #pragma unroll
                 for (int m1 = 0; m1 < P; ++m1)
                     tri_axpy<T, P>(v, St + (b1 * P + m1) * P, Ub[b1][i * PP + m1 * P + j], m1, P - 1);
+            }
 #pragma unroll
             for (int M1 = 0; M1 < P; ++M1) Ub[0][i * PP + M1 * P + j] = v[M1];
         }
@@ -709,6 +802,7 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
     for (int m = 0; m < P; ++m) q[m] = T(0);
 #pragma unroll 1
     for (int b0 = 0; b0 < 2; ++b0) {
+        if (!half[b0]) continue;
         const T* Vb = buf + size_t(b0) * NP;
 #pragma unroll
         for (int m0 = 0; m0 < P; ++m0) tri_axpy<T, P>(q, St + (b0 * P + m0) * P, Vb[m0 * PP + tid], m0, P - 1);
@@ -3123,11 +3217,19 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
             kern<<<I->nleafq, 256, smb, s>>>(I->d_leafq, s4, Q, inv_rc);
         };
-        if (D == 3 && pd.p == 16) gemm(k_leaf_moments3d_gemm<T, 16>, leaf_moments3d_gemm_smem<T, 16>());
+        bool tiled = false;
+        if constexpr (sizeof(T) == 4) {
+            const float* s4f = reinterpret_cast<const float*>(s4);
+            float* Qf = reinterpret_cast<float*>(Q);
+            tiled = D == 3 && (pd.p == 16 || pd.p == 24 || pd.p == 32);
+            if (D == 3 && pd.p == 16) k_leaf_moments3d_t<16, 2><<<I->nleafq, 128, 0, s>>>(I->d_leafq, s4f, Qf, inv_rc);
+            else if (D == 3 && pd.p == 24) k_leaf_moments3d_t<24, 4><<<I->nleafq, 216, 0, s>>>(I->d_leafq, s4f, Qf, inv_rc);
+            else if (D == 3 && pd.p == 32) k_leaf_moments3d_t<32, 4><<<I->nleafq, 512, 0, s>>>(I->d_leafq, s4f, Qf, inv_rc);
+        }
+        if (tiled) {
+        } else if (D == 3 && pd.p == 16) gemm(k_leaf_moments3d_gemm<T, 16>, leaf_moments3d_gemm_smem<T, 16>());
         else if (D == 3 && pd.p == 24) gemm(k_leaf_moments3d_gemm<T, 24>, leaf_moments3d_gemm_smem<T, 24>());
-        else if (D == 3 && pd.p == 32 && sizeof(T) == 4) {
-            if constexpr (sizeof(T) == 4) gemm(k_leaf_moments3d_gemm<T, 32>, leaf_moments3d_gemm_smem<T, 32>());
-        } else {
+        else {
             const size_t sm = ts * (32 * D * pd.p + 32);
             k_leaf_moments<T, D><<<I->nleafq, 128, sm, s>>>(I->d_leafq, s4, Q, pd, inv_rc);
         }
