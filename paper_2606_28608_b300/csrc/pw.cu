@@ -596,6 +596,10 @@ struct VecOf<float> { using V = float4; static constexpr int W = 4; };
 template <>
 struct VecOf<double> { using V = double2; static constexpr int W = 2; };
 
+// component jj of a vector (jj compile-time after unrolling)
+__device__ __forceinline__ float vlane(const float4& v, int jj) { return jj == 0 ? v.x : jj == 1 ? v.y : jj == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vlane(const double2& v, int jj) { return jj == 0 ? v.x : v.y; }
+
 // acc[m] += row[m] * x for m in [LO, HI]  (row 16-byte aligned; LO, HI compile-time after
 // unrolling)
 template <typename T, int P>
@@ -734,42 +738,64 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
     }
     // children present per quarter (b0, b1) and per half b0: absent quarters and halves are
     // skipped (block-uniform)
-    bool quarter[2][2], half[2];
+    int qmask = 0;  // bit 2 b0 + b1: quarter (b0, b1) has a child
 #pragma unroll
-    for (int b0 = 0; b0 < 2; ++b0) {
+    for (int b0 = 0; b0 < 2; ++b0)
 #pragma unroll
         for (int b1 = 0; b1 < 2; ++b1)
-            quarter[b0][b1] = e[1 + (b0 | (b1 << 1))] >= 0 || e[1 + (b0 | (b1 << 1) | 4)] >= 0;
-        half[b0] = quarter[b0][0] || quarter[b0][1];
+            if (e[1 + (b0 | (b1 << 1))] >= 0 || e[1 + (b0 | (b1 << 1) | 4)] >= 0) qmask |= 1 << (2 * b0 + b1);
+    auto quarter = [&](int b0, int b1) { return (qmask >> (2 * b0 + b1)) & 1; };
+    auto half = [&](int b0) { return (qmask >> (2 * b0)) & 3; };
+    // the children in processing order pos = 4 b0 + 2 b1 + b2; the row of the next present
+    // child is loaded while the current one is contracted
+    auto child = [&](int pos) { return e[1 + ((pos >> 2) | (((pos >> 1) & 1) << 1) | ((pos & 1) << 2))]; };
+    auto next_present = [&](int pos) {
+        int q = pos + 1;
+        while (q < 8 && child(q) < 0) ++q;
+        return q;
+    };
+    V nx[P / VW];
+    int pnext = next_present(-1);
+    if (pnext < 8) {
+        const V* qrow = reinterpret_cast<const V*>(Q + size_t(child(pnext)) * NP + size_t(tid) * P);
+#pragma unroll
+        for (int k = 0; k < P / VW; ++k) nx[k] = __ldg(qrow + k);
     }
     __syncthreads();
 #pragma unroll 1
     for (int b0 = 0; b0 < 2; ++b0) {
-        if (!half[b0]) continue;
-        T* Ub[2] = {buf + size_t(b0) * NP, buf + size_t(b0 + 1) * NP};
+        if (!half(b0)) continue;
+        // U_{b0 b1} in buffer b0 + b1
 #pragma unroll 1
         for (int b1 = 0; b1 < 2; ++b1) {
-            if (!quarter[b0][b1]) continue;
+            if (!quarter(b0, b1)) continue;
             // thread (m0 m1) = tid
             T u[P];
 #pragma unroll
             for (int m = 0; m < P; ++m) u[m] = T(0);
 #pragma unroll 1
             for (int b2 = 0; b2 < 2; ++b2) {
-                const int c = e[1 + (b0 | (b1 << 1) | (b2 << 2))];
-                if (c < 0) continue;
-                const V* qrow = reinterpret_cast<const V*>(Q + size_t(c) * NP + size_t(tid) * P);
+                const int pos = 4 * b0 + 2 * b1 + b2;
+                if (pos != pnext) continue;  // absent child
+                V cur[P / VW];
+#pragma unroll
+                for (int k = 0; k < P / VW; ++k) cur[k] = nx[k];
+                pnext = next_present(pos);
+                if (pnext < 8) {
+                    const V* qrow = reinterpret_cast<const V*>(Q + size_t(child(pnext)) * NP + size_t(tid) * P);
+#pragma unroll
+                    for (int k = 0; k < P / VW; ++k) nx[k] = __ldg(qrow + k);
+                }
 #pragma unroll
                 for (int k = 0; k < P / VW; ++k) {
-                    const V qv = __ldg(qrow + k);
 #pragma unroll
                     for (int jj = 0; jj < VW; ++jj) {
                         const int m2 = VW * k + jj;
-                        tri_axpy<T, P>(u, St + (b2 * P + m2) * P, reinterpret_cast<const T*>(&qv)[jj], m2, P - 1);
+                        tri_axpy<T, P>(u, St + (b2 * P + m2) * P, vlane(cur[k], jj), m2, P - 1);
                     }
                 }
             }
-            V* ud = reinterpret_cast<V*>(Ub[b1] + size_t(tid) * P);
+            V* ud = reinterpret_cast<V*>((buf + size_t(b0 + b1) * NP) + size_t(tid) * P);
 #pragma unroll
             for (int k = 0; k < P / VW; ++k) {
                 V v;
@@ -786,13 +812,13 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
             for (int m = 0; m < P; ++m) v[m] = T(0);
 #pragma unroll 1
             for (int b1 = 0; b1 < 2; ++b1) {
-                if (!quarter[b0][b1]) continue;
+                if (!quarter(b0, b1)) continue;
 #pragma unroll
                 for (int m1 = 0; m1 < P; ++m1)
-                    tri_axpy<T, P>(v, St + (b1 * P + m1) * P, Ub[b1][i * PP + m1 * P + j], m1, P - 1);
+                    tri_axpy<T, P>(v, St + (b1 * P + m1) * P, (buf + size_t(b0 + b1) * NP)[i * PP + m1 * P + j], m1, P - 1);
             }
 #pragma unroll
-            for (int M1 = 0; M1 < P; ++M1) Ub[0][i * PP + M1 * P + j] = v[M1];
+            for (int M1 = 0; M1 < P; ++M1) (buf + size_t(b0) * NP)[i * PP + M1 * P + j] = v[M1];
         }
         __syncthreads();
     }
@@ -802,7 +828,7 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
     for (int m = 0; m < P; ++m) q[m] = T(0);
 #pragma unroll 1
     for (int b0 = 0; b0 < 2; ++b0) {
-        if (!half[b0]) continue;
+        if (!half(b0)) continue;
         const T* Vb = buf + size_t(b0) * NP;
 #pragma unroll
         for (int m0 = 0; m0 < P; ++m0) tri_axpy<T, P>(q, St + (b0 * P + m0) * P, Vb[m0 * PP + tid], m0, P - 1);
