@@ -600,24 +600,35 @@ struct VecOf<double> { using V = double2; static constexpr int W = 2; };
 __device__ __forceinline__ float vlane(const float4& v, int jj) { return jj == 0 ? v.x : jj == 1 ? v.y : jj == 2 ? v.z : v.w; }
 __device__ __forceinline__ double vlane(const double2& v, int jj) { return jj == 0 ? v.x : v.y; }
 
-// acc[m] += row[m] * x for m in [LO, HI]  (row 16-byte aligned; LO, HI compile-time after
-// unrolling)
+// The shift matrices S_b[M][m] (index (b p + M) p + m) of the register-tiled 3D orders in
+// constant memory.  They depend on p alone; with compile-time indices the re-expansions'
+// multiply-adds take them as constant operands, with no shared-memory loads.
+__constant__ float c_shift_f16[2 * 16 * 16];
+__constant__ float c_shift_f24[2 * 24 * 24];
+__constant__ double c_shift_d16[2 * 16 * 16];
 template <typename T, int P>
-__device__ __forceinline__ void tri_axpy(T (&acc)[P], const T* __restrict__ row, T x, int lo, int hi) {
-    using V = typename VecOf<T>::V;
-    constexpr int VW = VecOf<T>::W;
+__device__ __forceinline__ T shiftc(int i);
+template <>
+__device__ __forceinline__ float shiftc<float, 16>(int i) { return c_shift_f16[i]; }
+template <>
+__device__ __forceinline__ float shiftc<float, 24>(int i) { return c_shift_f24[i]; }
+template <>
+__device__ __forceinline__ double shiftc<double, 16>(int i) { return c_shift_d16[i]; }
+// merge: acc[M] += S_b[M][m] x for M in [m, P)      (b, m compile-time after unrolling)
+template <typename T, int P>
+__device__ __forceinline__ void tri_merge_c(T (&acc)[P], int b, int m, T x) {
 #pragma unroll
-    for (int k = 0; k < P / VW; ++k) {
-        if (VW * k + VW - 1 < lo || VW * k > hi) continue;
-        const V v = reinterpret_cast<const V*>(row)[k];
-        const T* vv = reinterpret_cast<const T*>(&v);
-#pragma unroll
-        for (int j = 0; j < VW; ++j) {
-            const int m = VW * k + j;
-            if (m >= lo && m <= hi) acc[m] = fma(vv[j], x, acc[m]);
-        }
-    }
+    for (int M = 0; M < P; ++M)
+        if (M >= m) acc[M] = fma(shiftc<T, P>((b * P + M) * P + m), x, acc[M]);
 }
+// downward: acc[m] += S_b[M][m] x for m in [0, M]   (b, M compile-time after unrolling)
+template <typename T, int P>
+__device__ __forceinline__ void tri_down_c(T (&acc)[P], int b, int M, T x) {
+#pragma unroll
+    for (int m = 0; m < P; ++m)
+        if (m <= M) acc[m] = fma(shiftc<T, P>((b * P + M) * P + m), x, acc[m]);
+}
+
 
 // downward pass, two blocks per parent (one per first-axis child bit b0):
 //   V[m0][M1 M2]  = sum_{M0 >= m0} S_b0[M0][m0] a_P[M0][M1 M2]      thread (M1 M2)
@@ -628,13 +639,12 @@ __device__ __forceinline__ void tri_axpy(T (&acc)[P], const T* __restrict__ row,
 // no clearing.
 template <typename T, int P>
 __global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list, T* __restrict__ Lc,
-                                                    const T* __restrict__ Sg, const unsigned char* __restrict__ add) {
+                                                    const unsigned char* __restrict__ add) {
     constexpr int PP = P * P, NP = PP * P;
     using V = typename VecOf<T>::V;
     constexpr int VW = VecOf<T>::W;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* Sm = reinterpret_cast<T*>(smraw);  // [2][P][P]  S[b][M][m]
-    T* Vs = Sm + 2 * PP;                  // [P][PP]
+    T* Vs = reinterpret_cast<T*>(smraw);  // [P][PP]
     T* Ws = Vs + NP;                      // [P][PP]
     const int tid = threadIdx.x, b0 = blockIdx.x & 1;
     const int* e = list + size_t(blockIdx.x >> 1) * 9;
@@ -644,20 +654,24 @@ __global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list
 #pragma unroll
         for (int b2 = 0; b2 < 2; ++b2) ch[b1][b2] = e[1 + (b0 | (b1 << 1) | (b2 << 2))];
     if (ch[0][0] < 0 && ch[0][1] < 0 && ch[1][0] < 0 && ch[1][1] < 0) return;  // block-uniform
-    for (int k = tid; k < 2 * PP; k += PP) Sm[k] = Sg[k];
-    __syncthreads();
     {
         const T* aP = Lc + size_t(e[0]) * NP;
         T v[P];
 #pragma unroll
         for (int m = 0; m < P; ++m) v[m] = T(0);
+        if (b0 == 0) {
 #pragma unroll
-        for (int M0 = 0; M0 < P; ++M0) tri_axpy<T, P>(v, Sm + (b0 * P + M0) * P, aP[M0 * PP + tid], 0, M0);
+            for (int M0 = 0; M0 < P; ++M0) tri_down_c<T, P>(v, 0, M0, aP[M0 * PP + tid]);
+        } else {
+#pragma unroll
+            for (int M0 = 0; M0 < P; ++M0) tri_down_c<T, P>(v, 1, M0, aP[M0 * PP + tid]);
+        }
 #pragma unroll
         for (int m0 = 0; m0 < P; ++m0) Vs[m0 * PP + tid] = v[m0];
     }
     __syncthreads();
     const int i = tid / P, j = tid - (tid / P) * P;
+#pragma unroll
     for (int b1 = 0; b1 < 2; ++b1) {
         if (ch[b1][0] < 0 && ch[b1][1] < 0) continue;  // block-uniform
         {
@@ -666,7 +680,7 @@ __global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list
 #pragma unroll
             for (int m = 0; m < P; ++m) w[m] = T(0);
 #pragma unroll
-            for (int M1 = 0; M1 < P; ++M1) tri_axpy<T, P>(w, Sm + (b1 * P + M1) * P, Vs[i * PP + M1 * P + j], 0, M1);
+            for (int M1 = 0; M1 < P; ++M1) tri_down_c<T, P>(w, b1, M1, Vs[i * PP + M1 * P + j]);
 #pragma unroll
             for (int m1 = 0; m1 < P; ++m1) Ws[i * PP + m1 * P + j] = w[m1];
         }
@@ -688,7 +702,7 @@ __global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list
 #pragma unroll
                 for (int m = 0; m < P; ++m) o[m] = T(0);
 #pragma unroll
-                for (int M2 = 0; M2 < P; ++M2) tri_axpy<T, P>(o, Sm + (b2 * P + M2) * P, wr[M2], 0, M2);
+                for (int M2 = 0; M2 < P; ++M2) tri_down_c<T, P>(o, b2, M2, wr[M2]);
                 V* dst = reinterpret_cast<V*>(Lc + size_t(c) * NP + size_t(tid) * P);
                 if (add[c]) {
 #pragma unroll
@@ -722,20 +736,14 @@ __global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list
 // V_{b0} overwrites U_{b0 0} in place (a thread rewrites exactly the (m0, M2) slice it read).
 // b0 = 0 uses buffers (A, B) and leaves V_0 in A; b0 = 1 uses (B, C) and leaves V_1 in B.
 template <typename T, int P>
-__global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ list, T* __restrict__ Q,
-                                                     const T* __restrict__ Sg) {
+__global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ list, T* __restrict__ Q) {
     constexpr int PP = P * P, NP = PP * P;
     using V = typename VecOf<T>::V;
     constexpr int VW = VecOf<T>::W;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* St = reinterpret_cast<T*>(smraw);  // [2][P][P]  St[b][m][M] = S_b[M][m]
-    T* buf = St + 2 * PP;                 // [3][NP]
+    T* buf = reinterpret_cast<T*>(smraw);  // [3][NP]
     const int tid = threadIdx.x, i = tid / P, j = tid - (tid / P) * P;
     const int* e = list + size_t(blockIdx.x) * 9;
-    for (int k = tid; k < 2 * PP; k += PP) {
-        const int b = k / PP, M = (k / P) % P, m = k % P;
-        St[(b * P + m) * P + M] = Sg[k];
-    }
     // children present per quarter (b0, b1) and per half b0: absent quarters and halves are
     // skipped (block-uniform)
     int qmask = 0;  // bit 2 b0 + b1: quarter (b0, b1) has a child
@@ -746,21 +754,6 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
             if (e[1 + (b0 | (b1 << 1))] >= 0 || e[1 + (b0 | (b1 << 1) | 4)] >= 0) qmask |= 1 << (2 * b0 + b1);
     auto quarter = [&](int b0, int b1) { return (qmask >> (2 * b0 + b1)) & 1; };
     auto half = [&](int b0) { return (qmask >> (2 * b0)) & 3; };
-    // the children in processing order pos = 4 b0 + 2 b1 + b2; the row of the next present
-    // child is loaded while the current one is contracted
-    auto child = [&](int pos) { return e[1 + ((pos >> 2) | (((pos >> 1) & 1) << 1) | ((pos & 1) << 2))]; };
-    auto next_present = [&](int pos) {
-        int q = pos + 1;
-        while (q < 8 && child(q) < 0) ++q;
-        return q;
-    };
-    V nx[P / VW];
-    int pnext = next_present(-1);
-    if (pnext < 8) {
-        const V* qrow = reinterpret_cast<const V*>(Q + size_t(child(pnext)) * NP + size_t(tid) * P);
-#pragma unroll
-        for (int k = 0; k < P / VW; ++k) nx[k] = __ldg(qrow + k);
-    }
     __syncthreads();
 #pragma unroll 1
     for (int b0 = 0; b0 < 2; ++b0) {
@@ -773,25 +766,20 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
             T u[P];
 #pragma unroll
             for (int m = 0; m < P; ++m) u[m] = T(0);
-#pragma unroll 1
+#pragma unroll
             for (int b2 = 0; b2 < 2; ++b2) {
-                const int pos = 4 * b0 + 2 * b1 + b2;
-                if (pos != pnext) continue;  // absent child
+                const int c = e[1 + (b0 | (b1 << 1) | (b2 << 2))];
+                if (c < 0) continue;  // absent child
                 V cur[P / VW];
+                const V* qrow = reinterpret_cast<const V*>(Q + size_t(c) * NP + size_t(tid) * P);
 #pragma unroll
-                for (int k = 0; k < P / VW; ++k) cur[k] = nx[k];
-                pnext = next_present(pos);
-                if (pnext < 8) {
-                    const V* qrow = reinterpret_cast<const V*>(Q + size_t(child(pnext)) * NP + size_t(tid) * P);
-#pragma unroll
-                    for (int k = 0; k < P / VW; ++k) nx[k] = __ldg(qrow + k);
-                }
+                for (int k = 0; k < P / VW; ++k) cur[k] = __ldg(qrow + k);
 #pragma unroll
                 for (int k = 0; k < P / VW; ++k) {
 #pragma unroll
                     for (int jj = 0; jj < VW; ++jj) {
                         const int m2 = VW * k + jj;
-                        tri_axpy<T, P>(u, St + (b2 * P + m2) * P, vlane(cur[k], jj), m2, P - 1);
+                        tri_merge_c<T, P>(u, b2, m2, vlane(cur[k], jj));
                     }
                 }
             }
@@ -810,12 +798,12 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
             T v[P];
 #pragma unroll
             for (int m = 0; m < P; ++m) v[m] = T(0);
-#pragma unroll 1
+#pragma unroll
             for (int b1 = 0; b1 < 2; ++b1) {
                 if (!quarter(b0, b1)) continue;
 #pragma unroll
                 for (int m1 = 0; m1 < P; ++m1)
-                    tri_axpy<T, P>(v, St + (b1 * P + m1) * P, (buf + size_t(b0 + b1) * NP)[i * PP + m1 * P + j], m1, P - 1);
+                    tri_merge_c<T, P>(v, b1, m1, (buf + size_t(b0 + b1) * NP)[i * PP + m1 * P + j]);
             }
 #pragma unroll
             for (int M1 = 0; M1 < P; ++M1) (buf + size_t(b0) * NP)[i * PP + M1 * P + j] = v[M1];
@@ -826,12 +814,12 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
     T q[P];
 #pragma unroll
     for (int m = 0; m < P; ++m) q[m] = T(0);
-#pragma unroll 1
+#pragma unroll
     for (int b0 = 0; b0 < 2; ++b0) {
         if (!half(b0)) continue;
         const T* Vb = buf + size_t(b0) * NP;
 #pragma unroll
-        for (int m0 = 0; m0 < P; ++m0) tri_axpy<T, P>(q, St + (b0 * P + m0) * P, Vb[m0 * PP + tid], m0, P - 1);
+        for (int m0 = 0; m0 < P; ++m0) tri_merge_c<T, P>(q, b0, m0, Vb[m0 * PP + tid]);
     }
     T* dst = Q + size_t(e[0]) * NP;
 #pragma unroll
@@ -2821,6 +2809,17 @@ void pw_plan_create(PwPlan* pw, int d, double eps, double c, const KernelTables&
                 double v = (m <= M) ? cheb_coef(f, m).real() : 0.0;
                 I->host_S[(b * p + M) * p + m] = v;
             }
+    // the register-tiled 3D orders read S from constant memory (the same values for every plan
+    // of this order and precision)
+    if (d == 3 && ((mixed && (p == 16 || p == 24)) || (!mixed && p == 16))) {
+        if (mixed) {
+            std::vector<float> sf(I->host_S.begin(), I->host_S.end());
+            if (p == 16) cudaMemcpyToSymbol(c_shift_f16, sf.data(), sf.size() * sizeof(float));
+            else cudaMemcpyToSymbol(c_shift_f24, sf.data(), sf.size() * sizeof(float));
+        } else {
+            cudaMemcpyToSymbol(c_shift_d16, I->host_S.data(), I->host_S.size() * sizeof(double));
+        }
+    }
     I->host_ph.assign(size_t(3) * D.n1 * 2, 0.0);
     for (int dl = 0; dl < 3; ++dl)
         for (int kk = 0; kk < D.n1; ++kk) {
@@ -3294,9 +3293,9 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                 // register accumulators over the triangular shift matrices (three P^3
                 // shared buffers: FP32 up to P = 24, FP64 P = 16)
                 auto mr = [&](auto kern, int P) {
-                    const size_t smb = ts * (2 * P * P + 3 * P * P * P);
+                    const size_t smb = ts * (3 * P * P * P);
                     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
-                    kern<<<e - b, P * P, smb, s>>>(lst, Q, S);
+                    kern<<<e - b, P * P, smb, s>>>(lst, Q);
                 };
                 if (pd.p == 16) mr(k_merge3d_r<T, 16>, 16);
                 else if constexpr (sizeof(T) == 4) mr(k_merge3d_r<T, 24>, 24);
@@ -3432,9 +3431,9 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                 // two blocks per parent, register accumulators over the triangular shift
                 // matrices (two P^3 shared buffers)
                 auto dr = [&](auto kern, int P) {
-                    const size_t smb = ts * (2 * P * P + 2 * P * P * P);
+                    const size_t smb = ts * (2 * P * P * P);
                     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
-                    kern<<<2 * (e - b), P * P, smb, s>>>(lst, L, S, I->d_ladd);
+                    kern<<<2 * (e - b), P * P, smb, s>>>(lst, L, I->d_ladd);
                 };
                 if (pd.p == 16) dr(k_down3d_r<T, 16>, 16);
                 else if constexpr (sizeof(T) == 4) dr(k_down3d_r<T, 24>, 24);
