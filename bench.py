@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -147,6 +148,27 @@ def golden_sample(name):
     return np.asarray(c["idx"]), np.asarray(c["pot"]), np.asarray(c["grad"])
 
 
+def half_ball_counts(c, K):
+    """Slices k0 >= 0, rows (k0, k1 >= 0) and modes (k0, k1, k2 >= 0) of the plane-wave ball
+    |k| <= 3c/pi inside the (K+1)(2K+1)^2 half grid (the outgoing waves' support)."""
+    kb = 3.0 * c / math.pi
+    nk0 = nrows = nhalf = 0
+    for k0 in range(K + 1):
+        rows_k0 = 0
+        for k1 in range(-K, K + 1):
+            m = -1
+            for k2 in range(K + 1):
+                if math.sqrt(k0 * k0 + k1 * k1 + k2 * k2) <= kb:
+                    m = k2
+            nhalf += m + 1
+            if k1 >= 0 and m >= 0:
+                rows_k0 += 1
+        nrows += rows_k0
+        if rows_k0:
+            nk0 = k0 + 1
+    return nk0, nrows, nhalf
+
+
 def stage_flops(info, d, leaf_folded, out_folded):
     """Algorithmic flops of each timed stage, from the plan's work counts and the fixed
     per-unit costs of each kernel's formula (documented with the kernels):
@@ -156,17 +178,18 @@ def stage_flops(info, d, leaf_folded, out_folded):
                   residual series of n_A, n_B terms (2 flops/term) + 16 (2D) / 22 (3D)
       pw_moments  per (out box, source) pair: the p^d moment outer product (2 flops each) and
                   2 d p Chebyshev recurrence flops
-      pw_merge    per merge parent 12 p^3 (2D generic) or 28 p^4 (3D: the eight children summed
-                  axis by axis, 14 p^4 multiply-adds)
+      pw_merge    per merge parent 12 p^3 (2D generic) or 14 p^4 (3D: the eight children over
+                  the triangular shift matrices axis by axis, 7 p^4 multiply-adds)
       pw_out      per box (2D parity form): 2 (K+1) p^2 + 4 (K+1)^2 p; credited to pw_moments
                   where the moments launch computes the outgoing waves itself;
-                  3D parity form: 2 (K+1) p^3 + 4 (K+1)^2 p^2 + 4 (K+1)^2 (2K+1) p
+                  3D over the ball |k| <= 3c/pi: 2 n_k0 p^3 + 4 n_rows p^2 + 4 n_half p (n_half
+                  modes with k2 >= 0, n_rows rows (k0, k1 >= 0), n_k0 slices meeting the ball)
       pw_translate_in per box (2D parity form): ~100 (K+1)^2 + 4 (K+1)^2 p + 2 (K+1) p^2;
-                  3D: 27 phased colleagues over the (K+1)(2K+1)^2 half-space modes (14 flops
-                  each) + the three transposed axis contractions
-      pw_downward per parent 12 p^3 (2D) or 32 p^4 (3D, four blocks of 4 p^4 multiply-adds
-                  per two children), plus the leaf evaluation (4 p^d per target) where the
-                  single-launch pass folds it in
+                  3D: 27 phased colleagues per half-ball mode (14 flops each) + the three
+                  axis contractions (the transpose of pw_out's)
+      pw_downward per parent 12 p^3 (2D) or 14 p^4 (3D, the eight children over the
+                  triangular shift matrices), plus the leaf evaluation (4 p^d per target) where
+                  the single-launch pass folds it in
       pw_leaf_eval per target 2 (p^d + 3 p^{d-1} ... ) ~ 4 p^d (value and three derivatives)
     """
     w, p, K = info["window_w"], info["n_proxy"], info["n_pw"]
@@ -178,8 +201,8 @@ def stage_flops(info, d, leaf_folded, out_folded):
     out["interp"] = n * (4 * w ** d + 2 * d * w * 2 * nW)
     visit, inside = (5, 2 * (12 + 14) + 16) if d == 2 else (7, 2 * (13 + 14) + 22)
     out["nearfield"] = info["near_pairs"] * visit + info["near_pairs_in"] * inside
-    merge_unit = 12 * p ** 3 if d == 2 else 28 * p ** 4
-    down_unit = 12 * p ** 3 if d == 2 else 32 * p ** 4
+    merge_unit = 12 * p ** 3 if d == 2 else 14 * p ** 4
+    down_unit = 12 * p ** 3 if d == 2 else 14 * p ** 4
     out["pw_moments"] = info["pw_moment_sources"] * (2 * p ** d + 2 * d * p)
     out["pw_merge"] = info["pw_merge_parents"] * merge_unit
     if d == 2:
@@ -187,11 +210,10 @@ def stage_flops(info, d, leaf_folded, out_folded):
         out["pw_translate_in"] = info["n_pw_boxes_in"] * (100 * (K + 1) ** 2 + 4 * (K + 1) ** 2 * p
                                                           + 2 * (K + 1) * p ** 2)
     else:
-        out["pw_out"] = info["n_pw_boxes_out"] * (2 * (K + 1) * p ** 3 + 4 * (K + 1) ** 2 * p ** 2
-                                                  + 4 * (K + 1) ** 2 * n1 * p)
-        out["pw_translate_in"] = info["n_pw_boxes_in"] * (27 * 14 * (K + 1) * n1 * n1
-                                                          + 2 * (K + 1) * p ** 3 + 4 * (K + 1) ** 2 * p ** 2
-                                                          + 4 * (K + 1) ** 2 * n1 * p)
+        nk0, nrows, nhalf = half_ball_counts(info["c"], K)
+        transforms = 2 * nk0 * p ** 3 + 4 * nrows * p ** 2 + 4 * nhalf * p
+        out["pw_out"] = info["n_pw_boxes_out"] * transforms
+        out["pw_translate_in"] = info["n_pw_boxes_in"] * (27 * 14 * nhalf + transforms)
     if out_folded:
         out["pw_moments"] += out["pw_out"]
         out["pw_out"] = 0
@@ -205,8 +227,8 @@ def stage_flops(info, d, leaf_folded, out_folded):
 # `ncu` capture of the kernel as it stands (profiles/ holds the summaries); absent where no
 # capture of the current kernel exists
 STAGE_TRAFFIC = {
-    "oblique2d_200k": {"nearfield": 17922560, "pw_moments": 6190336, "pw_downward": 13728768},
-    "triclinic3d_4m": {"nearfield": 2306000000},  # 2.17 GB read + 0.136 GB written (k_near_warp)
+    "oblique2d_200k": {"nearfield": 17920000, "pw_moments": 6190336, "pw_downward": 13728768},
+    "triclinic3d_4m": {"nearfield": 2316000000},  # 2.18 GB read + 0.136 GB written (k_near_warp)
 }
 
 STAGE_KERNELS = {
@@ -215,8 +237,8 @@ STAGE_KERNELS = {
         "pw_out": "k_pw_out", "pw_translate_in": "k_pw_in2d_p",
         "pw_downward": "k_down_persist2d (leaf evaluation folded in)", "pw_leaf_eval": "k_leaf_eval"},
     3: {"spread": "k_spread3d_reg + k_fold", "interp": "k_interp3d_w", "nearfield": "k_near_warp",
-        "pw_moments": "k_leaf_moments3d_gemm", "pw_merge": "k_merge3d_r", "pw_out": "k_pw_out3d_p",
-        "pw_translate_in": "k_pw_in3d_p", "pw_downward": "k_down3d_r",
+        "pw_moments": "k_leaf_moments3d_t", "pw_merge": "k_merge3d_r", "pw_out": "k_pw_out3d_h",
+        "pw_translate_in": "k_pw_in3d_h", "pw_downward": "k_down3d_r",
         "pw_leaf_eval": "k_leaf_eval3d_tc (tcgen05 kind::tf32, split operands)"},
 }
 
