@@ -729,19 +729,22 @@ __global__ void __launch_bounds__(P * P) k_down3d_r(const int* __restrict__ list
     }
 }
 
-// upward merge, one block per parent, three P^3 buffers A, B, C in shared memory:
+// upward merge, one block per parent, two P^3 buffers A, B in shared memory, per half b0:
 //   U_{b0 b1}[m0 m1][M2] = sum_{b2} sum_{m2 <= M2} S_b2[M2][m2] Q_c[m0 m1][m2]   thread (m0 m1)
 //   V_{b0}[m0][M1 M2]    = sum_{b1} sum_{m1 <= M1} S_b1[M1][m1] U_{b0 b1}[m0][m1 M2]   thread (m0 M2)
-//   Q_P[M0][M1 M2]       = sum_{b0} sum_{m0 <= M0} S_b0[M0][m0] V_{b0}[m0][M1 M2]  thread (M1 M2)
-// V_{b0} overwrites U_{b0 0} in place (a thread rewrites exactly the (m0, M2) slice it read).
-// b0 = 0 uses buffers (A, B) and leaves V_0 in A; b0 = 1 uses (B, C) and leaves V_1 in B.
+//   Q_P[M0][M1 M2]      += sum_{m0 <= M0} S_b0[M0][m0] V_{b0}[m0][M1 M2]         thread (M1 M2)
+// U_{b0 b1} sits in buffer b1; V_{b0} overwrites U_{b0 0} in place (a thread rewrites exactly
+// the (m0, M2) slice it read).  The first half present writes the parent's moments, the
+// second adds to them (each thread its own elements), so two buffers suffice and FP32 order
+// 24 runs two blocks per SM.
 template <typename T, int P>
-__global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ list, T* __restrict__ Q) {
+__global__ void __launch_bounds__(P * P, (sizeof(T) == 4 && P == 24) ? 2 : 1)
+    k_merge3d_r(const int* __restrict__ list, T* __restrict__ Q) {
     constexpr int PP = P * P, NP = PP * P;
     using V = typename VecOf<T>::V;
     constexpr int VW = VecOf<T>::W;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* buf = reinterpret_cast<T*>(smraw);  // [3][NP]
+    T* buf = reinterpret_cast<T*>(smraw);  // [2][NP]
     const int tid = threadIdx.x, i = tid / P, j = tid - (tid / P) * P;
     const int* e = list + size_t(blockIdx.x) * 9;
     // children present per quarter (b0, b1) and per half b0: absent quarters and halves are
@@ -754,11 +757,12 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
             if (e[1 + (b0 | (b1 << 1))] >= 0 || e[1 + (b0 | (b1 << 1) | 4)] >= 0) qmask |= 1 << (2 * b0 + b1);
     auto quarter = [&](int b0, int b1) { return (qmask >> (2 * b0 + b1)) & 1; };
     auto half = [&](int b0) { return (qmask >> (2 * b0)) & 3; };
-    __syncthreads();
+    T* dst = Q + size_t(e[0]) * NP;
+    bool first = true;
 #pragma unroll 1
     for (int b0 = 0; b0 < 2; ++b0) {
         if (!half(b0)) continue;
-        // U_{b0 b1} in buffer b0 + b1
+        // U_{b0 b1} in buffer b1
 #pragma unroll 1
         for (int b1 = 0; b1 < 2; ++b1) {
             if (!quarter(b0, b1)) continue;
@@ -783,7 +787,7 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
                     }
                 }
             }
-            V* ud = reinterpret_cast<V*>((buf + size_t(b0 + b1) * NP) + size_t(tid) * P);
+            V* ud = reinterpret_cast<V*>((buf + size_t(b1) * NP) + size_t(tid) * P);
 #pragma unroll
             for (int k = 0; k < P / VW; ++k) {
                 V v;
@@ -803,27 +807,35 @@ __global__ void __launch_bounds__(P * P) k_merge3d_r(const int* __restrict__ lis
                 if (!quarter(b0, b1)) continue;
 #pragma unroll
                 for (int m1 = 0; m1 < P; ++m1)
-                    tri_merge_c<T, P>(v, b1, m1, (buf + size_t(b0 + b1) * NP)[i * PP + m1 * P + j]);
+                    tri_merge_c<T, P>(v, b1, m1, (buf + size_t(b1) * NP)[i * PP + m1 * P + j]);
             }
 #pragma unroll
-            for (int M1 = 0; M1 < P; ++M1) (buf + size_t(b0) * NP)[i * PP + M1 * P + j] = v[M1];
+            for (int M1 = 0; M1 < P; ++M1) buf[i * PP + M1 * P + j] = v[M1];
         }
         __syncthreads();
+        {
+            // thread (M1 M2) = tid
+            T q[P];
+#pragma unroll
+            for (int m = 0; m < P; ++m) q[m] = T(0);
+            if (b0 == 0) {
+#pragma unroll
+                for (int m0 = 0; m0 < P; ++m0) tri_merge_c<T, P>(q, 0, m0, buf[m0 * PP + tid]);
+            } else {
+#pragma unroll
+                for (int m0 = 0; m0 < P; ++m0) tri_merge_c<T, P>(q, 1, m0, buf[m0 * PP + tid]);
+            }
+            if (first) {
+#pragma unroll
+                for (int M0 = 0; M0 < P; ++M0) dst[size_t(M0) * PP + tid] = q[M0];
+            } else {
+#pragma unroll
+                for (int M0 = 0; M0 < P; ++M0) dst[size_t(M0) * PP + tid] += q[M0];
+            }
+        }
+        first = false;
+        __syncthreads();  // the buffers are rewritten by the next half
     }
-    // thread (M1 M2) = tid
-    T q[P];
-#pragma unroll
-    for (int m = 0; m < P; ++m) q[m] = T(0);
-#pragma unroll
-    for (int b0 = 0; b0 < 2; ++b0) {
-        if (!half(b0)) continue;
-        const T* Vb = buf + size_t(b0) * NP;
-#pragma unroll
-        for (int m0 = 0; m0 < P; ++m0) tri_merge_c<T, P>(q, b0, m0, Vb[m0 * PP + tid]);
-    }
-    T* dst = Q + size_t(e[0]) * NP;
-#pragma unroll
-    for (int M0 = 0; M0 < P; ++M0) dst[size_t(M0) * PP + tid] = q[M0];
 }
 
 // 2D: the whole re-expansion of all children in two shared-memory phases per parent.
@@ -3293,7 +3305,7 @@ static int pw_eval_t(PwPlan* pw, cudaStream_t s, int phase) {
                 // register accumulators over the triangular shift matrices (three P^3
                 // shared buffers: FP32 up to P = 24, FP64 P = 16)
                 auto mr = [&](auto kern, int P) {
-                    const size_t smb = ts * (3 * P * P * P);
+                    const size_t smb = ts * (2 * P * P * P);
                     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smb));
                     kern<<<e - b, P * P, smb, s>>>(lst, Q);
                 };
