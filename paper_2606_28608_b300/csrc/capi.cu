@@ -873,7 +873,8 @@ static void near_layout(pdmk_plan plan, const Tree& tree, const DirectLists& dl,
     };
     std::vector<TLeaf>& tl = *tl_out;
     tl.assign(dl.tleaf.size(), TLeaf{});
-    for (size_t k = 0; k < dl.tleaf.size(); ++k) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < int64_t(dl.tleaf.size()); ++k) {
         int b = dl.tleaf[k];
         tl[k].tgt_begin = int(tree.tgt_begin[b]);
         tl[k].tgt_count = int(tree.tgt_end[b] - tree.tgt_begin[b]);
@@ -887,6 +888,7 @@ static void near_layout(pdmk_plan plan, const Tree& tree, const DirectLists& dl,
     std::vector<int>& bsc = *bsc_out;
     bsb.resize(nb);
     bsc.resize(nb);
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < nb; ++b) {
         bsb[b] = int(tree.src_begin[b]);
         bsc[b] = int(tree.src_end[b] - tree.src_begin[b]);
@@ -941,7 +943,7 @@ static void near_layout(pdmk_plan plan, const Tree& tree, const DirectLists& dl,
         for (int e = tl[k].list_begin; e < tl[k].list_begin + tl[k].list_count; ++e) ns += bsc[dl.list[e]];
         key[size_t(k)] = {-ns * int64_t(tl[k].tgt_count), k};
     }
-    std::sort(key.begin(), key.end());
+    sort_pairs_parallel(&key);
     std::vector<TLeaf> tl2(tl.size());
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < int64_t(key.size()); ++k) tl2[size_t(k)] = tl[size_t(key[size_t(k)].second)];

@@ -4,6 +4,7 @@
 #include <chrono>
 #ifdef _OPENMP
 #include <omp.h>
+#include <parallel/algorithm>
 #endif
 
 #include <algorithm>
@@ -1090,8 +1091,22 @@ void box_direct_list(const Tree& t, int b, std::vector<int>* out, std::vector<in
             add_leaves_below(X, code, add_leaves_below);
             continue;
         }
-        // no same-level box here: the region is covered by a coarser leaf
-        int found = t.locate(t.level[b], c);
+        // no same-level box here: the region is covered by a coarser leaf.  With the level
+        // restriction that leaf is one level up, a colleague of b's parent (the colleague at
+        // the parent-level cell of c, a leaf whenever it exists); the root level searches
+        int found = -1;
+        const int pb = t.level[b] > 0 ? t.parent[b] : -1;
+        if (pb >= 0) {
+            int oi = 0, mul = 1;
+            for (int a = 0; a < d; ++a) {
+                const int64_t cc = t.coord[size_t(b) * d + a] + ((o / mul) % 3) - 1;  // unwrapped cell
+                oi += int((cc >> 1) - t.coord[size_t(pb) * d + a] + 1) * mul;
+                mul *= 3;
+            }
+            found = t.colleague[size_t(pb) * nn + oi];
+        } else {
+            found = t.locate(t.level[b], c);
+        }
         if (found >= 0 && !t.is_leaf(found)) found = -1;
         if (found >= 0 && t.src_end[found] > t.src_begin[found]) lst.push_back({found, code});
     }
@@ -1103,6 +1118,14 @@ void box_direct_list(const Tree& t, int b, std::vector<int>* out, std::vector<in
         (*out)[k] = lst[k].first;
         if (shift) (*shift)[k] = lst[k].second;
     }
+}
+
+void sort_pairs_parallel(std::vector<std::pair<int64_t, int64_t>>* v) {
+#ifdef _OPENMP
+    __gnu_parallel::sort(v->begin(), v->end());
+#else
+    std::sort(v->begin(), v->end());
+#endif
 }
 
 void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
@@ -1130,6 +1153,10 @@ void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
 #endif
         const int64_t k0 = nl * tid / nthr, k1 = nl * (tid + 1) / nthr;
         std::vector<int> lst, sh;
+        std::vector<int>& tl = tlist[size_t(tid)];
+        std::vector<int>& ts = tshift[size_t(tid)];
+        tl.reserve(size_t(k1 - k0) * 32);
+        ts.reserve(size_t(k1 - k0) * 32);
         int64_t np = 0;
         for (int64_t k = k0; k < k1; ++k) {
             const int b = dl->tleaf[size_t(k)];
@@ -1138,8 +1165,8 @@ void build_direct_lists(const Tree& t, DirectLists* dl, int64_t* pairs) {
             for (int x : lst) nsrc += t.src_end[x] - t.src_begin[x];
             np += nsrc * (t.tgt_end[b] - t.tgt_begin[b]);
             count[size_t(k) + 1] = int64_t(lst.size());
-            tlist[size_t(tid)].insert(tlist[size_t(tid)].end(), lst.begin(), lst.end());
-            tshift[size_t(tid)].insert(tshift[size_t(tid)].end(), sh.begin(), sh.end());
+            tl.insert(tl.end(), lst.begin(), lst.end());
+            ts.insert(ts.end(), sh.begin(), sh.end());
         }
         tpairs[size_t(tid)] = np;
     }

@@ -5,6 +5,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace pdmk {
@@ -180,6 +181,9 @@ inline void shift_of(int code, int* n) {
     n[1] = (code / 3) % 3 - 1;
     n[2] = code / 9 - 1;
 }
+
+// sort (ascending, lexicographic) on the host's threads: the same order as std::sort
+void sort_pairs_parallel(std::vector<std::pair<int64_t, int64_t>>* v);
 
 // default (kappa, n_s) from the paper's Table 1
 void table1_defaults(int d, double eps, const Geometry* g_or_null, const double* Lcol,

@@ -25,6 +25,9 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -2928,6 +2931,39 @@ bool pw_supported(const PwPlan*) { return true; }
 
 // the 2D orders with compile-time kernels (FP64 at P = 32 would exceed the shared memory
 // the static layouts assume)
+// Parallel stream compaction over [0, n) in index order: count(i) items for index i, emitted
+// by fill(i, first position); returns the total.  Static chunks per thread, their offsets by
+// a prefix sum, so the result equals the sequential loop's.
+template <class Count, class Fill>
+static int64_t compact_parallel(int64_t n, Count count, Fill fill) {
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    std::vector<int64_t> part(size_t(nthr) + 1, 0);
+#pragma omp parallel num_threads(nthr)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        const int64_t i0 = n * tid / nthr, i1 = n * (tid + 1) / nthr;
+        int64_t c = 0;
+        for (int64_t i = i0; i < i1; ++i) c += count(i);
+        part[size_t(tid) + 1] = c;
+#pragma omp barrier
+#pragma omp single
+        for (int k = 0; k < nthr; ++k) part[size_t(k) + 1] += part[size_t(k)];
+        int64_t pos = part[size_t(tid)];
+        for (int64_t i = i0; i < i1; ++i) {
+            const int64_t ci = count(i);
+            if (ci) fill(i, pos);
+            pos += ci;
+        }
+    }
+    return part[size_t(nthr)];
+}
+
 static bool direct2d_orders(const PwDims& pd, bool mixed) {
     return pd.d == 2 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16) || (pd.p == 32 && pd.K == 23 && mixed));
 }
@@ -2946,45 +2982,65 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     if (!pw->active) return PDMK_OK;
     auto has_src = [&](int b) { return t.src_end[b] > t.src_begin[b]; };
     auto has_tgt = [&](int b) { return t.tgt_end[b] > t.tgt_begin[b]; };
+    // the slot and list numberings below are ranks in box order, taken by parallel
+    // compaction (each equals its sequential loop's)
     // q slots: boxes with sources
     std::vector<int> qslot(nb, -1);
-    int nq = 0;
-    for (int b = 0; b < nb; ++b)
-        if (has_src(b)) qslot[b] = nq++;
-    // in-boxes: non-leaf boxes with targets; out slots: colleagues of in-boxes with sources
-    std::vector<int> oslot(nb, -1);
-    int nout = 0;
-    std::vector<int> inl;
+    int nq = int(compact_parallel(
+        nb, [&](int64_t b) { return int64_t(has_src(int(b))); }, [&](int64_t b, int64_t k) { qslot[b] = int(k); }));
+    // local slots: in-boxes (non-leaf boxes with targets) and boxes below the root with targets
     std::vector<int> lslot(nb, -1);
-    int nloc = 0;
-    for (int b = 0; b < nb; ++b) {
-        const bool inbox = !t.is_leaf(b) && has_tgt(b);
-        if (inbox || (t.level[b] >= 1 && has_tgt(b))) lslot[b] = nloc++;
-    }
+    const int nloc = int(compact_parallel(
+        nb, [&](int64_t b) { return int64_t(has_tgt(int(b)) && (!t.is_leaf(int(b)) || t.level[b] >= 1)); },
+        [&](int64_t b, int64_t k) { lslot[b] = int(k); }));
     pw->lslot = lslot;
     pw->local_full.assign(size_t(nb), 0);
     const bool leaves_in_smem = d == 2 && direct2d_orders(I->dims, pw->mixed);
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < nb; ++b)
         pw->local_full[b] = lslot[b] >= 0 && (!t.is_leaf(b) || !leaves_in_smem);
+    // out slots: the colleagues with sources of the in-boxes, in box order
+    auto inbox = [&](int b) { return !t.is_leaf(b) && has_tgt(b); };
+    std::vector<unsigned char> is_out(size_t(nb), 0);
+#pragma omp parallel for schedule(static)
     for (int b = 0; b < nb; ++b) {
-        if (t.is_leaf(b) || !has_tgt(b)) continue;
-        inl.push_back(lslot[b]);
-        inl.push_back(t.level[b]);
+        if (!inbox(b)) continue;
         for (int o = 0; o < ncol; ++o) {
             const int S = t.colleague[size_t(b) * ncol + o];
-            int os = -1;
             if (S >= 0 && has_src(S)) {
-                if (oslot[S] < 0) oslot[S] = nout++;
-                os = oslot[S];
+#pragma omp atomic write
+                is_out[size_t(S)] = 1;
             }
-            inl.push_back(os);
+        }
+    }
+    std::vector<int> oslot(nb, -1);
+    std::vector<int2> outl;
+    const int nout = int(compact_parallel(
+        nb, [&](int64_t b) { return int64_t(is_out[size_t(b)]); }, [&](int64_t b, int64_t k) { oslot[b] = int(k); }));
+    outl.resize(size_t(nout));
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < nb; ++b)
+        if (oslot[b] >= 0) outl[size_t(oslot[b])] = make_int2(qslot[b], oslot[b]);
+    // in-box records: local slot, level, the 27 (9) colleagues' out slots
+    std::vector<int> inl;
+    {
+        std::vector<int> in_rank(nb, -1);
+        const int64_t nin = compact_parallel(
+            nb, [&](int64_t b) { return int64_t(inbox(int(b))); }, [&](int64_t b, int64_t k) { in_rank[b] = int(k); });
+        inl.assign(size_t(nin) * (2 + ncol), -1);
+#pragma omp parallel for schedule(static)
+        for (int b = 0; b < nb; ++b) {
+            if (in_rank[b] < 0) continue;
+            int* e = &inl[size_t(in_rank[b]) * (2 + ncol)];
+            e[0] = lslot[b];
+            e[1] = t.level[b];
+            for (int o = 0; o < ncol; ++o) {
+                const int S = t.colleague[size_t(b) * ncol + o];
+                e[2 + o] = (S >= 0 && has_src(S)) ? oslot[S] : -1;
+            }
         }
     }
     I->nin = int(inl.size()) / (2 + ncol);
-    std::vector<int2> outl;
-    for (int b = 0; b < nb; ++b)
-        if (oslot[b] >= 0) outl.push_back(make_int2(qslot[b], oslot[b]));
-    std::sort(outl.begin(), outl.end(), [](const int2& a, const int2& b) { return a.y < b.y; });
     I->nout = nout;
     pw->moment_sources = 0;
     // 2D compile-time orders: the out boxes' moments straight from their sources, in
@@ -3019,39 +3075,53 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     }
     // leaf moments
     std::vector<int4> leafq;
-    for (int b = 0; b < nb; ++b)
-        if (!I->direct2d && t.is_leaf(b) && has_src(b))
-            leafq.push_back(make_int4(int(t.src_begin[b]), int(t.src_end[b] - t.src_begin[b]), qslot[b], t.level[b]));
+    if (!I->direct2d) {
+        auto is_lq = [&](int64_t b) { return int64_t(t.is_leaf(int(b)) && has_src(int(b))); };
+        leafq.resize(size_t(compact_parallel(nb, is_lq, [](int64_t, int64_t) {})));
+        compact_parallel(nb, is_lq, [&](int64_t b, int64_t k) {
+            leafq[size_t(k)] = make_int4(int(t.src_begin[b]), int(t.src_end[b] - t.src_begin[b]), qslot[b], t.level[b]);
+        });
+    }
     I->nleafq = int(leafq.size());
     if (!I->direct2d)
         for (const int4& l : leafq) pw->moment_sources += l.y;
-    // merges per level (non-leaf boxes with sources), deepest first at eval time
-    std::vector<int> merge;
+    // merges per level (non-leaf boxes with sources), deepest first at eval time;
+    // downward lists per parent level: [parent local slot, child local slots]
+    std::vector<int> merge, down;
     I->merge_start.assign(t.nlevels + 1, 0);
+    I->down_start.assign(t.nlevels + 1, 0);
+    auto is_mp = [&](int64_t b) { return int64_t(!I->direct2d && !t.is_leaf(int(b)) && has_src(int(b))); };
+    auto is_dp = [&](int64_t b) {
+        if (t.is_leaf(int(b)) || lslot[b] < 0) return int64_t(0);
+        for (int c = 0; c < nc; ++c)
+            if (lslot[t.child0[b] + c] >= 0) return int64_t(1);
+        return int64_t(0);
+    };
     for (int l = 0; l < t.nlevels; ++l) {
+        const int b0 = t.level_start[l], nl = t.level_start[l + 1] - b0;
         I->merge_start[l] = int(merge.size()) / (1 + nc);
-        for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
-            if (I->direct2d || t.is_leaf(b) || !has_src(b)) continue;
-            merge.push_back(qslot[b]);
-            for (int c = 0; c < nc; ++c) merge.push_back(qslot[t.child0[b] + c]);
-        }
+        const size_t m0 = merge.size();
+        merge.resize(m0 + size_t(compact_parallel(nl, [&](int64_t i) { return is_mp(b0 + i); }, [](int64_t, int64_t) {})) *
+                              (1 + nc));
+        compact_parallel(nl, [&](int64_t i) { return is_mp(b0 + i); }, [&](int64_t i, int64_t k) {
+            const int b = b0 + int(i);
+            int* e = &merge[m0 + size_t(k) * (1 + nc)];
+            e[0] = qslot[b];
+            for (int c = 0; c < nc; ++c) e[1 + c] = qslot[t.child0[b] + c];
+        });
+        I->down_start[l] = int(down.size()) / (1 + nc);
+        const size_t d0 = down.size();
+        down.resize(d0 + size_t(compact_parallel(nl, [&](int64_t i) { return is_dp(b0 + i); }, [](int64_t, int64_t) {})) *
+                             (1 + nc));
+        compact_parallel(nl, [&](int64_t i) { return is_dp(b0 + i); }, [&](int64_t i, int64_t k) {
+            const int b = b0 + int(i);
+            int* e = &down[d0 + size_t(k) * (1 + nc)];
+            e[0] = lslot[b];
+            for (int c = 0; c < nc; ++c) e[1 + c] = lslot[t.child0[b] + c];
+        });
     }
     I->merge_start[t.nlevels] = int(merge.size()) / (1 + nc);
     pw->merge_parents = I->merge_start[t.nlevels];
-    // downward lists per parent level: [parent local slot, child local slots]
-    std::vector<int> down;
-    I->down_start.assign(t.nlevels + 1, 0);
-    for (int l = 0; l < t.nlevels; ++l) {
-        I->down_start[l] = int(down.size()) / (1 + nc);
-        for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
-            if (t.is_leaf(b) || lslot[b] < 0) continue;
-            bool any = false;
-            for (int c = 0; c < nc; ++c) any |= lslot[t.child0[b] + c] >= 0;
-            if (!any) continue;
-            down.push_back(lslot[b]);
-            for (int c = 0; c < nc; ++c) down.push_back(lslot[t.child0[b] + c]);
-        }
-    }
     I->down_start[t.nlevels] = int(down.size()) / (1 + nc);
     pw->down_parents = I->down_start[t.nlevels];
     // single-launch downward items (top-down order: the down list is by parent level)
@@ -3092,9 +3162,13 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     }
     // leaf evaluation: target leaves below the root level
     std::vector<int4> ev;
-    for (int b = 0; b < nb; ++b)
-        if (t.is_leaf(b) && has_tgt(b) && t.level[b] >= 1)
-            ev.push_back(make_int4(lslot[b], int(t.tgt_begin[b]), int(t.tgt_end[b] - t.tgt_begin[b]), t.level[b]));
+    {
+        auto is_ev = [&](int64_t b) { return int64_t(t.is_leaf(int(b)) && has_tgt(int(b)) && t.level[b] >= 1); };
+        ev.resize(size_t(compact_parallel(nb, is_ev, [](int64_t, int64_t) {})));
+        compact_parallel(nb, is_ev, [&](int64_t b, int64_t k) {
+            ev[size_t(k)] = make_int4(lslot[b], int(t.tgt_begin[b]), int(t.tgt_end[b] - t.tgt_begin[b]), t.level[b]);
+        });
+    }
     I->neval = int(ev.size());
     pw->eval_targets = 0;
     for (const int4& e4 : ev) pw->eval_targets += e4.z;
@@ -3122,6 +3196,7 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         // per local slot: does the downward pass add (in-boxes, written by the incoming
         // waves) or write (leaves)
         std::vector<unsigned char> ladd(size_t(std::max(nloc, 1)), 0);
+#pragma omp parallel for schedule(static)
         for (int b = 0; b < nb; ++b)
             if (lslot[b] >= 0 && !t.is_leaf(b) && has_tgt(b)) ladd[size_t(lslot[b])] = 1;
         if ((r = pw_upload(pw, &I->d_ladd, ladd, stream))) return r;
