@@ -1652,15 +1652,31 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
         plan->setup_ms.push_back(st.phase_ms[k]);
     }
     clk = std::chrono::steady_clock::now();
+    // near-field direct lists and descriptors on the device (the host's lists whenever a
+    // list outgrows the device bound, which the level restriction rules out)
+    NearLists nlst;
     DirectLists dl;
     int64_t pairs = 0;
-    build_direct_lists(tree, &dl, &pairs);
+    const bool split32 = plan->near_nh > 0;
+    bool dev_lists = true;
+    {
+        std::string m2;
+        const int rl = gpu_near_count(&gb, g, split32, &nlst, s, &m2);
+        if (rl == PDMK_ERR_INTERNAL) {
+            dev_lists = false;
+        } else if (rl != PDMK_OK) {
+            plan->msg = m2;
+            return rl;
+        }
+    }
+    if (dev_lists) pairs = nlst.pairs;
+    else build_direct_lists(tree, &dl, &pairs);
     lap("direct_lists");
     plan->n = n;
     plan->nimg = st.n_images;
     plan->ntgt = gb.ntgt;
     plan->nbox = st.nboxes;
-    plan->ntleaf = int(dl.tleaf.size());
+    plan->ntleaf = dev_lists ? nlst.ntleaf : int(dl.tleaf.size());
     // caller-frame box centres, as the host build (in the previous set-up's array)
     std::vector<double> Cu = std::move(plan->h_Cu);
     Cu.resize(size_t(st.nboxes) * d);
@@ -1676,12 +1692,17 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     std::vector<unsigned char> ent_sh;
     std::vector<float> ent_shlo;
     std::vector<int> bsb, bsc;
-    near_layout(plan, tree, dl, Cu, &tl, &ent, &ent_sh, &ent_shlo, &bsb, &bsc, false);
-    plan->nnear = int(tl.size());
-    plan->nlist = int64_t(dl.list.size());
+    if (dev_lists) {
+        plan->nnear = int(nlst.ndesc);
+        plan->nlist = nlst.nlist;
+    } else {
+        near_layout(plan, tree, dl, Cu, &tl, &ent, &ent_sh, &ent_shlo, &bsb, &bsc, false);
+        plan->nnear = int(tl.size());
+        plan->nlist = int64_t(dl.list.size());
+    }
     lap("near_field_descriptors");
     // ---- per-point records (device) ----
-    if ((r = alloc_sources(plan, tl.size(), dl.list.size()))) return r;
+    if ((r = alloc_sources(plan, size_t(plan->nnear), size_t(plan->nlist)))) return r;
     DALLOC(AL, plan->d_src_disp, double, size_t(plan->nimg) * d);
     DALLOC(AL, plan->d_tgt_of_keep, int, plan->ntgt);
     CK(cudaMemsetAsync(plan->d_src4, 0, size_t(plan->nimg) * 4 * ts, s));
@@ -1778,10 +1799,18 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     if ((r = alloc_subs(plan, subs.size()))) return r;
     lap("far_field_layout");
     // ---- per-box uploads ----
-    if ((r = upload(plan, plan->d_tleaf, tl))) return r;
-    if ((r = upload(plan, plan->d_list, dl.list))) return r;
-    if ((r = upload(plan, plan->d_box_src_begin, bsb))) return r;
-    if ((r = upload(plan, plan->d_box_src_count, bsc))) return r;
+    if (dev_lists) {
+        if ((r = gpu_near_fill(&gb, g, split32, &nlst, plan->d_list, plan->d_tleaf, plan->d_box_src_begin,
+                               plan->d_box_src_count, s, &msg)) != PDMK_OK) {
+            plan->msg = msg;
+            return r;
+        }
+    } else {
+        if ((r = upload(plan, plan->d_tleaf, tl))) return r;
+        if ((r = upload(plan, plan->d_list, dl.list))) return r;
+        if ((r = upload(plan, plan->d_box_src_begin, bsb))) return r;
+        if ((r = upload(plan, plan->d_box_src_count, bsc))) return r;
+    }
     if ((r = upload(plan, plan->d_sub, subs))) return r;
     if ((r = upload(plan, plan->d_bin_sub_begin, bin_sub_begin))) return r;
     CK(cudaMemcpyAsync(plan->d_q_user, d_q, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1789,14 +1818,20 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     if (plan->nlist > 0) {
         int *d_tleafb, *d_shift;
         long long* d_lb;
-        SALLOC(d_tleafb, int, dl.tleaf.size());
-        SALLOC(d_lb, long long, dl.list_begin.size());
-        SALLOC(d_shift, int, dl.shift.size());
-        static_assert(sizeof(long long) == sizeof(int64_t), "64-bit list offsets");
-        if ((r = upload(plan, d_tleafb, dl.tleaf))) return r;
-        CK(cudaMemcpyAsync(d_lb, dl.list_begin.data(), dl.list_begin.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                           s));
-        if ((r = upload(plan, d_shift, dl.shift))) return r;
+        if (dev_lists) {
+            d_tleafb = nlst.d_tleaf;
+            d_lb = nlst.d_list_begin;
+            d_shift = nlst.d_shift;
+        } else {
+            SALLOC(d_tleafb, int, dl.tleaf.size());
+            SALLOC(d_lb, long long, dl.list_begin.size());
+            SALLOC(d_shift, int, dl.shift.size());
+            static_assert(sizeof(long long) == sizeof(int64_t), "64-bit list offsets");
+            if ((r = upload(plan, d_tleafb, dl.tleaf))) return r;
+            CK(cudaMemcpyAsync(d_lb, dl.list_begin.data(), dl.list_begin.size() * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+            if ((r = upload(plan, d_shift, dl.shift))) return r;
+        }
         CK(cudaMemsetAsync(plan->d_ent_sh, 0, size_t(plan->nlist) * 4 * ts, s));
         if (mixed) CK(cudaMemsetAsync(plan->d_ent_shlo, 0, size_t(plan->nlist) * 4 * sizeof(float), s));
         EntryArgs ea;
@@ -1804,7 +1839,7 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
         ea.d = d;
         ea.mixed = mixed ? 1 : 0;
         ea.nlist = plan->nlist;
-        ea.ntleaf = int(dl.tleaf.size());
+        ea.ntleaf = plan->ntleaf;
         std::memcpy(ea.Q, g.Q, sizeof(ea.Q));
         for (int code = 0; code < 27; ++code) lattice_shift(g, code, &ea.Ln[code * 3]);
         ea.tleaf = d_tleafb;

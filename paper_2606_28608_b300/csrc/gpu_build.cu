@@ -19,6 +19,7 @@
 // that no multiply-add is contracted: every coordinate, bound and record equals the host's.
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
+#include <cub/device/device_reduce.cuh>
 #include <cub/device/device_select.cuh>
 
 #include <algorithm>
@@ -26,6 +27,7 @@
 #include <cstring>
 
 #include "gpu_build.h"
+#include "kernels_common.cuh"
 #include "pdmk.h"
 
 namespace pdmk {
@@ -687,6 +689,9 @@ int own(GpuBuild* b, X** out, size_t count, std::string* msg) {
 void gpu_build_free(GpuBuild* b) {
     for (void* p : b->allocs) cudaFree(p);
     b->allocs.clear();
+    b->nb = 0;
+    b->d_level = b->d_parent = b->d_child0 = b->d_colleague = nullptr;
+    b->d_coord = b->d_src_b = b->d_src_e = b->d_tgt_b = b->d_tgt_e = nullptr;
     b->d_u = nullptr;
     b->d_orig = nullptr;
     b->d_pos = nullptr;
@@ -875,14 +880,18 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     }
     const int nb = lstart[nlev];
     BoxOut bx;
-    GB_ALLOC(bx.level, int, nb);
-    GB_ALLOC(bx.coord, long long, size_t(nb) * d);
-    GB_ALLOC(bx.parent, int, nb);
-    GB_ALLOC(bx.child0, int, nb);
-    GB_ALLOC(bx.src_b, long long, nb);
-    GB_ALLOC(bx.src_e, long long, nb);
+    // the box arrays the near-field lists read stay on the device (freed by gpu_build_free)
+    {
+        int r0;
+        if ((r0 = own(bo, &bx.level, nb, msg))) return r0;
+        if ((r0 = own(bo, &bx.coord, size_t(nb) * d, msg))) return r0;
+        if ((r0 = own(bo, &bx.parent, nb, msg))) return r0;
+        if ((r0 = own(bo, &bx.child0, nb, msg))) return r0;
+        if ((r0 = own(bo, &bx.src_b, nb, msg))) return r0;
+        if ((r0 = own(bo, &bx.src_e, nb, msg))) return r0;
+        if ((r0 = own(bo, &bx.colleague, size_t(nb) * nn, msg))) return r0;
+    }
     GB_ALLOC(bx.center, double, size_t(nb) * d);
-    GB_ALLOC(bx.colleague, int, size_t(nb) * nn);
     for (int L = 0; L < nlev; ++L) {
         const bool has_down = L < int(nl.size());
         k_boxes<<<blocks_for(nlk[L]), kThreads, 0, s>>>(
@@ -923,8 +932,8 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     k_targets_of<<<blocks_for(nimg), kThreads, 0, s>>>(nimg, d_istgt, d_tpos, bo->d_orig, bo->d_tgt_of,
                                                        bo->d_tgt_orig);
     long long *d_tb, *d_te;
-    GB_ALLOC(d_tb, long long, nb);
-    GB_ALLOC(d_te, long long, nb);
+    if ((r = own(bo, &d_tb, nb, msg))) return r;
+    if ((r = own(bo, &d_te, nb, msg))) return r;
     k_box_tgt<<<blocks_for(nb), kThreads, 0, s>>>(nb, bx.src_b, bx.src_e, d_tpos, d_tb, d_te);
     // the key-sorted and the final order share every leaf's range
     GB_CK(cudaMemcpyAsync(bo->d_leaf, d_leafpos, size_t(nimg) * sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -991,6 +1000,16 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     bo->nimg = nimg;
     bo->ntgt = h_ntgt;
     bo->key_levels = K;
+    bo->nb = nb;
+    bo->d_level = bx.level;
+    bo->d_coord = bx.coord;
+    bo->d_parent = bx.parent;
+    bo->d_child0 = bx.child0;
+    bo->d_src_b = bx.src_b;
+    bo->d_src_e = bx.src_e;
+    bo->d_tgt_b = d_tb;
+    bo->d_tgt_e = d_te;
+    bo->d_colleague = bx.colleague;
     if (st) {
         st->n = n;
         st->n_images = nimg;
@@ -1055,6 +1074,310 @@ int gpu_far_layout(const FarLayoutArgs& a, cudaStream_t s, std::string* msg) {
         if (a.mixed) k_far_targets<float><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
         else k_far_targets<double><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
     }
+    GB_CK(cudaGetLastError());
+    GB_CK(cudaStreamSynchronize(s));  // the scratch is freed on return
+    return PDMK_OK;
+}
+
+
+// ------------------------------------------------------------------ near-field lists
+namespace {
+
+constexpr int kMaxNear = 27 * 8 + 27;  // children of 27 colleagues, or 27 coarser leaves
+
+struct BoxView {
+    int d, nn;
+    const int* level;
+    const long long* coord;
+    const int* parent;
+    const int* child0;
+    const long long* src_b;
+    const long long* src_e;
+    const int* colleague;
+};
+
+// the shift code of the lattice vector that brings the level-L cell c into the root grid
+// (periodic roots; c is wrapped), 13 otherwise (as the host tree's wrap)
+__device__ int wrap_code(const Geo& g, int d, int L, long long* c) {
+    if (!g.periodic) return 13;
+    int code = 0, mul = 1;
+    for (int a = 0; a < d; ++a) {
+        const long long dim = static_cast<long long>(g.nroot[a]) << L;
+        int n = 0;
+        while (c[a] < 0) { c[a] += dim; --n; }
+        while (c[a] >= dim) { c[a] -= dim; ++n; }
+        code += (n + 1) * mul;
+        mul *= 3;
+    }
+    for (int a = d; a < 3; ++a) {
+        code += mul;
+        mul *= 3;
+    }
+    return code;
+}
+
+// the sorted, unique (source leaf, shift code) pairs of target leaf b; -1 when the list
+// outgrows kMaxNear or a colleague's child is refined (neither happens under the level
+// restriction; the host build then serves the inputs)
+__device__ int near_list_of(const BoxView& v, const Geo& g, int b, int2* lst) {
+    const int d = v.d, nn = v.nn, L = v.level[b];
+    int n = 0;
+    for (int o = 0; o < nn; ++o) {
+        long long c[3] = {0, 0, 0};
+        int r = o;
+        for (int a = 0; a < d; ++a) {
+            c[a] = v.coord[size_t(b) * d + a] + (r % 3) - 1;
+            r /= 3;
+        }
+        const int code = wrap_code(g, d, L, c);
+        const int X = v.colleague[size_t(b) * nn + o];
+        if (X >= 0) {
+            if (v.child0[X] < 0) {
+                if (v.src_e[X] > v.src_b[X]) {
+                    if (n >= kMaxNear) return -1;
+                    lst[n++] = make_int2(X, code);
+                }
+            } else {
+                for (int cc = 0; cc < (1 << d); ++cc) {
+                    const int Y = v.child0[X] + cc;
+                    if (v.child0[Y] >= 0) return -1;
+                    if (v.src_e[Y] > v.src_b[Y]) {
+                        if (n >= kMaxNear) return -1;
+                        lst[n++] = make_int2(Y, code);
+                    }
+                }
+            }
+            continue;
+        }
+        // no same-level box: the colleague of b's parent at the parent-level cell
+        if (L == 0) continue;
+        const int pb = v.parent[b];
+        int oi = 0, mul = 1, rr = o;
+        for (int a = 0; a < d; ++a) {
+            const long long cc = v.coord[size_t(b) * d + a] + (rr % 3) - 1;
+            rr /= 3;
+            oi += int((cc >> 1) - v.coord[size_t(pb) * d + a] + 1) * mul;
+            mul *= 3;
+        }
+        const int F = v.colleague[size_t(pb) * nn + oi];
+        if (F >= 0 && v.child0[F] < 0 && v.src_e[F] > v.src_b[F]) {
+            if (n >= kMaxNear) return -1;
+            lst[n++] = make_int2(F, code);
+        }
+    }
+    for (int i = 1; i < n; ++i) {
+        const int2 k = lst[i];
+        int j = i - 1;
+        while (j >= 0 && (lst[j].x > k.x || (lst[j].x == k.x && lst[j].y > k.y))) {
+            lst[j + 1] = lst[j];
+            --j;
+        }
+        lst[j + 1] = k;
+    }
+    int m = 0;
+    for (int i = 0; i < n; ++i)
+        if (m == 0 || lst[i].x != lst[m - 1].x || lst[i].y != lst[m - 1].y) lst[m++] = lst[i];
+    return m;
+}
+
+__global__ void k_tleaf_flags(int nb, const int* __restrict__ child0, const long long* __restrict__ tb,
+                              const long long* __restrict__ te, unsigned char* __restrict__ flag) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
+        flag[b] = child0[b] < 0 && te[b] > tb[b];
+}
+
+__global__ void k_near_count(BoxView v, Geo g, int ntleaf, const int* __restrict__ tleaf,
+                             const long long* __restrict__ tb, const long long* __restrict__ te, int split32,
+                             long long* __restrict__ cnt, long long* __restrict__ nsrc, long long* __restrict__ pairs,
+                             long long* __restrict__ ndesc, int* __restrict__ err) {
+    int2 lst[kMaxNear];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ntleaf; k += gridDim.x * blockDim.x) {
+        const int b = tleaf[k];
+        int m = near_list_of(v, g, b, lst);
+        if (m < 0) {
+            atomicExch(err, 1);
+            m = 0;
+        }
+        long long ns = 0;
+        for (int i = 0; i < m; ++i) ns += v.src_e[lst[i].x] - v.src_b[lst[i].x];
+        const long long nt = te[b] - tb[b];
+        cnt[k] = m;
+        nsrc[k] = ns;
+        pairs[k] = ns * nt;
+        ndesc[k] = split32 ? (nt > 32 ? (nt + 31) / 32 : 1) : 1;
+    }
+}
+
+__global__ void k_near_fill(BoxView v, Geo g, int ntleaf, const int* __restrict__ tleaf,
+                            const long long* __restrict__ tb, const long long* __restrict__ te,
+                            const long long* __restrict__ lbeg, const long long* __restrict__ dbeg,
+                            const long long* __restrict__ nsrc, int split32, int* __restrict__ list,
+                            int* __restrict__ shift, TLeaf* __restrict__ desc, unsigned long long* __restrict__ key) {
+    int2 lst[kMaxNear];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ntleaf; k += gridDim.x * blockDim.x) {
+        const int b = tleaf[k];
+        const int m = max(near_list_of(v, g, b, lst), 0);
+        const long long e0 = lbeg[k];
+        for (int i = 0; i < m; ++i) {
+            list[e0 + i] = lst[i].x;
+            shift[e0 + i] = lst[i].y;
+        }
+        const int nt = int(te[b] - tb[b]);
+        TLeaf base;
+        base.tgt_begin = int(tb[b]);
+        base.tgt_count = nt;
+        base.list_begin = int(e0);
+        base.list_count = m;
+        base.level = v.level[b];
+        base.box = b;
+        base.pad0 = base.pad1 = 0;
+        long long j = dbeg[k];
+        if (split32) {
+            for (int t0 = 0; t0 < max(nt, 1); t0 += 32, ++j) {
+                TLeaf c = base;
+                c.tgt_begin = base.tgt_begin + t0;
+                c.tgt_count = min(32, nt - t0);
+                desc[j] = c;
+                key[j] = ~static_cast<unsigned long long>(nsrc[k] * c.tgt_count);  // decreasing cost
+            }
+        } else {
+            desc[j] = base;
+            key[j] = ~static_cast<unsigned long long>(nsrc[k] * nt);
+        }
+    }
+}
+
+__global__ void k_gather_desc(int64_t n, const int* __restrict__ idx, const TLeaf* __restrict__ in,
+                              TLeaf* __restrict__ out) {
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x)
+        out[j] = in[idx[j]];
+}
+
+__global__ void k_box_src(int nb, const long long* __restrict__ sb, const long long* __restrict__ se,
+                          int* __restrict__ bsb, int* __restrict__ bsc) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        bsb[b] = int(sb[b]);
+        bsc[b] = int(se[b] - sb[b]);
+    }
+}
+
+BoxView box_view(const GpuBuild& b, int d) {
+    BoxView v;
+    v.d = d;
+    v.nn = d == 3 ? 27 : 9;
+    v.level = b.d_level;
+    v.coord = b.d_coord;
+    v.parent = b.d_parent;
+    v.child0 = b.d_child0;
+    v.src_b = b.d_src_b;
+    v.src_e = b.d_src_e;
+    v.colleague = b.d_colleague;
+    return v;
+}
+
+}  // namespace
+
+int gpu_near_count(GpuBuild* b, const Geometry& g, bool split32, NearLists* nl, cudaStream_t s, std::string* msg) {
+    Scratch scr;
+    const int nb = b->nb, d = g.d;
+    const Geo geo = make_geo(g);
+    unsigned char* flag;
+    int *iota, *nsel, *err;
+    GB_ALLOC(flag, unsigned char, nb);
+    GB_ALLOC(iota, int, nb);
+    GB_ALLOC(nsel, int, 1);
+    GB_ALLOC(err, int, 1);
+    int r;
+    if ((r = own(b, &nl->d_tleaf, nb, msg))) return r;
+    k_tleaf_flags<<<blocks_for(nb), kThreads, 0, s>>>(nb, b->d_child0, b->d_tgt_b, b->d_tgt_e, flag);
+    k_iota_int<<<blocks_for(nb), kThreads, 0, s>>>(iota, nb);
+    size_t tb = 0;
+    unsigned char* d_tmp = nullptr;
+    size_t have = 0;
+    auto tmp = [&](size_t need) -> bool {
+        if (need <= have) return true;
+        d_tmp = scr.get<unsigned char>(need);
+        have = d_tmp ? need : 0;
+        return d_tmp != nullptr;
+    };
+    GB_CK(cub::DeviceSelect::Flagged(nullptr, tb, iota, flag, nl->d_tleaf, nsel, nb, s));
+    if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+    GB_CK(cub::DeviceSelect::Flagged(d_tmp, tb, iota, flag, nl->d_tleaf, nsel, nb, s));
+    int ntl = 0;
+    GB_CK(cudaMemcpyAsync(&ntl, nsel, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    GB_CK(cudaStreamSynchronize(s));
+    nl->ntleaf = ntl;
+    long long *cnt, *pairs, *ndesc, *psum;
+    GB_ALLOC(cnt, long long, size_t(ntl) + 1);
+    GB_ALLOC(pairs, long long, std::max(ntl, 1));
+    GB_ALLOC(ndesc, long long, size_t(ntl) + 1);
+    GB_ALLOC(psum, long long, 1);
+    if ((r = own(b, &nl->d_nsrc, std::max(ntl, 1), msg))) return r;
+    if ((r = own(b, &nl->d_list_begin, size_t(ntl) + 1, msg))) return r;
+    if ((r = own(b, &nl->d_desc_begin, size_t(ntl) + 1, msg))) return r;
+    GB_CK(cudaMemsetAsync(cnt + ntl, 0, sizeof(long long), s));
+    GB_CK(cudaMemsetAsync(ndesc + ntl, 0, sizeof(long long), s));
+    GB_CK(cudaMemsetAsync(psum, 0, sizeof(long long), s));
+    if (ntl > 0) {
+        k_near_count<<<blocks_for(ntl), 128, 0, s>>>(box_view(*b, d), geo, ntl, nl->d_tleaf, b->d_tgt_b, b->d_tgt_e,
+                                                      split32 ? 1 : 0, cnt, nl->d_nsrc, pairs, ndesc, err);
+        GB_CK(cudaGetLastError());
+        GB_CK(cub::DeviceReduce::Sum(nullptr, tb, pairs, psum, ntl, s));
+        if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+        GB_CK(cub::DeviceReduce::Sum(d_tmp, tb, pairs, psum, ntl, s));
+    }
+    GB_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, nl->d_list_begin, ntl + 1, s));
+    if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+    GB_CK(cub::DeviceScan::ExclusiveSum(d_tmp, tb, cnt, nl->d_list_begin, ntl + 1, s));
+    GB_CK(cub::DeviceScan::ExclusiveSum(d_tmp, tb, ndesc, nl->d_desc_begin, ntl + 1, s));
+    long long h[3] = {0, 0, 0};
+    int herr = 0;
+    GB_CK(cudaMemcpyAsync(&h[0], nl->d_list_begin + ntl, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(&h[1], nl->d_desc_begin + ntl, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(&h[2], psum, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CK(cudaStreamSynchronize(s));  // the scratch is freed on return
+    if (herr) {
+        if (msg) *msg = "a near-field list outgrew its bound (host lists used)";
+        return PDMK_ERR_INTERNAL;
+    }
+    nl->nlist = h[0];
+    nl->ndesc = h[1];
+    nl->pairs = h[2];
+    if ((r = own(b, &nl->d_shift, std::max<int64_t>(nl->nlist, 1), msg))) return r;
+    return PDMK_OK;
+}
+
+int gpu_near_fill(GpuBuild* b, const Geometry& g, bool split32, NearLists* nl, int* d_list, TLeaf* d_desc,
+                  int* d_bsb, int* d_bsc, cudaStream_t s, std::string* msg) {
+    Scratch scr;
+    const int d = g.d, ntl = nl->ntleaf;
+    const int64_t nd = nl->ndesc;
+    k_box_src<<<blocks_for(b->nb), kThreads, 0, s>>>(b->nb, b->d_src_b, b->d_src_e, d_bsb, d_bsc);
+    if (ntl == 0 || nd == 0) {
+        GB_CK(cudaGetLastError());
+        return PDMK_OK;
+    }
+    TLeaf* dtmp;
+    unsigned long long *key, *key2;
+    int *idx, *idx2;
+    GB_ALLOC(dtmp, TLeaf, nd);
+    GB_ALLOC(key, unsigned long long, nd);
+    GB_ALLOC(key2, unsigned long long, nd);
+    GB_ALLOC(idx, int, nd);
+    GB_ALLOC(idx2, int, nd);
+    k_near_fill<<<blocks_for(ntl), 128, 0, s>>>(box_view(*b, d), make_geo(g), ntl, nl->d_tleaf, b->d_tgt_b, b->d_tgt_e,
+                                                 nl->d_list_begin, nl->d_desc_begin, nl->d_nsrc, split32 ? 1 : 0, d_list,
+                                                 nl->d_shift, dtmp, key);
+    GB_CK(cudaGetLastError());
+    k_iota_int<<<blocks_for(nd), kThreads, 0, s>>>(idx, nd);
+    size_t tb = 0;
+    GB_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, key, key2, idx, idx2, int(nd), 0, 64, s));
+    unsigned char* d_tmp = scr.get<unsigned char>(tb);
+    if (!d_tmp) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
+    GB_CK(cub::DeviceRadixSort::SortPairs(d_tmp, tb, key, key2, idx, idx2, int(nd), 0, 64, s));
+    k_gather_desc<<<blocks_for(nd), kThreads, 0, s>>>(nd, idx2, dtmp, d_desc);
     GB_CK(cudaGetLastError());
     GB_CK(cudaStreamSynchronize(s));  // the scratch is freed on return
     return PDMK_OK;

@@ -29,6 +29,17 @@ struct GpuBuild {
     std::vector<void*> allocs;
     unsigned char* h_stage = nullptr;  // optional page-locked staging buffer of the caller
     size_t stage_cap = 0;              // its bytes (used when at least 1 MiB)
+    // the tree's box arrays on the device, in the host tree's box order (nb boxes)
+    int nb = 0;
+    int* d_level = nullptr;
+    long long* d_coord = nullptr;   // d per box
+    int* d_parent = nullptr;
+    int* d_child0 = nullptr;
+    long long* d_src_b = nullptr;
+    long long* d_src_e = nullptr;
+    long long* d_tgt_b = nullptr;
+    long long* d_tgt_e = nullptr;
+    int* d_colleague = nullptr;     // 3^d per box
 };
 void gpu_build_free(GpuBuild* b);
 
@@ -128,5 +139,32 @@ struct EntryArgs {
     float* ent_shlo;            // out (mixed; zeroed by the caller)
 };
 void gpu_near_entries(const EntryArgs& a, cudaStream_t s);
+
+// ---- near-field lists on the device (after gpu_build_tree, from its box arrays) ----
+// The direct lists and descriptors of the host build (build_direct_lists, the descriptor
+// order of the near-field layout), identically: per target leaf (a leaf with targets, in box
+// order) the sorted, unique (source leaf, shift code) pairs of its 3^d neighbourhood, where a
+// missing same-level neighbour is covered by the colleague of the leaf's parent (one level
+// up, a leaf, by the level restriction); descriptors of at most 32 targets when split32,
+// ordered by decreasing pair count, ties in leaf order.
+struct NearLists {
+    int ntleaf = 0;                       // target leaves
+    int64_t nlist = 0;                    // direct-list entries
+    int64_t ndesc = 0;                    // descriptors
+    int64_t pairs = 0;                    // source-target pairs of the lists
+    int* d_tleaf = nullptr;               // target leaf boxes
+    long long* d_list_begin = nullptr;    // ntleaf + 1
+    int* d_shift = nullptr;               // per entry: shift code
+    long long* d_nsrc = nullptr;          // per target leaf: sources of its list
+    long long* d_desc_begin = nullptr;    // per target leaf: first descriptor (ntleaf + 1)
+};
+// counts (downloaded) and the lists' offsets; 0, or PDMK_ERR_CUDA, or PDMK_ERR_INTERNAL when a
+// list outgrows its bound (the host build serves the inputs then)
+int gpu_near_count(GpuBuild* b, const Geometry& g, bool split32, NearLists* nl, cudaStream_t s, std::string* msg);
+// the entries' source leaves (d_list, nlist), the descriptors (d_desc, ndesc TLeaf records),
+// the per-box source ranges (d_bsb, d_bsc: int, nb)
+struct TLeaf;
+int gpu_near_fill(GpuBuild* b, const Geometry& g, bool split32, NearLists* nl, int* d_list, TLeaf* d_desc,
+                  int* d_bsb, int* d_bsc, cudaStream_t s, std::string* msg);
 
 }  // namespace pdmk

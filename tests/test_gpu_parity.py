@@ -202,3 +202,16 @@ def test_split_parameters_leave_result_unchanged(case):
         assert rel(pot, pref) <= eps
         assert rel(grad, gref) <= 10 * eps
         assert rel(pot, p0) <= 2 * eps
+
+
+def test_mixed_explicit_proxy_order_32():
+    """A mixed 3D plan with the proxy order raised to 32 (the 512-thread tiled leaf moments, the
+    generic merges, plane-wave and leaf kernels) still meets eps against the oracle."""
+    g = dict(CASES["triclinic3d_deep"](), case="triclinic3d_deep")
+    pref, gref = oracle_ref(g)
+    pot, grad, info = run(g, 1e-6, precision="mixed", n_proxy=32)
+    ep, eg = rel(pot, pref), rel(grad, gref)
+    print(f"mixed p=32: E_pot={ep:.2e} E_grad={eg:.2e} depth={info['depth']}")
+    assert info["n_proxy"] == 32 and info["depth"] >= 2
+    assert ep <= 1e-6
+    assert eg <= 2e-6
