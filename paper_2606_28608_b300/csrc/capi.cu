@@ -1711,20 +1711,22 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
         CK(cudaMemsetAsync(plan->d_src_lo, 0, size_t(plan->nimg) * 4 * sizeof(float), s));
         CK(cudaMemsetAsync(plan->d_tgt_lo, 0, size_t(plan->ntgt) * 4 * sizeof(float), s));
     }
-    if ((r = upload(plan, plan->d_box_center, tree.center))) return r;
+    // box centres, caller-frame centres and levels from the device tree (no uploads)
+    CK(cudaMemcpyAsync(plan->d_box_center, gb.d_center, tree.center.size() * sizeof(double), cudaMemcpyDeviceToDevice,
+                       s));
     double *d_Cu, *d_selfw_level;
     int *d_level, *d_tgt_leaf;
     SALLOC(d_Cu, double, Cu.size());
-    SALLOC(d_level, int, tree.level.size());
     SALLOC(d_tgt_leaf, int, plan->ntgt);
+    d_level = gb.d_level;
+    gpu_box_cu(st.nboxes, d, g.Q, gb.d_center, d_Cu, s);
+    CK(cudaGetLastError());
     std::vector<double> selfw_level(size_t(tree.nlevels));
     for (int L = 0; L < tree.nlevels; ++L) {
         const double h = g.rc / double(1LL << L);
         selfw_level[size_t(L)] = (d == 3) ? plan->kt.self_coef / h : plan->kt.self_coef - std::log(h) / (2.0 * kPi);
     }
     SALLOC(d_selfw_level, double, selfw_level.size());
-    if ((r = upload(plan, d_Cu, Cu))) return r;
-    if ((r = upload(plan, d_level, tree.level))) return r;
     if ((r = upload(plan, d_selfw_level, selfw_level))) return r;
     RecordArgs ra;
     std::memset(&ra, 0, sizeof(ra));
@@ -1862,10 +1864,12 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     std::vector<int> none;
     r = pw_set_sources(&plan->pw, tree, ss_unused, none, none, g, s, gb.d_leaf, plan->nimg);
     if (r != PDMK_OK) return r;
+    CK(cudaStreamSynchronize(s));
+    lap("plane_wave_layout");
     r = set_charges_device(plan, false);
     if (r != PDMK_OK) return r;
     CK(cudaStreamSynchronize(s));
-    lap("plane_wave_layout_charges");
+    lap("charges");
     finish_info(plan, st, pairs, n_src, m);
     plan->h_Cu.swap(Cu);
     plan->h_tree = std::move(tree);

@@ -691,6 +691,7 @@ void gpu_build_free(GpuBuild* b) {
     b->allocs.clear();
     b->nb = 0;
     b->d_level = b->d_parent = b->d_child0 = b->d_colleague = nullptr;
+    b->d_center = nullptr;
     b->d_coord = b->d_src_b = b->d_src_e = b->d_tgt_b = b->d_tgt_e = nullptr;
     b->d_u = nullptr;
     b->d_orig = nullptr;
@@ -890,8 +891,8 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
         if ((r0 = own(bo, &bx.src_b, nb, msg))) return r0;
         if ((r0 = own(bo, &bx.src_e, nb, msg))) return r0;
         if ((r0 = own(bo, &bx.colleague, size_t(nb) * nn, msg))) return r0;
+        if ((r0 = own(bo, &bx.center, size_t(nb) * d, msg))) return r0;
     }
-    GB_ALLOC(bx.center, double, size_t(nb) * d);
     for (int L = 0; L < nlev; ++L) {
         const bool has_down = L < int(nl.size());
         k_boxes<<<blocks_for(nlk[L]), kThreads, 0, s>>>(
@@ -957,42 +958,84 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     t->center.resize(size_t(nb) * d);
     t->colleague.resize(size_t(nb) * nn);
     static_assert(sizeof(long long) == sizeof(int64_t), "64-bit box arrays");
-    // through the caller's page-locked staging buffer when it has one (chunked, the copy into
-    // the host arrays in parallel), else straight into the host arrays
-    auto download = [&](void* dst, const void* src, size_t bytes) -> int {
-        if (!bo->h_stage || bo->stage_cap < (size_t(1) << 20)) {
-            if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PDMK_ERR_CUDA;
-            return PDMK_OK;
+    // through the caller's page-locked staging buffer when it has one: its two halves take
+    // alternate chunks, so the copy of one chunk into the host arrays (on the host's threads)
+    // overlaps the transfer of the next; else straight into the host arrays
+    struct Piece {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    };
+    std::vector<Piece> pieces;
+    auto download = [&](void* dst, const void* src, size_t bytes) { pieces.push_back({dst, src, bytes}); };
+    download(t->level.data(), bx.level, size_t(nb) * sizeof(int));
+    download(t->coord.data(), bx.coord, size_t(nb) * d * sizeof(int64_t));
+    download(t->parent.data(), bx.parent, size_t(nb) * sizeof(int));
+    download(t->child0.data(), bx.child0, size_t(nb) * sizeof(int));
+    download(t->src_begin.data(), bx.src_b, size_t(nb) * sizeof(int64_t));
+    download(t->src_end.data(), bx.src_e, size_t(nb) * sizeof(int64_t));
+    download(t->tgt_begin.data(), d_tb, size_t(nb) * sizeof(int64_t));
+    download(t->tgt_end.data(), d_te, size_t(nb) * sizeof(int64_t));
+    download(t->center.data(), bx.center, size_t(nb) * d * sizeof(double));
+    download(t->colleague.data(), bx.colleague, size_t(nb) * nn * sizeof(int));
+    const size_t half = bo->stage_cap / 2;
+    if (!bo->h_stage || half < (size_t(1) << 20)) {
+        for (const Piece& pc : pieces)
+            GB_CK(cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDeviceToHost, s));
+    } else {
+        struct Chunk {
+            unsigned char* dst;
+            const unsigned char* src;
+            size_t len;
+        };
+        std::vector<Chunk> chunks;
+        for (const Piece& pc : pieces)
+            for (size_t off = 0; off < pc.bytes; off += half)
+                chunks.push_back({static_cast<unsigned char*>(pc.dst) + off, static_cast<const unsigned char*>(pc.src) + off,
+                                  std::min(half, pc.bytes - off)});
+        cudaEvent_t ev[2];
+        GB_CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        if (cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventDestroy(ev[0]);
+            if (msg) *msg = "event creation failed (set-up)";
+            return PDMK_ERR_CUDA;
         }
-        for (size_t off = 0; off < bytes; off += bo->stage_cap) {
-            const size_t len = std::min(bo->stage_cap, bytes - off);
-            if (cudaMemcpyAsync(bo->h_stage, static_cast<const unsigned char*>(src) + off, len, cudaMemcpyDeviceToHost,
-                                s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                return PDMK_ERR_CUDA;
+        auto drain = [&](size_t i) {  // chunk i from its half into the host array
+            const unsigned char* from = bo->h_stage + (i & 1) * half;
+            const size_t len = chunks[i].len;
             const int64_t npiece = int64_t((len + (size_t(1) << 20) - 1) >> 20);
 #pragma omp parallel for schedule(static)
             for (int64_t k = 0; k < npiece; ++k) {
                 const size_t o = size_t(k) << 20, l = std::min(size_t(1) << 20, len - o);
-                std::memcpy(static_cast<unsigned char*>(dst) + off + o, bo->h_stage + o, l);
+                std::memcpy(chunks[i].dst + o, from + o, l);
+            }
+        };
+        int rc = PDMK_OK;
+        for (size_t i = 0; i < chunks.size() && rc == PDMK_OK; ++i) {
+            if (cudaMemcpyAsync(bo->h_stage + (i & 1) * half, chunks[i].src, chunks[i].len, cudaMemcpyDeviceToHost,
+                                s) != cudaSuccess ||
+                cudaEventRecord(ev[i & 1], s) != cudaSuccess) {
+                rc = PDMK_ERR_CUDA;
+                break;
+            }
+            if (i > 0) {
+                if (cudaEventSynchronize(ev[(i - 1) & 1]) != cudaSuccess) {
+                    rc = PDMK_ERR_CUDA;
+                    break;
+                }
+                drain(i - 1);
             }
         }
-        return PDMK_OK;
-    };
-    int rd = PDMK_OK;
-    if (!rd) rd = download(t->level.data(), bx.level, size_t(nb) * sizeof(int));
-    if (!rd) rd = download(t->coord.data(), bx.coord, size_t(nb) * d * sizeof(int64_t));
-    if (!rd) rd = download(t->parent.data(), bx.parent, size_t(nb) * sizeof(int));
-    if (!rd) rd = download(t->child0.data(), bx.child0, size_t(nb) * sizeof(int));
-    if (!rd) rd = download(t->src_begin.data(), bx.src_b, size_t(nb) * sizeof(int64_t));
-    if (!rd) rd = download(t->src_end.data(), bx.src_e, size_t(nb) * sizeof(int64_t));
-    if (!rd) rd = download(t->tgt_begin.data(), d_tb, size_t(nb) * sizeof(int64_t));
-    if (!rd) rd = download(t->tgt_end.data(), d_te, size_t(nb) * sizeof(int64_t));
-    if (!rd) rd = download(t->center.data(), bx.center, size_t(nb) * d * sizeof(double));
-    if (!rd) rd = download(t->colleague.data(), bx.colleague, size_t(nb) * nn * sizeof(int));
-    if (rd) {
-        if (msg) *msg = cudaGetErrorString(cudaGetLastError());
-        return PDMK_ERR_CUDA;
+        if (rc == PDMK_OK && !chunks.empty()) {
+            if (cudaEventSynchronize(ev[(chunks.size() - 1) & 1]) != cudaSuccess) rc = PDMK_ERR_CUDA;
+            else drain(chunks.size() - 1);
+        }
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        if (rc != PDMK_OK) {
+            if (msg) *msg = cudaGetErrorString(cudaGetLastError());
+            return rc;
+        }
     }
     GB_CK(cudaStreamSynchronize(s));
     if (lap(5)) return PDMK_ERR_CUDA;
@@ -1010,6 +1053,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     bo->d_tgt_b = d_tb;
     bo->d_tgt_e = d_te;
     bo->d_colleague = bx.colleague;
+    bo->d_center = bx.center;
     if (st) {
         st->n = n;
         st->n_images = nimg;

@@ -40,6 +40,7 @@ struct GpuBuild {
     long long* d_tgt_b = nullptr;
     long long* d_tgt_e = nullptr;
     int* d_colleague = nullptr;     // 3^d per box
+    double* d_center = nullptr;     // d per box (tree frame)
 };
 void gpu_build_free(GpuBuild* b);
 
