@@ -16,6 +16,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "dev_pool.h"
 #include "gpu_build.h"
 #include "host_plan.h"
 #include "k_assemble.cuh"
@@ -90,7 +91,8 @@ struct pdmk_plan_s {
     bool ready = false;
     std::string msg;
     // plan-lifetime device buffers
-    std::vector<void*> plan_allocs, src_allocs;
+    std::vector<std::pair<void*, size_t>> plan_allocs, src_allocs;  // (buffer, bytes)
+    DevicePool pool;  // the previous set-up's buffers, offered to the next (dev_pool.h)
     void* d_coefA = nullptr;
     void* d_coefB = nullptr;
     void* d_coefW = nullptr;
@@ -197,17 +199,15 @@ static void plan_set_msg(pdmk_plan plan, const char* m) {
 }
 
 template <class X>
-static int dalloc(pdmk_plan plan, std::vector<void*>& list, X** out, size_t count) {
+static int dalloc(pdmk_plan plan, std::vector<std::pair<void*, size_t>>& list, X** out, size_t count) {
     *out = nullptr;
     if (count == 0) count = 1;
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(X));
-    if (e != cudaSuccess) {
-        plan_set_msg(plan, cudaGetErrorString(e));
-        cudaGetLastError();
+    void* p = plan->pool.get(count * sizeof(X));
+    if (!p) {
+        plan_set_msg(plan, "device allocation failed");
         return PDMK_ERR_OOM;
     }
-    list.push_back(p);
+    list.push_back({p, count * sizeof(X)});
     plan->device_bytes += int64_t(count * sizeof(X));
     *out = static_cast<X*>(p);
     return PDMK_OK;
@@ -227,8 +227,8 @@ static int upload(pdmk_plan plan, void* dst, const std::vector<X>& v) {
     return PDMK_OK;
 }
 
-static void free_list(std::vector<void*>& l, int64_t* bytes) {
-    for (void* p : l) cudaFree(p);
+static void free_list(std::vector<std::pair<void*, size_t>>& l, int64_t* bytes) {
+    for (auto& a : l) cudaFree(a.first);
     l.clear();
     (void)bytes;
 }
@@ -678,6 +678,7 @@ int pdmk_plan_create(int d, const double* L, double eps, const pdmk_opts* opts, 
     // plane-wave planning (proxy order, plane-wave counts, 1D operators)
     pw_plan_create(&plan->pw, d, eps, plan->c, plan->kt, plan->opts.n_proxy, plan->opts.n_pw, mixed);
     plan->pw.tensor_cores = plan->opts.tensor_cores == 0;
+    plan->pw.pool = &plan->pool;
     plan->pw.wait_test = plan->opts.wait_test;
     // device: coefficient arrays, far weights, grid, spectrum, FFT plans
     const size_t ts = tsize(plan);
@@ -770,6 +771,7 @@ extern "C" void pdmk_plan_destroy(pdmk_plan plan) {
     if (plan->tq_buf) cudaFree(plan->tq_buf);
     if (plan->h_stage) cudaFreeHost(plan->h_stage);
     pw_free(&plan->pw);
+    plan->pool.trim();
     if (plan->have_fft) {
         cufftDestroy(plan->fft_fwd);
         cufftDestroy(plan->fft_inv);
@@ -971,10 +973,13 @@ static void spread_subproblems(pdmk_plan plan, const std::vector<int64_t>& bin_c
 
 // drop the previous set-up's buffers and graph
 static void release_sources(pdmk_plan plan) {
-    cudaStreamSynchronize(plan->ws);
+    // the old arrays are reused, not freed: wait for all work that may still read them (the
+    // implicit synchronisation of cudaFree)
+    cudaDeviceSynchronize();
     drop_graph(plan);
     plan->evals_since_setup = 0;
-    free_list(plan->src_allocs, &plan->device_bytes);
+    for (auto& a : plan->src_allocs) plan->pool.put(a.first, a.second);  // offered to the next set-up
+    plan->src_allocs.clear();
     plan->d_adj = nullptr;
     if (plan->tq_buf) cudaFree(plan->tq_buf);
     plan->tq_buf = nullptr;
@@ -1222,6 +1227,10 @@ static int set_points(pdmk_plan plan, int64_t n_src, const double* y, const doub
 
 static int set_points_host(pdmk_plan plan, int64_t n_src, const double* y, const double* q, int64_t m,
                            const double* x, int where) {
+    struct TrimOnReturn {  // the spares this set-up did not take are freed on every return
+        DevicePool* pool;
+        ~TrimOnReturn() { pool->trim(); }
+    } trim_on_return{&plan->pool};
     const int64_t n = n_src + m;
     const int d = plan->d;
     auto clk = std::chrono::steady_clock::now();
@@ -1558,24 +1567,28 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
         clk = now;
     };
     // scratch of this call (freed on every return, after the stream has drained)
+    // scratch of this call: on every return, after the stream has drained, the spares that
+    // this set-up did not take are freed and the scratch becomes the spares of the next
     struct Scratch {
         cudaStream_t s;
-        std::vector<void*> p;
+        DevicePool* pool;
+        std::vector<std::pair<void*, size_t>> p;
         GpuBuild gb;
         ~Scratch() {
             cudaStreamSynchronize(s);
-            for (void* x : p) cudaFree(x);
             gpu_build_free(&gb);
+            pool->trim();
+            for (auto& x : p) pool->put(x.first, x.second);
         }
-    } scr{s, {}, {}};
+    } scr{s, &plan->pool, {}, {}};
     auto salloc = [&](void** out, size_t bytes) -> int {
-        *out = nullptr;
-        if (cudaMalloc(out, std::max<size_t>(bytes, 1)) != cudaSuccess) {
-            cudaGetLastError();
+        bytes = std::max<size_t>(bytes, 1);
+        *out = plan->pool.get(bytes);
+        if (!*out) {
             plan_set_msg(plan, "device allocation failed (set-up)");
             return PDMK_ERR_OOM;
         }
-        scr.p.push_back(*out);
+        scr.p.push_back({*out, bytes});
         return PDMK_OK;
     };
 #define SALLOC(ptr, type, count)                                                          \
@@ -2017,6 +2030,9 @@ static int autotune_plan(pdmk_plan plan, int64_t n, const double* y, const doubl
         fresh->opts.n_s = plan->opts.n_s;
         if (plan->ws) cudaStreamSynchronize(plan->ws);
         std::swap(*plan, *fresh);
+        // the plane-wave plan points at its own plan's buffer pool
+        plan->pw.pool = &plan->pool;
+        fresh->pw.pool = &fresh->pool;
         pdmk_plan_destroy(fresh);  // the old contents
     }
     plan->n_s = ns;

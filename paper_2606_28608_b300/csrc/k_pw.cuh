@@ -5,6 +5,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dev_pool.h"
+
 #include <cstdint>
 #include <vector>
 
@@ -37,7 +39,8 @@ struct PwPlan {
                                             // after the downward pass (every receiving non-leaf box,
                                             // and the target leaves unless the 2D single-launch pass
                                             // keeps theirs in shared memory)
-    std::vector<void*> allocs;
+    std::vector<std::pair<void*, size_t>> allocs;  // (buffer, bytes)
+    DevicePool* pool = nullptr;  // the plan's: buffers released by pw_free_sources go there
     void* impl = nullptr;
 };
 

@@ -2731,11 +2731,14 @@ template <class X>
 int pw_alloc(PwPlan* pw, X** p, size_t n) {
     if (n == 0) n = 1;
     void* q = nullptr;
-    if (cudaMalloc(&q, n * sizeof(X)) != cudaSuccess) {
+    if (pw->pool) {
+        q = pw->pool->get(n * sizeof(X));
+        if (!q) return PDMK_ERR_OOM;
+    } else if (cudaMalloc(&q, n * sizeof(X)) != cudaSuccess) {
         cudaGetLastError();
         return PDMK_ERR_OOM;
     }
-    pw->allocs.push_back(q);
+    pw->allocs.push_back({q, n * sizeof(X)});
     pw->device_bytes += int64_t(n * sizeof(X));
     *p = static_cast<X*>(q);
     return PDMK_OK;
@@ -3614,7 +3617,10 @@ int pw_eval_points(PwPlan* pw, cudaStream_t s, const int4* d_list, int nlist, co
 void pw_free_sources(PwPlan* pw) {
     pw->lslot.clear();
     pw->local_full.clear();
-    for (void* p : pw->allocs) cudaFree(p);
+    for (auto& a : pw->allocs) {
+        if (pw->pool) pw->pool->put(a.first, a.second);
+        else cudaFree(a.first);
+    }
     pw->allocs.clear();
     pw->device_bytes = 0;
     pw->active = false;
