@@ -1162,6 +1162,7 @@ static int setup_snapshot(pdmk_plan plan, std::vector<std::pair<std::string, std
                         plan->info.near_pairs, plan->info.pw_merge_parents, plan->info.pw_down_parents,
                         plan->info.n_pw_boxes_in};
     host("info", facts, sizeof(facts));
+    pw_layout_snapshot(&plan->pw, out);
     return PDMK_OK;
 }
 
@@ -1875,7 +1876,21 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     plan->pw.d_tgt4 = plan->d_tgt4;
     SortedSources ss_unused;
     std::vector<int> none;
-    r = pw_set_sources(&plan->pw, tree, ss_unused, none, none, g, s, gb.d_leaf, plan->nimg);
+    if (d == 3) {
+        // the plane-wave lists on the device, from the device tree
+        PwTreeDev dt;
+        dt.nb = gb.nb;
+        dt.level = gb.d_level;
+        dt.child0 = gb.d_child0;
+        dt.src_b = gb.d_src_b;
+        dt.src_e = gb.d_src_e;
+        dt.tgt_b = gb.d_tgt_b;
+        dt.tgt_e = gb.d_tgt_e;
+        dt.colleague = gb.d_colleague;
+        r = pw_set_sources_device(&plan->pw, dt, tree.level_start, tree.nlevels, g, s);
+    } else {
+        r = pw_set_sources(&plan->pw, tree, ss_unused, none, none, g, s, gb.d_leaf, plan->nimg);
+    }
     if (r != PDMK_OK) return r;
     CK(cudaStreamSynchronize(s));
     lap("plane_wave_layout");
@@ -2701,6 +2716,7 @@ static int build_target_layout(pdmk_plan plan, int64_t m, const double* hx, Targ
     const size_t ts = tsize(plan);
     const int depth = t.nlevels - 1;
     const double cscale = double(1LL << depth) / g.rc;
+    pw_host_slots(&plan->pw, t);  // after a device layout, the per-box slot tables are made here
     const std::vector<unsigned char>& full = plan->pw.local_full;
     std::vector<double> tu(size_t(m) * d), tsh(size_t(m) * d);
     std::vector<int> leaf(static_cast<size_t>(m)), vb(static_cast<size_t>(m)), ab(static_cast<size_t>(m));

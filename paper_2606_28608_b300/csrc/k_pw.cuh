@@ -8,6 +8,8 @@
 #include "dev_pool.h"
 
 #include <cstdint>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "host_plan.h"
@@ -52,6 +54,25 @@ bool pw_supported(const PwPlan* pw);
 int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& s, const std::vector<int>& leaf_of,
                    const std::vector<int>& tgt_leaf, const Geometry& g, cudaStream_t stream,
                    const int* d_leaf_of, int64_t nimg);
+// The same layout built on the device from the device tree's box arrays (3D plans; the
+// lists equal pw_set_sources', box for box).  The host per-box slot tables (lslot,
+// local_full) are then filled on demand by pw_host_slots.
+struct PwTreeDev {
+    int nb = 0;
+    const int* level = nullptr;
+    const int* child0 = nullptr;
+    const long long* src_b = nullptr;
+    const long long* src_e = nullptr;
+    const long long* tgt_b = nullptr;
+    const long long* tgt_e = nullptr;
+    const int* colleague = nullptr;  // 27 per box
+};
+int pw_set_sources_device(PwPlan* pw, const PwTreeDev& dt, const std::vector<int>& level_start, int nlevels,
+                          const Geometry& g, cudaStream_t stream);
+// the host per-box slot tables of the layout (lslot, local_full), if not filled yet
+void pw_host_slots(PwPlan* pw, const Tree& t);
+// the layout's device lists and counts, as named byte arrays (the set-up comparison)
+void pw_layout_snapshot(PwPlan* pw, std::vector<std::pair<std::string, std::vector<unsigned char>>>* out);
 int pw_set_charges(PwPlan* pw, cudaStream_t stream);
 // phase 0: leaf moments (in 2D compile-time orders: moments and outgoing waves straight
 // from the sources); 1: upward merges; 2: outgoing plane waves; 3: translation + incoming;

@@ -21,6 +21,7 @@
 // Passes: leaf moments -> merge (deepest level first) -> outgoing (all levels at once) ->
 // translate+incoming (all levels at once) -> downward (root first) -> leaf evaluation.
 #include <cuda_runtime.h>
+#include <cub/device/device_scan.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -2971,6 +2972,60 @@ static bool direct2d_orders(const PwDims& pd, bool mixed) {
     return pd.d == 2 && ((pd.p == 16 && pd.K == 9) || (pd.p == 24 && pd.K == 16) || (pd.p == 32 && pd.K == 23 && mixed));
 }
 
+// The part of a set-up both layout builders share: the operator tables, the moment,
+// outgoing-wave and local arrays, the four-way merge parts and the output arrays.
+static int pw_layout_tail(PwPlan* pw, int d, int nlevels, int64_t nq, int64_t nloc, int nout, int64_t ntg,
+                          cudaStream_t stream) {
+    PwImpl* I = impl(pw);
+    const size_t ts = pw->mixed ? 4 : 8;
+    int r;
+    if ((r = pw_upload_typed(pw, &I->d_Co, I->host_Co, stream))) return r;
+    if ((r = pw_upload_typed(pw, &I->d_S, I->host_S, stream))) return r;
+    if ((r = pw_upload_typed(pw, &I->d_ph, I->host_ph, stream))) return r;
+    if ((r = pw_upload_typed(pw, &I->d_f, I->host_f, stream))) return r;
+    unsigned char* p = nullptr;
+    const bool leaf_tc = d == 3 && pw->mixed && pw->tensor_cores && (I->dims.p == 16 || I->dims.p == 24);
+    if (leaf_tc && !pw->h_err) {
+        // the tensor-core leaf evaluation's bounded wait reports through the same flag
+        if (cudaHostAlloc(reinterpret_cast<void**>(&pw->h_err), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void**>(&pw->d_err), pw->h_err, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return PDMK_ERR_CUDA;
+        }
+        *pw->h_err = 0;
+    }
+    if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nq, 1)) * I->dims.np * ts))) return r;
+    I->d_Q = p;
+    const bool fixed3d_sz = d == 3 && ((I->dims.p == 16 && I->dims.K == 9) || (I->dims.p == 24 && I->dims.K == 16));
+    const size_t out_modes = I->half3d ? size_t(I->nhalf) * 2 : size_t(I->dims.npw);  // complex values per box
+    if ((r = pw_alloc(pw, &p, size_t(std::max(nout, 1)) * out_modes * 2 * ts))) return r;
+    I->d_out = p;
+    if (fixed3d_sz && (r = pw_upload(pw, &I->d_row, I->host_row, stream))) return r;
+    if (I->half3d) {
+        if ((r = pw_upload(pw, &I->d_item, I->host_item, stream))) return r;
+        if ((r = pw_upload_typed(pw, &I->d_fh, I->host_fh, stream))) return r;
+        if ((r = pw_upload(pw, &I->d_rowb, I->host_rowb, stream))) return r;
+        if ((r = pw_upload(pw, &I->d_k0rows, I->host_k0rows, stream))) return r;
+    }
+    if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nloc, 1)) * I->dims.np * ts))) return r;
+    I->d_L = p;
+    if (d == 3 && (I->dims.p == 16 || I->dims.p == 24)) {
+        int maxlev = 1;
+        for (int l = 0; l < nlevels; ++l) {
+            const int np_l = I->merge_start[l + 1] - I->merge_start[l];
+            if (np_l < pw->nsm) maxlev = std::max(maxlev, np_l);  // levels the four-way merge takes
+        }
+        if ((r = pw_alloc(pw, &p, size_t(maxlev) * 4 * I->dims.np * ts))) return r;
+        I->d_part3 = p;
+        if ((r = pw_alloc(pw, &I->d_done3, size_t(maxlev)))) return r;
+        if (cudaMemsetAsync(I->d_done3, 0, size_t(maxlev) * sizeof(int), stream) != cudaSuccess) return PDMK_ERR_CUDA;
+    }
+    if ((r = pw_alloc(pw, &pw->d_pot, size_t(std::max<int64_t>(ntg, 1))))) return r;
+    if ((r = pw_alloc(pw, &pw->d_grad, size_t(std::max<int64_t>(ntg, 1)) * d))) return r;
+    return PDMK_OK;
+}
+
+
 int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const std::vector<int>& leaf_of,
                    const std::vector<int>& /*tgt_leaf*/, const Geometry& g, cudaStream_t stream,
                    const int* d_leaf_of, int64_t nimg) {
@@ -3185,10 +3240,6 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
     // device
     const size_t ts = pw->mixed ? 4 : 8;
     int r;
-    if ((r = pw_upload_typed(pw, &I->d_Co, I->host_Co, stream))) return r;
-    if ((r = pw_upload_typed(pw, &I->d_S, I->host_S, stream))) return r;
-    if ((r = pw_upload_typed(pw, &I->d_ph, I->host_ph, stream))) return r;
-    if ((r = pw_upload_typed(pw, &I->d_f, I->host_f, stream))) return r;
     if ((r = pw_upload(pw, &I->d_leafq, leafq, stream))) return r;
     if ((r = pw_upload(pw, &I->d_merge, merge, stream))) return r;
     if ((r = pw_upload(pw, &I->d_outl, outl, stream))) return r;
@@ -3205,16 +3256,6 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         if ((r = pw_upload(pw, &I->d_ladd, ladd, stream))) return r;
     }
     unsigned char* p = nullptr;
-    const bool leaf_tc = d == 3 && pw->mixed && pw->tensor_cores && (I->dims.p == 16 || I->dims.p == 24);
-    if (leaf_tc && !pw->h_err) {
-        // the tensor-core leaf evaluation's bounded wait reports through the same flag
-        if (cudaHostAlloc(reinterpret_cast<void**>(&pw->h_err), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
-            cudaHostGetDevicePointer(reinterpret_cast<void**>(&pw->d_err), pw->h_err, 0) != cudaSuccess) {
-            cudaGetLastError();
-            return PDMK_ERR_CUDA;
-        }
-        *pw->h_err = 0;
-    }
     if (I->direct2d) {
         if (!pw->h_err) {
             if (cudaHostAlloc(reinterpret_cast<void**>(&pw->h_err), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
@@ -3243,35 +3284,261 @@ int pw_set_sources(PwPlan* pw, const Tree& t, const SortedSources& /*s*/, const 
         nq = 0;  // no per-box moments
         I->nq = 0;
     }
-    if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nq, 1)) * I->dims.np * ts))) return r;
-    I->d_Q = p;
-    const bool fixed3d_sz = d == 3 && ((I->dims.p == 16 && I->dims.K == 9) || (I->dims.p == 24 && I->dims.K == 16));
-    const size_t out_modes = I->half3d ? size_t(I->nhalf) * 2 : size_t(I->dims.npw);  // complex values per box
-    if ((r = pw_alloc(pw, &p, size_t(std::max(nout, 1)) * out_modes * 2 * ts))) return r;
-    I->d_out = p;
-    if (fixed3d_sz && (r = pw_upload(pw, &I->d_row, I->host_row, stream))) return r;
-    if (I->half3d) {
-        if ((r = pw_upload(pw, &I->d_item, I->host_item, stream))) return r;
-        if ((r = pw_upload_typed(pw, &I->d_fh, I->host_fh, stream))) return r;
-        if ((r = pw_upload(pw, &I->d_rowb, I->host_rowb, stream))) return r;
-        if ((r = pw_upload(pw, &I->d_k0rows, I->host_k0rows, stream))) return r;
+    return pw_layout_tail(pw, d, t.nlevels, nq, nloc, nout, ntg, stream);
+}
+
+// ------------------------------------------------------------------ layout on the device
+// The lists of pw_set_sources (3D), built from the device tree: per box the flags of each
+// list, exclusive scans for the slots and list positions (ranks in box order, as the host's
+// compactions), then one pass that writes every record.
+namespace {
+
+__global__ void k_pwl_flags(PwTreeDev t, int* __restrict__ fq, int* __restrict__ fl, int* __restrict__ fin,
+                            int* __restrict__ flq, int* __restrict__ fm, int* __restrict__ fev) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nb; b += gridDim.x * blockDim.x) {
+        const bool leaf = t.child0[b] < 0, src = t.src_e[b] > t.src_b[b], tgt = t.tgt_e[b] > t.tgt_b[b];
+        fq[b] = src;
+        fl[b] = tgt && (!leaf || t.level[b] >= 1);
+        fin[b] = !leaf && tgt;
+        flq[b] = leaf && src;
+        fm[b] = !leaf && src;
+        fev[b] = leaf && tgt && t.level[b] >= 1;
     }
-    if ((r = pw_alloc(pw, &p, size_t(std::max<int64_t>(nloc, 1)) * I->dims.np * ts))) return r;
-    I->d_L = p;
-    if (d == 3 && (I->dims.p == 16 || I->dims.p == 24)) {
-        int maxlev = 1;
-        for (int l = 0; l < t.nlevels; ++l) {
-            const int np_l = I->merge_start[l + 1] - I->merge_start[l];
-            if (np_l < pw->nsm) maxlev = std::max(maxlev, np_l);  // levels the four-way merge takes
+}
+
+// the colleagues with sources of the in-boxes send outgoing waves
+__global__ void k_pwl_mark_out(PwTreeDev t, int* __restrict__ fout) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nb; b += gridDim.x * blockDim.x) {
+        if (t.child0[b] < 0 || t.tgt_e[b] <= t.tgt_b[b]) continue;
+        for (int o = 0; o < 27; ++o) {
+            const int S = t.colleague[size_t(b) * 27 + o];
+            if (S >= 0 && t.src_e[S] > t.src_b[S]) fout[S] = 1;  // every writer writes 1
         }
-        if ((r = pw_alloc(pw, &p, size_t(maxlev) * 4 * I->dims.np * ts))) return r;
-        I->d_part3 = p;
-        if ((r = pw_alloc(pw, &I->d_done3, size_t(maxlev)))) return r;
-        if (cudaMemsetAsync(I->d_done3, 0, size_t(maxlev) * sizeof(int), stream) != cudaSuccess) return PDMK_ERR_CUDA;
     }
-    if ((r = pw_alloc(pw, &pw->d_pot, size_t(std::max<int64_t>(ntg, 1))))) return r;
-    if ((r = pw_alloc(pw, &pw->d_grad, size_t(std::max<int64_t>(ntg, 1)) * d))) return r;
-    return PDMK_OK;
+}
+
+// downward parents: non-leaf boxes with a local slot and a child with one
+__global__ void k_pwl_down_flag(PwTreeDev t, const int* __restrict__ fl, int* __restrict__ fd) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nb; b += gridDim.x * blockDim.x) {
+        int f = 0;
+        if (t.child0[b] >= 0 && fl[b])
+            for (int c = 0; c < 8; ++c) f |= fl[t.child0[b] + c];
+        fd[b] = f;
+    }
+}
+
+struct PwlRanks {
+    const int *fq, *qr, *fl, *lr, *fin, *inr, *fout, *outr, *flq, *lqr, *fm, *mr, *fd, *dr, *fev, *evr;
+};
+struct PwlOut {
+    int4* leafq;
+    int* merge;
+    int2* outl;
+    int* inl;
+    int* down;
+    int4* ev;
+    unsigned char* ladd;
+    unsigned long long* sums;  // moment sources, evaluation targets, targets of the root boxes
+};
+
+__global__ void k_pwl_fill(PwTreeDev t, int root_end, PwlRanks k, PwlOut o) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < t.nb; b += gridDim.x * blockDim.x) {
+        const bool leaf = t.child0[b] < 0;
+        const int lslot = k.fl[b] ? k.lr[b] : -1, qslot = k.fq[b] ? k.qr[b] : -1, lev = t.level[b];
+        const long long ns = t.src_e[b] - t.src_b[b], nt = t.tgt_e[b] - t.tgt_b[b];
+        if (k.fin[b]) {
+            int* e = o.inl + size_t(k.inr[b]) * 29;
+            e[0] = lslot;
+            e[1] = lev;
+            for (int c = 0; c < 27; ++c) {
+                const int S = t.colleague[size_t(b) * 27 + c];
+                e[2 + c] = (S >= 0 && k.fq[S]) ? k.outr[S] : -1;
+            }
+        }
+        if (k.fout[b]) o.outl[k.outr[b]] = make_int2(qslot, k.outr[b]);
+        if (k.flq[b]) {
+            o.leafq[k.lqr[b]] = make_int4(int(t.src_b[b]), int(ns), qslot, lev);
+            atomicAdd(&o.sums[0], static_cast<unsigned long long>(ns));
+        }
+        if (k.fm[b]) {
+            int* e = o.merge + size_t(k.mr[b]) * 9;
+            e[0] = qslot;
+            for (int c = 0; c < 8; ++c) {
+                const int ch = t.child0[b] + c;
+                e[1 + c] = k.fq[ch] ? k.qr[ch] : -1;
+            }
+        }
+        if (k.fd[b]) {
+            int* e = o.down + size_t(k.dr[b]) * 9;
+            e[0] = lslot;
+            for (int c = 0; c < 8; ++c) {
+                const int ch = t.child0[b] + c;
+                e[1 + c] = k.fl[ch] ? k.lr[ch] : -1;
+            }
+        }
+        if (k.fev[b]) {
+            o.ev[k.evr[b]] = make_int4(lslot, int(t.tgt_b[b]), int(nt), lev);
+            atomicAdd(&o.sums[1], static_cast<unsigned long long>(nt));
+        }
+        if (lslot >= 0 && !leaf && nt > 0) o.ladd[lslot] = 1;
+        if (b < root_end) atomicAdd(&o.sums[2], static_cast<unsigned long long>(nt));
+    }
+}
+
+// the scan totals and, per level boundary, the merge and downward list positions
+__global__ void k_pwl_counts(int nb, const int* __restrict__ ls, int nls, PwlRanks k, int* __restrict__ out) {
+    const int i = threadIdx.x;
+    if (i == 0) {
+        out[0] = k.qr[nb];
+        out[1] = k.lr[nb];
+        out[2] = k.inr[nb];
+        out[3] = k.outr[nb];
+        out[4] = k.lqr[nb];
+        out[5] = k.mr[nb];
+        out[6] = k.dr[nb];
+        out[7] = k.evr[nb];
+    }
+    for (int j = i; j < nls; j += blockDim.x) {
+        out[8 + j] = k.mr[ls[j]];
+        out[8 + nls + j] = k.dr[ls[j]];
+    }
+}
+
+}  // namespace
+
+int pw_set_sources_device(PwPlan* pw, const PwTreeDev& dt, const std::vector<int>& level_start, int nlevels,
+                          const Geometry& g, cudaStream_t stream) {
+    PwImpl* I = impl(pw);
+    I->rc = g.rc;
+    I->nlevels = nlevels;
+    I->direct2d = false;
+    pw->active = nlevels > 1;
+    pw->lslot.clear();  // filled on demand (pw_host_slots)
+    pw->local_full.clear();
+    if (!pw->active) return PDMK_OK;
+    const int nb = dt.nb;
+    const int nt = 256, nblk = int(std::min<int64_t>((int64_t(nb) + nt - 1) / nt, 1 << 16));
+    // flags and their exclusive scans, nb + 1 entries each (the total at nb)
+    enum { Q, L, IN, OUT, LQ, M, D, EV, NF };
+    int* f[NF];
+    int* rk[NF];
+    int r;
+    for (int k = 0; k < NF; ++k) {
+        if ((r = pw_alloc(pw, &f[k], size_t(nb) + 1))) return r;
+        if ((r = pw_alloc(pw, &rk[k], size_t(nb) + 1))) return r;
+        if (cudaMemsetAsync(f[k], 0, (size_t(nb) + 1) * sizeof(int), stream) != cudaSuccess) return PDMK_ERR_CUDA;
+    }
+    k_pwl_flags<<<nblk, nt, 0, stream>>>(dt, f[Q], f[L], f[IN], f[LQ], f[M], f[EV]);
+    k_pwl_mark_out<<<nblk, nt, 0, stream>>>(dt, f[OUT]);
+    k_pwl_down_flag<<<nblk, nt, 0, stream>>>(dt, f[L], f[D]);
+    size_t tb = 0;
+    if (cub::DeviceScan::ExclusiveSum(nullptr, tb, f[Q], rk[Q], nb + 1, stream) != cudaSuccess) return PDMK_ERR_CUDA;
+    unsigned char* tmp = nullptr;
+    if ((r = pw_alloc(pw, &tmp, tb))) return r;
+    for (int k = 0; k < NF; ++k)
+        if (cub::DeviceScan::ExclusiveSum(tmp, tb, f[k], rk[k], nb + 1, stream) != cudaSuccess) return PDMK_ERR_CUDA;
+    PwlRanks kr{f[Q], rk[Q], f[L], rk[L], f[IN], rk[IN], f[OUT], rk[OUT], f[LQ], rk[LQ], f[M], rk[M], f[D], rk[D],
+                f[EV], rk[EV]};
+    // counts and the per-level list positions
+    const int nls = nlevels + 1;
+    std::vector<int> ls(level_start.begin(), level_start.begin() + nls);
+    int *d_ls, *d_cnt;
+    if ((r = pw_upload(pw, &d_ls, ls, stream))) return r;
+    if ((r = pw_alloc(pw, &d_cnt, size_t(8 + 2 * nls)))) return r;
+    k_pwl_counts<<<1, 128, 0, stream>>>(nb, d_ls, nls, kr, d_cnt);
+    std::vector<int> cnt(size_t(8 + 2 * nls));
+    if (cudaMemcpyAsync(cnt.data(), d_cnt, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return PDMK_ERR_CUDA;
+    const int nq = cnt[0], nloc = cnt[1], nin = cnt[2], nout = cnt[3], nleafq = cnt[4], nmerge = cnt[5], ndown = cnt[6],
+              neval = cnt[7];
+    I->merge_start.assign(cnt.begin() + 8, cnt.begin() + 8 + nls);
+    I->down_start.assign(cnt.begin() + 8 + nls, cnt.begin() + 8 + 2 * nls);
+    // the lists
+    PwlOut o;
+    if ((r = pw_alloc(pw, &I->d_leafq, size_t(std::max(nleafq, 1))))) return r;
+    if ((r = pw_alloc(pw, &I->d_merge, size_t(std::max(nmerge, 1)) * 9))) return r;
+    if ((r = pw_alloc(pw, &I->d_outl, size_t(std::max(nout, 1))))) return r;
+    if ((r = pw_alloc(pw, &I->d_inl, size_t(std::max(nin, 1)) * 29))) return r;
+    if ((r = pw_alloc(pw, &I->d_down, size_t(std::max(ndown, 1)) * 9))) return r;
+    if ((r = pw_alloc(pw, &I->d_eval, size_t(std::max(neval, 1))))) return r;
+    if ((r = pw_alloc(pw, &I->d_ladd, size_t(std::max(nloc, 1))))) return r;
+    unsigned long long* d_sums;
+    if ((r = pw_alloc(pw, &d_sums, 3))) return r;
+    if (cudaMemsetAsync(I->d_ladd, 0, size_t(std::max(nloc, 1)), stream) != cudaSuccess ||
+        cudaMemsetAsync(d_sums, 0, 3 * sizeof(unsigned long long), stream) != cudaSuccess)
+        return PDMK_ERR_CUDA;
+    o.leafq = I->d_leafq;
+    o.merge = I->d_merge;
+    o.outl = I->d_outl;
+    o.inl = I->d_inl;
+    o.down = I->d_down;
+    o.ev = I->d_eval;
+    o.ladd = I->d_ladd;
+    o.sums = d_sums;
+    k_pwl_fill<<<nblk, nt, 0, stream>>>(dt, level_start[1], kr, o);
+    unsigned long long sums[3] = {0, 0, 0};
+    if (cudaMemcpyAsync(sums, d_sums, sizeof(sums), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return PDMK_ERR_CUDA;
+    I->nq = nq;
+    I->nloc = nloc;
+    I->nin = nin;
+    I->nout = nout;
+    I->nleafq = nleafq;
+    I->neval = neval;
+    I->ntgt = int64_t(sums[2]);
+    pw->moment_sources = int64_t(sums[0]);
+    pw->eval_targets = int64_t(sums[1]);
+    pw->merge_parents = nmerge;
+    pw->down_parents = ndown;
+    pw->nout = nout;
+    pw->nin = nin;
+    return pw_layout_tail(pw, 3, nlevels, nq, nloc, nout, I->ntgt, stream);
+}
+
+void pw_host_slots(PwPlan* pw, const Tree& t) {
+    if (!pw->active || !pw->lslot.empty()) return;
+    const int nb = int(t.level.size());
+    auto has_tgt = [&](int b) { return t.tgt_end[b] > t.tgt_begin[b]; };
+    std::vector<int> lslot(nb, -1);
+    compact_parallel(
+        nb, [&](int64_t b) { return int64_t(has_tgt(int(b)) && (!t.is_leaf(int(b)) || t.level[b] >= 1)); },
+        [&](int64_t b, int64_t k) { lslot[b] = int(k); });
+    PwImpl* I = impl(pw);
+    const bool leaves_in_smem = t.d == 2 && direct2d_orders(I->dims, pw->mixed);
+    pw->local_full.assign(size_t(nb), 0);
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < nb; ++b) pw->local_full[b] = lslot[b] >= 0 && (!t.is_leaf(b) || !leaves_in_smem);
+    pw->lslot.swap(lslot);
+}
+
+void pw_layout_snapshot(PwPlan* pw, std::vector<std::pair<std::string, std::vector<unsigned char>>>* out) {
+    PwImpl* I = impl(pw);
+    auto dev = [&](const char* name, const void* p, size_t bytes) {
+        std::vector<unsigned char> v(bytes);
+        if (bytes && p) cudaMemcpy(v.data(), p, bytes, cudaMemcpyDeviceToHost);
+        out->push_back({name, std::move(v)});
+    };
+    int64_t c[12] = {I->nq, I->nloc, I->nin, I->nout, I->nleafq, I->neval, I->ntgt, pw->moment_sources,
+                     pw->eval_targets, pw->merge_parents, pw->down_parents, int64_t(pw->active)};
+    std::vector<unsigned char> cv(sizeof(c));
+    std::memcpy(cv.data(), c, sizeof(c));
+    out->push_back({"pw_counts", cv});
+    if (!pw->active) return;
+    std::vector<unsigned char> st((I->merge_start.size() + I->down_start.size()) * sizeof(int));
+    std::memcpy(st.data(), I->merge_start.data(), I->merge_start.size() * sizeof(int));
+    std::memcpy(st.data() + I->merge_start.size() * sizeof(int), I->down_start.data(),
+                I->down_start.size() * sizeof(int));
+    out->push_back({"pw_starts", st});
+    const int nc = 1 << pw->d;
+    dev("pw_leafq", I->d_leafq, size_t(I->nleafq) * sizeof(int4));
+    dev("pw_merge", I->d_merge, size_t(pw->merge_parents) * (1 + nc) * sizeof(int));
+    dev("pw_outl", I->d_outl, size_t(I->nout) * sizeof(int2));
+    dev("pw_inl", I->d_inl, size_t(I->nin) * (pw->d == 3 ? 29 : 11) * sizeof(int));
+    dev("pw_down", I->d_down, size_t(pw->down_parents) * (1 + nc) * sizeof(int));
+    dev("pw_eval", I->d_eval, size_t(I->neval) * sizeof(int4));
+    dev("pw_ladd", I->d_ladd, size_t(I->nloc));
 }
 
 int pw_set_charges(PwPlan*, cudaStream_t) { return PDMK_OK; }
