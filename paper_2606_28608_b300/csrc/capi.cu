@@ -159,6 +159,11 @@ struct pdmk_plan_s {
     std::vector<int64_t> h_src_orig;           // sorted source -> point index
     std::vector<unsigned char> h_src_is_orig;  // the sorted source is the point itself, not an image
     std::vector<double> h_Cu;                  // caller-frame centre of every box (d per box)
+    // after a 3D device set-up the per-box arrays of h_tree (and h_Cu) are read back from the
+    // device tree only when a host path needs them (host_tree false until then)
+    bool host_tree = true;
+    GpuBuild tree_dev;                                      // its device arrays (pointers)
+    std::vector<std::pair<void*, size_t>> tree_keep;        // the same, owned by the plan
     std::vector<double> h_y;                   // the caller's positions (n x d)
     std::vector<double> h_src_disp;            // per sorted source: caller-frame lattice vector from
                                                // its point's given position to this copy (d each)
@@ -768,6 +773,7 @@ extern "C" void pdmk_plan_destroy(pdmk_plan plan) {
     drop_graph(plan);
     free_list(plan->src_allocs, &plan->device_bytes);
     free_list(plan->plan_allocs, &plan->device_bytes);
+    free_list(plan->tree_keep, &plan->device_bytes);
     if (plan->tq_buf) cudaFree(plan->tq_buf);
     if (plan->h_stage) cudaFreeHost(plan->h_stage);
     pw_free(&plan->pw);
@@ -980,6 +986,10 @@ static void release_sources(pdmk_plan plan) {
     plan->evals_since_setup = 0;
     for (auto& a : plan->src_allocs) plan->pool.put(a.first, a.second);  // offered to the next set-up
     plan->src_allocs.clear();
+    for (auto& a : plan->tree_keep) plan->pool.put(a.first, a.second);
+    plan->tree_keep.clear();
+    plan->tree_dev = GpuBuild();
+    plan->host_tree = true;
     plan->d_adj = nullptr;
     if (plan->tq_buf) cudaFree(plan->tq_buf);
     plan->tq_buf = nullptr;
@@ -1067,6 +1077,27 @@ static void finish_info(pdmk_plan plan, const BuildStats& st, int64_t pairs, int
 
 // the host copies of a device set-up (used by evaluations at new targets and Bloch sums)
 static int ensure_host_copies(pdmk_plan plan) {
+    if (!plan->host_tree) {
+        CK(cudaStreamSynchronize(plan->ws));
+        std::string msg;
+        const int r = gpu_tree_download(plan->tree_dev, &plan->h_tree, plan->ws, &msg);
+        if (r != PDMK_OK) {
+            plan->msg = msg;
+            return r;
+        }
+        const Tree& t = plan->h_tree;
+        const int d = plan->d;
+        const int nb = int(t.level.size());
+        plan->h_Cu.resize(size_t(nb) * d);
+#pragma omp parallel for schedule(static)
+        for (int b = 0; b < nb; ++b)
+            for (int i = 0; i < d; ++i) {
+                double sum = 0;
+                for (int k = 0; k < d; ++k) sum += plan->g.Q[k * d + i] * t.center[size_t(b) * d + k];
+                plan->h_Cu[size_t(b) * d + i] = sum;
+            }
+        plan->host_tree = true;
+    }
     if (plan->host_copies) return PDMK_OK;
     const int d = plan->d;
     CK(cudaStreamSynchronize(plan->ws));
@@ -1139,6 +1170,7 @@ static int setup_snapshot(pdmk_plan plan, std::vector<std::pair<std::string, std
     if ((r = dev("t_g0", plan->d_t_g0, size_t(plan->ntgt) * 16))) return r;
     if ((r = dev("t_dq", plan->d_t_dq, size_t(plan->ntgt) * 4 * ts))) return r;
     if ((r = dev("q_user", plan->d_q_user, size_t(plan->n) * 8))) return r;
+    if ((r = ensure_host_copies(plan))) return r;
     const Tree& t = plan->h_tree;
     host("tree.level_start", t.level_start.data(), t.level_start.size() * 4);
     host("tree.level", t.level.data(), t.level.size() * 4);
@@ -1655,6 +1687,8 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     BuildStats st;
     const int maxd = pw_supported(&plan->pw) ? plan->max_depth : 0;
     std::string msg;
+    // 3D: the host tree's per-box arrays are read back only when a host path asks for them
+    gb.download_tree = d != 3;
     int r = gpu_build_tree(g, n, plan->n_s, maxd, s, &gb, &tree, &st, &msg);
     if (r == kGpuBuildUnsupported) return r;
     if (r != PDMK_OK) {
@@ -1683,24 +1717,39 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
             return rl;
         }
     }
-    if (dev_lists) pairs = nlst.pairs;
-    else build_direct_lists(tree, &dl, &pairs);
+    bool have_tree = gb.download_tree;
+    if (dev_lists) {
+        pairs = nlst.pairs;
+    } else {
+        if (!have_tree) {
+            if ((r = gpu_tree_download(gb, &tree, s, &msg)) != PDMK_OK) {
+                plan->msg = msg;
+                return r;
+            }
+            have_tree = true;
+        }
+        build_direct_lists(tree, &dl, &pairs);
+    }
     lap("direct_lists");
     plan->n = n;
     plan->nimg = st.n_images;
     plan->ntgt = gb.ntgt;
     plan->nbox = st.nboxes;
     plan->ntleaf = dev_lists ? nlst.ntleaf : int(dl.tleaf.size());
-    // caller-frame box centres, as the host build (in the previous set-up's array)
+    // caller-frame box centres on the host, as the host build (in the previous set-up's
+    // array), when the host tree is here; else made on demand (ensure_host_copies)
     std::vector<double> Cu = std::move(plan->h_Cu);
-    Cu.resize(size_t(st.nboxes) * d);
+    Cu.clear();
+    if (have_tree) {
+        Cu.resize(size_t(st.nboxes) * d);
 #pragma omp parallel for schedule(static)
-    for (int b = 0; b < st.nboxes; ++b)
-        for (int i = 0; i < d; ++i) {
-            double sum = 0;
-            for (int k = 0; k < d; ++k) sum += g.Q[k * d + i] * tree.center[size_t(b) * d + k];
-            Cu[size_t(b) * d + i] = sum;
-        }
+        for (int b = 0; b < st.nboxes; ++b)
+            for (int i = 0; i < d; ++i) {
+                double sum = 0;
+                for (int k = 0; k < d; ++k) sum += g.Q[k * d + i] * tree.center[size_t(b) * d + k];
+                Cu[size_t(b) * d + i] = sum;
+            }
+    }
     std::vector<TLeaf> tl;
     std::vector<int2> ent;
     std::vector<unsigned char> ent_sh;
@@ -1726,11 +1775,11 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
         CK(cudaMemsetAsync(plan->d_tgt_lo, 0, size_t(plan->ntgt) * 4 * sizeof(float), s));
     }
     // box centres, caller-frame centres and levels from the device tree (no uploads)
-    CK(cudaMemcpyAsync(plan->d_box_center, gb.d_center, tree.center.size() * sizeof(double), cudaMemcpyDeviceToDevice,
-                       s));
+    CK(cudaMemcpyAsync(plan->d_box_center, gb.d_center, size_t(st.nboxes) * d * sizeof(double),
+                       cudaMemcpyDeviceToDevice, s));
     double *d_Cu, *d_selfw_level;
     int *d_level, *d_tgt_leaf;
-    SALLOC(d_Cu, double, Cu.size());
+    SALLOC(d_Cu, double, size_t(st.nboxes) * d);
     SALLOC(d_tgt_leaf, int, plan->ntgt);
     d_level = gb.d_level;
     gpu_box_cu(st.nboxes, d, g.Q, gb.d_center, d_Cu, s);
@@ -1901,6 +1950,24 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     finish_info(plan, st, pairs, n_src, m);
     plan->h_Cu.swap(Cu);
     plan->h_tree = std::move(tree);
+    plan->host_tree = have_tree;
+    if (!have_tree) {
+        // the plan keeps the device tree's per-box arrays for a later read-back
+        const int nb = gb.nb, nn = d == 3 ? 27 : 9;
+        const std::pair<void*, size_t> keep[10] = {
+            {gb.d_level, size_t(nb) * 4},      {gb.d_coord, size_t(nb) * d * 8}, {gb.d_parent, size_t(nb) * 4},
+            {gb.d_child0, size_t(nb) * 4},     {gb.d_src_b, size_t(nb) * 8},     {gb.d_src_e, size_t(nb) * 8},
+            {gb.d_tgt_b, size_t(nb) * 8},      {gb.d_tgt_e, size_t(nb) * 8},     {gb.d_center, size_t(nb) * d * 8},
+            {gb.d_colleague, size_t(nb) * nn * 4}};
+        for (const auto& k : keep) {
+            auto it = std::find(gb.allocs.begin(), gb.allocs.end(), k.first);
+            if (it == gb.allocs.end()) return PDMK_ERR_INTERNAL;
+            gb.allocs.erase(it);
+            plan->tree_keep.push_back(k);
+        }
+        plan->tree_dev = gb;
+        plan->tree_dev.allocs.clear();
+    }
     plan->h_u.clear();
     plan->h_y.clear();
     plan->h_src_disp.clear();

@@ -947,6 +947,57 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     t->periodic = g.periodic_root;
     t->nlevels = nlev;
     t->level_start = lstart;
+    bo->nb = nb;
+    bo->d_level = bx.level;
+    bo->d_coord = bx.coord;
+    bo->d_parent = bx.parent;
+    bo->d_child0 = bx.child0;
+    bo->d_src_b = bx.src_b;
+    bo->d_src_e = bx.src_e;
+    bo->d_tgt_b = d_tb;
+    bo->d_tgt_e = d_te;
+    bo->d_colleague = bx.colleague;
+    bo->d_center = bx.center;
+    if (bo->download_tree) {
+        GB_CK(cudaStreamSynchronize(s));
+        if ((r = gpu_tree_download(*bo, t, s, msg))) return r;
+    }
+    GB_CK(cudaStreamSynchronize(s));
+    if (lap(5)) return PDMK_ERR_CUDA;
+    bo->n = n;
+    bo->nimg = nimg;
+    bo->ntgt = h_ntgt;
+    bo->key_levels = K;
+    if (st) {
+        st->n = n;
+        st->n_images = nimg;
+        st->nboxes = nb;
+        // every non-leaf box has 2^d children, and every box below the root is a child
+        st->nleaves = nb - (nb - lstart[1]) / (1 << d);
+        st->depth = nlev - 1;
+    }
+    return PDMK_OK;
+}
+
+// the per-box arrays of the device tree into the host tree t (resized): through the page-locked
+// staging buffer when it has one, its two halves taking alternate chunks so that the copy of
+// one chunk into the host arrays (on the host's threads) overlaps the transfer of the next;
+// else straight into the host arrays
+int gpu_tree_download(const GpuBuild& b, Tree* t, cudaStream_t s, std::string* msg) {
+    const int nb = b.nb, d = t->d, nn = d == 3 ? 27 : 9;
+    const GpuBuild* bo = &b;
+    struct BoxPtrs {
+        int* level;
+        long long* coord;
+        int* parent;
+        int* child0;
+        long long* src_b;
+        long long* src_e;
+        double* center;
+        int* colleague;
+    } bx{b.d_level, b.d_coord, b.d_parent, b.d_child0, b.d_src_b, b.d_src_e, b.d_center, b.d_colleague};
+    const long long* d_tb = b.d_tgt_b;
+    const long long* d_te = b.d_tgt_e;
     t->level.resize(nb);
     t->coord.resize(size_t(nb) * d);
     t->parent.resize(nb);
@@ -958,9 +1009,6 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     t->center.resize(size_t(nb) * d);
     t->colleague.resize(size_t(nb) * nn);
     static_assert(sizeof(long long) == sizeof(int64_t), "64-bit box arrays");
-    // through the caller's page-locked staging buffer when it has one: its two halves take
-    // alternate chunks, so the copy of one chunk into the host arrays (on the host's threads)
-    // overlaps the transfer of the next; else straight into the host arrays
     struct Piece {
         void* dst;
         const void* src;
@@ -1038,31 +1086,6 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
         }
     }
     GB_CK(cudaStreamSynchronize(s));
-    if (lap(5)) return PDMK_ERR_CUDA;
-    bo->n = n;
-    bo->nimg = nimg;
-    bo->ntgt = h_ntgt;
-    bo->key_levels = K;
-    bo->nb = nb;
-    bo->d_level = bx.level;
-    bo->d_coord = bx.coord;
-    bo->d_parent = bx.parent;
-    bo->d_child0 = bx.child0;
-    bo->d_src_b = bx.src_b;
-    bo->d_src_e = bx.src_e;
-    bo->d_tgt_b = d_tb;
-    bo->d_tgt_e = d_te;
-    bo->d_colleague = bx.colleague;
-    bo->d_center = bx.center;
-    if (st) {
-        st->n = n;
-        st->n_images = nimg;
-        st->nboxes = nb;
-        int nlv = 0;
-        for (int k = 0; k < nb; ++k) nlv += t->child0[k] < 0;
-        st->nleaves = nlv;
-        st->depth = nlev - 1;
-    }
     return PDMK_OK;
 }
 

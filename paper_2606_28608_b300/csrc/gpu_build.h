@@ -41,6 +41,7 @@ struct GpuBuild {
     long long* d_tgt_e = nullptr;
     int* d_colleague = nullptr;     // 3^d per box
     double* d_center = nullptr;     // d per box (tree frame)
+    bool download_tree = true;      // gpu_build_tree fills the host tree's per-box arrays
 };
 void gpu_build_free(GpuBuild* b);
 
@@ -56,6 +57,9 @@ constexpr const char* kDeviceBuildPhases[6] = {"tree_device_images",      "tree_
                                                "tree_device_boxes_order", "tree_device_download"};
 int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStream_t s, GpuBuild* b, Tree* t,
                    BuildStats* st, std::string* msg);
+
+// the per-box arrays of b's device tree into the host tree t (whose scalars gpu_build_tree set)
+int gpu_tree_download(const GpuBuild& b, Tree* t, cudaStream_t s, std::string* msg);
 
 // ---- per-point passes (launchers; all arrays on the device) ----
 // the caller's positions (n x d) to wrapped fractional coordinates u (the orientation Q, then
