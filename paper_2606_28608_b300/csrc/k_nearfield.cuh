@@ -279,25 +279,28 @@ __device__ __forceinline__ float near_rcp<float>(float x) {
 
 constexpr int kNearWarps = 4;
 
-// per-warp shared state of the queue kernel
+// per-warp shared state of the queue kernel; a chunk holds CW sources (CW / 32 per lane)
 template <typename T, int D>
 struct NearWarpSmem {
     static constexpr int kLo = (sizeof(T) == 4) ? 1 : 0;
+    static constexpr int CW = (sizeof(T) == 4) ? 64 : 32;       // sources per chunk
+    static constexpr int SH = CW == 64 ? 6 : 5;                 // queue entry: t << SH | source
     T tx[32], ty[32], tz[D == 3 ? 32 : 1];                       // targets of the pass (hi)
     T tlx[kLo ? 32 : 1], tly[kLo ? 32 : 1], tlz[(D == 3 && kLo) ? 32 : 1];  // (lo)
-    T sx[32], sy[32], sz[D == 3 ? 32 : 1], sq[32];              // chunk sources (hi), charge
-    T lx[kLo ? 32 : 1], ly[kLo ? 32 : 1], lz[(D == 3 && kLo) ? 32 : 1];     // (lo)
+    T sx[CW], sy[CW], sz[D == 3 ? CW : 1], sq[CW];              // chunk sources (hi), charge
+    T lx[kLo ? CW : 1], ly[kLo ? CW : 1], lz[(D == 3 && kLo) ? CW : 1];     // (lo)
     // partial sums of the pair runs: [0, 32) a lane's first run, [32, 64) a run that starts
     // at target t's first pair
     T rp[64], rx[64], ry[64], rz[D == 3 ? 64 : 1];
-    unsigned short q[32 * 32];                                  // pair queue: t << 5 | source
+    unsigned short q[32 * CW];                                  // pair queue
 };
 
 // NH: padded length of the B series; NA <= NH: of the A series (usually two terms shorter)
 template <typename T, int D, int NH, int NA>
-__global__ void __launch_bounds__(32 * kNearWarps, sizeof(T) == 4 ? 8 : 1)
+__global__ void __launch_bounds__(32 * kNearWarps, sizeof(T) == 4 ? 7 : 1)
 k_near_warp(NearArgs<T> a) {
     constexpr int kLo = NearWarpSmem<T, D>::kLo;
+    constexpr int CW = NearWarpSmem<T, D>::CW, SH = NearWarpSmem<T, D>::SH, NHALF = CW / 32;
     constexpr unsigned kFull = 0xffffffffu;
     __shared__ NearWarpSmem<T, D> smem[kNearWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -336,14 +339,18 @@ k_near_warp(NearArgs<T> a) {
         kp.init(); kx.init(); ky.init(); kz.init();
         int e = 0, off = 0;  // warp-uniform stream position
         while (e < ne) {
-            // ---- chunk of up to 32 sources, lane j <-> source j, in the target leaf's frame
+            // ---- chunk of up to CW sources, lane l <-> sources l, l + 32, .., in the target
+            //      leaf's frame
             int filled = 0;
-            T mx = T(0), my = T(0), mz = T(0);
-            while (filled < 32 && e < ne) {
+            while (filled < CW && e < ne) {
                 const int2 bc = ent[e];
-                const int take = min(32 - filled, bc.y - off);
-                if (lane >= filled && lane < filled + take) {
-                    const int gi = bc.x + off + (lane - filled);
+                const int take = min(CW - filled, bc.y - off);
+#pragma unroll
+                for (int hh = 0; hh < NHALF; ++hh) {
+                const int slot = lane + 32 * hh;
+                if (slot >= filled && slot < filled + take) {
+                    const int gi = bc.x + off + (slot - filled);
+                    T mx, my, mz = T(0);
                     const T* s = a.src4 + size_t(gi) * 4;
                     if constexpr (kLo) {
                         // (y_hi + y_lo) + (sh_hi + sh_lo) as hi + lo: TwoSum of the hi parts
@@ -360,21 +367,22 @@ k_near_warp(NearArgs<T> a) {
                         }
                         mx = hi[0];
                         my = hi[1];
-                        S.lx[lane] = lo[0];
-                        S.ly[lane] = lo[1];
+                        S.lx[slot] = lo[0];
+                        S.ly[slot] = lo[1];
                         if constexpr (D == 3) {
                             mz = hi[2];
-                            S.lz[lane] = lo[2];
+                            S.lz[slot] = lo[2];
                         }
                     } else {
                         mx = s[0] + esh[e * 4 + 0];
                         my = s[1] + esh[e * 4 + 1];
                         if constexpr (D == 3) mz = s[2] + esh[e * 4 + 2];
                     }
-                    S.sx[lane] = mx;
-                    S.sy[lane] = my;
-                    if constexpr (D == 3) S.sz[lane] = mz;
-                    S.sq[lane] = s[3];
+                    S.sx[slot] = mx;
+                    S.sy[slot] = my;
+                    if constexpr (D == 3) S.sz[slot] = mz;
+                    S.sq[slot] = s[3];
+                }
                 }
                 filled += take;
                 off += take;
@@ -384,20 +392,36 @@ k_near_warp(NearArgs<T> a) {
                 }
             }
             __syncwarp();
-            // ---- cull: every lane tests its source against target t; accepted pairs queue
+            // ---- cull: every lane tests its sources against target t; accepted pairs queue
             //      in (t, source) order; lane t records where its target's run starts
-            const bool hs = lane < filled;
+            T mx[NHALF], my[NHALF], mz[NHALF];
+            bool hs[NHALF];
+#pragma unroll
+            for (int hh = 0; hh < NHALF; ++hh) {
+                hs[hh] = lane + 32 * hh < filled;
+                mx[hh] = S.sx[lane + 32 * hh];
+                my[hh] = S.sy[lane + 32 * hh];
+                mz[hh] = (D == 3) ? S.sz[lane + 32 * hh] : T(0);
+            }
             int N = 0, my_start = 0;
 #pragma unroll 4
             for (int t = 0; t < nt; ++t) {
-                const T dx = S.tx[t] - mx, dy = S.ty[t] - my;
-                const T dz = (D == 3) ? S.tz[t] - mz : T(0);
-                const T r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
-                const bool acc = hs && r2 * h2inv < T(1);
-                const unsigned b = __ballot_sync(kFull, acc);
-                if (acc) S.q[N + __popc(b & lt_mask)] = static_cast<unsigned short>((t << 5) | lane);
+                const T tx = S.tx[t], ty = S.ty[t];
+                const T tz = (D == 3) ? S.tz[t] : T(0);
+                int base = N;
+#pragma unroll
+                for (int hh = 0; hh < NHALF; ++hh) {
+                    const T dx = tx - mx[hh], dy = ty - my[hh];
+                    const T dz = (D == 3) ? tz - mz[hh] : T(0);
+                    const T r2 = (D == 3) ? fma(dx, dx, fma(dy, dy, dz * dz)) : fma(dx, dx, dy * dy);
+                    const bool acc = hs[hh] && r2 * h2inv < T(1);
+                    const unsigned b = __ballot_sync(kFull, acc);
+                    if (acc)
+                        S.q[base + __popc(b & lt_mask)] = static_cast<unsigned short>((t << SH) | (lane + 32 * hh));
+                    base += __popc(b);
+                }
                 if (lane == t) my_start = N;
-                N += __popc(b);
+                N = base;
             }
             int my_end = __shfl_down_sync(kFull, my_start, 1);
             if (lane == nt - 1) my_end = N;
@@ -411,7 +435,7 @@ k_near_warp(NearArgs<T> a) {
             T pp = 0, gx = 0, gy = 0, gz = 0;
             for (int i = b0; i < b1; ++i) {
                 const int qe = S.q[i];
-                const int t = qe >> 5, j = qe & 31;
+                const int t = qe >> SH, j = qe & (CW - 1);
                 if (t != cur) {
                     if (cur >= 0) {
                         const int sl = (first == b0) ? lane : 32 + cur;
