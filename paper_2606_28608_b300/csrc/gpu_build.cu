@@ -46,6 +46,8 @@ struct Geo {
     int periodic;
     double Q[9], R[9], Rinv[9];
     double lo[3], hi[3], rc;
+    double rdiag[3];  // 1 / R[a][a]
+    double inv_rc;    // 1 / r_c
     int nroot[3];
 };
 
@@ -63,6 +65,8 @@ Geo make_geo(const Geometry& g) {
         o.nroot[i] = i < g.d ? g.nroot[i] : 1;
     }
     o.rc = g.rc;
+    for (int a = 0; a < g.d; ++a) o.rdiag[a] = 1.0 / g.R[a * g.d + a];
+    o.inv_rc = 1.0 / g.rc;  // as the host build
     return o;
 }
 
@@ -123,7 +127,12 @@ __global__ void k_check(int64_t n, int d, const double* __restrict__ y, const do
 }
 
 // ---------------------------------------------------------------------------------------
-// images (Sec. 3.4): the host's candidate ranges and in-box test, arithmetic for arithmetic
+// images (Sec. 3.4): the host's candidate ranges and in-box test.  The in-box test is the
+// host's arithmetic for arithmetic.  The candidate ranges take the reciprocal of the diagonal
+// entry instead of dividing by it (FP64 division is slow on this part, and the ranges are
+// computed about ten times per point); they carry a slack of 1e-9 (1 + |bound|), far above
+// the few ulps this changes, so every shift the in-box test accepts is still a candidate
+// and the accepted shifts, in the host's order, are the same.
 
 __device__ __forceinline__ void frac_to_tree(const Geo& g, const double* uj, double* x) {
     const int d = g.d;
@@ -148,9 +157,8 @@ __device__ __forceinline__ void shift_range(const Geo& g, const ImgTab& t, const
     const int d = g.d;
     double off = 0;
     for (int k = a + 1; k < d; ++k) off = dadd(off, dmul(g.R[a * d + k], double(nv[k])));
-    const double raa = g.R[a * d + a];
-    const double l = ddiv(dsub(dsub(g.lo[a], x[a]), off), raa);
-    const double h = ddiv(dsub(dsub(g.hi[a], x[a]), off), raa);
+    const double l = dmul(dsub(dsub(g.lo[a], x[a]), off), g.rdiag[a]);
+    const double h = dmul(dsub(dsub(g.hi[a], x[a]), off), g.rdiag[a]);
     const double sl = dmul(1e-9, dadd(1.0, fabs(l))), sh = dmul(1e-9, dadd(1.0, fabs(h)));
     *lo_n = max(-t.Bx[a], int(ceil(dsub(l, sl))));
     *hi_n = min(t.Bx[a], int(floor(dadd(h, sh))));
@@ -197,9 +205,10 @@ __global__ void k_image_count(Geo g, ImgTab t, int64_t n, const double* __restri
 __global__ void k_image_write(Geo g, ImgTab t, int64_t n, const double* __restrict__ u, const int* __restrict__ off,
                               int* __restrict__ pk, int* __restrict__ pj) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        int w = off[j];
+        if (off[j + 1] == w) continue;  // no images (off holds n + 1 entries)
         double x[3];
         frac_to_tree(g, u + j * g.d, x);
-        int w = off[j];
         for_images(g, t, x, [&](int k) {
             pk[w] = k;
             pj[w] = int(j);
@@ -256,7 +265,7 @@ __global__ void k_image_pos(Geo g, ImgTab t, int64_t n, int64_t nimg, int K, con
         for (int a = 0; a < d; ++a) {
             const double p = dadd(x[a], t.trs[k * 3 + a]);
             pos[im * d + a] = p;
-            const double tsc = ddiv(dsub(p, g.lo[a]), g.rc);
+            const double tsc = dmul(dsub(p, g.lo[a]), g.inv_rc);
             long long ci = (long long)floor(tsc);
             ci = min(max(ci, 0LL), (long long)g.nroot[a] - 1);
             rcell[a] = ci;

@@ -793,9 +793,12 @@ int build_tree(const Geometry& g, int64_t n, const double* u, int n_s, int max_d
     }
     const int64_t nimg = int64_t(img_orig.size());
     bld.tsc.resize(size_t(nimg) * d);
+    // position in root-box units, (p - lo) times 1 / r_c (the device build does the same two
+    // rounded steps, so both builds put every point in the same box)
+    const double inv_rc = 1.0 / g.rc;
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < nimg; ++j)
-        for (int a = 0; a < d; ++a) bld.tsc[size_t(j) * d + a] = (bld.pos[size_t(j) * d + a] - g.lo[a]) / g.rc;
+        for (int a = 0; a < d; ++a) bld.tsc[size_t(j) * d + a] = (bld.pos[size_t(j) * d + a] - g.lo[a]) * inv_rc;
     bld.map.reserve(size_t(std::max<int64_t>(1024, 4 * nimg / std::max(n_s, 1))));
     lap(0);
     // ---- root boxes: counting sort by root cell ----
