@@ -1599,9 +1599,9 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
         plan->setup_ms.push_back(std::chrono::duration<double, std::milli>(now - clk).count());
         clk = now;
     };
-    // scratch of this call (freed on every return, after the stream has drained)
-    // scratch of this call: on every return, after the stream has drained, the spares that
-    // this set-up did not take are freed and the scratch becomes the spares of the next
+    // scratch of this call (the device build's temporary buffers included): on every return,
+    // after the stream has drained, the spares that this set-up did not take are freed, and
+    // the scratch and the device build's arrays become the spares of the next set-up
     struct Scratch {
         cudaStream_t s;
         DevicePool* pool;
@@ -1609,8 +1609,8 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
         GpuBuild gb;
         ~Scratch() {
             cudaStreamSynchronize(s);
-            gpu_build_free(&gb);
             pool->trim();
+            gpu_build_free(&gb);  // into the pool
             for (auto& x : p) pool->put(x.first, x.second);
         }
     } scr{s, &plan->pool, {}, {}};
@@ -1671,6 +1671,8 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     // ---- tree (device), lists (host) ----
     GpuBuild& gb = scr.gb;
     gb.d_u = plan->d_u_keep;
+    gb.pool = &plan->pool;
+    gb.scratch = &scr.p;
     if (!plan->h_stage) {
         void* hs = nullptr;
         if (cudaHostAlloc(&hs, size_t(64) << 20, cudaHostAllocDefault) == cudaSuccess) {
@@ -1850,6 +1852,8 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
     fa.bin_count = d_bin_count;
     fa.t_g0 = plan->d_t_g0;
     fa.t_dq = plan->d_t_dq;
+    fa.pool = &plan->pool;
+    fa.scratch = &scr.p;
     if ((r = gpu_far_layout(fa, s, &msg)) != PDMK_OK) {
         plan->msg = msg;
         return r;
@@ -1960,13 +1964,16 @@ static int set_points_device(pdmk_plan plan, int64_t n_src, const double* y, con
             {gb.d_tgt_b, size_t(nb) * 8},      {gb.d_tgt_e, size_t(nb) * 8},     {gb.d_center, size_t(nb) * d * 8},
             {gb.d_colleague, size_t(nb) * nn * 4}};
         for (const auto& k : keep) {
-            auto it = std::find(gb.allocs.begin(), gb.allocs.end(), k.first);
+            auto it = std::find_if(gb.allocs.begin(), gb.allocs.end(),
+                                   [&](const std::pair<void*, size_t>& a) { return a.first == k.first; });
             if (it == gb.allocs.end()) return PDMK_ERR_INTERNAL;
+            plan->tree_keep.push_back(*it);
             gb.allocs.erase(it);
-            plan->tree_keep.push_back(k);
         }
         plan->tree_dev = gb;
         plan->tree_dev.allocs.clear();
+        plan->tree_dev.pool = nullptr;  // pointers only: the plan owns the arrays (tree_keep)
+        plan->tree_dev.scratch = nullptr;
     }
     plan->h_u.clear();
     plan->h_y.clear();

@@ -640,15 +640,27 @@ __global__ void k_entries(EntryArgs a) {
 // ---------------------------------------------------------------------------------------
 // host helpers
 
+// temporary buffers of one call: from the plan's pool when there is one (the caller returns
+// them once the stream has drained), else cudaMalloc'd and freed on return
 struct Scratch {
+    DevicePool* pool = nullptr;
+    std::vector<std::pair<void*, size_t>>* keep = nullptr;
     std::vector<void*> ptrs;
+    Scratch(DevicePool* p, std::vector<std::pair<void*, size_t>>* k) : pool(p && k ? p : nullptr), keep(k) {}
     ~Scratch() {
         for (void* p : ptrs) cudaFree(p);
     }
     template <class X>
     X* get(size_t count) {
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(X);
         void* p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) {
+        if (pool) {
+            p = pool->get(bytes);
+            if (!p) return nullptr;
+            keep->push_back({p, bytes});
+            return static_cast<X*>(p);
+        }
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
@@ -682,13 +694,19 @@ int bits_for(uint64_t v) {  // bits to hold values < v
 
 template <class X>
 int own(GpuBuild* b, X** out, size_t count, std::string* msg) {
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(X);
     void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) {
+    if (b->pool) {
+        p = b->pool->get(bytes);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) {
         if (msg) *msg = "device allocation failed (set-up)";
         return PDMK_ERR_CUDA;
     }
-    b->allocs.push_back(p);
+    b->allocs.push_back({p, bytes});
     *out = static_cast<X*>(p);
     return PDMK_OK;
 }
@@ -696,7 +714,12 @@ int own(GpuBuild* b, X** out, size_t count, std::string* msg) {
 }  // namespace
 
 void gpu_build_free(GpuBuild* b) {
-    for (void* p : b->allocs) cudaFree(p);
+    for (auto& a : b->allocs) {
+        if (b->pool)
+            b->pool->put(a.first, a.second);
+        else
+            cudaFree(a.first);
+    }
     b->allocs.clear();
     b->nb = 0;
     b->d_level = b->d_parent = b->d_child0 = b->d_colleague = nullptr;
@@ -723,7 +746,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
                    BuildStats* st, std::string* msg) {
     const int d = g.d;
     const Geo geo = make_geo(g);
-    Scratch scr;
+    Scratch scr(bo->pool, bo->scratch);
     // host wall clock of the phases (kDeviceBuildPhases), the stream drained at each boundary
     auto clk = std::chrono::steady_clock::now();
     auto lap = [&](int k) -> int {
@@ -1124,7 +1147,7 @@ void gpu_near_entries(const EntryArgs& a, cudaStream_t s) {
 }
 
 int gpu_far_layout(const FarLayoutArgs& a, cudaStream_t s, std::string* msg) {
-    Scratch scr;
+    Scratch scr(a.pool, a.scratch);
     int *d_bin, *d_bin2, *d_vals, *d_order;
     int4* d_g0;
     double* d_del;
@@ -1354,7 +1377,7 @@ BoxView box_view(const GpuBuild& b, int d) {
 }  // namespace
 
 int gpu_near_count(GpuBuild* b, const Geometry& g, bool split32, NearLists* nl, cudaStream_t s, std::string* msg) {
-    Scratch scr;
+    Scratch scr(b->pool, b->scratch);
     const int nb = b->nb, d = g.d;
     const Geo geo = make_geo(g);
     unsigned char* flag;
@@ -1427,7 +1450,7 @@ int gpu_near_count(GpuBuild* b, const Geometry& g, bool split32, NearLists* nl, 
 
 int gpu_near_fill(GpuBuild* b, const Geometry& g, bool split32, NearLists* nl, int* d_list, TLeaf* d_desc,
                   int* d_bsb, int* d_bsc, cudaStream_t s, std::string* msg) {
-    Scratch scr;
+    Scratch scr(b->pool, b->scratch);
     const int d = g.d, ntl = nl->ntleaf;
     const int64_t nd = nl->ndesc;
     k_box_src<<<blocks_for(b->nb), kThreads, 0, s>>>(b->nb, b->d_src_b, b->d_src_e, d_bsb, d_bsc);

@@ -10,8 +10,10 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
+#include "dev_pool.h"
 #include "host_plan.h"
 
 namespace pdmk {
@@ -26,7 +28,12 @@ struct GpuBuild {
     int* d_leaf = nullptr;      // per sorted source: leaf box
     int* d_tgt_of = nullptr;    // per sorted target: sorted source index of the point
     int* d_tgt_orig = nullptr;  // per sorted target: point index
-    std::vector<void*> allocs;
+    std::vector<std::pair<void*, size_t>> allocs;  // the arrays below that b owns (buffer, bytes)
+    // with a pool: b's arrays come from it and go back to it (gpu_build_free), and the
+    // build's temporary buffers come from it and are appended to *scratch, for the caller
+    // to return once the stream has drained; without one, cudaMalloc and cudaFree
+    DevicePool* pool = nullptr;
+    std::vector<std::pair<void*, size_t>>* scratch = nullptr;
     unsigned char* h_stage = nullptr;  // optional page-locked staging buffer of the caller
     size_t stage_cap = 0;              // its bytes (used when at least 1 MiB)
     // the tree's box arrays on the device, in the host tree's box order (nb boxes)
@@ -118,6 +125,8 @@ struct FarLayoutArgs {
     int* sp_orig;          // out: point index per position in bin order
     int* bin_count;        // out: points per bin (nbins_tot)
     int4* t_g0;            // out: per sorted target
+    DevicePool* pool;      // optional: temporary buffers from it, appended to *scratch (as GpuBuild)
+    std::vector<std::pair<void*, size_t>>* scratch;
     void* t_dq;            // out
 };
 int gpu_far_layout(const FarLayoutArgs& a, cudaStream_t s, std::string* msg);
