@@ -191,22 +191,39 @@ __device__ bool for_images(const Geo& g, const ImgTab& t, const double* x, F f) 
     return true;
 }
 
+// per point: the number of images, and the first kImgKeep shifts (in the host's order),
+// which spare the write pass a second enumeration for points with at most kImgKeep images
+// (in 3D a point near a corner of the extended domain has up to seven)
+constexpr int kImgKeep = 8;
 __global__ void k_image_count(Geo g, ImgTab t, int64_t n, const double* __restrict__ u, int* __restrict__ cnt,
-                              int* __restrict__ missing) {
+                              int* __restrict__ kept, int* __restrict__ missing) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
         double x[3];
         frac_to_tree(g, u + j * g.d, x);
         int c = 0;
-        if (!for_images(g, t, x, [&](int) { ++c; })) atomicOr(missing, 1);
+        int* kj = kept + j * kImgKeep;
+        if (!for_images(g, t, x, [&](int k) {
+                if (c < kImgKeep) kj[c] = k;
+                ++c;
+            }))
+            atomicOr(missing, 1);
         cnt[j] = c;
     }
 }
 
 __global__ void k_image_write(Geo g, ImgTab t, int64_t n, const double* __restrict__ u, const int* __restrict__ off,
-                              int* __restrict__ pk, int* __restrict__ pj) {
+                              const int* __restrict__ kept, int* __restrict__ pk, int* __restrict__ pj) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
         int w = off[j];
-        if (off[j + 1] == w) continue;  // no images (off holds n + 1 entries)
+        const int c = off[j + 1] - w;  // off holds n + 1 entries
+        if (c == 0) continue;
+        if (c <= kImgKeep) {  // the shifts the count pass kept
+            for (int i = 0; i < c; ++i) {
+                pk[w + i] = kept[j * kImgKeep + i];
+                pj[w + i] = int(j);
+            }
+            continue;
+        }
         double x[3];
         frac_to_tree(g, u + j * g.d, x);
         for_images(g, t, x, [&](int k) {
@@ -774,12 +791,14 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     it.sidx = d_sidx;
     it.trs = d_trs;
     int *d_cnt, *d_off, *d_flag;
+    int* d_kept;
     GB_ALLOC(d_cnt, int, n + 1);
+    GB_ALLOC(d_kept, int, size_t(n) * kImgKeep);
     GB_ALLOC(d_off, int, n + 1);
     GB_ALLOC(d_flag, int, 1);
     GB_CK(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
     GB_CK(cudaMemsetAsync(d_cnt + n, 0, sizeof(int), s));
-    k_image_count<<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_cnt, d_flag);
+    k_image_count<<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_cnt, d_kept, d_flag);
     size_t tb = 0;
     GB_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, d_cnt, d_off, int(n + 1), s));
     void* d_tmp = nullptr;
@@ -810,7 +829,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     GB_ALLOC(d_pk2, int, nx);
     GB_ALLOC(d_pj2, int, nx);
     if (nx > 0) {
-        k_image_write<<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_off, d_pk, d_pj);
+        k_image_write<<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_off, d_kept, d_pk, d_pj);
         const int kb = std::max(1, bits_for(uint64_t(tab.ns)));
         GB_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, d_pk, d_pk2, d_pj, d_pj2, int(nx), 0, kb, s));
         if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
