@@ -134,8 +134,11 @@ __global__ void k_check(int64_t n, int d, const double* __restrict__ y, const do
 // the few ulps this changes, so every shift the in-box test accepts is still a candidate
 // and the accepted shifts, in the host's order, are the same.
 
+// D: the dimension (compile-time, so that the loops unroll and the small arrays stay in
+// registers)
+template <int D>
 __device__ __forceinline__ void frac_to_tree(const Geo& g, const double* uj, double* x) {
-    const int d = g.d;
+    constexpr int d = D;
     for (int i = 0; i < d; ++i) {
         double v = 0;
         for (int k = i; k < d; ++k) v = dadd(v, dmul(g.R[i * d + k], uj[k]));
@@ -143,18 +146,21 @@ __device__ __forceinline__ void frac_to_tree(const Geo& g, const double* uj, dou
     }
 }
 
+template <int D>
 __device__ __forceinline__ bool in_domain(const Geo& g, const ImgTab& t, const double* x, int k) {
     bool in = true;
-    for (int a = 0; a < g.d; ++a) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
         const double p = dadd(x[a], t.trs[k * 3 + a]);
         in &= (p >= g.lo[a] && p < g.hi[a]);
     }
     return in;
 }
 
+template <int D>
 __device__ __forceinline__ void shift_range(const Geo& g, const ImgTab& t, const double* x, int a, const int* nv,
                                             int* lo_n, int* hi_n) {
-    const int d = g.d;
+    constexpr int d = D;
     double off = 0;
     for (int k = a + 1; k < d; ++k) off = dadd(off, dmul(g.R[a * d + k], double(nv[k])));
     const double l = dmul(dsub(dsub(g.lo[a], x[a]), off), g.rdiag[a]);
@@ -166,25 +172,25 @@ __device__ __forceinline__ void shift_range(const Geo& g, const ImgTab& t, const
 
 // calls f(k) for every accepted shift k > 0 in the host's loop order; false if the point
 // itself lies outside the extended domain
-template <class F>
-__device__ bool for_images(const Geo& g, const ImgTab& t, const double* x, F f) {
-    const int d = g.d;
-    if (!in_domain(g, t, x, 0)) return false;
+template <int D, class F>
+__device__ __forceinline__ bool for_images(const Geo& g, const ImgTab& t, const double* x, F f) {
+    constexpr int d = D;
+    if (!in_domain<D>(g, t, x, 0)) return false;
     int nv[3] = {0, 0, 0};
     int l2 = 0, h2 = 0, l1 = 0, h1 = 0, l0 = 0, h0 = 0;
-    if (d == 3) shift_range(g, t, x, 2, nv, &l2, &h2);
+    if (d == 3) shift_range<D>(g, t, x, 2, nv, &l2, &h2);
     for (int v2 = l2; v2 <= h2; ++v2) {
         nv[2] = d == 3 ? v2 : 0;
-        shift_range(g, t, x, 1, nv, &l1, &h1);
+        shift_range<D>(g, t, x, 1, nv, &l1, &h1);
         for (int v1 = l1; v1 <= h1; ++v1) {
             nv[1] = v1;
-            shift_range(g, t, x, 0, nv, &l0, &h0);
+            shift_range<D>(g, t, x, 0, nv, &l0, &h0);
             for (int v0 = l0; v0 <= h0; ++v0) {
                 nv[0] = v0;
                 long long fl = 0;
                 for (int a = d - 1; a >= 0; --a) fl = fl * t.dimx[a] + (nv[a] + t.Bx[a]);
                 const int k = t.sidx[fl];
-                if (k > 0 && in_domain(g, t, x, k)) f(k);
+                if (k > 0 && in_domain<D>(g, t, x, k)) f(k);
             }
         }
     }
@@ -195,14 +201,15 @@ __device__ bool for_images(const Geo& g, const ImgTab& t, const double* x, F f) 
 // which spare the write pass a second enumeration for points with at most kImgKeep images
 // (in 3D a point near a corner of the extended domain has up to seven)
 constexpr int kImgKeep = 8;
+template <int D>
 __global__ void k_image_count(Geo g, ImgTab t, int64_t n, const double* __restrict__ u, int* __restrict__ cnt,
                               int* __restrict__ kept, int* __restrict__ missing) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
         double x[3];
-        frac_to_tree(g, u + j * g.d, x);
+        frac_to_tree<D>(g, u + j * D, x);
         int c = 0;
         int* kj = kept + j * kImgKeep;
-        if (!for_images(g, t, x, [&](int k) {
+        if (!for_images<D>(g, t, x, [&](int k) {
                 if (c < kImgKeep) kj[c] = k;
                 ++c;
             }))
@@ -211,6 +218,7 @@ __global__ void k_image_count(Geo g, ImgTab t, int64_t n, const double* __restri
     }
 }
 
+template <int D>
 __global__ void k_image_write(Geo g, ImgTab t, int64_t n, const double* __restrict__ u, const int* __restrict__ off,
                               const int* __restrict__ kept, int* __restrict__ pk, int* __restrict__ pj) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
@@ -225,8 +233,8 @@ __global__ void k_image_write(Geo g, ImgTab t, int64_t n, const double* __restri
             continue;
         }
         double x[3];
-        frac_to_tree(g, u + j * g.d, x);
-        for_images(g, t, x, [&](int k) {
+        frac_to_tree<D>(g, u + j * D, x);
+        for_images<D>(g, t, x, [&](int k) {
             pk[w] = k;
             pj[w] = int(j);
             ++w;
@@ -267,16 +275,17 @@ __device__ __forceinline__ void box_cell(const Geo& g, int L, unsigned long long
 }
 
 // positions of the copies in image order, and their keys
+template <int D>
 __global__ void k_image_pos(Geo g, ImgTab t, int64_t n, int64_t nimg, int K, const double* __restrict__ u,
                             const int* __restrict__ pk, const int* __restrict__ pj, double* __restrict__ pos,
                             unsigned long long* __restrict__ key, int* __restrict__ val) {
-    const int d = g.d;
+    constexpr int d = D;
     const double scale = ldexp(1.0, K);
     for (int64_t im = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; im < nimg; im += int64_t(gridDim.x) * blockDim.x) {
         const int64_t j = im < n ? im : pj[im - n];
         const int k = im < n ? 0 : pk[im - n];
         double x[3];
-        frac_to_tree(g, u + j * d, x);
+        frac_to_tree<D>(g, u + j * d, x);
         long long root = 0, w[3] = {0, 0, 0};
         long long rcell[3] = {0, 0, 0};
         for (int a = 0; a < d; ++a) {
@@ -481,9 +490,12 @@ __device__ __forceinline__ void put_rec(void* buf, int64_t idx, double v) {
     static_cast<T*>(buf)[idx] = T(v);
 }
 
-__device__ __forceinline__ void mat_vec(int d, const double* M, const double* v, double* out, bool transpose) {
+template <int d>
+__device__ __forceinline__ void mat_vec(const double* M, const double* v, double* out, bool transpose) {
+#pragma unroll
     for (int i = 0; i < d; ++i) {
         double s = 0;
+#pragma unroll
         for (int k = 0; k < d; ++k) s = dadd(s, dmul(transpose ? M[k * d + i] : M[i * d + k], v[k]));
         out[i] = s;
     }
@@ -491,13 +503,14 @@ __device__ __forceinline__ void mat_vec(int d, const double* M, const double* v,
 
 // leaf-relative position of sorted source j, in the tree frame, and the caller-frame lattice
 // vector of its copy (zero for the point itself)
-__device__ void relative_of(const RecordArgs& a, int64_t j, double* rel, double* disp) {
-    const int d = a.d;
+template <int D>
+__device__ __forceinline__ void relative_of(const RecordArgs& a, int64_t j, double* rel, double* disp) {
+    constexpr int d = D;
     const int b = a.leaf[j];
     const int64_t o = a.orig[j];
-    double yo[3] = {0, 0, 0}, xo[3], m[3], D[3], E[3], du[3];
+    double yo[3] = {0, 0, 0}, xo[3], m[3], Dv[3], E[3], du[3];
     for (int k = 0; k < d; ++k) yo[k] = a.y[o * d + k];
-    mat_vec(d, a.Q, yo, xo, false);
+    mat_vec<d>(a.Q, yo, xo, false);
     bool shifted = false;
     for (int i = 0; i < d; ++i) {
         double f = 0;
@@ -512,23 +525,23 @@ __device__ void relative_of(const RecordArgs& a, int64_t j, double* rel, double*
             double s = 0;
             for (int k = 0; k < d; ++k) s = dadd(s, dmul(a.R[i * d + k], m[k]));
             Rm[i] = s;
-            D[i] = dsub(a.center[int64_t(b) * d + i], s);
+            Dv[i] = dsub(a.center[int64_t(b) * d + i], s);
         }
-        mat_vec(d, a.Q, D, E, true);
-        mat_vec(d, a.Q, Rm, disp, true);
+        mat_vec<d>(a.Q, Dv, E, true);
+        mat_vec<d>(a.Q, Rm, disp, true);
     } else {
         for (int i = 0; i < d; ++i) E[i] = a.Cu[int64_t(b) * d + i];
     }
     for (int k = 0; k < d; ++k) du[k] = dsub(yo[k], E[k]);
-    mat_vec(d, a.Q, du, rel, false);
+    mat_vec<d>(a.Q, du, rel, false);
 }
 
-template <typename T>
+template <typename T, int D>
 __global__ void k_src_records(RecordArgs a) {
-    const int d = a.d;
+    constexpr int d = D;
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < a.nimg; j += int64_t(gridDim.x) * blockDim.x) {
         double rel[3], disp[3];
-        relative_of(a, j, rel, disp);
+        relative_of<D>(a, j, rel, disp);
         for (int k = 0; k < d; ++k) {
             put_rec<T>(a.src4, j * 4 + k, rel[k]);
             if (a.mixed) a.src_lo[j * 4 + k] = float(rel[k] - double(float(rel[k])));
@@ -538,14 +551,14 @@ __global__ void k_src_records(RecordArgs a) {
     }
 }
 
-template <typename T>
+template <typename T, int D>
 __global__ void k_tgt_records(RecordArgs a) {
-    const int d = a.d;
+    constexpr int d = D;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < a.ntgt; t += int64_t(gridDim.x) * blockDim.x) {
         const int64_t j = a.tgt_of[t];
         const int b = a.leaf[j];
         double rel[3], disp[3];
-        relative_of(a, j, rel, disp);
+        relative_of<D>(a, j, rel, disp);
         a.tgt_leaf[t] = b;
         for (int k = 0; k < d; ++k) {
             put_rec<T>(a.tgt4, t * 4 + k, rel[k]);
@@ -558,7 +571,8 @@ __global__ void k_tgt_records(RecordArgs a) {
 
 __global__ void k_box_cu(int nb, int d, Geo g, const double* __restrict__ center, double* __restrict__ Cu) {
     for (int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; b < nb; b += int64_t(gridDim.x) * blockDim.x)
-        mat_vec(d, g.Q, center + b * d, Cu + b * d, true);
+        if (d == 3) mat_vec<3>(g.Q, center + b * 3, Cu + b * 3, true);
+        else mat_vec<2>(g.Q, center + b * 2, Cu + b * 2, true);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -798,7 +812,8 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     GB_ALLOC(d_flag, int, 1);
     GB_CK(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
     GB_CK(cudaMemsetAsync(d_cnt + n, 0, sizeof(int), s));
-    k_image_count<<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_cnt, d_kept, d_flag);
+    if (d == 3) k_image_count<3><<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_cnt, d_kept, d_flag);
+    else k_image_count<2><<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_cnt, d_kept, d_flag);
     size_t tb = 0;
     GB_CK(cub::DeviceScan::ExclusiveSum(nullptr, tb, d_cnt, d_off, int(n + 1), s));
     void* d_tmp = nullptr;
@@ -829,7 +844,8 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     GB_ALLOC(d_pk2, int, nx);
     GB_ALLOC(d_pj2, int, nx);
     if (nx > 0) {
-        k_image_write<<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_off, d_kept, d_pk, d_pj);
+        if (d == 3) k_image_write<3><<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_off, d_kept, d_pk, d_pj);
+        else k_image_write<2><<<blocks_for(n), kThreads, 0, s>>>(geo, it, n, bo->d_u, d_off, d_kept, d_pk, d_pj);
         const int kb = std::max(1, bits_for(uint64_t(tab.ns)));
         GB_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, d_pk, d_pk2, d_pj, d_pj2, int(nx), 0, kb, s));
         if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
@@ -850,7 +866,11 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     GB_ALLOC(d_key2, unsigned long long, nimg);
     GB_ALLOC(d_val, int, nimg);
     GB_ALLOC(d_val2, int, nimg);
-    k_image_pos<<<blocks_for(nimg), kThreads, 0, s>>>(geo, it, n, nimg, K, bo->d_u, d_pk2, d_pj2, d_posimg, d_key,
+    if (d == 3)
+        k_image_pos<3><<<blocks_for(nimg), kThreads, 0, s>>>(geo, it, n, nimg, K, bo->d_u, d_pk2, d_pj2, d_posimg, d_key,
+                                                      d_val);
+    else
+        k_image_pos<2><<<blocks_for(nimg), kThreads, 0, s>>>(geo, it, n, nimg, K, bo->d_u, d_pk2, d_pj2, d_posimg, d_key,
                                                       d_val);
     const int keybits = rbits + d * K;
     GB_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, d_key, d_key2, d_val, d_val2, int(nimg), 0, keybits, s));
@@ -1150,12 +1170,14 @@ void gpu_box_cu(int nb, int d, const double* Q, const double* center, double* Cu
 
 void gpu_records(const RecordArgs& a, cudaStream_t s) {
     if (a.nimg > 0) {
-        if (a.mixed) k_src_records<float><<<blocks_for(a.nimg), kThreads, 0, s>>>(a);
-        else k_src_records<double><<<blocks_for(a.nimg), kThreads, 0, s>>>(a);
+        const int nb = blocks_for(a.nimg);
+        if (a.mixed) (a.d == 3 ? k_src_records<float, 3> : k_src_records<float, 2>)<<<nb, kThreads, 0, s>>>(a);
+        else (a.d == 3 ? k_src_records<double, 3> : k_src_records<double, 2>)<<<nb, kThreads, 0, s>>>(a);
     }
     if (a.ntgt > 0) {
-        if (a.mixed) k_tgt_records<float><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
-        else k_tgt_records<double><<<blocks_for(a.ntgt), kThreads, 0, s>>>(a);
+        const int nb = blocks_for(a.ntgt);
+        if (a.mixed) (a.d == 3 ? k_tgt_records<float, 3> : k_tgt_records<float, 2>)<<<nb, kThreads, 0, s>>>(a);
+        else (a.d == 3 ? k_tgt_records<double, 3> : k_tgt_records<double, 2>)<<<nb, kThreads, 0, s>>>(a);
     }
 }
 
