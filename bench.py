@@ -468,6 +468,8 @@ def main():
     ap.add_argument("--sweep-samples", type=int, default=32)
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the mixed plan, warm-up + steps evaluations, no other work")
+    ap.add_argument("--ncu-setup", action="store_true",
+                    help="profiling run: warm-up + steps set-ups (pdmk_set_sources) of the mixed plan, no evaluation")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
@@ -502,6 +504,15 @@ def main():
 
     pot = torch.empty(n, dtype=torch.float64, device=dev)
     grad = torch.empty((n, d), dtype=torch.float64, device=dev)
+    if args.ncu_setup:
+        plan = P.Plan(g["L"], EPS, precision="mixed", stream=stream.cuda_stream)
+        for _ in range(args.warmup + args.steps):
+            plan.set_sources(g["y"], g["q"])
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_setup_run": True, "set_ups": args.warmup + args.steps,
+                          "phases_ms_last": plan.setup_times()}))
+        plan.close()
+        return
     if args.ncu:
         plan = make("mixed")
         for _ in range(args.warmup + args.steps):
