@@ -245,29 +245,36 @@ __global__ void k_image_write(Geo g, ImgTab t, int64_t n, const double* __restri
 // ---------------------------------------------------------------------------------------
 // keys
 
-__device__ __forceinline__ unsigned long long morton(const long long* w, int d, int levels) {
+// Morton interleave of the per-axis cell bits, and the box key of the level-L cell c (in range)
+// and its inverse; D, the dimension, is compile-time (the loops unroll, the arrays stay in
+// registers)
+template <int D>
+__device__ __forceinline__ unsigned long long morton_d(const long long* w, int levels) {
     unsigned long long m = 0;
     for (int b = 0; b < levels; ++b)
-        for (int a = 0; a < d; ++a) m |= (unsigned long long)((w[a] >> b) & 1) << (d * b + a);
+#pragma unroll
+        for (int a = 0; a < D; ++a) m |= (unsigned long long)((w[a] >> b) & 1) << (D * b + a);
     return m;
 }
-__device__ __forceinline__ void unmorton(unsigned long long m, int d, int levels, long long* w) {
-    for (int a = 0; a < d; ++a) w[a] = 0;
-    for (int b = 0; b < levels; ++b)
-        for (int a = 0; a < d; ++a) w[a] |= (long long)((m >> (d * b + a)) & 1) << b;
-}
-// box key of the level-L cell c (in range) and its inverse
-__device__ __forceinline__ unsigned long long box_key(const Geo& g, int L, const long long* c) {
+template <int D>
+__device__ __forceinline__ unsigned long long box_key_d(const Geo& g, int L, const long long* c) {
     long long root = 0, w[3] = {0, 0, 0};
-    for (int a = g.d - 1; a >= 0; --a) root = root * g.nroot[a] + (c[a] >> L);
-    for (int a = 0; a < g.d; ++a) w[a] = c[a] & ((1LL << L) - 1);
-    return ((unsigned long long)root << (g.d * L)) | morton(w, g.d, L);
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) root = root * g.nroot[a] + (c[a] >> L);
+#pragma unroll
+    for (int a = 0; a < D; ++a) w[a] = c[a] & ((1LL << L) - 1);
+    return ((unsigned long long)root << (D * L)) | morton_d<D>(w, L);
 }
-__device__ __forceinline__ void box_cell(const Geo& g, int L, unsigned long long key, long long* c) {
-    long long root = (long long)(key >> (g.d * L));
-    long long w[3];
-    unmorton(key & ((1ULL << (g.d * L)) - 1), g.d, L, w);
-    for (int a = 0; a < g.d; ++a) {
+template <int D>
+__device__ __forceinline__ void box_cell_d(const Geo& g, int L, unsigned long long key, long long* c) {
+    long long root = (long long)(key >> (D * L));
+    long long w[3] = {0, 0, 0};
+    const unsigned long long m = key & ((1ULL << (D * L)) - 1);
+    for (int b = 0; b < L; ++b)
+#pragma unroll
+        for (int a = 0; a < D; ++a) w[a] |= (long long)((m >> (D * b + a)) & 1) << b;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
         const long long rc = root % g.nroot[a];
         root /= g.nroot[a];
         c[a] = (rc << L) | w[a];
@@ -300,7 +307,7 @@ __global__ void k_image_pos(Geo g, ImgTab t, int64_t n, int64_t nimg, int K, con
             w[a] = cK & ((1LL << K) - 1);
         }
         for (int a = d - 1; a >= 0; --a) root = root * g.nroot[a] + rcell[a];
-        key[im] = ((unsigned long long)root << (d * K)) | morton(w, d, K);
+        key[im] = ((unsigned long long)root << (d * K)) | morton_d<D>(w, K);
         val[im] = int(im);
     }
 }
@@ -332,15 +339,15 @@ __global__ void k_runs(int64_t nimg, const unsigned long long* __restrict__ key,
 
 // the parent's colleagues of every non-leaf box of level L (keys at level L - 1; invalid:
 // all ones)
+template <int D>
 __global__ void k_restrict_cands(Geo g, int L, const unsigned long long* __restrict__ nl, int64_t cnt,
                                  unsigned long long* __restrict__ out) {
-    const int d = g.d;
-    int nn = 1;
-    for (int a = 0; a < d; ++a) nn *= 3;
+    constexpr int d = D;
+    constexpr int nn = D == 3 ? 27 : 9;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cnt; i += int64_t(gridDim.x) * blockDim.x) {
         const unsigned long long P = nl[i] >> d;
         long long c[3];
-        box_cell(g, L - 1, P, c);
+        box_cell_d<D>(g, L - 1, P, c);
         for (int o = 0; o < nn; ++o) {
             long long c2[3] = {0, 0, 0};
             int r = o;
@@ -352,7 +359,7 @@ __global__ void k_restrict_cands(Geo g, int L, const unsigned long long* __restr
                 if (g.periodic) c2[a] = (c2[a] + dim) % dim;
                 ok &= (c2[a] >= 0 && c2[a] < dim);
             }
-            out[i * nn + o] = ok ? box_key(g, L - 1, c2) : ~0ULL;
+            out[i * nn + o] = ok ? box_key_d<D>(g, L - 1, c2) : ~0ULL;
         }
     }
 }
@@ -383,21 +390,21 @@ struct BoxOut {
     int* colleague;
 };
 
+template <int D>
 __global__ void k_boxes(Geo g, int L, int K, const unsigned long long* __restrict__ keys, int64_t nL, int baseL,
                         const unsigned long long* __restrict__ keysUp, int64_t nUp, int baseUp,
                         const unsigned long long* __restrict__ nlUp, const unsigned long long* __restrict__ nlL,
                         int64_t nnlL, int baseDown, const unsigned long long* __restrict__ skey, int64_t nimg,
                         BoxOut o) {
-    const int d = g.d;
-    int nn = 1;
-    for (int a = 0; a < d; ++a) nn *= 3;
+    constexpr int d = D;
+    constexpr int nn = D == 3 ? 27 : 9;
     const double h = ddiv(g.rc, double(1LL << L));
     const int shift = d * (K - L);
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nL; i += int64_t(gridDim.x) * blockDim.x) {
         const unsigned long long key = keys[i];
         const int64_t b = baseL + i;
         long long c[3] = {0, 0, 0};
-        box_cell(g, L, key, c);
+        box_cell_d<D>(g, L, key, c);
         o.level[b] = L;
         for (int a = 0; a < d; ++a) {
             o.coord[b * d + a] = c[a];
@@ -426,7 +433,7 @@ __global__ void k_boxes(Geo g, int L, int K, const unsigned long long* __restric
             }
             int X = -1;
             if (ok) {
-                const unsigned long long k2 = box_key(g, L, c2);
+                const unsigned long long k2 = box_key_d<D>(g, L, c2);
                 const int64_t x = lower_bound_u64(keys, 0, nL, k2);
                 if (x < nL && keys[x] == k2) X = baseL + int(x);
             }
@@ -916,7 +923,8 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
         GB_ALLOC(cat2, unsigned long long, tot);
         GB_ALLOC(uq, unsigned long long, tot);
         GB_CK(cudaMemcpyAsync(cat, nl[L - 1], nnl[L - 1] * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
-        k_restrict_cands<<<blocks_for(nnl[L]), kThreads, 0, s>>>(geo, L, nl[L], nnl[L], cat + nnl[L - 1]);
+        (d == 3 ? k_restrict_cands<3> : k_restrict_cands<2>)<<<blocks_for(nnl[L]), kThreads, 0, s>>>(
+            geo, L, nl[L], nnl[L], cat + nnl[L - 1]);
         GB_CK(cub::DeviceRadixSort::SortKeys(nullptr, tb, cat, cat2, int(tot), 0, 64, s));
         if (!tmp(tb)) { if (msg) *msg = "device allocation failed (set-up)"; return PDMK_ERR_CUDA; }
         GB_CK(cub::DeviceRadixSort::SortKeys(d_tmp, tb, cat, cat2, int(tot), 0, 64, s));
@@ -966,7 +974,7 @@ int gpu_build_tree(const Geometry& g, int64_t n, int n_s, int max_depth, cudaStr
     }
     for (int L = 0; L < nlev; ++L) {
         const bool has_down = L < int(nl.size());
-        k_boxes<<<blocks_for(nlk[L]), kThreads, 0, s>>>(
+        (d == 3 ? k_boxes<3> : k_boxes<2>)<<<blocks_for(nlk[L]), kThreads, 0, s>>>(
             geo, L, K, lk[L], nlk[L], lstart[L], L > 0 ? lk[L - 1] : nullptr, L > 0 ? nlk[L - 1] : 0,
             L > 0 ? lstart[L - 1] : 0, L > 0 ? nl[L - 1] : nullptr, has_down ? nl[L] : nullptr,
             has_down ? nnl[L] : 0, L + 1 <= nlev ? lstart[std::min(L + 1, nlev)] : 0, skey, nimg, bx);
